@@ -1,0 +1,28 @@
+"""CPU oracle for the encrypted query-point distance path of SANNS
+(arxiv 1904.02033, Sec. 5.3 and Fig. "SANNS linear-scan protocol").
+
+TEST INFRASTRUCTURE ONLY.  Only tests/, __graft_entry__.smoke() and the
+cpu_baseline / reference legs of bench.py may import, call, link or run
+anything in this package.  It shares no code with the CUDA library and never
+imports it; the only thing both sides consume in common is the seeded input
+generator module (paper_1904_02033_b300.inputs), which holds none of the
+method's arithmetic.
+
+Contents
+  sanns_oracle.c  plain C loops: textbook NTT/INTT, ChaCha20 (RFC 8439),
+                  keygen, encrypt, DB encoding, ct x pt MAC, INTT + mask,
+                  the c0 + c1 s step of decryption, schoolbook products.
+  params.py       exact-integer parameter derivation (primes, psi, t, Delta).
+  bfv.py          ctypes wrappers + exact big-integer CRT scale-and-round.
+  select.py       Algorithms 1 and 2 (NaiveTopk, ApproxTopk) in plaintext.
+
+Parity pins: every function above is pinned by a -m "not gpu" test against
+something other than itself (O(N^2) NTT definition, schoolbook products,
+RFC 8439 test vectors, decrypt(encrypt(m)) = m, brute-force distances,
+sympy primality, closed forms for ApproxTopk).  The concrete ciphertext bits
+depend on conventions the paper leaves open (RNG layout, NTT order); those
+are pinned only through the conventions and the round-trip identities --
+"parity unpinned" by a printed value from the paper.
+"""
+from .bfv import Oracle, chacha20_block  # noqa: F401
+from .params import make_params  # noqa: F401

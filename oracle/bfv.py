@@ -1,0 +1,222 @@
+"""The oracle's protocol steps: ctypes calls into the plain C loops plus the
+exact big-integer CRT decryption.
+
+TEST INFRASTRUCTURE ONLY (the oracle): only tests/, __graft_entry__.smoke()
+and bench.py's cpu_baseline leg may import this module.  It never imports the
+CUDA package.
+
+Follows SANNS (arxiv 1904.02033) Sec. 5.3 and Fig. "SANNS linear-scan
+protocol" (Pi_ls) steps 1-4; BFV as in Sec. 2.3 [FV12].
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+
+from . import build as _build
+from .params import Params, make_params
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        _lib = C.CDLL(_build.build())
+        u64p = C.POINTER(C.c_uint64)
+        _lib.oracle_ntt_tables.argtypes = [C.c_uint32, C.c_uint64, C.c_uint64, u64p, u64p]
+        _lib.oracle_ntt.argtypes = [u64p, C.c_uint32, C.c_uint64, u64p]
+        _lib.oracle_intt.argtypes = [u64p, C.c_uint32, C.c_uint64, u64p]
+        _lib.oracle_chacha20_block.argtypes = [C.c_void_p, C.c_uint32, C.c_void_p, C.c_void_p]
+        _lib.oracle_draw128.argtypes = [C.c_uint64, C.c_uint32, C.c_uint64, C.c_uint64, C.c_void_p]
+        _lib.oracle_keygen.argtypes = [C.c_void_p, C.c_uint64, C.c_void_p, C.c_void_p]
+        _lib.oracle_encrypt.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_uint64,
+                                        C.c_uint64, C.c_void_p]
+        _lib.oracle_encode_db.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_uint64,
+                                          C.c_uint64, C.c_uint64, C.c_void_p, C.c_void_p]
+        _lib.oracle_mac.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_uint64, C.c_void_p]
+        _lib.oracle_intt_mask.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_uint64,
+                                          C.c_uint64, C.c_uint64, C.c_uint64, C.c_uint64,
+                                          C.c_void_p, C.c_void_p]
+        _lib.oracle_decrypt_phase.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_uint64,
+                                              C.c_void_p]
+        _lib.oracle_negacyclic_schoolbook.argtypes = [C.c_void_p, C.c_void_p, C.c_uint32,
+                                                      C.c_uint64, C.c_void_p]
+    return _lib
+
+
+def _p(a: np.ndarray):
+    assert a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data_as(C.c_void_p)
+
+
+class _CParams(C.Structure):
+    _fields_ = [("N", C.c_uint32), ("L", C.c_uint32), ("d", C.c_uint32), ("pad", C.c_uint32),
+                ("t", C.c_uint64), ("q", C.c_void_p), ("fwd", C.c_void_p), ("inv", C.c_void_p),
+                ("delta", C.c_void_p)]
+
+
+class Oracle:
+    """One BFV parameter set with its twiddle tables, for the C loops."""
+
+    def __init__(self, N: int, L: int, prime_bits: int, t_rule: int, d: int):
+        self.P: Params = make_params(N, L, prime_bits, t_rule, d)
+        P = self.P
+        self.N, self.L, self.d, self.t = N, L, d, P.t
+        self.q = np.array(P.q, dtype=np.uint64)
+        self.delta = np.array(P.delta_mod_q, dtype=np.uint64)
+        self.fwd = np.zeros((L, N), dtype=np.uint64)
+        self.inv = np.zeros((L, N), dtype=np.uint64)
+        for j in range(L):
+            f = self.fwd[j]
+            v = self.inv[j]
+            lib().oracle_ntt_tables(N, int(self.q[j]), P.psi[j],
+                                    f.ctypes.data_as(C.POINTER(C.c_uint64)),
+                                    v.ctypes.data_as(C.POINTER(C.c_uint64)))
+        self._c = _CParams(N, L, d, 0, P.t, _p(self.q).value, _p(self.fwd).value,
+                           _p(self.inv).value, _p(self.delta).value)
+
+    # ---------------- transforms ----------------
+    def ntt(self, a: np.ndarray, j: int) -> np.ndarray:
+        a = np.ascontiguousarray(a, dtype=np.uint64).copy()
+        lib().oracle_ntt(a.ctypes.data_as(C.POINTER(C.c_uint64)), self.N, int(self.q[j]),
+                         self.fwd[j].ctypes.data_as(C.POINTER(C.c_uint64)))
+        return a
+
+    def intt(self, a: np.ndarray, j: int) -> np.ndarray:
+        a = np.ascontiguousarray(a, dtype=np.uint64).copy()
+        lib().oracle_intt(a.ctypes.data_as(C.POINTER(C.c_uint64)), self.N, int(self.q[j]),
+                          self.inv[j].ctypes.data_as(C.POINTER(C.c_uint64)))
+        return a
+
+    def schoolbook(self, a: np.ndarray, b: np.ndarray, j: int) -> np.ndarray:
+        a = np.ascontiguousarray(a, dtype=np.uint64)
+        b = np.ascontiguousarray(b, dtype=np.uint64)
+        out = np.zeros(self.N, dtype=np.uint64)
+        lib().oracle_negacyclic_schoolbook(_p(a), _p(b), self.N, int(self.q[j]), _p(out))
+        return out
+
+    # ---------------- protocol steps ----------------
+    def keygen(self, seed: int):
+        s = np.zeros(self.N, dtype=np.int8)
+        s_hat = np.zeros((self.L, self.N), dtype=np.uint64)
+        lib().oracle_keygen(C.byref(self._c), seed, _p(s), _p(s_hat))
+        return s, s_hat
+
+    def encrypt(self, s_hat: np.ndarray, qv: np.ndarray, seed: int, qid: int) -> np.ndarray:
+        qv = np.ascontiguousarray(qv, dtype=np.uint8)
+        assert qv.shape == (self.d,)
+        ct = np.zeros((self.d, 2, self.L, self.N), dtype=np.uint64)
+        lib().oracle_encrypt(C.byref(self._c), _p(np.ascontiguousarray(s_hat)), _p(qv),
+                             seed, qid, _p(ct))
+        return ct
+
+    def blocks(self, n: int) -> int:
+        return (n + self.N - 1) // self.N
+
+    def encode_db(self, coords: np.ndarray, perm: np.ndarray | None, k0: int = 0,
+                  k1: int | None = None):
+        coords = np.ascontiguousarray(coords, dtype=np.uint8)
+        n = coords.shape[0] if perm is None else len(perm)
+        if perm is None:
+            perm = np.arange(n, dtype=np.uint32)
+        perm = np.ascontiguousarray(perm, dtype=np.uint32)
+        k1 = self.blocks(n) if k1 is None else k1
+        nk = k1 - k0
+        pt = np.zeros((nk, self.L, self.d, self.N), dtype=np.uint64)
+        norms = np.zeros(nk * self.N, dtype=np.uint32)
+        lib().oracle_encode_db(C.byref(self._c), _p(coords), _p(perm), n, k0, k1,
+                               _p(pt), _p(norms))
+        return pt, norms
+
+    def mac(self, ct: np.ndarray, pt: np.ndarray) -> np.ndarray:
+        nk = pt.shape[0]
+        acc = np.zeros((nk, 2, self.L, self.N), dtype=np.uint64)
+        lib().oracle_mac(C.byref(self._c), _p(np.ascontiguousarray(ct)),
+                         _p(np.ascontiguousarray(pt)), nk, _p(acc))
+        return acc
+
+    def intt_mask(self, acc: np.ndarray, norms: np.ndarray, n: int, k0: int, k1: int,
+                  mask_seed: int, qid: int):
+        out = np.zeros_like(acc)
+        cnt = max(0, min(n, k1 * self.N) - k0 * self.N)
+        share = np.zeros(cnt, dtype=np.uint32)
+        lib().oracle_intt_mask(C.byref(self._c), _p(np.ascontiguousarray(acc)),
+                               _p(np.ascontiguousarray(norms, dtype=np.uint32)),
+                               n, k0, k1, mask_seed, qid, _p(out), _p(share))
+        return out, share
+
+    def distances(self, ct: np.ndarray, coords: np.ndarray, perm, mask_seed: int, qid: int,
+                  k0: int = 0, k1: int | None = None):
+        """Pi_ls step 3 for blocks [k0, k1): encode, MAC, INTT, mask."""
+        n = coords.shape[0] if perm is None else len(perm)
+        k1 = self.blocks(n) if k1 is None else k1
+        pt, norms = self.encode_db(coords, perm, k0, k1)
+        acc = self.mac(ct, pt)
+        return self.intt_mask(acc, norms, n, k0, k1, mask_seed, qid)
+
+    def decrypt_phase(self, ct_out: np.ndarray, s: np.ndarray) -> np.ndarray:
+        nk = ct_out.shape[0]
+        v = np.zeros((nk, self.L, self.N), dtype=np.uint64)
+        lib().oracle_decrypt_phase(C.byref(self._c), _p(np.ascontiguousarray(ct_out)),
+                                   _p(np.ascontiguousarray(s, dtype=np.int8)), nk, _p(v))
+        return v
+
+    def scale_round(self, v: np.ndarray) -> np.ndarray:
+        """BFV decryption's last step with exact integers: CRT the residues to
+        w in [0, Q), then m = floor((t w + floor(Q/2)) / Q) mod t."""
+        P = self.P
+        Q, t = P.Q, P.t
+        coef = []
+        for qj in P.q:
+            Qj = Q // qj
+            coef.append(Qj * pow(Qj, -1, qj) % Q)
+        flat = v.reshape(-1, self.L, self.N) if v.ndim == 3 else v
+        nk = flat.shape[0]
+        out = np.zeros(nk * self.N, dtype=np.int64)
+        half = Q // 2
+        for k in range(nk):
+            cols = [flat[k, j].tolist() for j in range(self.L)]
+            for x in range(self.N):
+                w = sum(int(cols[j][x]) * coef[j] for j in range(self.L)) % Q
+                out[k * self.N + x] = ((t * w + half) // Q) % t
+        return out
+
+    def noise_ok(self, v: np.ndarray, m: np.ndarray) -> bool:
+        """Check |w - Delta m| < Delta / 4 for every coefficient (decryption
+        margin): the rounding above is then unambiguous."""
+        P = self.P
+        Q = P.Q
+        coef = [(Q // qj) * pow(Q // qj, -1, qj) % Q for qj in P.q]
+        nk = v.shape[0]
+        lim = P.delta // 4
+        for k in range(nk):
+            cols = [v[k, j].tolist() for j in range(self.L)]
+            for x in range(self.N):
+                w = sum(int(cols[j][x]) * coef[j] for j in range(self.L)) % Q
+                e = (w - P.delta * int(m[k * self.N + x])) % Q
+                if min(e, Q - e) >= lim:
+                    return False
+        return True
+
+    def decrypt_shares(self, ct_out: np.ndarray, s: np.ndarray, qv: np.ndarray, n: int):
+        """Pi_ls step 4 plus the client's local term: sigma_C = m + ||q||^2 mod t
+        for the first n positions."""
+        v = self.decrypt_phase(ct_out, s)
+        m = self.scale_round(v)[:n]
+        qn = int(np.sum(np.asarray(qv, dtype=np.int64) ** 2))
+        return ((m + qn) % self.t).astype(np.uint32)
+
+    def draw128(self, seed: int, purpose: int, obj: int, c: int):
+        out = np.zeros(2, dtype=np.uint64)
+        lib().oracle_draw128(seed, purpose, obj, c, _p(out))
+        return int(out[0]), int(out[1])
+
+
+def chacha20_block(key_words, counter: int, nonce_words):
+    key = np.array(key_words, dtype=np.uint32)
+    nonce = np.array(nonce_words, dtype=np.uint32)
+    out = np.zeros(16, dtype=np.uint32)
+    lib().oracle_chacha20_block(_p(key), counter, _p(nonce), _p(out))
+    return out

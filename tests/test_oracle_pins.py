@@ -1,0 +1,314 @@
+"""Pins for the CPU oracle: each test checks the oracle against something other
+than itself -- a definition evaluated independently, a library routine, a
+published test vector or value, or an identity the method must satisfy.
+"""
+import math
+import os
+import random
+
+import numpy as np
+import pytest
+import sympy
+
+from oracle import chacha20_block
+from oracle.bfv import Oracle
+from oracle.params import make_params, ntt_primes, plain_modulus, min_primitive_root_2n
+from oracle import select
+from paper_1904_02033_b300 import inputs
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ---------------------------------------------------------------- params
+@pytest.mark.parametrize("N,L,bits", [(4096, 2, 54), (8192, 3, 60), (256, 2, 40), (64, 3, 30)])
+def test_primes_are_the_largest_ntt_primes(N, L, bits):
+    qs = ntt_primes(N, L, bits)
+    assert qs == sorted(qs, reverse=True) and len(set(qs)) == L
+    for q in qs:
+        assert sympy.isprime(q) and q % (2 * N) == 1 and q < 2 ** bits
+    # nothing skipped: every candidate = 1 mod 2N between q_L and 2^bits
+    # that is not in the list is composite (sympy decides)
+    x = qs[-1]
+    while x < 2 ** bits:
+        if x not in qs:
+            assert not sympy.isprime(x)
+        x += 2 * N
+
+
+def test_ntt_primes_match_printed_modulus_size():
+    # Sec. 7.1: N = 2^13 and a 180-bit modulus q made of three RNS words
+    P = make_params(8192, 3, 60, 0, 128)
+    assert P.Q.bit_length() == 180
+
+
+@pytest.mark.parametrize("N,bits", [(8, 20), (16, 30), (64, 40), (256, 54)])
+def test_psi_is_the_smallest_primitive_root(N, bits):
+    q = ntt_primes(N, 1, bits)[0]
+    psi = min_primitive_root_2n(q, N)
+    assert pow(psi, N, q) == q - 1
+    if N <= 16:
+        # brute force over all residues for tiny q is too big; instead compare
+        # with sympy's full list of N-th roots of -1
+        roots = sympy.nthroot_mod(q - 1, N, q, all_roots=True)
+        assert psi == min(roots)
+
+
+def test_plain_modulus_paper_rule_matches_printed_t():
+    # Sec. 7.1 prints t = 2^23 (SIFT, Deep1B) and t = 2^24 (Amazon); the rule
+    # b_d = 2 b_c + ceil(log2 d) comes from Fig. "hyperparameters".
+    rows = [l.split() for l in open(os.path.join(GOLD, "paper_comm_bytes.txt"))
+            if l.strip() and not l.startswith("#")]
+    trows = [r for r in rows if len(r) == 4 and r[1] in ("8", "9")]
+    assert len(trows) == 3
+    for name, b_c, d, t in trows:
+        assert plain_modulus(8192, 1, int(d), int(b_c)) == int(t), name
+
+
+def test_plain_modulus_prime_rule():
+    for N in (4096, 8192):
+        t = plain_modulus(N, 0, 128)
+        assert sympy.isprime(t) and t % (2 * N) == 1 and t > 2 ** 24
+        x = 2 ** 24 + 1
+        while x < t:
+            if x % (2 * N) == 1:
+                assert not sympy.isprime(x)
+            x += 1 if x % (2 * N) != 1 else 2 * N
+    # every squared distance of 8-bit points fits below t, so the shares
+    # reconstruct the exact integer (Sec. 5.3)
+    assert 128 * 255 ** 2 < plain_modulus(8192, 0, 128)
+
+
+def test_ciphertext_layout_reproduces_paper_communication():
+    # d query ciphertexts + ceil(n/N) response ciphertexts, each 2 polys x
+    # 3 RNS words x N coefficients x 8 bytes, equals the printed MB figures.
+    rows = [l.split() for l in open(os.path.join(GOLD, "paper_comm_bytes.txt"))
+            if l.strip() and not l.startswith("#")]
+    crow = [r for r in rows if len(r) == 4 and "." in r[3] or r[3] == "518"]
+    assert len(crow) == 4
+    N, L = 8192, 3
+    for name, n, d, mb in crow:
+        n, d = int(n), int(d)
+        K = -(-n // N)
+        ct_in = d * 2 * L * N * 8
+        ct_out = K * 2 * L * N * 8
+        got = (ct_in + ct_out) / 1e6
+        digits = len(mb.replace(".", "").lstrip("0"))
+        assert float(f"{got:.{digits}g}") == float(mb), (name, got, mb)
+
+
+# ---------------------------------------------------------------- ChaCha20
+def test_chacha20_rfc8439_block_vector():
+    kv = {}
+    for line in open(os.path.join(GOLD, "chacha20_rfc8439.txt")):
+        if line.strip() and not line.startswith("#"):
+            k, *v = line.split()
+            kv[k] = v
+    key = [int(w, 16) for w in kv["key_words"]]
+    nonce = [int(w, 16) for w in kv["nonce_words"]]
+    out = chacha20_block(key, int(kv["counter"][0]), nonce)
+    assert out.astype("<u4").tobytes().hex() == kv["block"][0]
+
+
+# ---------------------------------------------------------------- NTT
+def _ntt_definition(a, q, psi):
+    """O(N^2) definition of the convention: slot s holds a(psi^(2 brv(s)+1))."""
+    N = len(a)
+    logn = N.bit_length() - 1
+    out = []
+    for s in range(N):
+        r = int(format(s, f"0{logn}b")[::-1], 2) if logn else 0
+        x = pow(psi, 2 * r + 1, q)
+        acc = 0
+        for c in reversed(a):
+            acc = (acc * x + int(c)) % q
+        out.append(acc)
+    return out
+
+
+def _negacyclic(a, b, q):
+    N = len(a)
+    out = [0] * N
+    for i in range(N):
+        for j in range(N):
+            k = i + j
+            p = int(a[i]) * int(b[j])
+            if k < N:
+                out[k] += p
+            else:
+                out[k - N] -= p
+    return [v % q for v in out]
+
+
+@pytest.mark.parametrize("N,bits", [(8, 20), (16, 30), (64, 54), (256, 60)])
+def test_ntt_matches_definition_and_inverts(N, bits):
+    O = Oracle(N, 2, bits, 0, 4)
+    rnd = np.random.default_rng(N)
+    for j in range(2):
+        q = int(O.q[j])
+        for case in range(3):
+            if case == 0:
+                a = rnd.integers(0, q, size=N, dtype=np.uint64)
+            elif case == 1:
+                a = np.full(N, q - 1, dtype=np.uint64)
+            else:
+                a = np.zeros(N, dtype=np.uint64)
+                a[rnd.integers(0, N)] = rnd.integers(1, q)
+            f = O.ntt(a, j)
+            assert [int(v) for v in f] == _ntt_definition(a, q, O.P.psi[j])
+            assert np.array_equal(O.intt(f, j), a)
+
+
+@pytest.mark.parametrize("N,bits", [(8, 20), (32, 54), (128, 60)])
+def test_ntt_product_is_negacyclic_product(N, bits):
+    O = Oracle(N, 1, bits, 0, 4)
+    q = int(O.q[0])
+    rnd = np.random.default_rng(7)
+    a = rnd.integers(0, q, size=N, dtype=np.uint64)
+    b = rnd.integers(0, q, size=N, dtype=np.uint64)
+    fa, fb = O.ntt(a, 0), O.ntt(b, 0)
+    prod = np.array([(int(x) * int(y)) % q for x, y in zip(fa, fb)], dtype=np.uint64)
+    got = O.intt(prod, 0)
+    want = _negacyclic(a, b, q)
+    assert [int(v) for v in got] == want
+    assert [int(v) for v in O.schoolbook(a, b, 0)] == want
+
+
+# ---------------------------------------------------------------- BFV
+def _small():
+    return Oracle(256, 2, 40, 0, 5)
+
+
+def test_keygen_is_ternary_and_ntt_of_s():
+    O = _small()
+    s, s_hat = O.keygen(seed=3)
+    assert set(np.unique(s)).issubset({-1, 0, 1})
+    counts = np.bincount(s.astype(np.int64) + 1, minlength=3)
+    assert counts.min() > 256 / 3 * 0.6
+    for j in range(O.L):
+        q = int(O.q[j])
+        lifted = [(int(v) % q) for v in s]
+        assert [int(v) for v in s_hat[j]] == _ntt_definition(lifted, q, O.P.psi[j])
+
+
+def test_decrypt_of_encrypt_is_the_constant_plaintext():
+    O = _small()
+    s, s_hat = O.keygen(seed=1)
+    qv = np.array([0, 1, 7, 128, 255], dtype=np.uint8)
+    ct = O.encrypt(s_hat, qv, seed=11, qid=5)
+    # back to coefficient form, then decrypt each coordinate's ciphertext
+    ctc = np.zeros_like(ct)
+    for i in range(O.d):
+        for c in range(2):
+            for j in range(O.L):
+                ctc[i, c, j] = O.intt(ct[i, c, j], j)
+    v = O.decrypt_phase(ctc, s)
+    m = O.scale_round(v).reshape(O.d, O.N)
+    for i in range(O.d):
+        want = np.zeros(O.N, dtype=np.int64)
+        want[0] = (O.t - 2 * int(qv[i])) % O.t
+        assert np.array_equal(m[i], want)
+    assert O.noise_ok(v, m.reshape(-1))
+    # c1 is not a constant: the ciphertext actually hides the message
+    assert len(np.unique(ct[0, 1, 0])) > O.N // 2
+
+
+def _distances_case(O, n, seed, perm=True, qid=9):
+    coords = inputs.uniform_coords(n, O.d, seed)
+    qv = inputs.uniform_coords(1, O.d, seed + 1)[0]
+    pm = inputs.permutation(n, seed + 2) if perm else None
+    s, s_hat = O.keygen(seed=seed + 3)
+    ct = O.encrypt(s_hat, qv, seed=seed + 4, qid=qid)
+    out, srv = O.distances(ct, coords, pm, mask_seed=seed + 5, qid=qid)
+    cli = O.decrypt_shares(out, s, qv, n)
+    order = np.arange(n) if pm is None else pm
+    brute = np.sum((coords[order].astype(np.int64) - qv.astype(np.int64)) ** 2, axis=1)
+    return cli, srv, brute
+
+
+@pytest.mark.parametrize("n", [1, 255, 256, 600])
+def test_shares_reconstruct_bruteforce_distances(n):
+    """Sec. 5.3: sum_i f_i g_i holds <q, p_j> in coefficient j; with the
+    client's -2 factor, the server's ||p||^2 and the mask the two shares add
+    up to ||q - p||^2 mod t, and t exceeds every such distance."""
+    O = _small()
+    cli, srv, brute = _distances_case(O, n, seed=n)
+    assert np.array_equal((cli.astype(np.int64) + srv) % O.t, brute)
+    if n > 16:
+        # the mask hides the distances: the client share alone is not them
+        assert np.mean(cli.astype(np.int64) == brute) < 0.1
+
+
+def test_shares_at_small_config_scale():
+    """N = 4096, two 54-bit primes, d = 32, n = 4096 (one block)."""
+    O = Oracle(4096, 2, 54, 0, 32)
+    cli, srv, brute = _distances_case(O, 4096, seed=0)
+    assert np.array_equal((cli.astype(np.int64) + srv) % O.t, brute)
+
+
+def test_shares_with_paper_power_of_two_t():
+    O = Oracle(256, 3, 60, 1, 5)
+    assert O.t == 2 ** 19
+    cli, srv, brute = _distances_case(O, 300, seed=4)
+    assert np.array_equal((cli.astype(np.int64) + srv) % O.t, brute)
+
+
+def test_block_ranges_compose():
+    O = _small()
+    n = 700
+    coords = inputs.uniform_coords(n, O.d, 1)
+    s, s_hat = O.keygen(seed=2)
+    qv = inputs.uniform_coords(1, O.d, 3)[0]
+    ct = O.encrypt(s_hat, qv, seed=4, qid=1)
+    full, srv = O.distances(ct, coords, None, 5, 1)
+    parts = [O.distances(ct, coords, None, 5, 1, k0=k, k1=k + 1) for k in range(3)]
+    assert np.array_equal(np.concatenate([p[0] for p in parts]), full)
+    assert np.array_equal(np.concatenate([p[1] for p in parts]), srv)
+
+
+# ---------------------------------------------------------------- selection
+def test_naive_topk_is_sorted_selection():
+    rnd = random.Random(5)
+    for _ in range(20):
+        n = rnd.randint(1, 60)
+        k = rnd.randint(1, 12)
+        vals = [rnd.randint(0, 9) for _ in range(n)]
+        ids = list(range(100, 100 + n))
+        opt, idl = select.naive_topk(vals, ids, k)
+        ev, ei = select.exact_topk(np.array(vals), np.array(ids), k)
+        m = min(n, k)
+        # the values are unique; under ties Algorithm 1 may order equal
+        # values differently, so check the ids form a valid selection
+        assert opt[:m] == ev
+        assert len(set(idl[:m])) == m
+        assert all(vals[i - 100] == v for i, v in zip(idl[:m], opt[:m]))
+        if len(set(vals)) == n:
+            assert idl[:m] == ei
+
+
+def test_approx_topk_with_one_bin_per_element_is_exact():
+    rnd = np.random.default_rng(1)
+    v = rnd.integers(0, 1000, size=200)
+    ids = np.arange(200)
+    assert select.approx_topk(v, ids, 10, 200) == select.exact_topk(v, ids, 10)
+
+
+def test_approx_topk_expected_hits_closed_forms():
+    # independent-bins model of the Theorem 1 proof: l (1 - (1 - 1/l)^k);
+    # with fixed bins the hypergeometric value is close to it for large n
+    n, k, l = 10 ** 6, 10, 7813
+    indep = l * (1 - (1 - 1 / l) ** k)
+    fixed = select.expected_hits(n, k, l)
+    assert abs(indep - fixed) < 1e-3
+    assert 9.99 < fixed < 10
+    # Monte Carlo on a small case
+    n, k, l = 2000, 10, 40
+    rnd = np.random.default_rng(0)
+    v = np.arange(n)
+    hits = []
+    for _ in range(400):
+        pm = rnd.permutation(n)
+        vals = v[pm]
+        _, got = select.approx_topk(vals, pm, k, l)
+        hits.append(len(set(got) & set(range(k))))
+    want = select.expected_hits(n, k, l)
+    assert abs(np.mean(hits) - want) < 4 * np.std(hits) / math.sqrt(len(hits)) + 0.02
