@@ -1,0 +1,362 @@
+"""Benchmark of the encrypted query-point distance step (SANNS linear scan).
+
+One step = the server's whole distance computation for one encrypted query
+against the resident encoded database: ct x pt MAC over all d dimensions
+(K2), then INTT + ||p||^2 + mask (K1/K3).  Workload: n = 1,000,000 points,
+d = 128, uint8 coordinates from a 64-component Gaussian mixture (sigma = 20),
+BFV N = 8192 with three 60-bit RNS primes, t = the smallest prime > 2^24 that
+is 1 mod 2N; 100 queries from the same mixture, one per step, cycled.
+
+Prints one JSON line.  `value` is query-point distances per second with all
+inputs resident in HBM; `e2e` is the same metric through the C-ABI call with
+the query ciphertext copied from pinned host memory and the response
+ciphertexts plus the server share copied back, inside the timed region.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl sanns|reference]
+
+--impl reference times the CPU oracle (the plain C loops under oracle/) on a
+bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = dict(n=1_000_000, d=128, N=8192, L=3, prime_bits=60, t_rule=0, n_comp=64,
+                sigma=20.0, n_queries=100, seed=0)
+METRIC = "encrypted query-point distances/s (bit-exact, plain per-query path)"
+UNIT = "qp/s"
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6400.0, "fallback"
+
+
+def _env_rank():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines: list[str] = []
+        self.t = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        if self.t:
+            self.t.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _roofline_bytes(W) -> dict:
+    """Algorithmic HBM bytes of one MAC launch for one query: the encoded
+    database once (K L d N 8), the query ciphertext once (d 2 L N 8) and the
+    accumulator output (K 2 L N 8)."""
+    K = -(-W["n"] // W["N"])
+    pt = K * W["L"] * W["d"] * W["N"] * 8
+    ct = W["d"] * 2 * W["L"] * W["N"] * 8
+    out = K * 2 * W["L"] * W["N"] * 8
+    return {"pt": pt, "ct": ct, "out": out, "total": pt + ct + out, "K": K}
+
+
+def run_gpu(args) -> None:
+    import torch
+
+    from paper_1904_02033_b300 import inputs
+    from paper_1904_02033_b300 import sanns as S
+
+    rank, world, local = _env_rank()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    W = WORKLOAD
+    n, d, N, L = W["n"], W["d"], W["N"], W["L"]
+    ctx = S.sanns_ctx_create(N, L, W["prime_bits"], W["t_rule"], d)
+    # every rank holds its own full database and query stream (weak scaling)
+    coords = inputs.mixture_coords(n, d, W["n_comp"], W["sigma"], W["seed"] + 1000 * rank,
+                                   means_seed=W["seed"])
+    queries = inputs.mixture_coords(W["n_queries"], d, W["n_comp"], W["sigma"],
+                                    W["seed"] + 1 + 1000 * rank, means_seed=W["seed"])
+    perm = inputs.permutation(n, W["seed"] + 2 + rank)
+    sk = S.sanns_keygen(ctx, W["seed"] + 3)
+    db = S.sanns_encode_db(ctx, torch.from_numpy(coords).cuda(), torch.from_numpy(perm).cuda())
+    qdev = torch.from_numpy(queries).cuda()
+    qids = torch.arange(W["n_queries"], dtype=torch.int64).to(torch.uint64).cuda()
+    ct_all = S.sanns_encrypt_query(ctx, sk, qdev, W["seed"] + 4, qids)
+    K = db.K
+    ct_out = torch.empty((1, K, 2, L, N), dtype=torch.uint64, device="cuda")
+    srv = torch.empty((1, n), dtype=torch.uint32, device="cuda")
+    stream = torch.cuda.current_stream()
+    mask_seed = W["seed"] + 5
+
+    def step(s):
+        qi = s % W["n_queries"]
+        S.sanns_distances_mac(ctx, db, ct_all[qi:qi + 1], ct_out, stream=stream)
+        mac_end[s].record(stream)
+        S.sanns_distances_finish(ctx, db, ct_out, mask_seed, qids[qi:qi + 1], srv, stream=stream)
+
+    total_steps = args.warmup + args.steps
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(total_steps)]
+    mac_end = [torch.cuda.Event(enable_timing=True) for _ in range(total_steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(total_steps)]
+    for s in range(args.warmup):
+        starts[s].record(stream)
+        step(s)
+        ends[s].record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.4)
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    t0.record(stream)
+    for s in range(args.warmup, total_steps):
+        starts[s].record(stream)
+        step(s)
+        ends[s].record(stream)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    ck = clocks.stop()
+    ms = t0.elapsed_time(t1)
+    if dist:
+        tt = torch.tensor([ms], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+    timed = range(args.warmup, total_steps)
+    lat = sorted(starts[s].elapsed_time(ends[s]) for s in timed)
+    mac_ms = [starts[s].elapsed_time(mac_end[s]) for s in timed]
+    mac_avg = sum(mac_ms) / len(mac_ms)
+
+    # end-to-end through the C ABI: pinned host ct in, response + share out
+    ct_host = ct_all[: min(4, W["n_queries"])].cpu().pin_memory()
+    out_host = torch.empty((1, K, 2, L, N), dtype=torch.uint64).pin_memory()
+    srv_host = torch.empty((1, n), dtype=torch.uint32).pin_memory()
+    ct_dev = torch.empty((1, d, 2, L, N), dtype=torch.uint64, device="cuda")
+    e2e_steps = max(3, min(args.steps, 10))
+
+    def e2e_step(s):
+        qi = s % ct_host.shape[0]
+        ct_dev.copy_(ct_host[qi:qi + 1], non_blocking=True)
+        S.sanns_distances(ctx, db, ct_dev, mask_seed, qids[qi:qi + 1], ct_out, srv, stream=stream)
+        out_host.copy_(ct_out, non_blocking=True)
+        srv_host.copy_(srv, non_blocking=True)
+
+    for s in range(2):
+        e2e_step(s)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for s in range(e2e_steps):
+        e2e_step(s)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1) / e2e_steps
+    if dist:
+        tt = torch.tensor([e2e_ms], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e_ms = float(tt.item())
+
+    rb = _roofline_bytes(W)
+    peak, peak_kind = _peaks()
+    achieved = rb["total"] / (mac_avg * 1e-3) / 1e9
+    ms_step = ms / args.steps
+    value = world * n * args.steps / (ms * 1e-3)
+    cpu = None
+    if rank == 0:
+        cpu = cpu_baseline(quick=args.quick_cpu)
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": {"workload": f"linear scan, 1 query per step: n={n:,} d=128 uint8 "
+                                   "64-component Gaussian mixture (sigma 20); BFV N=8192, three "
+                                   "60-bit primes, t=16957441",
+                       "n": n, "d": d, "N": N, "L": L, "K": K, "queries_cycled": W["n_queries"],
+                       "parallelism": f"replicas{world}" if world > 1 else "single",
+                       "l2": "inputs larger than L2: the 3.1 GB encoded database is streamed "
+                             "from HBM every step"},
+            "latency_ms": {"p50": lat[len(lat) // 2],
+                           "p99": lat[min(len(lat) - 1, int(round(0.99 * (len(lat) - 1))))]},
+            "roofline": {"kernel": "mac_kernel (K2 ct x pt MAC)", "bound": "hbm",
+                         "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "peak_source": peak_kind,
+                         "traffic": None, "algorithmic_bytes": rb["total"],
+                         "launch_ms": mac_avg},
+            "e2e": {"value": world * n / (e2e_ms * 1e-3), "unit": UNIT,
+                    "h2d_bytes_per_step": d * 2 * L * N * 8,
+                    "d2h_bytes_per_step": K * 2 * L * N * 8 + n * 4, "ms_per_step": e2e_ms},
+            "gpu_launches": 2 * args.steps,
+            "clocks": ck,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def _oracle_sample(n_blocks: int, n_queries: int):
+    """Oracle setup for a bounded sample of the workload: the first n_blocks
+    blocks of the database and n_queries encrypted queries."""
+    from oracle.bfv import Oracle
+    from paper_1904_02033_b300 import inputs
+
+    W = WORKLOAD
+    O = Oracle(W["N"], W["L"], W["prime_bits"], W["t_rule"], W["d"])
+    npts = n_blocks * W["N"]
+    coords = inputs.mixture_coords(npts, W["d"], W["n_comp"], W["sigma"], W["seed"] + 1,
+                                   means_seed=W["seed"])
+    queries = inputs.mixture_coords(n_queries, W["d"], W["n_comp"], W["sigma"], W["seed"] + 1,
+                                    means_seed=W["seed"])
+    _, s_hat = O.keygen(W["seed"] + 3)
+    cts = [O.encrypt(s_hat, queries[i], W["seed"] + 4, i) for i in range(n_queries)]
+    pt, norms = O.encode_db(coords, None)
+    return O, pt, norms, cts, npts
+
+
+def cpu_baseline(quick: bool = False) -> dict:
+    """Time the oracle (single thread, as it stands) on a bounded sample: the
+    MAC + INTT + mask of `blocks` database blocks for `queries` queries, with
+    the sample's plaintexts encoded beforehand (untimed, like the resident
+    database on the GPU)."""
+    blocks, queries = (2, 1) if quick else (40, 2)
+    O, pt, norms, cts, npts = _oracle_sample(blocks, queries)
+    t0 = time.perf_counter()
+    for ct in cts:
+        acc = O.mac(ct, pt)
+        O.intt_mask(acc, norms, npts, 0, blocks, WORKLOAD["seed"] + 5, 0)
+    dt = time.perf_counter() - t0
+    qp = npts * queries
+    return {"value": qp / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{queries} queries x {blocks} blocks of 8192 points (d=128, N=8192, L=3): "
+                      f"MAC + INTT + mask, {dt:.1f} s"}
+
+
+def run_reference(args) -> None:
+    rank, world, _ = _env_rank()
+    if rank != 0:
+        return
+    blocks = 4
+    O, pt, norms, cts, npts = _oracle_sample(blocks, 1)
+    ct = cts[0]
+
+    def step():
+        acc = O.mac(ct, pt)
+        O.intt_mask(acc, norms, npts, 0, blocks, WORKLOAD["seed"] + 5, 0)
+
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    dt = time.perf_counter() - t0
+    value = npts * args.steps / dt
+    sample = f"per step 1 query x {blocks} blocks of 8192 points (d=128, N=8192, L=3): MAC + INTT + mask"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
+        "data": "synthetic",
+        "config": {"workload": "linear scan, 1 query per step: n=1,000,000 d=128 uint8 "
+                               "64-component Gaussian mixture (sigma 20); BFV N=8192, three "
+                               "60-bit primes, t=16957441 (CPU oracle on a bounded sample)"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="sanns", choices=["sanns", "reference"])
+    ap.add_argument("--quick-cpu", action="store_true", help="smaller CPU baseline sample")
+    ap.add_argument("--n", type=int, default=None,
+                    help="smaller database (profiling captures); the line then names it")
+    ap.add_argument("--queries", type=int, default=None, help="number of distinct queries")
+    args = ap.parse_args()
+    if args.n is not None:
+        WORKLOAD["n"] = args.n
+    if args.queries is not None:
+        WORKLOAD["n_queries"] = args.queries
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

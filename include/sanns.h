@@ -1,0 +1,182 @@
+/*
+ * sanns.h -- C ABI of libsanns.so, the B300 (sm_103a) implementation of the
+ * server-side hot path of SANNS (Chen et al., "SANNS: Scaling Up Secure
+ * Approximate k-Nearest Neighbors Search", arxiv 1904.02033): homomorphic
+ * evaluation of query-to-point squared distances under RNS BFV.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Buffers named *_dev are device memory of the current CUDA device (for
+ *   instance a torch tensor's data_ptr()); *_host are host memory; "any" means
+ *   either (copied with cudaMemcpyDefault).  The caller owns every buffer it
+ *   passes; opaque handles (sanns_ctx, sanns_sk, sanns_db, sanns_clusters) are
+ *   owned by the library and released with the matching sanns_*_free.
+ * - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *   Calls enqueue work on it and return without synchronising unless stated;
+ *   buffers must stay alive until the stream has passed the call.
+ * - Residues are uint64 in [0, q_j).  Ciphertext polynomials are laid out
+ *   [..][2][L][N]: component c0/c1, prime j, coefficient/slot.  "NTT form"
+ *   means slot s holds the evaluation at psi_j^(2 brv(s) + 1).
+ * - Every call returns SANNS_OK (0) or a negative code; the message of the
+ *   last failure on the calling thread is sanns_last_error().  Arguments are
+ *   validated on the host before anything is launched; an invalid argument
+ *   launches nothing.
+ *
+ * Readings of the paper that fix the exact bits (the paper leaves them to
+ * SEAL): primes = the L largest primes below 2^prime_bits that are 1 mod 2N;
+ * psi_j = the smallest primitive 2N-th root of unity; Delta = floor(Q/t);
+ * randomness = ChaCha20 (RFC 8439) streams keyed by a 64-bit seed.
+ */
+#ifndef SANNS_H_
+#define SANNS_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SANNS_OK 0
+#define SANNS_EINVAL (-1)   /* bad shape, parameter or pointer */
+#define SANNS_ENOMEM (-2)   /* device allocation failed */
+#define SANNS_ECUDA (-3)    /* a CUDA call failed; see sanns_last_error() */
+#define SANNS_ETIMEOUT (-4) /* a bounded device-side wait gave up */
+
+typedef struct sanns_ctx sanns_ctx;
+typedef struct sanns_sk sanns_sk;
+typedef struct sanns_db sanns_db;
+typedef struct sanns_clusters sanns_clusters;
+
+/*
+ * BFV parameters (Sec. 7.1 "Parameter choices": N = 2^13, 180-bit q as three
+ * machine words, t = 2^b_d; Fig. "hyperparameters": b_d = 2 b_c + ceil(log2 d)).
+ *   N           ring degree, a power of two in [64, 16384]
+ *   L           number of RNS primes, 1..4
+ *   prime_bits  bit size of each prime, 20..60
+ *   t_rule      0: t = smallest prime > 2^24 with t = 1 mod 2N;
+ *               1: t = 2^(2 b_c + ceil(log2 d)) as in the paper
+ *   d           vector dimension, 1..224
+ *   b_c         coordinate bits for t_rule 1 (coordinates are uint8 here)
+ */
+typedef struct {
+  uint32_t N, L, prime_bits, t_rule, d, b_c;
+} sanns_params;
+
+const char *sanns_last_error(void);
+
+/* Derive primes, psi, t, Delta and the twiddle tables; upload them to the
+ * current device.  Synchronous.  *out is NULL on failure. */
+int sanns_ctx_create(const sanns_params *params, sanns_ctx **out);
+void sanns_ctx_free(sanns_ctx *ctx);
+/* Read back derived values (host arrays of L entries; any pointer may be
+ * NULL). */
+int sanns_ctx_query(const sanns_ctx *ctx, uint64_t *q_host, uint64_t *psi_host, uint64_t *t_host,
+                    uint64_t *delta_host);
+
+/*
+ * In-place negacyclic NTT (inverse != 0: inverse NTT) of `count` groups of L
+ * polynomials, data_dev laid out [count][L][N]; polynomial (g, j) uses prime
+ * j.  Inputs must be canonical; outputs are canonical.  The transform the
+ * ct x pt product is taken through (Sec. 5.3's products g_i f_i live in
+ * R_q = Z_q[x]/(x^N + 1)).
+ */
+int sanns_ntt(sanns_ctx *ctx, uint64_t *data_dev, uint64_t count, int inverse, void *stream);
+
+/*
+ * AHE.Keygen (Fig. "SANNS linear-scan protocol", step 1): ternary secret s,
+ * coefficient x = (lo mod 3) - 1 of ChaCha20 stream (seed, purpose 1,
+ * object 0).  The key stays on the device.
+ */
+int sanns_keygen(sanns_ctx *ctx, uint64_t seed, sanns_sk **out, void *stream);
+void sanns_sk_free(sanns_sk *sk);
+/* Copy s (int8 [N]) and its NTT s_hat ([L][N]) to `any` memory; either
+ * pointer may be NULL. */
+int sanns_sk_export(const sanns_sk *sk, int8_t *s_any, uint64_t *s_hat_any, void *stream);
+
+/*
+ * Server-side encoding (Pi_ls step 3; Sec. 5.3 "g_i = sum_j p_{j+1}[i] x^j"):
+ * position pos in [0, n) holds point perm[pos] (perm_dev NULL: identity,
+ * n <= n_points).  Block k, dimension i is the polynomial whose coefficient x
+ * is coordinate i of the point at position kN + x (zero past n), stored in
+ * NTT form per prime and kept resident in HBM together with ||p||^2 per
+ * position.  coords_dev: uint8 [n_points][d] row-major.  Synchronous; an
+ * out-of-range perm entry returns SANNS_EINVAL.
+ */
+int sanns_encode_db(sanns_ctx *ctx, const uint8_t *coords_dev, uint64_t n_points,
+                    const uint32_t *perm_dev, uint64_t n, sanns_db **out, void *stream);
+void sanns_db_free(sanns_db *db);
+/* n and K = ceil(n / N) of an encoded database. */
+int sanns_db_info(const sanns_db *db, uint64_t *n, uint64_t *K);
+/* Copy blocks [k0, k1) of the encoded plaintexts, layout [k][L][d][N], and
+ * ||p||^2 of their (k1 - k0) N positions, to `any` memory (NULL skips). */
+int sanns_db_export(const sanns_db *db, uint64_t k0, uint64_t k1, uint64_t *pt_any,
+                    uint32_t *norms_any, void *stream);
+
+/*
+ * AHE.Enc (Pi_ls step 2) of B queries, private-key BFV.  Coordinate i of
+ * query b becomes the constant plaintext m = (t - 2 q[i]) mod t; per prime j
+ *   a  = uniform mod q_j in NTT form, ChaCha20 stream (seed, 2,
+ *        qid << 16 | j << 12 | i), slot s = draw s, value (hi 2^64 + lo) mod q_j;
+ *   e  = centred binomial eta = 21 from stream (seed, 3, qid << 16 | i),
+ *        draw x -> popcount(lo & (2^21-1)) - popcount((lo >> 21) & (2^21-1));
+ *   c1 = a,   c0 = -a s_hat + NTT(e) + Delta_j m.
+ * q_dev: uint8 [B][d]; qids_dev: uint64 [B] (qid < 2^48); ct_in_dev output
+ * [B][d][2][L][N] in NTT form.
+ */
+int sanns_encrypt_query(sanns_ctx *ctx, const sanns_sk *sk, const uint8_t *q_dev, uint32_t B,
+                        uint64_t seed, const uint64_t *qids_dev, uint64_t *ct_in_dev,
+                        void *stream);
+
+/*
+ * The server's distance step (Pi_ls step 3) for B queries against one
+ * encoded database:
+ *   acc[b][k][c][j][s] = sum_i ct_in[b][i][c][j][s] pt[k][j][i][s]  mod q_j
+ *   ct_out[b][k][c][j] = INTT_j(acc[b][k][c][j])
+ *   ct_out[b][k][0][j][x] += Delta_j ((||p_pos||^2 + r_pos) mod t)
+ * with pos = kN + x (padding included), r_pos uniform mod t from ChaCha20
+ * stream (mask_seed, 4, qids[b]) draw pos, and the server's share
+ *   srv_share[b][pos] = (t - r_pos) mod t for pos < n.
+ * ct_in_dev [B][d][2][L][N] (NTT form), qids_dev uint64 [B], outputs
+ * ct_out_dev [B][K][2][L][N] (coefficient form) and srv_share_dev uint32
+ * [B][n].  The client's decryption plus ||q||^2 and the server's share add up
+ * to ||q - p_pos||^2 mod t.
+ */
+int sanns_distances(sanns_ctx *ctx, const sanns_db *db, const uint64_t *ct_in_dev, uint32_t B,
+                    uint64_t mask_seed, const uint64_t *qids_dev, uint64_t *ct_out_dev,
+                    uint32_t *srv_share_dev, void *stream);
+
+/*
+ * The two stages of sanns_distances, callable separately (same arguments,
+ * same kernels, same launch configuration):
+ *   sanns_distances_mac     acc[b][k][c][j][s] = sum_i ct_in pt mod q_j,
+ *                           written to ct_out_dev in NTT form;
+ *   sanns_distances_finish  in place on ct_out_dev: INTT, + Delta (||p||^2 +
+ *                           r), and the server share.
+ * sanns_distances(...) == sanns_distances_mac(...) then
+ * sanns_distances_finish(...) on the same stream.
+ */
+int sanns_distances_mac(sanns_ctx *ctx, const sanns_db *db, const uint64_t *ct_in_dev,
+                        uint32_t B, uint64_t *ct_out_dev, void *stream);
+int sanns_distances_finish(sanns_ctx *ctx, const sanns_db *db, uint32_t B, uint64_t mask_seed,
+                           const uint64_t *qids_dev, uint64_t *ct_out_dev,
+                           uint32_t *srv_share_dev, void *stream);
+
+/*
+ * Client decryption (Pi_ls step 4) plus its local term: per query b and
+ * position pos < n, m = round(t (c0 + c1 s mod Q) / Q) mod t (CRT over the L
+ * primes), cli_share[b][pos] = (m + ||q_b||^2) mod t.  ct_out_dev
+ * [B][K][2][L][N] with K = ceil(n / N); q_dev uint8 [B][d]; cli_share_dev
+ * uint32 [B][n].  Uses a stream-ordered scratch allocation of B K L N words.
+ */
+int sanns_decrypt_shares(sanns_ctx *ctx, const sanns_sk *sk, const uint64_t *ct_out_dev,
+                         uint32_t B, uint64_t n, const uint8_t *q_dev, uint32_t *cli_share_dev,
+                         void *stream);
+
+/* Number of multiprocessors the persistent kernels size their grids by. */
+int sanns_device_sms(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SANNS_H_ */

@@ -1,0 +1,324 @@
+// The extern "C" entry points of sanns.h: host-side validation, handle
+// management and the launch sequences.
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+
+namespace sanns {
+
+namespace {
+thread_local std::string g_last_error;
+}
+
+int fail(int code, const std::string& msg) {
+  g_last_error = msg;
+  return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+  g_last_error = std::string(what) + ": " + cudaGetErrorString(e);
+  return e == cudaErrorMemoryAllocation ? SANNS_ENOMEM : SANNS_ECUDA;
+}
+
+}  // namespace sanns
+
+using namespace sanns;
+
+namespace {
+
+cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
+
+int check_device(const sanns_ctx* ctx) {
+  int dev = -1;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+  if (dev != ctx->device) return fail(SANNS_EINVAL, "current device differs from the context's device");
+  return SANNS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* sanns_last_error(void) { return g_last_error.c_str(); }
+
+int sanns_device_sms(void) {
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+  return sms;
+}
+
+int sanns_ctx_create(const sanns_params* p, sanns_ctx** out) {
+  if (!out) return fail(SANNS_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!p) return fail(SANNS_EINVAL, "params is NULL");
+  const uint32_t N = p->N;
+  if (N < kMinN || N > kMaxN || (N & (N - 1)))
+    return fail(SANNS_EINVAL, "N must be a power of two in [64, 16384]");
+  if (p->L < 1 || p->L > (uint32_t)kMaxPrimes) return fail(SANNS_EINVAL, "L must be in [1, 4]");
+  if (p->d < 1 || p->d > kMaxD) return fail(SANNS_EINVAL, "d must be in [1, 224]");
+  if (p->t_rule == 1 && (p->b_c < 1 || p->b_c > 12)) return fail(SANNS_EINVAL, "b_c must be in [1, 12]");
+  uint64_t q[kMaxPrimes], psi[kMaxPrimes], t = 0;
+  int rc = derive_params(*p, q, psi, &t);
+  if (rc) return rc;
+  if (t >= (1ull << 31)) return fail(SANNS_EINVAL, "t must be below 2^31");
+
+  sanns_ctx* c = new sanns_ctx();
+  c->params = *p;
+  memset(&c->P, 0, sizeof(c->P));
+  c->P.N = N;
+  uint32_t logN = 0;
+  while ((1u << logN) < N) ++logN;
+  c->P.logN = logN;
+  fill_prime_constants(c->P, q, t, p->L);
+  for (uint32_t j = 0; j < p->L; ++j) c->psi[j] = psi[j];
+  cudaError_t e = cudaGetDevice(&c->device);
+  if (e != cudaSuccess) { delete c; return cuda_fail(e, "cudaGetDevice"); }
+  cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, c->device);
+
+  const size_t per = (size_t)p->L * N;
+  std::vector<uint64_t> host(4 * per);
+  for (uint32_t j = 0; j < p->L; ++j)
+    fill_twiddles(N, q[j], psi[j], &host[0 * per + j * N], &host[1 * per + j * N],
+                  &host[2 * per + j * N], &host[3 * per + j * N]);
+  e = cudaMalloc(&c->d_tables, sizeof(uint64_t) * 4 * per);
+  if (e != cudaSuccess) { delete c; return cuda_fail(e, "cudaMalloc(tables)"); }
+  e = cudaMemcpy(c->d_tables, host.data(), sizeof(uint64_t) * 4 * per, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) { cudaFree(c->d_tables); delete c; return cuda_fail(e, "cudaMemcpy(tables)"); }
+  c->P.tw = c->d_tables;
+  c->P.tw_shoup = c->d_tables + per;
+  c->P.itw = c->d_tables + 2 * per;
+  c->P.itw_shoup = c->d_tables + 3 * per;
+  *out = c;
+  return SANNS_OK;
+}
+
+void sanns_ctx_free(sanns_ctx* ctx) {
+  if (!ctx) return;
+  cudaFree(ctx->d_tables);
+  delete ctx;
+}
+
+int sanns_ctx_query(const sanns_ctx* ctx, uint64_t* q, uint64_t* psi, uint64_t* t, uint64_t* delta) {
+  if (!ctx) return fail(SANNS_EINVAL, "ctx is NULL");
+  for (uint32_t j = 0; j < ctx->params.L; ++j) {
+    if (q) q[j] = ctx->P.q[j];
+    if (psi) psi[j] = ctx->psi[j];
+    if (delta) delta[j] = ctx->P.delta[j];
+  }
+  if (t) *t = ctx->P.t;
+  return SANNS_OK;
+}
+
+int sanns_ntt(sanns_ctx* ctx, uint64_t* data, uint64_t count, int inverse, void* stream) {
+  if (!ctx) return fail(SANNS_EINVAL, "ctx is NULL");
+  if (count && !data) return fail(SANNS_EINVAL, "data is NULL");
+  if (count * ctx->params.L > 0x7fffffffull) return fail(SANNS_EINVAL, "too many polynomials");
+  int rc = check_device(ctx);
+  if (rc) return rc;
+  SANNS_CUDA(launch_ntt(ctx->P, data, count, inverse != 0, as_stream(stream)));
+  return SANNS_OK;
+}
+
+int sanns_keygen(sanns_ctx* ctx, uint64_t seed, sanns_sk** out, void* stream) {
+  if (!out) return fail(SANNS_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!ctx) return fail(SANNS_EINVAL, "ctx is NULL");
+  int rc = check_device(ctx);
+  if (rc) return rc;
+  const uint32_t N = ctx->P.N, L = ctx->P.L;
+  sanns_sk* sk = new sanns_sk();
+  sk->ctx = ctx;
+  cudaError_t e = cudaMalloc(&sk->d_s, N);
+  if (e == cudaSuccess) e = cudaMalloc(&sk->d_s_hat, sizeof(uint64_t) * 2 * L * N);
+  if (e != cudaSuccess) {
+    cudaFree(sk->d_s);
+    delete sk;
+    return cuda_fail(e, "cudaMalloc(sk)");
+  }
+  sk->d_s_hat_shoup = sk->d_s_hat + (size_t)L * N;
+  e = launch_keygen(ctx->P, seed, sk->d_s, sk->d_s_hat, sk->d_s_hat_shoup, as_stream(stream));
+  if (e != cudaSuccess) {
+    sanns_sk_free(sk);
+    return cuda_fail(e, "keygen kernel");
+  }
+  *out = sk;
+  return SANNS_OK;
+}
+
+void sanns_sk_free(sanns_sk* sk) {
+  if (!sk) return;
+  cudaFree(sk->d_s);
+  cudaFree(sk->d_s_hat);
+  delete sk;
+}
+
+int sanns_sk_export(const sanns_sk* sk, int8_t* s, uint64_t* s_hat, void* stream) {
+  if (!sk) return fail(SANNS_EINVAL, "sk is NULL");
+  const uint32_t N = sk->ctx->P.N, L = sk->ctx->P.L;
+  cudaStream_t st = as_stream(stream);
+  if (s) SANNS_CUDA(cudaMemcpyAsync(s, sk->d_s, N, cudaMemcpyDefault, st));
+  if (s_hat) SANNS_CUDA(cudaMemcpyAsync(s_hat, sk->d_s_hat, sizeof(uint64_t) * L * N, cudaMemcpyDefault, st));
+  SANNS_CUDA(cudaStreamSynchronize(st));
+  return SANNS_OK;
+}
+
+int sanns_encode_db(sanns_ctx* ctx, const uint8_t* coords, uint64_t n_points, const uint32_t* perm,
+                    uint64_t n, sanns_db** out, void* stream) {
+  if (!out) return fail(SANNS_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!ctx) return fail(SANNS_EINVAL, "ctx is NULL");
+  if (n == 0) return fail(SANNS_EINVAL, "n must be positive");
+  if (!coords) return fail(SANNS_EINVAL, "coords is NULL");
+  if (!perm && n > n_points) return fail(SANNS_EINVAL, "n exceeds n_points without a permutation");
+  int rc = check_device(ctx);
+  if (rc) return rc;
+  const uint32_t N = ctx->P.N, L = ctx->P.L, d = ctx->params.d;
+  const uint64_t K = (n + N - 1) / N;
+  if (K > 0x7fffffffull) return fail(SANNS_EINVAL, "too many blocks");
+  cudaStream_t st = as_stream(stream);
+  sanns_db* db = new sanns_db();
+  db->ctx = ctx;
+  db->n = n;
+  db->K = K;
+  int* d_bad = nullptr;
+  cudaError_t e = cudaMalloc(&db->d_pt, sizeof(uint64_t) * K * L * d * N);
+  if (e == cudaSuccess) e = cudaMalloc(&db->d_norms, sizeof(uint32_t) * K * N);
+  if (e == cudaSuccess) e = cudaMalloc(&d_bad, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemsetAsync(d_bad, 0, sizeof(int), st);
+  if (e == cudaSuccess)
+    e = launch_encode(ctx->P, coords, n_points, perm, n, d, K, db->d_pt, db->d_norms, d_bad, st);
+  int bad = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&bad, d_bad, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFree(d_bad);
+  if (e != cudaSuccess) {
+    sanns_db_free(db);
+    return cuda_fail(e, "encode_db");
+  }
+  if (bad) {
+    sanns_db_free(db);
+    return fail(SANNS_EINVAL, "perm holds an index >= n_points");
+  }
+  *out = db;
+  return SANNS_OK;
+}
+
+void sanns_db_free(sanns_db* db) {
+  if (!db) return;
+  cudaFree(db->d_pt);
+  cudaFree(db->d_norms);
+  delete db;
+}
+
+int sanns_db_info(const sanns_db* db, uint64_t* n, uint64_t* K) {
+  if (!db) return fail(SANNS_EINVAL, "db is NULL");
+  if (n) *n = db->n;
+  if (K) *K = db->K;
+  return SANNS_OK;
+}
+
+int sanns_db_export(const sanns_db* db, uint64_t k0, uint64_t k1, uint64_t* pt, uint32_t* norms,
+                    void* stream) {
+  if (!db) return fail(SANNS_EINVAL, "db is NULL");
+  if (k0 > k1 || k1 > db->K) return fail(SANNS_EINVAL, "block range out of bounds");
+  const sanns_ctx* ctx = db->ctx;
+  const size_t per_block = (size_t)ctx->P.L * ctx->params.d * ctx->P.N;
+  cudaStream_t st = as_stream(stream);
+  if (pt)
+    SANNS_CUDA(cudaMemcpyAsync(pt, db->d_pt + k0 * per_block, sizeof(uint64_t) * (k1 - k0) * per_block,
+                               cudaMemcpyDefault, st));
+  if (norms)
+    SANNS_CUDA(cudaMemcpyAsync(norms, db->d_norms + k0 * ctx->P.N,
+                               sizeof(uint32_t) * (k1 - k0) * ctx->P.N, cudaMemcpyDefault, st));
+  SANNS_CUDA(cudaStreamSynchronize(st));
+  return SANNS_OK;
+}
+
+int sanns_encrypt_query(sanns_ctx* ctx, const sanns_sk* sk, const uint8_t* qv, uint32_t B,
+                        uint64_t seed, const uint64_t* qids, uint64_t* ct, void* stream) {
+  if (!ctx || !sk) return fail(SANNS_EINVAL, "ctx or sk is NULL");
+  if (sk->ctx != ctx) return fail(SANNS_EINVAL, "sk belongs to another context");
+  if (B == 0) return SANNS_OK;
+  if (!qv || !qids || !ct) return fail(SANNS_EINVAL, "NULL buffer");
+  if (B > 65535) return fail(SANNS_EINVAL, "B must be <= 65535");
+  int rc = check_device(ctx);
+  if (rc) return rc;
+  SANNS_CUDA(launch_encrypt(ctx->P, sk->d_s_hat, sk->d_s_hat_shoup, qv, B, ctx->params.d, seed, qids,
+                            ct, as_stream(stream)));
+  return SANNS_OK;
+}
+
+namespace {
+int check_distance_args(sanns_ctx* ctx, const sanns_db* db, uint32_t B) {
+  if (!ctx || !db) return fail(SANNS_EINVAL, "ctx or db is NULL");
+  if (db->ctx != ctx) return fail(SANNS_EINVAL, "db belongs to another context");
+  if ((uint64_t)B * db->K * 2 * ctx->P.L > 0x7fffffffull) return fail(SANNS_EINVAL, "batch too large");
+  return check_device(ctx);
+}
+}  // namespace
+
+int sanns_distances_mac(sanns_ctx* ctx, const sanns_db* db, const uint64_t* ct_in, uint32_t B,
+                        uint64_t* ct_out, void* stream) {
+  int rc = check_distance_args(ctx, db, B);
+  if (rc) return rc;
+  if (B == 0) return SANNS_OK;
+  if (!ct_in || !ct_out) return fail(SANNS_EINVAL, "NULL buffer");
+  if (!aligned16(ct_in) || !aligned16(ct_out)) return fail(SANNS_EINVAL, "ct buffers must be 16-byte aligned");
+  SANNS_CUDA(launch_mac(ctx->P, ct_in, db->d_pt, B, ctx->params.d, db->K, ct_out, ctx->sms,
+                        as_stream(stream)));
+  return SANNS_OK;
+}
+
+int sanns_distances_finish(sanns_ctx* ctx, const sanns_db* db, uint32_t B, uint64_t mask_seed,
+                           const uint64_t* qids, uint64_t* ct_out, uint32_t* srv_share, void* stream) {
+  int rc = check_distance_args(ctx, db, B);
+  if (rc) return rc;
+  if (B == 0) return SANNS_OK;
+  if (!qids || !ct_out || !srv_share) return fail(SANNS_EINVAL, "NULL buffer");
+  SANNS_CUDA(launch_intt_mask(ctx->P, ct_out, db->d_norms, B, db->K, db->n, mask_seed, qids,
+                              srv_share, as_stream(stream)));
+  return SANNS_OK;
+}
+
+int sanns_distances(sanns_ctx* ctx, const sanns_db* db, const uint64_t* ct_in, uint32_t B,
+                    uint64_t mask_seed, const uint64_t* qids, uint64_t* ct_out, uint32_t* srv_share,
+                    void* stream) {
+  int rc = check_distance_args(ctx, db, B);
+  if (rc) return rc;
+  if (B == 0) return SANNS_OK;
+  if (!ct_in || !qids || !ct_out || !srv_share) return fail(SANNS_EINVAL, "NULL buffer");
+  rc = sanns_distances_mac(ctx, db, ct_in, B, ct_out, stream);
+  if (rc) return rc;
+  return sanns_distances_finish(ctx, db, B, mask_seed, qids, ct_out, srv_share, stream);
+}
+
+int sanns_decrypt_shares(sanns_ctx* ctx, const sanns_sk* sk, const uint64_t* ct_out, uint32_t B,
+                         uint64_t n, const uint8_t* qv, uint32_t* cli_share, void* stream) {
+  if (!ctx || !sk) return fail(SANNS_EINVAL, "ctx or sk is NULL");
+  if (sk->ctx != ctx) return fail(SANNS_EINVAL, "sk belongs to another context");
+  if (B == 0 || n == 0) return SANNS_OK;
+  if (!ct_out || !qv || !cli_share) return fail(SANNS_EINVAL, "NULL buffer");
+  const uint64_t K = (n + ctx->P.N - 1) / ctx->P.N;
+  if ((uint64_t)B * K * ctx->P.L > 0x7fffffffull || (uint64_t)B * n > (1ull << 40))
+    return fail(SANNS_EINVAL, "batch too large");
+  int rc = check_device(ctx);
+  if (rc) return rc;
+  cudaStream_t st = as_stream(stream);
+  uint64_t* scratch = nullptr;
+  SANNS_CUDA(cudaMallocAsync(&scratch, sizeof(uint64_t) * B * K * ctx->P.L * ctx->P.N, st));
+  cudaError_t e = launch_decrypt(ctx->P, ct_out, sk->d_s, sk->d_s_hat, sk->d_s_hat_shoup, B, K, n, qv,
+                                 ctx->params.d, scratch, cli_share, st);
+  cudaError_t e2 = cudaFreeAsync(scratch, st);
+  if (e != cudaSuccess) return cuda_fail(e, "decrypt kernels");
+  if (e2 != cudaSuccess) return cuda_fail(e2, "cudaFreeAsync");
+  return SANNS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,207 @@
+// Device-side building blocks of the SANNS encrypted-distance library:
+// 64-bit modular arithmetic (Shoup and Montgomery forms), ChaCha20 draws and
+// the context structures every kernel receives by value.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/sanns.h"
+
+namespace sanns {
+
+typedef unsigned __int128 u128;
+
+constexpr int kMaxPrimes = 4;
+constexpr uint32_t kMaxN = 16384;
+constexpr uint32_t kMinN = 64;
+constexpr uint32_t kMaxD = 224;   // ct tile of the MAC kernel lives in shared memory
+
+// Stream purposes of the counter-based generator (ChaCha20, RFC 8439).
+enum : uint32_t { kPurposeSk = 1, kPurposeA = 2, kPurposeE = 3, kPurposeMask = 4 };
+
+// Per-prime constants, passed to kernels by value.
+struct PrimeSet {
+  uint32_t N, logN, L, pad;
+  uint64_t t;                       // plaintext modulus
+  uint64_t t_barrett;               // floor(2^64 / t)
+  uint64_t two64_mod_t;             // 2^64 mod t
+  uint64_t q[kMaxPrimes];
+  uint64_t q_neg_inv[kMaxPrimes];   // -q^-1 mod 2^64 (Montgomery REDC)
+  uint64_t r64[kMaxPrimes];         // 2^64 mod q
+  uint64_t r64_shoup[kMaxPrimes];
+  uint64_t delta[kMaxPrimes];       // floor(Q / t) mod q
+  uint64_t delta_shoup[kMaxPrimes];
+  uint64_t n_inv[kMaxPrimes];       // N^-1 mod q
+  uint64_t n_inv_shoup[kMaxPrimes];
+  uint64_t crt_inv[kMaxPrimes];     // (Q / q_j)^-1 mod q_j
+  uint64_t crt_inv_shoup[kMaxPrimes];
+  // twiddles, [L][N] each: psi^brv(m), psi^-brv(m) and their Shoup companions
+  const uint64_t* tw;
+  const uint64_t* tw_shoup;
+  const uint64_t* itw;
+  const uint64_t* itw_shoup;
+};
+
+// ------------------------------------------------------------------------
+// modular arithmetic
+// ------------------------------------------------------------------------
+// w * y mod q, lazily in [0, 2q), for any y < 2^64, w < q < 2^62 and
+// w_shoup = floor(w 2^64 / q) (Shoup's precomputed-quotient product).
+__device__ __forceinline__ uint64_t mul_shoup_lazy(uint64_t y, uint64_t w, uint64_t w_shoup,
+                                                   uint64_t q) {
+  uint64_t qt = __umul64hi(w_shoup, y);
+  return w * y - qt * q;
+}
+
+__device__ __forceinline__ uint64_t csub(uint64_t x, uint64_t m) { return x >= m ? x - m : x; }
+
+__device__ __forceinline__ uint64_t mul_shoup(uint64_t y, uint64_t w, uint64_t w_shoup,
+                                              uint64_t q) {
+  return csub(mul_shoup_lazy(y, w, w_shoup, q), q);
+}
+
+__device__ __forceinline__ uint64_t add_mod(uint64_t a, uint64_t b, uint64_t q) {
+  return csub(a + b, q);
+}
+
+__device__ __forceinline__ uint64_t sub_mod(uint64_t a, uint64_t b, uint64_t q) {
+  return a >= b ? a - b : a + q - b;
+}
+
+// Montgomery reduction of a 128-bit value r < 2^64 * 2^64 - ..., returning
+// (r + m q) / 2^64 with m = r_lo * (-q^-1) mod 2^64; the value is r 2^-64 mod q
+// and lies below r / 2^64 + q.
+__device__ __forceinline__ uint64_t redc128(u128 r, uint64_t q, uint64_t q_neg_inv) {
+  uint64_t lo = (uint64_t)r, hi = (uint64_t)(r >> 64);
+  uint64_t m = lo * q_neg_inv;
+  uint64_t mh = __umul64hi(m, q);
+  return hi + mh + (lo != 0 ? 1ull : 0ull);
+}
+
+// x mod q for x < 16 q.
+__device__ __forceinline__ uint64_t reduce_below_16q(uint64_t x, uint64_t q) {
+  x = csub(x, q << 3);
+  x = csub(x, q << 2);
+  x = csub(x, q << 1);
+  return csub(x, q);
+}
+
+// x mod t for x < 2^64 with t_barrett = floor(2^64 / t): the estimate
+// floor(x * t_barrett / 2^64) is at most one below floor(x / t).
+__device__ __forceinline__ uint64_t mod_t64(uint64_t x, uint64_t t, uint64_t t_barrett) {
+  uint64_t qt = __umul64hi(x, t_barrett);
+  return csub(x - qt * t, t);
+}
+
+// (hi 2^64 + lo) mod t, t < 2^32.
+__device__ __forceinline__ uint64_t mod_t128(uint64_t lo, uint64_t hi, const PrimeSet& P) {
+  uint64_t h = mod_t64(hi, P.t, P.t_barrett);
+  uint64_t l = mod_t64(lo, P.t, P.t_barrett);
+  return mod_t64(h * P.two64_mod_t + l, P.t, P.t_barrett);
+}
+
+// (hi 2^64 + lo) mod q for any q < 2^63 (not on the hot path).
+__device__ __forceinline__ uint64_t mod_q128(uint64_t lo, uint64_t hi, uint64_t q) {
+  u128 v = ((u128)hi << 64) | lo;
+  return (uint64_t)(v % q);
+}
+
+// ------------------------------------------------------------------------
+// ChaCha20 block function, RFC 8439 Sec. 2.3.  key = (seed lo, seed hi, 0..),
+// nonce = (purpose, object lo, object hi), counter = block index.  Block c/4
+// yields the 128-bit draws of coefficients 4(c/4) .. 4(c/4)+3, draw u being
+// words 4u..4u+3 read as lo = w0 | w1 << 32, hi = w2 | w3 << 32.
+// ------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t rotl32(uint32_t x, int n) { return __funnelshift_l(x, x, n); }
+
+#define SANNS_QR(a, b, c, d)             \
+  a += b; d ^= a; d = rotl32(d, 16);     \
+  c += d; b ^= c; b = rotl32(b, 12);     \
+  a += b; d ^= a; d = rotl32(d, 8);      \
+  c += d; b ^= c; b = rotl32(b, 7);
+
+__device__ __forceinline__ void chacha20_block(uint64_t seed, uint32_t purpose, uint64_t object,
+                                               uint32_t counter, uint32_t out[16]) {
+  const uint32_t s0 = 0x61707865u, s1 = 0x3320646eu, s2 = 0x79622d32u, s3 = 0x6b206574u;
+  const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+  const uint32_t n0 = purpose, n1 = (uint32_t)object, n2 = (uint32_t)(object >> 32);
+  uint32_t x0 = s0, x1 = s1, x2 = s2, x3 = s3;
+  uint32_t x4 = k0, x5 = k1, x6 = 0, x7 = 0, x8 = 0, x9 = 0, x10 = 0, x11 = 0;
+  uint32_t x12 = counter, x13 = n0, x14 = n1, x15 = n2;
+#pragma unroll
+  for (int r = 0; r < 10; r++) {
+    SANNS_QR(x0, x4, x8, x12)
+    SANNS_QR(x1, x5, x9, x13)
+    SANNS_QR(x2, x6, x10, x14)
+    SANNS_QR(x3, x7, x11, x15)
+    SANNS_QR(x0, x5, x10, x15)
+    SANNS_QR(x1, x6, x11, x12)
+    SANNS_QR(x2, x7, x8, x13)
+    SANNS_QR(x3, x4, x9, x14)
+  }
+  out[0] = x0 + s0;   out[1] = x1 + s1;   out[2] = x2 + s2;   out[3] = x3 + s3;
+  out[4] = x4 + k0;   out[5] = x5 + k1;   out[6] = x6;        out[7] = x7;
+  out[8] = x8;        out[9] = x9;        out[10] = x10;      out[11] = x11;
+  out[12] = x12 + counter; out[13] = x13 + n0; out[14] = x14 + n1; out[15] = x15 + n2;
+}
+#undef SANNS_QR
+
+__device__ __forceinline__ void draw_pair(const uint32_t blk[16], int u, uint64_t& lo,
+                                          uint64_t& hi) {
+  lo = (uint64_t)blk[4 * u] | ((uint64_t)blk[4 * u + 1] << 32);
+  hi = (uint64_t)blk[4 * u + 2] | ((uint64_t)blk[4 * u + 3] << 32);
+}
+
+// ------------------------------------------------------------------------
+// negacyclic NTT on a polynomial held in shared memory, executed by the whole
+// block.  Forward: Cooley-Tukey with Harvey's lazy butterflies, values kept
+// in [0, 4q); output slot s = a(psi^(2 brv(s) + 1)), canonicalised to [0, q).
+// Inverse: Gentleman-Sande, values in [0, 2q), N^-1 folded at the end.
+// Callers synchronise the block before and after.
+// ------------------------------------------------------------------------
+__device__ __forceinline__ void ntt_forward_smem(uint64_t* a, const PrimeSet& P, int j) {
+  const uint32_t N = P.N, logN = P.logN, half = N >> 1;
+  const uint64_t q = P.q[j], q2 = 2 * q;
+  const uint64_t* tw = P.tw + (size_t)j * N;
+  const uint64_t* tws = P.tw_shoup + (size_t)j * N;
+  for (uint32_t m = 1, lt = logN - 1; m < N; m <<= 1, --lt) {
+    const uint32_t t = 1u << lt;
+    for (uint32_t bf = threadIdx.x; bf < half; bf += blockDim.x) {
+      uint32_t i = bf >> lt, jj = bf & (t - 1);
+      uint32_t x = (i << (lt + 1)) + jj;
+      uint64_t w = __ldg(tw + m + i), ws = __ldg(tws + m + i);
+      uint64_t X = a[x], Y = a[x + t];
+      X = csub(X, q2);
+      uint64_t T = mul_shoup_lazy(Y, w, ws, q);
+      a[x] = X + T;
+      a[x + t] = X - T + q2;
+    }
+    __syncthreads();
+  }
+  for (uint32_t x = threadIdx.x; x < N; x += blockDim.x) a[x] = csub(csub(a[x], q2), q);
+}
+
+__device__ __forceinline__ void ntt_inverse_smem(uint64_t* a, const PrimeSet& P, int j) {
+  const uint32_t N = P.N, half = N >> 1;
+  const uint64_t q = P.q[j], q2 = 2 * q;
+  const uint64_t* tw = P.itw + (size_t)j * N;
+  const uint64_t* tws = P.itw_shoup + (size_t)j * N;
+  for (uint32_t lt = 0, h = half; h >= 1; ++lt, h >>= 1) {
+    const uint32_t t = 1u << lt;
+    for (uint32_t bf = threadIdx.x; bf < half; bf += blockDim.x) {
+      uint32_t i = bf >> lt, jj = bf & (t - 1);
+      uint32_t x = (i << (lt + 1)) + jj;
+      uint64_t w = __ldg(tw + h + i), ws = __ldg(tws + h + i);
+      uint64_t X = a[x], Y = a[x + t];
+      uint64_t S = csub(X + Y, q2);
+      uint64_t D = X - Y + q2;
+      a[x] = S;
+      a[x + t] = mul_shoup_lazy(D, w, ws, q);
+    }
+    __syncthreads();
+  }
+  const uint64_t ni = P.n_inv[j], nis = P.n_inv_shoup[j];
+  for (uint32_t x = threadIdx.x; x < N; x += blockDim.x) a[x] = mul_shoup(a[x], ni, nis, q);
+}
+
+}  // namespace sanns

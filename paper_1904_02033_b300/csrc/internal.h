@@ -1,0 +1,71 @@
+// Host-side structures behind the opaque handles of sanns.h.
+#pragma once
+#include <cstdint>
+#include <string>
+
+#include "common.cuh"
+
+struct sanns_ctx {
+  sanns_params params;
+  sanns::PrimeSet P;        // device pointers inside
+  uint64_t psi[sanns::kMaxPrimes];
+  uint64_t* d_tables;       // one allocation for the four twiddle tables
+  int device;
+  int sms;
+};
+
+struct sanns_sk {
+  const sanns_ctx* ctx;
+  int8_t* d_s;              // [N]
+  uint64_t* d_s_hat;        // [L][N]
+  uint64_t* d_s_hat_shoup;  // [L][N]
+};
+
+struct sanns_db {
+  const sanns_ctx* ctx;
+  uint64_t n, K;
+  uint64_t* d_pt;           // [K][L][d][N]
+  uint32_t* d_norms;        // [K N]
+};
+
+namespace sanns {
+
+// error reporting (thread-local message)
+int fail(int code, const std::string& msg);
+int cuda_fail(cudaError_t e, const char* what);
+
+#define SANNS_CUDA(call)                                  \
+  do {                                                    \
+    cudaError_t _e = (call);                              \
+    if (_e != cudaSuccess) return sanns::cuda_fail(_e, #call); \
+  } while (0)
+
+// parameter derivation (params.cpp)
+int derive_params(const sanns_params& in, uint64_t q[], uint64_t psi[], uint64_t* t);
+void fill_prime_constants(PrimeSet& P, const uint64_t q[], uint64_t t, uint32_t L);
+void fill_twiddles(uint32_t N, uint64_t q, uint64_t psi, uint64_t* tw, uint64_t* tws, uint64_t* itw,
+                   uint64_t* itws);
+uint64_t shoup_of(uint64_t w, uint64_t q);
+
+// kernel launchers (ntt.cu, mac.cu, client.cu)
+cudaError_t launch_ntt(const PrimeSet& P, uint64_t* data, uint64_t count, bool inverse,
+                       cudaStream_t st);
+cudaError_t launch_keygen(const PrimeSet& P, uint64_t seed, int8_t* s, uint64_t* s_hat,
+                          uint64_t* s_hat_shoup, cudaStream_t st);
+cudaError_t launch_encrypt(const PrimeSet& P, const uint64_t* s_hat, const uint64_t* s_hat_shoup,
+                           const uint8_t* qv, uint32_t B, uint32_t d, uint64_t seed,
+                           const uint64_t* qids, uint64_t* ct, cudaStream_t st);
+cudaError_t launch_encode(const PrimeSet& P, const uint8_t* coords, uint64_t n_points,
+                          const uint32_t* perm, uint64_t n, uint32_t d, uint64_t K, uint64_t* pt,
+                          uint32_t* norms, int* bad, cudaStream_t st);
+cudaError_t launch_mac(const PrimeSet& P, const uint64_t* ct, const uint64_t* pt, uint32_t B,
+                       uint32_t d, uint64_t K, uint64_t* out, int sms, cudaStream_t st);
+cudaError_t launch_intt_mask(const PrimeSet& P, uint64_t* ct_out, const uint32_t* norms,
+                             uint32_t B, uint64_t K, uint64_t n, uint64_t mask_seed,
+                             const uint64_t* qids, uint32_t* srv_share, cudaStream_t st);
+cudaError_t launch_decrypt(const PrimeSet& P, const uint64_t* ct_out, const int8_t* s,
+                           const uint64_t* s_hat, const uint64_t* s_hat_shoup, uint32_t B,
+                           uint64_t K, uint64_t n, const uint8_t* qv, uint32_t d,
+                           uint64_t* scratch, uint32_t* cli_share, cudaStream_t st);
+
+}  // namespace sanns

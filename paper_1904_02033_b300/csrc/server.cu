@@ -1,0 +1,163 @@
+// Server-side kernels around the MAC: standalone NTT/INTT, the database
+// encoding (Sec. 5.3: coordinate i of N consecutive permuted points becomes
+// one plaintext polynomial, kept in NTT form), and the fused epilogue of the
+// distance step (INTT back to coefficient form, + Delta (||p||^2 + r), the
+// server's share t - r).
+#include "internal.h"
+
+namespace sanns {
+
+namespace {
+
+__host__ __device__ inline uint32_t ntt_threads(uint32_t N) { return N / 2 < 512 ? N / 2 : 512; }
+
+// One block per polynomial: data [count][L][N], polynomial p uses prime p % L.
+__global__ void ntt_kernel(PrimeSet P, uint64_t* data, int inverse) {
+  extern __shared__ uint64_t sa[];
+  const uint32_t N = P.N;
+  const uint64_t poly = blockIdx.x;
+  const int j = (int)(poly % P.L);
+  uint64_t* g = data + poly * N;
+  for (uint32_t x = threadIdx.x; x < N; x += blockDim.x) sa[x] = g[x];
+  __syncthreads();
+  if (inverse) ntt_inverse_smem(sa, P, j);
+  else ntt_forward_smem(sa, P, j);
+  __syncthreads();
+  for (uint32_t x = threadIdx.x; x < N; x += blockDim.x) g[x] = sa[x];
+}
+
+// Encoding: block (k, i) builds coordinate i of positions kN .. kN+N-1 and
+// writes its NTT for every prime into pt[k][j][i][:].
+__global__ void encode_kernel(PrimeSet P, const uint8_t* __restrict__ coords, uint64_t n_points,
+                              const uint32_t* __restrict__ perm, uint64_t n, uint32_t d,
+                              uint64_t* __restrict__ pt, int* bad) {
+  extern __shared__ uint64_t sa[];
+  const uint32_t N = P.N;
+  const uint64_t k = blockIdx.x;
+  const uint32_t i = blockIdx.y;
+  for (uint32_t j = 0; j < P.L; ++j) {
+    for (uint32_t x = threadIdx.x; x < N; x += blockDim.x) {
+      uint64_t pos = k * N + x;
+      uint64_t v = 0;
+      if (pos < n) {
+        uint64_t id = perm ? perm[pos] : pos;
+        if (id < n_points) v = coords[id * d + i];
+        else if (j == 0) atomicExch(bad, 1);
+      }
+      sa[x] = v;
+    }
+    __syncthreads();
+    ntt_forward_smem(sa, P, j);
+    __syncthreads();
+    uint64_t* dst = pt + ((k * P.L + j) * d + i) * N;
+    for (uint32_t x = threadIdx.x; x < N; x += blockDim.x) dst[x] = sa[x];
+    __syncthreads();
+  }
+}
+
+__global__ void norms_kernel(const uint8_t* __restrict__ coords, uint64_t n_points,
+                             const uint32_t* __restrict__ perm, uint64_t n, uint32_t d,
+                             uint64_t total, uint32_t* __restrict__ norms) {
+  uint64_t pos = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+  if (pos >= total) return;
+  uint32_t s = 0;
+  if (pos < n) {
+    uint64_t id = perm ? perm[pos] : pos;
+    if (id < n_points) {
+      const uint8_t* p = coords + id * d;
+      for (uint32_t i = 0; i < d; ++i) s += (uint32_t)p[i] * p[i];
+    }
+  }
+  norms[pos] = s;
+}
+
+// Fused epilogue, one block per (b, k, c, j) polynomial of ct_out (in place):
+// INTT; for c = 0 add Delta_j ((||p||^2 + r) mod t) per coefficient, r drawn
+// from ChaCha20 stream (mask_seed, 4, qid_b) at position kN + x; the j = 0
+// block also writes the server share (t - r) mod t for positions < n.
+__global__ void intt_mask_kernel(PrimeSet P, uint64_t* __restrict__ ct_out,
+                                 const uint32_t* __restrict__ norms, uint64_t K, uint64_t n,
+                                 uint64_t mask_seed, const uint64_t* __restrict__ qids,
+                                 uint32_t* __restrict__ srv_share) {
+  extern __shared__ uint64_t sa[];
+  const uint32_t N = P.N, L = P.L;
+  const uint64_t poly = blockIdx.x;                 // ((b K + k) 2 + c) L + j
+  const uint32_t j = (uint32_t)(poly % L);
+  const uint32_t c = (uint32_t)((poly / L) % 2);
+  const uint64_t bk = poly / (2 * L);
+  const uint64_t k = bk % K, b = bk / K;
+  uint64_t* g = ct_out + poly * N;
+  for (uint32_t x = threadIdx.x; x < N; x += blockDim.x) sa[x] = g[x];
+  __syncthreads();
+  ntt_inverse_smem(sa, P, j);
+  __syncthreads();
+  if (c == 0) {
+    const uint64_t q = P.q[j], dl = P.delta[j], dls = P.delta_shoup[j];
+    const uint64_t qid = qids[b];
+    for (uint32_t u = threadIdx.x; u < N / 4; u += blockDim.x) {
+      const uint64_t pos0 = k * N + 4 * u;
+      uint32_t blk[16];
+      chacha20_block(mask_seed, kPurposeMask, qid, (uint32_t)(pos0 / 4), blk);
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        uint64_t lo, hi;
+        draw_pair(blk, v, lo, hi);
+        const uint64_t r = mod_t128(lo, hi, P);
+        const uint64_t pos = pos0 + v;
+        const uint64_t val = mod_t64((uint64_t)norms[pos] + r, P.t, P.t_barrett);
+        const uint32_t x = 4 * u + v;
+        sa[x] = add_mod(sa[x], mul_shoup(val, dl, dls, q), q);
+        if (j == 0 && pos < n) srv_share[b * n + pos] = (uint32_t)(r == 0 ? 0 : P.t - r);
+      }
+    }
+    __syncthreads();
+  }
+  for (uint32_t x = threadIdx.x; x < N; x += blockDim.x) g[x] = sa[x];
+}
+
+}  // namespace
+
+cudaError_t launch_ntt(const PrimeSet& P, uint64_t* data, uint64_t count, bool inverse,
+                       cudaStream_t st) {
+  const uint64_t polys = count * P.L;
+  if (polys == 0) return cudaSuccess;
+  const size_t smem = sizeof(uint64_t) * P.N;
+  cudaError_t e = cudaFuncSetAttribute(ntt_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  ntt_kernel<<<(unsigned)polys, ntt_threads(P.N), smem, st>>>(P, data, inverse ? 1 : 0);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_encode(const PrimeSet& P, const uint8_t* coords, uint64_t n_points,
+                          const uint32_t* perm, uint64_t n, uint32_t d, uint64_t K, uint64_t* pt,
+                          uint32_t* norms, int* bad, cudaStream_t st) {
+  const size_t smem = sizeof(uint64_t) * P.N;
+  cudaError_t e = cudaFuncSetAttribute(encode_kernel,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  dim3 grid((unsigned)K, d);
+  encode_kernel<<<grid, ntt_threads(P.N), smem, st>>>(P, coords, n_points, perm, n, d, pt, bad);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const uint64_t total = K * P.N;
+  norms_kernel<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(coords, n_points, perm, n, d,
+                                                                 total, norms);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_intt_mask(const PrimeSet& P, uint64_t* ct_out, const uint32_t* norms,
+                             uint32_t B, uint64_t K, uint64_t n, uint64_t mask_seed,
+                             const uint64_t* qids, uint32_t* srv_share, cudaStream_t st) {
+  const uint64_t polys = (uint64_t)B * K * 2 * P.L;
+  if (polys == 0) return cudaSuccess;
+  const size_t smem = sizeof(uint64_t) * P.N;
+  cudaError_t e = cudaFuncSetAttribute(intt_mask_kernel,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  intt_mask_kernel<<<(unsigned)polys, ntt_threads(P.N), smem, st>>>(P, ct_out, norms, K, n,
+                                                                    mask_seed, qids, srv_share);
+  return cudaGetLastError();
+}
+
+}  // namespace sanns

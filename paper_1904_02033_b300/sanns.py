@@ -1,0 +1,254 @@
+"""Python binding of libsanns.so (include/sanns.h): argument marshalling only.
+
+Every function has the name of the C entry point it calls.  Buffers are torch
+tensors on the current CUDA device (uint8 / uint32 / uint64); the stream is
+torch's current stream unless one is passed.  There is no fallback: if the
+shared library is missing or no GPU is present the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import torch
+
+from . import build as _build
+
+_LIB = None
+
+
+class SannsError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"sanns error {code}: {msg}")
+        self.code = code
+
+
+class _Params(C.Structure):
+    _fields_ = [("N", C.c_uint32), ("L", C.c_uint32), ("prime_bits", C.c_uint32),
+                ("t_rule", C.c_uint32), ("d", C.c_uint32), ("b_c", C.c_uint32)]
+
+
+_VP = C.c_void_p
+_SIGS = {
+    "sanns_last_error": ([], C.c_char_p),
+    "sanns_device_sms": ([], C.c_int),
+    "sanns_ctx_create": ([C.POINTER(_Params), C.POINTER(_VP)], C.c_int),
+    "sanns_ctx_free": ([_VP], None),
+    "sanns_ctx_query": ([_VP, _VP, _VP, _VP, _VP], C.c_int),
+    "sanns_ntt": ([_VP, _VP, C.c_uint64, C.c_int, _VP], C.c_int),
+    "sanns_keygen": ([_VP, C.c_uint64, C.POINTER(_VP), _VP], C.c_int),
+    "sanns_sk_free": ([_VP], None),
+    "sanns_sk_export": ([_VP, _VP, _VP, _VP], C.c_int),
+    "sanns_encode_db": ([_VP, _VP, C.c_uint64, _VP, C.c_uint64, C.POINTER(_VP), _VP], C.c_int),
+    "sanns_db_free": ([_VP], None),
+    "sanns_db_info": ([_VP, _VP, _VP], C.c_int),
+    "sanns_db_export": ([_VP, C.c_uint64, C.c_uint64, _VP, _VP, _VP], C.c_int),
+    "sanns_encrypt_query": ([_VP, _VP, _VP, C.c_uint32, C.c_uint64, _VP, _VP, _VP], C.c_int),
+    "sanns_distances": ([_VP, _VP, _VP, C.c_uint32, C.c_uint64, _VP, _VP, _VP, _VP], C.c_int),
+    "sanns_distances_mac": ([_VP, _VP, _VP, C.c_uint32, _VP, _VP], C.c_int),
+    "sanns_distances_finish": ([_VP, _VP, C.c_uint32, C.c_uint64, _VP, _VP, _VP, _VP], C.c_int),
+    "sanns_decrypt_shares": ([_VP, _VP, _VP, C.c_uint32, C.c_uint64, _VP, _VP, _VP], C.c_int),
+}
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = False):
+    """Load libsanns.so (built by __graft_entry__.build() / build.py)."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    path = lib_path()
+    if not os.path.exists(path):
+        if not build_if_missing:
+            raise RuntimeError(f"{path} is missing: build it with paper_1904_02033_b300.build")
+        _build.build()
+    lib = C.CDLL(path)
+    for name, (args, res) in _SIGS.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = res
+    _LIB = lib
+    return lib
+
+
+def _check(rc: int):
+    if rc != 0:
+        raise SannsError(rc, load().sanns_last_error().decode())
+
+
+def _ptr(t: torch.Tensor | None):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return C.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+
+
+class Context:
+    def __init__(self, handle, N, L, prime_bits, t_rule, d, b_c):
+        self.handle = handle
+        self.N, self.L, self.prime_bits, self.t_rule, self.d, self.b_c = (
+            N, L, prime_bits, t_rule, d, b_c)
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _LIB is not None:
+            _LIB.sanns_ctx_free(self.handle)
+            self.handle = None
+
+    def query(self) -> dict:
+        q = (C.c_uint64 * self.L)()
+        psi = (C.c_uint64 * self.L)()
+        dl = (C.c_uint64 * self.L)()
+        t = C.c_uint64()
+        _check(load().sanns_ctx_query(self.handle, q, psi, C.byref(t), dl))
+        return {"q": list(q), "psi": list(psi), "t": t.value, "delta": list(dl)}
+
+
+class SecretKey:
+    def __init__(self, handle, ctx):
+        self.handle, self.ctx = handle, ctx
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _LIB is not None:
+            _LIB.sanns_sk_free(self.handle)
+            self.handle = None
+
+
+class Database:
+    def __init__(self, handle, ctx, n, K):
+        self.handle, self.ctx, self.n, self.K = handle, ctx, n, K
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _LIB is not None:
+            _LIB.sanns_db_free(self.handle)
+            self.handle = None
+
+
+def sanns_device_sms() -> int:
+    return load().sanns_device_sms()
+
+
+def sanns_ctx_create(N: int, L: int, prime_bits: int, t_rule: int, d: int, b_c: int = 8) -> Context:
+    p = _Params(N, L, prime_bits, t_rule, d, b_c)
+    h = _VP()
+    _check(load().sanns_ctx_create(C.byref(p), C.byref(h)))
+    return Context(h, N, L, prime_bits, t_rule, d, b_c)
+
+
+def sanns_ntt(ctx: Context, data: torch.Tensor, inverse: bool = False, stream=None):
+    assert data.dtype == torch.uint64 and data.numel() % (ctx.L * ctx.N) == 0
+    count = data.numel() // (ctx.L * ctx.N)
+    _check(load().sanns_ntt(ctx.handle, _ptr(data), count, 1 if inverse else 0, _stream(stream)))
+    return data
+
+
+def sanns_keygen(ctx: Context, seed: int, stream=None) -> SecretKey:
+    h = _VP()
+    _check(load().sanns_keygen(ctx.handle, seed, C.byref(h), _stream(stream)))
+    return SecretKey(h, ctx)
+
+
+def sanns_sk_export(sk: SecretKey, stream=None):
+    ctx = sk.ctx
+    s = torch.empty(ctx.N, dtype=torch.int8, device="cuda")
+    s_hat = torch.empty((ctx.L, ctx.N), dtype=torch.uint64, device="cuda")
+    _check(load().sanns_sk_export(sk.handle, _ptr(s), _ptr(s_hat), _stream(stream)))
+    return s, s_hat
+
+
+def sanns_encode_db(ctx: Context, coords: torch.Tensor, perm: torch.Tensor | None = None,
+                    n: int | None = None, stream=None) -> Database:
+    assert coords.dtype == torch.uint8 and coords.dim() == 2 and coords.shape[1] == ctx.d
+    if perm is not None:
+        assert perm.dtype == torch.uint32
+        n = perm.numel() if n is None else n
+    else:
+        n = coords.shape[0] if n is None else n
+    h = _VP()
+    _check(load().sanns_encode_db(ctx.handle, _ptr(coords), coords.shape[0], _ptr(perm), n,
+                                  C.byref(h), _stream(stream)))
+    K = (n + ctx.N - 1) // ctx.N
+    return Database(h, ctx, n, K)
+
+
+def sanns_db_export(db: Database, k0: int = 0, k1: int | None = None, stream=None):
+    ctx = db.ctx
+    k1 = db.K if k1 is None else k1
+    pt = torch.empty((k1 - k0, ctx.L, ctx.d, ctx.N), dtype=torch.uint64, device="cuda")
+    norms = torch.empty((k1 - k0) * ctx.N, dtype=torch.uint32, device="cuda")
+    _check(load().sanns_db_export(db.handle, k0, k1, _ptr(pt), _ptr(norms), _stream(stream)))
+    return pt, norms
+
+
+def sanns_encrypt_query(ctx: Context, sk: SecretKey, q: torch.Tensor, seed: int,
+                        qids: torch.Tensor, out: torch.Tensor | None = None, stream=None):
+    assert q.dtype == torch.uint8 and q.dim() == 2 and q.shape[1] == ctx.d
+    B = q.shape[0]
+    assert qids.dtype == torch.uint64 and qids.numel() == B
+    if out is None:
+        out = torch.empty((B, ctx.d, 2, ctx.L, ctx.N), dtype=torch.uint64, device="cuda")
+    _check(load().sanns_encrypt_query(ctx.handle, sk.handle, _ptr(q), B, seed, _ptr(qids),
+                                      _ptr(out), _stream(stream)))
+    return out
+
+
+def sanns_distances(ctx: Context, db: Database, ct_in: torch.Tensor, mask_seed: int,
+                    qids: torch.Tensor, ct_out: torch.Tensor | None = None,
+                    srv_share: torch.Tensor | None = None, stream=None):
+    assert ct_in.dtype == torch.uint64
+    B = ct_in.shape[0]
+    assert ct_in.shape == (B, ctx.d, 2, ctx.L, ctx.N)
+    assert qids.dtype == torch.uint64 and qids.numel() == B
+    if ct_out is None:
+        ct_out = torch.empty((B, db.K, 2, ctx.L, ctx.N), dtype=torch.uint64, device="cuda")
+    if srv_share is None:
+        srv_share = torch.empty((B, db.n), dtype=torch.uint32, device="cuda")
+    _check(load().sanns_distances(ctx.handle, db.handle, _ptr(ct_in), B, mask_seed, _ptr(qids),
+                                  _ptr(ct_out), _ptr(srv_share), _stream(stream)))
+    return ct_out, srv_share
+
+
+def sanns_distances_mac(ctx: Context, db: Database, ct_in: torch.Tensor,
+                        ct_out: torch.Tensor | None = None, stream=None):
+    B = ct_in.shape[0]
+    assert ct_in.dtype == torch.uint64 and ct_in.shape == (B, ctx.d, 2, ctx.L, ctx.N)
+    if ct_out is None:
+        ct_out = torch.empty((B, db.K, 2, ctx.L, ctx.N), dtype=torch.uint64, device="cuda")
+    _check(load().sanns_distances_mac(ctx.handle, db.handle, _ptr(ct_in), B, _ptr(ct_out),
+                                      _stream(stream)))
+    return ct_out
+
+
+def sanns_distances_finish(ctx: Context, db: Database, ct_out: torch.Tensor, mask_seed: int,
+                           qids: torch.Tensor, srv_share: torch.Tensor | None = None,
+                           stream=None):
+    B = ct_out.shape[0]
+    assert ct_out.dtype == torch.uint64 and ct_out.shape == (B, db.K, 2, ctx.L, ctx.N)
+    assert qids.dtype == torch.uint64 and qids.numel() == B
+    if srv_share is None:
+        srv_share = torch.empty((B, db.n), dtype=torch.uint32, device="cuda")
+    _check(load().sanns_distances_finish(ctx.handle, db.handle, B, mask_seed, _ptr(qids),
+                                         _ptr(ct_out), _ptr(srv_share), _stream(stream)))
+    return ct_out, srv_share
+
+
+def sanns_decrypt_shares(ctx: Context, sk: SecretKey, ct_out: torch.Tensor, n: int,
+                         q: torch.Tensor, out: torch.Tensor | None = None, stream=None):
+    B = ct_out.shape[0]
+    assert q.dtype == torch.uint8 and q.shape == (B, ctx.d)
+    if out is None:
+        out = torch.empty((B, n), dtype=torch.uint32, device="cuda")
+    _check(load().sanns_decrypt_shares(ctx.handle, sk.handle, _ptr(ct_out), B, n, _ptr(q),
+                                       _ptr(out), _stream(stream)))
+    return out

@@ -1,0 +1,181 @@
+"""GPU parity: every output of the CUDA path, called through the C ABI, is
+compared element by element with the CPU oracle on the same seeded inputs.
+All comparisons are bit-exact (integer arithmetic throughout)."""
+import numpy as np
+import pytest
+import torch
+
+from oracle.bfv import Oracle
+from paper_1904_02033_b300 import inputs
+from paper_1904_02033_b300 import sanns as S
+
+pytestmark = pytest.mark.gpu
+
+_ORACLES = {}
+
+
+def oracle(N, L, bits, rule, d, b_c=8):
+    key = (N, L, bits, rule, d)
+    if key not in _ORACLES:
+        _ORACLES[key] = Oracle(N, L, bits, rule, d)
+    return _ORACLES[key]
+
+
+def cu(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def np_(t):
+    torch.cuda.synchronize()
+    return t.cpu().numpy()
+
+
+CONFIGS = [
+    # N, L, bits, t_rule, d
+    (64, 1, 30, 0, 3),
+    (256, 2, 40, 0, 5),
+    (256, 3, 60, 1, 17),
+    (4096, 2, 54, 0, 32),
+    (8192, 3, 60, 0, 7),
+]
+
+
+@pytest.mark.parametrize("cfg", CONFIGS)
+def test_context_constants_match_oracle(cfg):
+    ctx = S.sanns_ctx_create(*cfg)
+    O = oracle(*cfg)
+    info = ctx.query()
+    assert info["q"] == O.P.q
+    assert info["psi"] == O.P.psi
+    assert info["t"] == O.P.t
+    assert info["delta"] == O.P.delta_mod_q
+
+
+@pytest.mark.parametrize("cfg", CONFIGS)
+def test_ntt_forward_inverse_match_oracle(cfg):
+    N, L = cfg[0], cfg[1]
+    ctx = S.sanns_ctx_create(*cfg)
+    O = oracle(*cfg)
+    rnd = np.random.default_rng(N + L)
+    cnt = 3
+    a = np.zeros((cnt, L, N), dtype=np.uint64)
+    for j in range(L):
+        a[:, j] = rnd.integers(0, int(O.q[j]), size=(cnt, N), dtype=np.uint64)
+    a[1, 0] = O.q[0] - 1   # all q - 1
+    a[2, 0] = 0
+    a[2, 0, N // 3] = 1
+    t = cu(a)
+    S.sanns_ntt(ctx, t)
+    f = np_(t)
+    for g in range(cnt):
+        for j in range(L):
+            assert np.array_equal(f[g, j], O.ntt(a[g, j], j))
+    S.sanns_ntt(ctx, t, inverse=True)
+    assert np.array_equal(np_(t), a)
+
+
+@pytest.mark.parametrize("cfg", CONFIGS)
+def test_keygen_matches_oracle(cfg):
+    ctx = S.sanns_ctx_create(*cfg)
+    O = oracle(*cfg)
+    sk = S.sanns_keygen(ctx, seed=5)
+    s, s_hat = S.sanns_sk_export(sk)
+    os_, os_hat = O.keygen(5)
+    assert np.array_equal(np_(s), os_)
+    assert np.array_equal(np_(s_hat), os_hat)
+
+
+@pytest.mark.parametrize("cfg", CONFIGS)
+def test_encrypt_matches_oracle(cfg):
+    ctx = S.sanns_ctx_create(*cfg)
+    O = oracle(*cfg)
+    d = cfg[4]
+    sk = S.sanns_keygen(ctx, seed=1)
+    _, os_hat = O.keygen(1)
+    B = 2
+    q = inputs.uniform_coords(B, d, 3)
+    q[0, 0] = 0
+    q[1, -1] = 255
+    qids = np.array([7, 2 ** 40 + 3], dtype=np.uint64)
+    ct = S.sanns_encrypt_query(ctx, sk, cu(q), seed=9, qids=cu(qids))
+    got = np_(ct)
+    for b in range(B):
+        want = O.encrypt(os_hat, q[b], seed=9, qid=int(qids[b]))
+        assert np.array_equal(got[b], want)
+
+
+@pytest.mark.parametrize("cfg,n", [(CONFIGS[1], 600), (CONFIGS[2], 256), (CONFIGS[3], 4096),
+                                   (CONFIGS[4], 8192 * 2 + 77), (CONFIGS[0], 1)])
+def test_encode_db_matches_oracle(cfg, n):
+    ctx = S.sanns_ctx_create(*cfg)
+    O = oracle(*cfg)
+    d = cfg[4]
+    coords = inputs.uniform_coords(n + 5, d, 11)
+    perm = inputs.permutation(n + 5, 12)[:n]
+    db = S.sanns_encode_db(ctx, cu(coords), cu(perm))
+    pt, norms = S.sanns_db_export(db)
+    opt, onorms = O.encode_db(coords, perm)
+    assert np.array_equal(np_(pt), opt)
+    assert np.array_equal(np_(norms), onorms)
+
+
+def _pipeline(cfg, n, B, seed, perm=True):
+    N, L, bits, rule, d = cfg
+    ctx = S.sanns_ctx_create(*cfg)
+    coords = inputs.uniform_coords(n, d, seed)
+    pm = inputs.permutation(n, seed + 1) if perm else None
+    q = inputs.uniform_coords(B, d, seed + 2)
+    qids = np.arange(100, 100 + B, dtype=np.uint64)
+    sk = S.sanns_keygen(ctx, seed + 3)
+    db = S.sanns_encode_db(ctx, cu(coords), cu(pm) if perm else None)
+    ct_in = S.sanns_encrypt_query(ctx, sk, cu(q), seed + 4, cu(qids))
+    ct_out, srv = S.sanns_distances(ctx, db, ct_in, seed + 5, cu(qids))
+    cli = S.sanns_decrypt_shares(ctx, sk, ct_out, n, cu(q))
+    return dict(ctx=ctx, coords=coords, pm=pm, q=q, qids=qids, ct_in=np_(ct_in),
+                ct_out=np_(ct_out), srv=np_(srv), cli=np_(cli), seed=seed)
+
+
+@pytest.mark.parametrize("cfg,n,B", [
+    (CONFIGS[0], 1, 1),
+    (CONFIGS[1], 600, 2),         # three blocks, ragged tail, two queries
+    (CONFIGS[2], 700, 1),         # d = 17 (not a multiple of the 16-dim fold), t = 2^b_d
+    (CONFIGS[3], 4096, 1),        # the one-block N = 4096 configuration
+    (CONFIGS[4], 8192 * 3 - 5, 1),  # N = 8192, three 60-bit primes, ragged
+])
+def test_distances_match_oracle_bit_exact(cfg, n, B):
+    r = _pipeline(cfg, n, B, seed=n % 97)
+    O = oracle(*cfg)
+    _, os_hat = O.keygen(r["seed"] + 3)
+    os_, _ = O.keygen(r["seed"] + 3)
+    for b in range(B):
+        assert np.array_equal(r["ct_in"][b], O.encrypt(os_hat, r["q"][b], r["seed"] + 4,
+                                                       int(r["qids"][b])))
+        out, srv = O.distances(r["ct_in"][b], r["coords"], r["pm"], r["seed"] + 5,
+                               int(r["qids"][b]))
+        assert np.array_equal(r["ct_out"][b], out)
+        assert np.array_equal(r["srv"][b], srv)
+        cli = O.decrypt_shares(out, os_, r["q"][b], n)
+        assert np.array_equal(r["cli"][b], cli)
+        order = r["pm"] if r["pm"] is not None else np.arange(n)
+        brute = np.sum((r["coords"][order].astype(np.int64) - r["q"][b].astype(np.int64)) ** 2,
+                       axis=1)
+        assert np.array_equal((r["cli"][b].astype(np.int64) + r["srv"][b]) % O.t, brute)
+
+
+def test_max_dimension_and_identity_perm():
+    cfg = (64, 2, 40, 0, 224)
+    r = _pipeline(cfg, 130, 1, seed=3, perm=False)
+    O = oracle(*cfg)
+    os_, _ = O.keygen(6)
+    out, srv = O.distances(r["ct_in"][0], r["coords"], None, 8, int(r["qids"][0]))
+    assert np.array_equal(r["ct_out"][0], out)
+    assert np.array_equal(r["srv"][0], srv)
+
+
+def test_bad_permutation_rejected():
+    ctx = S.sanns_ctx_create(256, 2, 40, 0, 5)
+    coords = cu(inputs.uniform_coords(10, 5, 1))
+    perm = cu(np.array([0, 3, 10], dtype=np.uint32))
+    with pytest.raises(S.SannsError) as e:
+        S.sanns_encode_db(ctx, coords, perm)
+    assert e.value.code == -1
