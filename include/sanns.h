@@ -163,6 +163,48 @@ int sanns_distances_finish(sanns_ctx *ctx, const sanns_db *db, uint32_t B, uint6
                            uint32_t *srv_share_dev, void *stream);
 
 /*
+ * Clustering protocol (Pi_cl steps 5-8; Algorithm 4, the distance loop over
+ * the points of the retrieved clusters).  A clustering is C lists of point
+ * indices in CSR form: cluster c holds members[offsets[c] .. offsets[c+1]).
+ * sanns_clusters_create copies coords_dev (uint8 [n][d], any memory) and
+ * members (uint32, any memory) into library-owned device memory and keeps
+ * offsets_host (uint64 [C + 1]); a member index >= n returns SANNS_EINVAL.
+ * Synchronous.
+ */
+int sanns_clusters_create(sanns_ctx *ctx, const uint8_t *coords_any, uint64_t n,
+                          const uint64_t *offsets_host, const uint32_t *members_any, uint32_t C,
+                          sanns_clusters **out, void *stream);
+void sanns_clusters_free(sanns_clusters *cl);
+
+/*
+ * Host-only planning: for each query b with probe list probes_host[b][0..P)
+ * (cluster ids, nearest first), n_out[b] = number of gathered points and
+ * blocks_out[b] = ceil(n_out[b] / N) (blocks_out may be NULL).  The gathered
+ * list of query b is the concatenation, in probe order, of the probed
+ * clusters' member lists.
+ */
+int sanns_gather_plan(const sanns_clusters *cl, const uint32_t *probes_host, uint32_t B, uint32_t P,
+                      uint64_t *n_out, uint64_t *blocks_out);
+
+/*
+ * Distances of B queries to their gathered lists in one persistent launch.
+ * For query b the gathered list plays the role of the permuted database of
+ * sanns_distances: position pos of the list is a point, blocks of N
+ * positions are encoded, multiplied with ct_in[b], transformed back and
+ * masked with r drawn from stream (mask_seed, 4, qids[b]) at pos.
+ * Outputs are concatenated query by query: ct_out_dev [sum_b blocks_b][2][L][N]
+ * (coefficient form), srv_share_dev uint32 [sum_b n_b], ids_dev uint32
+ * [sum_b n_b] = the point index at each gathered position (may be NULL).
+ * Requires N <= 8192.  Uses a stream-ordered scratch allocation of about
+ * sum_b blocks_b (d + 4) N bytes and synchronises the stream once after
+ * uploading the plan.
+ */
+int sanns_distances_gather(sanns_ctx *ctx, const sanns_clusters *cl, const uint64_t *ct_in_dev,
+                           uint32_t B, const uint32_t *probes_host, uint32_t P, uint64_t mask_seed,
+                           const uint64_t *qids_dev, uint64_t *ct_out_dev, uint32_t *srv_share_dev,
+                           uint32_t *ids_dev, void *stream);
+
+/*
  * Client decryption (Pi_ls step 4) plus its local term: per query b and
  * position pos < n, m = round(t (c0 + c1 s mod Q) / Q) mod t (CRT over the L
  * primes), cli_share[b][pos] = (m + ||q_b||^2) mod t.  ct_out_dev

@@ -299,6 +299,103 @@ int sanns_distances(sanns_ctx* ctx, const sanns_db* db, const uint64_t* ct_in, u
   return sanns_distances_finish(ctx, db, B, mask_seed, qids, ct_out, srv_share, stream);
 }
 
+int sanns_clusters_create(sanns_ctx* ctx, const uint8_t* coords, uint64_t n,
+                          const uint64_t* offsets_host, const uint32_t* members, uint32_t C,
+                          sanns_clusters** out, void* stream) {
+  if (!out) return fail(SANNS_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!ctx) return fail(SANNS_EINVAL, "ctx is NULL");
+  if (!coords || !offsets_host || !members || n == 0 || C == 0)
+    return fail(SANNS_EINVAL, "NULL buffer or empty clustering");
+  if (offsets_host[0] != 0) return fail(SANNS_EINVAL, "offsets[0] must be 0");
+  for (uint32_t c = 0; c < C; ++c)
+    if (offsets_host[c + 1] < offsets_host[c]) return fail(SANNS_EINVAL, "offsets must be non-decreasing");
+  const uint64_t M = offsets_host[C];
+  if (M > n) return fail(SANNS_EINVAL, "more members than points");
+  int rc = check_device(ctx);
+  if (rc) return rc;
+  cudaStream_t st = as_stream(stream);
+  const uint32_t d = ctx->params.d;
+  sanns_clusters* cl = new sanns_clusters();
+  cl->ctx = ctx;
+  cl->n = n;
+  cl->C = C;
+  cl->h_offsets.assign(offsets_host, offsets_host + C + 1);
+  int* d_bad = nullptr;
+  cudaError_t e = cudaMalloc(&cl->d_coords, n * d);
+  if (e == cudaSuccess) e = cudaMalloc(&cl->d_members, sizeof(uint32_t) * (M ? M : 1));
+  if (e == cudaSuccess) e = cudaMalloc(&cl->d_offsets, sizeof(uint64_t) * (C + 1));
+  if (e == cudaSuccess) e = cudaMalloc(&d_bad, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemcpyAsync(cl->d_coords, coords, n * d, cudaMemcpyDefault, st);
+  if (e == cudaSuccess && M) e = cudaMemcpyAsync(cl->d_members, members, sizeof(uint32_t) * M, cudaMemcpyDefault, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(cl->d_offsets, offsets_host, sizeof(uint64_t) * (C + 1), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(d_bad, 0, sizeof(int), st);
+  if (e == cudaSuccess && M) e = launch_check_indices(cl->d_members, M, n, d_bad, st);
+  int bad = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&bad, d_bad, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFree(d_bad);
+  if (e != cudaSuccess) {
+    sanns_clusters_free(cl);
+    return cuda_fail(e, "clusters_create");
+  }
+  if (bad) {
+    sanns_clusters_free(cl);
+    return fail(SANNS_EINVAL, "members holds an index >= n");
+  }
+  *out = cl;
+  return SANNS_OK;
+}
+
+void sanns_clusters_free(sanns_clusters* cl) {
+  if (!cl) return;
+  cudaFree(cl->d_coords);
+  cudaFree(cl->d_members);
+  cudaFree(cl->d_offsets);
+  delete cl;
+}
+
+int sanns_gather_plan(const sanns_clusters* cl, const uint32_t* probes, uint32_t B, uint32_t P,
+                      uint64_t* n_out, uint64_t* blocks_out) {
+  if (!cl) return fail(SANNS_EINVAL, "clusters is NULL");
+  if (B && (!probes || !n_out)) return fail(SANNS_EINVAL, "NULL buffer");
+  if (B && P == 0) return fail(SANNS_EINVAL, "P must be positive");
+  const uint32_t N = cl->ctx->P.N;
+  for (uint32_t b = 0; b < B; ++b) {
+    uint64_t acc = 0;
+    for (uint32_t p = 0; p < P; ++p) {
+      const uint32_t c = probes[(size_t)b * P + p];
+      if (c >= cl->C) return fail(SANNS_EINVAL, "probe names a cluster id >= C");
+      acc += cl->h_offsets[c + 1] - cl->h_offsets[c];
+    }
+    n_out[b] = acc;
+    if (blocks_out) blocks_out[b] = (acc + N - 1) / N;
+  }
+  return SANNS_OK;
+}
+
+int sanns_distances_gather(sanns_ctx* ctx, const sanns_clusters* cl, const uint64_t* ct_in, uint32_t B,
+                           const uint32_t* probes, uint32_t P, uint64_t mask_seed, const uint64_t* qids,
+                           uint64_t* ct_out, uint32_t* srv_share, uint32_t* ids, void* stream) {
+  if (!ctx || !cl) return fail(SANNS_EINVAL, "ctx or clusters is NULL");
+  if (cl->ctx != ctx) return fail(SANNS_EINVAL, "clusters belong to another context");
+  if (ctx->P.N > 8192) return fail(SANNS_EINVAL, "the gather path supports N <= 8192");
+  if (B == 0) return SANNS_OK;
+  if (!ct_in || !qids || !ct_out || !srv_share || !probes) return fail(SANNS_EINVAL, "NULL buffer");
+  std::vector<uint64_t> nb(B), kb(B);
+  int rc = sanns_gather_plan(cl, probes, B, P, nb.data(), kb.data());
+  if (rc) return rc;
+  uint64_t W = 0;
+  for (uint32_t b = 0; b < B; ++b) W += kb[b];
+  if (W * 2 * ctx->P.L > 0x7fffffffull || W * ctx->P.N > (1ull << 40)) return fail(SANNS_EINVAL, "batch too large");
+  rc = check_device(ctx);
+  if (rc) return rc;
+  SANNS_CUDA(launch_gather(ctx->P, ctx->params.d, cl, ct_in, B, probes, P, nb.data(), mask_seed, qids,
+                           ct_out, srv_share, ids, ctx->sms, as_stream(stream)));
+  return SANNS_OK;
+}
+
 int sanns_decrypt_shares(sanns_ctx* ctx, const sanns_sk* sk, const uint64_t* ct_out, uint32_t B,
                          uint64_t n, const uint8_t* qv, uint32_t* cli_share, void* stream) {
   if (!ctx || !sk) return fail(SANNS_EINVAL, "ctx or sk is NULL");

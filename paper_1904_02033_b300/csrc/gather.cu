@@ -1,0 +1,253 @@
+// K4: distances for the clustering protocol (Pi_cl steps 5-8 / Algorithm 4's
+// "for p in C u S: d_p = ||q - p||^2" over the retrieved clusters).  Each
+// query b probes P clusters; the points of those clusters, concatenated in
+// probe order with members ascending, form the query's own gathered list of
+// n_b points.  That list is treated exactly like a permuted database in the
+// linear scan: blocks of N positions (zero padded), one plaintext polynomial
+// per (block, dimension, prime), ct x pt MAC over the d dimensions, INTT,
+// + Delta (||p||^2 + r), server share t - r.  The paper fetches the points as
+// secret shares through DORAM; here the server holds them in the clear.
+//
+// Two launches:
+//   pack       one thread per gathered position: finds the probe segment by
+//              binary search, copies the point's d bytes into a
+//              coordinate-major tile [item][i][x] and its ||p||^2;
+//   persistent one block per multiprocessor walks the (query, block) work
+//              items of every query -- uneven per-query counts included --
+//              and runs encode (NTT) -> MAC -> INTT -> mask for each item,
+//              the accumulators of SPT slots per thread kept in registers.
+#include <vector>
+
+#include "internal.h"
+
+namespace sanns {
+
+namespace {
+
+__global__ void check_indices_kernel(const uint32_t* idx, uint64_t m, uint64_t bound, int* bad) {
+  const uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+  if (i < m && idx[i] >= bound) atomicExch(bad, 1);
+}
+
+struct GatherItem {
+  uint32_t b;       // query
+  uint32_t kb;      // block within the query's gathered list
+  uint64_t blk;     // output block index (query-major)
+};
+
+struct GatherQuery {
+  uint64_t n;       // gathered points
+  uint64_t pos_off; // offset of the query's positions in srv_share / ids
+};
+
+__global__ void pack_kernel(uint32_t N, uint32_t d, uint64_t W, const GatherItem* __restrict__ items,
+                            const GatherQuery* __restrict__ qs, const uint64_t* __restrict__ seg,
+                            const uint32_t* __restrict__ probes, uint32_t P,
+                            const uint64_t* __restrict__ offsets, const uint32_t* __restrict__ members,
+                            const uint8_t* __restrict__ coords, uint8_t* __restrict__ gco,
+                            uint32_t* __restrict__ gnorm, uint32_t* __restrict__ ids) {
+  const uint64_t gid = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+  if (gid >= W * N) return;
+  const uint64_t w = gid / N;
+  const uint32_t x = (uint32_t)(gid % N);
+  const GatherItem it = items[w];
+  const uint64_t pos = (uint64_t)it.kb * N + x;
+  const GatherQuery Q = qs[it.b];
+  uint8_t* dst = gco + w * (uint64_t)d * N + x;
+  if (pos >= Q.n) {
+    for (uint32_t i = 0; i < d; ++i) dst[(uint64_t)i * N] = 0;
+    gnorm[w * N + x] = 0;
+    return;
+  }
+  // segment p with seg[p] <= pos < seg[p + 1] (seg has P + 1 entries per query)
+  const uint64_t* sg = seg + (uint64_t)it.b * (P + 1);
+  uint32_t lo = 0, hi = P;  // invariant: sg[lo] <= pos < sg[hi]
+  while (hi - lo > 1) {
+    uint32_t mid = (lo + hi) >> 1;
+    if (sg[mid] <= pos) lo = mid; else hi = mid;
+  }
+  const uint32_t c = probes[(uint64_t)it.b * P + lo];
+  const uint32_t pt = members[offsets[c] + (pos - sg[lo])];
+  const uint8_t* src = coords + (uint64_t)pt * d;
+  uint32_t nrm = 0;
+  for (uint32_t i = 0; i < d; ++i) {
+    const uint32_t v = src[i];
+    nrm += v * v;
+    dst[(uint64_t)i * N] = (uint8_t)v;
+  }
+  gnorm[w * N + x] = nrm;
+  if (ids) ids[Q.pos_off + pos] = pt;
+}
+
+// c * p mod q for c, p < q < 2^60 with p_mont = p 2^64 mod q: one Montgomery
+// reduction of the 120-bit product gives a value below q + 2^56 < 2q.
+__device__ __forceinline__ uint64_t mont_mul(uint64_t c, uint64_t p_mont, uint64_t q, uint64_t qn) {
+  return csub(redc128((u128)c * p_mont, q, qn), q);
+}
+
+template <int SPT>
+__global__ void __launch_bounds__(512, 1)
+gather_kernel(PrimeSet P, uint32_t d, uint64_t W, const GatherItem* __restrict__ items,
+              const GatherQuery* __restrict__ qs, const uint8_t* __restrict__ gco,
+              const uint32_t* __restrict__ gnorm, const uint64_t* __restrict__ ct_in,
+              uint64_t mask_seed, const uint64_t* __restrict__ qids,
+              uint64_t* __restrict__ ct_out, uint32_t* __restrict__ srv_share) {
+  extern __shared__ uint64_t poly[];
+  const uint32_t N = P.N, L = P.L;
+  for (uint64_t w = blockIdx.x; w < W; w += gridDim.x) {
+    const GatherItem it = items[w];
+    const GatherQuery Q = qs[it.b];
+    const uint8_t* g = gco + w * (uint64_t)d * N;
+    for (uint32_t j = 0; j < L; ++j) {
+      const uint64_t q = P.q[j], qn = P.q_neg_inv[j];
+      uint64_t acc0[SPT], acc1[SPT];
+#pragma unroll
+      for (int r = 0; r < SPT; ++r) acc0[r] = acc1[r] = 0;
+      for (uint32_t i = 0; i < d; ++i) {
+        __syncthreads();
+        for (uint32_t x = threadIdx.x; x < N; x += blockDim.x) poly[x] = g[(uint64_t)i * N + x];
+        __syncthreads();
+        ntt_forward_smem(poly, P, (int)j);
+        __syncthreads();
+        const uint64_t* c0 = ct_in + ((((uint64_t)it.b * d + i) * 2 + 0) * L + j) * N;
+        const uint64_t* c1 = ct_in + ((((uint64_t)it.b * d + i) * 2 + 1) * L + j) * N;
+#pragma unroll
+        for (int r = 0; r < SPT; ++r) {
+          const uint32_t s = threadIdx.x + r * blockDim.x;
+          const uint64_t pm = mul_shoup(poly[s], P.r64[j], P.r64_shoup[j], q);
+          acc0[r] = add_mod(acc0[r], mont_mul(__ldg(c0 + s), pm, q, qn), q);
+          acc1[r] = add_mod(acc1[r], mont_mul(__ldg(c1 + s), pm, q, qn), q);
+        }
+      }
+      // back to coefficient form, mask, store
+      for (uint32_t c = 0; c < 2; ++c) {
+        __syncthreads();
+#pragma unroll
+        for (int r = 0; r < SPT; ++r) poly[threadIdx.x + r * blockDim.x] = c == 0 ? acc0[r] : acc1[r];
+        __syncthreads();
+        ntt_inverse_smem(poly, P, (int)j);
+        __syncthreads();
+        if (c == 0) {
+          const uint64_t dl = P.delta[j], dls = P.delta_shoup[j];
+          const uint64_t qid = qids[it.b];
+          for (uint32_t u = threadIdx.x; u < N / 4; u += blockDim.x) {
+            const uint64_t pos0 = (uint64_t)it.kb * N + 4 * u;
+            uint32_t blk[16];
+            chacha20_block(mask_seed, kPurposeMask, qid, (uint32_t)(pos0 / 4), blk);
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+              uint64_t lo, hi;
+              draw_pair(blk, v, lo, hi);
+              const uint64_t rr = mod_t128(lo, hi, P);
+              const uint32_t x = 4 * u + v;
+              const uint64_t val = mod_t64((uint64_t)gnorm[w * N + x] + rr, P.t, P.t_barrett);
+              poly[x] = add_mod(poly[x], mul_shoup(val, dl, dls, q), q);
+              const uint64_t pos = pos0 + v;
+              if (j == 0 && pos < Q.n)
+                srv_share[Q.pos_off + pos] = (uint32_t)(rr == 0 ? 0 : P.t - rr);
+            }
+          }
+          __syncthreads();
+        }
+        uint64_t* dst = ct_out + ((it.blk * 2 + c) * L + j) * N;
+        for (uint32_t x = threadIdx.x; x < N; x += blockDim.x) dst[x] = poly[x];
+      }
+    }
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_check_indices(const uint32_t* idx, uint64_t m, uint64_t bound, int* bad,
+                                 cudaStream_t st) {
+  check_indices_kernel<<<(unsigned)((m + 255) / 256), 256, 0, st>>>(idx, m, bound, bad);
+  return cudaGetLastError();
+}
+
+int gather_threads(uint32_t N) { return N >= 8192 ? 512 : (N >= 512 ? (int)(N / 16) : 32); }
+
+cudaError_t launch_gather(const PrimeSet& P, uint32_t d, const sanns_clusters* cl,
+                          const uint64_t* ct_in, uint32_t B, const uint32_t* probes_host,
+                          uint32_t Pr, const uint64_t* n_b, uint64_t mask_seed,
+                          const uint64_t* qids, uint64_t* ct_out, uint32_t* srv_share,
+                          uint32_t* ids, int sms, cudaStream_t st) {
+  const uint32_t N = P.N;
+  // host plan: items (query-major), per-query offsets, probe segments
+  std::vector<GatherItem> items;
+  std::vector<GatherQuery> qs(B);
+  std::vector<uint64_t> seg((size_t)B * (Pr + 1));
+  uint64_t blk = 0, pos = 0;
+  for (uint32_t b = 0; b < B; ++b) {
+    uint64_t acc = 0;
+    for (uint32_t p = 0; p < Pr; ++p) {
+      seg[(size_t)b * (Pr + 1) + p] = acc;
+      const uint32_t c = probes_host[(size_t)b * Pr + p];
+      acc += cl->h_offsets[c + 1] - cl->h_offsets[c];
+    }
+    seg[(size_t)b * (Pr + 1) + Pr] = acc;
+    qs[b].n = n_b[b];
+    qs[b].pos_off = pos;
+    const uint64_t Kb = (n_b[b] + N - 1) / N;
+    for (uint64_t k = 0; k < Kb; ++k) items.push_back(GatherItem{b, (uint32_t)k, blk + k});
+    blk += Kb;
+    pos += n_b[b];
+  }
+  const uint64_t W = items.size();
+  if (W == 0) return cudaSuccess;
+  // one stream-ordered scratch allocation: tables + packed coordinates + norms
+  const size_t sz_items = sizeof(GatherItem) * W, sz_qs = sizeof(GatherQuery) * B;
+  const size_t sz_seg = sizeof(uint64_t) * seg.size(), sz_pr = sizeof(uint32_t) * (size_t)B * Pr;
+  auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
+  const size_t o_items = 0, o_qs = up(sz_items), o_seg = o_qs + up(sz_qs), o_pr = o_seg + up(sz_seg);
+  const size_t o_norm = o_pr + up(sz_pr), o_gco = o_norm + up(sizeof(uint32_t) * W * N);
+  const size_t total = o_gco + up((size_t)W * d * N);
+  uint8_t* scratch = nullptr;
+  cudaError_t e = cudaMallocAsync(&scratch, total, st);
+  if (e != cudaSuccess) return e;
+  e = cudaMemcpyAsync(scratch + o_items, items.data(), sz_items, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(scratch + o_qs, qs.data(), sz_qs, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(scratch + o_seg, seg.data(), sz_seg, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(scratch + o_pr, probes_host, sz_pr, cudaMemcpyHostToDevice, st);
+  // the host vectors must outlive the copies
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  const GatherItem* d_items = reinterpret_cast<const GatherItem*>(scratch + o_items);
+  const GatherQuery* d_qs = reinterpret_cast<const GatherQuery*>(scratch + o_qs);
+  if (e == cudaSuccess) {
+    const uint64_t threads = W * N;
+    pack_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(
+        N, d, W, d_items, d_qs, reinterpret_cast<const uint64_t*>(scratch + o_seg),
+        reinterpret_cast<const uint32_t*>(scratch + o_pr), Pr, cl->d_offsets, cl->d_members,
+        cl->d_coords, scratch + o_gco, reinterpret_cast<uint32_t*>(scratch + o_norm), ids);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) {
+    const int th = gather_threads(N);
+    const int spt = (int)(N / th);
+    const size_t smem = sizeof(uint64_t) * N;
+    unsigned grid = (unsigned)(W < (uint64_t)(sms > 0 ? sms : 148) ? W : (uint64_t)(sms > 0 ? sms : 148));
+#define SANNS_GATHER_CASE(S)                                                                     \
+  case S:                                                                                        \
+    e = cudaFuncSetAttribute(gather_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,      \
+                             (int)smem);                                                         \
+    if (e == cudaSuccess) {                                                                      \
+      gather_kernel<S><<<grid, th, smem, st>>>(P, d, W, d_items, d_qs, scratch + o_gco,          \
+                                               reinterpret_cast<const uint32_t*>(scratch + o_norm), \
+                                               ct_in, mask_seed, qids, ct_out, srv_share);       \
+      e = cudaGetLastError();                                                                    \
+    }                                                                                            \
+    break;
+    switch (spt) {
+      SANNS_GATHER_CASE(2)
+      SANNS_GATHER_CASE(4)
+      SANNS_GATHER_CASE(8)
+      SANNS_GATHER_CASE(16)
+      default:
+        e = cudaErrorInvalidValue;
+    }
+#undef SANNS_GATHER_CASE
+  }
+  cudaError_t e2 = cudaFreeAsync(scratch, st);
+  return e != cudaSuccess ? e : e2;
+}
+
+}  // namespace sanns

@@ -2,6 +2,7 @@
 #pragma once
 #include <cstdint>
 #include <string>
+#include <vector>
 
 #include "common.cuh"
 
@@ -26,6 +27,16 @@ struct sanns_db {
   uint64_t n, K;
   uint64_t* d_pt;           // [K][L][d][N]
   uint32_t* d_norms;        // [K N]
+};
+
+struct sanns_clusters {
+  const sanns_ctx* ctx;
+  uint64_t n;               // points
+  uint32_t C;               // clusters
+  uint8_t* d_coords;        // [n][d], library-owned copy
+  uint32_t* d_members;      // [offsets[C]]
+  uint64_t* d_offsets;      // [C + 1]
+  std::vector<uint64_t> h_offsets;
 };
 
 namespace sanns {
@@ -63,6 +74,14 @@ cudaError_t launch_mac(const PrimeSet& P, const uint64_t* ct, const uint64_t* pt
 cudaError_t launch_intt_mask(const PrimeSet& P, uint64_t* ct_out, const uint32_t* norms,
                              uint32_t B, uint64_t K, uint64_t n, uint64_t mask_seed,
                              const uint64_t* qids, uint32_t* srv_share, cudaStream_t st);
+int gather_threads(uint32_t N);
+cudaError_t launch_check_indices(const uint32_t* idx, uint64_t m, uint64_t bound, int* bad,
+                                 cudaStream_t st);
+cudaError_t launch_gather(const PrimeSet& P, uint32_t d, const sanns_clusters* cl,
+                          const uint64_t* ct_in, uint32_t B, const uint32_t* probes_host,
+                          uint32_t Pr, const uint64_t* n_b, uint64_t mask_seed,
+                          const uint64_t* qids, uint64_t* ct_out, uint32_t* srv_share,
+                          uint32_t* ids, int sms, cudaStream_t st);
 cudaError_t launch_decrypt(const PrimeSet& P, const uint64_t* ct_out, const int8_t* s,
                            const uint64_t* s_hat, const uint64_t* s_hat_shoup, uint32_t B,
                            uint64_t K, uint64_t n, const uint8_t* qv, uint32_t d,

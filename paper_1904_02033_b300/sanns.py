@@ -47,6 +47,12 @@ _SIGS = {
     "sanns_distances": ([_VP, _VP, _VP, C.c_uint32, C.c_uint64, _VP, _VP, _VP, _VP], C.c_int),
     "sanns_distances_mac": ([_VP, _VP, _VP, C.c_uint32, _VP, _VP], C.c_int),
     "sanns_distances_finish": ([_VP, _VP, C.c_uint32, C.c_uint64, _VP, _VP, _VP, _VP], C.c_int),
+    "sanns_clusters_create": ([_VP, _VP, C.c_uint64, _VP, _VP, C.c_uint32, C.POINTER(_VP), _VP],
+                              C.c_int),
+    "sanns_clusters_free": ([_VP], None),
+    "sanns_gather_plan": ([_VP, _VP, C.c_uint32, C.c_uint32, _VP, _VP], C.c_int),
+    "sanns_distances_gather": ([_VP, _VP, _VP, C.c_uint32, _VP, C.c_uint32, C.c_uint64, _VP, _VP,
+                                _VP, _VP, _VP], C.c_int),
     "sanns_decrypt_shares": ([_VP, _VP, _VP, C.c_uint32, C.c_uint64, _VP, _VP, _VP], C.c_int),
 }
 
@@ -132,6 +138,16 @@ class Database:
     def __del__(self):
         if getattr(self, "handle", None) and _LIB is not None:
             _LIB.sanns_db_free(self.handle)
+            self.handle = None
+
+
+class Clusters:
+    def __init__(self, handle, ctx, n, C, offsets):
+        self.handle, self.ctx, self.n, self.C, self.offsets = handle, ctx, n, C, offsets
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _LIB is not None:
+            _LIB.sanns_clusters_free(self.handle)
             self.handle = None
 
 
@@ -252,3 +268,51 @@ def sanns_decrypt_shares(ctx: Context, sk: SecretKey, ct_out: torch.Tensor, n: i
     _check(load().sanns_decrypt_shares(ctx.handle, sk.handle, _ptr(ct_out), B, n, _ptr(q),
                                        _ptr(out), _stream(stream)))
     return out
+
+
+def sanns_clusters_create(ctx: Context, coords: torch.Tensor, offsets, members: torch.Tensor,
+                          stream=None) -> Clusters:
+    """coords uint8 [n][d] (CUDA), offsets uint64 [C+1] (numpy, host), members
+    uint32 (CUDA)."""
+    import numpy as np
+    off = np.ascontiguousarray(offsets, dtype=np.uint64)
+    assert coords.dtype == torch.uint8 and coords.shape[1] == ctx.d
+    assert members.dtype == torch.uint32
+    h = _VP()
+    _check(load().sanns_clusters_create(ctx.handle, _ptr(coords), coords.shape[0],
+                                        off.ctypes.data_as(C.c_void_p), _ptr(members),
+                                        len(off) - 1, C.byref(h), _stream(stream)))
+    return Clusters(h, ctx, coords.shape[0], len(off) - 1, off)
+
+
+def sanns_gather_plan(cl: Clusters, probes):
+    """probes: numpy uint32 [B][P] -> (n_b, blocks_b) numpy uint64 arrays."""
+    import numpy as np
+    pr = np.ascontiguousarray(probes, dtype=np.uint32)
+    B, P = pr.shape
+    n_b = np.zeros(B, dtype=np.uint64)
+    k_b = np.zeros(B, dtype=np.uint64)
+    _check(load().sanns_gather_plan(cl.handle, pr.ctypes.data_as(C.c_void_p), B, P,
+                                    n_b.ctypes.data_as(C.c_void_p),
+                                    k_b.ctypes.data_as(C.c_void_p)))
+    return n_b, k_b
+
+
+def sanns_distances_gather(ctx: Context, cl: Clusters, ct_in: torch.Tensor, probes,
+                           mask_seed: int, qids: torch.Tensor, with_ids: bool = True,
+                           stream=None):
+    """Returns (ct_out [sum K_b][2][L][N], srv_share [sum n_b], ids [sum n_b] or
+    None, n_b, blocks_b)."""
+    import numpy as np
+    pr = np.ascontiguousarray(probes, dtype=np.uint32)
+    B, P = pr.shape
+    assert ct_in.dtype == torch.uint64 and ct_in.shape == (B, ctx.d, 2, ctx.L, ctx.N)
+    n_b, k_b = sanns_gather_plan(cl, pr)
+    tot_k, tot_n = int(k_b.sum()), int(n_b.sum())
+    ct_out = torch.empty((max(tot_k, 1), 2, ctx.L, ctx.N), dtype=torch.uint64, device="cuda")
+    srv = torch.empty(max(tot_n, 1), dtype=torch.uint32, device="cuda")
+    ids = torch.empty(max(tot_n, 1), dtype=torch.uint32, device="cuda") if with_ids else None
+    _check(load().sanns_distances_gather(ctx.handle, cl.handle, _ptr(ct_in), B,
+                                         pr.ctypes.data_as(C.c_void_p), P, mask_seed, _ptr(qids),
+                                         _ptr(ct_out), _ptr(srv), _ptr(ids), _stream(stream)))
+    return ct_out[:tot_k], srv[:tot_n], (ids[:tot_n] if with_ids else None), n_b, k_b

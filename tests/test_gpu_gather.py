@@ -1,0 +1,77 @@
+"""GPU parity of the clustering-protocol gather path (one persistent launch
+over uneven per-query cluster gathers) against the oracle, which treats each
+query's gathered list as a permuted database."""
+import numpy as np
+import pytest
+import torch
+
+from oracle.bfv import Oracle
+from paper_1904_02033_b300 import inputs
+from paper_1904_02033_b300 import sanns as S
+
+pytestmark = pytest.mark.gpu
+
+
+def cu(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def gathered_list(offsets, members, probes_b):
+    return np.concatenate([members[offsets[c]:offsets[c + 1]] for c in probes_b]
+                          + [np.zeros(0, dtype=np.uint32)]).astype(np.uint32)
+
+
+@pytest.mark.parametrize("cfg,n,C,B,P", [
+    ((256, 2, 40, 0, 5), 3000, 20, 3, 4),
+    ((64, 2, 50, 0, 3), 500, 7, 2, 7),       # probes covering every cluster, tiny N
+    ((8192, 3, 60, 0, 4), 30000, 9, 2, 3),   # N = 8192, three 60-bit primes
+])
+def test_gather_matches_oracle(cfg, n, C, B, P):
+    N, L, bits, rule, d = cfg
+    rnd = np.random.default_rng(n)
+    coords = inputs.uniform_coords(n, d, 1)
+    # skewed cluster sizes, one empty cluster
+    w = inputs.zipf_weights(C, 1.1)
+    assign = rnd.choice(C, size=n, p=w)
+    assign[assign == C - 1] = 0
+    offsets, members = inputs.clusters_csr(assign, C)
+    assert offsets[C] - offsets[C - 1] == 0
+    probes = np.stack([rnd.permutation(C)[:P] for _ in range(B)]).astype(np.uint32)
+    probes[0, -1] = C - 1  # an empty cluster among the probes
+    q = inputs.uniform_coords(B, d, 2)
+    qids = np.array([5 + 3 * b for b in range(B)], dtype=np.uint64)
+
+    ctx = S.sanns_ctx_create(*cfg)
+    sk = S.sanns_keygen(ctx, 3)
+    cl = S.sanns_clusters_create(ctx, cu(coords), offsets, cu(members))
+    ct_in = S.sanns_encrypt_query(ctx, sk, cu(q), 4, cu(qids))
+    ct_out, srv, ids, n_b, k_b = S.sanns_distances_gather(ctx, cl, ct_in, probes, 6, cu(qids))
+    torch.cuda.synchronize()
+    ct_out, srv, ids = ct_out.cpu().numpy(), srv.cpu().numpy(), ids.cpu().numpy()
+    ct_np = ct_in.cpu().numpy()
+
+    O = Oracle(*cfg)
+    s, _ = O.keygen(3)
+    kb0 = nb0 = 0
+    for b in range(B):
+        g = gathered_list(offsets, members, probes[b])
+        assert int(n_b[b]) == len(g) and int(k_b[b]) == -(-len(g) // N)
+        assert np.array_equal(ids[nb0:nb0 + len(g)], g)
+        if len(g):
+            want_out, want_srv = O.distances(ct_np[b], coords, g, 6, int(qids[b]))
+            assert np.array_equal(ct_out[kb0:kb0 + int(k_b[b])], want_out)
+            assert np.array_equal(srv[nb0:nb0 + len(g)], want_srv)
+            cli = O.decrypt_shares(want_out, s, q[b], len(g))
+            brute = np.sum((coords[g].astype(np.int64) - q[b].astype(np.int64)) ** 2, axis=1)
+            assert np.array_equal((cli.astype(np.int64) + want_srv) % O.t, brute)
+        kb0 += int(k_b[b])
+        nb0 += len(g)
+
+
+def test_gather_rejects_bad_probe():
+    ctx = S.sanns_ctx_create(256, 2, 40, 0, 5)
+    coords = inputs.uniform_coords(100, 5, 1)
+    offsets, members = inputs.clusters_csr(np.arange(100) % 4, 4)
+    cl = S.sanns_clusters_create(ctx, cu(coords), offsets, cu(members))
+    with pytest.raises(S.SannsError):
+        S.sanns_gather_plan(cl, np.array([[0, 4]], dtype=np.uint32))

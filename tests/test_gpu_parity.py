@@ -136,7 +136,11 @@ def _pipeline(cfg, n, B, seed, perm=True):
 
 
 @pytest.mark.parametrize("cfg,n,B", [
-    (CONFIGS[0], 1, 1),
+    # a single 60-bit prime: Delta = floor(q / t) ~ 2^36 exceeds twice the
+    # noise, whose largest term is (Q mod t) floor(M / t) <= t d 255 ~ 2^33.6
+    # for the plaintext product M = sum_i m_i g_i (smaller primes are not
+    # decryptable at t ~ 2^24)
+    ((64, 1, 60, 0, 3), 1, 1),
     (CONFIGS[1], 600, 2),         # three blocks, ragged tail, two queries
     (CONFIGS[2], 700, 1),         # d = 17 (not a multiple of the 16-dim fold), t = 2^b_d
     (CONFIGS[3], 4096, 1),        # the one-block N = 4096 configuration
