@@ -215,6 +215,32 @@ int sanns_decrypt_shares(sanns_ctx *ctx, const sanns_sk *sk, const uint64_t *ct_
                          uint32_t B, uint64_t n, const uint8_t *q_dev, uint32_t *cli_share_dev,
                          void *stream);
 
+/*
+ * sanns_decrypt_shares_noalloc -- the paper has no counterpart to this entry
+ * point; it exists for callers that cannot allocate device memory while they
+ * run: code being captured into a CUDA graph, real-time loops that may not
+ * call cudaMalloc (it can synchronise the device and has unbounded latency),
+ * and processes held to a fixed device-memory budget.  Same arguments,
+ * kernels and results as sanns_decrypt_shares, but it allocates nothing: its
+ * scratch is a file-scope device array of sanns_decrypt_noalloc_max_words()
+ * = 4,194,304 uint64 words (32 MiB), which every GPU that loads the library
+ * holds until the process exits.
+ *   - B * ceil(n / N) * L * N must not exceed that maximum; larger requests
+ *     return SANNS_EINVAL before anything is launched (one N = 8192, L = 3
+ *     query fits up to n = 1,392,640 points).
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     before any stream capture.
+ *   - All calls share the one array and it keeps the last call's contents;
+ *     each call writes every word it later reads, so nothing is cleared, but
+ *     calls that overlap on the GPU (different streams, no ordering between
+ *     them) race on the array: order them on one stream or with events.
+ */
+int sanns_decrypt_shares_noalloc(sanns_ctx *ctx, const sanns_sk *sk, const uint64_t *ct_out_dev,
+                                 uint32_t B, uint64_t n, const uint8_t *q_dev,
+                                 uint32_t *cli_share_dev, void *stream);
+uint64_t sanns_decrypt_noalloc_max_words(void);
+
 /* Number of multiprocessors the persistent kernels size their grids by. */
 int sanns_device_sms(void);
 

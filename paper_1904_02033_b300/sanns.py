@@ -53,6 +53,9 @@ _SIGS = {
     "sanns_gather_plan": ([_VP, _VP, C.c_uint32, C.c_uint32, _VP, _VP], C.c_int),
     "sanns_distances_gather": ([_VP, _VP, _VP, C.c_uint32, _VP, C.c_uint32, C.c_uint64, _VP, _VP,
                                 _VP, _VP, _VP], C.c_int),
+    "sanns_decrypt_shares_noalloc": ([_VP, _VP, _VP, C.c_uint32, C.c_uint64, _VP, _VP, _VP],
+                                     C.c_int),
+    "sanns_decrypt_noalloc_max_words": ([], C.c_uint64),
     "sanns_decrypt_shares": ([_VP, _VP, _VP, C.c_uint32, C.c_uint64, _VP, _VP, _VP], C.c_int),
 }
 
@@ -316,3 +319,21 @@ def sanns_distances_gather(ctx: Context, cl: Clusters, ct_in: torch.Tensor, prob
                                          pr.ctypes.data_as(C.c_void_p), P, mask_seed, _ptr(qids),
                                          _ptr(ct_out), _ptr(srv), _ptr(ids), _stream(stream)))
     return ct_out[:tot_k], srv[:tot_n], (ids[:tot_n] if with_ids else None), n_b, k_b
+
+
+def sanns_decrypt_shares_noalloc(ctx: Context, sk: SecretKey, ct_out: torch.Tensor, n: int,
+                                 q: torch.Tensor, out: torch.Tensor | None = None, stream=None):
+    """Decryption that allocates no device memory inside the call (its scratch
+    is a fixed 32 MiB device array); `out` must be preallocated by callers
+    that cannot allocate at all."""
+    B = ct_out.shape[0]
+    assert q.dtype == torch.uint8 and q.shape == (B, ctx.d)
+    if out is None:
+        out = torch.empty((B, n), dtype=torch.uint32, device="cuda")
+    _check(load().sanns_decrypt_shares_noalloc(ctx.handle, sk.handle, _ptr(ct_out), B, n,
+                                               _ptr(q), _ptr(out), _stream(stream)))
+    return out
+
+
+def sanns_decrypt_noalloc_max_words() -> int:
+    return load().sanns_decrypt_noalloc_max_words()
