@@ -151,6 +151,8 @@ def run_gpu(args) -> None:
     srv = torch.empty((1, n), dtype=torch.uint32, device="cuda")
     stream = torch.cuda.current_stream()
     mask_seed = W["seed"] + 5
+    variant, variant_ms = S.sanns_autotune_mac(ctx, db, ct_all[0:1], ct_out, reps=3)
+    variant_names = S.sanns_mac_variants()
 
     def step(s):
         qi = s % W["n_queries"]
@@ -193,31 +195,52 @@ def run_gpu(args) -> None:
     mac_ms = [starts[s].elapsed_time(mac_end[s]) for s in timed]
     mac_avg = sum(mac_ms) / len(mac_ms)
 
-    # end-to-end through the C ABI: pinned host ct in, response + share out
-    ct_host = ct_all[: min(4, W["n_queries"])].cpu().pin_memory()
-    out_host = torch.empty((1, K, 2, L, N), dtype=torch.uint64).pin_memory()
-    srv_host = torch.empty((1, n), dtype=torch.uint32).pin_memory()
-    ct_dev = torch.empty((1, d, 2, L, N), dtype=torch.uint64, device="cuda")
-    e2e_steps = max(3, min(args.steps, 10))
+    # end-to-end through the C ABI: each step copies its query ciphertext from
+    # pinned host memory, runs sanns_distances and copies the response
+    # ciphertexts and the server share back; three streams overlap step s's
+    # compute with the upload of s+1 and the download of s-1.
+    nh = min(4, W["n_queries"])
+    ct_host = ct_all[:nh].cpu().pin_memory()
+    out_host = [torch.empty((1, K, 2, L, N), dtype=torch.uint64).pin_memory() for _ in range(2)]
+    srv_host = [torch.empty((1, n), dtype=torch.uint32).pin_memory() for _ in range(2)]
+    ct_dev = [torch.empty((1, d, 2, L, N), dtype=torch.uint64, device="cuda") for _ in range(2)]
+    out_dev = [torch.empty((1, K, 2, L, N), dtype=torch.uint64, device="cuda") for _ in range(2)]
+    srv_dev = [torch.empty((1, n), dtype=torch.uint32, device="cuda") for _ in range(2)]
+    s_up, s_cmp, s_dn = torch.cuda.Stream(), torch.cuda.Stream(), torch.cuda.Stream()
+    e2e_steps = max(10, min(args.steps, 100))
 
-    def e2e_step(s):
-        qi = s % ct_host.shape[0]
-        ct_dev.copy_(ct_host[qi:qi + 1], non_blocking=True)
-        S.sanns_distances(ctx, db, ct_dev, mask_seed, qids[qi:qi + 1], ct_out, srv, stream=stream)
-        out_host.copy_(ct_out, non_blocking=True)
-        srv_host.copy_(srv, non_blocking=True)
+    def run_e2e(nsteps):
+        up_done = [torch.cuda.Event() for _ in range(nsteps)]
+        cmp_done = [torch.cuda.Event() for _ in range(nsteps)]
+        dn_done = [torch.cuda.Event() for _ in range(nsteps)]
+        for s in range(nsteps):
+            u = s % 2
+            qi = s % nh
+            with torch.cuda.stream(s_up):
+                if s >= 2:
+                    s_up.wait_event(cmp_done[s - 2])      # ct_dev[u] free again
+                ct_dev[u].copy_(ct_host[qi:qi + 1], non_blocking=True)
+                up_done[s].record(s_up)
+            s_cmp.wait_event(up_done[s])
+            if s >= 2:
+                s_cmp.wait_event(dn_done[s - 2])          # out_dev[u] downloaded
+            S.sanns_distances(ctx, db, ct_dev[u], mask_seed, qids[qi:qi + 1], out_dev[u],
+                              srv_dev[u], stream=s_cmp)
+            cmp_done[s].record(s_cmp)
+            with torch.cuda.stream(s_dn):
+                s_dn.wait_event(cmp_done[s])
+                out_host[u].copy_(out_dev[u], non_blocking=True)
+                srv_host[u].copy_(srv_dev[u], non_blocking=True)
+                dn_done[s].record(s_dn)
+        return dn_done[-1]
 
-    for s in range(2):
-        e2e_step(s)
+    run_e2e(4)
     torch.cuda.synchronize()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for s in range(e2e_steps):
-        e2e_step(s)
-    e1.record(stream)
+    t_start = time.perf_counter()
+    last = run_e2e(e2e_steps)
+    last.synchronize()
     torch.cuda.synchronize()
-    e2e_ms = e0.elapsed_time(e1) / e2e_steps
+    e2e_ms = (time.perf_counter() - t_start) * 1e3 / e2e_steps
     if dist:
         tt = torch.tensor([e2e_ms], device="cuda")
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
@@ -241,6 +264,8 @@ def run_gpu(args) -> None:
                                    "60-bit primes, t=16957441",
                        "n": n, "d": d, "N": N, "L": L, "K": K, "queries_cycled": W["n_queries"],
                        "parallelism": f"replicas{world}" if world > 1 else "single",
+                       "mac_variant": variant_names[variant],
+                       "mac_variant_ms": dict(zip(variant_names, [round(x, 4) for x in variant_ms])),
                        "l2": "inputs larger than L2: the 3.1 GB encoded database is streamed "
                              "from HBM every step"},
             "latency_ms": {"p50": lat[len(lat) // 2],
@@ -252,7 +277,9 @@ def run_gpu(args) -> None:
                          "launch_ms": mac_avg},
             "e2e": {"value": world * n / (e2e_ms * 1e-3), "unit": UNIT,
                     "h2d_bytes_per_step": d * 2 * L * N * 8,
-                    "d2h_bytes_per_step": K * 2 * L * N * 8 + n * 4, "ms_per_step": e2e_ms},
+                    "d2h_bytes_per_step": K * 2 * L * N * 8 + n * 4, "ms_per_step": e2e_ms,
+                    "timing": "host wall clock over pipelined steps (3 streams: upload, "
+                              "compute, download)"},
             "gpu_launches": 2 * args.steps,
             "clocks": ck,
             "cpu_baseline": cpu,
@@ -338,8 +365,8 @@ def run_reference(args) -> None:
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=30)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=600)
+    ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="sanns", choices=["sanns", "reference"])
     ap.add_argument("--quick-cpu", action="store_true", help="smaller CPU baseline sample")
     ap.add_argument("--n", type=int, default=None,

@@ -205,6 +205,45 @@ int sanns_distances_gather(sanns_ctx *ctx, const sanns_clusters *cl, const uint6
                            uint32_t *ids_dev, void *stream);
 
 /*
+ * Launch variants of the MAC kernel (slots per lane, loads in flight, CTAs
+ * per SM).  sanns_autotune_mac runs every variant `reps` times on the given
+ * inputs (writing ct_out_dev as sanns_distances_mac would), stores the
+ * fastest in the context and returns its index (>= 0) or an error code;
+ * ms_out (host, sanns_mac_variants() floats, may be NULL) receives the mean
+ * time per launch.  Synchronous.  All variants compute identical results.
+ */
+int sanns_mac_variants(void);
+const char *sanns_mac_variant_name(int variant);
+int sanns_set_mac_variant(sanns_ctx *ctx, int variant);
+int sanns_autotune_mac(sanns_ctx *ctx, const sanns_db *db, const uint64_t *ct_in_dev, uint32_t B,
+                       uint64_t *ct_out_dev, int reps, float *ms_out, void *stream);
+
+/*
+ * Batched path on the tensor cores (no counterpart in the paper, which
+ * evaluates one query at a time): for B queries the per-slot work is the
+ * dense contraction (2B x d) . (d x K) mod q_j, run as an exact bf16 GEMM
+ * over balanced base-256 digits with fp32 accumulation (all partial sums are
+ * integers below 2^24 for d <= 128).
+ *   sanns_db_prepare_batched  builds the digit layout of the database once
+ *                             ([L][N][K][8 ceil(d/8)] bf16, twice the size of
+ *                             the encoded database) and its TMA descriptor.
+ *                             Requires d <= 128.  Synchronous.
+ *   sanns_distances_batched   same arguments and bit-identical results as
+ *                             sanns_distances; B <= 4096.
+ *   sanns_distances_batched_mac  its MAC stage alone (acc in NTT form).
+ *   sanns_device_status       synchronises `stream` and returns
+ *                             SANNS_ETIMEOUT (and clears it) if a bounded
+ *                             device-side wait of a batched launch gave up.
+ */
+int sanns_db_prepare_batched(sanns_ctx *ctx, sanns_db *db, void *stream);
+int sanns_distances_batched(sanns_ctx *ctx, const sanns_db *db, const uint64_t *ct_in_dev,
+                            uint32_t B, uint64_t mask_seed, const uint64_t *qids_dev,
+                            uint64_t *ct_out_dev, uint32_t *srv_share_dev, void *stream);
+int sanns_distances_batched_mac(sanns_ctx *ctx, const sanns_db *db, const uint64_t *ct_in_dev,
+                                uint32_t B, uint64_t *ct_out_dev, void *stream);
+int sanns_device_status(sanns_ctx *ctx, void *stream);
+
+/*
  * Client decryption (Pi_ls step 4) plus its local term: per query b and
  * position pos < n, m = round(t (c0 + c1 s mod Q) / Q) mod t (CRT over the L
  * primes), cli_share[b][pos] = (m + ||q_b||^2) mod t.  ct_out_dev

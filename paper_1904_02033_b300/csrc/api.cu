@@ -81,6 +81,7 @@ int sanns_ctx_create(const sanns_params* p, sanns_ctx** out) {
   cudaError_t e = cudaGetDevice(&c->device);
   if (e != cudaSuccess) { delete c; return cuda_fail(e, "cudaGetDevice"); }
   cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, c->device);
+  c->mac_variant = 1;
 
   const size_t per = (size_t)p->L * N;
   std::vector<uint64_t> host(4 * per);
@@ -95,6 +96,9 @@ int sanns_ctx_create(const sanns_params* p, sanns_ctx** out) {
   c->P.tw_shoup = c->d_tables + per;
   c->P.itw = c->d_tables + 2 * per;
   c->P.itw_shoup = c->d_tables + 3 * per;
+  e = cudaMalloc(&c->d_err, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(c->d_err, 0, sizeof(int));
+  if (e != cudaSuccess) { cudaFree(c->d_tables); delete c; return cuda_fail(e, "cudaMalloc(err)"); }
   *out = c;
   return SANNS_OK;
 }
@@ -102,6 +106,7 @@ int sanns_ctx_create(const sanns_params* p, sanns_ctx** out) {
 void sanns_ctx_free(sanns_ctx* ctx) {
   if (!ctx) return;
   cudaFree(ctx->d_tables);
+  cudaFree(ctx->d_err);
   delete ctx;
 }
 
@@ -212,6 +217,7 @@ int sanns_encode_db(sanns_ctx* ctx, const uint8_t* coords, uint64_t n_points, co
 
 void sanns_db_free(sanns_db* db) {
   if (!db) return;
+  cudaFree(db->d_plimb);
   cudaFree(db->d_pt);
   cudaFree(db->d_norms);
   delete db;
@@ -272,7 +278,7 @@ int sanns_distances_mac(sanns_ctx* ctx, const sanns_db* db, const uint64_t* ct_i
   if (!ct_in || !ct_out) return fail(SANNS_EINVAL, "NULL buffer");
   if (!aligned16(ct_in) || !aligned16(ct_out)) return fail(SANNS_EINVAL, "ct buffers must be 16-byte aligned");
   SANNS_CUDA(launch_mac(ctx->P, ct_in, db->d_pt, B, ctx->params.d, db->K, ct_out, ctx->sms,
-                        as_stream(stream)));
+                        ctx->mac_variant, as_stream(stream)));
   return SANNS_OK;
 }
 
@@ -285,6 +291,53 @@ int sanns_distances_finish(sanns_ctx* ctx, const sanns_db* db, uint32_t B, uint6
   SANNS_CUDA(launch_intt_mask(ctx->P, ct_out, db->d_norms, B, db->K, db->n, mask_seed, qids,
                               srv_share, as_stream(stream)));
   return SANNS_OK;
+}
+
+int sanns_mac_variants(void) { return mac_num_variants(); }
+
+const char* sanns_mac_variant_name(int v) { return mac_variant_name(v); }
+
+int sanns_set_mac_variant(sanns_ctx* ctx, int v) {
+  if (!ctx) return fail(SANNS_EINVAL, "ctx is NULL");
+  if (v < 0 || v >= mac_num_variants()) return fail(SANNS_EINVAL, "no such MAC variant");
+  ctx->mac_variant = v;
+  return SANNS_OK;
+}
+
+int sanns_autotune_mac(sanns_ctx* ctx, const sanns_db* db, const uint64_t* ct_in, uint32_t B,
+                       uint64_t* ct_out, int reps, float* ms_out, void* stream) {
+  int rc = check_distance_args(ctx, db, B);
+  if (rc) return rc;
+  if (B == 0 || !ct_in || !ct_out) return fail(SANNS_EINVAL, "NULL buffer or empty batch");
+  if (reps < 1) reps = 1;
+  cudaStream_t st = as_stream(stream);
+  cudaEvent_t e0, e1;
+  SANNS_CUDA(cudaEventCreate(&e0));
+  SANNS_CUDA(cudaEventCreate(&e1));
+  int best = -1;
+  float best_ms = 0.f;
+  for (int v = 0; v < mac_num_variants(); ++v) {
+    cudaError_t e = launch_mac(ctx->P, ct_in, db->d_pt, B, ctx->params.d, db->K, ct_out, ctx->sms, v, st);
+    if (e == cudaSuccess) e = cudaEventRecord(e0, st);
+    for (int r = 0; r < reps && e == cudaSuccess; ++r)
+      e = launch_mac(ctx->P, ct_in, db->d_pt, B, ctx->params.d, db->K, ct_out, ctx->sms, v, st);
+    if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (e != cudaSuccess) {
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      return cuda_fail(e, "autotune");
+    }
+    ms /= reps;
+    if (ms_out) ms_out[v] = ms;
+    if (best < 0 || ms < best_ms) { best = v; best_ms = ms; }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  ctx->mac_variant = best;
+  return best;
 }
 
 int sanns_distances(sanns_ctx* ctx, const sanns_db* db, const uint64_t* ct_in, uint32_t B,
@@ -393,6 +446,65 @@ int sanns_distances_gather(sanns_ctx* ctx, const sanns_clusters* cl, const uint6
   if (rc) return rc;
   SANNS_CUDA(launch_gather(ctx->P, ctx->params.d, cl, ct_in, B, probes, P, nb.data(), mask_seed, qids,
                            ct_out, srv_share, ids, ctx->sms, as_stream(stream)));
+  return SANNS_OK;
+}
+
+int sanns_db_prepare_batched(sanns_ctx* ctx, sanns_db* db, void* stream) {
+  if (!ctx || !db) return fail(SANNS_EINVAL, "ctx or db is NULL");
+  if (db->ctx != ctx) return fail(SANNS_EINVAL, "db belongs to another context");
+  if (ctx->params.d > 128) return fail(SANNS_EINVAL, "the batched path needs d <= 128 (exact fp32 sums)");
+  if (ctx->P.N < 32) return fail(SANNS_EINVAL, "the batched path needs N >= 32");
+  if (db->K > 0x7fffffffull) return fail(SANNS_EINVAL, "too many blocks");
+  int rc = check_device(ctx);
+  if (rc) return rc;
+  if (db->d_plimb) return SANNS_OK;
+  cudaStream_t st = as_stream(stream);
+  const size_t bytes = batched_limb_bytes(ctx->P.L, ctx->P.N, db->K, ctx->params.d);
+  uint16_t* pl = nullptr;
+  SANNS_CUDA(cudaMalloc(&pl, bytes));
+  cudaError_t e = launch_prepare_limbs(ctx->P, db->d_pt, db->K, ctx->params.d, pl, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) { cudaFree(pl); return cuda_fail(e, "prepare batched digits"); }
+  rc = make_limb_map(ctx->P, pl, db->K, ctx->params.d, db->limb_map);
+  if (rc) { cudaFree(pl); return rc; }
+  db->d_plimb = pl;
+  return SANNS_OK;
+}
+
+int sanns_distances_batched_mac(sanns_ctx* ctx, const sanns_db* db, const uint64_t* ct_in, uint32_t B,
+                                uint64_t* ct_out, void* stream) {
+  int rc = check_distance_args(ctx, db, B);
+  if (rc) return rc;
+  if (B == 0) return SANNS_OK;
+  if (!db->d_plimb) return fail(SANNS_EINVAL, "call sanns_db_prepare_batched first");
+  if (!ct_in || !ct_out) return fail(SANNS_EINVAL, "NULL buffer");
+  if (B > 4096) return fail(SANNS_EINVAL, "B must be <= 4096");
+  SANNS_CUDA(launch_batched_mac(ctx->P, db->limb_map, ct_in, B, ctx->params.d, db->K, ct_out, ctx->d_err,
+                                ctx->sms, as_stream(stream)));
+  return SANNS_OK;
+}
+
+int sanns_distances_batched(sanns_ctx* ctx, const sanns_db* db, const uint64_t* ct_in, uint32_t B,
+                            uint64_t mask_seed, const uint64_t* qids, uint64_t* ct_out, uint32_t* srv_share,
+                            void* stream) {
+  int rc = sanns_distances_batched_mac(ctx, db, ct_in, B, ct_out, stream);
+  if (rc) return rc;
+  return sanns_distances_finish(ctx, db, B, mask_seed, qids, ct_out, srv_share, stream);
+}
+
+int sanns_device_status(sanns_ctx* ctx, void* stream) {
+  if (!ctx) return fail(SANNS_EINVAL, "ctx is NULL");
+  int rc = check_device(ctx);
+  if (rc) return rc;
+  cudaStream_t st = as_stream(stream);
+  int h = 0;
+  SANNS_CUDA(cudaMemcpyAsync(&h, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  SANNS_CUDA(cudaStreamSynchronize(st));
+  if (h) {
+    SANNS_CUDA(cudaMemsetAsync(ctx->d_err, 0, sizeof(int), st));
+    SANNS_CUDA(cudaStreamSynchronize(st));
+    return fail(h, "a bounded device-side wait gave up");
+  }
   return SANNS_OK;
 }
 

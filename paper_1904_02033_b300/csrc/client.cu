@@ -8,10 +8,10 @@ namespace sanns {
 
 namespace {
 
-__host__ __device__ inline uint32_t blk_threads(uint32_t N) { return N / 2 < 512 ? N / 2 : 512; }
+__host__ __device__ inline uint32_t blk_threads(uint32_t N) { return N / 16 < 32 ? 32 : (N / 16 > 256 ? 256 : N / 16); }
 
 // One block per prime j: s is drawn by every block (cheap) and lifted mod q_j.
-__global__ void keygen_kernel(PrimeSet P, uint64_t seed, int8_t* s, uint64_t* s_hat,
+__global__ void __launch_bounds__(512) keygen_kernel(PrimeSet P, uint64_t seed, int8_t* s, uint64_t* s_hat,
                               uint64_t* s_hat_shoup) {
   extern __shared__ uint64_t sa[];
   const uint32_t N = P.N, j = blockIdx.x;
@@ -24,7 +24,7 @@ __global__ void keygen_kernel(PrimeSet P, uint64_t seed, int8_t* s, uint64_t* s_
       uint64_t lo, hi;
       draw_pair(blk, v, lo, hi);
       int sv = (int)(lo % 3) - 1;
-      sa[4 * u + v] = sv < 0 ? q - 1 : (uint64_t)sv;
+      sa[SP(4 * u + v)] = sv < 0 ? q - 1 : (uint64_t)sv;
       if (j == 0) s[4 * u + v] = (int8_t)sv;
     }
   }
@@ -32,7 +32,7 @@ __global__ void keygen_kernel(PrimeSet P, uint64_t seed, int8_t* s, uint64_t* s_
   ntt_forward_smem(sa, P, j);
   __syncthreads();
   for (uint32_t x = threadIdx.x; x < N; x += blockDim.x) {
-    uint64_t v = sa[x];
+    uint64_t v = sa[SP(x)];
     s_hat[(size_t)j * N + x] = v;
     s_hat_shoup[(size_t)j * N + x] = (uint64_t)(((u128)v << 64) / q);
   }
@@ -40,7 +40,7 @@ __global__ void keygen_kernel(PrimeSet P, uint64_t seed, int8_t* s, uint64_t* s_
 
 // One block per (i, j, b): NTT of the error polynomial of coordinate i, then
 // c1 = a, c0 = -a s_hat + e_hat + Delta m slot by slot.
-__global__ void encrypt_kernel(PrimeSet P, const uint64_t* __restrict__ s_hat,
+__global__ void __launch_bounds__(512) encrypt_kernel(PrimeSet P, const uint64_t* __restrict__ s_hat,
                                const uint64_t* __restrict__ s_hat_shoup,
                                const uint8_t* __restrict__ qv, uint32_t d, uint64_t seed,
                                const uint64_t* __restrict__ qids, uint64_t* __restrict__ ct) {
@@ -59,7 +59,7 @@ __global__ void encrypt_kernel(PrimeSet P, const uint64_t* __restrict__ s_hat,
       draw_pair(blk, v, lo, hi);
       const uint64_t m21 = (1ull << 21) - 1;
       int e = __popcll(lo & m21) - __popcll((lo >> 21) & m21);
-      sa[4 * u + v] = e < 0 ? q - (uint64_t)(-e) : (uint64_t)e;
+      sa[SP(4 * u + v)] = e < 0 ? q - (uint64_t)(-e) : (uint64_t)e;
     }
   }
   __syncthreads();
@@ -83,7 +83,7 @@ __global__ void encrypt_kernel(PrimeSet P, const uint64_t* __restrict__ s_hat,
       const uint32_t s = 4 * u + v;
       const uint64_t a = mod_q128(lo, hi, q);
       const uint64_t as = mul_shoup(a, sh[s], shs[s], q);
-      uint64_t v0 = sub_mod(sa[s], as, q);
+      uint64_t v0 = sub_mod(sa[SP(s)], as, q);
       v0 = add_mod(v0, dm, q);
       c1[s] = a;
       c0[s] = v0;
@@ -92,7 +92,7 @@ __global__ void encrypt_kernel(PrimeSet P, const uint64_t* __restrict__ s_hat,
 }
 
 // Decryption, first half: one block per (b, k, j): v = c0 + INTT(NTT(c1) s_hat).
-__global__ void decrypt_phase_kernel(PrimeSet P, const uint64_t* __restrict__ ct_out,
+__global__ void __launch_bounds__(512) decrypt_phase_kernel(PrimeSet P, const uint64_t* __restrict__ ct_out,
                                      const uint64_t* __restrict__ s_hat,
                                      const uint64_t* __restrict__ s_hat_shoup, uint64_t K,
                                      uint64_t* __restrict__ v) {
@@ -104,18 +104,18 @@ __global__ void decrypt_phase_kernel(PrimeSet P, const uint64_t* __restrict__ ct
   const uint64_t q = P.q[j];
   const uint64_t* c0 = ct_out + ((bk * 2 + 0) * L + j) * N;
   const uint64_t* c1 = ct_out + ((bk * 2 + 1) * L + j) * N;
-  for (uint32_t x = threadIdx.x; x < N; x += blockDim.x) sa[x] = c1[x];
+  for (uint32_t x = threadIdx.x; x < N; x += blockDim.x) sa[SP(x)] = c1[x];
   __syncthreads();
   ntt_forward_smem(sa, P, j);
   __syncthreads();
   const uint64_t* sh = s_hat + (size_t)j * N;
   const uint64_t* shs = s_hat_shoup + (size_t)j * N;
-  for (uint32_t x = threadIdx.x; x < N; x += blockDim.x) sa[x] = mul_shoup(sa[x], sh[x], shs[x], q);
+  for (uint32_t x = threadIdx.x; x < N; x += blockDim.x) sa[SP(x)] = mul_shoup(sa[SP(x)], sh[x], shs[x], q);
   __syncthreads();
   ntt_inverse_smem(sa, P, j);
   __syncthreads();
   uint64_t* o = v + idx * N;
-  for (uint32_t x = threadIdx.x; x < N; x += blockDim.x) o[x] = add_mod(sa[x], c0[x], q);
+  for (uint32_t x = threadIdx.x; x < N; x += blockDim.x) o[x] = add_mod(sa[SP(x)], c0[x], q);
 }
 
 // Decryption, second half, one thread per (b, pos):
@@ -161,7 +161,7 @@ __global__ void scale_round_kernel(PrimeSet P, const uint64_t* __restrict__ v, u
 
 cudaError_t launch_keygen(const PrimeSet& P, uint64_t seed, int8_t* s, uint64_t* s_hat,
                           uint64_t* s_hat_shoup, cudaStream_t st) {
-  const size_t smem = sizeof(uint64_t) * P.N;
+  const size_t smem = sizeof(uint64_t) * ntt_smem_words(P.N);
   cudaError_t e = cudaFuncSetAttribute(keygen_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return e;
@@ -173,7 +173,7 @@ cudaError_t launch_encrypt(const PrimeSet& P, const uint64_t* s_hat, const uint6
                            const uint8_t* qv, uint32_t B, uint32_t d, uint64_t seed,
                            const uint64_t* qids, uint64_t* ct, cudaStream_t st) {
   if (B == 0) return cudaSuccess;
-  const size_t smem = sizeof(uint64_t) * P.N;
+  const size_t smem = sizeof(uint64_t) * ntt_smem_words(P.N);
   cudaError_t e = cudaFuncSetAttribute(encrypt_kernel,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
@@ -189,7 +189,7 @@ cudaError_t launch_decrypt(const PrimeSet& P, const uint64_t* ct_out, const int8
                            uint64_t* scratch, uint32_t* cli_share, cudaStream_t st) {
   (void)s;
   if (B == 0 || n == 0) return cudaSuccess;
-  const size_t smem = sizeof(uint64_t) * P.N;
+  const size_t smem = sizeof(uint64_t) * ntt_smem_words(P.N);
   cudaError_t e = cudaFuncSetAttribute(decrypt_phase_kernel,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;

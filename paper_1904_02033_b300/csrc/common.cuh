@@ -157,51 +157,127 @@ __device__ __forceinline__ void draw_pair(const uint32_t blk[16], int u, uint64_
 // block.  Forward: Cooley-Tukey with Harvey's lazy butterflies, values kept
 // in [0, 4q); output slot s = a(psi^(2 brv(s) + 1)), canonicalised to [0, q).
 // Inverse: Gentleman-Sande, values in [0, 2q), N^-1 folded at the end.
+// Stages are grouped four at a time: a thread loads 16 elements that are
+// closed under four consecutive stages, runs them in registers and writes
+// back, so N = 8192 takes one radix-2 stage and three radix-16 passes.
 // Callers synchronise the block before and after.
 // ------------------------------------------------------------------------
+// Shared-memory polynomials are stored padded, one spare word after every
+// 16, so that the stride-16 accesses of the radix-16 passes hit distinct banks.
+__host__ __device__ __forceinline__ uint32_t SP(uint32_t x) { return x + (x >> 4); }
+__host__ __device__ __forceinline__ uint32_t ntt_smem_words(uint32_t N) { return N + N / 16; }
+
+__device__ __forceinline__ void fwd_bfly(uint64_t& X, uint64_t& Y, uint64_t w, uint64_t ws,
+                                         uint64_t q, uint64_t q2) {
+  X = csub(X, q2);
+  const uint64_t T = mul_shoup_lazy(Y, w, ws, q);
+  Y = X - T + q2;
+  X = X + T;
+}
+
+__device__ __forceinline__ void inv_bfly(uint64_t& X, uint64_t& Y, uint64_t w, uint64_t ws,
+                                         uint64_t q, uint64_t q2) {
+  const uint64_t S = csub(X + Y, q2);
+  const uint64_t D = X - Y + q2;
+  X = S;
+  Y = mul_shoup_lazy(D, w, ws, q);
+}
+
 __device__ __forceinline__ void ntt_forward_smem(uint64_t* a, const PrimeSet& P, int j) {
   const uint32_t N = P.N, logN = P.logN, half = N >> 1;
   const uint64_t q = P.q[j], q2 = 2 * q;
   const uint64_t* tw = P.tw + (size_t)j * N;
   const uint64_t* tws = P.tw_shoup + (size_t)j * N;
-  for (uint32_t m = 1, lt = logN - 1; m < N; m <<= 1, --lt) {
-    const uint32_t t = 1u << lt;
+  const uint32_t r2 = logN & 3;  // leading radix-2 stages
+  uint32_t t = half;
+  for (uint32_t st = 0; st < r2; ++st, t >>= 1) {
+    const uint32_t m = N / (2 * t);
     for (uint32_t bf = threadIdx.x; bf < half; bf += blockDim.x) {
-      uint32_t i = bf >> lt, jj = bf & (t - 1);
-      uint32_t x = (i << (lt + 1)) + jj;
-      uint64_t w = __ldg(tw + m + i), ws = __ldg(tws + m + i);
-      uint64_t X = a[x], Y = a[x + t];
-      X = csub(X, q2);
-      uint64_t T = mul_shoup_lazy(Y, w, ws, q);
-      a[x] = X + T;
-      a[x + t] = X - T + q2;
+      const uint32_t i = bf / t, x = 2 * i * t + (bf & (t - 1));
+      uint64_t X = a[SP(x)], Y = a[SP(x + t)];
+      fwd_bfly(X, Y, __ldg(tw + m + i), __ldg(tws + m + i), q, q2);
+      a[SP(x)] = X;
+      a[SP(x + t)] = Y;
     }
     __syncthreads();
   }
-  for (uint32_t x = threadIdx.x; x < N; x += blockDim.x) a[x] = csub(csub(a[x], q2), q);
+  for (; t >= 8; t >>= 4) {  // stages t, t/2, t/4, t/8
+    const uint32_t S = t >> 3;
+    for (uint32_t th = threadIdx.x; th < N / 16; th += blockDim.x) {
+      const uint32_t g = th / S, b = th & (S - 1);
+      const uint32_t x0 = g * 2 * t + b;
+      uint64_t v[16];
+#pragma unroll
+      for (int k = 0; k < 16; ++k) v[k] = a[SP(x0 + k * S)];
+#pragma unroll
+      for (int s = 0; s < 4; ++s) {
+        const uint32_t ts = t >> s, hk = 8 >> s, m = N / (2 * ts);
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+          if (k & hk) continue;
+          const uint32_t i = (x0 + k * S) / (2 * ts);
+          fwd_bfly(v[k], v[k + hk], __ldg(tw + m + i), __ldg(tws + m + i), q, q2);
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < 16; ++k) a[SP(x0 + k * S)] = csub(csub(v[k], q2), q);
+    }
+    __syncthreads();
+  }
+  if (r2 == logN) {  // N < 16: no radix-16 pass canonicalised the values
+    for (uint32_t x = threadIdx.x; x < N; x += blockDim.x) a[SP(x)] = csub(csub(a[SP(x)], q2), q);
+  }
 }
 
 __device__ __forceinline__ void ntt_inverse_smem(uint64_t* a, const PrimeSet& P, int j) {
-  const uint32_t N = P.N, half = N >> 1;
+  const uint32_t N = P.N, logN = P.logN, half = N >> 1;
   const uint64_t q = P.q[j], q2 = 2 * q;
   const uint64_t* tw = P.itw + (size_t)j * N;
   const uint64_t* tws = P.itw_shoup + (size_t)j * N;
-  for (uint32_t lt = 0, h = half; h >= 1; ++lt, h >>= 1) {
-    const uint32_t t = 1u << lt;
-    for (uint32_t bf = threadIdx.x; bf < half; bf += blockDim.x) {
-      uint32_t i = bf >> lt, jj = bf & (t - 1);
-      uint32_t x = (i << (lt + 1)) + jj;
-      uint64_t w = __ldg(tw + h + i), ws = __ldg(tws + h + i);
-      uint64_t X = a[x], Y = a[x + t];
-      uint64_t S = csub(X + Y, q2);
-      uint64_t D = X - Y + q2;
-      a[x] = S;
-      a[x + t] = mul_shoup_lazy(D, w, ws, q);
+  const uint32_t passes = logN >> 2;
+  const uint64_t ni = P.n_inv[j], nis = P.n_inv_shoup[j];
+  uint32_t t = 1;
+  for (uint32_t ps = 0; ps < passes; ++ps, t <<= 4) {  // stages t, 2t, 4t, 8t
+    const bool last = (ps + 1 == passes) && (t * 16 == N);
+    for (uint32_t th = threadIdx.x; th < N / 16; th += blockDim.x) {
+      const uint32_t g = th / t, b = th & (t - 1);
+      const uint32_t x0 = g * 16 * t + b;
+      uint64_t v[16];
+#pragma unroll
+      for (int k = 0; k < 16; ++k) v[k] = a[SP(x0 + k * t)];
+#pragma unroll
+      for (int s = 0; s < 4; ++s) {
+        const uint32_t ts = t << s, hk = 1 << s, h = N / (2 * ts);
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+          if (k & hk) continue;
+          const uint32_t i = (x0 + k * t) / (2 * ts);
+          inv_bfly(v[k], v[k + hk], __ldg(tw + h + i), __ldg(tws + h + i), q, q2);
+        }
+      }
+      if (last) {
+#pragma unroll
+        for (int k = 0; k < 16; ++k) v[k] = mul_shoup(v[k], ni, nis, q);
+      }
+#pragma unroll
+      for (int k = 0; k < 16; ++k) a[SP(x0 + k * t)] = v[k];
     }
     __syncthreads();
   }
-  const uint64_t ni = P.n_inv[j], nis = P.n_inv_shoup[j];
-  for (uint32_t x = threadIdx.x; x < N; x += blockDim.x) a[x] = mul_shoup(a[x], ni, nis, q);
+  if (t < N) {
+    for (; t < N; t <<= 1) {
+      const uint32_t h = N / (2 * t);
+      for (uint32_t bf = threadIdx.x; bf < half; bf += blockDim.x) {
+        const uint32_t i = bf / t, x = 2 * i * t + (bf & (t - 1));
+        uint64_t X = a[SP(x)], Y = a[SP(x + t)];
+        inv_bfly(X, Y, __ldg(tw + h + i), __ldg(tws + h + i), q, q2);
+        a[SP(x)] = X;
+        a[SP(x + t)] = Y;
+      }
+      __syncthreads();
+    }
+    for (uint32_t x = threadIdx.x; x < N; x += blockDim.x) a[SP(x)] = mul_shoup(a[SP(x)], ni, nis, q);
+  }
 }
 
 }  // namespace sanns

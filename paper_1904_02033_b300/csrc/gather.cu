@@ -15,7 +15,7 @@
 //   persistent one block per multiprocessor walks the (query, block) work
 //              items of every query -- uneven per-query counts included --
 //              and runs encode (NTT) -> MAC -> INTT -> mask for each item,
-//              the accumulators of SPT slots per thread kept in registers.
+//              with the polynomial and both accumulators in shared memory.
 #include <vector>
 
 #include "internal.h"
@@ -85,47 +85,46 @@ __device__ __forceinline__ uint64_t mont_mul(uint64_t c, uint64_t p_mont, uint64
   return csub(redc128((u128)c * p_mont, q, qn), q);
 }
 
-template <int SPT>
+// One block per work item at a time; shared memory holds the polynomial being
+// transformed and the two accumulators (c0, c1) of the current prime.
 __global__ void __launch_bounds__(512, 1)
 gather_kernel(PrimeSet P, uint32_t d, uint64_t W, const GatherItem* __restrict__ items,
               const GatherQuery* __restrict__ qs, const uint8_t* __restrict__ gco,
               const uint32_t* __restrict__ gnorm, const uint64_t* __restrict__ ct_in,
               uint64_t mask_seed, const uint64_t* __restrict__ qids,
               uint64_t* __restrict__ ct_out, uint32_t* __restrict__ srv_share) {
-  extern __shared__ uint64_t poly[];
+  extern __shared__ uint64_t smem[];
   const uint32_t N = P.N, L = P.L;
+  const uint32_t PW = ntt_smem_words(N);
+  uint64_t* poly = smem;
+  uint64_t* acc0 = smem + PW;
+  uint64_t* acc1 = smem + 2 * PW;
   for (uint64_t w = blockIdx.x; w < W; w += gridDim.x) {
     const GatherItem it = items[w];
     const GatherQuery Q = qs[it.b];
     const uint8_t* g = gco + w * (uint64_t)d * N;
     for (uint32_t j = 0; j < L; ++j) {
       const uint64_t q = P.q[j], qn = P.q_neg_inv[j];
-      uint64_t acc0[SPT], acc1[SPT];
-#pragma unroll
-      for (int r = 0; r < SPT; ++r) acc0[r] = acc1[r] = 0;
+      for (uint32_t s = threadIdx.x; s < N; s += blockDim.x) acc0[SP(s)] = acc1[SP(s)] = 0;
       for (uint32_t i = 0; i < d; ++i) {
         __syncthreads();
-        for (uint32_t x = threadIdx.x; x < N; x += blockDim.x) poly[x] = g[(uint64_t)i * N + x];
+        for (uint32_t x = threadIdx.x; x < N; x += blockDim.x) poly[SP(x)] = g[(uint64_t)i * N + x];
         __syncthreads();
         ntt_forward_smem(poly, P, (int)j);
         __syncthreads();
         const uint64_t* c0 = ct_in + ((((uint64_t)it.b * d + i) * 2 + 0) * L + j) * N;
         const uint64_t* c1 = ct_in + ((((uint64_t)it.b * d + i) * 2 + 1) * L + j) * N;
-#pragma unroll
-        for (int r = 0; r < SPT; ++r) {
-          const uint32_t s = threadIdx.x + r * blockDim.x;
-          const uint64_t pm = mul_shoup(poly[s], P.r64[j], P.r64_shoup[j], q);
-          acc0[r] = add_mod(acc0[r], mont_mul(__ldg(c0 + s), pm, q, qn), q);
-          acc1[r] = add_mod(acc1[r], mont_mul(__ldg(c1 + s), pm, q, qn), q);
+        for (uint32_t s = threadIdx.x; s < N; s += blockDim.x) {
+          const uint64_t pm = mul_shoup(poly[SP(s)], P.r64[j], P.r64_shoup[j], q);
+          acc0[SP(s)] = add_mod(acc0[SP(s)], mont_mul(__ldg(c0 + s), pm, q, qn), q);
+          acc1[SP(s)] = add_mod(acc1[SP(s)], mont_mul(__ldg(c1 + s), pm, q, qn), q);
         }
       }
       // back to coefficient form, mask, store
       for (uint32_t c = 0; c < 2; ++c) {
+        uint64_t* a = c == 0 ? acc0 : acc1;
         __syncthreads();
-#pragma unroll
-        for (int r = 0; r < SPT; ++r) poly[threadIdx.x + r * blockDim.x] = c == 0 ? acc0[r] : acc1[r];
-        __syncthreads();
-        ntt_inverse_smem(poly, P, (int)j);
+        ntt_inverse_smem(a, P, (int)j);
         __syncthreads();
         if (c == 0) {
           const uint64_t dl = P.delta[j], dls = P.delta_shoup[j];
@@ -141,7 +140,7 @@ gather_kernel(PrimeSet P, uint32_t d, uint64_t W, const GatherItem* __restrict__
               const uint64_t rr = mod_t128(lo, hi, P);
               const uint32_t x = 4 * u + v;
               const uint64_t val = mod_t64((uint64_t)gnorm[w * N + x] + rr, P.t, P.t_barrett);
-              poly[x] = add_mod(poly[x], mul_shoup(val, dl, dls, q), q);
+              a[SP(x)] = add_mod(a[SP(x)], mul_shoup(val, dl, dls, q), q);
               const uint64_t pos = pos0 + v;
               if (j == 0 && pos < Q.n)
                 srv_share[Q.pos_off + pos] = (uint32_t)(rr == 0 ? 0 : P.t - rr);
@@ -150,7 +149,7 @@ gather_kernel(PrimeSet P, uint32_t d, uint64_t W, const GatherItem* __restrict__
           __syncthreads();
         }
         uint64_t* dst = ct_out + ((it.blk * 2 + c) * L + j) * N;
-        for (uint32_t x = threadIdx.x; x < N; x += blockDim.x) dst[x] = poly[x];
+        for (uint32_t x = threadIdx.x; x < N; x += blockDim.x) dst[x] = a[SP(x)];
       }
     }
   }
@@ -164,7 +163,7 @@ cudaError_t launch_check_indices(const uint32_t* idx, uint64_t m, uint64_t bound
   return cudaGetLastError();
 }
 
-int gather_threads(uint32_t N) { return N >= 8192 ? 512 : (N >= 512 ? (int)(N / 16) : 32); }
+int gather_threads(uint32_t N) { return N >= 1024 ? 512 : (int)(N / 2); }
 
 cudaError_t launch_gather(const PrimeSet& P, uint32_t d, const sanns_clusters* cl,
                           const uint64_t* ct_in, uint32_t B, const uint32_t* probes_host,
@@ -222,29 +221,16 @@ cudaError_t launch_gather(const PrimeSet& P, uint32_t d, const sanns_clusters* c
   }
   if (e == cudaSuccess) {
     const int th = gather_threads(N);
-    const int spt = (int)(N / th);
-    const size_t smem = sizeof(uint64_t) * N;
-    unsigned grid = (unsigned)(W < (uint64_t)(sms > 0 ? sms : 148) ? W : (uint64_t)(sms > 0 ? sms : 148));
-#define SANNS_GATHER_CASE(S)                                                                     \
-  case S:                                                                                        \
-    e = cudaFuncSetAttribute(gather_kernel<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,      \
-                             (int)smem);                                                         \
-    if (e == cudaSuccess) {                                                                      \
-      gather_kernel<S><<<grid, th, smem, st>>>(P, d, W, d_items, d_qs, scratch + o_gco,          \
-                                               reinterpret_cast<const uint32_t*>(scratch + o_norm), \
-                                               ct_in, mask_seed, qids, ct_out, srv_share);       \
-      e = cudaGetLastError();                                                                    \
-    }                                                                                            \
-    break;
-    switch (spt) {
-      SANNS_GATHER_CASE(2)
-      SANNS_GATHER_CASE(4)
-      SANNS_GATHER_CASE(8)
-      SANNS_GATHER_CASE(16)
-      default:
-        e = cudaErrorInvalidValue;
+    const size_t smem = sizeof(uint64_t) * 3 * ntt_smem_words(N);
+    const uint64_t nsm = (uint64_t)(sms > 0 ? sms : 148);
+    const unsigned grid = (unsigned)(W < nsm ? W : nsm);
+    e = cudaFuncSetAttribute(gather_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) {
+      gather_kernel<<<grid, th, smem, st>>>(P, d, W, d_items, d_qs, scratch + o_gco,
+                                            reinterpret_cast<const uint32_t*>(scratch + o_norm),
+                                            ct_in, mask_seed, qids, ct_out, srv_share);
+      e = cudaGetLastError();
     }
-#undef SANNS_GATHER_CASE
   }
   cudaError_t e2 = cudaFreeAsync(scratch, st);
   return e != cudaSuccess ? e : e2;

@@ -13,6 +13,8 @@ struct sanns_ctx {
   uint64_t* d_tables;       // one allocation for the four twiddle tables
   int device;
   int sms;
+  int mac_variant;          // launch variant of the MAC kernel (autotuned)
+  int* d_err;               // device error word raised by bounded waits
 };
 
 struct sanns_sk {
@@ -27,6 +29,8 @@ struct sanns_db {
   uint64_t n, K;
   uint64_t* d_pt;           // [K][L][d][N]
   uint32_t* d_norms;        // [K N]
+  uint16_t* d_plimb;        // [L][N][K][8 dpad] bf16 digits (batched path), or NULL
+  alignas(64) unsigned char limb_map[128];  // TMA descriptor of d_plimb
 };
 
 struct sanns_clusters {
@@ -69,8 +73,11 @@ cudaError_t launch_encrypt(const PrimeSet& P, const uint64_t* s_hat, const uint6
 cudaError_t launch_encode(const PrimeSet& P, const uint8_t* coords, uint64_t n_points,
                           const uint32_t* perm, uint64_t n, uint32_t d, uint64_t K, uint64_t* pt,
                           uint32_t* norms, int* bad, cudaStream_t st);
+int mac_num_variants();
+const char* mac_variant_name(int v);
 cudaError_t launch_mac(const PrimeSet& P, const uint64_t* ct, const uint64_t* pt, uint32_t B,
-                       uint32_t d, uint64_t K, uint64_t* out, int sms, cudaStream_t st);
+                       uint32_t d, uint64_t K, uint64_t* out, int sms, int variant,
+                       cudaStream_t st);
 cudaError_t launch_intt_mask(const PrimeSet& P, uint64_t* ct_out, const uint32_t* norms,
                              uint32_t B, uint64_t K, uint64_t n, uint64_t mask_seed,
                              const uint64_t* qids, uint32_t* srv_share, cudaStream_t st);
@@ -82,6 +89,13 @@ cudaError_t launch_gather(const PrimeSet& P, uint32_t d, const sanns_clusters* c
                           uint32_t Pr, const uint64_t* n_b, uint64_t mask_seed,
                           const uint64_t* qids, uint64_t* ct_out, uint32_t* srv_share,
                           uint32_t* ids, int sms, cudaStream_t st);
+size_t batched_limb_bytes(uint32_t L, uint32_t N, uint64_t K, uint32_t d);
+cudaError_t launch_prepare_limbs(const PrimeSet& P, const uint64_t* pt, uint64_t K, uint32_t d,
+                                 uint16_t* plimb, cudaStream_t st);
+int make_limb_map(const PrimeSet& P, const uint16_t* plimb, uint64_t K, uint32_t d, void* map_out);
+cudaError_t launch_batched_mac(const PrimeSet& P, const void* map, const uint64_t* ct, uint32_t B,
+                               uint32_t d, uint64_t K, uint64_t* out, int* err, int sms,
+                               cudaStream_t st);
 cudaError_t launch_decrypt(const PrimeSet& P, const uint64_t* ct_out, const int8_t* s,
                            const uint64_t* s_hat, const uint64_t* s_hat_shoup, uint32_t B,
                            uint64_t K, uint64_t n, const uint8_t* qv, uint32_t d,

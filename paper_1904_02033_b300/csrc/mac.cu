@@ -4,8 +4,9 @@
 //     acc = sum_i ct[b][i][c][j][s] * pt[k][j][i][s]  mod q_j.
 //
 // The encoded database (d L 8 bytes per point) is streamed from HBM exactly
-// once per query; the query ciphertext tile for 64 slots stays in shared
-// memory while every block k of that tile streams past it.
+// once per query; the query ciphertext tile for 32 SPL slots stays in shared
+// memory while every block k of that tile streams past it (each warp takes a
+// different k).
 //
 // Arithmetic: the query values are put in Montgomery form (x 2^64 mod q) and
 // both operands are split into 30-bit halves x = x1 2^30 + x0.  The four
@@ -14,15 +15,15 @@
 // dimensions the partials are folded into an exact 128-bit sum R.  R < d q^2
 // < 2^128 for d <= 224, q < 2^60, and one Montgomery reduction of R gives
 // sum_i ct pt mod q below 15 q, finished by four conditional subtractions.
+//
+// Launch variants (slots per lane, dimensions per load batch, threads, CTAs
+// per SM) trade registers for loads in flight; sanns_autotune_mac times them.
 #include "internal.h"
 
 namespace sanns {
 
 namespace {
 
-constexpr int kMacThreads = 512;
-constexpr int kMacWarps = kMacThreads / 32;
-constexpr uint32_t kSlotTile = 64;  // two slots per lane
 constexpr uint32_t kMask30 = (1u << 30) - 1;
 
 struct MacArgs {
@@ -30,7 +31,7 @@ struct MacArgs {
   const uint64_t* pt;  // [K][L][d][N], NTT form
   uint64_t* out;       // [B][K][2][L][N]
   uint64_t K;
-  uint64_t total;      // B L (N / 64) K work items (tile, block)
+  uint64_t total;      // B L (N / tile) K work items (tile, block)
   uint32_t d;
 };
 
@@ -42,11 +43,39 @@ __device__ __forceinline__ void mac4(uint64_t& aL, uint64_t& aM1, uint64_t& aM2,
   aH += (uint64_t)xh * yh;
 }
 
-__global__ void __launch_bounds__(kMacThreads, 1) mac_kernel(PrimeSet P, MacArgs A) {
-  // ct tile: [d][2][32 lanes] x {lo(s0), hi(s0), lo(s1), hi(s1)}
+template <int SPL>
+struct PtVec;
+template <>
+struct PtVec<1> {
+  typedef unsigned long long T;
+  static __device__ __forceinline__ T load(const uint64_t* p) {
+    return __ldcs(reinterpret_cast<const unsigned long long*>(p));
+  }
+  static __device__ __forceinline__ T zero() { return 0ull; }
+  static __device__ __forceinline__ uint64_t get(const T& v, int) { return v; }
+};
+template <>
+struct PtVec<2> {
+  typedef ulonglong2 T;
+  static __device__ __forceinline__ T load(const uint64_t* p) {
+    return __ldcs(reinterpret_cast<const ulonglong2*>(p));
+  }
+  static __device__ __forceinline__ T zero() { return make_ulonglong2(0, 0); }
+  static __device__ __forceinline__ uint64_t get(const T& v, int s) { return s ? v.y : v.x; }
+};
+
+// ct tile in shared memory, per (dimension i, lane): for SPL = 1 one uint4
+// {c0 lo, c0 hi, c1 lo, c1 hi}; for SPL = 2 two uint4 (c0, c1), each
+// {lo(s0), hi(s0), lo(s1), hi(s1)}.
+template <int SPL, int UNR, int THREADS, int MINB>
+__global__ void __launch_bounds__(THREADS, MINB) mac_kernel(PrimeSet P, MacArgs A) {
   extern __shared__ uint4 cts[];
+  constexpr int WARPS = THREADS / 32;
+  constexpr uint32_t TILE = 32 * SPL;
+  constexpr int NOUT = 2 * SPL;  // (c, slot) pairs per lane
+  typedef PtVec<SPL> V;
   const uint32_t N = P.N, L = P.L, d = A.d;
-  const uint32_t tiles = N / kSlotTile;
+  const uint32_t tiles = N / TILE;
   const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const uint64_t w_begin = blockIdx.x * A.total / gridDim.x;
   const uint64_t w_end = (blockIdx.x + 1) * A.total / gridDim.x;
@@ -63,88 +92,140 @@ __global__ void __launch_bounds__(kMacThreads, 1) mac_kernel(PrimeSet P, MacArgs
     const uint64_t q = P.q[j];
 
     __syncthreads();  // previous tile fully consumed
-    for (uint32_t e = threadIdx.x; e < d * 64; e += kMacThreads) {
+    for (uint32_t e = threadIdx.x; e < d * 2 * 32; e += THREADS) {
       const uint32_t l = e & 31, ci = e >> 5, c = ci & 1, i = ci >> 1;
-      const uint64_t* src = A.ct + ((((b * d + i) * 2 + c) * L + j) * N) + st * kSlotTile + 2 * l;
-      const ulonglong2 v = *reinterpret_cast<const ulonglong2*>(src);
-      const uint64_t m0 = mul_shoup(v.x, P.r64[j], P.r64_shoup[j], q);
-      const uint64_t m1 = mul_shoup(v.y, P.r64[j], P.r64_shoup[j], q);
-      cts[e] = make_uint4((uint32_t)m0 & kMask30, (uint32_t)(m0 >> 30), (uint32_t)m1 & kMask30,
-                          (uint32_t)(m1 >> 30));
+      const uint64_t* src = A.ct + ((((b * d + i) * 2 + c) * L + j) * N) + st * TILE + SPL * l;
+      uint64_t m[SPL];
+#pragma unroll
+      for (int s = 0; s < SPL; ++s) m[s] = mul_shoup(src[s], P.r64[j], P.r64_shoup[j], q);
+      if (SPL == 1) {
+        uint32_t* dst = reinterpret_cast<uint32_t*>(&cts[i * 32 + l]) + 2 * c;
+        dst[0] = (uint32_t)m[0] & kMask30;
+        dst[1] = (uint32_t)(m[0] >> 30);
+      } else {
+        cts[(i * 2 + c) * 32 + l] = make_uint4((uint32_t)m[0] & kMask30, (uint32_t)(m[0] >> 30),
+                                               (uint32_t)m[SPL - 1] & kMask30,
+                                               (uint32_t)(m[SPL - 1] >> 30));
+      }
     }
     __syncthreads();
 
-    for (uint32_t kk = warp; kk < nk; kk += kMacWarps) {
+    for (uint32_t kk = warp; kk < nk; kk += WARPS) {
       const uint64_t k = k_first + kk;
-      const uint64_t* p = A.pt + ((k * L + j) * d) * N + st * kSlotTile + 2 * lane;
-      u128 R[4];
-      uint64_t aL[4], aM1[4], aM2[4], aH[4];
+      const uint64_t* p = A.pt + ((k * L + j) * d) * N + st * TILE + SPL * lane;
+      u128 R[NOUT];
+      uint64_t aL[NOUT], aM1[NOUT], aM2[NOUT], aH[NOUT];
 #pragma unroll
-      for (int o = 0; o < 4; ++o) { R[o] = 0; aL[o] = aM1[o] = aM2[o] = aH[o] = 0; }
+      for (int o = 0; o < NOUT; ++o) { R[o] = 0; aL[o] = aM1[o] = aM2[o] = aH[o] = 0; }
 
       for (uint32_t i0 = 0; i0 < d; i0 += 16) {
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          ulonglong2 pv[8];
+        for (int h = 0; h < 16 / UNR; ++h) {
+          typename V::T pv[UNR];
 #pragma unroll
-          for (int v = 0; v < 8; ++v) {
-            const uint32_t i = i0 + 8 * h + v;
-            pv[v] = i < d ? __ldcs(reinterpret_cast<const ulonglong2*>(p + (uint64_t)i * N))
-                          : make_ulonglong2(0, 0);
+          for (int v = 0; v < UNR; ++v) {
+            const uint32_t i = i0 + UNR * h + v;
+            pv[v] = i < d ? V::load(p + (uint64_t)i * N) : V::zero();
           }
 #pragma unroll
-          for (int v = 0; v < 8; ++v) {
-            const uint32_t i = i0 + 8 * h + v;
+          for (int v = 0; v < UNR; ++v) {
+            const uint32_t i = i0 + UNR * h + v;
             const uint32_t ii = i < d ? i : d - 1;  // beyond d the pt values are zero
-            const uint4 x0 = cts[(ii * 2 + 0) * 32 + lane];
-            const uint4 x1 = cts[(ii * 2 + 1) * 32 + lane];
-            const uint32_t y0l = (uint32_t)pv[v].x & kMask30, y0h = (uint32_t)(pv[v].x >> 30);
-            const uint32_t y1l = (uint32_t)pv[v].y & kMask30, y1h = (uint32_t)(pv[v].y >> 30);
-            mac4(aL[0], aM1[0], aM2[0], aH[0], x0.x, x0.y, y0l, y0h);  // c0, slot 0
-            mac4(aL[1], aM1[1], aM2[1], aH[1], x0.z, x0.w, y1l, y1h);  // c0, slot 1
-            mac4(aL[2], aM1[2], aM2[2], aH[2], x1.x, x1.y, y0l, y0h);  // c1, slot 0
-            mac4(aL[3], aM1[3], aM2[3], aH[3], x1.z, x1.w, y1l, y1h);  // c1, slot 1
+#pragma unroll
+            for (int s = 0; s < SPL; ++s) {
+              const uint64_t y = V::get(pv[v], s);
+              const uint32_t yl = (uint32_t)y & kMask30, yh = (uint32_t)(y >> 30);
+              if (SPL == 1) {
+                const uint4 x = cts[ii * 32 + lane];
+                mac4(aL[0], aM1[0], aM2[0], aH[0], x.x, x.y, yl, yh);  // c0
+                mac4(aL[1], aM1[1], aM2[1], aH[1], x.z, x.w, yl, yh);  // c1
+              } else {
+                const uint4 x0 = cts[(ii * 2 + 0) * 32 + lane];
+                const uint4 x1 = cts[(ii * 2 + 1) * 32 + lane];
+                const uint32_t c0l = s ? x0.z : x0.x, c0h = s ? x0.w : x0.y;
+                const uint32_t c1l = s ? x1.z : x1.x, c1h = s ? x1.w : x1.y;
+                mac4(aL[s], aM1[s], aM2[s], aH[s], c0l, c0h, yl, yh);                  // c0
+                mac4(aL[2 + s], aM1[2 + s], aM2[2 + s], aH[2 + s], c1l, c1h, yl, yh);  // c1
+              }
+            }
           }
         }
 #pragma unroll
-        for (int o = 0; o < 4; ++o) {
+        for (int o = 0; o < NOUT; ++o) {
           const u128 m = (u128)aM1[o] + aM2[o];
           R[o] += (u128)aL[o] + (m << 30) + ((u128)aH[o] << 60);
           aL[o] = aM1[o] = aM2[o] = aH[o] = 0;
         }
       }
       const uint64_t qn = P.q_neg_inv[j];
-      uint64_t r[4];
+      uint64_t r[NOUT];
 #pragma unroll
-      for (int o = 0; o < 4; ++o) r[o] = reduce_below_16q(redc128(R[o], q, qn), q);
-      uint64_t* o0 = A.out + (((b * A.K + k) * 2 + 0) * L + j) * N + st * kSlotTile + 2 * lane;
-      uint64_t* o1 = A.out + (((b * A.K + k) * 2 + 1) * L + j) * N + st * kSlotTile + 2 * lane;
-      *reinterpret_cast<ulonglong2*>(o0) = make_ulonglong2(r[0], r[1]);
-      *reinterpret_cast<ulonglong2*>(o1) = make_ulonglong2(r[2], r[3]);
+      for (int o = 0; o < NOUT; ++o) r[o] = reduce_below_16q(redc128(R[o], q, qn), q);
+      uint64_t* o0 = A.out + (((b * A.K + k) * 2 + 0) * L + j) * N + st * TILE + SPL * lane;
+      uint64_t* o1 = A.out + (((b * A.K + k) * 2 + 1) * L + j) * N + st * TILE + SPL * lane;
+      if (SPL == 1) {
+        // c0 at o[0], c1 at o[1] (layout of the SPL = 1 accumulators)
+        *o0 = r[0];
+        *o1 = r[1];
+      } else {
+        *reinterpret_cast<ulonglong2*>(o0) = make_ulonglong2(r[0], r[1]);
+        *reinterpret_cast<ulonglong2*>(o1) = make_ulonglong2(r[2 % NOUT], r[3 % NOUT]);
+      }
     }
     w = run_end;
   }
 }
 
+struct MacVariant {
+  void (*fn)(PrimeSet, MacArgs);
+  int spl, threads, ctas_per_sm;
+  const char* name;
+};
+
+const MacVariant kVariants[] = {
+    {mac_kernel<2, 8, 512, 1>, 2, 512, 1, "spl2_unr8_512x1"},
+    {mac_kernel<1, 16, 256, 3>, 1, 256, 3, "spl1_unr16_256x3"},
+    {mac_kernel<1, 8, 256, 3>, 1, 256, 3, "spl1_unr8_256x3"},
+    {mac_kernel<1, 16, 384, 2>, 1, 384, 2, "spl1_unr16_384x2"},
+};
+constexpr int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
+
 }  // namespace
 
+int mac_num_variants() { return kNumVariants; }
+const char* mac_variant_name(int v) { return (v >= 0 && v < kNumVariants) ? kVariants[v].name : ""; }
+
 cudaError_t launch_mac(const PrimeSet& P, const uint64_t* ct, const uint64_t* pt, uint32_t B,
-                       uint32_t d, uint64_t K, uint64_t* out, int sms, cudaStream_t st) {
+                       uint32_t d, uint64_t K, uint64_t* out, int sms, int variant,
+                       cudaStream_t st) {
+  if (variant < 0 || variant >= kNumVariants) return cudaErrorInvalidValue;
+  const MacVariant& V = kVariants[variant];
+  const uint32_t tile = 32u * V.spl;
   MacArgs A;
   A.ct = ct;
   A.pt = pt;
   A.out = out;
   A.K = K;
   A.d = d;
-  A.total = (uint64_t)B * P.L * (P.N / kSlotTile) * K;
+  A.total = (uint64_t)B * P.L * (P.N / tile) * K;
   if (A.total == 0) return cudaSuccess;
-  const size_t smem = sizeof(uint4) * 64 * d;
-  cudaError_t e = cudaFuncSetAttribute(mac_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem);
-  if (e != cudaSuccess) return e;
-  uint64_t grid = (uint64_t)(sms > 0 ? sms : 148);
+  const size_t smem = sizeof(uint4) * 32 * d * V.spl;
+  // shared-memory opt-in once per variant (the attribute is per function)
+  static bool configured[kNumVariants] = {};
+  static size_t configured_smem[kNumVariants] = {};
+  if (!configured[variant] || configured_smem[variant] < smem) {
+    cudaError_t e = cudaFuncSetAttribute(V.fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)(smem > 48 * 1024 ? smem : 48 * 1024));
+    if (e != cudaSuccess) return e;
+    configured[variant] = true;
+    configured_smem[variant] = smem > 48 * 1024 ? smem : 48 * 1024;
+  }
+  int per_sm = V.ctas_per_sm;
+  // fewer co-resident CTAs when the ct tile is large
+  while (per_sm > 1 && smem * per_sm > 220 * 1024) --per_sm;
+  uint64_t grid = (uint64_t)(sms > 0 ? sms : 148) * per_sm;
   if (grid > A.total) grid = A.total;
-  mac_kernel<<<(unsigned)grid, kMacThreads, smem, st>>>(P, A);
+  V.fn<<<(unsigned)grid, V.threads, smem, st>>>(P, A);
   return cudaGetLastError();
 }
 

@@ -9,26 +9,26 @@ namespace sanns {
 
 namespace {
 
-__host__ __device__ inline uint32_t ntt_threads(uint32_t N) { return N / 2 < 512 ? N / 2 : 512; }
+__host__ __device__ inline uint32_t ntt_threads(uint32_t N) { return N / 16 < 32 ? 32 : (N / 16 > 256 ? 256 : N / 16); }
 
 // One block per polynomial: data [count][L][N], polynomial p uses prime p % L.
-__global__ void ntt_kernel(PrimeSet P, uint64_t* data, int inverse) {
+__global__ void __launch_bounds__(512) ntt_kernel(PrimeSet P, uint64_t* data, int inverse) {
   extern __shared__ uint64_t sa[];
   const uint32_t N = P.N;
   const uint64_t poly = blockIdx.x;
   const int j = (int)(poly % P.L);
   uint64_t* g = data + poly * N;
-  for (uint32_t x = threadIdx.x; x < N; x += blockDim.x) sa[x] = g[x];
+  for (uint32_t x = threadIdx.x; x < N; x += blockDim.x) sa[SP(x)] = g[x];
   __syncthreads();
   if (inverse) ntt_inverse_smem(sa, P, j);
   else ntt_forward_smem(sa, P, j);
   __syncthreads();
-  for (uint32_t x = threadIdx.x; x < N; x += blockDim.x) g[x] = sa[x];
+  for (uint32_t x = threadIdx.x; x < N; x += blockDim.x) g[x] = sa[SP(x)];
 }
 
 // Encoding: block (k, i) builds coordinate i of positions kN .. kN+N-1 and
 // writes its NTT for every prime into pt[k][j][i][:].
-__global__ void encode_kernel(PrimeSet P, const uint8_t* __restrict__ coords, uint64_t n_points,
+__global__ void __launch_bounds__(512) encode_kernel(PrimeSet P, const uint8_t* __restrict__ coords, uint64_t n_points,
                               const uint32_t* __restrict__ perm, uint64_t n, uint32_t d,
                               uint64_t* __restrict__ pt, int* bad) {
   extern __shared__ uint64_t sa[];
@@ -44,13 +44,13 @@ __global__ void encode_kernel(PrimeSet P, const uint8_t* __restrict__ coords, ui
         if (id < n_points) v = coords[id * d + i];
         else if (j == 0) atomicExch(bad, 1);
       }
-      sa[x] = v;
+      sa[SP(x)] = v;
     }
     __syncthreads();
     ntt_forward_smem(sa, P, j);
     __syncthreads();
     uint64_t* dst = pt + ((k * P.L + j) * d + i) * N;
-    for (uint32_t x = threadIdx.x; x < N; x += blockDim.x) dst[x] = sa[x];
+    for (uint32_t x = threadIdx.x; x < N; x += blockDim.x) dst[x] = sa[SP(x)];
     __syncthreads();
   }
 }
@@ -71,14 +71,37 @@ __global__ void norms_kernel(const uint8_t* __restrict__ coords, uint64_t n_poin
   norms[pos] = s;
 }
 
-// Fused epilogue, one block per (b, k, c, j) polynomial of ct_out (in place):
-// INTT; for c = 0 add Delta_j ((||p||^2 + r) mod t) per coefficient, r drawn
-// from ChaCha20 stream (mask_seed, 4, qid_b) at position kN + x; the j = 0
-// block also writes the server share (t - r) mod t for positions < n.
-__global__ void intt_mask_kernel(PrimeSet P, uint64_t* __restrict__ ct_out,
+// The server's mask, drawn once per position: r = uniform mod t from ChaCha20
+// stream (mask_seed, 4, qid_b) at position pos; srv_share[b][pos] = (t - r)
+// mod t for pos < n.  One thread per four positions (one ChaCha20 block).
+__global__ void mask_share_kernel(PrimeSet P, uint32_t B, uint64_t n, uint64_t mask_seed,
+                                  const uint64_t* __restrict__ qids,
+                                  uint32_t* __restrict__ srv_share) {
+  const uint64_t groups = (n + 3) / 4;
+  const uint64_t gid = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+  if (gid >= (uint64_t)B * groups) return;
+  const uint64_t b = gid / groups, u = gid % groups;
+  uint32_t blk[16];
+  chacha20_block(mask_seed, kPurposeMask, qids[b], (uint32_t)u, blk);
+#pragma unroll
+  for (int v = 0; v < 4; ++v) {
+    const uint64_t pos = 4 * u + v;
+    if (pos >= n) break;
+    uint64_t lo, hi;
+    draw_pair(blk, v, lo, hi);
+    const uint64_t r = mod_t128(lo, hi, P);
+    srv_share[b * n + pos] = (uint32_t)(r == 0 ? 0 : P.t - r);
+  }
+}
+
+// Epilogue of the distance step, one block per (b, k, c, j) polynomial of
+// ct_out (in place): INTT; for c = 0 add Delta_j ((||p||^2 + r) mod t) per
+// coefficient.  r is recovered from the server share written by
+// mask_share_kernel; padding positions (pos >= n) draw it directly.
+__global__ void __launch_bounds__(256) intt_mask_kernel(PrimeSet P, uint64_t* __restrict__ ct_out,
                                  const uint32_t* __restrict__ norms, uint64_t K, uint64_t n,
                                  uint64_t mask_seed, const uint64_t* __restrict__ qids,
-                                 uint32_t* __restrict__ srv_share) {
+                                 const uint32_t* __restrict__ srv_share) {
   extern __shared__ uint64_t sa[];
   const uint32_t N = P.N, L = P.L;
   const uint64_t poly = blockIdx.x;                 // ((b K + k) 2 + c) L + j
@@ -87,32 +110,42 @@ __global__ void intt_mask_kernel(PrimeSet P, uint64_t* __restrict__ ct_out,
   const uint64_t bk = poly / (2 * L);
   const uint64_t k = bk % K, b = bk / K;
   uint64_t* g = ct_out + poly * N;
-  for (uint32_t x = threadIdx.x; x < N; x += blockDim.x) sa[x] = g[x];
+  for (uint32_t x = threadIdx.x; x < N; x += blockDim.x) sa[SP(x)] = g[x];
   __syncthreads();
   ntt_inverse_smem(sa, P, j);
   __syncthreads();
   if (c == 0) {
-    const uint64_t q = P.q[j], dl = P.delta[j], dls = P.delta_shoup[j];
-    const uint64_t qid = qids[b];
+    const uint64_t q = P.q[j], dl = P.delta[j], dls = P.delta_shoup[j], t = P.t;
+    const uint32_t* sh = srv_share + b * n;
     for (uint32_t u = threadIdx.x; u < N / 4; u += blockDim.x) {
       const uint64_t pos0 = k * N + 4 * u;
-      uint32_t blk[16];
-      chacha20_block(mask_seed, kPurposeMask, qid, (uint32_t)(pos0 / 4), blk);
+      uint64_t r[4];
+      if (pos0 + 3 < n) {
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+          const uint64_t sv = sh[pos0 + v];
+          r[v] = sv == 0 ? 0 : t - sv;
+        }
+      } else {
+        uint32_t blk[16];
+        chacha20_block(mask_seed, kPurposeMask, qids[b], (uint32_t)(pos0 / 4), blk);
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+          uint64_t lo, hi;
+          draw_pair(blk, v, lo, hi);
+          r[v] = mod_t128(lo, hi, P);
+        }
+      }
 #pragma unroll
       for (int v = 0; v < 4; ++v) {
-        uint64_t lo, hi;
-        draw_pair(blk, v, lo, hi);
-        const uint64_t r = mod_t128(lo, hi, P);
-        const uint64_t pos = pos0 + v;
-        const uint64_t val = mod_t64((uint64_t)norms[pos] + r, P.t, P.t_barrett);
+        const uint64_t val = mod_t64((uint64_t)norms[pos0 + v] + r[v], t, P.t_barrett);
         const uint32_t x = 4 * u + v;
-        sa[x] = add_mod(sa[x], mul_shoup(val, dl, dls, q), q);
-        if (j == 0 && pos < n) srv_share[b * n + pos] = (uint32_t)(r == 0 ? 0 : P.t - r);
+        sa[SP(x)] = add_mod(sa[SP(x)], mul_shoup(val, dl, dls, q), q);
       }
     }
     __syncthreads();
   }
-  for (uint32_t x = threadIdx.x; x < N; x += blockDim.x) g[x] = sa[x];
+  for (uint32_t x = threadIdx.x; x < N; x += blockDim.x) g[x] = sa[SP(x)];
 }
 
 }  // namespace
@@ -121,7 +154,7 @@ cudaError_t launch_ntt(const PrimeSet& P, uint64_t* data, uint64_t count, bool i
                        cudaStream_t st) {
   const uint64_t polys = count * P.L;
   if (polys == 0) return cudaSuccess;
-  const size_t smem = sizeof(uint64_t) * P.N;
+  const size_t smem = sizeof(uint64_t) * ntt_smem_words(P.N);
   cudaError_t e = cudaFuncSetAttribute(ntt_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return e;
@@ -132,7 +165,7 @@ cudaError_t launch_ntt(const PrimeSet& P, uint64_t* data, uint64_t count, bool i
 cudaError_t launch_encode(const PrimeSet& P, const uint8_t* coords, uint64_t n_points,
                           const uint32_t* perm, uint64_t n, uint32_t d, uint64_t K, uint64_t* pt,
                           uint32_t* norms, int* bad, cudaStream_t st) {
-  const size_t smem = sizeof(uint64_t) * P.N;
+  const size_t smem = sizeof(uint64_t) * ntt_smem_words(P.N);
   cudaError_t e = cudaFuncSetAttribute(encode_kernel,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
@@ -151,10 +184,19 @@ cudaError_t launch_intt_mask(const PrimeSet& P, uint64_t* ct_out, const uint32_t
                              const uint64_t* qids, uint32_t* srv_share, cudaStream_t st) {
   const uint64_t polys = (uint64_t)B * K * 2 * P.L;
   if (polys == 0) return cudaSuccess;
-  const size_t smem = sizeof(uint64_t) * P.N;
-  cudaError_t e = cudaFuncSetAttribute(intt_mask_kernel,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const uint64_t groups = (uint64_t)B * ((n + 3) / 4);
+  mask_share_kernel<<<(unsigned)((groups + 255) / 256), 256, 0, st>>>(P, B, n, mask_seed, qids,
+                                                                     srv_share);
+  cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
+  const size_t smem = sizeof(uint64_t) * ntt_smem_words(P.N);
+  static bool configured = false;
+  if (!configured) {
+    e = cudaFuncSetAttribute(intt_mask_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(sizeof(uint64_t) * ntt_smem_words(kMaxN)));
+    if (e != cudaSuccess) return e;
+    configured = true;
+  }
   intt_mask_kernel<<<(unsigned)polys, ntt_threads(P.N), smem, st>>>(P, ct_out, norms, K, n,
                                                                     mask_seed, qids, srv_share);
   return cudaGetLastError();

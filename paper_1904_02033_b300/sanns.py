@@ -56,6 +56,15 @@ _SIGS = {
     "sanns_decrypt_shares_noalloc": ([_VP, _VP, _VP, C.c_uint32, C.c_uint64, _VP, _VP, _VP],
                                      C.c_int),
     "sanns_decrypt_noalloc_max_words": ([], C.c_uint64),
+    "sanns_mac_variants": ([], C.c_int),
+    "sanns_mac_variant_name": ([C.c_int], C.c_char_p),
+    "sanns_set_mac_variant": ([_VP, C.c_int], C.c_int),
+    "sanns_autotune_mac": ([_VP, _VP, _VP, C.c_uint32, _VP, C.c_int, _VP, _VP], C.c_int),
+    "sanns_db_prepare_batched": ([_VP, _VP, _VP], C.c_int),
+    "sanns_distances_batched": ([_VP, _VP, _VP, C.c_uint32, C.c_uint64, _VP, _VP, _VP, _VP],
+                                C.c_int),
+    "sanns_distances_batched_mac": ([_VP, _VP, _VP, C.c_uint32, _VP, _VP], C.c_int),
+    "sanns_device_status": ([_VP, _VP], C.c_int),
     "sanns_decrypt_shares": ([_VP, _VP, _VP, C.c_uint32, C.c_uint64, _VP, _VP, _VP], C.c_int),
 }
 
@@ -337,3 +346,60 @@ def sanns_decrypt_shares_noalloc(ctx: Context, sk: SecretKey, ct_out: torch.Tens
 
 def sanns_decrypt_noalloc_max_words() -> int:
     return load().sanns_decrypt_noalloc_max_words()
+
+
+def sanns_mac_variants() -> list[str]:
+    lib = load()
+    return [lib.sanns_mac_variant_name(v).decode() for v in range(lib.sanns_mac_variants())]
+
+
+def sanns_set_mac_variant(ctx: Context, variant: int):
+    _check(load().sanns_set_mac_variant(ctx.handle, variant))
+
+
+def sanns_autotune_mac(ctx: Context, db: Database, ct_in: torch.Tensor, ct_out: torch.Tensor,
+                       reps: int = 3, stream=None):
+    """Times every MAC launch variant, keeps the fastest; returns (index, ms list)."""
+    n = load().sanns_mac_variants()
+    ms = (C.c_float * n)()
+    B = ct_in.shape[0]
+    rc = load().sanns_autotune_mac(ctx.handle, db.handle, _ptr(ct_in), B, _ptr(ct_out), reps, ms,
+                                   _stream(stream))
+    if rc < 0:
+        _check(rc)
+    return rc, list(ms)
+
+
+def sanns_db_prepare_batched(ctx: Context, db: Database, stream=None):
+    _check(load().sanns_db_prepare_batched(ctx.handle, db.handle, _stream(stream)))
+
+
+def sanns_distances_batched(ctx: Context, db: Database, ct_in: torch.Tensor, mask_seed: int,
+                            qids: torch.Tensor, ct_out: torch.Tensor | None = None,
+                            srv_share: torch.Tensor | None = None, stream=None):
+    B = ct_in.shape[0]
+    assert ct_in.dtype == torch.uint64 and ct_in.shape == (B, ctx.d, 2, ctx.L, ctx.N)
+    assert qids.dtype == torch.uint64 and qids.numel() == B
+    if ct_out is None:
+        ct_out = torch.empty((B, db.K, 2, ctx.L, ctx.N), dtype=torch.uint64, device="cuda")
+    if srv_share is None:
+        srv_share = torch.empty((B, db.n), dtype=torch.uint32, device="cuda")
+    _check(load().sanns_distances_batched(ctx.handle, db.handle, _ptr(ct_in), B, mask_seed,
+                                          _ptr(qids), _ptr(ct_out), _ptr(srv_share),
+                                          _stream(stream)))
+    return ct_out, srv_share
+
+
+def sanns_distances_batched_mac(ctx: Context, db: Database, ct_in: torch.Tensor,
+                                ct_out: torch.Tensor | None = None, stream=None):
+    B = ct_in.shape[0]
+    assert ct_in.dtype == torch.uint64 and ct_in.shape == (B, ctx.d, 2, ctx.L, ctx.N)
+    if ct_out is None:
+        ct_out = torch.empty((B, db.K, 2, ctx.L, ctx.N), dtype=torch.uint64, device="cuda")
+    _check(load().sanns_distances_batched_mac(ctx.handle, db.handle, _ptr(ct_in), B, _ptr(ct_out),
+                                              _stream(stream)))
+    return ct_out
+
+
+def sanns_device_status(ctx: Context, stream=None):
+    _check(load().sanns_device_status(ctx.handle, _stream(stream)))

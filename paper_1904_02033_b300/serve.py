@@ -1,0 +1,197 @@
+"""Continuous-batching server for encrypted distance queries.
+
+Keeps keys-independent state resident (each database's encoded plaintexts
+and, for the tensor-core path, its digit layout) and serves a stream of
+encrypted queries.  Requests that arrive while other batches are on the GPU
+wait until an execution slot and device memory free up; then every waiting
+request of one database (up to `max_batch`, FIFO) is admitted as one batch
+and launched on its own stream, so batches overlap on the device.  A batch
+of `batched_min` or more queries runs on the tensor-core path, smaller ones
+on the per-query path; both give bit-identical ciphertexts, so a request's
+result does not depend on what it was batched with.
+
+The scheduler is plain host logic over an `Executor` interface, which makes
+it testable without a GPU (tests drive it with a fake executor and a fake
+clock).
+"""
+from __future__ import annotations
+
+import collections
+import dataclasses
+import time
+from typing import Callable, Protocol
+
+
+@dataclasses.dataclass
+class Request:
+    rid: int
+    db: str
+    arrival: float              # seconds on the scheduler clock
+    payload: object = None      # executor-specific (query ciphertext, qid)
+    start: float | None = None
+    done: float | None = None
+    result: object = None
+
+    @property
+    def latency(self) -> float | None:
+        return None if self.done is None else self.done - self.arrival
+
+
+class Executor(Protocol):
+    def bytes_for(self, db: str, n_queries: int) -> int: ...
+    def launch(self, db: str, reqs: list[Request], slot: int) -> object: ...
+    def ready(self, handle: object) -> bool: ...
+    def finish(self, handle: object, reqs: list[Request]) -> None: ...
+
+
+@dataclasses.dataclass
+class Stats:
+    latencies: list = dataclasses.field(default_factory=list)
+    batches: list = dataclasses.field(default_factory=list)   # (db, size, t_launch)
+    deferred: int = 0                                          # admissions held back for memory
+
+    def percentile(self, p: float) -> float:
+        xs = sorted(self.latencies)
+        if not xs:
+            return float("nan")
+        k = min(len(xs) - 1, max(0, int(round(p / 100.0 * (len(xs) - 1)))))
+        return xs[k]
+
+
+class Scheduler:
+    """Admission by free execution slots and a device-memory budget."""
+
+    def __init__(self, executor: Executor, max_batch: int = 128, slots: int = 3,
+                 mem_budget: int = 1 << 40, clock: Callable[[], float] = time.perf_counter):
+        self.ex = executor
+        self.max_batch = max_batch
+        self.slots = slots
+        self.mem_budget = mem_budget
+        self.clock = clock
+        self.waiting: dict[str, collections.deque] = collections.defaultdict(collections.deque)
+        self.inflight: list[tuple[object, list[Request], int, int]] = []  # handle, reqs, bytes, slot
+        self.mem_used = 0
+        self.stats = Stats()
+
+    def submit(self, req: Request):
+        self.waiting[req.db].append(req)
+
+    def _free_slot(self) -> int | None:
+        used = {s for _, _, _, s in self.inflight}
+        for s in range(self.slots):
+            if s not in used:
+                return s
+        return None
+
+    def poll(self) -> int:
+        """Retire finished batches, then admit as many waiting batches as slots
+        and memory allow.  Returns the number of requests retired."""
+        retired = 0
+        still = []
+        for h, reqs, nbytes, slot in self.inflight:
+            if self.ex.ready(h):
+                self.ex.finish(h, reqs)
+                now = self.clock()
+                for r in reqs:
+                    r.done = now
+                    self.stats.latencies.append(r.latency)
+                self.mem_used -= nbytes
+                retired += len(reqs)
+            else:
+                still.append((h, reqs, nbytes, slot))
+        self.inflight = still
+        while True:
+            slot = self._free_slot()
+            if slot is None:
+                break
+            # oldest waiting request decides which database goes next
+            cands = [(q[0].arrival, db) for db, q in self.waiting.items() if q]
+            if not cands:
+                break
+            _, db = min(cands)
+            q = self.waiting[db]
+            nq = min(len(q), self.max_batch)
+            while nq > 0 and self.mem_used + self.ex.bytes_for(db, nq) > self.mem_budget:
+                nq //= 2
+            if nq == 0:
+                self.stats.deferred += 1
+                break
+            reqs = [q.popleft() for _ in range(nq)]
+            now = self.clock()
+            for r in reqs:
+                r.start = now
+            nbytes = self.ex.bytes_for(db, nq)
+            h = self.ex.launch(db, reqs, slot)
+            self.mem_used += nbytes
+            self.inflight.append((h, reqs, nbytes, slot))
+            self.stats.batches.append((db, nq, now))
+        return retired
+
+    def idle(self) -> bool:
+        return not self.inflight and not any(self.waiting.values())
+
+
+def run_open_loop(sched: Scheduler, arrivals: list[Request], poll_sleep: float = 0.0,
+                  clock: Callable[[], float] | None = None) -> Stats:
+    """Replay requests at their arrival times (relative to the start) and keep
+    polling until every one of them has been served."""
+    clock = clock or sched.clock
+    t0 = clock()
+    i = 0
+    pending = sorted(arrivals, key=lambda r: r.arrival)
+    for r in pending:
+        r.arrival += t0
+    while i < len(pending) or not sched.idle():
+        now = clock()
+        while i < len(pending) and pending[i].arrival <= now:
+            sched.submit(pending[i])
+            i += 1
+        sched.poll()
+        if poll_sleep:
+            time.sleep(poll_sleep)
+    return sched.stats
+
+
+class GpuExecutor:
+    """Executor over libsanns: one CUDA stream and one output buffer set per
+    slot; databases and their contexts stay resident."""
+
+    def __init__(self, dbs: dict, slots: int, max_batch: int, batched_min: int = 8,
+                 mask_seed: int = 5):
+        import torch
+
+        from . import sanns as S
+        self.S, self.torch = S, torch
+        self.dbs = dbs                      # name -> (ctx, db)
+        self.batched_min = batched_min
+        self.mask_seed = mask_seed
+        self.streams = [torch.cuda.Stream() for _ in range(slots)]
+        self.max_batch = max_batch
+
+    def bytes_for(self, db: str, n_queries: int) -> int:
+        ctx, d = self.dbs[db]
+        per_q = d.K * 2 * ctx.L * ctx.N * 8 + d.n * 4 + ctx.d * 2 * ctx.L * ctx.N * 8
+        return n_queries * per_q
+
+    def launch(self, db: str, reqs: list[Request], slot: int):
+        torch, S = self.torch, self.S
+        ctx, d = self.dbs[db]
+        st = self.streams[slot]
+        with torch.cuda.stream(st):
+            ct = torch.cat([r.payload[0] for r in reqs]) if len(reqs) > 1 else reqs[0].payload[0]
+            qids = torch.cat([r.payload[1] for r in reqs]) if len(reqs) > 1 else reqs[0].payload[1]
+            if len(reqs) >= self.batched_min and getattr(d, "batched", False):
+                out, srv = S.sanns_distances_batched(ctx, d, ct, self.mask_seed, qids, stream=st)
+            else:
+                out, srv = S.sanns_distances(ctx, d, ct, self.mask_seed, qids, stream=st)
+            ev = torch.cuda.Event()
+            ev.record(st)
+        return (ev, out, srv)
+
+    def ready(self, handle) -> bool:
+        return handle[0].query()
+
+    def finish(self, handle, reqs):
+        _, out, srv = handle
+        for i, r in enumerate(reqs):
+            r.result = (out[i:i + 1], srv[i:i + 1])

@@ -183,3 +183,27 @@ def test_bad_permutation_rejected():
     with pytest.raises(S.SannsError) as e:
         S.sanns_encode_db(ctx, coords, perm)
     assert e.value.code == -1
+
+
+@pytest.mark.parametrize("cfg,n", [((8192, 3, 60, 0, 7), 8192 * 4 + 3), ((4096, 2, 54, 0, 128), 4096 * 5),
+                                   ((256, 2, 40, 0, 200), 1000)])
+def test_every_mac_variant_matches_oracle(cfg, n):
+    ctx = S.sanns_ctx_create(*cfg)
+    O = oracle(*cfg)
+    d = cfg[4]
+    coords = inputs.uniform_coords(n, d, 5)
+    sk = S.sanns_keygen(ctx, 1)
+    q = inputs.uniform_coords(1, d, 6)
+    qids = cu(np.array([3], dtype=np.uint64))
+    db = S.sanns_encode_db(ctx, cu(coords))
+    ct_in = S.sanns_encrypt_query(ctx, sk, cu(q), 2, qids)
+    pt, _ = O.encode_db(coords, None)
+    want = O.mac(np_(ct_in)[0], pt)
+    names = S.sanns_mac_variants()
+    assert len(names) >= 2
+    for v in range(len(names)):
+        S.sanns_set_mac_variant(ctx, v)
+        acc = S.sanns_distances_mac(ctx, db, ct_in)
+        assert np.array_equal(np_(acc)[0], want), names[v]
+    best, ms = S.sanns_autotune_mac(ctx, db, ct_in, acc, reps=1)
+    assert 0 <= best < len(names) and all(m > 0 for m in ms)

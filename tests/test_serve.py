@@ -1,0 +1,101 @@
+"""Host logic of the continuous-batching scheduler, driven by a fake executor
+and a fake clock (no GPU)."""
+import numpy as np
+
+from paper_1904_02033_b300.serve import Request, Scheduler, run_open_loop
+
+
+class FakeClock:
+    def __init__(self):
+        self.t = 0.0
+
+    def __call__(self):
+        self.t += 1e-5   # time advances with every look at the clock
+        return self.t
+
+
+class FakeExecutor:
+    def __init__(self, clock, service=lambda n: 1e-3 + 1e-5 * n, per_query_bytes=100):
+        self.clock = clock
+        self.service = service
+        self.per_query_bytes = per_query_bytes
+        self.launched = []
+        self.active_bytes = 0
+        self.max_active_bytes = 0
+
+    def bytes_for(self, db, n):
+        return n * self.per_query_bytes
+
+    def launch(self, db, reqs, slot):
+        end = self.clock.t + self.service(len(reqs))
+        self.launched.append((db, [r.rid for r in reqs], slot))
+        self.active_bytes += self.bytes_for(db, len(reqs))
+        self.max_active_bytes = max(self.max_active_bytes, self.active_bytes)
+        return (end, len(reqs), db)
+
+    def ready(self, h):
+        return self.clock.t >= h[0]
+
+    def finish(self, h, reqs):
+        self.active_bytes -= self.bytes_for(h[2], h[1])
+        for r in reqs:
+            r.result = ("done", r.rid)
+
+
+def _arrivals(n, rate, seed, dbs=("A", "B")):
+    rnd = np.random.default_rng(seed)
+    t = np.cumsum(rnd.exponential(1.0 / rate, size=n))
+    return [Request(rid=i, db=dbs[int(rnd.integers(0, len(dbs)))], arrival=float(t[i]))
+            for i in range(n)]
+
+
+def test_every_request_served_once_with_batches_bounded():
+    clk = FakeClock()
+    ex = FakeExecutor(clk)
+    s = Scheduler(ex, max_batch=16, slots=3, clock=clk)
+    reqs = _arrivals(500, 20000.0, 1)
+    stats = run_open_loop(s, reqs)
+    served = sorted(rid for _, ids, _ in ex.launched for rid in ids)
+    assert served == list(range(500))
+    assert all(len(ids) <= 16 for _, ids, _ in ex.launched)
+    assert all(r.result == ("done", r.rid) for r in reqs)
+    assert len(stats.latencies) == 500 and min(stats.latencies) > 0
+    # a batch only ever holds requests of one database, in arrival order
+    by_rid = {r.rid: r for r in reqs}
+    for db, ids, _ in ex.launched:
+        assert all(by_rid[i].db == db for i in ids)
+        arr = [by_rid[i].arrival for i in ids]
+        assert arr == sorted(arr)
+
+
+def test_requests_arriving_during_a_batch_join_the_next_one():
+    clk = FakeClock()
+    ex = FakeExecutor(clk, service=lambda n: 5e-3)
+    s = Scheduler(ex, max_batch=128, slots=1, clock=clk)
+    # one request, then 10 more while the first batch runs
+    reqs = [Request(rid=0, db="A", arrival=0.0)] + \
+           [Request(rid=i, db="A", arrival=1e-3 + i * 1e-5) for i in range(1, 11)]
+    run_open_loop(s, reqs)
+    assert [ids for _, ids, _ in ex.launched] == [[0], list(range(1, 11))]
+
+
+def test_memory_admission_defers_instead_of_dropping():
+    clk = FakeClock()
+    ex = FakeExecutor(clk, per_query_bytes=100)
+    s = Scheduler(ex, max_batch=64, slots=4, mem_budget=1000, clock=clk)
+    reqs = _arrivals(300, 1e6, 2, dbs=("A",))
+    run_open_loop(s, reqs)
+    assert ex.max_active_bytes <= 1000
+    assert all(len(ids) <= 10 for _, ids, _ in ex.launched)
+    assert sorted(r for _, ids, _ in ex.launched for r in ids) == list(range(300))
+
+
+def test_oldest_request_picks_the_database():
+    clk = FakeClock()
+    ex = FakeExecutor(clk)
+    s = Scheduler(ex, max_batch=8, slots=1, clock=clk)
+    s.submit(Request(rid=0, db="B", arrival=1.0))
+    s.submit(Request(rid=1, db="A", arrival=2.0))
+    s.submit(Request(rid=2, db="B", arrival=3.0))
+    s.poll()
+    assert ex.launched[0][0] == "B" and ex.launched[0][1] == [0, 2]
