@@ -254,6 +254,11 @@ def run_gpu(args) -> None:
     cpu = None
     if rank == 0:
         cpu = cpu_baseline(quick=args.quick_cpu)
+    batched = None
+    if rank == 0 and not args.no_batched:
+        del ct_all
+        torch.cuda.empty_cache()
+        batched = run_batched_section(quick=args.quick_batched)
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -283,11 +288,103 @@ def run_gpu(args) -> None:
             "gpu_launches": 2 * args.steps,
             "clocks": ck,
             "cpu_baseline": cpu,
+            "batched": batched,
         }
         print(json.dumps(line), flush=True)
     if dist:
         dist.barrier()
         dist.destroy_process_group()
+
+
+BATCHED = dict(n=10_000_000, d=96, N=8192, L=3, prime_bits=60, t_rule=0, n_comp=256, sigma=12.0,
+               B=64, seed=7)
+
+
+def run_batched_section(quick: bool = False, n_override: int | None = None) -> dict:
+    """The batched configuration: n = 10^7, d = 96 (Deep1B-10M-shaped), 64
+    queries per launch on the tensor-core path, against the same queries run
+    one at a time on the per-query path; outputs compared in full."""
+    import torch
+
+    from paper_1904_02033_b300 import inputs
+    from paper_1904_02033_b300 import sanns as S
+
+    W = dict(BATCHED)
+    if quick:
+        W["n"] = 1_000_000
+    if n_override:
+        W["n"] = n_override
+    n, d, N, L, B = W["n"], W["d"], W["N"], W["L"], W["B"]
+    ctx = S.sanns_ctx_create(N, L, W["prime_bits"], W["t_rule"], d)
+    coords = inputs.mixture_coords_device(n, d, W["n_comp"], W["sigma"], W["seed"])
+    perm = inputs.permutation_device(n, W["seed"] + 1)
+    db = S.sanns_encode_db(ctx, coords, perm)
+    del coords
+    S.sanns_db_prepare_batched(ctx, db)
+    q = inputs.mixture_coords_device(B, d, W["n_comp"], W["sigma"], W["seed"] + 2,
+                                     means_seed=W["seed"])
+    qids = torch.arange(B, dtype=torch.int64).to(torch.uint64).cuda()
+    sk = S.sanns_keygen(ctx, W["seed"] + 3)
+    ct = S.sanns_encrypt_query(ctx, sk, q, W["seed"] + 4, qids)
+    K = db.K
+    st = torch.cuda.current_stream()
+    out_b = torch.empty((B, K, 2, L, N), dtype=torch.uint64, device="cuda")
+    srv_b = torch.empty((B, n), dtype=torch.uint32, device="cuda")
+    out_p = torch.empty((1, K, 2, L, N), dtype=torch.uint64, device="cuda")
+    srv_p = torch.empty((1, n), dtype=torch.uint32, device="cuda")
+    S.sanns_autotune_mac(ctx, db, ct[0:1], out_p, reps=2)
+
+    def timed(fn, reps):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        for _ in range(reps):
+            fn()
+        e1.record(st)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    # per-query path, the B queries one at a time
+    def plain():
+        for b in range(B):
+            S.sanns_distances(ctx, db, ct[b:b + 1], 9, qids[b:b + 1], out_p, srv_p)
+    t_plain = timed(plain, 1)
+    # batched path, MAC stage alone then the whole step
+    t_bmac = timed(lambda: S.sanns_distances_batched_mac(ctx, db, ct, out_b), 2)
+    t_batch = timed(lambda: S.sanns_distances_batched(ctx, db, ct, 9, qids, out_b, srv_b), 2)
+    S.sanns_device_status(ctx)
+    # parity of the whole batch against the per-query path
+    same = True
+    for b in range(B):
+        S.sanns_distances(ctx, db, ct[b:b + 1], 9, qids[b:b + 1], out_p, srv_p)
+        same &= bool(torch.equal(out_p[0], out_b[b])) and bool(torch.equal(srv_p[0], srv_b[b]))
+    dpad = (d + 7) // 8 * 8
+    flops = 2.0 * (2 * B * 8) * K * (8 * dpad) * L * N
+    peak = _peaks_tensor()
+    return {
+        "workload": f"batched: n={n:,} d={d} uint8 256-component Gaussian mixture (sigma 12); "
+                    f"{B} queries per launch; BFV N=8192, three 60-bit primes",
+        "qp_per_s_batched": B * n / (t_batch * 1e-3),
+        "qp_per_s_plain_per_query": B * n / (t_plain * 1e-3),
+        "speedup_vs_plain": t_plain / t_batch,
+        "ms_per_batch": t_batch, "ms_batched_mac": t_bmac, "ms_plain_for_B_queries": t_plain,
+        "bit_identical_to_per_query_path": same,
+        "roofline": {"kernel": "batched_mac_kernel (tcgen05 kind::f16, bf16 digits)",
+                     "bound": "tensor", "achieved": flops / (t_bmac * 1e-3) / 1e12,
+                     "peak": peak[0], "unit": "TFLOP/s",
+                     "frac": flops / (t_bmac * 1e-3) / 1e12 / peak[0], "peak_source": peak[1],
+                     "algorithmic_flops": flops},
+    }
+
+
+def _peaks_tensor():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["bf16_tflops"]), "measured bf16 dense (burst)"
+    except Exception:
+        return 1800.0, "fallback"
 
 
 def _oracle_sample(n_blocks: int, n_queries: int):
@@ -369,6 +466,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="sanns", choices=["sanns", "reference"])
     ap.add_argument("--quick-cpu", action="store_true", help="smaller CPU baseline sample")
+    ap.add_argument("--no-batched", action="store_true", help="skip the batched section")
+    ap.add_argument("--quick-batched", action="store_true", help="batched section at n = 10^6")
+    ap.add_argument("--only-batched", type=int, default=None, metavar="N_POINTS",
+                    help="run only the batched section on N_POINTS points (profiling)")
     ap.add_argument("--n", type=int, default=None,
                     help="smaller database (profiling captures); the line then names it")
     ap.add_argument("--queries", type=int, default=None, help="number of distinct queries")
@@ -379,7 +480,11 @@ def main():
         WORKLOAD["n_queries"] = args.queries
     if args.warmup < 3:
         args.warmup = 3
-    if args.impl == "reference":
+    if args.only_batched:
+        import torch
+        torch.cuda.set_device(0)
+        print(json.dumps({"batched": run_batched_section(n_override=args.only_batched)}), flush=True)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_gpu(args)

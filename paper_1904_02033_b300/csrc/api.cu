@@ -84,18 +84,23 @@ int sanns_ctx_create(const sanns_params* p, sanns_ctx** out) {
   c->mac_variant = 1;
 
   const size_t per = (size_t)p->L * N;
-  std::vector<uint64_t> host(4 * per);
+  std::vector<uint64_t> fw(per), fws(per), iw(per), iws(per);
   for (uint32_t j = 0; j < p->L; ++j)
-    fill_twiddles(N, q[j], psi[j], &host[0 * per + j * N], &host[1 * per + j * N],
-                  &host[2 * per + j * N], &host[3 * per + j * N]);
+    fill_twiddles(N, q[j], psi[j], &fw[j * N], &fws[j * N], &iw[j * N], &iws[j * N]);
+  // interleave {w, w_shoup}: forward table then inverse table, [L][N] pairs each
+  std::vector<uint64_t> host(4 * per);
+  for (size_t x = 0; x < per; ++x) {
+    host[2 * x] = fw[x];
+    host[2 * x + 1] = fws[x];
+    host[2 * per + 2 * x] = iw[x];
+    host[2 * per + 2 * x + 1] = iws[x];
+  }
   e = cudaMalloc(&c->d_tables, sizeof(uint64_t) * 4 * per);
   if (e != cudaSuccess) { delete c; return cuda_fail(e, "cudaMalloc(tables)"); }
   e = cudaMemcpy(c->d_tables, host.data(), sizeof(uint64_t) * 4 * per, cudaMemcpyHostToDevice);
   if (e != cudaSuccess) { cudaFree(c->d_tables); delete c; return cuda_fail(e, "cudaMemcpy(tables)"); }
-  c->P.tw = c->d_tables;
-  c->P.tw_shoup = c->d_tables + per;
-  c->P.itw = c->d_tables + 2 * per;
-  c->P.itw_shoup = c->d_tables + 3 * per;
+  c->P.tw = reinterpret_cast<const ulonglong2*>(c->d_tables);
+  c->P.itw = reinterpret_cast<const ulonglong2*>(c->d_tables + 2 * per);
   e = cudaMalloc(&c->d_err, sizeof(int));
   if (e == cudaSuccess) e = cudaMemset(c->d_err, 0, sizeof(int));
   if (e != cudaSuccess) { cudaFree(c->d_tables); delete c; return cuda_fail(e, "cudaMalloc(err)"); }

@@ -17,12 +17,13 @@
 //   warp 0      TMA producer: database digit tile (256 rows x 64 bf16) per stage
 //   warp 1      TMEM owner and MMA issuer (one thread): 4 MMAs of
 //               M = 128, N = 256, K = 16 per stage
-//   warps 2-3   query-digit producers: 128 rows x 64 bf16 per stage, written
+//   warps 2-5   query-digit producers: 128 rows x 64 bf16 per stage, written
 //               into shared memory in the 128-byte swizzled layout
-//   warps 4-11  epilogue: TMEM -> registers, S_a -> residues, weighted sum of
-//               the 8 digit rows across lanes, store acc[b][k][c][j][s]
-// Work unit = (prime, 16-row M tile, 256-column N tile, slot), slot fastest,
-// so CTAs running side by side write neighbouring slots of the same outputs.
+//   warps 6-13  epilogue: TMEM -> registers -> int32, transposed through
+//               shared memory so each lane combines the 8 digit rows of one
+//               output exactly, store acc[b][k][c][j][s]
+// Work unit = (prime, slot, 256-column N tile, 16-row M tile), M tile fastest,
+// so the CTAs running side by side share each database tile through L2.
 // Every wait is bounded: on time-out the kernel raises a device error flag,
 // drains its own copies, frees TMEM and returns.
 #include <cuda.h>
@@ -44,10 +45,15 @@ constexpr int kBK = 64;                  // contraction columns (8 dims x 8 digi
 constexpr int kATile = kBM * kBK * 2;    // 16 KB
 constexpr int kBTile = kBN * kBK * 2;    // 32 KB
 constexpr int kStageBytes = kATile + kBTile;
-constexpr int kThreads = 384;
-constexpr int kEpiWarp0 = 4;
+constexpr int kProdWarp0 = 2;
+constexpr int kProdWarps = 4;
+constexpr int kProdThreads = 32 * kProdWarps;
+static_assert(kProdThreads == 16 * 8, "one (row group, dimension) item per producer thread");
+constexpr int kEpiWarp0 = kProdWarp0 + kProdWarps;   // 6
 constexpr int kEpiWarps = 8;
-constexpr int kProdThreads = 64;
+constexpr int kThreads = 32 * (kEpiWarp0 + kEpiWarps);  // 448
+constexpr int kEpiCols = 16;                             // TMEM columns per load
+constexpr int kTrStride = kEpiCols + 1;                  // padded transpose row (words)
 constexpr unsigned long long kWaitCycles = 4ull << 30;  // ~2 s at 2 GHz
 
 struct BatchArgs {
@@ -60,7 +66,17 @@ struct BatchArgs {
   uint64_t w256[kMaxPrimes][8];        // 256^a mod q_j
   uint64_t w256_shoup[kMaxPrimes][8];
   uint64_t r256_shoup[kMaxPrimes];     // Shoup companion of 256
+  uint64_t w32[kMaxPrimes];            // 2^32 mod q_j
+  uint64_t w32_shoup[kMaxPrimes];
+  uint64_t mu64[kMaxPrimes];           // floor(2^64 / q_j)
 };
+
+// |v| mod q for |v| < 2^63 with mu = floor(2^64 / q), returned as v mod q.
+__device__ __forceinline__ uint64_t signed_mod(int64_t v, uint64_t q, uint64_t mu) {
+  const uint64_t m = v >= 0 ? (uint64_t)v : (uint64_t)(-v);
+  const uint64_t r = mod_t64(m, q, mu);
+  return (v >= 0 || r == 0) ? r : q - r;
+}
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -93,10 +109,11 @@ __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
 // Bounded wait; false when the CTA is aborting or the wait timed out (which
 // also raises the abort flag and the device error word).
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag,
-                                          int* err) {
+                                          int* err, uint32_t sleep_ns = 0) {
   const unsigned long long t0 = clock64();
   for (uint32_t it = 0;; ++it) {
     if (mbar_try(bar, parity)) return true;
+    if (sleep_ns && it > 2) __nanosleep(sleep_ns);
     if ((it & 255) == 255) {
       if (*abort_flag) return false;
       if (clock64() - t0 > kWaitCycles) {
@@ -148,37 +165,20 @@ __device__ __forceinline__ void tc_fence_after() {
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 }
 
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
-      "%12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, "
-      "%30, %31}, [%32];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
-        "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
-        "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-}
-
-// bf16 bit pattern of a small integer (|v| <= 256 is exact in bf16).
-__device__ __forceinline__ uint32_t bf16_of(int v) {
-  return __float_as_uint((float)v) >> 16;
-}
-
 struct Decoded {
   uint32_t j, mt, nt, s;
 };
 
+// unit = ((j N + s) NT + nt) MT + mt: the M tiles of one database tile are
+// consecutive, so CTAs running side by side share it through L2.
 __device__ __forceinline__ Decoded decode_unit(uint64_t u, uint32_t N, const BatchArgs& A) {
   Decoded D;
-  D.s = (uint32_t)(u % N);
-  uint64_t r = u / N;
+  D.mt = (uint32_t)(u % A.MT);
+  uint64_t r = u / A.MT;
   D.nt = (uint32_t)(r % A.NT);
   r /= A.NT;
-  D.mt = (uint32_t)(r % A.MT);
-  D.j = (uint32_t)(r / A.MT);
+  D.s = (uint32_t)(r % N);
+  D.j = (uint32_t)(r / N);
   return D;
 }
 
@@ -189,6 +189,7 @@ batched_mac_kernel(const __grid_constant__ CUtensorMap pmap, PrimeSet P, BatchAr
   __shared__ __align__(8) uint64_t bar_tfull[2], bar_tempty[2];
   __shared__ uint32_t tmem_base_slot;
   __shared__ volatile int abort_flag;
+  __shared__ int32_t tr[kEpiWarps][32 * kTrStride];
 
   const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   uint8_t* base = dsmem + ((1024 - (smem_u32(dsmem) & 1023)) & 1023);
@@ -270,90 +271,120 @@ batched_mac_kernel(const __grid_constant__ CUtensorMap pmap, PrimeSet P, BatchAr
     }
   } else if (warp < kEpiWarp0) {
     // ---------------- query-digit producers ----------------
-    const uint32_t pt = threadIdx.x - 64;  // 0..63
+    // Balanced base-256 digits of X in [-128, 127]: the bytes of
+    // X + 0x8080808080808080 are exactly the digits plus 128 (X < 2^60, so the
+    // sum is an ordinary base-256 number without overflow).
+    const uint32_t pt = threadIdx.x - 32 * kProdWarp0;   // one (b, c, dim) item per thread
+    const uint32_t bcl = pt >> 3, il = pt & 7;             // local (b, c) row group, dim in chunk
+    // the ciphertext value this thread encodes in chunk kc of unit u
+    auto fetch = [&](uint64_t u, uint32_t kc) -> uint64_t {
+      const Decoded D = decode_unit(u, N, A);
+      const uint32_t bc = D.mt * 16 + bcl, i = kc * 8 + il;
+      if (bc >= 2 * A.B || i >= A.d) return 0;
+      const uint32_t b = bc >> 1, c = bc & 1;
+      return __ldg(A.ct + ((((uint64_t)b * A.d + i) * 2 + c) * L + D.j) * N + D.s);
+    };
     uint64_t g = 0;
+    uint64_t X_next = blockIdx.x < A.units ? fetch(blockIdx.x, 0) : 0;
     for (uint64_t u = blockIdx.x; u < A.units && !abort_flag; u += gridDim.x) {
       const Decoded D = decode_unit(u, N, A);
       const uint64_t q = P.q[D.j];
       const uint64_t r256s = A.r256_shoup[D.j];
       bool ok = true;
       for (uint32_t kc = 0; kc < A.chunks; ++kc, ++g) {
+        uint64_t X = X_next;
+        if (kc + 1 < A.chunks) X_next = fetch(u, kc + 1);
+        else if (u + gridDim.x < A.units) X_next = fetch(u + gridDim.x, 0);
         const uint32_t st = (uint32_t)(g % kStages), ph = (uint32_t)((g / kStages) & 1);
-        if (!mbar_wait(smem_u32(&bar_empty[st]), ph ^ 1, &abort_flag, A.err)) { ok = false; break; }
+        if (!mbar_wait(smem_u32(&bar_empty[st]), ph ^ 1, &abort_flag, A.err, 32)) { ok = false; break; }
         uint8_t* at = base + st * kStageBytes;
-        for (uint32_t e = pt; e < 16 * 8; e += kProdThreads) {
-          const uint32_t bcl = e >> 3, il = e & 7;  // local (b, c) row group, dim in chunk
-          const uint32_t bc = D.mt * 16 + bcl, i = kc * 8 + il;
-          uint64_t X = 0;
-          if (bc < 2 * A.B && i < A.d) {
-            const uint32_t b = bc >> 1, c = bc & 1;
-            X = A.ct[((((uint64_t)b * A.d + i) * 2 + c) * L + D.j) * N + D.s];
-          }
-          // digits[b8][a] of X_b8 = X 256^b8 mod q, packed per a as 8 bf16
-          uint32_t packed[8][4];
+        uint32_t ylo[8], yhi[8];  // X 256^b8 mod q + 0x80..80, b8 = 0..7
 #pragma unroll
-          for (int b8 = 0; b8 < 8; ++b8) {
-            uint64_t y = X;
+        for (int b8 = 0; b8 < 8; ++b8) {
+          const uint64_t y = X + 0x8080808080808080ull;
+          ylo[b8] = (uint32_t)y;
+          yhi[b8] = (uint32_t)(y >> 32);
+          if (b8 < 7) X = mul_shoup(X, 256, r256s, q);
+        }
 #pragma unroll
-            for (int a = 0; a < 8; ++a) {
-              int t = (int)(y & 255);
-              y >>= 8;
-              if (t >= 128) { t -= 256; y += 1; }
-              const uint32_t h = bf16_of(t);
-              if (b8 & 1) packed[a][b8 >> 1] |= h << 16;
-              else packed[a][b8 >> 1] = h;
-            }
-            X = mul_shoup(X, 256, r256s, q);
-          }
+        for (int a = 0; a < 8; ++a) {
+          const uint32_t sel = 0x7440u + (uint32_t)(a & 3);  // byte a, two zero bytes, 0x4B
+          uint32_t w[4];
 #pragma unroll
-          for (int a = 0; a < 8; ++a) {
-            const uint32_t row = bcl * 8 + a;
-            uint4* dst = reinterpret_cast<uint4*>(at + row * 128 + ((il ^ (row & 7)) << 4));
-            *dst = make_uint4(packed[a][0], packed[a][1], packed[a][2], packed[a][3]);
+          for (int m = 0; m < 4; ++m) {
+            const uint32_t w0 = a < 4 ? ylo[2 * m] : yhi[2 * m];
+            const uint32_t w1 = a < 4 ? ylo[2 * m + 1] : yhi[2 * m + 1];
+            const float f0 = __uint_as_float(__byte_perm(w0, 0x4B000000u, sel)) - 8388736.0f;
+            const float f1 = __uint_as_float(__byte_perm(w1, 0x4B000000u, sel)) - 8388736.0f;
+            w[m] = __byte_perm(__float_as_uint(f0), __float_as_uint(f1), 0x7632);
           }
+          const uint32_t row = bcl * 8 + a;
+          uint4* dst = reinterpret_cast<uint4*>(at + row * 128 + ((il ^ (row & 7)) << 4));
+          *dst = make_uint4(w[0], w[1], w[2], w[3]);
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        asm volatile("bar.sync 1, 64;" ::: "memory");
+        asm volatile("bar.sync 1, %0;" ::"n"(kProdThreads) : "memory");
         if (pt == 0) mbar_arrive(smem_u32(&bar_full[st]));
       }
       if (!ok) break;
     }
   } else {
     // ---------------- epilogue ----------------
+    // A warp reads 32 TMEM lanes (rows (b, c, a) of 4 row groups) x 16
+    // columns, converts the exact fp32 sums to int32, transposes them through
+    // shared memory so that each lane holds the 8 digit rows of one output,
+    // and combines them exactly: lo = sum_{a<4} S_a 256^a and hi = sum_{a>=4}
+    // S_a 256^(a-4) (both below 2^49 in magnitude), acc = lo + hi 2^32 mod q.
     const uint32_t ew = warp - kEpiWarp0;         // 0..7
     const uint32_t quarter = warp & 3;            // TMEM lanes 32 quarter ..
     const uint32_t half = ew >> 2;                // columns 128 half ..
-    const uint32_t row = quarter * 32 + lane;     // (b, c, a) row of the tile
-    const uint32_t a = row & 7, bcl = row >> 3;
+    int32_t* trw = tr[ew];
+    const uint32_t og = lane >> 3;                // output row group (0..3) of this lane
+    const uint32_t oc = lane & 7;                 // output column within 8
     uint64_t r = 0;
     for (uint64_t u = blockIdx.x; u < A.units && !abort_flag; u += gridDim.x, ++r) {
       const uint32_t slot = (uint32_t)(r & 1), aph = (uint32_t)((r >> 1) & 1);
-      if (!mbar_wait(smem_u32(&bar_tfull[slot]), aph, &abort_flag, A.err)) break;
+      if (!mbar_wait(smem_u32(&bar_tfull[slot]), aph, &abort_flag, A.err, 128)) break;
       tc_fence_after();
       const Decoded D = decode_unit(u, N, A);
       const uint64_t q = P.q[D.j];
-      const uint64_t wa = A.w256[D.j][a], was = A.w256_shoup[D.j][a];
-      const uint32_t bc = D.mt * 16 + bcl;
+      const uint64_t w32 = A.w32[D.j], w32s = A.w32_shoup[D.j];
+      const uint32_t bc = D.mt * 16 + quarter * 4 + og;   // (b, c) of this lane's outputs
       const bool row_ok = bc < 2 * A.B;
       const uint32_t b = bc >> 1, c = bc & 1;
-      for (uint32_t cc = 0; cc < 4; ++cc) {
-        const uint32_t col0 = half * 128 + cc * 32;
-        uint32_t v[32];
-        tmem_ld32(tmem + ((quarter * 32) << 16) + slot * kBN + col0, v);
+      uint64_t* orow = A.out + ((((uint64_t)b * A.K) * 2 + c) * L + D.j) * N + D.s;
+      const uint64_t kstride = 2ull * L * N;
+      for (uint32_t cc = 0; cc < 128 / kEpiCols; ++cc) {
+        const uint32_t col0 = half * 128 + cc * kEpiCols;
+        uint32_t v[kEpiCols];
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, "
+            "%10, %11, %12, %13, %14, %15}, [%16];"
+            : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]),
+              "=r"(v[6]), "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]),
+              "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+            : "r"(tmem + ((quarter * 32) << 16) + slot * kBN + col0));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-        for (int x = 0; x < 32; ++x) {
-          const int sa = __float2int_rn(__uint_as_float(v[x]));
-          uint64_t res = sa >= 0 ? (uint64_t)sa : q - (uint64_t)(-sa);
-          res = mul_shoup(res, wa, was, q);
+        for (int x = 0; x < kEpiCols; ++x)
+          trw[lane * kTrStride + x] = __float2int_rn(__uint_as_float(v[x]));
+        __syncwarp();
 #pragma unroll
-          for (int off = 1; off < 8; off <<= 1) {
-            const uint64_t o = __shfl_xor_sync(0xffffffffu, res, off);
-            res = add_mod(res, o, q);
-          }
-          const uint32_t k = D.nt * kBN + col0 + x;
-          if (a == 0 && row_ok && k < A.K)
-            A.out[((((uint64_t)b * A.K + k) * 2 + c) * L + D.j) * N + D.s] = res;
+        for (int h = 0; h < kEpiCols / 8; ++h) {
+          const uint32_t col = h * 8 + oc;
+          const int32_t* src = trw + (og * 8) * kTrStride + col;
+          const int64_t lo = (int64_t)src[0] + ((int64_t)src[kTrStride] << 8) +
+                             ((int64_t)src[2 * kTrStride] << 16) + ((int64_t)src[3 * kTrStride] << 24);
+          const int64_t hi = (int64_t)src[4 * kTrStride] + ((int64_t)src[5 * kTrStride] << 8) +
+                             ((int64_t)src[6 * kTrStride] << 16) + ((int64_t)src[7 * kTrStride] << 24);
+          const uint64_t mu = A.mu64[D.j];
+          const uint64_t rl = signed_mod(lo, q, mu);
+          const uint64_t rh = signed_mod(hi, q, mu);
+          const uint64_t res = add_mod(rl, mul_shoup(rh, w32, w32s, q), q);
+          const uint32_t k = D.nt * kBN + col0 + col;
+          if (row_ok && k < A.K) orow[(uint64_t)k * kstride] = res;
         }
+        __syncwarp();
       }
       tc_fence_before();
       __syncwarp();
@@ -469,7 +500,7 @@ cudaError_t launch_batched_mac(const PrimeSet& P, const void* map, const uint64_
   A.MT = (2 * B + 15) / 16;
   A.NT = (uint32_t)((K + kBN - 1) / kBN);
   A.chunks = A.dpad / 8;
-  A.units = (uint64_t)P.L * A.MT * A.NT * P.N;
+  A.units = (uint64_t)P.L * P.N * A.NT * A.MT;
   for (uint32_t j = 0; j < P.L; ++j) {
     uint64_t w = 1 % P.q[j];
     for (int a = 0; a < 8; ++a) {
@@ -478,6 +509,9 @@ cudaError_t launch_batched_mac(const PrimeSet& P, const void* map, const uint64_
       w = (uint64_t)(((u128)w * 256) % P.q[j]);
     }
     A.r256_shoup[j] = shoup_of(256 % P.q[j], P.q[j]);
+    A.w32[j] = (uint64_t)(((u128)1 << 32) % P.q[j]);
+    A.w32_shoup[j] = shoup_of(A.w32[j], P.q[j]);
+    A.mu64[j] = (uint64_t)(((u128)1 << 64) / P.q[j]);
   }
   const size_t smem = (size_t)kStages * kStageBytes + 1024;
   cudaError_t e = cudaFuncSetAttribute(batched_mac_kernel,

@@ -35,11 +35,9 @@ struct PrimeSet {
   uint64_t n_inv_shoup[kMaxPrimes];
   uint64_t crt_inv[kMaxPrimes];     // (Q / q_j)^-1 mod q_j
   uint64_t crt_inv_shoup[kMaxPrimes];
-  // twiddles, [L][N] each: psi^brv(m), psi^-brv(m) and their Shoup companions
-  const uint64_t* tw;
-  const uint64_t* tw_shoup;
-  const uint64_t* itw;
-  const uint64_t* itw_shoup;
+  // twiddles, [L][N] pairs {w, Shoup companion}: psi^brv(m) and psi^-brv(m)
+  const ulonglong2* tw;
+  const ulonglong2* itw;
 };
 
 // ------------------------------------------------------------------------
@@ -184,45 +182,51 @@ __device__ __forceinline__ void inv_bfly(uint64_t& X, uint64_t& Y, uint64_t w, u
 }
 
 __device__ __forceinline__ void ntt_forward_smem(uint64_t* a, const PrimeSet& P, int j) {
-  const uint32_t N = P.N, logN = P.logN, half = N >> 1;
+  const uint32_t N = P.N, logN = P.logN;
   const uint64_t q = P.q[j], q2 = 2 * q;
-  const uint64_t* tw = P.tw + (size_t)j * N;
-  const uint64_t* tws = P.tw_shoup + (size_t)j * N;
+  const ulonglong2* tw = P.tw + (size_t)j * N;
   const uint32_t r2 = logN & 3;  // leading radix-2 stages
-  uint32_t t = half;
-  for (uint32_t st = 0; st < r2; ++st, t >>= 1) {
-    const uint32_t m = N / (2 * t);
-    for (uint32_t bf = threadIdx.x; bf < half; bf += blockDim.x) {
-      const uint32_t i = bf / t, x = 2 * i * t + (bf & (t - 1));
+  uint32_t lt = logN - 1;         // log2 of the butterfly distance t
+  for (uint32_t st = 0; st < r2; ++st, --lt) {
+    const uint32_t t = 1u << lt, m = 1u << st;
+    for (uint32_t bf = threadIdx.x; bf < N / 2; bf += blockDim.x) {
+      const uint32_t i = bf >> lt, x = (i << (lt + 1)) + (bf & (t - 1));
       uint64_t X = a[SP(x)], Y = a[SP(x + t)];
-      fwd_bfly(X, Y, __ldg(tw + m + i), __ldg(tws + m + i), q, q2);
+      const ulonglong2 w = __ldg(tw + m + i);
+      fwd_bfly(X, Y, w.x, w.y, q, q2);
       a[SP(x)] = X;
       a[SP(x + t)] = Y;
     }
     __syncthreads();
   }
-  for (; t >= 8; t >>= 4) {  // stages t, t/2, t/4, t/8
-    const uint32_t S = t >> 3;
+  // radix-16 passes: stages t, t/2, t/4, t/8 with t = 2^lt; a thread owns the
+  // 16 elements x0 + k S (S = t/8) of one group; in stage s the lower element
+  // k of a pair uses twiddle m_s + (g << s) + (k >> (4 - s)), m_s = N / (2 t_s)
+  for (; lt >= 3 && lt + 1 <= logN; lt -= 4) {
+    const uint32_t ls = lt - 3, S = 1u << ls;
+    const uint32_t m0 = 1u << (logN - 1 - lt);
     for (uint32_t th = threadIdx.x; th < N / 16; th += blockDim.x) {
-      const uint32_t g = th / S, b = th & (S - 1);
-      const uint32_t x0 = g * 2 * t + b;
+      const uint32_t g = th >> ls, b = th & (S - 1);
+      const uint32_t x0 = (g << (lt + 1)) + b;
       uint64_t v[16];
 #pragma unroll
-      for (int k = 0; k < 16; ++k) v[k] = a[SP(x0 + k * S)];
+      for (int k = 0; k < 16; ++k) v[k] = a[SP(x0 + (k << ls))];
 #pragma unroll
       for (int s = 0; s < 4; ++s) {
-        const uint32_t ts = t >> s, hk = 8 >> s, m = N / (2 * ts);
+        const int hk = 8 >> s;
+        const uint32_t base = (m0 << s) + (g << s);
 #pragma unroll
         for (int k = 0; k < 16; ++k) {
           if (k & hk) continue;
-          const uint32_t i = (x0 + k * S) / (2 * ts);
-          fwd_bfly(v[k], v[k + hk], __ldg(tw + m + i), __ldg(tws + m + i), q, q2);
+          const ulonglong2 w = __ldg(tw + base + (k >> (4 - s)));
+          fwd_bfly(v[k], v[k + hk], w.x, w.y, q, q2);
         }
       }
 #pragma unroll
-      for (int k = 0; k < 16; ++k) a[SP(x0 + k * S)] = csub(csub(v[k], q2), q);
+      for (int k = 0; k < 16; ++k) a[SP(x0 + (k << ls))] = csub(csub(v[k], q2), q);
     }
     __syncthreads();
+    if (lt < 4) break;
   }
   if (r2 == logN) {  // N < 16: no radix-16 pass canonicalised the values
     for (uint32_t x = threadIdx.x; x < N; x += blockDim.x) a[SP(x)] = csub(csub(a[SP(x)], q2), q);
@@ -230,29 +234,33 @@ __device__ __forceinline__ void ntt_forward_smem(uint64_t* a, const PrimeSet& P,
 }
 
 __device__ __forceinline__ void ntt_inverse_smem(uint64_t* a, const PrimeSet& P, int j) {
-  const uint32_t N = P.N, logN = P.logN, half = N >> 1;
+  const uint32_t N = P.N, logN = P.logN;
   const uint64_t q = P.q[j], q2 = 2 * q;
-  const uint64_t* tw = P.itw + (size_t)j * N;
-  const uint64_t* tws = P.itw_shoup + (size_t)j * N;
+  const ulonglong2* tw = P.itw + (size_t)j * N;
   const uint32_t passes = logN >> 2;
   const uint64_t ni = P.n_inv[j], nis = P.n_inv_shoup[j];
-  uint32_t t = 1;
-  for (uint32_t ps = 0; ps < passes; ++ps, t <<= 4) {  // stages t, 2t, 4t, 8t
-    const bool last = (ps + 1 == passes) && (t * 16 == N);
+  // radix-16 passes: stages t, 2t, 4t, 8t with t = 2^lt; a thread owns the 16
+  // elements x0 + k t of one group; in stage s the lower element k of a pair
+  // uses twiddle h_s + (g << (3 - s)) + (k >> (s + 1)), h_s = N / (2 t 2^s)
+  uint32_t lt = 0;
+  for (uint32_t ps = 0; ps < passes; ++ps, lt += 4) {
+    const uint32_t t = 1u << lt;
+    const bool last = (ps + 1 == passes) && (lt + 4 == logN);
     for (uint32_t th = threadIdx.x; th < N / 16; th += blockDim.x) {
-      const uint32_t g = th / t, b = th & (t - 1);
-      const uint32_t x0 = g * 16 * t + b;
+      const uint32_t g = th >> lt, b = th & (t - 1);
+      const uint32_t x0 = (g << (lt + 4)) + b;
       uint64_t v[16];
 #pragma unroll
-      for (int k = 0; k < 16; ++k) v[k] = a[SP(x0 + k * t)];
+      for (int k = 0; k < 16; ++k) v[k] = a[SP(x0 + (k << lt))];
 #pragma unroll
       for (int s = 0; s < 4; ++s) {
-        const uint32_t ts = t << s, hk = 1 << s, h = N / (2 * ts);
+        const int hk = 1 << s;
+        const uint32_t base = (1u << (logN - 1 - lt - s)) + (g << (3 - s));
 #pragma unroll
         for (int k = 0; k < 16; ++k) {
           if (k & hk) continue;
-          const uint32_t i = (x0 + k * t) / (2 * ts);
-          inv_bfly(v[k], v[k + hk], __ldg(tw + h + i), __ldg(tws + h + i), q, q2);
+          const ulonglong2 w = __ldg(tw + base + (k >> (s + 1)));
+          inv_bfly(v[k], v[k + hk], w.x, w.y, q, q2);
         }
       }
       if (last) {
@@ -260,17 +268,18 @@ __device__ __forceinline__ void ntt_inverse_smem(uint64_t* a, const PrimeSet& P,
         for (int k = 0; k < 16; ++k) v[k] = mul_shoup(v[k], ni, nis, q);
       }
 #pragma unroll
-      for (int k = 0; k < 16; ++k) a[SP(x0 + k * t)] = v[k];
+      for (int k = 0; k < 16; ++k) a[SP(x0 + (k << lt))] = v[k];
     }
     __syncthreads();
   }
-  if (t < N) {
-    for (; t < N; t <<= 1) {
-      const uint32_t h = N / (2 * t);
-      for (uint32_t bf = threadIdx.x; bf < half; bf += blockDim.x) {
-        const uint32_t i = bf / t, x = 2 * i * t + (bf & (t - 1));
+  if (lt < logN) {
+    for (; lt < logN; ++lt) {
+      const uint32_t t = 1u << lt, h = 1u << (logN - 1 - lt);
+      for (uint32_t bf = threadIdx.x; bf < N / 2; bf += blockDim.x) {
+        const uint32_t i = bf >> lt, x = (i << (lt + 1)) + (bf & (t - 1));
         uint64_t X = a[SP(x)], Y = a[SP(x + t)];
-        inv_bfly(X, Y, __ldg(tw + h + i), __ldg(tws + h + i), q, q2);
+        const ulonglong2 w = __ldg(tw + h + i);
+        inv_bfly(X, Y, w.x, w.y, q, q2);
         a[SP(x)] = X;
         a[SP(x + t)] = Y;
       }

@@ -98,7 +98,7 @@ __global__ void mask_share_kernel(PrimeSet P, uint32_t B, uint64_t n, uint64_t m
 // ct_out (in place): INTT; for c = 0 add Delta_j ((||p||^2 + r) mod t) per
 // coefficient.  r is recovered from the server share written by
 // mask_share_kernel; padding positions (pos >= n) draw it directly.
-__global__ void __launch_bounds__(256) intt_mask_kernel(PrimeSet P, uint64_t* __restrict__ ct_out,
+__global__ void __launch_bounds__(256, 3) intt_mask_kernel(PrimeSet P, uint64_t* __restrict__ ct_out,
                                  const uint32_t* __restrict__ norms, uint64_t K, uint64_t n,
                                  uint64_t mask_seed, const uint64_t* __restrict__ qids,
                                  const uint32_t* __restrict__ srv_share) {

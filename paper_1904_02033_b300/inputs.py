@@ -124,3 +124,30 @@ def poisson_arrivals(rate_per_s: float, duration_s: float, seed: int) -> np.ndar
             break
         out.append(t)
     return np.array(out, dtype=np.float64)
+
+
+def mixture_coords_device(n: int, d: int, n_comp: int, sigma: float, seed: int,
+                          means_seed: int | None = None, device: str = "cuda",
+                          chunk: int = 1 << 22):
+    """Large mixture draws on the GPU (seeded torch generator): the same
+    distribution as mixture_coords, for databases too big to draw on the host
+    in reasonable time.  Returns a uint8 tensor [n][d] on `device`."""
+    import torch
+
+    gm = torch.Generator(device="cpu").manual_seed(seed if means_seed is None else means_seed)
+    means = (torch.rand((n_comp, d), generator=gm, dtype=torch.float32) * 255.0).to(device)
+    g = torch.Generator(device=device).manual_seed(seed + 0x9E3779B9)
+    out = torch.empty((n, d), dtype=torch.uint8, device=device)
+    for s in range(0, n, chunk):
+        e = min(n, s + chunk)
+        comp = torch.randint(0, n_comp, (e - s,), generator=g, device=device)
+        x = means[comp] + torch.randn((e - s, d), generator=g, device=device) * sigma
+        out[s:e] = x.round_().clamp_(0, 255).to(torch.uint8)
+    return out
+
+
+def permutation_device(n: int, seed: int, device: str = "cuda"):
+    import torch
+
+    g = torch.Generator(device=device).manual_seed(seed)
+    return torch.randperm(n, generator=g, device=device, dtype=torch.int32).view(torch.uint32)
