@@ -300,7 +300,8 @@ BATCHED = dict(n=10_000_000, d=96, N=8192, L=3, prime_bits=60, t_rule=0, n_comp=
                B=64, seed=7)
 
 
-def run_batched_section(quick: bool = False, n_override: int | None = None) -> dict:
+def run_batched_section(quick: bool = False, n_override: int | None = None,
+                        d_override: int | None = None, b_override: int | None = None) -> dict:
     """The batched configuration: n = 10^7, d = 96 (Deep1B-10M-shaped), 64
     queries per launch on the tensor-core path, against the same queries run
     one at a time on the per-query path; outputs compared in full."""
@@ -314,6 +315,10 @@ def run_batched_section(quick: bool = False, n_override: int | None = None) -> d
         W["n"] = 1_000_000
     if n_override:
         W["n"] = n_override
+    if d_override:
+        W["d"] = d_override
+    if b_override:
+        W["B"] = b_override
     n, d, N, L, B = W["n"], W["d"], W["N"], W["L"], W["B"]
     ctx = S.sanns_ctx_create(N, L, W["prime_bits"], W["t_rule"], d)
     coords = inputs.mixture_coords_device(n, d, W["n_comp"], W["sigma"], W["seed"])
@@ -470,6 +475,8 @@ def main():
     ap.add_argument("--quick-batched", action="store_true", help="batched section at n = 10^6")
     ap.add_argument("--only-batched", type=int, default=None, metavar="N_POINTS",
                     help="run only the batched section on N_POINTS points (profiling)")
+    ap.add_argument("--batched-d", type=int, default=None, help="dimension for --only-batched")
+    ap.add_argument("--batched-B", type=int, default=None, help="queries per launch for --only-batched")
     ap.add_argument("--n", type=int, default=None,
                     help="smaller database (profiling captures); the line then names it")
     ap.add_argument("--queries", type=int, default=None, help="number of distinct queries")
@@ -483,7 +490,9 @@ def main():
     if args.only_batched:
         import torch
         torch.cuda.set_device(0)
-        print(json.dumps({"batched": run_batched_section(n_override=args.only_batched)}), flush=True)
+        print(json.dumps({"batched": run_batched_section(n_override=args.only_batched,
+                                                         d_override=args.batched_d,
+                                                         b_override=args.batched_B)}), flush=True)
     elif args.impl == "reference":
         run_reference(args)
     else:

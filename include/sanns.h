@@ -242,6 +242,13 @@ int sanns_distances_batched(sanns_ctx *ctx, const sanns_db *db, const uint64_t *
 int sanns_distances_batched_mac(sanns_ctx *ctx, const sanns_db *db, const uint64_t *ct_in_dev,
                                 uint32_t B, uint64_t *ct_out_dev, void *stream);
 int sanns_device_status(sanns_ctx *ctx, void *stream);
+/* Tuning of the batched kernel's waits: back-off sleep (ns) of the TMA
+ * thread, the MMA thread, the digit producers and the epilogue when their
+ * barrier is not ready yet, and whether every producer polls its stage
+ * (otherwise one polls and the others follow its result).  Results never
+ * depend on these values. */
+int sanns_batched_set_waits(sanns_ctx *ctx, uint32_t tma_ns, uint32_t mma_ns, uint32_t producer_ns,
+                            uint32_t epilogue_ns, int all_producers_poll);
 
 /*
  * Client decryption (Pi_ls step 4) plus its local term: per query b and

@@ -81,7 +81,22 @@ int sanns_ctx_create(const sanns_params* p, sanns_ctx** out) {
   cudaError_t e = cudaGetDevice(&c->device);
   if (e != cudaSuccess) { delete c; return cuda_fail(e, "cudaGetDevice"); }
   cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, c->device);
-  c->mac_variant = 1;
+  {
+    // stream-ordered scratch (decryption, gather, batched path) stays cached
+    // in the device's default pool instead of going back to the driver at
+    // every synchronisation
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, c->device) == cudaSuccess) {
+      uint64_t keep = ~0ull;
+      cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    }
+  }
+  c->mac_variant = 0;
+  c->batched_tune[0] = 0;
+  c->batched_tune[1] = 0;
+  c->batched_tune[2] = 32;
+  c->batched_tune[3] = 128;
+  c->batched_tune[4] = 0;
 
   const size_t per = (size_t)p->L * N;
   std::vector<uint64_t> fw(per), fws(per), iw(per), iws(per);
@@ -485,7 +500,7 @@ int sanns_distances_batched_mac(sanns_ctx* ctx, const sanns_db* db, const uint64
   if (!ct_in || !ct_out) return fail(SANNS_EINVAL, "NULL buffer");
   if (B > 4096) return fail(SANNS_EINVAL, "B must be <= 4096");
   SANNS_CUDA(launch_batched_mac(ctx->P, db->limb_map, ct_in, B, ctx->params.d, db->K, ct_out, ctx->d_err,
-                                ctx->sms, as_stream(stream)));
+                                ctx->sms, ctx->batched_tune, as_stream(stream)));
   return SANNS_OK;
 }
 
@@ -495,6 +510,19 @@ int sanns_distances_batched(sanns_ctx* ctx, const sanns_db* db, const uint64_t* 
   int rc = sanns_distances_batched_mac(ctx, db, ct_in, B, ct_out, stream);
   if (rc) return rc;
   return sanns_distances_finish(ctx, db, B, mask_seed, qids, ct_out, srv_share, stream);
+}
+
+int sanns_batched_set_waits(sanns_ctx* ctx, uint32_t tma_ns, uint32_t mma_ns, uint32_t producer_ns,
+                            uint32_t epilogue_ns, int all_producers_poll) {
+  if (!ctx) return fail(SANNS_EINVAL, "ctx is NULL");
+  if (tma_ns > 100000 || mma_ns > 100000 || producer_ns > 100000 || epilogue_ns > 100000)
+    return fail(SANNS_EINVAL, "back-off above 100 us");
+  ctx->batched_tune[0] = tma_ns;
+  ctx->batched_tune[1] = mma_ns;
+  ctx->batched_tune[2] = producer_ns;
+  ctx->batched_tune[3] = epilogue_ns;
+  ctx->batched_tune[4] = all_producers_poll ? 1 : 0;
+  return SANNS_OK;
 }
 
 int sanns_device_status(sanns_ctx* ctx, void* stream) {

@@ -1,10 +1,10 @@
-// K5: the batched ct x pt MAC on the tensor cores (tcgen05, kind::f16, bf16
+// K5: the batched ct x pt MAC on the tensor cores (tcgen05, kind::f16, fp16
 // operands, fp32 accumulation in TMEM), exact.
 //
 // With B queries, every (prime j, slot s) is the contraction
 //     C[(b, c)][k] = sum_i A[(b, c)][i] P[k][i]  mod q_j,
 // A = the query ciphertexts (NTT form), P = the encoded database.  Residues
-// are split into balanced base-256 digits in [-128, 127], which bf16 holds
+// are split into balanced base-256 digits in [-128, 127], which fp16 holds
 // exactly.  The database side is split once, P[k][i] = sum_b p_b 256^b; the
 // query side is folded with the digit weight of the database side,
 // X_b = A 256^b mod q = sum_a x_{b,a} 256^a, so that
@@ -13,20 +13,27 @@
 // every product is at most 2^14 in magnitude and a sum of 8 d <= 1024 of them
 // stays within 2^24, so the fp32 accumulation is exact for d <= 128.
 //
+// The GEMM is laid out with the database on the M side: rows are blocks k
+// (128 per tile, read by TMA from the resident digit layout), columns are
+// (b, c, a) for 16 queries (256 per tile, generated in shared memory), so one
+// TMEM lane holds the 8 digit sums S_0..S_7 of an output in 8 consecutive
+// columns and the epilogue needs no data exchange between lanes.
+//
 // One persistent CTA per SM, warp-specialised:
-//   warp 0      TMA producer: database digit tile (256 rows x 64 bf16) per stage
+//   warp 0      TMA producer: database digit tile (128 rows x 64 fp16) per stage
 //   warp 1      TMEM owner and MMA issuer (one thread): 4 MMAs of
 //               M = 128, N = 256, K = 16 per stage
-//   warps 2-5   query-digit producers: 128 rows x 64 bf16 per stage, written
+//   warps 2-9   query-digit producers: 256 rows x 64 fp16 per stage, written
 //               into shared memory in the 128-byte swizzled layout
-//   warps 6-13  epilogue: TMEM -> registers -> int32, transposed through
-//               shared memory so each lane combines the 8 digit rows of one
-//               output exactly, store acc[b][k][c][j][s]
-// Work unit = (prime, slot, 256-column N tile, 16-row M tile), M tile fastest,
-// so the CTAs running side by side share each database tile through L2.
+//   warps 10-13 epilogue: TMEM -> registers, exact int64 combination of each
+//               output's 8 digit sums, one mod-q step, store acc[b][k][c][j][s]
+// Work unit = (prime, slot, 128-block K tile, 16-query Q tile), Q tile
+// fastest, so the CTAs running side by side share each database tile
+// through L2.
 // Every wait is bounded: on time-out the kernel raises a device error flag,
 // drains its own copies, frees TMEM and returns.
 #include <cuda.h>
+#include <cuda_fp16.h>
 #include <cudaTypedefs.h>
 
 #include <cstring>
@@ -39,29 +46,29 @@ namespace sanns {
 namespace {
 
 constexpr int kStages = 4;
-constexpr int kBM = 128;                 // rows (b, c, a) per tile: 16 (b, c) x 8 digits
-constexpr int kBN = 256;                 // database blocks per tile
+constexpr int kBM = 128;                 // database blocks per tile (A operand, TMA)
+constexpr int kBN = 256;                 // query rows (b, c, a) per tile: 32 (b, c) x 8 digits
 constexpr int kBK = 64;                  // contraction columns (8 dims x 8 digits) per stage
+constexpr int kQG = kBN / 8;             // (b, c) row groups per tile
 constexpr int kATile = kBM * kBK * 2;    // 16 KB
 constexpr int kBTile = kBN * kBK * 2;    // 32 KB
 constexpr int kStageBytes = kATile + kBTile;
 constexpr int kProdWarp0 = 2;
-constexpr int kProdWarps = 4;
+constexpr int kProdWarps = 8;
 constexpr int kProdThreads = 32 * kProdWarps;
-static_assert(kProdThreads == 16 * 8, "one (row group, dimension) item per producer thread");
-constexpr int kEpiWarp0 = kProdWarp0 + kProdWarps;   // 6
-constexpr int kEpiWarps = 8;
-constexpr int kThreads = 32 * (kEpiWarp0 + kEpiWarps);  // 448
-constexpr int kEpiCols = 16;                             // TMEM columns per load
-constexpr int kTrStride = kEpiCols + 1;                  // padded transpose row (words)
+static_assert(kProdThreads == kQG * 8, "one (row group, dimension) item per producer thread");
+constexpr int kEpiWarp0 = kProdWarp0 + kProdWarps;   // 10
+constexpr int kEpiWarps = 8;                          // two per TMEM lane quarter
+constexpr int kThreads = 32 * (kEpiWarp0 + kEpiWarps);  // 576
 constexpr unsigned long long kWaitCycles = 4ull << 30;  // ~2 s at 2 GHz
 
 struct BatchArgs {
-  const uint64_t* ct;     // [B][d][2][L][N]
+  const uint64_t* xm;     // [S][2B][dpad][8]: query values times 256^b mod q, slot range
+  uint32_t s_begin, s_count;
   uint64_t* out;          // [B][K][2][L][N]
   int* err;               // device error word
   uint32_t B, d, dpad, K;
-  uint32_t MT, NT, chunks;
+  uint32_t QT, KT, chunks;
   uint64_t units;
   uint64_t w256[kMaxPrimes][8];        // 256^a mod q_j
   uint64_t w256_shoup[kMaxPrimes][8];
@@ -69,6 +76,8 @@ struct BatchArgs {
   uint64_t w32[kMaxPrimes];            // 2^32 mod q_j
   uint64_t w32_shoup[kMaxPrimes];
   uint64_t mu64[kMaxPrimes];           // floor(2^64 / q_j)
+  // wait back-off (ns) per role and whether every producer polls its stage
+  uint32_t sleep_tma, sleep_mma, sleep_prod, sleep_epi, all_poll;
 };
 
 // |v| mod q for |v| < 2^63 with mu = floor(2^64 / q), returned as v mod q.
@@ -140,11 +149,10 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
          ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
 }
 
-// kind::f16: D fp32, A and B bf16, both K-major, M = 128, N = 256.
-constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kBN >> 3) << 17) |
-                            ((uint32_t)(kBM >> 4) << 24);
+// kind::f16: D fp32, A and B fp16 (format 0), both K-major, M = 128, N = 256.
+constexpr uint32_t kIdesc = (1u << 4) | ((uint32_t)(kBN >> 3) << 17) | ((uint32_t)(kBM >> 4) << 24);
 
-__device__ __forceinline__ void mma_bf16(uint32_t dtmem, uint64_t adesc, uint64_t bdesc,
+__device__ __forceinline__ void mma_f16(uint32_t dtmem, uint64_t adesc, uint64_t bdesc,
                                          uint32_t accumulate) {
   asm volatile(
       "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
@@ -166,21 +174,26 @@ __device__ __forceinline__ void tc_fence_after() {
 }
 
 struct Decoded {
-  uint32_t j, mt, nt, s;
+  uint32_t j, qt, kt, s, sl;
 };
 
-// unit = ((j N + s) NT + nt) MT + mt: the M tiles of one database tile are
-// consecutive, so CTAs running side by side share it through L2.
-__device__ __forceinline__ Decoded decode_unit(uint64_t u, uint32_t N, const BatchArgs& A) {
+// unit = ((j S + s') KT + kt) QT + qt over the launch's slot range s' in
+// [0, s_count): the query tiles of one database tile are consecutive, so CTAs
+// running side by side share it through L2.  D.s is the absolute slot and
+// D.sl the slot within the range.  Units fit in 32 bits (the launcher checks).
+__device__ __forceinline__ Decoded decode_unit(uint32_t u, uint32_t logN, const BatchArgs& A) {
   Decoded D;
-  D.mt = (uint32_t)(u % A.MT);
-  uint64_t r = u / A.MT;
-  D.nt = (uint32_t)(r % A.NT);
-  r /= A.NT;
-  D.s = (uint32_t)(r % N);
-  D.j = (uint32_t)(r / N);
+  D.qt = u % A.QT;
+  uint32_t r = u / A.QT;
+  D.kt = r % A.KT;
+  r /= A.KT;
+  D.sl = r % A.s_count;
+  D.s = A.s_begin + D.sl;
+  D.j = r / A.s_count;
+  (void)logN;
   return D;
 }
+
 
 __global__ void __launch_bounds__(kThreads, 1)
 batched_mac_kernel(const __grid_constant__ CUtensorMap pmap, PrimeSet P, BatchArgs A) {
@@ -189,7 +202,6 @@ batched_mac_kernel(const __grid_constant__ CUtensorMap pmap, PrimeSet P, BatchAr
   __shared__ __align__(8) uint64_t bar_tfull[2], bar_tempty[2];
   __shared__ uint32_t tmem_base_slot;
   __shared__ volatile int abort_flag;
-  __shared__ int32_t tr[kEpiWarps][32 * kTrStride];
 
   const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   uint8_t* base = dsmem + ((1024 - (smem_u32(dsmem) & 1023)) & 1023);
@@ -198,7 +210,7 @@ batched_mac_kernel(const __grid_constant__ CUtensorMap pmap, PrimeSet P, BatchAr
   if (threadIdx.x == 0) {
     abort_flag = 0;
     for (int s = 0; s < kStages; ++s) {
-      mbar_init(smem_u32(&bar_full[s]), 2);
+      mbar_init(smem_u32(&bar_full[s]), 1 + kProdWarps);
       mbar_init(smem_u32(&bar_empty[s]), 1);
     }
     for (int a = 0; a < 2; ++a) {
@@ -220,171 +232,204 @@ batched_mac_kernel(const __grid_constant__ CUtensorMap pmap, PrimeSet P, BatchAr
 
   if (warp == 0) {
     // ---------------- TMA producer ----------------
-    if (lane == 0) {
-      uint64_t g = 0;
-      for (uint64_t u = blockIdx.x; u < A.units && !abort_flag; u += gridDim.x) {
-        const Decoded D = decode_unit(u, N, A);
-        for (uint32_t kc = 0; kc < A.chunks; ++kc, ++g) {
-          const uint32_t st = (uint32_t)(g % kStages), ph = (uint32_t)((g / kStages) & 1);
-          if (!mbar_wait(smem_u32(&bar_empty[st]), ph ^ 1, &abort_flag, A.err)) break;
+    // the whole warp walks the loop (converged); lane 0 waits and issues
+    uint64_t g = 0;
+    bool ok = true;
+    for (uint64_t u = blockIdx.x; u < A.units && ok; u += gridDim.x) {
+      const Decoded D = decode_unit((uint32_t)u, P.logN, A);
+      for (uint32_t kc = 0; kc < A.chunks; ++kc, ++g) {
+        const uint32_t st = (uint32_t)(g % kStages), ph = (uint32_t)((g / kStages) & 1);
+        bool ready = true;
+        if (lane == 0) ready = mbar_wait(smem_u32(&bar_empty[st]), ph ^ 1, &abort_flag, A.err, A.sleep_tma);
+        if (!__shfl_sync(0xffffffffu, (int)ready, 0)) { ok = false; break; }
+        if (lane == 0) {
           const uint32_t full = smem_u32(&bar_full[st]);
-          mbar_arrive_tx(full, kBTile);
-          tma_load_3d(sbase + st * kStageBytes + kATile, &pmap, (int)(kc * kBK), (int)(D.nt * kBN),
+          mbar_arrive_tx(full, kATile);
+          tma_load_3d(sbase + st * kStageBytes, &pmap, (int)(kc * kBK), (int)(D.kt * kBM),
                       (int)(D.j * N + D.s), full);
         }
+        __syncwarp();
       }
-      // drain: every issued copy completes before the CTA may exit
-      if (abort_flag) {
-        const uint64_t first = g > kStages ? g - kStages : 0;
-        for (uint64_t h = first; h < g; ++h) {
-          const uint32_t st = (uint32_t)(h % kStages), ph = (uint32_t)((h / kStages) & 1);
-          const unsigned long long t0 = clock64();
-          while (!mbar_try(smem_u32(&bar_full[st]), ph) && clock64() - t0 < kWaitCycles) {
-          }
+    }
+    // drain: every issued copy completes before the CTA may exit
+    if (!ok && lane == 0) {
+      const uint64_t first = g > kStages ? g - kStages : 0;
+      for (uint64_t h = first; h < g; ++h) {
+        const uint32_t st = (uint32_t)(h % kStages), ph = (uint32_t)((h / kStages) & 1);
+        const unsigned long long t0 = clock64();
+        while (!mbar_try(smem_u32(&bar_full[st]), ph) && clock64() - t0 < kWaitCycles) {
         }
       }
     }
+    __syncwarp();
   } else if (warp == 1) {
     // ---------------- MMA issuer ----------------
-    if (lane == 0) {
-      uint64_t g = 0, r = 0;
-      for (uint64_t u = blockIdx.x; u < A.units && !abort_flag; u += gridDim.x, ++r) {
-        const uint32_t slot = (uint32_t)(r & 1), aph = (uint32_t)((r >> 1) & 1);
-        if (!mbar_wait(smem_u32(&bar_tempty[slot]), aph ^ 1, &abort_flag, A.err)) break;
+    // the whole warp walks the loop (converged); lane 0 waits and issues
+    uint64_t g = 0, r = 0;
+    bool ok = true;
+    for (uint64_t u = blockIdx.x; u < A.units && ok; u += gridDim.x, ++r) {
+      const uint32_t slot = (uint32_t)(r & 1), aph = (uint32_t)((r >> 1) & 1);
+      bool ready = true;
+      if (lane == 0) ready = mbar_wait(smem_u32(&bar_tempty[slot]), aph ^ 1, &abort_flag, A.err, A.sleep_mma);
+      if (!__shfl_sync(0xffffffffu, (int)ready, 0)) break;
+      tc_fence_after();
+      const uint32_t dt = tmem + slot * kBN;
+      for (uint32_t kc = 0; kc < A.chunks; ++kc, ++g) {
+        const uint32_t st = (uint32_t)(g % kStages), ph = (uint32_t)((g / kStages) & 1);
+        if (lane == 0) ready = mbar_wait(smem_u32(&bar_full[st]), ph, &abort_flag, A.err, A.sleep_mma);
+        if (!__shfl_sync(0xffffffffu, (int)ready, 0)) { ok = false; break; }
         tc_fence_after();
-        const uint32_t dt = tmem + slot * kBN;
-        bool ok = true;
-        for (uint32_t kc = 0; kc < A.chunks; ++kc, ++g) {
-          const uint32_t st = (uint32_t)(g % kStages), ph = (uint32_t)((g / kStages) & 1);
-          if (!mbar_wait(smem_u32(&bar_full[st]), ph, &abort_flag, A.err)) { ok = false; break; }
-          tc_fence_after();
+        if (lane == 0) {
           const uint32_t a_addr = sbase + st * kStageBytes, b_addr = a_addr + kATile;
           const uint64_t ad = smem_desc(a_addr), bd = smem_desc(b_addr);
 #pragma unroll
           for (int k = 0; k < kBK / 16; ++k)
-            mma_bf16(dt, ad + 2 * k, bd + 2 * k, (kc > 0 || k > 0) ? 1u : 0u);
+            mma_f16(dt, ad + 2 * k, bd + 2 * k, (kc > 0 || k > 0) ? 1u : 0u);
           mma_commit(smem_u32(&bar_empty[st]));
         }
-        if (!ok) break;
-        mma_commit(smem_u32(&bar_tfull[slot]));
+        __syncwarp();
       }
+      if (!ok) break;
+      if (lane == 0) mma_commit(smem_u32(&bar_tfull[slot]));
+      __syncwarp();
     }
   } else if (warp < kEpiWarp0) {
     // ---------------- query-digit producers ----------------
-    // Balanced base-256 digits of X in [-128, 127]: the bytes of
-    // X + 0x8080808080808080 are exactly the digits plus 128 (X < 2^60, so the
-    // sum is an ordinary base-256 number without overflow).
+    // The pre-kernel stored X_b = X 256^b mod q (b = 0..7) for every query
+    // value.  Balanced base-256 digits of X_b in [-128, 127]: the bytes of
+    // X_b + 0x8080808080808080 are exactly the digits plus 128 (X_b < 2^60).
     const uint32_t pt = threadIdx.x - 32 * kProdWarp0;   // one (b, c, dim) item per thread
-    const uint32_t bcl = pt >> 3, il = pt & 7;             // local (b, c) row group, dim in chunk
-    // the ciphertext value this thread encodes in chunk kc of unit u
-    auto fetch = [&](uint64_t u, uint32_t kc) -> uint64_t {
-      const Decoded D = decode_unit(u, N, A);
-      const uint32_t bc = D.mt * 16 + bcl, i = kc * 8 + il;
-      if (bc >= 2 * A.B || i >= A.d) return 0;
-      const uint32_t b = bc >> 1, c = bc & 1;
-      return __ldg(A.ct + ((((uint64_t)b * A.d + i) * 2 + c) * L + D.j) * N + D.s);
+    const uint32_t bcl = pt >> 3, il = pt & 7;             // (b, c) row group in tile, dim in chunk
+    const uint32_t units = (uint32_t)A.units, chunks = A.chunks;
+    const uint32_t twoB = 2 * A.B;
+    // address of this thread's 8 multiples in chunk kc of unit u (or null)
+    auto item_ptr = [&](uint32_t u, uint32_t kc) -> const ulonglong2* {
+      if (u >= units) return nullptr;
+      const Decoded D = decode_unit(u, P.logN, A);
+      const uint32_t bc = D.qt * kQG + bcl, i = kc * 8 + il;
+      if (bc >= twoB || i >= A.d) return nullptr;
+      return reinterpret_cast<const ulonglong2*>(
+          A.xm + ((((uint64_t)D.j * A.s_count + D.sl) * twoB + bc) * A.dpad + i) * 8);
     };
+    // Each warp fills its own 32 items (4 row groups x 8 dims) of every stage
+    // and arrives on the stage's barrier itself, so warps run ahead of one
+    // another; values are prefetched two chunks ahead.
+    uint32_t cu = blockIdx.x, ck = 0;
+    auto next_pos = [&](uint32_t& u, uint32_t& k) {
+      if (++k == chunks) { k = 0; u += gridDim.x; }
+    };
+    auto load_item = [&](uint32_t u, uint32_t k, ulonglong2 (&dst)[4]) {
+      const ulonglong2* p = item_ptr(u, k);
+#pragma unroll
+      for (int h = 0; h < 4; ++h) dst[h] = p ? __ldg(p + h) : make_ulonglong2(0, 0);
+    };
+    ulonglong2 nx0[4], nx1[4];
+    uint32_t fu = cu, fk = ck;
+    load_item(fu, fk, nx0);
+    next_pos(fu, fk);
+    load_item(fu, fk, nx1);
+    next_pos(fu, fk);
     uint64_t g = 0;
-    uint64_t X_next = blockIdx.x < A.units ? fetch(blockIdx.x, 0) : 0;
-    for (uint64_t u = blockIdx.x; u < A.units && !abort_flag; u += gridDim.x) {
-      const Decoded D = decode_unit(u, N, A);
-      const uint64_t q = P.q[D.j];
-      const uint64_t r256s = A.r256_shoup[D.j];
-      bool ok = true;
-      for (uint32_t kc = 0; kc < A.chunks; ++kc, ++g) {
-        uint64_t X = X_next;
-        if (kc + 1 < A.chunks) X_next = fetch(u, kc + 1);
-        else if (u + gridDim.x < A.units) X_next = fetch(u + gridDim.x, 0);
-        const uint32_t st = (uint32_t)(g % kStages), ph = (uint32_t)((g / kStages) & 1);
-        if (!mbar_wait(smem_u32(&bar_empty[st]), ph ^ 1, &abort_flag, A.err, 32)) { ok = false; break; }
-        uint8_t* at = base + st * kStageBytes;
-        uint32_t ylo[8], yhi[8];  // X 256^b8 mod q + 0x80..80, b8 = 0..7
+    bool ok = cu < units;
+    while (ok) {
+      ulonglong2 cur[4];
 #pragma unroll
-        for (int b8 = 0; b8 < 8; ++b8) {
-          const uint64_t y = X + 0x8080808080808080ull;
-          ylo[b8] = (uint32_t)y;
-          yhi[b8] = (uint32_t)(y >> 32);
-          if (b8 < 7) X = mul_shoup(X, 256, r256s, q);
-        }
+      for (int h = 0; h < 4; ++h) { cur[h] = nx0[h]; nx0[h] = nx1[h]; }
+      load_item(fu, fk, nx1);
+      next_pos(fu, fk);
+      const uint32_t st = (uint32_t)(g % kStages), ph = (uint32_t)((g / kStages) & 1);
+      ++g;
+      // lane 0 polls the stage, the warp follows its decision
+      bool ready = true;
+      if (lane == 0) ready = mbar_wait(smem_u32(&bar_empty[st]), ph ^ 1, &abort_flag, A.err, A.sleep_prod);
+      if (!__shfl_sync(0xffffffffu, (int)ready, 0)) break;
+      uint8_t* at = base + st * kStageBytes + kATile;
+      uint32_t ylo[8], yhi[8];
 #pragma unroll
-        for (int a = 0; a < 8; ++a) {
-          const uint32_t sel = 0x7440u + (uint32_t)(a & 3);  // byte a, two zero bytes, 0x4B
-          uint32_t w[4];
-#pragma unroll
-          for (int m = 0; m < 4; ++m) {
-            const uint32_t w0 = a < 4 ? ylo[2 * m] : yhi[2 * m];
-            const uint32_t w1 = a < 4 ? ylo[2 * m + 1] : yhi[2 * m + 1];
-            const float f0 = __uint_as_float(__byte_perm(w0, 0x4B000000u, sel)) - 8388736.0f;
-            const float f1 = __uint_as_float(__byte_perm(w1, 0x4B000000u, sel)) - 8388736.0f;
-            w[m] = __byte_perm(__float_as_uint(f0), __float_as_uint(f1), 0x7632);
-          }
-          const uint32_t row = bcl * 8 + a;
-          uint4* dst = reinterpret_cast<uint4*>(at + row * 128 + ((il ^ (row & 7)) << 4));
-          *dst = make_uint4(w[0], w[1], w[2], w[3]);
-        }
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        asm volatile("bar.sync 1, %0;" ::"n"(kProdThreads) : "memory");
-        if (pt == 0) mbar_arrive(smem_u32(&bar_full[st]));
+      for (int h = 0; h < 4; ++h) {
+        const uint64_t y0 = cur[h].x + 0x8080808080808080ull;
+        const uint64_t y1 = cur[h].y + 0x8080808080808080ull;
+        ylo[2 * h] = (uint32_t)y0;
+        yhi[2 * h] = (uint32_t)(y0 >> 32);
+        ylo[2 * h + 1] = (uint32_t)y1;
+        yhi[2 * h + 1] = (uint32_t)(y1 >> 32);
       }
-      if (!ok) break;
+      // an item past d or past 2B reads X_b = 0, whose digits are all zero
+#pragma unroll
+      for (int a = 0; a < 8; ++a) {
+        // byte a of the two words into the low bytes of two fp16 halves
+        const uint32_t sel = (uint32_t)(a & 3) | ((uint32_t)(4 + (a & 3)) << 8);
+        uint32_t w[4];
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+          const uint32_t w0 = a < 4 ? ylo[2 * m] : yhi[2 * m];
+          const uint32_t w1 = a < 4 ? ylo[2 * m + 1] : yhi[2 * m + 1];
+          // fp16 1024 + v (0x6400 | v) minus 1152 = v - 128, exact
+          const uint32_t hv = (__byte_perm(w0, w1, sel) & 0x00FF00FFu) | 0x64006400u;
+          uint32_t h;
+          asm("sub.rn.f16x2 %0, %1, %2;" : "=r"(h) : "r"(hv), "r"(0x64806480u));
+          w[m] = h;
+        }
+        const uint32_t row = bcl * 8 + a;
+        uint4* dst = reinterpret_cast<uint4*>(at + row * 128 + ((il ^ (row & 7)) << 4));
+        *dst = make_uint4(w[0], w[1], w[2], w[3]);
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_u32(&bar_full[st]));
+      next_pos(cu, ck);
+      if (cu >= units) ok = false;
     }
   } else {
     // ---------------- epilogue ----------------
-    // A warp reads 32 TMEM lanes (rows (b, c, a) of 4 row groups) x 16
-    // columns, converts the exact fp32 sums to int32, transposes them through
-    // shared memory so that each lane holds the 8 digit rows of one output,
-    // and combines them exactly: lo = sum_{a<4} S_a 256^a and hi = sum_{a>=4}
-    // S_a 256^(a-4) (both below 2^49 in magnitude), acc = lo + hi 2^32 mod q.
-    const uint32_t ew = warp - kEpiWarp0;         // 0..7
+    // Lane = database block k of the tile; columns (bc, a) with a fastest, so
+    // each x32 load holds the 8 digit sums of 4 outputs.  Exact combination:
+    // lo = sum_{a<4} S_a 256^a and hi = sum_{a>=4} S_a 256^(a-4) (both below
+    // 2^49 in magnitude), acc = lo + hi 2^32 mod q.
     const uint32_t quarter = warp & 3;            // TMEM lanes 32 quarter ..
-    const uint32_t half = ew >> 2;                // columns 128 half ..
-    int32_t* trw = tr[ew];
-    const uint32_t og = lane >> 3;                // output row group (0..3) of this lane
-    const uint32_t oc = lane & 7;                 // output column within 8
+    const uint32_t chalf = (warp - kEpiWarp0) >> 2;  // column half of the tile
     uint64_t r = 0;
     for (uint64_t u = blockIdx.x; u < A.units && !abort_flag; u += gridDim.x, ++r) {
       const uint32_t slot = (uint32_t)(r & 1), aph = (uint32_t)((r >> 1) & 1);
-      if (!mbar_wait(smem_u32(&bar_tfull[slot]), aph, &abort_flag, A.err, 128)) break;
+      // lane 0 waits for the accumulator, the warp follows its decision
+      bool ready = true;
+      if (lane == 0) ready = mbar_wait(smem_u32(&bar_tfull[slot]), aph, &abort_flag, A.err, A.sleep_epi);
+      if (!__shfl_sync(0xffffffffu, (int)ready, 0)) break;
       tc_fence_after();
-      const Decoded D = decode_unit(u, N, A);
-      const uint64_t q = P.q[D.j];
+      const Decoded D = decode_unit((uint32_t)u, P.logN, A);
+      const uint64_t q = P.q[D.j], mu = A.mu64[D.j];
       const uint64_t w32 = A.w32[D.j], w32s = A.w32_shoup[D.j];
-      const uint32_t bc = D.mt * 16 + quarter * 4 + og;   // (b, c) of this lane's outputs
-      const bool row_ok = bc < 2 * A.B;
-      const uint32_t b = bc >> 1, c = bc & 1;
-      uint64_t* orow = A.out + ((((uint64_t)b * A.K) * 2 + c) * L + D.j) * N + D.s;
-      const uint64_t kstride = 2ull * L * N;
-      for (uint32_t cc = 0; cc < 128 / kEpiCols; ++cc) {
-        const uint32_t col0 = half * 128 + cc * kEpiCols;
-        uint32_t v[kEpiCols];
+      const uint32_t k = D.kt * kBM + quarter * 32 + lane;
+      const bool k_ok = k < A.K;
+      for (uint32_t cc = chalf * (kBN / 64); cc < (chalf + 1) * (kBN / 64); ++cc) {
+        uint32_t v[32];
         asm volatile(
-            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, "
-            "%10, %11, %12, %13, %14, %15}, [%16];"
+            "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, "
+            "%10, %11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, "
+            "%27, %28, %29, %30, %31}, [%32];"
             : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]),
               "=r"(v[6]), "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]),
-              "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
-            : "r"(tmem + ((quarter * 32) << 16) + slot * kBN + col0));
+              "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]),
+              "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
+              "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]),
+              "=r"(v[30]), "=r"(v[31])
+            : "r"(tmem + ((quarter * 32) << 16) + slot * kBN + cc * 32));
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-        for (int x = 0; x < kEpiCols; ++x)
-          trw[lane * kTrStride + x] = __float2int_rn(__uint_as_float(v[x]));
-        __syncwarp();
+        for (int o = 0; o < 4; ++o) {
+          int64_t sa[8];
 #pragma unroll
-        for (int h = 0; h < kEpiCols / 8; ++h) {
-          const uint32_t col = h * 8 + oc;
-          const int32_t* src = trw + (og * 8) * kTrStride + col;
-          const int64_t lo = (int64_t)src[0] + ((int64_t)src[kTrStride] << 8) +
-                             ((int64_t)src[2 * kTrStride] << 16) + ((int64_t)src[3 * kTrStride] << 24);
-          const int64_t hi = (int64_t)src[4 * kTrStride] + ((int64_t)src[5 * kTrStride] << 8) +
-                             ((int64_t)src[6 * kTrStride] << 16) + ((int64_t)src[7 * kTrStride] << 24);
-          const uint64_t mu = A.mu64[D.j];
-          const uint64_t rl = signed_mod(lo, q, mu);
-          const uint64_t rh = signed_mod(hi, q, mu);
-          const uint64_t res = add_mod(rl, mul_shoup(rh, w32, w32s, q), q);
-          const uint32_t k = D.nt * kBN + col0 + col;
-          if (row_ok && k < A.K) orow[(uint64_t)k * kstride] = res;
+          for (int a = 0; a < 8; ++a) sa[a] = __float2int_rn(__uint_as_float(v[o * 8 + a]));
+          const int64_t lo = sa[0] + (sa[1] << 8) + (sa[2] << 16) + (sa[3] << 24);
+          const int64_t hi = sa[4] + (sa[5] << 8) + (sa[6] << 16) + (sa[7] << 24);
+          const uint64_t res =
+              add_mod(signed_mod(lo, q, mu), mul_shoup(signed_mod(hi, q, mu), w32, w32s, q), q);
+          const uint32_t bc = D.qt * kQG + cc * 4 + o;
+          if (k_ok && bc < 2 * A.B) {
+            const uint32_t b = bc >> 1, c = bc & 1;
+            A.out[((((uint64_t)b * A.K + k) * 2 + c) * L + D.j) * N + D.s] = res;
+          }
         }
-        __syncwarp();
       }
       tc_fence_before();
       __syncwarp();
@@ -400,7 +445,7 @@ batched_mac_kernel(const __grid_constant__ CUtensorMap pmap, PrimeSet P, BatchAr
   }
 }
 
-// Database digits: pt [K][L][d][N] u64 -> plimb [L][N][K][8 dpad] bf16, column
+// Database digits: pt [K][L][d][N] u64 -> plimb [L][N][K][8 dpad] fp16, column
 // 8 i + b = digit b of pt[k][j][i][s] (zero for i >= d).  One block per
 // (k, j, 32-slot group) transposes through shared memory.
 __global__ void prepare_limbs_kernel(const uint64_t* __restrict__ pt, uint32_t K, uint32_t L,
@@ -422,13 +467,44 @@ __global__ void prepare_limbs_kernel(const uint64_t* __restrict__ pt, uint32_t K
       int t = (int)(y & 255);
       y >>= 8;
       if (t >= 128) { t -= 256; y += 1; }
-      const uint32_t h = __float_as_uint((float)t) >> 16;
+      const uint32_t h = (uint32_t)__half_as_ushort(__float2half_rn((float)t));
       if (b & 1) w[b >> 1] |= h << 16;
       else w[b >> 1] = h;
     }
     uint16_t* dst = plimb + (((uint64_t)j * N + s0 + s) * K + k) * (8ull * dpad) + 8ull * i;
     *reinterpret_cast<uint4*>(dst) = make_uint4(w[0], w[1], w[2], w[3]);
   }
+}
+
+// X_b = ct 256^b mod q for b = 0..7, for the slots [s_begin, s_begin + S):
+// xm[j][s'][bc][i][b], bc = 2 b_query + c.  One thread per (j, s', bc, i),
+// slot fastest so that the ciphertext reads coalesce.
+__global__ void expand_query_kernel(PrimeSet P, const uint64_t* __restrict__ ct, uint32_t B,
+                                    uint32_t d, uint32_t dpad, uint32_t s_begin, uint32_t S,
+                                    const uint64_t* __restrict__ w256,
+                                    const uint64_t* __restrict__ w256s,
+                                    uint64_t* __restrict__ xm) {
+  const uint64_t gid = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+  const uint64_t total = (uint64_t)P.L * S * 2 * B * d;
+  if (gid >= total) return;
+  const uint32_t sl = (uint32_t)(gid % S);
+  uint64_t r = gid / S;
+  const uint32_t i = (uint32_t)(r % d);
+  r /= d;
+  const uint32_t bc = (uint32_t)(r % (2 * B));
+  const uint32_t j = (uint32_t)(r / (2 * B));
+  const uint32_t b = bc >> 1, c = bc & 1;
+  const uint32_t N = P.N, L = P.L;
+  const uint64_t q = P.q[j];
+  const uint64_t X = ct[((((uint64_t)b * d + i) * 2 + c) * L + j) * N + s_begin + sl];
+  uint64_t v[8];
+  v[0] = X;
+#pragma unroll
+  for (int k = 1; k < 8; ++k) v[k] = mul_shoup(X, w256[j * 8 + k], w256s[j * 8 + k], q);
+  ulonglong2* dst = reinterpret_cast<ulonglong2*>(
+      xm + ((((uint64_t)j * S + sl) * 2 * B + bc) * dpad + i) * 8);
+#pragma unroll
+  for (int h = 0; h < 4; ++h) dst[h] = make_ulonglong2(v[2 * h], v[2 * h + 1]);
 }
 
 std::mutex g_encode_mu;
@@ -475,9 +551,9 @@ int make_limb_map(const PrimeSet& P, const uint16_t* plimb, uint64_t K, uint32_t
   const uint32_t dpad = (d + 7) / 8 * 8;
   const cuuint64_t dims[3] = {8ull * dpad, K, (cuuint64_t)P.L * P.N};
   const cuuint64_t strides[2] = {8ull * dpad * 2, K * 8ull * dpad * 2};
-  const cuuint32_t box[3] = {(cuuint32_t)kBK, (cuuint32_t)kBN, 1};
+  const cuuint32_t box[3] = {(cuuint32_t)kBK, (cuuint32_t)kBM, 1};
   const cuuint32_t estr[3] = {1, 1, 1};
-  CUresult r = enc(reinterpret_cast<CUtensorMap*>(map_out), CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3,
+  CUresult r = enc(reinterpret_cast<CUtensorMap*>(map_out), CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 3,
                    const_cast<uint16_t*>(plimb), dims, strides, box, estr,
                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
@@ -487,25 +563,31 @@ int make_limb_map(const PrimeSet& P, const uint16_t* plimb, uint64_t K, uint32_t
 
 cudaError_t launch_batched_mac(const PrimeSet& P, const void* map, const uint64_t* ct, uint32_t B,
                                uint32_t d, uint64_t K, uint64_t* out, int* err, int sms,
-                               cudaStream_t st) {
+                               const uint32_t tune[5], cudaStream_t st) {
   BatchArgs A;
   memset(&A, 0, sizeof(A));
-  A.ct = ct;
+  A.sleep_tma = tune[0];
+  A.sleep_mma = tune[1];
+  A.sleep_prod = tune[2];
+  A.sleep_epi = tune[3];
+  A.all_poll = tune[4];
   A.out = out;
   A.err = err;
   A.B = B;
   A.d = d;
   A.dpad = (d + 7) / 8 * 8;
   A.K = (uint32_t)K;
-  A.MT = (2 * B + 15) / 16;
-  A.NT = (uint32_t)((K + kBN - 1) / kBN);
+  A.QT = (2 * B + kQG - 1) / kQG;
+  A.KT = (uint32_t)((K + kBM - 1) / kBM);
   A.chunks = A.dpad / 8;
-  A.units = (uint64_t)P.L * P.N * A.NT * A.MT;
+  uint64_t hw[kMaxPrimes * 16];
   for (uint32_t j = 0; j < P.L; ++j) {
     uint64_t w = 1 % P.q[j];
     for (int a = 0; a < 8; ++a) {
       A.w256[j][a] = w;
       A.w256_shoup[j][a] = shoup_of(w, P.q[j]);
+      hw[j * 8 + a] = w;
+      hw[kMaxPrimes * 8 + j * 8 + a] = A.w256_shoup[j][a];
       w = (uint64_t)(((u128)w * 256) % P.q[j]);
     }
     A.r256_shoup[j] = shoup_of(256 % P.q[j], P.q[j]);
@@ -513,16 +595,41 @@ cudaError_t launch_batched_mac(const PrimeSet& P, const void* map, const uint64_
     A.w32_shoup[j] = shoup_of(A.w32[j], P.q[j]);
     A.mu64[j] = (uint64_t)(((u128)1 << 64) / P.q[j]);
   }
+  // slot ranges bound the scratch of the query multiples to about 4 GiB
+  const uint64_t per_slot = (uint64_t)P.L * 2 * B * A.dpad * 8 * sizeof(uint64_t);
+  uint64_t S = (4ull << 30) / per_slot;
+  if (S < 1) S = 1;
+  if (S > P.N) S = P.N;
   const size_t smem = (size_t)kStages * kStageBytes + 1024;
   cudaError_t e = cudaFuncSetAttribute(batched_mac_kernel,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  uint64_t grid = (uint64_t)(sms > 0 ? sms : 148);
-  if (grid > A.units) grid = A.units;
+  uint64_t* scratch = nullptr;
+  e = cudaMallocAsync(&scratch, per_slot * S + sizeof(hw), st);
+  if (e != cudaSuccess) return e;
+  uint64_t* dw = scratch + per_slot * S / sizeof(uint64_t);
+  e = cudaMemcpyAsync(dw, hw, sizeof(hw), cudaMemcpyHostToDevice, st);
   CUtensorMap m;
   memcpy(&m, map, sizeof(m));
-  batched_mac_kernel<<<(unsigned)grid, kThreads, smem, st>>>(m, P, A);
-  return cudaGetLastError();
+  for (uint64_t s0 = 0; s0 < P.N && e == cudaSuccess; s0 += S) {
+    const uint32_t cnt = (uint32_t)(s0 + S <= P.N ? S : P.N - s0);
+    A.s_begin = (uint32_t)s0;
+    A.s_count = cnt;
+    A.xm = scratch;
+    A.units = (uint64_t)P.L * cnt * A.KT * A.QT;
+    if (A.units >= (1ull << 31)) { e = cudaErrorInvalidValue; break; }
+    const uint64_t threads = (uint64_t)P.L * cnt * 2 * B * d;
+    expand_query_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(
+        P, ct, B, d, A.dpad, (uint32_t)s0, cnt, dw, dw + kMaxPrimes * 8, scratch);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) break;
+    uint64_t grid = (uint64_t)(sms > 0 ? sms : 148);
+    if (grid > A.units) grid = A.units;
+    batched_mac_kernel<<<(unsigned)grid, kThreads, smem, st>>>(m, P, A);
+    e = cudaGetLastError();
+  }
+  cudaError_t e2 = cudaFreeAsync(scratch, st);
+  return e != cudaSuccess ? e : e2;
 }
 
 }  // namespace sanns

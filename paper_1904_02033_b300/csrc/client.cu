@@ -104,7 +104,7 @@ __global__ void __launch_bounds__(512) decrypt_phase_kernel(PrimeSet P, const ui
   const uint64_t q = P.q[j];
   const uint64_t* c0 = ct_out + ((bk * 2 + 0) * L + j) * N;
   const uint64_t* c1 = ct_out + ((bk * 2 + 1) * L + j) * N;
-  for (uint32_t x = threadIdx.x; x < N; x += blockDim.x) sa[SP(x)] = c1[x];
+  load_poly(sa, c1, N);
   __syncthreads();
   ntt_forward_smem(sa, P, j);
   __syncthreads();

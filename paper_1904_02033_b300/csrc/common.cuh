@@ -165,6 +165,33 @@ __device__ __forceinline__ void draw_pair(const uint32_t blk[16], int u, uint64_
 __host__ __device__ __forceinline__ uint32_t SP(uint32_t x) { return x + (x >> 4); }
 __host__ __device__ __forceinline__ uint32_t ntt_smem_words(uint32_t N) { return N + N / 16; }
 
+// Global <-> padded shared-memory copies of one polynomial by the whole block,
+// 16-byte accesses, eight in flight per thread before any is used.
+__device__ __forceinline__ void load_poly(uint64_t* sa, const uint64_t* __restrict__ g, uint32_t N) {
+  const uint32_t step = 2 * blockDim.x;
+  for (uint32_t base = 0; base < N; base += 8 * step) {
+    ulonglong2 v[8];
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+      const uint32_t x = base + r * step + 2 * threadIdx.x;
+      v[r] = x < N ? __ldg(reinterpret_cast<const ulonglong2*>(g + x)) : make_ulonglong2(0, 0);
+    }
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+      const uint32_t x = base + r * step + 2 * threadIdx.x;
+      if (x < N) {
+        sa[SP(x)] = v[r].x;
+        sa[SP(x + 1)] = v[r].y;
+      }
+    }
+  }
+}
+
+__device__ __forceinline__ void store_poly(uint64_t* __restrict__ g, const uint64_t* sa, uint32_t N) {
+  for (uint32_t x = 2 * threadIdx.x; x < N; x += 2 * blockDim.x)
+    *reinterpret_cast<ulonglong2*>(g + x) = make_ulonglong2(sa[SP(x)], sa[SP(x + 1)]);
+}
+
 __device__ __forceinline__ void fwd_bfly(uint64_t& X, uint64_t& Y, uint64_t w, uint64_t ws,
                                          uint64_t q, uint64_t q2) {
   X = csub(X, q2);

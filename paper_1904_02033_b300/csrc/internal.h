@@ -15,6 +15,7 @@ struct sanns_ctx {
   int sms;
   int mac_variant;          // launch variant of the MAC kernel (autotuned)
   int* d_err;               // device error word raised by bounded waits
+  uint32_t batched_tune[5]; // batched kernel: back-off ns (TMA, MMA, producers, epilogue), all-poll
 };
 
 struct sanns_sk {
@@ -95,7 +96,7 @@ cudaError_t launch_prepare_limbs(const PrimeSet& P, const uint64_t* pt, uint64_t
 int make_limb_map(const PrimeSet& P, const uint16_t* plimb, uint64_t K, uint32_t d, void* map_out);
 cudaError_t launch_batched_mac(const PrimeSet& P, const void* map, const uint64_t* ct, uint32_t B,
                                uint32_t d, uint64_t K, uint64_t* out, int* err, int sms,
-                               cudaStream_t st);
+                               const uint32_t tune[5], cudaStream_t st);
 cudaError_t launch_decrypt(const PrimeSet& P, const uint64_t* ct_out, const int8_t* s,
                            const uint64_t* s_hat, const uint64_t* s_hat_shoup, uint32_t B,
                            uint64_t K, uint64_t n, const uint8_t* qv, uint32_t d,

@@ -18,12 +18,12 @@ __global__ void __launch_bounds__(512) ntt_kernel(PrimeSet P, uint64_t* data, in
   const uint64_t poly = blockIdx.x;
   const int j = (int)(poly % P.L);
   uint64_t* g = data + poly * N;
-  for (uint32_t x = threadIdx.x; x < N; x += blockDim.x) sa[SP(x)] = g[x];
+  load_poly(sa, g, N);
   __syncthreads();
   if (inverse) ntt_inverse_smem(sa, P, j);
   else ntt_forward_smem(sa, P, j);
   __syncthreads();
-  for (uint32_t x = threadIdx.x; x < N; x += blockDim.x) g[x] = sa[SP(x)];
+  store_poly(g, sa, N);
 }
 
 // Encoding: block (k, i) builds coordinate i of positions kN .. kN+N-1 and
@@ -110,42 +110,62 @@ __global__ void __launch_bounds__(256, 3) intt_mask_kernel(PrimeSet P, uint64_t*
   const uint64_t bk = poly / (2 * L);
   const uint64_t k = bk % K, b = bk / K;
   uint64_t* g = ct_out + poly * N;
-  for (uint32_t x = threadIdx.x; x < N; x += blockDim.x) sa[SP(x)] = g[x];
+  load_poly(sa, g, N);
   __syncthreads();
   ntt_inverse_smem(sa, P, j);
   __syncthreads();
   if (c == 0) {
     const uint64_t q = P.q[j], dl = P.delta[j], dls = P.delta_shoup[j], t = P.t;
     const uint32_t* sh = srv_share + b * n;
-    for (uint32_t u = threadIdx.x; u < N / 4; u += blockDim.x) {
-      const uint64_t pos0 = k * N + 4 * u;
-      uint64_t r[4];
-      if (pos0 + 3 < n) {
+    // four positions per thread per round; all loads of a round are issued
+    // before any is used
+    for (uint32_t u0 = 0; u0 < N / 4; u0 += 4 * blockDim.x) {
+      uint4 nv[4], sv[4];
 #pragma unroll
-        for (int v = 0; v < 4; ++v) {
-          const uint64_t sv = sh[pos0 + v];
-          r[v] = sv == 0 ? 0 : t - sv;
-        }
-      } else {
-        uint32_t blk[16];
-        chacha20_block(mask_seed, kPurposeMask, qids[b], (uint32_t)(pos0 / 4), blk);
-#pragma unroll
-        for (int v = 0; v < 4; ++v) {
-          uint64_t lo, hi;
-          draw_pair(blk, v, lo, hi);
-          r[v] = mod_t128(lo, hi, P);
-        }
+      for (int z = 0; z < 4; ++z) {
+        const uint32_t u = u0 + z * blockDim.x + threadIdx.x;
+        const uint64_t pos0 = k * N + 4 * u;
+        nv[z] = u < N / 4 ? __ldg(reinterpret_cast<const uint4*>(norms + pos0)) : make_uint4(0, 0, 0, 0);
+        // server shares exist only below n; n need not be a multiple of 4
+        if (u < N / 4 && pos0 + 3 < n && (reinterpret_cast<uintptr_t>(sh + pos0) & 15) == 0)
+          sv[z] = __ldg(reinterpret_cast<const uint4*>(sh + pos0));
+        else if (u < N / 4 && pos0 + 3 < n)
+          sv[z] = make_uint4(sh[pos0], sh[pos0 + 1], sh[pos0 + 2], sh[pos0 + 3]);
+        else
+          sv[z] = make_uint4(0, 0, 0, 0);
       }
 #pragma unroll
-      for (int v = 0; v < 4; ++v) {
-        const uint64_t val = mod_t64((uint64_t)norms[pos0 + v] + r[v], t, P.t_barrett);
-        const uint32_t x = 4 * u + v;
-        sa[SP(x)] = add_mod(sa[SP(x)], mul_shoup(val, dl, dls, q), q);
+      for (int z = 0; z < 4; ++z) {
+        const uint32_t u = u0 + z * blockDim.x + threadIdx.x;
+        if (u >= N / 4) continue;
+        const uint64_t pos0 = k * N + 4 * u;
+        uint64_t r[4];
+        if (pos0 + 3 < n) {
+          const uint32_t svv[4] = {sv[z].x, sv[z].y, sv[z].z, sv[z].w};
+#pragma unroll
+          for (int v = 0; v < 4; ++v) r[v] = svv[v] == 0 ? 0 : t - svv[v];
+        } else {
+          uint32_t blk[16];
+          chacha20_block(mask_seed, kPurposeMask, qids[b], (uint32_t)(pos0 / 4), blk);
+#pragma unroll
+          for (int v = 0; v < 4; ++v) {
+            uint64_t lo, hi;
+            draw_pair(blk, v, lo, hi);
+            r[v] = mod_t128(lo, hi, P);
+          }
+        }
+        const uint32_t nvv[4] = {nv[z].x, nv[z].y, nv[z].z, nv[z].w};
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+          const uint64_t val = mod_t64((uint64_t)nvv[v] + r[v], t, P.t_barrett);
+          const uint32_t x = 4 * u + v;
+          sa[SP(x)] = add_mod(sa[SP(x)], mul_shoup(val, dl, dls, q), q);
+        }
       }
     }
     __syncthreads();
   }
-  for (uint32_t x = threadIdx.x; x < N; x += blockDim.x) g[x] = sa[SP(x)];
+  store_poly(g, sa, N);
 }
 
 }  // namespace

@@ -65,6 +65,8 @@ _SIGS = {
                                 C.c_int),
     "sanns_distances_batched_mac": ([_VP, _VP, _VP, C.c_uint32, _VP, _VP], C.c_int),
     "sanns_device_status": ([_VP, _VP], C.c_int),
+    "sanns_batched_set_waits": ([_VP, C.c_uint32, C.c_uint32, C.c_uint32, C.c_uint32, C.c_int],
+                                C.c_int),
     "sanns_decrypt_shares": ([_VP, _VP, _VP, C.c_uint32, C.c_uint64, _VP, _VP, _VP], C.c_int),
 }
 
@@ -403,3 +405,9 @@ def sanns_distances_batched_mac(ctx: Context, db: Database, ct_in: torch.Tensor,
 
 def sanns_device_status(ctx: Context, stream=None):
     _check(load().sanns_device_status(ctx.handle, _stream(stream)))
+
+
+def sanns_batched_set_waits(ctx: Context, tma_ns: int, mma_ns: int, producer_ns: int,
+                            epilogue_ns: int, all_producers_poll: bool):
+    _check(load().sanns_batched_set_waits(ctx.handle, tma_ns, mma_ns, producer_ns, epilogue_ns,
+                                          1 if all_producers_poll else 0))
