@@ -254,11 +254,17 @@ def run_gpu(args) -> None:
     cpu = None
     if rank == 0:
         cpu = cpu_baseline(quick=args.quick_cpu)
-    batched = None
+    batched = cluster = serving = None
     if rank == 0 and not args.no_batched:
         del ct_all
         torch.cuda.empty_cache()
         batched = run_batched_section(quick=args.quick_batched)
+        torch.cuda.empty_cache()
+    if rank == 0 and not args.no_extra:
+        cluster = run_cluster_section()
+        torch.cuda.empty_cache()
+        serving = run_serving_section()
+        torch.cuda.empty_cache()
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -289,6 +295,8 @@ def run_gpu(args) -> None:
             "clocks": ck,
             "cpu_baseline": cpu,
             "batched": batched,
+            "clustering": cluster,
+            "serving": serving,
         }
         print(json.dumps(line), flush=True)
     if dist:
@@ -383,6 +391,140 @@ def run_batched_section(quick: bool = False, n_override: int | None = None,
     }
 
 
+CLUSTER = dict(n=1_000_000, d=128, N=8192, L=3, prime_bits=60, t_rule=0, k=1024, zipf=1.1,
+               sigma=20.0, B=256, P=32, iters=20, seed=11)
+
+
+def run_cluster_section() -> dict:
+    """Clustering protocol: 1024 Lloyd clusters over Zipf(1.1)-weighted mixture
+    data (n = 10^6, d = 128); 256 queries each probe their 32 nearest centres;
+    all (query, block) work items of the batch run in one persistent launch."""
+    import numpy as np
+    import torch
+
+    from paper_1904_02033_b300 import inputs
+    from paper_1904_02033_b300 import sanns as S
+
+    W = CLUSTER
+    n, d, N, L, B, Pr = W["n"], W["d"], W["N"], W["L"], W["B"], W["P"]
+    ctx = S.sanns_ctx_create(N, L, W["prime_bits"], W["t_rule"], d)
+    wts = inputs.zipf_weights(W["k"], W["zipf"])
+    coords = inputs.mixture_coords_device_weighted(n, d, W["k"], W["sigma"], W["seed"], wts)
+    centres, assign = inputs.lloyd_kmeans_device(coords, W["k"], W["iters"], W["seed"] + 1)
+    order = torch.argsort(assign, stable=True).to(torch.int32).view(torch.uint32)
+    cnt = torch.bincount(assign, minlength=W["k"]).cpu().numpy()
+    offsets = np.zeros(W["k"] + 1, dtype=np.uint64)
+    offsets[1:] = np.cumsum(cnt)
+    cl = S.sanns_clusters_create(ctx, coords, offsets, order.contiguous())
+    q = inputs.mixture_coords_device_weighted(B, d, W["k"], W["sigma"], W["seed"] + 2, wts,
+                                              means_seed=W["seed"])
+    probes = inputs.probes_device(q, centres, Pr).cpu().numpy().astype(np.uint32)
+    qids = torch.arange(B, dtype=torch.int64).to(torch.uint64).cuda()
+    sk = S.sanns_keygen(ctx, W["seed"] + 3)
+    ct = S.sanns_encrypt_query(ctx, sk, q, W["seed"] + 4, qids)
+    st = torch.cuda.current_stream()
+    # warm-up, then timed launches
+    out = S.sanns_distances_gather(ctx, cl, ct, probes, 5, qids)
+    torch.cuda.synchronize()
+    reps = 3
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for _ in range(reps):
+        out = S.sanns_distances_gather(ctx, cl, ct, probes, 5, qids)
+    e1.record(st)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    ct_out, srv, ids, n_b, k_b = out
+    total_pts, total_blocks = int(n_b.sum()), int(k_b.sum())
+    # the same query through the linear-scan entry point on its gathered list
+    b = 0
+    g = ids[: int(n_b[0])]
+    db_b = S.sanns_encode_db(ctx, coords, g.contiguous())
+    ref_out, ref_srv = S.sanns_distances(ctx, db_b, ct[0:1], 5, qids[0:1])
+    same = bool(torch.equal(ref_out[0], ct_out[: int(k_b[0])])) and bool(
+        torch.equal(ref_srv[0], srv[: int(n_b[0])]))
+    S.sanns_device_status(ctx)
+    return {
+        "workload": "clustering: n=1,000,000 d=128 uint8 mixture of 1024 Zipf(1.1)-weighted "
+                    "components (sigma 20); seeded Lloyd k-means to 1024 clusters; 256 queries x "
+                    "32 probes; one persistent launch per batch; BFV N=8192, three 60-bit primes",
+        "qp_per_s": total_pts / (ms * 1e-3),
+        "ms_per_batch": ms, "queries": B, "gathered_points": total_pts,
+        "work_items": total_blocks, "block_fill": total_pts / (total_blocks * N),
+        "cluster_size_max_mean": [int(cnt.max()), float(cnt.mean())],
+        "query0_bit_identical_to_linear_scan_on_its_gathered_list": same,
+    }
+
+
+SERVE = dict(rate=2000.0, duration=3.0, max_batch=128, slots=3, seed=21, sample_frac=0.02)
+
+
+def run_serving_section() -> dict:
+    """Serving: Poisson arrivals at 2000 queries/s over two resident databases
+    (n = 220,000, d = 50 and n = 10^6, d = 128, uint8 mixtures), continuous
+    batching up to 128 queries, memory admission, p50/p99 latency."""
+    import numpy as np
+    import torch
+
+    from paper_1904_02033_b300 import inputs
+    from paper_1904_02033_b300 import sanns as S
+    from paper_1904_02033_b300.serve import GpuExecutor, Request, Scheduler, run_open_loop
+
+    W = SERVE
+    specs = {"A": (220_000, 50, 64), "B": (1_000_000, 128, 64)}
+    dbs, pools = {}, {}
+    for i, (name, (n, d, ncomp)) in enumerate(specs.items()):
+        ctx = S.sanns_ctx_create(8192, 3, 60, 0, d)
+        coords = inputs.mixture_coords_device(n, d, ncomp, 20.0, 100 + i)
+        db = S.sanns_encode_db(ctx, coords, inputs.permutation_device(n, 200 + i))
+        S.sanns_db_prepare_batched(ctx, db)
+        db.batched = True
+        dbs[name] = (ctx, db)
+        # a pool of client-encrypted queries, reused cyclically
+        npool = 64
+        q = inputs.mixture_coords_device(npool, d, ncomp, 20.0, 300 + i, means_seed=100 + i)
+        qids = torch.arange(npool, dtype=torch.int64).to(torch.uint64).cuda()
+        sk = S.sanns_keygen(ctx, 400 + i)
+        pools[name] = (S.sanns_encrypt_query(ctx, sk, q, 500 + i, qids), qids)
+    rnd = np.random.default_rng(W["seed"])
+    times = inputs.poisson_arrivals(W["rate"], W["duration"], W["seed"])
+    reqs = []
+    for rid, t in enumerate(times):
+        name = "A" if rnd.random() < 0.5 else "B"
+        ct, qids = pools[name]
+        k = rid % ct.shape[0]
+        reqs.append(Request(rid=rid, db=name, arrival=float(t),
+                            payload=(ct[k:k + 1], qids[k:k + 1])))
+    ex = GpuExecutor(dbs, slots=W["slots"], max_batch=W["max_batch"], batched_min=8)
+    free, _ = torch.cuda.mem_get_info()
+    sched = Scheduler(ex, max_batch=W["max_batch"], slots=W["slots"], mem_budget=int(free * 0.5))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    stats = run_open_loop(sched, reqs)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    # bit-exactness of a seeded sample: each result equals the query run alone
+    sample = rnd.choice(len(reqs), size=max(1, int(W["sample_frac"] * len(reqs))), replace=False)
+    exact = 0
+    for i in sample:
+        r = reqs[int(i)]
+        ctx, db = dbs[r.db]
+        o, sv = S.sanns_distances(ctx, db, r.payload[0], 5, r.payload[1])
+        exact += int(torch.equal(o, r.result[0]) and torch.equal(sv, r.result[1]))
+    pts = sum(specs[r.db][0] for r in reqs)
+    sizes = [n for _, n, _ in stats.batches]
+    return {
+        "workload": "serving: Poisson 2000 q/s for 3 s over two resident databases "
+                    "(n=220,000 d=50 and n=1,000,000 d=128), batches up to 128, 3 slots",
+        "queries": len(reqs), "wall_s": wall, "qps": len(reqs) / wall,
+        "qp_per_s": pts / wall,
+        "latency_ms": {"p50": stats.percentile(50) * 1e3, "p99": stats.percentile(99) * 1e3},
+        "batches": len(sizes), "mean_batch": float(np.mean(sizes)), "max_batch": int(max(sizes)),
+        "deferred_for_memory": stats.deferred,
+        "sample_bit_exact": f"{exact}/{len(sample)}",
+    }
+
+
 def _peaks_tensor():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -472,6 +614,9 @@ def main():
     ap.add_argument("--impl", default="sanns", choices=["sanns", "reference"])
     ap.add_argument("--quick-cpu", action="store_true", help="smaller CPU baseline sample")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched section")
+    ap.add_argument("--no-extra", action="store_true", help="skip the clustering and serving sections")
+    ap.add_argument("--only", choices=["cluster", "serving"], default=None,
+                    help="run only one of the extra sections")
     ap.add_argument("--quick-batched", action="store_true", help="batched section at n = 10^6")
     ap.add_argument("--only-batched", type=int, default=None, metavar="N_POINTS",
                     help="run only the batched section on N_POINTS points (profiling)")
@@ -487,7 +632,12 @@ def main():
         WORKLOAD["n_queries"] = args.queries
     if args.warmup < 3:
         args.warmup = 3
-    if args.only_batched:
+    if args.only:
+        import torch
+        torch.cuda.set_device(0)
+        fn = run_cluster_section if args.only == "cluster" else run_serving_section
+        print(json.dumps({args.only: fn()}), flush=True)
+    elif args.only_batched:
         import torch
         torch.cuda.set_device(0)
         print(json.dumps({"batched": run_batched_section(n_override=args.only_batched,

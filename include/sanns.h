@@ -106,6 +106,12 @@ int sanns_sk_export(const sanns_sk *sk, int8_t *s_any, uint64_t *s_hat_any, void
 int sanns_encode_db(sanns_ctx *ctx, const uint8_t *coords_dev, uint64_t n_points,
                     const uint32_t *perm_dev, uint64_t n, sanns_db **out, void *stream);
 void sanns_db_free(sanns_db *db);
+/* Sharding (one shard of a database per GPU): the database encodes positions
+ * pos0 .. pos0 + n - 1 of the whole permuted list (its perm argument being
+ * that slice), so the mask of its local position x is drawn at global
+ * position pos0 + x; outputs stay indexed locally.  pos0 must be a multiple
+ * of N (shards are whole blocks).  Default 0. */
+int sanns_db_set_position_base(sanns_db *db, uint64_t pos0);
 /* n and K = ceil(n / N) of an encoded database. */
 int sanns_db_info(const sanns_db *db, uint64_t *n, uint64_t *K);
 /* Copy blocks [k0, k1) of the encoded plaintexts, layout [k][L][d][N], and

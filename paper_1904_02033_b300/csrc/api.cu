@@ -243,6 +243,14 @@ void sanns_db_free(sanns_db* db) {
   delete db;
 }
 
+int sanns_db_set_position_base(sanns_db* db, uint64_t pos0) {
+  if (!db) return fail(SANNS_EINVAL, "db is NULL");
+  if (pos0 % db->ctx->P.N) return fail(SANNS_EINVAL, "the position base must be a multiple of N");
+  if (pos0 + db->K * db->ctx->P.N > (1ull << 34)) return fail(SANNS_EINVAL, "positions beyond 2^34");
+  db->pos0 = pos0;
+  return SANNS_OK;
+}
+
 int sanns_db_info(const sanns_db* db, uint64_t* n, uint64_t* K) {
   if (!db) return fail(SANNS_EINVAL, "db is NULL");
   if (n) *n = db->n;
@@ -308,7 +316,7 @@ int sanns_distances_finish(sanns_ctx* ctx, const sanns_db* db, uint32_t B, uint6
   if (rc) return rc;
   if (B == 0) return SANNS_OK;
   if (!qids || !ct_out || !srv_share) return fail(SANNS_EINVAL, "NULL buffer");
-  SANNS_CUDA(launch_intt_mask(ctx->P, ct_out, db->d_norms, B, db->K, db->n, mask_seed, qids,
+  SANNS_CUDA(launch_intt_mask(ctx->P, ct_out, db->d_norms, B, db->K, db->n, db->pos0, mask_seed, qids,
                               srv_share, as_stream(stream)));
   return SANNS_OK;
 }

@@ -28,6 +28,7 @@ struct sanns_sk {
 struct sanns_db {
   const sanns_ctx* ctx;
   uint64_t n, K;
+  uint64_t pos0;            // global position of local position 0 (shards), multiple of N
   uint64_t* d_pt;           // [K][L][d][N]
   uint32_t* d_norms;        // [K N]
   uint16_t* d_plimb;        // [L][N][K][8 dpad] bf16 digits (batched path), or NULL
@@ -80,7 +81,7 @@ cudaError_t launch_mac(const PrimeSet& P, const uint64_t* ct, const uint64_t* pt
                        uint32_t d, uint64_t K, uint64_t* out, int sms, int variant,
                        cudaStream_t st);
 cudaError_t launch_intt_mask(const PrimeSet& P, uint64_t* ct_out, const uint32_t* norms,
-                             uint32_t B, uint64_t K, uint64_t n, uint64_t mask_seed,
+                             uint32_t B, uint64_t K, uint64_t n, uint64_t pos0, uint64_t mask_seed,
                              const uint64_t* qids, uint32_t* srv_share, cudaStream_t st);
 int gather_threads(uint32_t N);
 cudaError_t launch_check_indices(const uint32_t* idx, uint64_t m, uint64_t bound, int* bad,

@@ -72,17 +72,18 @@ __global__ void norms_kernel(const uint8_t* __restrict__ coords, uint64_t n_poin
 }
 
 // The server's mask, drawn once per position: r = uniform mod t from ChaCha20
-// stream (mask_seed, 4, qid_b) at position pos; srv_share[b][pos] = (t - r)
-// mod t for pos < n.  One thread per four positions (one ChaCha20 block).
-__global__ void mask_share_kernel(PrimeSet P, uint32_t B, uint64_t n, uint64_t mask_seed,
-                                  const uint64_t* __restrict__ qids,
+// stream (mask_seed, 4, qid_b) at global position pos0 + pos; srv_share[b][pos]
+// = (t - r) mod t for pos < n.  One thread per four positions (one ChaCha20
+// block; pos0 is a multiple of N, hence of 4).
+__global__ void mask_share_kernel(PrimeSet P, uint32_t B, uint64_t n, uint64_t pos0,
+                                  uint64_t mask_seed, const uint64_t* __restrict__ qids,
                                   uint32_t* __restrict__ srv_share) {
   const uint64_t groups = (n + 3) / 4;
   const uint64_t gid = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
   if (gid >= (uint64_t)B * groups) return;
   const uint64_t b = gid / groups, u = gid % groups;
   uint32_t blk[16];
-  chacha20_block(mask_seed, kPurposeMask, qids[b], (uint32_t)u, blk);
+  chacha20_block(mask_seed, kPurposeMask, qids[b], (uint32_t)(pos0 / 4 + u), blk);
 #pragma unroll
   for (int v = 0; v < 4; ++v) {
     const uint64_t pos = 4 * u + v;
@@ -100,7 +101,7 @@ __global__ void mask_share_kernel(PrimeSet P, uint32_t B, uint64_t n, uint64_t m
 // mask_share_kernel; padding positions (pos >= n) draw it directly.
 __global__ void __launch_bounds__(256, 3) intt_mask_kernel(PrimeSet P, uint64_t* __restrict__ ct_out,
                                  const uint32_t* __restrict__ norms, uint64_t K, uint64_t n,
-                                 uint64_t mask_seed, const uint64_t* __restrict__ qids,
+                                 uint64_t pos0g, uint64_t mask_seed, const uint64_t* __restrict__ qids,
                                  const uint32_t* __restrict__ srv_share) {
   extern __shared__ uint64_t sa[];
   const uint32_t N = P.N, L = P.L;
@@ -146,7 +147,7 @@ __global__ void __launch_bounds__(256, 3) intt_mask_kernel(PrimeSet P, uint64_t*
           for (int v = 0; v < 4; ++v) r[v] = svv[v] == 0 ? 0 : t - svv[v];
         } else {
           uint32_t blk[16];
-          chacha20_block(mask_seed, kPurposeMask, qids[b], (uint32_t)(pos0 / 4), blk);
+          chacha20_block(mask_seed, kPurposeMask, qids[b], (uint32_t)((pos0g + pos0) / 4), blk);
 #pragma unroll
           for (int v = 0; v < 4; ++v) {
             uint64_t lo, hi;
@@ -200,13 +201,13 @@ cudaError_t launch_encode(const PrimeSet& P, const uint8_t* coords, uint64_t n_p
 }
 
 cudaError_t launch_intt_mask(const PrimeSet& P, uint64_t* ct_out, const uint32_t* norms,
-                             uint32_t B, uint64_t K, uint64_t n, uint64_t mask_seed,
+                             uint32_t B, uint64_t K, uint64_t n, uint64_t pos0, uint64_t mask_seed,
                              const uint64_t* qids, uint32_t* srv_share, cudaStream_t st) {
   const uint64_t polys = (uint64_t)B * K * 2 * P.L;
   if (polys == 0) return cudaSuccess;
   const uint64_t groups = (uint64_t)B * ((n + 3) / 4);
-  mask_share_kernel<<<(unsigned)((groups + 255) / 256), 256, 0, st>>>(P, B, n, mask_seed, qids,
-                                                                     srv_share);
+  mask_share_kernel<<<(unsigned)((groups + 255) / 256), 256, 0, st>>>(P, B, n, pos0, mask_seed,
+                                                                     qids, srv_share);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const size_t smem = sizeof(uint64_t) * ntt_smem_words(P.N);
@@ -217,7 +218,7 @@ cudaError_t launch_intt_mask(const PrimeSet& P, uint64_t* ct_out, const uint32_t
     if (e != cudaSuccess) return e;
     configured = true;
   }
-  intt_mask_kernel<<<(unsigned)polys, ntt_threads(P.N), smem, st>>>(P, ct_out, norms, K, n,
+  intt_mask_kernel<<<(unsigned)polys, ntt_threads(P.N), smem, st>>>(P, ct_out, norms, K, n, pos0,
                                                                     mask_seed, qids, srv_share);
   return cudaGetLastError();
 }

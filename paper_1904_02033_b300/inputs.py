@@ -151,3 +151,66 @@ def permutation_device(n: int, seed: int, device: str = "cuda"):
 
     g = torch.Generator(device=device).manual_seed(seed)
     return torch.randperm(n, generator=g, device=device, dtype=torch.int32).view(torch.uint32)
+
+
+def mixture_coords_device_weighted(n: int, d: int, n_comp: int, sigma: float, seed: int,
+                                   weights, means_seed: int | None = None, device: str = "cuda",
+                                   chunk: int = 1 << 22):
+    """mixture_coords_device with mixture weights (e.g. Zipf-skewed)."""
+    import torch
+
+    gm = torch.Generator(device="cpu").manual_seed(seed if means_seed is None else means_seed)
+    means = (torch.rand((n_comp, d), generator=gm, dtype=torch.float32) * 255.0).to(device)
+    w = torch.as_tensor(np.asarray(weights, dtype=np.float64), device=device)
+    g = torch.Generator(device=device).manual_seed(seed + 0x9E3779B9)
+    out = torch.empty((n, d), dtype=torch.uint8, device=device)
+    for s in range(0, n, chunk):
+        e = min(n, s + chunk)
+        comp = torch.multinomial(w, e - s, replacement=True, generator=g)
+        x = means[comp] + torch.randn((e - s, d), generator=g, device=device) * sigma
+        out[s:e] = x.round_().clamp_(0, 255).to(torch.uint8)
+    return out
+
+
+def lloyd_kmeans_device(x, k: int, iters: int, seed: int):
+    """Lloyd iterations on the GPU in fp32 (data preparation only): initial
+    centres = the first k points of a seeded permutation; returns quantised
+    centres (uint8 [k][d]) and the final assignment (int64 [n])."""
+    import torch
+
+    xf = x.float()
+    g = torch.Generator(device=x.device).manual_seed(seed)
+    init = torch.randperm(x.shape[0], generator=g, device=x.device)[:k]
+    c = xf[init].clone()
+    xn = (xf * xf).sum(1)
+
+    def assign(c):
+        cn = (c * c).sum(1)
+        out = torch.empty(x.shape[0], dtype=torch.int64, device=x.device)
+        for s in range(0, x.shape[0], 1 << 18):
+            e = min(x.shape[0], s + (1 << 18))
+            dist = xn[s:e, None] - 2.0 * (xf[s:e] @ c.T) + cn[None, :]
+            out[s:e] = dist.argmin(1)
+        return out
+
+    for _ in range(iters):
+        a = assign(c)
+        sums = torch.zeros_like(c).index_add_(0, a, xf)
+        cnt = torch.bincount(a, minlength=k).float()
+        nz = cnt > 0
+        c[nz] = sums[nz] / cnt[nz, None]
+    a = assign(c)
+    return c.round().clamp(0, 255).to(torch.uint8), a
+
+
+def probes_device(queries, centres, n_probe: int):
+    """Exact integer squared distances on the GPU; the n_probe nearest centres
+    per query, ties to the lower id (stable sort), nearest first."""
+    import torch
+
+    # integer inner products below 2^24 are exact in fp64
+    qi = queries.double()
+    ci = centres.double()
+    dist = ((qi * qi).sum(1)[:, None] - 2 * qi @ ci.T + (ci * ci).sum(1)[None, :]).round().long()
+    order = torch.sort(dist, dim=1, stable=True).indices[:, :n_probe]
+    return order.to(torch.int32)

@@ -42,6 +42,7 @@ _SIGS = {
     "sanns_encode_db": ([_VP, _VP, C.c_uint64, _VP, C.c_uint64, C.POINTER(_VP), _VP], C.c_int),
     "sanns_db_free": ([_VP], None),
     "sanns_db_info": ([_VP, _VP, _VP], C.c_int),
+    "sanns_db_set_position_base": ([_VP, C.c_uint64], C.c_int),
     "sanns_db_export": ([_VP, C.c_uint64, C.c_uint64, _VP, _VP, _VP], C.c_int),
     "sanns_encrypt_query": ([_VP, _VP, _VP, C.c_uint32, C.c_uint64, _VP, _VP, _VP], C.c_int),
     "sanns_distances": ([_VP, _VP, _VP, C.c_uint32, C.c_uint64, _VP, _VP, _VP, _VP], C.c_int),
@@ -411,3 +412,8 @@ def sanns_batched_set_waits(ctx: Context, tma_ns: int, mma_ns: int, producer_ns:
                             epilogue_ns: int, all_producers_poll: bool):
     _check(load().sanns_batched_set_waits(ctx.handle, tma_ns, mma_ns, producer_ns, epilogue_ns,
                                           1 if all_producers_poll else 0))
+
+
+def sanns_db_set_position_base(db: Database, pos0: int):
+    _check(load().sanns_db_set_position_base(db.handle, pos0))
+    db.pos0 = pos0
