@@ -383,7 +383,7 @@ def run_batched_section(quick: bool = False, n_override: int | None = None,
         "speedup_vs_plain": t_plain / t_batch,
         "ms_per_batch": t_batch, "ms_batched_mac": t_bmac, "ms_plain_for_B_queries": t_plain,
         "bit_identical_to_per_query_path": same,
-        "roofline": {"kernel": "batched_mac_kernel (tcgen05 kind::f16, bf16 digits)",
+        "roofline": {"kernel": "batched_mac_kernel (tcgen05 kind::f16, fp16 digits)",
                      "bound": "tensor", "achieved": flops / (t_bmac * 1e-3) / 1e12,
                      "peak": peak[0], "unit": "TFLOP/s",
                      "frac": flops / (t_bmac * 1e-3) / 1e12 / peak[0], "peak_source": peak[1],

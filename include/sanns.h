@@ -227,11 +227,11 @@ int sanns_autotune_mac(sanns_ctx *ctx, const sanns_db *db, const uint64_t *ct_in
 /*
  * Batched path on the tensor cores (no counterpart in the paper, which
  * evaluates one query at a time): for B queries the per-slot work is the
- * dense contraction (2B x d) . (d x K) mod q_j, run as an exact bf16 GEMM
+ * dense contraction (2B x d) . (d x K) mod q_j, run as an exact fp16 GEMM
  * over balanced base-256 digits with fp32 accumulation (all partial sums are
  * integers below 2^24 for d <= 128).
  *   sanns_db_prepare_batched  builds the digit layout of the database once
- *                             ([L][N][K][8 ceil(d/8)] bf16, twice the size of
+ *                             ([L][N][K][8 ceil(d/8)] fp16, twice the size of
  *                             the encoded database) and its TMA descriptor.
  *                             Requires d <= 128.  Synchronous.
  *   sanns_distances_batched   same arguments and bit-identical results as

@@ -31,7 +31,7 @@ struct sanns_db {
   uint64_t pos0;            // global position of local position 0 (shards), multiple of N
   uint64_t* d_pt;           // [K][L][d][N]
   uint32_t* d_norms;        // [K N]
-  uint16_t* d_plimb;        // [L][N][K][8 dpad] bf16 digits (batched path), or NULL
+  uint16_t* d_plimb;        // [L][N][K][8 dpad] fp16 digits (batched path), or NULL
   alignas(64) unsigned char limb_map[128];  // TMA descriptor of d_plimb
 };
 
