@@ -248,13 +248,17 @@ int sanns_distances_batched(sanns_ctx *ctx, const sanns_db *db, const uint64_t *
 int sanns_distances_batched_mac(sanns_ctx *ctx, const sanns_db *db, const uint64_t *ct_in_dev,
                                 uint32_t B, uint64_t *ct_out_dev, void *stream);
 int sanns_device_status(sanns_ctx *ctx, void *stream);
-/* Tuning of the batched kernel's waits: back-off sleep (ns) of the TMA
+/* Tuning of the batched kernel: back-off sleep (ns, <= 100000) of the TMA
  * thread, the MMA thread, the digit producers and the epilogue when their
- * barrier is not ready yet, and whether every producer polls its stage
- * (otherwise one polls and the others follow its result).  Results never
- * depend on these values. */
-int sanns_batched_set_waits(sanns_ctx *ctx, uint32_t tma_ns, uint32_t mma_ns, uint32_t producer_ns,
-                            uint32_t epilogue_ns, int all_producers_poll);
+ * barrier is not ready yet; how many of its own work units ahead each CTA
+ * prefetches the database-digit and query tiles into L2 (0 = no prefetch,
+ * <= 8; default 1); and the cap (MiB, default 4096) on the stream-ordered
+ * scratch that holds the query multiples of one range of slots (a smaller cap
+ * means more, shorter launches; at least one slot's worth is always used).
+ * Results never depend on these values.  Returns SANNS_EINVAL for
+ * out-of-range values. */
+int sanns_batched_tune(sanns_ctx *ctx, uint32_t tma_ns, uint32_t mma_ns, uint32_t producer_ns,
+                       uint32_t epilogue_ns, uint32_t prefetch_units, uint32_t scratch_mib);
 
 /*
  * Client decryption (Pi_ls step 4) plus its local term: per query b and

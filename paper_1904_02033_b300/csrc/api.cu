@@ -96,12 +96,17 @@ int sanns_ctx_create(const sanns_params* p, sanns_ctx** out) {
   c->batched_tune[1] = 0;
   c->batched_tune[2] = 32;
   c->batched_tune[3] = 128;
-  c->batched_tune[4] = 0;
+  c->batched_tune[4] = 1;
+  c->batched_tune[5] = 4096;
 
   const size_t per = (size_t)p->L * N;
   std::vector<uint64_t> fw(per), fws(per), iw(per), iws(per);
   for (uint32_t j = 0; j < p->L; ++j)
     fill_twiddles(N, q[j], psi[j], &fw[j * N], &fws[j * N], &iw[j * N], &iws[j * N]);
+  for (uint32_t j = 0; j < p->L; ++j) {
+    c->P.last_inv[j] = (uint64_t)(((unsigned __int128)iw[j * N + 1] * c->P.n_inv[j]) % q[j]);
+    c->P.last_inv_shoup[j] = shoup_of(c->P.last_inv[j], q[j]);
+  }
   // interleave {w, w_shoup}: forward table then inverse table, [L][N] pairs each
   std::vector<uint64_t> host(4 * per);
   for (size_t x = 0; x < per; ++x) {
@@ -317,7 +322,7 @@ int sanns_distances_finish(sanns_ctx* ctx, const sanns_db* db, uint32_t B, uint6
   if (B == 0) return SANNS_OK;
   if (!qids || !ct_out || !srv_share) return fail(SANNS_EINVAL, "NULL buffer");
   SANNS_CUDA(launch_intt_mask(ctx->P, ct_out, db->d_norms, B, db->K, db->n, db->pos0, mask_seed, qids,
-                              srv_share, as_stream(stream)));
+                              srv_share, ctx->sms, as_stream(stream)));
   return SANNS_OK;
 }
 
@@ -507,7 +512,7 @@ int sanns_distances_batched_mac(sanns_ctx* ctx, const sanns_db* db, const uint64
   if (!db->d_plimb) return fail(SANNS_EINVAL, "call sanns_db_prepare_batched first");
   if (!ct_in || !ct_out) return fail(SANNS_EINVAL, "NULL buffer");
   if (B > 4096) return fail(SANNS_EINVAL, "B must be <= 4096");
-  SANNS_CUDA(launch_batched_mac(ctx->P, db->limb_map, ct_in, B, ctx->params.d, db->K, ct_out, ctx->d_err,
+  SANNS_CUDA(launch_batched_mac(ctx->P, db->limb_map, db->d_plimb, ct_in, B, ctx->params.d, db->K, ct_out, ctx->d_err,
                                 ctx->sms, ctx->batched_tune, as_stream(stream)));
   return SANNS_OK;
 }
@@ -520,16 +525,19 @@ int sanns_distances_batched(sanns_ctx* ctx, const sanns_db* db, const uint64_t* 
   return sanns_distances_finish(ctx, db, B, mask_seed, qids, ct_out, srv_share, stream);
 }
 
-int sanns_batched_set_waits(sanns_ctx* ctx, uint32_t tma_ns, uint32_t mma_ns, uint32_t producer_ns,
-                            uint32_t epilogue_ns, int all_producers_poll) {
+int sanns_batched_tune(sanns_ctx* ctx, uint32_t tma_ns, uint32_t mma_ns, uint32_t producer_ns,
+                       uint32_t epilogue_ns, uint32_t prefetch_units, uint32_t scratch_mib) {
   if (!ctx) return fail(SANNS_EINVAL, "ctx is NULL");
   if (tma_ns > 100000 || mma_ns > 100000 || producer_ns > 100000 || epilogue_ns > 100000)
     return fail(SANNS_EINVAL, "back-off above 100 us");
+  if (prefetch_units > 8) return fail(SANNS_EINVAL, "prefetch distance above 8 units");
+  if (scratch_mib < 1 || scratch_mib > (1u << 20)) return fail(SANNS_EINVAL, "scratch cap outside 1 MiB .. 1 TiB");
   ctx->batched_tune[0] = tma_ns;
   ctx->batched_tune[1] = mma_ns;
   ctx->batched_tune[2] = producer_ns;
   ctx->batched_tune[3] = epilogue_ns;
-  ctx->batched_tune[4] = all_producers_poll ? 1 : 0;
+  ctx->batched_tune[4] = prefetch_units;
+  ctx->batched_tune[5] = scratch_mib;
   return SANNS_OK;
 }
 

@@ -19,13 +19,14 @@
 // TMEM lane holds the 8 digit sums S_0..S_7 of an output in 8 consecutive
 // columns and the epilogue needs no data exchange between lanes.
 //
-// One persistent CTA per SM, warp-specialised:
-//   warp 0      TMA producer: database digit tile (128 rows x 64 fp16) per stage
+// One persistent CTA per SM, warp-specialised (18 warps):
+//   warp 0      TMA producer: database digit tile (128 rows x 64 fp16) per
+//               stage, and an L2 prefetch of a later unit's tiles
 //   warp 1      TMEM owner and MMA issuer (one thread): 4 MMAs of
 //               M = 128, N = 256, K = 16 per stage
 //   warps 2-9   query-digit producers: 256 rows x 64 fp16 per stage, written
 //               into shared memory in the 128-byte swizzled layout
-//   warps 10-13 epilogue: TMEM -> registers, exact int64 combination of each
+//   warps 10-17 epilogue: TMEM -> registers, exact int64 combination of each
 //               output's 8 digit sums, one mod-q step, store acc[b][k][c][j][s]
 // Work unit = (prime, slot, 128-block K tile, 16-query Q tile), Q tile
 // fastest, so the CTAs running side by side share each database tile
@@ -57,7 +58,7 @@ constexpr int kProdWarp0 = 2;
 constexpr int kProdWarps = 8;
 constexpr int kProdThreads = 32 * kProdWarps;
 static_assert(kProdThreads == kQG * 8, "one (row group, dimension) item per producer thread");
-constexpr int kEpiWarp0 = kProdWarp0 + kProdWarps;   // 10
+constexpr int kEpiWarp0 = kProdWarp0 + kProdWarps;    // 10
 constexpr int kEpiWarps = 8;                          // two per TMEM lane quarter
 constexpr int kThreads = 32 * (kEpiWarp0 + kEpiWarps);  // 576
 constexpr unsigned long long kWaitCycles = 4ull << 30;  // ~2 s at 2 GHz
@@ -76,15 +77,21 @@ struct BatchArgs {
   uint64_t w32[kMaxPrimes];            // 2^32 mod q_j
   uint64_t w32_shoup[kMaxPrimes];
   uint64_t mu64[kMaxPrimes];           // floor(2^64 / q_j)
-  // wait back-off (ns) per role and whether every producer polls its stage
-  uint32_t sleep_tma, sleep_mma, sleep_prod, sleep_epi, all_poll;
+  // wait back-off (ns) per role; how many of its own units ahead a CTA
+  // prefetches the database and query tiles into L2 (0: none)
+  uint32_t sleep_tma, sleep_mma, sleep_prod, sleep_epi, prefetch_units;
+  const uint16_t* plimb;  // [L][N][K][8 dpad] database digits (prefetch addresses)
+  uint64_t lo_bias[kMaxPrimes];  // a multiple of q_j at or above 2^49
 };
 
-// |v| mod q for |v| < 2^63 with mu = floor(2^64 / q), returned as v mod q.
-__device__ __forceinline__ uint64_t signed_mod(int64_t v, uint64_t q, uint64_t mu) {
-  const uint64_t m = v >= 0 ? (uint64_t)v : (uint64_t)(-v);
-  const uint64_t r = mod_t64(m, q, mu);
-  return (v >= 0 || r == 0) ? r : q - r;
+// L2 prefetch of [p, p + bytes) in pieces of at most 32 KB (16-byte aligned
+// address and size).
+__device__ __forceinline__ void prefetch_l2(const void* p, uint32_t bytes) {
+  const char* c = static_cast<const char*>(p);
+  for (uint32_t off = 0; off < bytes; off += 32768) {
+    const uint32_t n = bytes - off < 32768 ? bytes - off : 32768;
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(c + off), "r"(n) : "memory");
+  }
 }
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -237,6 +244,19 @@ batched_mac_kernel(const __grid_constant__ CUtensorMap pmap, PrimeSet P, BatchAr
     bool ok = true;
     for (uint64_t u = blockIdx.x; u < A.units && ok; u += gridDim.x) {
       const Decoded D = decode_unit((uint32_t)u, P.logN, A);
+      const uint64_t pu = u + (uint64_t)A.prefetch_units * gridDim.x;
+      if (lane == 0 && A.prefetch_units && pu < A.units) {
+        // database tile (rows kt*128 .. of slot (j, s)) and query multiples
+        // (row groups qt*32 .. of slot (j, s')) of a later unit of this CTA
+        const Decoded F = decode_unit((uint32_t)pu, P.logN, A);
+        const uint32_t rows = A.K - F.kt * kBM < (uint32_t)kBM ? A.K - F.kt * kBM : (uint32_t)kBM;
+        prefetch_l2(A.plimb + (((uint64_t)F.j * N + F.s) * A.K + (uint64_t)F.kt * kBM) * 8 * A.dpad,
+                    rows * 16u * A.dpad);
+        const uint32_t twoB = 2 * A.B, bc0 = F.qt * kQG;
+        const uint32_t groups = twoB - bc0 < (uint32_t)kQG ? twoB - bc0 : (uint32_t)kQG;
+        prefetch_l2(A.xm + (((uint64_t)F.j * A.s_count + F.sl) * twoB + bc0) * A.dpad * 8,
+                    groups * 64u * A.dpad);
+      }
       for (uint32_t kc = 0; kc < A.chunks; ++kc, ++g) {
         const uint32_t st = (uint32_t)(g % kStages), ph = (uint32_t)((g / kStages) & 1);
         bool ready = true;
@@ -295,48 +315,55 @@ batched_mac_kernel(const __grid_constant__ CUtensorMap pmap, PrimeSet P, BatchAr
     }
   } else if (warp < kEpiWarp0) {
     // ---------------- query-digit producers ----------------
-    // The pre-kernel stored X_b = X 256^b mod q (b = 0..7) for every query
-    // value.  Balanced base-256 digits of X_b in [-128, 127]: the bytes of
-    // X_b + 0x8080808080808080 are exactly the digits plus 128 (X_b < 2^60).
+    // The pre-kernel stored, for every query value, Y_b = X 256^b mod q +
+    // 0x8080808080808080 (b = 0..7), whose bytes are the balanced base-256
+    // digits of X 256^b plus 128, with the bytes of Y_2m and Y_2m+1
+    // interleaved (byte 2a of pair m = byte a of Y_2m, byte 2a + 1 = byte a
+    // of Y_2m+1).  Row a of the tile takes bytes 2a, 2a + 1 of every pair: one
+    // byte permute puts them under the fp16 exponent of 1024 (0x64vv = 1024 +
+    // v, exact) and one f16x2 subtraction of 1152 leaves the digits.
     const uint32_t pt = threadIdx.x - 32 * kProdWarp0;   // one (b, c, dim) item per thread
     const uint32_t bcl = pt >> 3, il = pt & 7;             // (b, c) row group in tile, dim in chunk
     const uint32_t units = (uint32_t)A.units, chunks = A.chunks;
     const uint32_t twoB = 2 * A.B;
-    // address of this thread's 8 multiples in chunk kc of unit u (or null)
-    auto item_ptr = [&](uint32_t u, uint32_t kc) -> const ulonglong2* {
+    // this thread's 8 values of chunk 0 in unit u (null past the units or 2B)
+    auto unit_base = [&](uint32_t u) -> const ulonglong2* {
       if (u >= units) return nullptr;
       const Decoded D = decode_unit(u, P.logN, A);
-      const uint32_t bc = D.qt * kQG + bcl, i = kc * 8 + il;
-      if (bc >= twoB || i >= A.d) return nullptr;
+      const uint32_t bc = D.qt * kQG + bcl;
+      if (bc >= twoB) return nullptr;
       return reinterpret_cast<const ulonglong2*>(
-          A.xm + ((((uint64_t)D.j * A.s_count + D.sl) * twoB + bc) * A.dpad + i) * 8);
+          A.xm + ((((uint64_t)D.j * A.s_count + D.sl) * twoB + bc) * A.dpad + il) * 8);
+    };
+    // chunk k advances the dimension by 8: 8 items x 64 bytes; an item past d
+    // or past 2B holds Y_b = 0x80.. (all digits zero)
+    auto load_item = [&](const ulonglong2* b0, uint32_t k, ulonglong2 (&dst)[4]) {
+      const bool v = b0 != nullptr && k * 8 + il < A.d;
+#pragma unroll
+      for (int h = 0; h < 4; ++h)
+        dst[h] = v ? __ldg(b0 + 32 * k + h) : make_ulonglong2(0x8080808080808080ull, 0x8080808080808080ull);
     };
     // Each warp fills its own 32 items (4 row groups x 8 dims) of every stage
     // and arrives on the stage's barrier itself, so warps run ahead of one
     // another; values are prefetched two chunks ahead.
-    uint32_t cu = blockIdx.x, ck = 0;
-    auto next_pos = [&](uint32_t& u, uint32_t& k) {
-      if (++k == chunks) { k = 0; u += gridDim.x; }
-    };
-    auto load_item = [&](uint32_t u, uint32_t k, ulonglong2 (&dst)[4]) {
-      const ulonglong2* p = item_ptr(u, k);
-#pragma unroll
-      for (int h = 0; h < 4; ++h) dst[h] = p ? __ldg(p + h) : make_ulonglong2(0, 0);
+    uint32_t fu = blockIdx.x, fk = 0;
+    const ulonglong2* fb = unit_base(fu);
+    auto advance = [&]() {
+      if (++fk == chunks) { fk = 0; fu += gridDim.x; fb = unit_base(fu); }
     };
     ulonglong2 nx0[4], nx1[4];
-    uint32_t fu = cu, fk = ck;
-    load_item(fu, fk, nx0);
-    next_pos(fu, fk);
-    load_item(fu, fk, nx1);
-    next_pos(fu, fk);
+    load_item(fb, fk, nx0);
+    advance();
+    load_item(fb, fk, nx1);
+    advance();
     uint64_t g = 0;
-    bool ok = cu < units;
-    while (ok) {
+    uint32_t cu = blockIdx.x, ck = 0;
+    while (cu < units) {
       ulonglong2 cur[4];
 #pragma unroll
       for (int h = 0; h < 4; ++h) { cur[h] = nx0[h]; nx0[h] = nx1[h]; }
-      load_item(fu, fk, nx1);
-      next_pos(fu, fk);
+      load_item(fb, fk, nx1);
+      advance();
       const uint32_t st = (uint32_t)(g % kStages), ph = (uint32_t)((g / kStages) & 1);
       ++g;
       // lane 0 polls the stage, the warp follows its decision
@@ -344,28 +371,15 @@ batched_mac_kernel(const __grid_constant__ CUtensorMap pmap, PrimeSet P, BatchAr
       if (lane == 0) ready = mbar_wait(smem_u32(&bar_empty[st]), ph ^ 1, &abort_flag, A.err, A.sleep_prod);
       if (!__shfl_sync(0xffffffffu, (int)ready, 0)) break;
       uint8_t* at = base + st * kStageBytes + kATile;
-      uint32_t ylo[8], yhi[8];
-#pragma unroll
-      for (int h = 0; h < 4; ++h) {
-        const uint64_t y0 = cur[h].x + 0x8080808080808080ull;
-        const uint64_t y1 = cur[h].y + 0x8080808080808080ull;
-        ylo[2 * h] = (uint32_t)y0;
-        yhi[2 * h] = (uint32_t)(y0 >> 32);
-        ylo[2 * h + 1] = (uint32_t)y1;
-        yhi[2 * h + 1] = (uint32_t)(y1 >> 32);
-      }
-      // an item past d or past 2B reads X_b = 0, whose digits are all zero
 #pragma unroll
       for (int a = 0; a < 8; ++a) {
-        // byte a of the two words into the low bytes of two fp16 halves
-        const uint32_t sel = (uint32_t)(a & 3) | ((uint32_t)(4 + (a & 3)) << 8);
+        const uint32_t sel = (a & 1) ? 0x4342u : 0x4140u;
         uint32_t w[4];
 #pragma unroll
         for (int m = 0; m < 4; ++m) {
-          const uint32_t w0 = a < 4 ? ylo[2 * m] : yhi[2 * m];
-          const uint32_t w1 = a < 4 ? ylo[2 * m + 1] : yhi[2 * m + 1];
-          // fp16 1024 + v (0x6400 | v) minus 1152 = v - 128, exact
-          const uint32_t hv = (__byte_perm(w0, w1, sel) & 0x00FF00FFu) | 0x64006400u;
+          const uint64_t z = (a >> 1) < 2 ? cur[m].x : cur[m].y;
+          const uint32_t zw = ((a >> 1) & 1) ? (uint32_t)(z >> 32) : (uint32_t)z;
+          const uint32_t hv = __byte_perm(zw, 0x64646464u, sel);
           uint32_t h;
           asm("sub.rn.f16x2 %0, %1, %2;" : "=r"(h) : "r"(hv), "r"(0x64806480u));
           w[m] = h;
@@ -377,8 +391,7 @@ batched_mac_kernel(const __grid_constant__ CUtensorMap pmap, PrimeSet P, BatchAr
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       __syncwarp();
       if (lane == 0) mbar_arrive(smem_u32(&bar_full[st]));
-      next_pos(cu, ck);
-      if (cu >= units) ok = false;
+      if (++ck == chunks) { ck = 0; cu += gridDim.x; }
     }
   } else {
     // ---------------- epilogue ----------------
@@ -398,6 +411,7 @@ batched_mac_kernel(const __grid_constant__ CUtensorMap pmap, PrimeSet P, BatchAr
       tc_fence_after();
       const Decoded D = decode_unit((uint32_t)u, P.logN, A);
       const uint64_t q = P.q[D.j], mu = A.mu64[D.j];
+      const int64_t bias = (int64_t)A.lo_bias[D.j];
       const uint64_t w32 = A.w32[D.j], w32s = A.w32_shoup[D.j];
       const uint32_t k = D.kt * kBM + quarter * 32 + lane;
       const bool k_ok = k < A.K;
@@ -417,13 +431,17 @@ batched_mac_kernel(const __grid_constant__ CUtensorMap pmap, PrimeSet P, BatchAr
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
         for (int o = 0; o < 4; ++o) {
-          int64_t sa[8];
+          int32_t sa[8];
 #pragma unroll
           for (int a = 0; a < 8; ++a) sa[a] = __float2int_rn(__uint_as_float(v[o * 8 + a]));
-          const int64_t lo = sa[0] + (sa[1] << 8) + (sa[2] << 16) + (sa[3] << 24);
-          const int64_t hi = sa[4] + (sa[5] << 8) + (sa[6] << 16) + (sa[7] << 24);
-          const uint64_t res =
-              add_mod(signed_mod(lo, q, mu), mul_shoup(signed_mod(hi, q, mu), w32, w32s, q), q);
+          const int64_t lo = (int64_t)sa[0] + (int64_t)sa[1] * 256 + (int64_t)sa[2] * 65536 +
+                             (int64_t)sa[3] * 16777216;
+          const int64_t hi = (int64_t)sa[4] + (int64_t)sa[5] * 256 + (int64_t)sa[6] * 65536 +
+                             (int64_t)sa[7] * 16777216;
+          // |lo|, |hi| < 2^49 <= bias: both biased values are positive and
+          // below 2^50 + q; hi 2^32 lazily below 2q, the sum below 2^64
+          const uint64_t hs = mul_shoup_lazy((uint64_t)(hi + bias), w32, w32s, q);
+          const uint64_t res = mod_t64(hs + (uint64_t)(lo + bias), q, mu);
           const uint32_t bc = D.qt * kQG + cc * 4 + o;
           if (k_ok && bc < 2 * A.B) {
             const uint32_t b = bc >> 1, c = bc & 1;
@@ -477,7 +495,8 @@ __global__ void prepare_limbs_kernel(const uint64_t* __restrict__ pt, uint32_t K
 }
 
 // X_b = ct 256^b mod q for b = 0..7, for the slots [s_begin, s_begin + S):
-// xm[j][s'][bc][i][b], bc = 2 b_query + c.  One thread per (j, s', bc, i),
+// xm[j][s'][bc][i][8 words], bc = 2 b_query + c, stored as the biased and
+// pairwise byte-interleaved form the digit producers read.  One thread per (j, s', bc, i),
 // slot fastest so that the ciphertext reads coalesce.
 __global__ void expand_query_kernel(PrimeSet P, const uint64_t* __restrict__ ct, uint32_t B,
                                     uint32_t d, uint32_t dpad, uint32_t s_begin, uint32_t S,
@@ -504,7 +523,14 @@ __global__ void expand_query_kernel(PrimeSet P, const uint64_t* __restrict__ ct,
   ulonglong2* dst = reinterpret_cast<ulonglong2*>(
       xm + ((((uint64_t)j * S + sl) * 2 * B + bc) * dpad + i) * 8);
 #pragma unroll
-  for (int h = 0; h < 4; ++h) dst[h] = make_ulonglong2(v[2 * h], v[2 * h + 1]);
+  for (int m = 0; m < 4; ++m) {
+    // + 0x80 per byte (no carry out: X < 2^62), then bytes of the pair interleaved
+    const uint64_t y0 = v[2 * m] + 0x8080808080808080ull, y1 = v[2 * m + 1] + 0x8080808080808080ull;
+    const uint32_t l0 = (uint32_t)y0, h0 = (uint32_t)(y0 >> 32), l1 = (uint32_t)y1, h1 = (uint32_t)(y1 >> 32);
+    const uint64_t zx = (uint64_t)__byte_perm(l0, l1, 0x5140) | ((uint64_t)__byte_perm(l0, l1, 0x7362) << 32);
+    const uint64_t zy = (uint64_t)__byte_perm(h0, h1, 0x5140) | ((uint64_t)__byte_perm(h0, h1, 0x7362) << 32);
+    dst[m] = make_ulonglong2(zx, zy);
+  }
 }
 
 std::mutex g_encode_mu;
@@ -561,16 +587,18 @@ int make_limb_map(const PrimeSet& P, const uint16_t* plimb, uint64_t K, uint32_t
   return SANNS_OK;
 }
 
-cudaError_t launch_batched_mac(const PrimeSet& P, const void* map, const uint64_t* ct, uint32_t B,
+cudaError_t launch_batched_mac(const PrimeSet& P, const void* map, const uint16_t* plimb,
+                               const uint64_t* ct, uint32_t B,
                                uint32_t d, uint64_t K, uint64_t* out, int* err, int sms,
-                               const uint32_t tune[5], cudaStream_t st) {
+                               const uint32_t tune[6], cudaStream_t st) {
   BatchArgs A;
   memset(&A, 0, sizeof(A));
   A.sleep_tma = tune[0];
   A.sleep_mma = tune[1];
   A.sleep_prod = tune[2];
   A.sleep_epi = tune[3];
-  A.all_poll = tune[4];
+  A.prefetch_units = tune[4];
+  A.plimb = plimb;
   A.out = out;
   A.err = err;
   A.B = B;
@@ -594,10 +622,12 @@ cudaError_t launch_batched_mac(const PrimeSet& P, const void* map, const uint64_
     A.w32[j] = (uint64_t)(((u128)1 << 32) % P.q[j]);
     A.w32_shoup[j] = shoup_of(A.w32[j], P.q[j]);
     A.mu64[j] = (uint64_t)(((u128)1 << 64) / P.q[j]);
+    A.lo_bias[j] = ((1ull << 49) + P.q[j] - 1) / P.q[j] * P.q[j];
   }
-  // slot ranges bound the scratch of the query multiples to about 4 GiB
+  // slot ranges bound the scratch of the query multiples (tune[5] MiB, at
+  // least one slot)
   const uint64_t per_slot = (uint64_t)P.L * 2 * B * A.dpad * 8 * sizeof(uint64_t);
-  uint64_t S = (4ull << 30) / per_slot;
+  uint64_t S = ((uint64_t)tune[5] << 20) / per_slot;
   if (S < 1) S = 1;
   if (S > P.N) S = P.N;
   const size_t smem = (size_t)kStages * kStageBytes + 1024;

@@ -35,6 +35,8 @@ struct PrimeSet {
   uint64_t n_inv_shoup[kMaxPrimes];
   uint64_t crt_inv[kMaxPrimes];     // (Q / q_j)^-1 mod q_j
   uint64_t crt_inv_shoup[kMaxPrimes];
+  uint64_t last_inv[kMaxPrimes];    // psi^-brv(1) N^-1 mod q: last inverse stage with N^-1
+  uint64_t last_inv_shoup[kMaxPrimes];
   // twiddles, [L][N] pairs {w, Shoup companion}: psi^brv(m) and psi^-brv(m)
   const ulonglong2* tw;
   const ulonglong2* itw;
@@ -260,60 +262,64 @@ __device__ __forceinline__ void ntt_forward_smem(uint64_t* a, const PrimeSet& P,
   }
 }
 
+// One radix-16 pass of the inverse transform over the padded shared copy:
+// stages t, 2t, 4t, 8t with t = 2^lt; a thread owns the 16 elements x0 + k t
+// of one group; in stage s the lower element k of a pair uses twiddle
+// h_s + (g << (3 - s)) + (k >> (s + 1)), h_s = N / (2 t 2^s).
+__device__ __forceinline__ void inv_pass16(uint64_t* a, const ulonglong2* tw, uint32_t N,
+                                           uint32_t logN, uint32_t lt, uint64_t q, uint64_t q2) {
+  for (uint32_t th = threadIdx.x; th < N / 16; th += blockDim.x) {
+    const uint32_t g = th >> lt, b = th & ((1u << lt) - 1);
+    const uint32_t x0 = (g << (lt + 4)) + b;
+    uint64_t v[16];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) v[k] = a[SP(x0 + (k << lt))];
+#pragma unroll
+    for (int s = 0; s < 4; ++s) {
+      const int hk = 1 << s;
+      const uint32_t base = (1u << (logN - 1 - lt - s)) + (g << (3 - s));
+#pragma unroll
+      for (int k = 0; k < 16; ++k) {
+        if (k & hk) continue;
+        const ulonglong2 w = __ldg(tw + base + (k >> (s + 1)));
+        inv_bfly(v[k], v[k + hk], w.x, w.y, q, q2);
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < 16; ++k) a[SP(x0 + (k << lt))] = v[k];
+  }
+}
+
+// One radix-2 stage of the inverse transform, butterfly distance t = 2^lt.
+__device__ __forceinline__ void inv_pass2(uint64_t* a, const ulonglong2* tw, uint32_t N,
+                                          uint32_t logN, uint32_t lt, uint64_t q, uint64_t q2) {
+  const uint32_t t = 1u << lt, h = 1u << (logN - 1 - lt);
+  for (uint32_t bf = threadIdx.x; bf < N / 2; bf += blockDim.x) {
+    const uint32_t i = bf >> lt, x = (i << (lt + 1)) + (bf & (t - 1));
+    uint64_t X = a[SP(x)], Y = a[SP(x + t)];
+    const ulonglong2 w = __ldg(tw + h + i);
+    inv_bfly(X, Y, w.x, w.y, q, q2);
+    a[SP(x)] = X;
+    a[SP(x + t)] = Y;
+  }
+}
+
 __device__ __forceinline__ void ntt_inverse_smem(uint64_t* a, const PrimeSet& P, int j) {
   const uint32_t N = P.N, logN = P.logN;
   const uint64_t q = P.q[j], q2 = 2 * q;
   const ulonglong2* tw = P.itw + (size_t)j * N;
   const uint32_t passes = logN >> 2;
   const uint64_t ni = P.n_inv[j], nis = P.n_inv_shoup[j];
-  // radix-16 passes: stages t, 2t, 4t, 8t with t = 2^lt; a thread owns the 16
-  // elements x0 + k t of one group; in stage s the lower element k of a pair
-  // uses twiddle h_s + (g << (3 - s)) + (k >> (s + 1)), h_s = N / (2 t 2^s)
   uint32_t lt = 0;
   for (uint32_t ps = 0; ps < passes; ++ps, lt += 4) {
-    const uint32_t t = 1u << lt;
-    const bool last = (ps + 1 == passes) && (lt + 4 == logN);
-    for (uint32_t th = threadIdx.x; th < N / 16; th += blockDim.x) {
-      const uint32_t g = th >> lt, b = th & (t - 1);
-      const uint32_t x0 = (g << (lt + 4)) + b;
-      uint64_t v[16];
-#pragma unroll
-      for (int k = 0; k < 16; ++k) v[k] = a[SP(x0 + (k << lt))];
-#pragma unroll
-      for (int s = 0; s < 4; ++s) {
-        const int hk = 1 << s;
-        const uint32_t base = (1u << (logN - 1 - lt - s)) + (g << (3 - s));
-#pragma unroll
-        for (int k = 0; k < 16; ++k) {
-          if (k & hk) continue;
-          const ulonglong2 w = __ldg(tw + base + (k >> (s + 1)));
-          inv_bfly(v[k], v[k + hk], w.x, w.y, q, q2);
-        }
-      }
-      if (last) {
-#pragma unroll
-        for (int k = 0; k < 16; ++k) v[k] = mul_shoup(v[k], ni, nis, q);
-      }
-#pragma unroll
-      for (int k = 0; k < 16; ++k) a[SP(x0 + (k << lt))] = v[k];
-    }
+    inv_pass16(a, tw, N, logN, lt, q, q2);
     __syncthreads();
   }
-  if (lt < logN) {
-    for (; lt < logN; ++lt) {
-      const uint32_t t = 1u << lt, h = 1u << (logN - 1 - lt);
-      for (uint32_t bf = threadIdx.x; bf < N / 2; bf += blockDim.x) {
-        const uint32_t i = bf >> lt, x = (i << (lt + 1)) + (bf & (t - 1));
-        uint64_t X = a[SP(x)], Y = a[SP(x + t)];
-        const ulonglong2 w = __ldg(tw + h + i);
-        inv_bfly(X, Y, w.x, w.y, q, q2);
-        a[SP(x)] = X;
-        a[SP(x + t)] = Y;
-      }
-      __syncthreads();
-    }
-    for (uint32_t x = threadIdx.x; x < N; x += blockDim.x) a[SP(x)] = mul_shoup(a[SP(x)], ni, nis, q);
+  for (; lt < logN; ++lt) {
+    inv_pass2(a, tw, N, logN, lt, q, q2);
+    __syncthreads();
   }
+  for (uint32_t x = threadIdx.x; x < N; x += blockDim.x) a[SP(x)] = mul_shoup(a[SP(x)], ni, nis, q);
 }
 
 }  // namespace sanns

@@ -15,7 +15,8 @@ struct sanns_ctx {
   int sms;
   int mac_variant;          // launch variant of the MAC kernel (autotuned)
   int* d_err;               // device error word raised by bounded waits
-  uint32_t batched_tune[5]; // batched kernel: back-off ns (TMA, MMA, producers, epilogue), all-poll
+  uint32_t batched_tune[6]; // batched kernel: back-off ns (TMA, MMA, producers, epilogue), L2 prefetch
+                            // units, scratch cap (MiB) of the query multiples
 };
 
 struct sanns_sk {
@@ -82,7 +83,7 @@ cudaError_t launch_mac(const PrimeSet& P, const uint64_t* ct, const uint64_t* pt
                        cudaStream_t st);
 cudaError_t launch_intt_mask(const PrimeSet& P, uint64_t* ct_out, const uint32_t* norms,
                              uint32_t B, uint64_t K, uint64_t n, uint64_t pos0, uint64_t mask_seed,
-                             const uint64_t* qids, uint32_t* srv_share, cudaStream_t st);
+                             const uint64_t* qids, uint32_t* srv_share, int sms, cudaStream_t st);
 int gather_threads(uint32_t N);
 cudaError_t launch_check_indices(const uint32_t* idx, uint64_t m, uint64_t bound, int* bad,
                                  cudaStream_t st);
@@ -95,9 +96,10 @@ size_t batched_limb_bytes(uint32_t L, uint32_t N, uint64_t K, uint32_t d);
 cudaError_t launch_prepare_limbs(const PrimeSet& P, const uint64_t* pt, uint64_t K, uint32_t d,
                                  uint16_t* plimb, cudaStream_t st);
 int make_limb_map(const PrimeSet& P, const uint16_t* plimb, uint64_t K, uint32_t d, void* map_out);
-cudaError_t launch_batched_mac(const PrimeSet& P, const void* map, const uint64_t* ct, uint32_t B,
+cudaError_t launch_batched_mac(const PrimeSet& P, const void* map, const uint16_t* plimb,
+                               const uint64_t* ct, uint32_t B,
                                uint32_t d, uint64_t K, uint64_t* out, int* err, int sms,
-                               const uint32_t tune[5], cudaStream_t st);
+                               const uint32_t tune[6], cudaStream_t st);
 cudaError_t launch_decrypt(const PrimeSet& P, const uint64_t* ct_out, const int8_t* s,
                            const uint64_t* s_hat, const uint64_t* s_hat_shoup, uint32_t B,
                            uint64_t K, uint64_t n, const uint8_t* qv, uint32_t d,

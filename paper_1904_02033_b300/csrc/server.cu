@@ -95,11 +95,157 @@ __global__ void mask_share_kernel(PrimeSet P, uint32_t B, uint64_t n, uint64_t p
   }
 }
 
+// r of a padding position (global position gpos >= the database size), drawn
+// directly from the mask stream; kept out of line so that the unrolled
+// epilogue keeps its registers.
+__device__ __noinline__ uint64_t mask_draw(const PrimeSet P, uint64_t gpos, uint64_t mask_seed,
+                                           uint64_t qid) {
+  uint32_t blk[16];
+  chacha20_block(mask_seed, kPurposeMask, qid, (uint32_t)(gpos / 4), blk);
+  uint64_t lo, hi;
+  draw_pair(blk, (int)(gpos & 3), lo, hi);
+  return mod_t128(lo, hi, P);
+}
+
 // Epilogue of the distance step, one block per (b, k, c, j) polynomial of
-// ct_out (in place): INTT; for c = 0 add Delta_j ((||p||^2 + r) mod t) per
-// coefficient.  r is recovered from the server share written by
-// mask_share_kernel; padding positions (pos >= n) draw it directly.
+// ct_out (in place): the inverse NTT back to coefficient form and, for c = 0,
+// + Delta_j ((||p||^2 + r) mod t) per coefficient.  The first stage
+// (distance 1) runs while the polynomial is loaded, N^-1 is folded into the
+// last stage (psi^-brv(1) N^-1 on the difference side, one extra product on
+// the sum side), and the last radix-16 pass adds the mask in registers and
+// writes the result straight back to global memory.
 __global__ void __launch_bounds__(256, 3) intt_mask_kernel(PrimeSet P, uint64_t* __restrict__ ct_out,
+                                 const uint32_t* __restrict__ norms, uint64_t K, uint64_t n,
+                                 uint64_t pos0g, uint64_t mask_seed, const uint64_t* __restrict__ qids,
+                                 const uint32_t* __restrict__ srv_share) {
+  extern __shared__ uint64_t sa[];
+  const uint32_t N = P.N, L = P.L, logN = P.logN;
+  const uint64_t poly = blockIdx.x;                 // ((b K + k) 2 + c) L + j
+  const uint32_t j = (uint32_t)(poly % L);
+  const uint32_t c = (uint32_t)((poly / L) % 2);
+  const uint64_t bk = poly / (2 * L);
+  const uint64_t kb = bk % K, b = bk / K;
+  const uint64_t q = P.q[j], q2 = 2 * q;
+  const ulonglong2* itw = P.itw + (size_t)j * N;
+  uint64_t* g = ct_out + poly * N;
+  const uint32_t r2 = logN & 3;  // leading radix-2 stages
+  if (c == 0 && threadIdx.x == 0) {
+    // the mask inputs of this block are read only in the last pass: start
+    // pulling them into L2 now (16-byte aligned interior of each range)
+    auto prefetch = [](const void* p, uint64_t bytes) {
+      const uintptr_t a0 = (reinterpret_cast<uintptr_t>(p) + 15) & ~(uintptr_t)15;
+      const uintptr_t a1 = (reinterpret_cast<uintptr_t>(p) + bytes) & ~(uintptr_t)15;
+      for (uintptr_t a = a0; a + 16 <= a1; a += 32768) {
+        const uint32_t len = (uint32_t)(a1 - a < 32768 ? a1 - a : 32768);
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a), "r"(len) : "memory");
+      }
+    };
+    prefetch(norms + kb * N, 4ull * N);
+    if (kb * N < n) prefetch(srv_share + b * n + kb * N, 4ull * ((kb + 1) * N <= n ? N : n - kb * N));
+  }
+
+  // load; for r2 >= 1 the distance-1 stage (pair i = (2i, 2i + 1), twiddle
+  // N / 2 + i) on the fly, four pairs in flight per thread
+  {
+    const ulonglong2* g2 = reinterpret_cast<const ulonglong2*>(g);
+    for (uint32_t i0 = 0; i0 < N / 2; i0 += 4 * blockDim.x) {
+      ulonglong2 v[4], w[4];
+#pragma unroll
+      for (int z = 0; z < 4; ++z) {
+        const uint32_t i = i0 + z * blockDim.x + threadIdx.x;
+        v[z] = i < N / 2 ? __ldg(g2 + i) : make_ulonglong2(0, 0);
+        w[z] = (r2 && i < N / 2) ? __ldg(itw + N / 2 + i) : make_ulonglong2(0, 0);
+      }
+#pragma unroll
+      for (int z = 0; z < 4; ++z) {
+        const uint32_t i = i0 + z * blockDim.x + threadIdx.x;
+        if (i >= N / 2) continue;
+        uint64_t X = v[z].x, Y = v[z].y;
+        if (r2) inv_bfly(X, Y, w[z].x, w[z].y, q, q2);
+        sa[SP(2 * i)] = X;
+        sa[SP(2 * i + 1)] = Y;
+      }
+    }
+  }
+  __syncthreads();
+  uint32_t lt = r2 ? 1 : 0;
+  for (; lt < r2; ++lt) {
+    inv_pass2(sa, itw, N, logN, lt, q, q2);
+    __syncthreads();
+  }
+  for (; lt + 4 < logN; lt += 4) {
+    inv_pass16(sa, itw, N, logN, lt, q, q2);
+    __syncthreads();
+  }
+  // last radix-16 pass, lt = logN - 4: a thread owns x0 + k N/16, k = 0..15
+  const uint32_t t16 = N / 16;
+  const uint64_t ni = P.n_inv[j], nis = P.n_inv_shoup[j];
+  const uint64_t wl = P.last_inv[j], wls = P.last_inv_shoup[j];
+  const uint64_t dl = P.delta[j], dls = P.delta_shoup[j], t = P.t;
+  const uint32_t* sh = srv_share + b * n;
+  for (uint32_t x0 = threadIdx.x; x0 < t16; x0 += blockDim.x) {
+    uint64_t v[16];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) v[k] = sa[SP(x0 + k * t16)];
+#pragma unroll
+    for (int s = 0; s < 3; ++s) {
+      const int hk = 1 << s;
+      const uint32_t base = 1u << (3 - s);
+#pragma unroll
+      for (int k = 0; k < 16; ++k) {
+        if (k & hk) continue;
+        const ulonglong2 w = __ldg(itw + base + (k >> (s + 1)));
+        inv_bfly(v[k], v[k + hk], w.x, w.y, q, q2);
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const uint64_t S = csub(v[k] + v[k + 8], q2);
+      const uint64_t D = v[k] - v[k + 8] + q2;
+      v[k] = mul_shoup(S, ni, nis, q);
+      v[k + 8] = mul_shoup(D, wl, wls, q);
+    }
+    if (c == 0 && (kb + 1) * N <= n) {
+      // every position holds a server share
+#pragma unroll
+      for (int k = 0; k < 16; ++k) {
+        const uint64_t pos = kb * N + x0 + k * t16;
+        const uint32_t sv = sh[pos];
+        const uint64_t r = sv == 0 ? 0 : t - sv;
+        const uint64_t val = mod_t64((uint64_t)norms[pos] + r, t, P.t_barrett);
+        v[k] = add_mod(v[k], mul_shoup(val, dl, dls, q), q);
+      }
+    } else if (c == 0) {
+      // block with padding positions (the last one): element by element
+      // through this thread's own shared-memory slots
+#pragma unroll
+      for (int k = 0; k < 16; ++k) sa[SP(x0 + k * t16)] = v[k];
+      for (int k = 0; k < 16; ++k) {
+        const uint32_t x = x0 + k * t16;
+        const uint64_t pos = kb * N + x;
+        uint64_t r;
+        if (pos < n) {
+          const uint32_t sv = sh[pos];
+          r = sv == 0 ? 0 : t - sv;
+        } else {
+          r = mask_draw(P, pos0g + pos, mask_seed, qids[b]);
+        }
+        const uint64_t val = mod_t64((uint64_t)norms[pos] + r, t, P.t_barrett);
+        g[x] = add_mod(sa[SP(x)], mul_shoup(val, dl, dls, q), q);
+      }
+      continue;
+    }
+#pragma unroll
+    for (int k = 0; k < 16; ++k) g[x0 + k * t16] = v[k];
+  }
+}
+
+// The same epilogue as separate shared-memory passes (INTT, then the mask,
+// then the store), which finishes a polynomial sooner: used when the launch
+// is at most a couple of waves, where the latency of each block decides.
+// r is recovered from the server share written by mask_share_kernel; padding
+// positions (pos >= n) draw it directly.
+__global__ void __launch_bounds__(256, 3) intt_mask_short_kernel(PrimeSet P, uint64_t* __restrict__ ct_out,
                                  const uint32_t* __restrict__ norms, uint64_t K, uint64_t n,
                                  uint64_t pos0g, uint64_t mask_seed, const uint64_t* __restrict__ qids,
                                  const uint32_t* __restrict__ srv_share) {
@@ -202,7 +348,7 @@ cudaError_t launch_encode(const PrimeSet& P, const uint8_t* coords, uint64_t n_p
 
 cudaError_t launch_intt_mask(const PrimeSet& P, uint64_t* ct_out, const uint32_t* norms,
                              uint32_t B, uint64_t K, uint64_t n, uint64_t pos0, uint64_t mask_seed,
-                             const uint64_t* qids, uint32_t* srv_share, cudaStream_t st) {
+                             const uint64_t* qids, uint32_t* srv_share, int sms, cudaStream_t st) {
   const uint64_t polys = (uint64_t)B * K * 2 * P.L;
   if (polys == 0) return cudaSuccess;
   const uint64_t groups = (uint64_t)B * ((n + 3) / 4);
@@ -215,11 +361,20 @@ cudaError_t launch_intt_mask(const PrimeSet& P, uint64_t* ct_out, const uint32_t
   if (!configured) {
     e = cudaFuncSetAttribute(intt_mask_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)(sizeof(uint64_t) * ntt_smem_words(kMaxN)));
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(intt_mask_short_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)(sizeof(uint64_t) * ntt_smem_words(kMaxN)));
     if (e != cudaSuccess) return e;
     configured = true;
   }
-  intt_mask_kernel<<<(unsigned)polys, ntt_threads(P.N), smem, st>>>(P, ct_out, norms, K, n, pos0,
-                                                                    mask_seed, qids, srv_share);
+  // three blocks per SM; up to two waves the per-block latency decides, past
+  // that the throughput of the fused kernel
+  if (polys <= 2ull * 3 * (uint64_t)(sms > 0 ? sms : 148))
+    intt_mask_short_kernel<<<(unsigned)polys, ntt_threads(P.N), smem, st>>>(
+        P, ct_out, norms, K, n, pos0, mask_seed, qids, srv_share);
+  else
+    intt_mask_kernel<<<(unsigned)polys, ntt_threads(P.N), smem, st>>>(P, ct_out, norms, K, n, pos0,
+                                                                      mask_seed, qids, srv_share);
   return cudaGetLastError();
 }
 

@@ -66,8 +66,8 @@ _SIGS = {
                                 C.c_int),
     "sanns_distances_batched_mac": ([_VP, _VP, _VP, C.c_uint32, _VP, _VP], C.c_int),
     "sanns_device_status": ([_VP, _VP], C.c_int),
-    "sanns_batched_set_waits": ([_VP, C.c_uint32, C.c_uint32, C.c_uint32, C.c_uint32, C.c_int],
-                                C.c_int),
+    "sanns_batched_tune": ([_VP, C.c_uint32, C.c_uint32, C.c_uint32, C.c_uint32, C.c_uint32,
+                            C.c_uint32], C.c_int),
     "sanns_decrypt_shares": ([_VP, _VP, _VP, C.c_uint32, C.c_uint64, _VP, _VP, _VP], C.c_int),
 }
 
@@ -408,10 +408,10 @@ def sanns_device_status(ctx: Context, stream=None):
     _check(load().sanns_device_status(ctx.handle, _stream(stream)))
 
 
-def sanns_batched_set_waits(ctx: Context, tma_ns: int, mma_ns: int, producer_ns: int,
-                            epilogue_ns: int, all_producers_poll: bool):
-    _check(load().sanns_batched_set_waits(ctx.handle, tma_ns, mma_ns, producer_ns, epilogue_ns,
-                                          1 if all_producers_poll else 0))
+def sanns_batched_tune(ctx: Context, tma_ns: int = 0, mma_ns: int = 0, producer_ns: int = 32,
+                       epilogue_ns: int = 128, prefetch_units: int = 1, scratch_mib: int = 4096):
+    _check(load().sanns_batched_tune(ctx.handle, tma_ns, mma_ns, producer_ns, epilogue_ns,
+                                     prefetch_units, scratch_mib))
 
 
 def sanns_db_set_position_base(db: Database, pos0: int):

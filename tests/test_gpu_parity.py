@@ -145,6 +145,10 @@ def _pipeline(cfg, n, B, seed, perm=True):
     (CONFIGS[2], 700, 1),         # d = 17 (not a multiple of the 16-dim fold), t = 2^b_d
     (CONFIGS[3], 4096, 1),        # the one-block N = 4096 configuration
     (CONFIGS[4], 8192 * 3 - 5, 1),  # N = 8192, three 60-bit primes, ragged
+    # more than two waves of epilogue blocks (B K 2 L > 2 x 3 x SMs): the fused
+    # INTT + mask kernel, with the padding positions of the last block
+    (CONFIGS[1], 256 * 60 - 17, 8),
+    (CONFIGS[4], 8192 * 38 - 1000, 4),
 ])
 def test_distances_match_oracle_bit_exact(cfg, n, B):
     r = _pipeline(cfg, n, B, seed=n % 97)
