@@ -346,6 +346,8 @@ def run_batched_section(quick: bool = False, n_override: int | None = None,
     out_p = torch.empty((1, K, 2, L, N), dtype=torch.uint64, device="cuda")
     srv_p = torch.empty((1, n), dtype=torch.uint32, device="cuda")
     S.sanns_autotune_mac(ctx, db, ct[0:1], out_p, reps=2)
+    tuned, tune_ms = S.sanns_autotune_batched(ctx, db, ct, out_b, reps=1)
+    tile, prefetch = S.BATCHED_CONFIGS[tuned]
 
     def timed(fn, reps):
         fn()
@@ -383,6 +385,11 @@ def run_batched_section(quick: bool = False, n_override: int | None = None,
         "speedup_vs_plain": t_plain / t_batch,
         "ms_per_batch": t_batch, "ms_batched_mac": t_bmac, "ms_plain_for_B_queries": t_plain,
         "bit_identical_to_per_query_path": same,
+        "autotuned": {"tile": ["128 blocks x 256 query rows per SM",
+                               "256 blocks x 256 query rows per SM pair"][tile],
+                      "l2_prefetch_units": prefetch,
+                      "ms_per_config": {f"tile{t}_prefetch{p}": round(m, 3)
+                                        for (t, p), m in zip(S.BATCHED_CONFIGS, tune_ms)}},
         "roofline": {"kernel": "batched_mac_kernel (tcgen05 kind::f16, fp16 digits)",
                      "bound": "tensor", "achieved": flops / (t_bmac * 1e-3) / 1e12,
                      "peak": peak[0], "unit": "TFLOP/s",

@@ -252,13 +252,24 @@ int sanns_device_status(sanns_ctx *ctx, void *stream);
  * thread, the MMA thread, the digit producers and the epilogue when their
  * barrier is not ready yet; how many of its own work units ahead each CTA
  * prefetches the database-digit and query tiles into L2 (0 = no prefetch,
- * <= 8; default 1); and the cap (MiB, default 4096) on the stream-ordered
+ * <= 8; default 1); the cap (MiB, default 4096) on the stream-ordered
  * scratch that holds the query multiples of one range of slots (a smaller cap
- * means more, shorter launches; at least one slot's worth is always used).
+ * means more, shorter launches; at least one slot's worth is always used);
+ * and the tile shape: 0 (default) = 128 database blocks x 256 query rows per
+ * SM, 1 = 256 x 256 per pair of SMs (cluster of two CTAs sharing one MMA).
  * Results never depend on these values.  Returns SANNS_EINVAL for
  * out-of-range values. */
 int sanns_batched_tune(sanns_ctx *ctx, uint32_t tma_ns, uint32_t mma_ns, uint32_t producer_ns,
-                       uint32_t epilogue_ns, uint32_t prefetch_units, uint32_t scratch_mib);
+                       uint32_t epilogue_ns, uint32_t prefetch_units, uint32_t scratch_mib,
+                       uint32_t tile);
+/* Autotuner of the batched MAC: times the four configurations cfg = 2 tile +
+ * prefetch_units (tile 0 or 1, L2 prefetch 0 or 1 unit ahead) `reps` times
+ * each on the given inputs (writing ct_out_dev as sanns_distances_batched_mac
+ * would), keeps the fastest in the context and returns its index (>= 0) or an
+ * error code; ms_out (host, 4 floats, may be NULL) receives the mean time per
+ * launch.  Synchronous.  Every configuration computes identical results. */
+int sanns_autotune_batched(sanns_ctx *ctx, const sanns_db *db, const uint64_t *ct_in_dev, uint32_t B,
+                           uint64_t *ct_out_dev, int reps, float *ms_out, void *stream);
 
 /*
  * Client decryption (Pi_ls step 4) plus its local term: per query b and

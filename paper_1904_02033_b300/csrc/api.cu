@@ -98,6 +98,7 @@ int sanns_ctx_create(const sanns_params* p, sanns_ctx** out) {
   c->batched_tune[3] = 128;
   c->batched_tune[4] = 1;
   c->batched_tune[5] = 4096;
+  c->batched_tune[6] = 0;
 
   const size_t per = (size_t)p->L * N;
   std::vector<uint64_t> fw(per), fws(per), iw(per), iws(per);
@@ -526,19 +527,69 @@ int sanns_distances_batched(sanns_ctx* ctx, const sanns_db* db, const uint64_t* 
 }
 
 int sanns_batched_tune(sanns_ctx* ctx, uint32_t tma_ns, uint32_t mma_ns, uint32_t producer_ns,
-                       uint32_t epilogue_ns, uint32_t prefetch_units, uint32_t scratch_mib) {
+                       uint32_t epilogue_ns, uint32_t prefetch_units, uint32_t scratch_mib,
+                       uint32_t tile) {
   if (!ctx) return fail(SANNS_EINVAL, "ctx is NULL");
   if (tma_ns > 100000 || mma_ns > 100000 || producer_ns > 100000 || epilogue_ns > 100000)
     return fail(SANNS_EINVAL, "back-off above 100 us");
   if (prefetch_units > 8) return fail(SANNS_EINVAL, "prefetch distance above 8 units");
   if (scratch_mib < 1 || scratch_mib > (1u << 20)) return fail(SANNS_EINVAL, "scratch cap outside 1 MiB .. 1 TiB");
+  if (tile > 1) return fail(SANNS_EINVAL, "tile must be 0 (128 blocks, one SM) or 1 (256 blocks, SM pair)");
   ctx->batched_tune[0] = tma_ns;
   ctx->batched_tune[1] = mma_ns;
   ctx->batched_tune[2] = producer_ns;
   ctx->batched_tune[3] = epilogue_ns;
   ctx->batched_tune[4] = prefetch_units;
   ctx->batched_tune[5] = scratch_mib;
+  ctx->batched_tune[6] = tile;
   return SANNS_OK;
+}
+
+int sanns_autotune_batched(sanns_ctx* ctx, const sanns_db* db, const uint64_t* ct_in, uint32_t B,
+                           uint64_t* ct_out, int reps, float* ms_out, void* stream) {
+  int rc = check_distance_args(ctx, db, B);
+  if (rc) return rc;
+  if (B == 0 || !ct_in || !ct_out) return fail(SANNS_EINVAL, "NULL buffer or empty batch");
+  if (!db->d_plimb) return fail(SANNS_EINVAL, "call sanns_db_prepare_batched first");
+  if (B > 4096) return fail(SANNS_EINVAL, "B must be <= 4096");
+  if (reps < 1) reps = 1;
+  cudaStream_t st = as_stream(stream);
+  cudaEvent_t e0, e1;
+  SANNS_CUDA(cudaEventCreate(&e0));
+  SANNS_CUDA(cudaEventCreate(&e1));
+  const uint32_t saved[2] = {ctx->batched_tune[4], ctx->batched_tune[6]};
+  int best = -1;
+  float best_ms = 0.f;
+  for (int cfg = 0; cfg < kBatchedConfigs; ++cfg) {
+    ctx->batched_tune[6] = (uint32_t)(cfg >> 1);   // tile shape
+    ctx->batched_tune[4] = (uint32_t)(cfg & 1);    // L2 prefetch distance
+    auto launch = [&]() {
+      return launch_batched_mac(ctx->P, db->limb_map, db->d_plimb, ct_in, B, ctx->params.d, db->K, ct_out,
+                                ctx->d_err, ctx->sms, ctx->batched_tune, st);
+    };
+    cudaError_t e = launch();
+    if (e == cudaSuccess) e = cudaEventRecord(e0, st);
+    for (int r = 0; r < reps && e == cudaSuccess; ++r) e = launch();
+    if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (e != cudaSuccess) {
+      ctx->batched_tune[4] = saved[0];
+      ctx->batched_tune[6] = saved[1];
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      return cuda_fail(e, "batched autotune");
+    }
+    ms /= reps;
+    if (ms_out) ms_out[cfg] = ms;
+    if (best < 0 || ms < best_ms) { best = cfg; best_ms = ms; }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  ctx->batched_tune[6] = (uint32_t)(best >> 1);
+  ctx->batched_tune[4] = (uint32_t)(best & 1);
+  return best;
 }
 
 int sanns_device_status(sanns_ctx* ctx, void* stream) {

@@ -64,7 +64,7 @@ constexpr int kThreads = 32 * (kEpiWarp0 + kEpiWarps);  // 576
 constexpr unsigned long long kWaitCycles = 4ull << 30;  // ~2 s at 2 GHz
 
 struct BatchArgs {
-  const uint64_t* xm;     // [S][2B][dpad][8]: query values times 256^b mod q, slot range
+  const uint64_t* xm;     // query multiples of the slot range, layout of expand_query_kernel
   uint32_t s_begin, s_count;
   uint64_t* out;          // [B][K][2][L][N]
   int* err;               // device error word
@@ -202,6 +202,76 @@ __device__ __forceinline__ Decoded decode_unit(uint32_t u, uint32_t logN, const 
 }
 
 
+// Digit rows of one (b, c, dimension) item into a swizzled B stage: row
+// 8 bcl + a holds digit a of the item's eight multiples (columns 8 il .. 8 il
+// + 7 of the 64-column stage).  cur = the pre-kernel's biased, pairwise
+// byte-interleaved multiples (see expand_query_kernel).
+__device__ __forceinline__ void store_digit_rows(uint8_t* at, uint32_t bcl, uint32_t il,
+                                                 const ulonglong2 (&cur)[4]) {
+#pragma unroll
+  for (int a = 0; a < 8; ++a) {
+    const uint32_t sel = (a & 1) ? 0x4342u : 0x4140u;
+    uint32_t w[4];
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+      const uint64_t z = (a >> 1) < 2 ? cur[m].x : cur[m].y;
+      const uint32_t zw = ((a >> 1) & 1) ? (uint32_t)(z >> 32) : (uint32_t)z;
+      const uint32_t hv = __byte_perm(zw, 0x64646464u, sel);
+      uint32_t h;
+      asm("sub.rn.f16x2 %0, %1, %2;" : "=r"(h) : "r"(hv), "r"(0x64806480u));
+      w[m] = h;
+    }
+    const uint32_t row = bcl * 8 + a;
+    uint4* dst = reinterpret_cast<uint4*>(at + row * 128 + ((il ^ (row & 7)) << 4));
+    *dst = make_uint4(w[0], w[1], w[2], w[3]);
+  }
+}
+
+// One 32-column TMEM load of the epilogue: columns (bc, a) with a fastest hold
+// the 8 digit sums of 4 outputs.  Exact combination: lo = sum_{a<4} S_a 256^a
+// and hi = sum_{a>=4} S_a 256^(a-4) (both below 2^49 in magnitude), acc = lo +
+// hi 2^32 mod q; bc0 = the (b, c) row of the first of the 4 outputs.
+__device__ __forceinline__ void epilogue_chunk(uint32_t taddr, const BatchArgs& A, const PrimeSet& P,
+                                               const Decoded& D, uint32_t k, bool k_ok,
+                                               uint32_t bc0) {
+  uint32_t v[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, "
+      "%10, %11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, "
+      "%27, %28, %29, %30, %31}, [%32];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]),
+        "=r"(v[6]), "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]),
+        "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]),
+        "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
+        "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]),
+        "=r"(v[30]), "=r"(v[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+  const uint64_t q = P.q[D.j], mu = A.mu64[D.j];
+  const int64_t bias = (int64_t)A.lo_bias[D.j];
+  const uint64_t w32 = A.w32[D.j], w32s = A.w32_shoup[D.j];
+  const uint32_t N = P.N, L = P.L;
+#pragma unroll
+  for (int o = 0; o < 4; ++o) {
+    int32_t sa[8];
+#pragma unroll
+    for (int a = 0; a < 8; ++a) sa[a] = __float2int_rn(__uint_as_float(v[o * 8 + a]));
+    const int64_t lo = (int64_t)sa[0] + (int64_t)sa[1] * 256 + (int64_t)sa[2] * 65536 +
+                       (int64_t)sa[3] * 16777216;
+    const int64_t hi = (int64_t)sa[4] + (int64_t)sa[5] * 256 + (int64_t)sa[6] * 65536 +
+                       (int64_t)sa[7] * 16777216;
+    // |lo|, |hi| < 2^49 <= bias: both biased values are positive and below
+    // 2^50 + q; hi 2^32 lazily below 2q, the sum below 2^64
+    const uint64_t hs = mul_shoup_lazy((uint64_t)(hi + bias), w32, w32s, q);
+    const uint64_t res = mod_t64(hs + (uint64_t)(lo + bias), q, mu);
+    const uint32_t bc = bc0 + o;
+    if (k_ok && bc < 2 * A.B) {
+      const uint32_t b = bc >> 1, c = bc & 1;
+      A.out[((((uint64_t)b * A.K + k) * 2 + c) * L + D.j) * N + D.s] = res;
+    }
+  }
+}
+
 __global__ void __launch_bounds__(kThreads, 1)
 batched_mac_kernel(const __grid_constant__ CUtensorMap pmap, PrimeSet P, BatchArgs A) {
   extern __shared__ __align__(1024) uint8_t dsmem[];
@@ -235,7 +305,7 @@ batched_mac_kernel(const __grid_constant__ CUtensorMap pmap, PrimeSet P, BatchAr
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = tmem_base_slot;
-  const uint32_t N = P.N, L = P.L;
+  const uint32_t N = P.N;
 
   if (warp == 0) {
     // ---------------- TMA producer ----------------
@@ -326,22 +396,21 @@ batched_mac_kernel(const __grid_constant__ CUtensorMap pmap, PrimeSet P, BatchAr
     const uint32_t bcl = pt >> 3, il = pt & 7;             // (b, c) row group in tile, dim in chunk
     const uint32_t units = (uint32_t)A.units, chunks = A.chunks;
     const uint32_t twoB = 2 * A.B;
-    // this thread's 8 values of chunk 0 in unit u (null past the units or 2B)
+    // this thread's item in dimension block 0 of unit u (null past the units
+    // or past 2B: such an item reads Y_b = 0x80.., all digits zero)
     auto unit_base = [&](uint32_t u) -> const ulonglong2* {
       if (u >= units) return nullptr;
       const Decoded D = decode_unit(u, P.logN, A);
       const uint32_t bc = D.qt * kQG + bcl;
       if (bc >= twoB) return nullptr;
-      return reinterpret_cast<const ulonglong2*>(
-          A.xm + ((((uint64_t)D.j * A.s_count + D.sl) * twoB + bc) * A.dpad + il) * 8);
+      return reinterpret_cast<const ulonglong2*>(A.xm) +
+             (((uint64_t)D.j * A.s_count + D.sl) * twoB + bc) * (A.dpad / 8) * 32 + il;
     };
-    // chunk k advances the dimension by 8: 8 items x 64 bytes; an item past d
-    // or past 2B holds Y_b = 0x80.. (all digits zero)
+    // dimension block k: 32 sixteen-byte words further; pair m at + 8 m
     auto load_item = [&](const ulonglong2* b0, uint32_t k, ulonglong2 (&dst)[4]) {
-      const bool v = b0 != nullptr && k * 8 + il < A.d;
 #pragma unroll
       for (int h = 0; h < 4; ++h)
-        dst[h] = v ? __ldg(b0 + 32 * k + h) : make_ulonglong2(0x8080808080808080ull, 0x8080808080808080ull);
+        dst[h] = b0 ? __ldg(b0 + 32 * k + 8 * h) : make_ulonglong2(0x8080808080808080ull, 0x8080808080808080ull);
     };
     // Each warp fills its own 32 items (4 row groups x 8 dims) of every stage
     // and arrives on the stage's barrier itself, so warps run ahead of one
@@ -370,24 +439,7 @@ batched_mac_kernel(const __grid_constant__ CUtensorMap pmap, PrimeSet P, BatchAr
       bool ready = true;
       if (lane == 0) ready = mbar_wait(smem_u32(&bar_empty[st]), ph ^ 1, &abort_flag, A.err, A.sleep_prod);
       if (!__shfl_sync(0xffffffffu, (int)ready, 0)) break;
-      uint8_t* at = base + st * kStageBytes + kATile;
-#pragma unroll
-      for (int a = 0; a < 8; ++a) {
-        const uint32_t sel = (a & 1) ? 0x4342u : 0x4140u;
-        uint32_t w[4];
-#pragma unroll
-        for (int m = 0; m < 4; ++m) {
-          const uint64_t z = (a >> 1) < 2 ? cur[m].x : cur[m].y;
-          const uint32_t zw = ((a >> 1) & 1) ? (uint32_t)(z >> 32) : (uint32_t)z;
-          const uint32_t hv = __byte_perm(zw, 0x64646464u, sel);
-          uint32_t h;
-          asm("sub.rn.f16x2 %0, %1, %2;" : "=r"(h) : "r"(hv), "r"(0x64806480u));
-          w[m] = h;
-        }
-        const uint32_t row = bcl * 8 + a;
-        uint4* dst = reinterpret_cast<uint4*>(at + row * 128 + ((il ^ (row & 7)) << 4));
-        *dst = make_uint4(w[0], w[1], w[2], w[3]);
-      }
+      store_digit_rows(base + st * kStageBytes + kATile, bcl, il, cur);
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       __syncwarp();
       if (lane == 0) mbar_arrive(smem_u32(&bar_full[st]));
@@ -395,10 +447,7 @@ batched_mac_kernel(const __grid_constant__ CUtensorMap pmap, PrimeSet P, BatchAr
     }
   } else {
     // ---------------- epilogue ----------------
-    // Lane = database block k of the tile; columns (bc, a) with a fastest, so
-    // each x32 load holds the 8 digit sums of 4 outputs.  Exact combination:
-    // lo = sum_{a<4} S_a 256^a and hi = sum_{a>=4} S_a 256^(a-4) (both below
-    // 2^49 in magnitude), acc = lo + hi 2^32 mod q.
+    // Lane = database block k of the tile (see epilogue_chunk).
     const uint32_t quarter = warp & 3;            // TMEM lanes 32 quarter ..
     const uint32_t chalf = (warp - kEpiWarp0) >> 2;  // column half of the tile
     uint64_t r = 0;
@@ -410,45 +459,10 @@ batched_mac_kernel(const __grid_constant__ CUtensorMap pmap, PrimeSet P, BatchAr
       if (!__shfl_sync(0xffffffffu, (int)ready, 0)) break;
       tc_fence_after();
       const Decoded D = decode_unit((uint32_t)u, P.logN, A);
-      const uint64_t q = P.q[D.j], mu = A.mu64[D.j];
-      const int64_t bias = (int64_t)A.lo_bias[D.j];
-      const uint64_t w32 = A.w32[D.j], w32s = A.w32_shoup[D.j];
       const uint32_t k = D.kt * kBM + quarter * 32 + lane;
-      const bool k_ok = k < A.K;
-      for (uint32_t cc = chalf * (kBN / 64); cc < (chalf + 1) * (kBN / 64); ++cc) {
-        uint32_t v[32];
-        asm volatile(
-            "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, "
-            "%10, %11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, "
-            "%27, %28, %29, %30, %31}, [%32];"
-            : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]),
-              "=r"(v[6]), "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]),
-              "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]),
-              "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
-              "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]),
-              "=r"(v[30]), "=r"(v[31])
-            : "r"(tmem + ((quarter * 32) << 16) + slot * kBN + cc * 32));
-        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-        for (int o = 0; o < 4; ++o) {
-          int32_t sa[8];
-#pragma unroll
-          for (int a = 0; a < 8; ++a) sa[a] = __float2int_rn(__uint_as_float(v[o * 8 + a]));
-          const int64_t lo = (int64_t)sa[0] + (int64_t)sa[1] * 256 + (int64_t)sa[2] * 65536 +
-                             (int64_t)sa[3] * 16777216;
-          const int64_t hi = (int64_t)sa[4] + (int64_t)sa[5] * 256 + (int64_t)sa[6] * 65536 +
-                             (int64_t)sa[7] * 16777216;
-          // |lo|, |hi| < 2^49 <= bias: both biased values are positive and
-          // below 2^50 + q; hi 2^32 lazily below 2q, the sum below 2^64
-          const uint64_t hs = mul_shoup_lazy((uint64_t)(hi + bias), w32, w32s, q);
-          const uint64_t res = mod_t64(hs + (uint64_t)(lo + bias), q, mu);
-          const uint32_t bc = D.qt * kQG + cc * 4 + o;
-          if (k_ok && bc < 2 * A.B) {
-            const uint32_t b = bc >> 1, c = bc & 1;
-            A.out[((((uint64_t)b * A.K + k) * 2 + c) * L + D.j) * N + D.s] = res;
-          }
-        }
-      }
+      for (uint32_t cc = chalf * (kBN / 64); cc < (chalf + 1) * (kBN / 64); ++cc)
+        epilogue_chunk(tmem + ((quarter * 32) << 16) + slot * kBN + cc * 32, A, P, D, k, k < A.K,
+                       D.qt * kQG + cc * 4);
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(smem_u32(&bar_tempty[slot]));
@@ -460,6 +474,354 @@ batched_mac_kernel(const __grid_constant__ CUtensorMap pmap, PrimeSet P, BatchAr
   if (warp == 1) {
     tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem));
+  }
+}
+
+// ------------------------------------------------------------------------
+// The same contraction on CTA pairs (cluster of 2, tcgen05 cta_group::2): one
+// MMA of M = 256 (128 database blocks from each CTA's shared memory) by
+// N = 256 query rows (128 generated by each CTA) by K = 16.  Per SM this
+// halves the query-digit rows the producers write and the B operand the MMA
+// reads from shared memory, the resource the single-CTA tile is bound by.
+// The even CTA (rank 0) issues the MMAs and owns the stage-full and
+// accumulator-empty barriers; the odd CTA's TMA completes its bytes on them,
+// its producers and epilogue arrive remotely, and the MMA completion is
+// multicast to the stage-empty and accumulator-full barriers of both.
+// ------------------------------------------------------------------------
+namespace pair {
+constexpr int kStages = 6;
+constexpr int kXStages = 4;               // query-multiple tiles in flight (TMA)
+constexpr int kBM = 128;                  // database blocks per CTA (M = 256 per pair)
+constexpr int kBN = 256;                  // query rows per pair (N)
+constexpr int kBNh = 128;                 // query rows generated per CTA
+constexpr int kBK = 64;
+constexpr int kQG = kBN / 8;              // (b, c) row groups per pair tile
+constexpr int kQGh = kBNh / 8;            // per CTA
+constexpr int kATile = kBM * kBK * 2;     // 16 KB
+constexpr int kBTile = kBNh * kBK * 2;    // 16 KB
+constexpr int kStageBytes = kATile + kBTile;
+constexpr int kXTile = kQGh * 8 * 64;     // 16 row groups x 8 dimensions x 64 bytes = 8 KB
+constexpr int kSmem = kStages * kStageBytes + kXStages * kXTile + 1024;
+constexpr int kProdWarp0 = 2;
+constexpr int kProdWarps = 4;
+static_assert(32 * kProdWarps == kQGh * 8, "one (row group, dimension) item per producer thread");
+constexpr int kEpiWarp0 = kProdWarp0 + kProdWarps;    // 6
+constexpr int kEpiWarps = 8;
+constexpr int kThreads = 32 * (kEpiWarp0 + kEpiWarps);  // 448
+// kind::f16: D fp32, A and B fp16, both K-major, M = 256, N = 256.
+constexpr uint32_t kIdesc = (1u << 4) | ((uint32_t)(kBN >> 3) << 17) | ((uint32_t)(256 >> 4) << 24);
+}  // namespace pair
+
+__device__ __forceinline__ uint32_t cluster_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+
+// shared::cluster address of the same variable in CTA `rank` of the cluster
+__device__ __forceinline__ uint32_t map_rank(uint32_t addr, uint32_t rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(addr), "r"(rank));
+  return r;
+}
+
+__device__ __forceinline__ void cluster_sync_all() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\nbarrier.cluster.wait.acquire.aligned;" ::
+                   : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_cluster(uint32_t cluster_addr) {
+  asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(cluster_addr)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_cluster(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait (cluster-scope acquire), as mbar_wait.
+__device__ __forceinline__ bool mbar_wait_cl(uint32_t bar, uint32_t parity, volatile int* abort_flag,
+                                             int* err, uint32_t sleep_ns = 0) {
+  const unsigned long long t0 = clock64();
+  for (uint32_t it = 0;; ++it) {
+    if (mbar_try_cluster(bar, parity)) return true;
+    if (sleep_ns && it > 2) __nanosleep(sleep_ns);
+    if ((it & 255) == 255) {
+      if (*abort_flag) return false;
+      if (clock64() - t0 > kWaitCycles) {
+        *abort_flag = 1;
+        atomicExch(err, SANNS_ETIMEOUT);
+        return false;
+      }
+    }
+  }
+}
+
+// Tile load into this CTA's shared memory whose completion is counted on an
+// mbarrier of either CTA of the pair (cluster address).
+__device__ __forceinline__ void tma_load_3d_pair(uint32_t dst, const CUtensorMap* map, int x, int y,
+                                                 int z, uint32_t bar_cluster) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes.cta_group::2"
+      " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(bar_cluster)
+      : "memory");
+}
+
+__device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap* map, int x, int y, int z,
+                                            int w, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(w), "r"(bar)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_f16_pair(uint32_t dtmem, uint64_t adesc, uint64_t bdesc,
+                                             uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dtmem),
+      "l"(adesc), "l"(bdesc), "r"(pair::kIdesc), "r"(accumulate));
+}
+
+// completion of this thread's prior MMAs arrives on the barrier at the same
+// offset in every CTA of `mask`
+__device__ __forceinline__ void mma_commit_mc(uint32_t bar, uint16_t mask) {
+  asm volatile(
+      "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64"
+      " [%0], %1;" ::"r"(bar), "h"(mask)
+      : "memory");
+}
+
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(pair::kThreads, 1)
+batched_mac_pair_kernel(const __grid_constant__ CUtensorMap pmap, const __grid_constant__ CUtensorMap xmap,
+                        PrimeSet P, BatchArgs A) {
+  constexpr int kStages = pair::kStages;
+  constexpr int kXStages = pair::kXStages;
+  constexpr int kXTile = pair::kXTile;
+  constexpr int kBM = pair::kBM;
+  constexpr int kBN = pair::kBN;
+  constexpr int kBK = pair::kBK;
+  constexpr int kQG = pair::kQG;
+  constexpr int kQGh = pair::kQGh;
+  constexpr int kATile = pair::kATile;
+  constexpr int kStageBytes = pair::kStageBytes;
+  constexpr int kProdWarp0 = pair::kProdWarp0;
+  constexpr int kProdWarps = pair::kProdWarps;
+  constexpr int kEpiWarp0 = pair::kEpiWarp0;
+  constexpr int kEpiWarps = pair::kEpiWarps;
+  extern __shared__ __align__(1024) uint8_t dsmem[];
+  __shared__ __align__(8) uint64_t bar_full[kStages], bar_empty[kStages];
+  __shared__ __align__(8) uint64_t bar_tfull[2], bar_tempty[2], bar_done;
+  __shared__ __align__(8) uint64_t bar_xfull[kXStages], bar_xempty[kXStages];
+  __shared__ uint32_t tmem_base_slot;
+  __shared__ volatile int abort_flag;
+
+  const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t rank = cluster_rank();
+  const uint32_t cl = blockIdx.x >> 1, ncl = gridDim.x >> 1;
+  uint8_t* base = dsmem + ((1024 - (smem_u32(dsmem) & 1023)) & 1023);
+  const uint32_t sbase = smem_u32(base);
+  const uint32_t xbase = sbase + kStages * kStageBytes;  // query-multiple tiles
+
+  if (threadIdx.x == 0) {
+    abort_flag = 0;
+    for (int s = 0; s < kXStages; ++s) {
+      mbar_init(smem_u32(&bar_xfull[s]), 1);
+      mbar_init(smem_u32(&bar_xempty[s]), kProdWarps);
+    }
+    for (int s = 0; s < kStages; ++s) {
+      // leader: its TMA thread (expecting both CTAs' bytes) + both CTAs' producers
+      mbar_init(smem_u32(&bar_full[s]), 1 + 2 * kProdWarps);
+      mbar_init(smem_u32(&bar_empty[s]), 1);
+    }
+    for (int a = 0; a < 2; ++a) {
+      mbar_init(smem_u32(&bar_tfull[a]), 1);
+      mbar_init(smem_u32(&bar_tempty[a]), 2 * kEpiWarps);
+    }
+    mbar_init(smem_u32(&bar_done), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    // one warp of each CTA allocates the same columns in both
+    asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(
+                     smem_u32(&tmem_base_slot)));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;");
+  }
+  tc_fence_before();
+  __syncthreads();
+  cluster_sync_all();  // barriers of both CTAs initialised before any remote arrival
+  tc_fence_after();
+  const uint32_t tmem = tmem_base_slot;
+  const uint32_t N = P.N;
+
+  if (warp == 0) {
+    // ---------------- TMA producer (both CTAs) ----------------
+    uint64_t g = 0;
+    bool ok = true;
+    for (uint64_t u = cl; u < A.units && ok; u += ncl) {
+      const Decoded D = decode_unit((uint32_t)u, P.logN, A);
+      const uint64_t pu = u + (uint64_t)A.prefetch_units * ncl;
+      if (lane == 0 && A.prefetch_units && pu < A.units) {
+        const Decoded F = decode_unit((uint32_t)pu, P.logN, A);
+        const uint32_t r0 = F.kt * 2 * kBM + rank * kBM;
+        if (r0 < A.K) {
+          const uint32_t rows = A.K - r0 < (uint32_t)kBM ? A.K - r0 : (uint32_t)kBM;
+          prefetch_l2(A.plimb + (((uint64_t)F.j * N + F.s) * A.K + r0) * 8 * A.dpad,
+                      rows * 16u * A.dpad);
+        }
+        const uint32_t twoB = 2 * A.B, bc0 = F.qt * kQG + rank * kQGh;
+        if (bc0 < twoB) {
+          const uint32_t groups = twoB - bc0 < (uint32_t)kQGh ? twoB - bc0 : (uint32_t)kQGh;
+          prefetch_l2(A.xm + (((uint64_t)F.j * A.s_count + F.sl) * twoB + bc0) * A.dpad * 8,
+                      groups * 64u * A.dpad);
+        }
+      }
+      for (uint32_t kc = 0; kc < A.chunks; ++kc, ++g) {
+        const uint32_t st = (uint32_t)(g % kStages), ph = (uint32_t)((g / kStages) & 1);
+        const uint32_t xs = (uint32_t)(g % kXStages), xph = (uint32_t)((g / kXStages) & 1);
+        bool ready = true;
+        // this CTA's query multiples of the stage: 16 row groups x 8 dimensions
+        if (lane == 0) ready = mbar_wait_cl(smem_u32(&bar_xempty[xs]), xph ^ 1, &abort_flag, A.err, A.sleep_tma);
+        if (!__shfl_sync(0xffffffffu, (int)ready, 0)) { ok = false; break; }
+        if (lane == 0) {
+          const uint32_t xf = smem_u32(&bar_xfull[xs]);
+          mbar_arrive_tx(xf, kXTile);
+          tma_load_4d(xbase + xs * kXTile, &xmap, 0, (int)kc, (int)(D.qt * kQG + rank * kQGh),
+                      (int)(D.j * A.s_count + D.sl), xf);
+        }
+        __syncwarp();
+        if (lane == 0) ready = mbar_wait_cl(smem_u32(&bar_empty[st]), ph ^ 1, &abort_flag, A.err, A.sleep_tma);
+        if (!__shfl_sync(0xffffffffu, (int)ready, 0)) { ok = false; break; }
+        if (lane == 0) {
+          const uint32_t full = smem_u32(&bar_full[st]);
+          if (rank == 0) mbar_arrive_tx(full, 2 * kATile);
+          tma_load_3d_pair(sbase + st * kStageBytes, &pmap, (int)(kc * kBK),
+                           (int)(D.kt * 2 * kBM + rank * kBM), (int)(D.j * N + D.s),
+                           map_rank(full, 0));
+        }
+        __syncwarp();
+      }
+    }
+    if (!ok && lane == 0) {
+      // copies in flight complete on the leader's barriers: give them a
+      // bounded moment before the CTA may leave
+      const unsigned long long t0 = clock64();
+      while (clock64() - t0 < (1ull << 22)) {
+      }
+    }
+    __syncwarp();
+  } else if (warp == 1) {
+    // ---------------- MMA issuer (rank 0 only) ----------------
+    if (rank == 0) {
+      uint64_t g = 0, r = 0;
+      bool ok = true;
+      for (uint64_t u = cl; u < A.units && ok; u += ncl, ++r) {
+        const uint32_t slot = (uint32_t)(r & 1), aph = (uint32_t)((r >> 1) & 1);
+        bool ready = true;
+        if (lane == 0) ready = mbar_wait_cl(smem_u32(&bar_tempty[slot]), aph ^ 1, &abort_flag, A.err, A.sleep_mma);
+        if (!__shfl_sync(0xffffffffu, (int)ready, 0)) break;
+        tc_fence_after();
+        const uint32_t dt = tmem + slot * kBN;
+        for (uint32_t kc = 0; kc < A.chunks; ++kc, ++g) {
+          const uint32_t st = (uint32_t)(g % kStages), ph = (uint32_t)((g / kStages) & 1);
+          if (lane == 0) ready = mbar_wait_cl(smem_u32(&bar_full[st]), ph, &abort_flag, A.err, A.sleep_mma);
+          if (!__shfl_sync(0xffffffffu, (int)ready, 0)) { ok = false; break; }
+          tc_fence_after();
+          if (lane == 0) {
+            const uint32_t a_addr = sbase + st * kStageBytes, b_addr = a_addr + kATile;
+            const uint64_t ad = smem_desc(a_addr), bd = smem_desc(b_addr);
+#pragma unroll
+            for (int k = 0; k < kBK / 16; ++k)
+              mma_f16_pair(dt, ad + 2 * k, bd + 2 * k, (kc > 0 || k > 0) ? 1u : 0u);
+            mma_commit_mc(smem_u32(&bar_empty[st]), 0x3);
+          }
+          __syncwarp();
+        }
+        if (!ok) break;
+        if (lane == 0) mma_commit_mc(smem_u32(&bar_tfull[slot]), 0x3);
+        __syncwarp();
+      }
+      // every MMA issued has completed before the pair may tear down
+      if (lane == 0) {
+        mma_commit_mc(smem_u32(&bar_done), 0x1);
+        const unsigned long long t0 = clock64();
+        while (!mbar_try_cluster(smem_u32(&bar_done), 0) && clock64() - t0 < kWaitCycles) {
+        }
+      }
+      __syncwarp();
+    }
+  } else if (warp < kEpiWarp0) {
+    // ---------------- query-digit producers (both CTAs) ----------------
+    // this CTA's half of the tile's query rows: row groups rank 16 .. rank 16
+    // + 15; their multiples arrive by TMA (rows past 2B read as zero, whose
+    // digit columns are never stored)
+    const uint32_t pt = threadIdx.x - 32 * kProdWarp0;
+    const uint32_t bcl = pt >> 3, il = pt & 7;
+    const uint32_t units = (uint32_t)A.units, chunks = A.chunks;
+    uint64_t g = 0;
+    for (uint32_t cu = cl; cu < units; cu += ncl) {
+      bool ok = true;
+      for (uint32_t kc = 0; kc < chunks; ++kc, ++g) {
+        const uint32_t st = (uint32_t)(g % kStages), ph = (uint32_t)((g / kStages) & 1);
+        const uint32_t xs = (uint32_t)(g % kXStages), xph = (uint32_t)((g / kXStages) & 1);
+        bool ready = true;
+        if (lane == 0) ready = mbar_wait_cl(smem_u32(&bar_xfull[xs]), xph, &abort_flag, A.err, A.sleep_prod);
+        if (!__shfl_sync(0xffffffffu, (int)ready, 0)) { ok = false; break; }
+        // item (bcl, il): pair m at 16-byte word 32 bcl + 8 m + il (conflict-free)
+        const ulonglong2* xt = reinterpret_cast<const ulonglong2*>(base + kStages * kStageBytes + xs * kXTile);
+        ulonglong2 cur[4];
+#pragma unroll
+        for (int m = 0; m < 4; ++m) cur[m] = xt[32 * bcl + 8 * m + il];
+        __syncwarp();
+        if (lane == 0) mbar_arrive(smem_u32(&bar_xempty[xs]));
+        if (lane == 0) ready = mbar_wait_cl(smem_u32(&bar_empty[st]), ph ^ 1, &abort_flag, A.err, A.sleep_prod);
+        if (!__shfl_sync(0xffffffffu, (int)ready, 0)) { ok = false; break; }
+        store_digit_rows(base + st * kStageBytes + kATile, bcl, il, cur);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncwarp();
+        if (lane == 0) mbar_arrive_cluster(map_rank(smem_u32(&bar_full[st]), 0));
+      }
+      if (!ok) break;
+    }
+  } else {
+    // ---------------- epilogue (both CTAs) ----------------
+    // Lane = database block k (this CTA's 128 of the pair's 256); all 256
+    // query columns of the pair tile.
+    const uint32_t quarter = warp & 3;
+    const uint32_t chalf = (warp - kEpiWarp0) >> 2;
+    uint64_t r = 0;
+    for (uint64_t u = cl; u < A.units && !abort_flag; u += ncl, ++r) {
+      const uint32_t slot = (uint32_t)(r & 1), aph = (uint32_t)((r >> 1) & 1);
+      bool ready = true;
+      if (lane == 0) ready = mbar_wait_cl(smem_u32(&bar_tfull[slot]), aph, &abort_flag, A.err, A.sleep_epi);
+      if (!__shfl_sync(0xffffffffu, (int)ready, 0)) break;
+      tc_fence_after();
+      const Decoded D = decode_unit((uint32_t)u, P.logN, A);
+      const uint32_t k = D.kt * 2 * kBM + rank * kBM + quarter * 32 + lane;
+      for (uint32_t cc = chalf * (kBN / 64); cc < (chalf + 1) * (kBN / 64); ++cc)
+        epilogue_chunk(tmem + ((quarter * 32) << 16) + slot * kBN + cc * 32, A, P, D, k, k < A.K,
+                       D.qt * kQG + cc * 4);
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive_cluster(map_rank(smem_u32(&bar_tempty[slot]), 0));
+    }
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  cluster_sync_all();  // no CTA leaves while its peer may still reach its memory
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, 512;" ::"r"(tmem));
   }
 }
 
@@ -494,42 +856,55 @@ __global__ void prepare_limbs_kernel(const uint64_t* __restrict__ pt, uint32_t K
   }
 }
 
-// X_b = ct 256^b mod q for b = 0..7, for the slots [s_begin, s_begin + S):
-// xm[j][s'][bc][i][8 words], bc = 2 b_query + c, stored as the biased and
-// pairwise byte-interleaved form the digit producers read.  One thread per (j, s', bc, i),
-// slot fastest so that the ciphertext reads coalesce.
-__global__ void expand_query_kernel(PrimeSet P, const uint64_t* __restrict__ ct, uint32_t B,
-                                    uint32_t d, uint32_t dpad, uint32_t s_begin, uint32_t S,
+// X_b = ct 256^b mod q for b = 0..7, for the slots [s_begin, s_begin + S),
+// stored for the digit producers as Y_b = X_b + 0x8080808080808080 (whose
+// bytes are the balanced base-256 digits plus 128; no carry out, X_b < 2^62)
+// with the bytes of Y_2m and Y_2m+1 interleaved into one 16-byte word Z_m.
+// Layout, in 16-byte words: xm[j][s'][bc][i / 8][m][i % 8], bc = 2 b_query + c,
+// i < dpad (dimensions d .. dpad - 1 hold Y_b = 0x80.., all digits zero).  A
+// block takes (j, bc, 8 dimensions, 32 slots): coalesced ciphertext reads
+// along the slots, a shared-memory transpose, then 512 contiguous bytes per
+// slot.
+__global__ void __launch_bounds__(256) expand_query_kernel(PrimeSet P, const uint64_t* __restrict__ ct,
+                                    uint32_t B, uint32_t d, uint32_t dpad, uint32_t s_begin, uint32_t S,
                                     const uint64_t* __restrict__ w256,
                                     const uint64_t* __restrict__ w256s,
-                                    uint64_t* __restrict__ xm) {
-  const uint64_t gid = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
-  const uint64_t total = (uint64_t)P.L * S * 2 * B * d;
-  if (gid >= total) return;
-  const uint32_t sl = (uint32_t)(gid % S);
-  uint64_t r = gid / S;
-  const uint32_t i = (uint32_t)(r % d);
-  r /= d;
-  const uint32_t bc = (uint32_t)(r % (2 * B));
-  const uint32_t j = (uint32_t)(r / (2 * B));
+                                    ulonglong2* __restrict__ xm) {
+  __shared__ ulonglong2 tile[32][4][8];  // [slot][m][dim in block]
+  const uint32_t s0 = blockIdx.x * 32, ib = blockIdx.y;
+  const uint32_t j = blockIdx.z / (2 * B), bc = blockIdx.z % (2 * B);
   const uint32_t b = bc >> 1, c = bc & 1;
   const uint32_t N = P.N, L = P.L;
   const uint64_t q = P.q[j];
-  const uint64_t X = ct[((((uint64_t)b * d + i) * 2 + c) * L + j) * N + s_begin + sl];
-  uint64_t v[8];
-  v[0] = X;
+  {
+    const uint32_t il = threadIdx.x >> 5, sl = threadIdx.x & 31;
+    const uint32_t i = ib * 8 + il;
+    uint64_t v[8];
+    if (i < d && s0 + sl < S) {
+      const uint64_t X = ct[((((uint64_t)b * d + i) * 2 + c) * L + j) * N + s_begin + s0 + sl];
+      v[0] = X;
 #pragma unroll
-  for (int k = 1; k < 8; ++k) v[k] = mul_shoup(X, w256[j * 8 + k], w256s[j * 8 + k], q);
-  ulonglong2* dst = reinterpret_cast<ulonglong2*>(
-      xm + ((((uint64_t)j * S + sl) * 2 * B + bc) * dpad + i) * 8);
+      for (int k = 1; k < 8; ++k) v[k] = mul_shoup(X, w256[j * 8 + k], w256s[j * 8 + k], q);
+    } else {
 #pragma unroll
-  for (int m = 0; m < 4; ++m) {
-    // + 0x80 per byte (no carry out: X < 2^62), then bytes of the pair interleaved
-    const uint64_t y0 = v[2 * m] + 0x8080808080808080ull, y1 = v[2 * m + 1] + 0x8080808080808080ull;
-    const uint32_t l0 = (uint32_t)y0, h0 = (uint32_t)(y0 >> 32), l1 = (uint32_t)y1, h1 = (uint32_t)(y1 >> 32);
-    const uint64_t zx = (uint64_t)__byte_perm(l0, l1, 0x5140) | ((uint64_t)__byte_perm(l0, l1, 0x7362) << 32);
-    const uint64_t zy = (uint64_t)__byte_perm(h0, h1, 0x5140) | ((uint64_t)__byte_perm(h0, h1, 0x7362) << 32);
-    dst[m] = make_ulonglong2(zx, zy);
+      for (int k = 0; k < 8; ++k) v[k] = 0;
+    }
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+      const uint64_t y0 = v[2 * m] + 0x8080808080808080ull, y1 = v[2 * m + 1] + 0x8080808080808080ull;
+      const uint32_t l0 = (uint32_t)y0, h0 = (uint32_t)(y0 >> 32), l1 = (uint32_t)y1, h1 = (uint32_t)(y1 >> 32);
+      const uint64_t zx = (uint64_t)__byte_perm(l0, l1, 0x5140) | ((uint64_t)__byte_perm(l0, l1, 0x7362) << 32);
+      const uint64_t zy = (uint64_t)__byte_perm(h0, h1, 0x5140) | ((uint64_t)__byte_perm(h0, h1, 0x7362) << 32);
+      tile[sl][m][il] = make_ulonglong2(zx, zy);
+    }
+  }
+  __syncthreads();
+  // warp w writes slots w, w + 8, ..: 32 words = the slot's 512-byte block
+  const uint32_t w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (uint32_t sl = w; sl < 32; sl += 8) {
+    if (s0 + sl >= S) break;
+    xm[((((uint64_t)j * S + s0 + sl) * 2 * B + bc) * (dpad / 8) + ib) * 32 + lane] =
+        tile[sl][lane >> 3][lane & 7];
   }
 }
 
@@ -590,7 +965,7 @@ int make_limb_map(const PrimeSet& P, const uint16_t* plimb, uint64_t K, uint32_t
 cudaError_t launch_batched_mac(const PrimeSet& P, const void* map, const uint16_t* plimb,
                                const uint64_t* ct, uint32_t B,
                                uint32_t d, uint64_t K, uint64_t* out, int* err, int sms,
-                               const uint32_t tune[6], cudaStream_t st) {
+                               const uint32_t tune[7], cudaStream_t st) {
   BatchArgs A;
   memset(&A, 0, sizeof(A));
   A.sleep_tma = tune[0];
@@ -605,8 +980,9 @@ cudaError_t launch_batched_mac(const PrimeSet& P, const void* map, const uint16_
   A.d = d;
   A.dpad = (d + 7) / 8 * 8;
   A.K = (uint32_t)K;
+  const bool use_pair = tune[6] == 1;   // 256-block tiles on SM pairs
   A.QT = (2 * B + kQG - 1) / kQG;
-  A.KT = (uint32_t)((K + kBM - 1) / kBM);
+  A.KT = (uint32_t)(use_pair ? (K + 2 * pair::kBM - 1) / (2 * pair::kBM) : (K + kBM - 1) / kBM);
   A.chunks = A.dpad / 8;
   uint64_t hw[kMaxPrimes * 16];
   for (uint32_t j = 0; j < P.L; ++j) {
@@ -630,10 +1006,24 @@ cudaError_t launch_batched_mac(const PrimeSet& P, const void* map, const uint16_
   uint64_t S = ((uint64_t)tune[5] << 20) / per_slot;
   if (S < 1) S = 1;
   if (S > P.N) S = P.N;
-  const size_t smem = (size_t)kStages * kStageBytes + 1024;
-  cudaError_t e = cudaFuncSetAttribute(batched_mac_kernel,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const size_t smem = use_pair ? (size_t)pair::kSmem : (size_t)kStages * kStageBytes + 1024;
+  cudaError_t e = use_pair ? cudaFuncSetAttribute(batched_mac_pair_kernel,
+                                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
+                           : cudaFuncSetAttribute(batched_mac_kernel,
+                                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
+  // co-resident CTA pairs (clusters of 2 need two SMs of one GPC)
+  int pairs_resident = 0;
+  if (use_pair) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(2 * (unsigned)(sms > 0 ? sms / 2 : 74));
+    cfg.blockDim = dim3(pair::kThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    e = cudaOccupancyMaxActiveClusters(&pairs_resident, batched_mac_pair_kernel, &cfg);
+    if (e != cudaSuccess) return e;
+    if (pairs_resident < 1) return cudaErrorInvalidConfiguration;
+  }
   uint64_t* scratch = nullptr;
   e = cudaMallocAsync(&scratch, per_slot * S + sizeof(hw), st);
   if (e != cudaSuccess) return e;
@@ -648,14 +1038,36 @@ cudaError_t launch_batched_mac(const PrimeSet& P, const void* map, const uint16_
     A.xm = scratch;
     A.units = (uint64_t)P.L * cnt * A.KT * A.QT;
     if (A.units >= (1ull << 31)) { e = cudaErrorInvalidValue; break; }
-    const uint64_t threads = (uint64_t)P.L * cnt * 2 * B * d;
-    expand_query_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(
-        P, ct, B, d, A.dpad, (uint32_t)s0, cnt, dw, dw + kMaxPrimes * 8, scratch);
+    expand_query_kernel<<<dim3((cnt + 31) / 32, A.dpad / 8, P.L * 2 * B), 256, 0, st>>>(
+        P, ct, B, d, A.dpad, (uint32_t)s0, cnt, dw, dw + kMaxPrimes * 8,
+        reinterpret_cast<ulonglong2*>(scratch));
     e = cudaGetLastError();
     if (e != cudaSuccess) break;
-    uint64_t grid = (uint64_t)(sms > 0 ? sms : 148);
-    if (grid > A.units) grid = A.units;
-    batched_mac_kernel<<<(unsigned)grid, kThreads, smem, st>>>(m, P, A);
+    if (use_pair) {
+      // query multiples of this range as a tensor: [L S'][2B][dpad / 8][64 u64],
+      // boxes of 16 row groups x one 8-dimension block (8 KB)
+      CUtensorMap xmap;
+      {
+        PFN_cuTensorMapEncodeTiled_v12000 enc = nullptr;
+        e = get_encode(&enc);
+        if (e != cudaSuccess) break;
+        const cuuint64_t dims[4] = {64, A.dpad / 8, 2ull * B, (cuuint64_t)P.L * cnt};
+        const cuuint64_t strides[3] = {512, 64ull * A.dpad, 128ull * B * A.dpad};
+        const cuuint32_t box[4] = {64, 1, (cuuint32_t)pair::kQGh, 1};
+        const cuuint32_t estr[4] = {1, 1, 1, 1};
+        CUresult cr = enc(&xmap, CU_TENSOR_MAP_DATA_TYPE_UINT64, 4, scratch, dims, strides, box, estr,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (cr != CUDA_SUCCESS) { e = cudaErrorInvalidValue; break; }
+      }
+      uint64_t clusters = (uint64_t)pairs_resident;
+      if (clusters > A.units) clusters = A.units;
+      batched_mac_pair_kernel<<<(unsigned)(2 * clusters), pair::kThreads, smem, st>>>(m, xmap, P, A);
+    } else {
+      uint64_t grid = (uint64_t)(sms > 0 ? sms : 148);
+      if (grid > A.units) grid = A.units;
+      batched_mac_kernel<<<(unsigned)grid, kThreads, smem, st>>>(m, P, A);
+    }
     e = cudaGetLastError();
   }
   cudaError_t e2 = cudaFreeAsync(scratch, st);

@@ -55,6 +55,19 @@ __device__ __forceinline__ uint64_t mul_shoup_lazy(uint64_t y, uint64_t w, uint6
 
 __device__ __forceinline__ uint64_t csub(uint64_t x, uint64_t m) { return x >= m ? x - m : x; }
 
+// w * y mod q lazily in [0, 4q), for any y < 2^64, w < q < 2^61: the Shoup
+// quotient floor(y w_shoup / 2^64) is estimated from three of the four 32-bit
+// partial products (the dropped low terms add less than 3 to the exact
+// value), so the estimate is at most 2 below it and the remainder below 4q.
+__device__ __forceinline__ uint64_t mul_shoup_lazy4(uint64_t y, uint64_t w, uint64_t w_shoup,
+                                                    uint64_t q) {
+  const uint32_t y0 = (uint32_t)y, y1 = (uint32_t)(y >> 32);
+  const uint32_t s0 = (uint32_t)w_shoup, s1 = (uint32_t)(w_shoup >> 32);
+  uint64_t qt = (uint64_t)y1 * s1 + __umulhi(y0, s1);
+  qt += __umulhi(y1, s0);
+  return w * y - qt * q;
+}
+
 __device__ __forceinline__ uint64_t mul_shoup(uint64_t y, uint64_t w, uint64_t w_shoup,
                                               uint64_t q) {
   return csub(mul_shoup_lazy(y, w, w_shoup, q), q);
@@ -210,6 +223,23 @@ __device__ __forceinline__ void inv_bfly(uint64_t& X, uint64_t& Y, uint64_t w, u
   Y = mul_shoup_lazy(D, w, ws, q);
 }
 
+// The same butterfly on values kept below 4q (q < 2^61, so sums stay below
+// 2^64): bound = 4q.
+__device__ __forceinline__ void inv_bfly4(uint64_t& X, uint64_t& Y, uint64_t w, uint64_t ws,
+                                          uint64_t q, uint64_t q4) {
+  const uint64_t S = csub(X + Y, q4);
+  const uint64_t D = X - Y + q4;
+  X = S;
+  Y = mul_shoup_lazy4(D, w, ws, q);
+}
+
+template <bool LAZY4>
+__device__ __forceinline__ void inv_bfly_t(uint64_t& X, uint64_t& Y, uint64_t w, uint64_t ws,
+                                           uint64_t q, uint64_t bound) {
+  if (LAZY4) inv_bfly4(X, Y, w, ws, q, bound);
+  else inv_bfly(X, Y, w, ws, q, bound);
+}
+
 __device__ __forceinline__ void ntt_forward_smem(uint64_t* a, const PrimeSet& P, int j) {
   const uint32_t N = P.N, logN = P.logN;
   const uint64_t q = P.q[j], q2 = 2 * q;
@@ -266,6 +296,8 @@ __device__ __forceinline__ void ntt_forward_smem(uint64_t* a, const PrimeSet& P,
 // stages t, 2t, 4t, 8t with t = 2^lt; a thread owns the 16 elements x0 + k t
 // of one group; in stage s the lower element k of a pair uses twiddle
 // h_s + (g << (3 - s)) + (k >> (s + 1)), h_s = N / (2 t 2^s).
+// bound = 2q (values below 2q) or, with LAZY4, 4q (values below 4q).
+template <bool LAZY4 = false>
 __device__ __forceinline__ void inv_pass16(uint64_t* a, const ulonglong2* tw, uint32_t N,
                                            uint32_t logN, uint32_t lt, uint64_t q, uint64_t q2) {
   for (uint32_t th = threadIdx.x; th < N / 16; th += blockDim.x) {
@@ -282,7 +314,7 @@ __device__ __forceinline__ void inv_pass16(uint64_t* a, const ulonglong2* tw, ui
       for (int k = 0; k < 16; ++k) {
         if (k & hk) continue;
         const ulonglong2 w = __ldg(tw + base + (k >> (s + 1)));
-        inv_bfly(v[k], v[k + hk], w.x, w.y, q, q2);
+        inv_bfly_t<LAZY4>(v[k], v[k + hk], w.x, w.y, q, q2);
       }
     }
 #pragma unroll
@@ -291,6 +323,7 @@ __device__ __forceinline__ void inv_pass16(uint64_t* a, const ulonglong2* tw, ui
 }
 
 // One radix-2 stage of the inverse transform, butterfly distance t = 2^lt.
+template <bool LAZY4 = false>
 __device__ __forceinline__ void inv_pass2(uint64_t* a, const ulonglong2* tw, uint32_t N,
                                           uint32_t logN, uint32_t lt, uint64_t q, uint64_t q2) {
   const uint32_t t = 1u << lt, h = 1u << (logN - 1 - lt);
@@ -298,7 +331,7 @@ __device__ __forceinline__ void inv_pass2(uint64_t* a, const ulonglong2* tw, uin
     const uint32_t i = bf >> lt, x = (i << (lt + 1)) + (bf & (t - 1));
     uint64_t X = a[SP(x)], Y = a[SP(x + t)];
     const ulonglong2 w = __ldg(tw + h + i);
-    inv_bfly(X, Y, w.x, w.y, q, q2);
+    inv_bfly_t<LAZY4>(X, Y, w.x, w.y, q, q2);
     a[SP(x)] = X;
     a[SP(x + t)] = Y;
   }

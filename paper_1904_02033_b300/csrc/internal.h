@@ -15,8 +15,9 @@ struct sanns_ctx {
   int sms;
   int mac_variant;          // launch variant of the MAC kernel (autotuned)
   int* d_err;               // device error word raised by bounded waits
-  uint32_t batched_tune[6]; // batched kernel: back-off ns (TMA, MMA, producers, epilogue), L2 prefetch
-                            // units, scratch cap (MiB) of the query multiples
+  uint32_t batched_tune[7]; // batched kernel: back-off ns (TMA, MMA, producers, epilogue), L2 prefetch
+                            // units, scratch cap (MiB) of the query multiples, tile (0: 128 blocks
+                            // on one SM, 1: 256 blocks on an SM pair)
 };
 
 struct sanns_sk {
@@ -95,11 +96,12 @@ cudaError_t launch_gather(const PrimeSet& P, uint32_t d, const sanns_clusters* c
 size_t batched_limb_bytes(uint32_t L, uint32_t N, uint64_t K, uint32_t d);
 cudaError_t launch_prepare_limbs(const PrimeSet& P, const uint64_t* pt, uint64_t K, uint32_t d,
                                  uint16_t* plimb, cudaStream_t st);
+constexpr int kBatchedConfigs = 4;  // (tile shape, L2 prefetch) pairs timed by the autotuner
 int make_limb_map(const PrimeSet& P, const uint16_t* plimb, uint64_t K, uint32_t d, void* map_out);
 cudaError_t launch_batched_mac(const PrimeSet& P, const void* map, const uint16_t* plimb,
                                const uint64_t* ct, uint32_t B,
                                uint32_t d, uint64_t K, uint64_t* out, int* err, int sms,
-                               const uint32_t tune[6], cudaStream_t st);
+                               const uint32_t tune[7], cudaStream_t st);
 cudaError_t launch_decrypt(const PrimeSet& P, const uint64_t* ct_out, const int8_t* s,
                            const uint64_t* s_hat, const uint64_t* s_hat_shoup, uint32_t B,
                            uint64_t K, uint64_t n, const uint8_t* qv, uint32_t d,

@@ -125,7 +125,7 @@ __global__ void __launch_bounds__(256, 3) intt_mask_kernel(PrimeSet P, uint64_t*
   const uint32_t c = (uint32_t)((poly / L) % 2);
   const uint64_t bk = poly / (2 * L);
   const uint64_t kb = bk % K, b = bk / K;
-  const uint64_t q = P.q[j], q2 = 2 * q;
+  const uint64_t q = P.q[j], q2 = 2 * q, q4 = 4 * q;  // values stay below 4q
   const ulonglong2* itw = P.itw + (size_t)j * N;
   uint64_t* g = ct_out + poly * N;
   const uint32_t r2 = logN & 3;  // leading radix-2 stages
@@ -161,7 +161,7 @@ __global__ void __launch_bounds__(256, 3) intt_mask_kernel(PrimeSet P, uint64_t*
         const uint32_t i = i0 + z * blockDim.x + threadIdx.x;
         if (i >= N / 2) continue;
         uint64_t X = v[z].x, Y = v[z].y;
-        if (r2) inv_bfly(X, Y, w[z].x, w[z].y, q, q2);
+        if (r2) inv_bfly4(X, Y, w[z].x, w[z].y, q, q4);
         sa[SP(2 * i)] = X;
         sa[SP(2 * i + 1)] = Y;
       }
@@ -170,11 +170,11 @@ __global__ void __launch_bounds__(256, 3) intt_mask_kernel(PrimeSet P, uint64_t*
   __syncthreads();
   uint32_t lt = r2 ? 1 : 0;
   for (; lt < r2; ++lt) {
-    inv_pass2(sa, itw, N, logN, lt, q, q2);
+    inv_pass2<true>(sa, itw, N, logN, lt, q, q4);
     __syncthreads();
   }
   for (; lt + 4 < logN; lt += 4) {
-    inv_pass16(sa, itw, N, logN, lt, q, q2);
+    inv_pass16<true>(sa, itw, N, logN, lt, q, q4);
     __syncthreads();
   }
   // last radix-16 pass, lt = logN - 4: a thread owns x0 + k N/16, k = 0..15
@@ -195,15 +195,15 @@ __global__ void __launch_bounds__(256, 3) intt_mask_kernel(PrimeSet P, uint64_t*
       for (int k = 0; k < 16; ++k) {
         if (k & hk) continue;
         const ulonglong2 w = __ldg(itw + base + (k >> (s + 1)));
-        inv_bfly(v[k], v[k + hk], w.x, w.y, q, q2);
+        inv_bfly4(v[k], v[k + hk], w.x, w.y, q, q4);
       }
     }
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
-      const uint64_t S = csub(v[k] + v[k + 8], q2);
-      const uint64_t D = v[k] - v[k + 8] + q2;
-      v[k] = mul_shoup(S, ni, nis, q);
-      v[k + 8] = mul_shoup(D, wl, wls, q);
+      const uint64_t S = csub(v[k] + v[k + 8], q4);
+      const uint64_t D = v[k] - v[k + 8] + q4;
+      v[k] = csub(csub(mul_shoup_lazy4(S, ni, nis, q), q2), q);
+      v[k + 8] = csub(csub(mul_shoup_lazy4(D, wl, wls, q), q2), q);
     }
     if (c == 0 && (kb + 1) * N <= n) {
       // every position holds a server share

@@ -61,13 +61,14 @@ _SIGS = {
     "sanns_mac_variant_name": ([C.c_int], C.c_char_p),
     "sanns_set_mac_variant": ([_VP, C.c_int], C.c_int),
     "sanns_autotune_mac": ([_VP, _VP, _VP, C.c_uint32, _VP, C.c_int, _VP, _VP], C.c_int),
+    "sanns_autotune_batched": ([_VP, _VP, _VP, C.c_uint32, _VP, C.c_int, _VP, _VP], C.c_int),
     "sanns_db_prepare_batched": ([_VP, _VP, _VP], C.c_int),
     "sanns_distances_batched": ([_VP, _VP, _VP, C.c_uint32, C.c_uint64, _VP, _VP, _VP, _VP],
                                 C.c_int),
     "sanns_distances_batched_mac": ([_VP, _VP, _VP, C.c_uint32, _VP, _VP], C.c_int),
     "sanns_device_status": ([_VP, _VP], C.c_int),
     "sanns_batched_tune": ([_VP, C.c_uint32, C.c_uint32, C.c_uint32, C.c_uint32, C.c_uint32,
-                            C.c_uint32], C.c_int),
+                            C.c_uint32, C.c_uint32], C.c_int),
     "sanns_decrypt_shares": ([_VP, _VP, _VP, C.c_uint32, C.c_uint64, _VP, _VP, _VP], C.c_int),
 }
 
@@ -373,6 +374,22 @@ def sanns_autotune_mac(ctx: Context, db: Database, ct_in: torch.Tensor, ct_out: 
     return rc, list(ms)
 
 
+BATCHED_CONFIGS = [(tile, pf) for tile in (0, 1) for pf in (0, 1)]  # index = 2 tile + prefetch
+
+
+def sanns_autotune_batched(ctx: Context, db: Database, ct_in: torch.Tensor, ct_out: torch.Tensor,
+                           reps: int = 2, stream=None):
+    """Times the batched MAC's (tile shape, L2 prefetch) configurations, keeps
+    the fastest; returns (index into BATCHED_CONFIGS, ms list)."""
+    ms = (C.c_float * len(BATCHED_CONFIGS))()
+    B = ct_in.shape[0]
+    rc = load().sanns_autotune_batched(ctx.handle, db.handle, _ptr(ct_in), B, _ptr(ct_out), reps, ms,
+                                       _stream(stream))
+    if rc < 0:
+        _check(rc)
+    return rc, list(ms)
+
+
 def sanns_db_prepare_batched(ctx: Context, db: Database, stream=None):
     _check(load().sanns_db_prepare_batched(ctx.handle, db.handle, _stream(stream)))
 
@@ -409,9 +426,10 @@ def sanns_device_status(ctx: Context, stream=None):
 
 
 def sanns_batched_tune(ctx: Context, tma_ns: int = 0, mma_ns: int = 0, producer_ns: int = 32,
-                       epilogue_ns: int = 128, prefetch_units: int = 1, scratch_mib: int = 4096):
+                       epilogue_ns: int = 128, prefetch_units: int = 1, scratch_mib: int = 4096,
+                       tile: int = 0):
     _check(load().sanns_batched_tune(ctx.handle, tma_ns, mma_ns, producer_ns, epilogue_ns,
-                                     prefetch_units, scratch_mib))
+                                     prefetch_units, scratch_mib, tile))
 
 
 def sanns_db_set_position_base(db: Database, pos0: int):
