@@ -856,6 +856,13 @@ __global__ void prepare_limbs_kernel(const uint64_t* __restrict__ pt, uint32_t K
   }
 }
 
+// 256^b mod q_j and Shoup companions, passed by value (no host buffer to copy,
+// so a launch can be captured into a CUDA graph)
+struct W256 {
+  uint64_t w[kMaxPrimes][8];
+  uint64_t ws[kMaxPrimes][8];
+};
+
 // X_b = ct 256^b mod q for b = 0..7, for the slots [s_begin, s_begin + S),
 // stored for the digit producers as Y_b = X_b + 0x8080808080808080 (whose
 // bytes are the balanced base-256 digits plus 128; no carry out, X_b < 2^62)
@@ -867,8 +874,7 @@ __global__ void prepare_limbs_kernel(const uint64_t* __restrict__ pt, uint32_t K
 // slot.
 __global__ void __launch_bounds__(256) expand_query_kernel(PrimeSet P, const uint64_t* __restrict__ ct,
                                     uint32_t B, uint32_t d, uint32_t dpad, uint32_t s_begin, uint32_t S,
-                                    const uint64_t* __restrict__ w256,
-                                    const uint64_t* __restrict__ w256s,
+                                    const W256 W,
                                     ulonglong2* __restrict__ xm) {
   __shared__ ulonglong2 tile[32][4][8];  // [slot][m][dim in block]
   const uint32_t s0 = blockIdx.x * 32, ib = blockIdx.y;
@@ -884,7 +890,7 @@ __global__ void __launch_bounds__(256) expand_query_kernel(PrimeSet P, const uin
       const uint64_t X = ct[((((uint64_t)b * d + i) * 2 + c) * L + j) * N + s_begin + s0 + sl];
       v[0] = X;
 #pragma unroll
-      for (int k = 1; k < 8; ++k) v[k] = mul_shoup(X, w256[j * 8 + k], w256s[j * 8 + k], q);
+      for (int k = 1; k < 8; ++k) v[k] = mul_shoup(X, W.w[j][k], W.ws[j][k], q);
     } else {
 #pragma unroll
       for (int k = 0; k < 8; ++k) v[k] = 0;
@@ -984,14 +990,15 @@ cudaError_t launch_batched_mac(const PrimeSet& P, const void* map, const uint16_
   A.QT = (2 * B + kQG - 1) / kQG;
   A.KT = (uint32_t)(use_pair ? (K + 2 * pair::kBM - 1) / (2 * pair::kBM) : (K + kBM - 1) / kBM);
   A.chunks = A.dpad / 8;
-  uint64_t hw[kMaxPrimes * 16];
+  W256 W;
+  memset(&W, 0, sizeof(W));
   for (uint32_t j = 0; j < P.L; ++j) {
     uint64_t w = 1 % P.q[j];
     for (int a = 0; a < 8; ++a) {
       A.w256[j][a] = w;
       A.w256_shoup[j][a] = shoup_of(w, P.q[j]);
-      hw[j * 8 + a] = w;
-      hw[kMaxPrimes * 8 + j * 8 + a] = A.w256_shoup[j][a];
+      W.w[j][a] = w;
+      W.ws[j][a] = A.w256_shoup[j][a];
       w = (uint64_t)(((u128)w * 256) % P.q[j]);
     }
     A.r256_shoup[j] = shoup_of(256 % P.q[j], P.q[j]);
@@ -1007,28 +1014,39 @@ cudaError_t launch_batched_mac(const PrimeSet& P, const void* map, const uint16_
   if (S < 1) S = 1;
   if (S > P.N) S = P.N;
   const size_t smem = use_pair ? (size_t)pair::kSmem : (size_t)kStages * kStageBytes + 1024;
-  cudaError_t e = use_pair ? cudaFuncSetAttribute(batched_mac_pair_kernel,
-                                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
-                           : cudaFuncSetAttribute(batched_mac_kernel,
-                                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  // kernel attributes and the number of co-resident CTA pairs (clusters of 2
+  // need two SMs of one GPC) are set up once per device, outside any capture
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
-  // co-resident CTA pairs (clusters of 2 need two SMs of one GPC)
+  static std::mutex setup_mu;
+  static int pairs_resident_dev[64] = {};
+  static bool configured_dev[64] = {};
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
   int pairs_resident = 0;
-  if (use_pair) {
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(2 * (unsigned)(sms > 0 ? sms / 2 : 74));
-    cfg.blockDim = dim3(pair::kThreads);
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = st;
-    e = cudaOccupancyMaxActiveClusters(&pairs_resident, batched_mac_pair_kernel, &cfg);
-    if (e != cudaSuccess) return e;
-    if (pairs_resident < 1) return cudaErrorInvalidConfiguration;
+  {
+    std::lock_guard<std::mutex> lock(setup_mu);
+    if (!configured_dev[dev]) {
+      e = cudaFuncSetAttribute(batched_mac_pair_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)pair::kSmem);
+      if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(batched_mac_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)((size_t)kStages * kStageBytes + 1024));
+      if (e != cudaSuccess) return e;
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3(2 * (unsigned)(sms > 0 ? sms / 2 : 74));
+      cfg.blockDim = dim3(pair::kThreads);
+      cfg.dynamicSmemBytes = pair::kSmem;
+      e = cudaOccupancyMaxActiveClusters(&pairs_resident_dev[dev], batched_mac_pair_kernel, &cfg);
+      if (e != cudaSuccess) return e;
+      configured_dev[dev] = true;
+    }
+    pairs_resident = pairs_resident_dev[dev];
   }
+  if (use_pair && pairs_resident < 1) return cudaErrorInvalidConfiguration;
   uint64_t* scratch = nullptr;
-  e = cudaMallocAsync(&scratch, per_slot * S + sizeof(hw), st);
+  e = cudaMallocAsync(&scratch, per_slot * S, st);
   if (e != cudaSuccess) return e;
-  uint64_t* dw = scratch + per_slot * S / sizeof(uint64_t);
-  e = cudaMemcpyAsync(dw, hw, sizeof(hw), cudaMemcpyHostToDevice, st);
   CUtensorMap m;
   memcpy(&m, map, sizeof(m));
   for (uint64_t s0 = 0; s0 < P.N && e == cudaSuccess; s0 += S) {
@@ -1039,7 +1057,7 @@ cudaError_t launch_batched_mac(const PrimeSet& P, const void* map, const uint16_
     A.units = (uint64_t)P.L * cnt * A.KT * A.QT;
     if (A.units >= (1ull << 31)) { e = cudaErrorInvalidValue; break; }
     expand_query_kernel<<<dim3((cnt + 31) / 32, A.dpad / 8, P.L * 2 * B), 256, 0, st>>>(
-        P, ct, B, d, A.dpad, (uint32_t)s0, cnt, dw, dw + kMaxPrimes * 8,
+        P, ct, B, d, A.dpad, (uint32_t)s0, cnt, W,
         reinterpret_cast<ulonglong2*>(scratch));
     e = cudaGetLastError();
     if (e != cudaSuccess) break;

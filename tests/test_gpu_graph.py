@@ -1,0 +1,73 @@
+"""The distance step (per-query and batched paths) captured into a CUDA graph
+and replayed gives the same bits as the eager calls: every launch of the step
+goes to the caller's stream and its scratch is stream-ordered."""
+import numpy as np
+import pytest
+import torch
+
+from paper_1904_02033_b300 import inputs
+from paper_1904_02033_b300 import sanns as S
+
+pytestmark = pytest.mark.gpu
+
+
+def cu(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def _setup(cfg, n, B, seed):
+    ctx = S.sanns_ctx_create(*cfg)
+    d = cfg[4]
+    coords = inputs.uniform_coords(n, d, seed)
+    q = inputs.uniform_coords(B, d, seed + 1)
+    qids = cu(np.arange(40, 40 + B, dtype=np.uint64))
+    sk = S.sanns_keygen(ctx, seed + 2)
+    db = S.sanns_encode_db(ctx, cu(coords), cu(inputs.permutation(n, seed + 3)))
+    ct = S.sanns_encrypt_query(ctx, sk, cu(q), seed + 4, qids)
+    return ctx, db, ct, qids
+
+
+def _capture(fn):
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        fn()
+    torch.cuda.current_stream().wait_stream(side)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        fn()
+    return g
+
+
+@pytest.mark.parametrize("cfg,n,B", [((8192, 3, 60, 0, 16), 8192 * 3 - 11, 1),
+                                     ((256, 2, 40, 0, 9), 256 * 12 + 5, 3)])
+def test_per_query_step_replays_bit_exact(cfg, n, B):
+    ctx, db, ct, qids = _setup(cfg, n, B, 31)
+    ref_out, ref_srv = S.sanns_distances(ctx, db, ct, 8, qids)
+    out, srv = torch.empty_like(ref_out), torch.empty_like(ref_srv)
+    g = _capture(lambda: S.sanns_distances(ctx, db, ct, 8, qids, out, srv))
+    for _ in range(3):
+        out.zero_()
+        srv.zero_()
+        g.replay()
+        torch.cuda.synchronize()
+        assert torch.equal(out, ref_out) and torch.equal(srv, ref_srv)
+
+
+@pytest.mark.parametrize("tile", [0, 1])
+def test_batched_step_replays_bit_exact(tile):
+    cfg = (256, 2, 40, 0, 24)
+    ctx, db, ct, qids = _setup(cfg, 256 * 30 + 3, 6, 41)
+    S.sanns_db_prepare_batched(ctx, db)
+    S.sanns_batched_tune(ctx, tile=tile)
+    ref_out, ref_srv = S.sanns_distances(ctx, db, ct, 9, qids)
+    out, srv = torch.empty_like(ref_out), torch.empty_like(ref_srv)
+    g = _capture(lambda: S.sanns_distances_batched(ctx, db, ct, 9, qids, out, srv))
+    for _ in range(2):
+        out.zero_()
+        srv.zero_()
+        g.replay()
+        torch.cuda.synchronize()
+        S.sanns_device_status(ctx)
+        assert torch.equal(out, ref_out) and torch.equal(srv, ref_srv)
