@@ -272,6 +272,37 @@ int sanns_autotune_batched(sanns_ctx *ctx, const sanns_db *db, const uint64_t *c
                            uint64_t *ct_out_dev, int reps, float *ms_out, void *stream);
 
 /*
+ * Circuit privacy (Sec. 2, "Additive Homomorphic Encryption": the AHE scheme
+ * must not reveal the server's operations beyond the decrypted message; the
+ * paper obtains this by noise flooding, with 108 bits of statistical circuit
+ * privacy at its parameters, Sec. 7.1).  Private-key BFV leaves the server
+ * unable to re-randomise c1, so the client also publishes a public key and
+ * the server adds a fresh encryption of zero (pk0 u + e1, pk1 u + e2) to every
+ * response block, e1 being the flooding term, uniform in [-2^F, 2^F).
+ *   sanns_public_key      client: pk_dev (device, [2][L][N] u64, NTT form,
+ *                         caller-owned) = (-a s + e, a), a drawn in NTT form
+ *                         from stream (seed, 5, prime j), e centred binomial
+ *                         (eta = 21) from (seed, 6, 0).  Asynchronous on stream.
+ *   sanns_set_circuit_privacy  server: copies the key into the context (the
+ *                         caller's buffer may be freed afterwards) and sets F;
+ *                         every later sanns_distances / _finish /
+ *                         _batched on this context then adds, per query b and
+ *                         global position x (streams keyed by mask_seed and
+ *                         qids[b]): u ternary (purpose 7), pk * NTT(u) before
+ *                         the inverse transform; e1 = low F + 1 bits of two
+ *                         128-bit draws (purposes 9, 10) minus 2^F to c0 and
+ *                         e2 centred binomial (purpose 8) to c1 after it.
+ *                         pk_dev = NULL turns it off.  F above
+ *                         sanns_circuit_privacy_max_flood_bits (2^F <= Delta /
+ *                         4, so decryption stays correct) returns SANNS_EINVAL.
+ *                         Synchronous.  The gather path rejects calls while it
+ *                         is on.
+ */
+int sanns_public_key(sanns_ctx *ctx, const sanns_sk *sk, uint64_t seed, uint64_t *pk_dev, void *stream);
+int sanns_circuit_privacy_max_flood_bits(const sanns_ctx *ctx);
+int sanns_set_circuit_privacy(sanns_ctx *ctx, const uint64_t *pk_dev, uint32_t flood_bits, void *stream);
+
+/*
  * Client decryption (Pi_ls step 4) plus its local term: per query b and
  * position pos < n, m = round(t (c0 + c1 s mod Q) / Q) mod t (CRT over the L
  * primes), cli_share[b][pos] = (m + ||q_b||^2) mod t.  ct_out_dev

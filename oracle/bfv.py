@@ -43,6 +43,11 @@ def lib():
                                               C.c_void_p]
         _lib.oracle_negacyclic_schoolbook.argtypes = [C.c_void_p, C.c_void_p, C.c_uint32,
                                                       C.c_uint64, C.c_void_p]
+        _lib.oracle_public_key.argtypes = [C.c_void_p, C.c_void_p, C.c_uint64, C.c_void_p]
+        _lib.oracle_rerandomize.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_uint64,
+                                            C.c_uint64, C.c_uint64, C.c_uint64]
+        _lib.oracle_flood.argtypes = [C.c_void_p, C.c_void_p, C.c_uint64, C.c_uint64,
+                                      C.c_uint64, C.c_uint64, C.c_uint32]
     return _lib
 
 
@@ -148,13 +153,58 @@ class Oracle:
         return out, share
 
     def distances(self, ct: np.ndarray, coords: np.ndarray, perm, mask_seed: int, qid: int,
-                  k0: int = 0, k1: int | None = None):
-        """Pi_ls step 3 for blocks [k0, k1): encode, MAC, INTT, mask."""
+                  k0: int = 0, k1: int | None = None, pk: np.ndarray | None = None,
+                  flood_bits: int = 0):
+        """Pi_ls step 3 for blocks [k0, k1): encode, MAC, INTT, mask; with a
+        public key also the circuit-privacy terms (re-randomisation before the
+        INTT, flooding after it)."""
         n = coords.shape[0] if perm is None else len(perm)
         k1 = self.blocks(n) if k1 is None else k1
         pt, norms = self.encode_db(coords, perm, k0, k1)
         acc = self.mac(ct, pt)
-        return self.intt_mask(acc, norms, n, k0, k1, mask_seed, qid)
+        if pk is not None:
+            self.rerandomize(acc, pk, mask_seed, qid, k0)
+        out, share = self.intt_mask(acc, norms, n, k0, k1, mask_seed, qid)
+        if pk is not None:
+            self.flood(out, mask_seed, qid, k0, flood_bits)
+        return out, share
+
+    # ---------------- circuit privacy ----------------
+    def public_key(self, s_hat: np.ndarray, seed: int) -> np.ndarray:
+        pk = np.zeros((2, self.L, self.N), dtype=np.uint64)
+        lib().oracle_public_key(C.byref(self._c), _p(np.ascontiguousarray(s_hat)), seed, _p(pk))
+        return pk
+
+    def rerandomize(self, acc: np.ndarray, pk: np.ndarray, seed: int, qid: int, k0: int):
+        """In place: acc[k] (NTT form) += pk * NTT(u) for blocks k0, k0 + 1, .."""
+        assert acc.flags["C_CONTIGUOUS"]
+        lib().oracle_rerandomize(C.byref(self._c), _p(acc), _p(np.ascontiguousarray(pk)), seed,
+                                 qid, k0, acc.shape[0])
+
+    def flood(self, out: np.ndarray, seed: int, qid: int, k0: int, flood_bits: int):
+        """In place: c0 += e1 (uniform in [-2^F, 2^F)), c1 += e2 (CBD 21)."""
+        assert out.flags["C_CONTIGUOUS"] and 0 <= flood_bits <= 255
+        lib().oracle_flood(C.byref(self._c), _p(out), seed, qid, k0, out.shape[0], flood_bits)
+
+    def max_flood_bits(self) -> int:
+        """Largest F with 2^F + (structured noise) < Delta / 2 for every
+        decryptable response: F <= floor(log2 Delta) - 2."""
+        return self.P.delta.bit_length() - 3
+
+    def phase_noise(self, ct_out: np.ndarray, s: np.ndarray, m: np.ndarray) -> list:
+        """Exact |c0 + c1 s - Delta m| (centred mod Q) of every coefficient."""
+        P = self.P
+        Q = P.Q
+        v = self.decrypt_phase(ct_out, s)
+        coef = [(Q // qj) * pow(Q // qj, -1, qj) % Q for qj in P.q]
+        out = []
+        for k in range(v.shape[0]):
+            cols = [v[k, j].tolist() for j in range(self.L)]
+            for x in range(self.N):
+                w = sum(int(cols[j][x]) * coef[j] for j in range(self.L)) % Q
+                e = (w - P.delta * int(m[k * self.N + x])) % Q
+                out.append(min(e, Q - e))
+        return out
 
     def decrypt_phase(self, ct_out: np.ndarray, s: np.ndarray) -> np.ndarray:
         nk = ct_out.shape[0]

@@ -189,7 +189,10 @@ void oracle_chacha20_block(const uint32_t key[8], uint32_t counter,
  * four words 4 (c mod 4) .. 4 (c mod 4) + 3 of that block, read as
  * lo = w0 | w1 << 32, hi = w2 | w3 << 32.
  */
-enum { PURPOSE_SK = 1, PURPOSE_A = 2, PURPOSE_E = 3, PURPOSE_MASK = 4 };
+enum { PURPOSE_SK = 1, PURPOSE_A = 2, PURPOSE_E = 3, PURPOSE_MASK = 4,
+       /* circuit privacy: public key (client), re-randomisation and flooding (server) */
+       PURPOSE_A_PK = 5, PURPOSE_E_PK = 6, PURPOSE_U = 7, PURPOSE_E2 = 8,
+       PURPOSE_FLOOD_LO = 9, PURPOSE_FLOOD_HI = 10 };
 
 static void draw128(uint64_t seed, uint32_t purpose, uint64_t object,
                     uint64_t c, uint64_t *lo, uint64_t *hi)
@@ -424,6 +427,131 @@ void oracle_intt_mask(const oracle_params *P, const uint64_t *acc,
             if (pos < n) srv_share[pos - k0 * N] = (uint32_t)((t - r) % t);
         }
     }
+}
+
+/* ------------------------------------------------------------------ */
+/* circuit privacy                                                      */
+/* ------------------------------------------------------------------ */
+/*
+ * The paper asks the AHE scheme for circuit privacy and obtains it by noise
+ * flooding (Sec. 2, "Additive Homomorphic Encryption"; 108 bits of
+ * statistical circuit privacy with its parameters, Sec. 7.1).  With
+ * private-key BFV the server cannot re-randomise c1 = sum_i a_i g_i on its
+ * own, so the client also publishes a public key and the server adds a fresh
+ * encryption of zero, (pk0 u + e1, pk1 u + e2), to every response block, e1
+ * being the large flooding term.
+ *
+ * Public key from stream seed:
+ *   a  uniform mod q_j, drawn directly in NTT form from (seed, A_PK, j), slot s
+ *   e  centred binomial (eta = 21) from (seed, E_PK, 0), coefficient x
+ *   pk1 = a,  pk0 = -a * s_hat + NTT(e)   (slot-wise), layout pk[c][j][s].
+ */
+void oracle_public_key(const oracle_params *P, const uint64_t *s_hat, uint64_t seed,
+                       uint64_t *pk)
+{
+    uint32_t N = P->N, L = P->L;
+    int64_t *ei = (int64_t *)malloc(sizeof(int64_t) * N);
+    uint64_t *e = (uint64_t *)malloc(sizeof(uint64_t) * N);
+    for (uint32_t x = 0; x < N; x++) {
+        uint64_t lo, hi;
+        draw128(seed, PURPOSE_E_PK, 0, x, &lo, &hi);
+        ei[x] = cbd21_of(lo);
+    }
+    for (uint32_t j = 0; j < L; j++) {
+        uint64_t q = P->q[j];
+        for (uint32_t x = 0; x < N; x++) e[x] = lift(ei[x], q);
+        oracle_ntt(e, N, q, P->fwd + (size_t)j * N);
+        uint64_t *p0 = pk + (size_t)j * N, *p1 = pk + ((size_t)L + j) * N;
+        const uint64_t *sh = s_hat + (size_t)j * N;
+        for (uint32_t s = 0; s < N; s++) {
+            uint64_t lo, hi;
+            draw128(seed, PURPOSE_A_PK, j, s, &lo, &hi);
+            uint64_t a = uniform_of(lo, hi, q);
+            p1[s] = a;
+            p0[s] = add_mod(sub_mod(0, mul_mod(a, sh[s], q), q), e[s], q);
+        }
+    }
+    free(e);
+    free(ei);
+}
+
+/*
+ * Re-randomisation in the NTT domain, before the inverse transform: for
+ * blocks k in [k0, k0 + nk) (global block index, positions k N + x) of one
+ * query,
+ *   u  ternary, (lo mod 3) - 1 of draw (seed, U, qid) at position k N + x,
+ *   acc[k][c][j] += pk_c[j] * NTT(u)   (slot-wise), c = 0, 1.
+ * acc is [nk][2][L][N], NTT form, modified in place.
+ */
+void oracle_rerandomize(const oracle_params *P, uint64_t *acc, const uint64_t *pk,
+                        uint64_t seed, uint64_t qid, uint64_t k0, uint64_t nk)
+{
+    uint32_t N = P->N, L = P->L;
+    int64_t *ui = (int64_t *)malloc(sizeof(int64_t) * N);
+    uint64_t *u = (uint64_t *)malloc(sizeof(uint64_t) * N);
+    for (uint64_t k = k0; k < k0 + nk; k++) {
+        for (uint32_t x = 0; x < N; x++) {
+            uint64_t lo, hi;
+            draw128(seed, PURPOSE_U, qid, k * N + x, &lo, &hi);
+            ui[x] = ternary_of(lo);
+        }
+        for (uint32_t j = 0; j < L; j++) {
+            uint64_t q = P->q[j];
+            for (uint32_t x = 0; x < N; x++) u[x] = lift(ui[x], q);
+            oracle_ntt(u, N, q, P->fwd + (size_t)j * N);
+            for (uint32_t c = 0; c < 2; c++) {
+                uint64_t *a = acc + (((k - k0) * 2 + c) * L + j) * N;
+                const uint64_t *p = pk + ((size_t)c * L + j) * N;
+                for (uint32_t s = 0; s < N; s++) a[s] = add_mod(a[s], mul_mod(p[s], u[s], q), q);
+            }
+        }
+    }
+    free(u);
+    free(ui);
+}
+
+/*
+ * Flooding, in coefficient form after the inverse transform and the mask:
+ * at position k N + x of one query
+ *   e1 = v - 2^F, v = the low F + 1 bits of the 256-bit integer
+ *        lo_a + hi_a 2^64 + lo_b 2^128 + hi_b 2^192, (lo_a, hi_a) the draw
+ *        (seed, FLOOD_LO, qid) and (lo_b, hi_b) the draw (seed, FLOOD_HI, qid)
+ *        at that position: uniform in [-2^F, 2^F), F <= 255;
+ *   e2 = centred binomial (eta = 21) of draw (seed, E2, qid);
+ *   out[k][0][j][x] += e1 mod q_j,  out[k][1][j][x] += e2 mod q_j.
+ */
+void oracle_flood(const oracle_params *P, uint64_t *out, uint64_t seed, uint64_t qid,
+                  uint64_t k0, uint64_t nk, uint32_t F)
+{
+    uint32_t N = P->N, L = P->L;
+    for (uint64_t k = k0; k < k0 + nk; k++)
+        for (uint32_t x = 0; x < N; x++) {
+            uint64_t pos = k * N + x, w[4];
+            draw128(seed, PURPOSE_FLOOD_LO, qid, pos, &w[0], &w[1]);
+            draw128(seed, PURPOSE_FLOOD_HI, qid, pos, &w[2], &w[3]);
+            /* keep bits 0 .. F of the 256-bit value */
+            for (uint32_t b = 0; b < 4; b++) {
+                int keep = (int)(F + 1) - 64 * (int)b;
+                if (keep <= 0) w[b] = 0;
+                else if (keep < 64) w[b] &= (1ull << keep) - 1;
+            }
+            uint64_t lo, hi;
+            draw128(seed, PURPOSE_E2, qid, pos, &lo, &hi);
+            int64_t e2 = cbd21_of(lo);
+            for (uint32_t j = 0; j < L; j++) {
+                uint64_t q = P->q[j];
+                /* v mod q by Horner over the 64-bit words, then minus 2^F mod q */
+                u128 r = 0;
+                for (int b = 3; b >= 0; b--) r = ((r << 64) | w[b]) % q;
+                u128 pf = 1;
+                for (uint32_t i = 0; i < F; i++) pf = (pf * 2) % q;
+                uint64_t e1 = sub_mod((uint64_t)r, (uint64_t)pf, q);
+                size_t o0 = (((k - k0) * 2 + 0) * L + j) * N + x;
+                size_t o1 = (((k - k0) * 2 + 1) * L + j) * N + x;
+                out[o0] = add_mod(out[o0], e1, q);
+                out[o1] = add_mod(out[o1], lift(e2, q), q);
+            }
+        }
 }
 
 /*

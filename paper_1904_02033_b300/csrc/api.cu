@@ -131,6 +131,8 @@ int sanns_ctx_create(const sanns_params* p, sanns_ctx** out) {
 
 void sanns_ctx_free(sanns_ctx* ctx) {
   if (!ctx) return;
+  cudaFree(ctx->d_pk);
+  cudaFree(ctx->d_pk_shoup);
   cudaFree(ctx->d_tables);
   cudaFree(ctx->d_err);
   delete ctx;
@@ -322,8 +324,83 @@ int sanns_distances_finish(sanns_ctx* ctx, const sanns_db* db, uint32_t B, uint6
   if (rc) return rc;
   if (B == 0) return SANNS_OK;
   if (!qids || !ct_out || !srv_share) return fail(SANNS_EINVAL, "NULL buffer");
+  cudaStream_t st = as_stream(stream);
+  if (ctx->d_pk)
+    SANNS_CUDA(launch_rerandomize(ctx->P, ct_out, B, db->K, db->pos0, mask_seed, qids, ctx->d_pk,
+                                  ctx->d_pk_shoup, st));
   SANNS_CUDA(launch_intt_mask(ctx->P, ct_out, db->d_norms, B, db->K, db->n, db->pos0, mask_seed, qids,
-                              srv_share, ctx->sms, as_stream(stream)));
+                              srv_share, ctx->sms, st));
+  if (ctx->d_pk)
+    SANNS_CUDA(launch_flood(ctx->P, ct_out, B, db->K, db->pos0, mask_seed, qids, ctx->flood_bits,
+                            ctx->privacy, st));
+  return SANNS_OK;
+}
+
+int sanns_public_key(sanns_ctx* ctx, const sanns_sk* sk, uint64_t seed, uint64_t* pk, void* stream) {
+  if (!ctx || !sk || !pk) return fail(SANNS_EINVAL, "ctx, sk or pk is NULL");
+  if (sk->ctx != ctx) return fail(SANNS_EINVAL, "key belongs to another context");
+  int rc = check_device(ctx);
+  if (rc) return rc;
+  SANNS_CUDA(launch_public_key(ctx->P, sk->d_s_hat, sk->d_s_hat_shoup, seed, pk, as_stream(stream)));
+  return SANNS_OK;
+}
+
+int sanns_circuit_privacy_max_flood_bits(const sanns_ctx* ctx) {
+  if (!ctx) return fail(SANNS_EINVAL, "ctx is NULL");
+  // Delta = floor(Q / t): Q = prod q_j in 64-bit limbs, long division by t
+  uint64_t Q[kMaxPrimes + 1] = {1};
+  for (uint32_t j = 0; j < ctx->params.L; ++j) {
+    u128 carry = 0;
+    for (uint32_t i = 0; i <= kMaxPrimes; ++i) {
+      const u128 v = (u128)Q[i] * ctx->P.q[j] + carry;
+      Q[i] = (uint64_t)v;
+      carry = v >> 64;
+    }
+  }
+  u128 rem = 0;
+  int bits = 0;
+  for (int i = kMaxPrimes; i >= 0; --i) {
+    const u128 cur = (rem << 64) | Q[i];
+    const uint64_t qd = (uint64_t)(cur / ctx->P.t);
+    rem = cur % ctx->P.t;
+    if (!bits && qd) bits = 64 * i + (64 - __builtin_clzll(qd));
+  }
+  // 2^F plus the structured noise stays below Delta / 2
+  return bits - 3 > 255 ? 255 : bits - 3;
+}
+
+int sanns_set_circuit_privacy(sanns_ctx* ctx, const uint64_t* pk, uint32_t flood_bits, void* stream) {
+  if (!ctx) return fail(SANNS_EINVAL, "ctx is NULL");
+  int rc = check_device(ctx);
+  if (rc) return rc;
+  cudaStream_t st = as_stream(stream);
+  if (!pk) {
+    SANNS_CUDA(cudaStreamSynchronize(st));
+    cudaFree(ctx->d_pk);
+    cudaFree(ctx->d_pk_shoup);
+    ctx->d_pk = ctx->d_pk_shoup = nullptr;
+    return SANNS_OK;
+  }
+  const int fmax = sanns_circuit_privacy_max_flood_bits(ctx);
+  if ((int)flood_bits > fmax)
+    return fail(SANNS_EINVAL, "flood_bits above " + std::to_string(fmax) +
+                                  " would break decryption (2^F must stay below Delta / 4)");
+  const size_t words = 2ull * ctx->params.L * ctx->P.N;
+  if (!ctx->d_pk) {
+    SANNS_CUDA(cudaMalloc(&ctx->d_pk, sizeof(uint64_t) * words));
+    SANNS_CUDA(cudaMalloc(&ctx->d_pk_shoup, sizeof(uint64_t) * words));
+  }
+  SANNS_CUDA(cudaMemcpyAsync(ctx->d_pk, pk, sizeof(uint64_t) * words, cudaMemcpyDefault, st));
+  SANNS_CUDA(launch_key_shoup(ctx->P, ctx->d_pk, ctx->d_pk_shoup, st));
+  SANNS_CUDA(cudaStreamSynchronize(st));
+  ctx->flood_bits = flood_bits;
+  for (uint32_t j = 0; j < ctx->params.L; ++j) {
+    const uint64_t q = ctx->P.q[j];
+    ctx->privacy.q_barrett[j] = (uint64_t)(((u128)1 << 64) / q);
+    u128 v = 1 % q;
+    for (uint32_t i = 0; i < flood_bits; ++i) v = (v * 2) % q;
+    ctx->privacy.two_f[j] = (uint64_t)v;
+  }
   return SANNS_OK;
 }
 
@@ -468,6 +545,7 @@ int sanns_distances_gather(sanns_ctx* ctx, const sanns_clusters* cl, const uint6
   if (!ctx || !cl) return fail(SANNS_EINVAL, "ctx or clusters is NULL");
   if (cl->ctx != ctx) return fail(SANNS_EINVAL, "clusters belong to another context");
   if (ctx->P.N > 8192) return fail(SANNS_EINVAL, "the gather path supports N <= 8192");
+  if (ctx->d_pk) return fail(SANNS_EINVAL, "circuit privacy is not available on the gather path");
   if (B == 0) return SANNS_OK;
   if (!ct_in || !qids || !ct_out || !srv_share || !probes) return fail(SANNS_EINVAL, "NULL buffer");
   std::vector<uint64_t> nb(B), kb(B);

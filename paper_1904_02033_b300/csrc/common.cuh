@@ -17,7 +17,18 @@ constexpr uint32_t kMinN = 64;
 constexpr uint32_t kMaxD = 224;   // ct tile of the MAC kernel lives in shared memory
 
 // Stream purposes of the counter-based generator (ChaCha20, RFC 8439).
-enum : uint32_t { kPurposeSk = 1, kPurposeA = 2, kPurposeE = 3, kPurposeMask = 4 };
+enum : uint32_t {
+  kPurposeSk = 1, kPurposeA = 2, kPurposeE = 3, kPurposeMask = 4,
+  // circuit privacy: public key (client), re-randomisation and flooding (server)
+  kPurposeAPk = 5, kPurposeEPk = 6, kPurposeU = 7, kPurposeE2 = 8, kPurposeFloodLo = 9,
+  kPurposeFloodHi = 10
+};
+
+// Constants of the flooding term (circuit privacy), per prime.
+struct PrivacyConsts {
+  uint64_t q_barrett[kMaxPrimes];   // floor(2^64 / q_j)
+  uint64_t two_f[kMaxPrimes];       // 2^F mod q_j
+};
 
 // Per-prime constants, passed to kernels by value.
 struct PrimeSet {

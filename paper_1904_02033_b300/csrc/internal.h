@@ -18,6 +18,12 @@ struct sanns_ctx {
   uint32_t batched_tune[7]; // batched kernel: back-off ns (TMA, MMA, producers, epilogue), L2 prefetch
                             // units, scratch cap (MiB) of the query multiples, tile (0: 128 blocks
                             // on one SM, 1: 256 blocks on an SM pair)
+  // circuit privacy: the client's public key (library copy, [2][L][N] NTT
+  // form) and its Shoup companions, or NULL; flooding exponent F
+  uint64_t* d_pk;
+  uint64_t* d_pk_shoup;
+  uint32_t flood_bits;
+  sanns::PrivacyConsts privacy;
 };
 
 struct sanns_sk {
@@ -69,6 +75,15 @@ uint64_t shoup_of(uint64_t w, uint64_t q);
 // kernel launchers (ntt.cu, mac.cu, client.cu)
 cudaError_t launch_ntt(const PrimeSet& P, uint64_t* data, uint64_t count, bool inverse,
                        cudaStream_t st);
+cudaError_t launch_public_key(const PrimeSet& P, const uint64_t* s_hat, const uint64_t* s_hat_shoup,
+                              uint64_t seed, uint64_t* pk, cudaStream_t st);
+cudaError_t launch_key_shoup(const PrimeSet& P, const uint64_t* pk, uint64_t* pks, cudaStream_t st);
+cudaError_t launch_rerandomize(const PrimeSet& P, uint64_t* ct, uint32_t B, uint64_t K, uint64_t pos0,
+                               uint64_t seed, const uint64_t* qids, const uint64_t* pk,
+                               const uint64_t* pks, cudaStream_t st);
+cudaError_t launch_flood(const PrimeSet& P, uint64_t* ct, uint32_t B, uint64_t K, uint64_t pos0,
+                         uint64_t seed, const uint64_t* qids, uint32_t F, const PrivacyConsts& C,
+                         cudaStream_t st);
 cudaError_t launch_keygen(const PrimeSet& P, uint64_t seed, int8_t* s, uint64_t* s_hat,
                           uint64_t* s_hat_shoup, cudaStream_t st);
 cudaError_t launch_encrypt(const PrimeSet& P, const uint64_t* s_hat, const uint64_t* s_hat_shoup,

@@ -62,6 +62,9 @@ _SIGS = {
     "sanns_set_mac_variant": ([_VP, C.c_int], C.c_int),
     "sanns_autotune_mac": ([_VP, _VP, _VP, C.c_uint32, _VP, C.c_int, _VP, _VP], C.c_int),
     "sanns_autotune_batched": ([_VP, _VP, _VP, C.c_uint32, _VP, C.c_int, _VP, _VP], C.c_int),
+    "sanns_public_key": ([_VP, _VP, C.c_uint64, _VP, _VP], C.c_int),
+    "sanns_circuit_privacy_max_flood_bits": ([_VP], C.c_int),
+    "sanns_set_circuit_privacy": ([_VP, _VP, C.c_uint32, _VP], C.c_int),
     "sanns_db_prepare_batched": ([_VP, _VP, _VP], C.c_int),
     "sanns_distances_batched": ([_VP, _VP, _VP, C.c_uint32, C.c_uint64, _VP, _VP, _VP, _VP],
                                 C.c_int),
@@ -372,6 +375,28 @@ def sanns_autotune_mac(ctx: Context, db: Database, ct_in: torch.Tensor, ct_out: 
     if rc < 0:
         _check(rc)
     return rc, list(ms)
+
+
+def sanns_public_key(ctx: Context, sk: SecretKey, seed: int, stream=None) -> torch.Tensor:
+    """The client's public key (-a s + e, a), [2][L][N] NTT form, for circuit privacy."""
+    pk = torch.empty((2, ctx.L, ctx.N), dtype=torch.uint64, device="cuda")
+    _check(load().sanns_public_key(ctx.handle, sk.handle, seed, _ptr(pk), _stream(stream)))
+    return pk
+
+
+def sanns_circuit_privacy_max_flood_bits(ctx: Context) -> int:
+    rc = load().sanns_circuit_privacy_max_flood_bits(ctx.handle)
+    if rc < 0:
+        _check(rc)
+    return rc
+
+
+def sanns_set_circuit_privacy(ctx: Context, pk: torch.Tensor | None, flood_bits: int = 0,
+                              stream=None):
+    """Re-randomise and flood every later response of this context (pk = None: off)."""
+    if pk is not None:
+        assert pk.dtype == torch.uint64 and pk.shape == (2, ctx.L, ctx.N) and pk.is_contiguous()
+    _check(load().sanns_set_circuit_privacy(ctx.handle, _ptr(pk), flood_bits, _stream(stream)))
 
 
 BATCHED_CONFIGS = [(tile, pf) for tile in (0, 1) for pf in (0, 1)]  # index = 2 tile + prefetch

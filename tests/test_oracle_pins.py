@@ -312,3 +312,53 @@ def test_approx_topk_expected_hits_closed_forms():
         hits.append(len(set(got) & set(range(k))))
     want = select.expected_hits(n, k, l)
     assert abs(np.mean(hits) - want) < 4 * np.std(hits) / math.sqrt(len(hits)) + 0.02
+
+
+# ---------------------------------------------------------------------------
+# circuit privacy (Sec. 2 "Additive Homomorphic Encryption": circuit privacy by
+# noise flooding; a public key lets the server re-randomise c1)
+# ---------------------------------------------------------------------------
+def test_public_key_is_an_encryption_of_zero():
+    O = Oracle(256, 2, 60, 0, 3)
+    s, s_hat = O.keygen(11)
+    pk = O.public_key(s_hat, 12)
+    ct = np.zeros((1, 2, O.L, O.N), dtype=np.uint64)
+    for c in range(2):
+        for j in range(O.L):
+            ct[0, c, j] = O.intt(pk[c, j], j)
+    v = O.decrypt_phase(ct, s)          # c0 + c1 s = e, the same small integer per prime
+    for j in range(O.L):
+        q = int(O.q[j])
+        cen = [int(x) if int(x) <= q // 2 else int(x) - q for x in v[0, j]]
+        assert max(abs(x) for x in cen) <= 21 and any(cen)
+        if j:
+            assert cen == prev
+        prev = cen
+
+
+@pytest.mark.parametrize("F", [0, 120])
+def test_circuit_privacy_keeps_shares_and_floods_the_noise(F):
+    cfg = (256, 3, 60, 0, 5)
+    O = Oracle(*cfg)
+    n, d = 256 * 3 - 7, cfg[4]
+    rnd = np.random.default_rng(F + 1)
+    coords = rnd.integers(0, 256, size=(n, d), dtype=np.uint8)
+    qv = rnd.integers(0, 256, size=d, dtype=np.uint8)
+    s, s_hat = O.keygen(21)
+    pk = O.public_key(s_hat, 22)
+    ct = O.encrypt(s_hat, qv, 23, 5)
+    plain, srv0 = O.distances(ct, coords, None, 24, 5)
+    priv, srv = O.distances(ct, coords, None, 24, 5, pk=pk, flood_bits=F)
+    assert np.array_equal(srv, srv0)                    # the mask is unchanged
+    assert not np.array_equal(priv[:, 1], plain[:, 1])  # c1 re-randomised
+    cli = O.decrypt_shares(priv, s, qv, n)
+    brute = np.sum((coords.astype(np.int64) - qv.astype(np.int64)) ** 2, axis=1)
+    assert np.array_equal((cli.astype(np.int64) + srv) % O.t, brute)
+    # the phase noise is the flooding term: about 2^F, and below Delta / 2
+    m = O.scale_round(O.decrypt_phase(priv, s))
+    noise = max(O.phase_noise(priv, s, m))
+    if F:
+        assert 2 ** (F - 2) <= noise <= 2 ** F + 2 ** 50
+    else:
+        assert noise < 2 ** 50
+    assert noise < O.P.delta // 2
