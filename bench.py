@@ -364,7 +364,8 @@ BATCHED = dict(n=10_000_000, d=96, N=8192, L=3, prime_bits=60, t_rule=0, n_comp=
 
 
 def run_batched_section(quick: bool = False, n_override: int | None = None,
-                        d_override: int | None = None, b_override: int | None = None) -> dict:
+                        d_override: int | None = None, b_override: int | None = None,
+                        scratch_mib: int | None = None) -> dict:
     """The batched configuration: n = 10^7, d = 96 (Deep1B-10M-shaped), 64
     queries per launch on the tensor-core path, against the same queries run
     one at a time on the per-query path; outputs compared in full."""
@@ -401,6 +402,8 @@ def run_batched_section(quick: bool = False, n_override: int | None = None,
     out_p = torch.empty((1, K, 2, L, N), dtype=torch.uint64, device="cuda")
     srv_p = torch.empty((1, n), dtype=torch.uint32, device="cuda")
     S.sanns_autotune_mac(ctx, db, ct[0:1], out_p, reps=2)
+    if scratch_mib:
+        S.sanns_batched_tune(ctx, scratch_mib=scratch_mib)
     tuned, tune_ms = S.sanns_autotune_batched(ctx, db, ct, out_b, reps=1)
     tile, prefetch = S.BATCHED_CONFIGS[tuned]
 
@@ -684,6 +687,8 @@ def main():
                     help="run only the batched section on N_POINTS points (profiling)")
     ap.add_argument("--batched-d", type=int, default=None, help="dimension for --only-batched")
     ap.add_argument("--batched-B", type=int, default=None, help="queries per launch for --only-batched")
+    ap.add_argument("--batched-scratch-mib", type=int, default=None,
+                    help="cap on the batched path's query-multiple scratch (smaller launches)")
     ap.add_argument("--n", type=int, default=None,
                     help="smaller database (profiling captures); the line then names it")
     ap.add_argument("--queries", type=int, default=None, help="number of distinct queries")
@@ -704,7 +709,9 @@ def main():
         torch.cuda.set_device(0)
         print(json.dumps({"batched": run_batched_section(n_override=args.only_batched,
                                                          d_override=args.batched_d,
-                                                         b_override=args.batched_B)}), flush=True)
+                                                         b_override=args.batched_B,
+                                                         scratch_mib=args.batched_scratch_mib)}),
+              flush=True)
     elif args.impl == "reference":
         run_reference(args)
     else:
