@@ -272,6 +272,24 @@ int sanns_autotune_batched(sanns_ctx *ctx, const sanns_db *db, const uint64_t *c
                            uint64_t *ct_out_dev, int reps, float *ms_out, void *stream);
 
 /*
+ * Plaintext meaning of the selection step (Sec. 4, Algorithms 1 and 2; the
+ * paper evaluates it inside garbled circuits, which this library does not):
+ * for every query b the k smallest reconstructed distances
+ * (cli_dev[b][x] + srv_dev[b][x]) mod t over positions x < n.
+ *   bins = 0:  exact, the k smallest (distance, position) pairs in that order,
+ *              which is the result Algorithm 1 (NaiveTopk) produces.
+ *   bins = l:  Algorithm 2 (ApproxTopk): position x falls in bin
+ *              floor(x l / n); the minimum of every bin (the earlier position
+ *              on ties), then the k smallest of the l minima.
+ * Output (device, caller-owned): dist_dev [B][k] u32 ascending, pos_dev
+ * [B][k] u64 positions (in the server's permuted order).  Needs 1 <= k <= 32,
+ * k <= n < 2^32 and, for l > 0, k <= l <= n; SANNS_EINVAL otherwise.
+ * Asynchronous on stream (stream-ordered scratch).
+ */
+int sanns_topk(sanns_ctx *ctx, const uint32_t *cli_dev, const uint32_t *srv_dev, uint32_t B, uint64_t n,
+               uint32_t k, uint64_t bins, uint32_t *dist_dev, uint64_t *pos_dev, void *stream);
+
+/*
  * Circuit privacy (Sec. 2, "Additive Homomorphic Encryption": the AHE scheme
  * must not reveal the server's operations beyond the decrypted message; the
  * paper obtains this by noise flooding, with 108 bits of statistical circuit

@@ -8,9 +8,14 @@ TEST INFRASTRUCTURE ONLY (the oracle).
 * approx_topk     -- Algorithm 2 (ApproxTopk): l bins of consecutive
                      (already shuffled) positions, the minimum of each bin,
                      then NaiveTopk over the l minima.
-* exact_topk      -- the same result as naive_topk, computed by sorting on
-                     (value, position); used at sizes where the O(nk) loop
-                     is too slow.
+* exact_topk      -- the k smallest (value, position) pairs: the same values
+                     as naive_topk (its compare-and-swap chain re-inserts a
+                     displaced element after equal ones, so its order among
+                     equal values is not positional); used where the O(nk)
+                     loop is too slow and as the deterministic definition.
+* approx_topk_by_position -- Algorithm 2 with that definition for the final
+                     selection: bin minima (earlier position on ties), then
+                     the k smallest (value, position) of the minima.
 * expected_hits   -- E|I| for ApproxTopk under the random-order assumption of
                      Theorem 1, for fixed bin sizes (hypergeometric form).
 """
@@ -38,8 +43,9 @@ def naive_topk(values, ids, k: int):
 
 
 def exact_topk(values: np.ndarray, ids: np.ndarray, k: int):
-    """Ascending by (value, position): the order Algorithm 1 produces (a later
-    equal value never displaces an earlier one)."""
+    """The k smallest (value, position) pairs, ascending.  Algorithm 1 selects
+    the same values; among equal values its order (and, at the k-th value,
+    its choice) can differ."""
     values = np.asarray(values, dtype=np.int64)
     order = np.lexsort((np.arange(len(values)), values))[:k]
     return values[order].tolist(), np.asarray(ids)[order].tolist()
@@ -71,6 +77,25 @@ def approx_topk(values: np.ndarray, ids: np.ndarray, k: int, l: int):
         mids.append(int(ids[start + r]))
         start = end
     return naive_topk(mins, mids, k)
+
+
+def approx_topk_by_position(values: np.ndarray, ids: np.ndarray, k: int, l: int):
+    """Algorithm 2's bins and per-bin minima (earlier position on ties), then
+    the k smallest (value, position) pairs of the minima."""
+    values = np.asarray(values, dtype=np.int64)
+    ids = np.asarray(ids)
+    n = len(values)
+    b = bin_of(n, l)
+    starts = np.searchsorted(b, np.arange(l), side="left")
+    ends = np.searchsorted(b, np.arange(l), side="right")
+    mval, mpos = [], []
+    for i in range(l):
+        seg = values[starts[i]:ends[i]]
+        r = int(np.argmin(seg))
+        mval.append(int(seg[r]))
+        mpos.append(int(starts[i] + r))
+    order = np.lexsort((np.array(mpos), np.array(mval)))[:k]
+    return [mval[o] for o in order], [int(ids[mpos[o]]) for o in order]
 
 
 def expected_hits(n: int, k: int, l: int) -> float:

@@ -336,6 +336,20 @@ int sanns_distances_finish(sanns_ctx* ctx, const sanns_db* db, uint32_t B, uint6
   return SANNS_OK;
 }
 
+int sanns_topk(sanns_ctx* ctx, const uint32_t* cli, const uint32_t* srv, uint32_t B, uint64_t n,
+               uint32_t k, uint64_t bins, uint32_t* dist, uint64_t* pos, void* stream) {
+  if (!ctx) return fail(SANNS_EINVAL, "ctx is NULL");
+  if (B == 0) return SANNS_OK;
+  if (!cli || !srv || !dist || !pos) return fail(SANNS_EINVAL, "NULL buffer");
+  if (k < 1 || k > 32) return fail(SANNS_EINVAL, "k must be in [1, 32]");
+  if (n < k || n >= (1ull << 32)) return fail(SANNS_EINVAL, "need k <= n < 2^32");
+  if (bins && (bins < k || bins > n)) return fail(SANNS_EINVAL, "need k <= bins <= n");
+  int rc = check_device(ctx);
+  if (rc) return rc;
+  SANNS_CUDA(launch_topk(cli, srv, B, n, ctx->P.t, k, bins, dist, pos, as_stream(stream)));
+  return SANNS_OK;
+}
+
 int sanns_public_key(sanns_ctx* ctx, const sanns_sk* sk, uint64_t seed, uint64_t* pk, void* stream) {
   if (!ctx || !sk || !pk) return fail(SANNS_EINVAL, "ctx, sk or pk is NULL");
   if (sk->ctx != ctx) return fail(SANNS_EINVAL, "key belongs to another context");

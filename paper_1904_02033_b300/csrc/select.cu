@@ -1,0 +1,204 @@
+// Plaintext meaning of the selection step (the paper evaluates it inside
+// garbled circuits, which stay out of scope): the k smallest reconstructed
+// distances dist = (client share + server share) mod t of every query.
+//   exact:        the k smallest (value, position) pairs (the order of
+//                 Algorithm 1, NaiveTopk, which never lets a later equal value
+//                 displace an earlier one)
+//   approximate:  Algorithm 2, ApproxTopk: position x falls in bin
+//                 floor(x l / n); the minimum of every bin (the earlier
+//                 position on ties), then the k smallest of the l minima.
+// A (value, position) pair is one 64-bit key, value << 32 | position, so
+// every comparison is a plain integer comparison and the result is unique.
+#include "internal.h"
+
+namespace sanns {
+
+namespace {
+
+constexpr int kTopkMax = 32;
+constexpr int kTopkThreads = 256;
+constexpr uint64_t kNoKey = ~0ull;
+
+// A thread keeps its kTopkMax smallest keys, ascending (at least the k the
+// block needs, k <= kTopkMax; static indices keep the list in registers).
+// Insert key, only called when key < best[kTopkMax - 1].
+__device__ __forceinline__ void topk_insert(uint64_t (&best)[kTopkMax], uint64_t key) {
+#pragma unroll
+  for (int j = kTopkMax - 1; j >= 1; --j) {
+    const uint64_t prev = best[j - 1];
+    if (prev > key) best[j] = prev;
+    else if (best[j] > key) best[j] = key;
+  }
+  if (best[0] > key) best[0] = key;
+}
+
+// The block's k smallest keys from every thread's ascending list, in k
+// rounds of a block-wide minimum; thread 0 writes them to out[0 .. k-1].
+__device__ void topk_block_merge(uint64_t (&best)[kTopkMax], int k, uint64_t* out) {
+  __shared__ uint64_t warp_min[kTopkThreads / 32];
+  __shared__ uint64_t round_min;
+  const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int r = 0; r < k; ++r) {
+    uint64_t m = best[0];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const uint64_t other = __shfl_xor_sync(0xffffffffu, m, o);
+      m = other < m ? other : m;
+    }
+    if (lane == 0) warp_min[warp] = m;
+    __syncthreads();
+    if (warp == 0) {
+      uint64_t w = lane < blockDim.x / 32 ? warp_min[lane] : kNoKey;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const uint64_t other = __shfl_xor_sync(0xffffffffu, w, o);
+        w = other < w ? other : w;
+      }
+      if (lane == 0) {
+        round_min = w;
+        out[r] = w;
+      }
+    }
+    __syncthreads();
+    // keys are unique: exactly one thread holds a real minimum and pops it
+    if (best[0] == round_min && round_min != kNoKey) {
+#pragma unroll
+      for (int j = 0; j < kTopkMax - 1; ++j) best[j] = best[j + 1];
+      best[kTopkMax - 1] = kNoKey;
+    }
+    __syncthreads();
+  }
+}
+
+// Pass 1, from the shares: block (chunk c, query b) keeps the k smallest keys
+// of positions [c chunk, (c + 1) chunk) in part[b][c][0 .. k-1].
+__global__ void __launch_bounds__(kTopkThreads) topk_shares_kernel(const uint32_t* __restrict__ cli,
+                                                                   const uint32_t* __restrict__ srv,
+                                                                   uint64_t n, uint64_t t, int k,
+                                                                   uint64_t chunk, uint64_t* part) {
+  const uint64_t b = blockIdx.y, c = blockIdx.x;
+  uint64_t best[kTopkMax];
+#pragma unroll
+  for (int j = 0; j < kTopkMax; ++j) best[j] = kNoKey;
+  const uint64_t p0 = c * chunk, p1 = p0 + chunk < n ? p0 + chunk : n;
+  const uint32_t* cs = cli + b * n;
+  const uint32_t* ss = srv + b * n;
+  for (uint64_t p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
+    uint64_t v = (uint64_t)cs[p] + ss[p];
+    v = v >= t ? v - t : v;
+    const uint64_t key = (v << 32) | p;
+    if (key < best[kTopkMax - 1]) topk_insert(best, key);
+  }
+  topk_block_merge(best, k, part + (b * gridDim.x + c) * k);
+}
+
+// Bin minima for ApproxTopk: one warp per bin i = positions [ceil(i n / l),
+// ceil((i + 1) n / l)); mins[b][i] = the smallest key of the bin.
+__global__ void __launch_bounds__(kTopkThreads) bin_min_kernel(const uint32_t* __restrict__ cli,
+                                                               const uint32_t* __restrict__ srv,
+                                                               uint64_t n, uint64_t t, uint64_t l,
+                                                               uint64_t* mins) {
+  const uint64_t b = blockIdx.y;
+  const uint64_t i = blockIdx.x * (uint64_t)(blockDim.x / 32) + (threadIdx.x >> 5);
+  const uint32_t lane = threadIdx.x & 31;
+  if (i >= l) return;
+  const uint64_t p0 = (i * n + l - 1) / l, p1 = ((i + 1) * n + l - 1) / l;
+  const uint32_t* cs = cli + b * n;
+  const uint32_t* ss = srv + b * n;
+  uint64_t m = kNoKey;
+  for (uint64_t p = p0 + lane; p < p1; p += 32) {
+    uint64_t v = (uint64_t)cs[p] + ss[p];
+    v = v >= t ? v - t : v;
+    const uint64_t key = (v << 32) | p;
+    m = key < m ? key : m;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const uint64_t other = __shfl_xor_sync(0xffffffffu, m, o);
+    m = other < m ? other : m;
+  }
+  if (lane == 0) mins[b * l + i] = m;
+}
+
+// Pass over keys: block (chunk c, query b) keeps the k smallest of
+// keys[b][c chunk .. (c + 1) chunk) (count per query m).
+__global__ void __launch_bounds__(kTopkThreads) topk_keys_kernel(const uint64_t* __restrict__ keys,
+                                                                 uint64_t m, int k, uint64_t chunk,
+                                                                 uint64_t* part) {
+  const uint64_t b = blockIdx.y, c = blockIdx.x;
+  uint64_t best[kTopkMax];
+#pragma unroll
+  for (int j = 0; j < kTopkMax; ++j) best[j] = kNoKey;
+  const uint64_t p0 = c * chunk, p1 = p0 + chunk < m ? p0 + chunk : m;
+  const uint64_t* ks = keys + b * m;
+  for (uint64_t p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
+    const uint64_t key = ks[p];
+    if (key < best[kTopkMax - 1]) topk_insert(best, key);
+  }
+  topk_block_merge(best, k, part + (b * gridDim.x + c) * k);
+}
+
+// Split the keys: dist[b][r] = key >> 32, pos[b][r] = key & (2^32 - 1).
+__global__ void topk_split_kernel(const uint64_t* __restrict__ keys, uint64_t count,
+                                  uint32_t* __restrict__ dist, uint64_t* __restrict__ pos) {
+  const uint64_t e = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+  if (e >= count) return;
+  dist[e] = (uint32_t)(keys[e] >> 32);
+  pos[e] = keys[e] & 0xffffffffull;
+}
+
+// k smallest of m keys per query, B queries, through chunked passes into
+// scratch (ping-pong between a and b); the result ends in *res.
+cudaError_t reduce_keys(const uint64_t* keys, uint32_t B, uint64_t m, int k, uint64_t* a, uint64_t* b,
+                        const uint64_t** res, cudaStream_t st) {
+  const uint64_t chunk = 8192;
+  const uint64_t* src = keys;
+  uint64_t* dst = a;
+  while (true) {
+    const uint64_t chunks = (m + chunk - 1) / chunk;
+    topk_keys_kernel<<<dim3((unsigned)chunks, B), kTopkThreads, 0, st>>>(src, m, k, chunk, dst);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    m = chunks * (uint64_t)k;
+    src = dst;
+    dst = dst == a ? b : a;
+    if (chunks == 1) break;
+  }
+  *res = src;
+  return cudaSuccess;
+}
+
+}  // namespace
+
+cudaError_t launch_topk(const uint32_t* cli, const uint32_t* srv, uint32_t B, uint64_t n, uint64_t t,
+                        uint32_t k, uint64_t bins, uint32_t* dist, uint64_t* pos, cudaStream_t st) {
+  const uint64_t chunk = 1 << 16;
+  const uint64_t first = bins ? bins : (n + chunk - 1) / chunk * k;  // keys per query after pass 1
+  const uint64_t words = 2 * (uint64_t)B * (first + 64);
+  uint64_t* scratch = nullptr;
+  cudaError_t e = cudaMallocAsync(&scratch, sizeof(uint64_t) * words, st);
+  if (e != cudaSuccess) return e;
+  uint64_t* a = scratch;
+  uint64_t* b = scratch + words / 2;
+  if (bins) {
+    const unsigned per_block = kTopkThreads / 32;
+    bin_min_kernel<<<dim3((unsigned)((bins + per_block - 1) / per_block), B), kTopkThreads, 0, st>>>(
+        cli, srv, n, t, bins, a);
+  } else {
+    topk_shares_kernel<<<dim3((unsigned)((n + chunk - 1) / chunk), B), kTopkThreads, 0, st>>>(
+        cli, srv, n, t, (int)k, chunk, a);
+  }
+  e = cudaGetLastError();
+  const uint64_t* res = nullptr;
+  // the first pass's keys sit in a; later passes alternate b, a, ..
+  if (e == cudaSuccess) e = reduce_keys(a, B, first, (int)k, b, a, &res, st);
+  if (e == cudaSuccess) {
+    const uint64_t count = (uint64_t)B * k;
+    topk_split_kernel<<<(unsigned)((count + 255) / 256), 256, 0, st>>>(res, count, dist, pos);
+    e = cudaGetLastError();
+  }
+  cudaError_t e2 = cudaFreeAsync(scratch, st);
+  return e != cudaSuccess ? e : e2;
+}
+
+}  // namespace sanns

@@ -63,6 +63,8 @@ _SIGS = {
     "sanns_autotune_mac": ([_VP, _VP, _VP, C.c_uint32, _VP, C.c_int, _VP, _VP], C.c_int),
     "sanns_autotune_batched": ([_VP, _VP, _VP, C.c_uint32, _VP, C.c_int, _VP, _VP], C.c_int),
     "sanns_public_key": ([_VP, _VP, C.c_uint64, _VP, _VP], C.c_int),
+    "sanns_topk": ([_VP, _VP, _VP, C.c_uint32, C.c_uint64, C.c_uint32, C.c_uint64, _VP, _VP, _VP],
+                   C.c_int),
     "sanns_circuit_privacy_max_flood_bits": ([_VP], C.c_int),
     "sanns_set_circuit_privacy": ([_VP, _VP, C.c_uint32, _VP], C.c_int),
     "sanns_db_prepare_batched": ([_VP, _VP, _VP], C.c_int),
@@ -375,6 +377,20 @@ def sanns_autotune_mac(ctx: Context, db: Database, ct_in: torch.Tensor, ct_out: 
     if rc < 0:
         _check(rc)
     return rc, list(ms)
+
+
+def sanns_topk(ctx: Context, cli_share: torch.Tensor, srv_share: torch.Tensor, k: int,
+               bins: int = 0, stream=None):
+    """The k smallest reconstructed distances per query: exact (bins = 0) or
+    ApproxTopk over `bins` bins.  Returns (dist [B][k] uint32, pos [B][k] int64)."""
+    assert cli_share.dtype == torch.uint32 and srv_share.dtype == torch.uint32
+    assert cli_share.shape == srv_share.shape and cli_share.dim() == 2
+    B, n = cli_share.shape
+    dist = torch.empty((B, k), dtype=torch.uint32, device="cuda")
+    pos = torch.empty((B, k), dtype=torch.int64, device="cuda")
+    _check(load().sanns_topk(ctx.handle, _ptr(cli_share), _ptr(srv_share), B, n, k, bins,
+                             _ptr(dist), _ptr(pos), _stream(stream)))
+    return dist, pos
 
 
 def sanns_public_key(ctx: Context, sk: SecretKey, seed: int, stream=None) -> torch.Tensor:

@@ -1,0 +1,78 @@
+"""GPU selection (plaintext meaning of Algorithms 1 and 2) against the oracle's
+selection code, and the first configuration end to end: encrypted distances,
+decryption, exact top-10, compared with a brute-force top-10."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import select
+from oracle.bfv import Oracle
+from paper_1904_02033_b300 import inputs
+from paper_1904_02033_b300 import sanns as S
+
+pytestmark = pytest.mark.gpu
+
+
+def cu(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    return S.sanns_ctx_create(256, 2, 40, 0, 4)
+
+
+@pytest.mark.parametrize("n,spread", [(100_003, 50), (70_000, 1 << 24), (33, 5)])
+@pytest.mark.parametrize("k", [1, 10, 32])
+def test_topk_matches_oracle(ctx, n, spread, k):
+    if k > n:
+        pytest.skip("k > n")
+    t = ctx.query()["t"]
+    rnd = np.random.default_rng(n + k)
+    B = 3
+    dist = rnd.integers(0, spread, size=(B, n)).astype(np.int64) % t   # many ties for small spread
+    srv = rnd.integers(0, t, size=(B, n)).astype(np.int64)
+    cli = (dist - srv) % t
+    cli_d, srv_d = cu(cli.astype(np.uint32)), cu(srv.astype(np.uint32))
+    pos = np.arange(n)
+    for bins in sorted({0, max(k, n // 128), max(k, n // 7), n}):
+        gd, gp = S.sanns_topk(ctx, cli_d, srv_d, k, bins)
+        gd, gp = gd.cpu().numpy(), gp.cpu().numpy()
+        for b in range(B):
+            if bins:
+                ov, oi = select.approx_topk_by_position(dist[b], pos, k, bins)
+                assert ov == select.approx_topk(dist[b], pos, k, bins)[0]
+            else:
+                ov, oi = select.exact_topk(dist[b], pos, k)
+            assert gd[b].tolist() == ov and gp[b].tolist() == oi, (bins, b)
+
+
+def test_topk_rejects_bad_arguments(ctx):
+    z = torch.zeros((1, 100), dtype=torch.uint32, device="cuda")
+    for k, bins in [(0, 0), (33, 0), (10, 5), (10, 101), (101, 0)]:
+        with pytest.raises(S.SannsError):
+            S.sanns_topk(ctx, z, z, k, bins)
+
+
+def test_first_configuration_end_to_end_top10():
+    # n = 4096, d = 32 uniform coordinates, N = 4096, two 54-bit primes
+    cfg = (4096, 2, 54, 0, 32)
+    n, d, k = 4096, 32, 10
+    ctx = S.sanns_ctx_create(*cfg)
+    coords = inputs.uniform_coords(n, d, 0)
+    perm = inputs.permutation(n, 1)
+    q = inputs.uniform_coords(1, d, 2)
+    qids = cu(np.array([0], dtype=np.uint64))
+    sk = S.sanns_keygen(ctx, 0)
+    db = S.sanns_encode_db(ctx, cu(coords), cu(perm))
+    ct = S.sanns_encrypt_query(ctx, sk, cu(q), 0, qids)
+    out, srv = S.sanns_distances(ctx, db, ct, 0, qids)
+    cli = S.sanns_decrypt_shares(ctx, sk, out, n, cu(q))
+    gd, gp = S.sanns_topk(ctx, cli, srv, k)
+    brute = np.sum((coords[perm].astype(np.int64) - q[0].astype(np.int64)) ** 2, axis=1)
+    ev, ep = select.exact_topk(brute, np.arange(n), k)
+    assert gd.cpu().numpy()[0].tolist() == ev and gp.cpu().numpy()[0].tolist() == ep
+    # positions name points of the server's permuted order
+    ids = perm[gp.cpu().numpy()[0]]
+    assert np.array_equal(np.sort(np.sum((coords[ids].astype(np.int64) - q[0]) ** 2, axis=1)),
+                          np.array(ev))

@@ -362,3 +362,25 @@ def test_circuit_privacy_keeps_shares_and_floods_the_noise(F):
     else:
         assert noise < 2 ** 50
     assert noise < O.P.delta // 2
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_approx_topk_by_position_selects_algorithm_2_values(seed):
+    rnd = np.random.default_rng(seed)
+    n = int(rnd.integers(40, 400))
+    vals = rnd.integers(0, 6, size=n)             # many ties
+    ids = np.arange(n)
+    for l in (10, n // 3, n):
+        k = min(10, l)
+        lit_v, lit_i = select.approx_topk(vals, ids, k, l)
+        pos_v, pos_i = select.approx_topk_by_position(vals, ids, k, l)
+        assert pos_v == lit_v                      # the same values in the same order
+        b = select.bin_of(n, l)
+        mins = {}
+        for x in range(n):
+            if b[x] not in mins or vals[x] < vals[mins[b[x]]]:
+                mins[b[x]] = x
+        minpos = set(mins.values())
+        assert set(pos_i) <= minpos and set(lit_i) <= minpos   # both pick bin minima
+        assert len(set(pos_i)) == k
+        assert pos_i == sorted(pos_i, key=lambda x: (vals[x], x))
