@@ -223,6 +223,35 @@ def run_gpu(args) -> None:
     graph_ms = g0.elapsed_time(g1) / (g_reps * G)
     del graph
 
+    # selection on the reconstructed shares (this workload's check): client
+    # decryption, exact top-10 and ApproxTopk with l = n / 128 bins, against
+    # brute-force squared distances of the permuted points
+    k_sel, l_sel = 10, n // 128
+    out1, srv1 = S.sanns_distances(ctx, db, ct_all[0:1], mask_seed, qids[0:1])
+    cli1 = S.sanns_decrypt_shares(ctx, sk, out1, n, qdev[0:1])
+    S.sanns_topk(ctx, cli1, srv1, k_sel)
+    S.sanns_topk(ctx, cli1, srv1, k_sel, l_sel)
+    s0, s1, s2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+    s0.record(stream)
+    ed, ep = S.sanns_topk(ctx, cli1, srv1, k_sel)
+    s1.record(stream)
+    ad, ap = S.sanns_topk(ctx, cli1, srv1, k_sel, l_sel)
+    s2.record(stream)
+    torch.cuda.synchronize()
+    pts = torch.from_numpy(coords).cuda()[torch.from_numpy(perm.astype(np.int64)).cuda()]
+    brute = ((pts.int() - qdev[0].int()) ** 2).sum(1)
+    bv, _ = torch.sort(brute)
+    ex = set(ep[0].tolist())
+    selection = {
+        "k": k_sel, "bins": l_sel,
+        "exact_top10_equals_brute_force": bool(torch.equal(ed[0].long().sort().values,
+                                                           bv[:k_sel].long()))
+        and bool(torch.equal(brute[ep[0]].long(), ed[0].long())),
+        "approx_recall_vs_exact": len(ex & set(ap[0].tolist())) / k_sel,
+        "ms_exact": s0.elapsed_time(s1), "ms_approx": s1.elapsed_time(s2),
+    }
+    del pts, brute, out1, srv1, cli1
+
     # the same step with circuit privacy on (public-key re-randomisation and
     # noise flooding, F = 148: 108 bits of statistical privacy over a
     # structured noise below 2^40)
@@ -340,6 +369,7 @@ def run_gpu(args) -> None:
                     "d2h_bytes_per_step": K * 2 * L * N * 8 + n * 4, "ms_per_step": e2e_ms,
                     "timing": "host wall clock over pipelined steps (3 streams: upload, "
                               "compute, download)"},
+            "selection": selection,
             "circuit_privacy": {"ms_per_step": cp_ms, "flood_bits": flood, "steps": cp_steps,
                                 "value": world * n / (cp_ms * 1e-3), "unit": UNIT,
                                 "what": "public-key re-randomisation (one NTT per block per "
