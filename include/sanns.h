@@ -272,6 +272,19 @@ int sanns_autotune_batched(sanns_ctx *ctx, const sanns_db *db, const uint64_t *c
                            uint64_t *ct_out_dev, int reps, float *ms_out, void *stream);
 
 /*
+ * Response form.  0 (default): coefficient form, as the paper's protocol
+ * returns (the server transforms every response polynomial back).  1: NTT
+ * form, the NTT (per prime, the same negacyclic transform as the queries') of
+ * the coefficient-form response, bit for bit: the server skips both inverse
+ * transforms and adds NTT(Delta (||p||^2 + r)) to c0 (L forward transforms per
+ * block instead of 2L inverse ones), and sanns_decrypt_shares on a context in
+ * this form takes one inverse transform per block and prime.  Both sides of a
+ * protocol run must use the same form.  The gather path answers in
+ * coefficient form only and rejects calls while form 1 is set.
+ */
+int sanns_set_response_form(sanns_ctx *ctx, int form);
+
+/*
  * Plaintext meaning of the selection step (Sec. 4, Algorithms 1 and 2; the
  * paper evaluates it inside garbled circuits, which this library does not):
  * for every query b the k smallest reconstructed distances

@@ -169,6 +169,24 @@ class Oracle:
             self.flood(out, mask_seed, qid, k0, flood_bits)
         return out, share
 
+    # ---------------- response form ----------------
+    def to_ntt_form(self, ct_out: np.ndarray) -> np.ndarray:
+        """The NTT-form response: every polynomial [k][c][j] transformed."""
+        out = np.empty_like(ct_out)
+        for k in range(ct_out.shape[0]):
+            for c in range(2):
+                for j in range(self.L):
+                    out[k, c, j] = self.ntt(ct_out[k, c, j], j)
+        return out
+
+    def from_ntt_form(self, ct_ntt: np.ndarray) -> np.ndarray:
+        out = np.empty_like(ct_ntt)
+        for k in range(ct_ntt.shape[0]):
+            for c in range(2):
+                for j in range(self.L):
+                    out[k, c, j] = self.intt(ct_ntt[k, c, j], j)
+        return out
+
     # ---------------- circuit privacy ----------------
     def public_key(self, s_hat: np.ndarray, seed: int) -> np.ndarray:
         pk = np.zeros((2, self.L, self.N), dtype=np.uint64)

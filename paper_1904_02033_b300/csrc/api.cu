@@ -328,11 +328,23 @@ int sanns_distances_finish(sanns_ctx* ctx, const sanns_db* db, uint32_t B, uint6
   if (ctx->d_pk)
     SANNS_CUDA(launch_rerandomize(ctx->P, ct_out, B, db->K, db->pos0, mask_seed, qids, ctx->d_pk,
                                   ctx->d_pk_shoup, st));
+  if (ctx->ntt_responses) {
+    SANNS_CUDA(launch_mask_ntt(ctx->P, ct_out, db->d_norms, B, db->K, db->n, db->pos0, mask_seed, qids,
+                               srv_share, ctx->d_pk != nullptr, ctx->flood_bits, ctx->privacy, st));
+    return SANNS_OK;
+  }
   SANNS_CUDA(launch_intt_mask(ctx->P, ct_out, db->d_norms, B, db->K, db->n, db->pos0, mask_seed, qids,
                               srv_share, ctx->sms, st));
   if (ctx->d_pk)
     SANNS_CUDA(launch_flood(ctx->P, ct_out, B, db->K, db->pos0, mask_seed, qids, ctx->flood_bits,
                             ctx->privacy, st));
+  return SANNS_OK;
+}
+
+int sanns_set_response_form(sanns_ctx* ctx, int form) {
+  if (!ctx) return fail(SANNS_EINVAL, "ctx is NULL");
+  if (form != 0 && form != 1) return fail(SANNS_EINVAL, "form must be 0 (coefficients) or 1 (NTT)");
+  ctx->ntt_responses = form == 1;
   return SANNS_OK;
 }
 
@@ -560,6 +572,7 @@ int sanns_distances_gather(sanns_ctx* ctx, const sanns_clusters* cl, const uint6
   if (cl->ctx != ctx) return fail(SANNS_EINVAL, "clusters belong to another context");
   if (ctx->P.N > 8192) return fail(SANNS_EINVAL, "the gather path supports N <= 8192");
   if (ctx->d_pk) return fail(SANNS_EINVAL, "circuit privacy is not available on the gather path");
+  if (ctx->ntt_responses) return fail(SANNS_EINVAL, "the gather path returns coefficient-form responses only");
   if (B == 0) return SANNS_OK;
   if (!ct_in || !qids || !ct_out || !srv_share || !probes) return fail(SANNS_EINVAL, "NULL buffer");
   std::vector<uint64_t> nb(B), kb(B);
@@ -715,7 +728,7 @@ int sanns_decrypt_shares(sanns_ctx* ctx, const sanns_sk* sk, const uint64_t* ct_
   uint64_t* scratch = nullptr;
   SANNS_CUDA(cudaMallocAsync(&scratch, sizeof(uint64_t) * B * K * ctx->P.L * ctx->P.N, st));
   cudaError_t e = launch_decrypt(ctx->P, ct_out, sk->d_s, sk->d_s_hat, sk->d_s_hat_shoup, B, K, n, qv,
-                                 ctx->params.d, scratch, cli_share, st);
+                                 ctx->params.d, scratch, cli_share, ctx->ntt_responses, st);
   cudaError_t e2 = cudaFreeAsync(scratch, st);
   if (e != cudaSuccess) return cuda_fail(e, "decrypt kernels");
   if (e2 != cudaSuccess) return cuda_fail(e2, "cudaFreeAsync");

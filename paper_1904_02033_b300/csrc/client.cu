@@ -91,11 +91,12 @@ __global__ void __launch_bounds__(512) encrypt_kernel(PrimeSet P, const uint64_t
   }
 }
 
-// Decryption, first half: one block per (b, k, j): v = c0 + INTT(NTT(c1) s_hat).
+// Decryption, first half: one block per (b, k, j): v = c0 + INTT(NTT(c1) s_hat)
+// for coefficient-form responses, v = INTT(c0 + c1 s_hat) for NTT-form ones.
 __global__ void __launch_bounds__(512) decrypt_phase_kernel(PrimeSet P, const uint64_t* __restrict__ ct_out,
                                      const uint64_t* __restrict__ s_hat,
                                      const uint64_t* __restrict__ s_hat_shoup, uint64_t K,
-                                     uint64_t* __restrict__ v) {
+                                     uint64_t* __restrict__ v, int ntt_form) {
   extern __shared__ uint64_t sa[];
   const uint32_t N = P.N, L = P.L;
   const uint64_t idx = blockIdx.x;  // (b K + k) L + j
@@ -104,6 +105,18 @@ __global__ void __launch_bounds__(512) decrypt_phase_kernel(PrimeSet P, const ui
   const uint64_t q = P.q[j];
   const uint64_t* c0 = ct_out + ((bk * 2 + 0) * L + j) * N;
   const uint64_t* c1 = ct_out + ((bk * 2 + 1) * L + j) * N;
+  if (ntt_form) {
+    const uint64_t* sh = s_hat + (size_t)j * N;
+    const uint64_t* shs = s_hat_shoup + (size_t)j * N;
+    for (uint32_t x = threadIdx.x; x < N; x += blockDim.x)
+      sa[SP(x)] = add_mod(mul_shoup(c1[x], sh[x], shs[x], q), c0[x], q);
+    __syncthreads();
+    ntt_inverse_smem(sa, P, j);
+    __syncthreads();
+    uint64_t* o = v + idx * N;
+    for (uint32_t x = threadIdx.x; x < N; x += blockDim.x) o[x] = sa[SP(x)];
+    return;
+  }
   load_poly(sa, c1, N);
   __syncthreads();
   ntt_forward_smem(sa, P, j);
@@ -186,7 +199,7 @@ cudaError_t launch_encrypt(const PrimeSet& P, const uint64_t* s_hat, const uint6
 cudaError_t launch_decrypt(const PrimeSet& P, const uint64_t* ct_out, const int8_t* s,
                            const uint64_t* s_hat, const uint64_t* s_hat_shoup, uint32_t B,
                            uint64_t K, uint64_t n, const uint8_t* qv, uint32_t d,
-                           uint64_t* scratch, uint32_t* cli_share, cudaStream_t st) {
+                           uint64_t* scratch, uint32_t* cli_share, bool ntt_form, cudaStream_t st) {
   (void)s;
   if (B == 0 || n == 0) return cudaSuccess;
   const size_t smem = sizeof(uint64_t) * ntt_smem_words(P.N);
@@ -194,7 +207,7 @@ cudaError_t launch_decrypt(const PrimeSet& P, const uint64_t* ct_out, const int8
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   decrypt_phase_kernel<<<(unsigned)((uint64_t)B * K * P.L), blk_threads(P.N), smem, st>>>(
-      P, ct_out, s_hat, s_hat_shoup, K, scratch);
+      P, ct_out, s_hat, s_hat_shoup, K, scratch, ntt_form ? 1 : 0);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const uint64_t total = (uint64_t)B * n;

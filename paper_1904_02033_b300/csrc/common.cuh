@@ -124,6 +124,29 @@ __device__ __forceinline__ uint64_t mod_t128(uint64_t lo, uint64_t hi, const Pri
   return mod_t64(h * P.two64_mod_t + l, P.t, P.t_barrett);
 }
 
+// centred binomial, eta = 21, of the low 42 bits of a draw
+__device__ __forceinline__ int cbd21_of(uint64_t lo) {
+  const uint64_t m21 = (1ull << 21) - 1;
+  return __popcll(lo & m21) - __popcll((lo >> 21) & m21);
+}
+
+// Flooding term e1 = v - 2^F mod q for the 256-bit w[0] + w[1] 2^64 + ..,
+// keeping its low F + 1 bits (v); Horner over the 64-bit words with
+// qb = floor(2^64 / q), r64 = 2^64 mod q and two_f = 2^F mod q.
+__device__ __forceinline__ uint64_t flood_e1(uint64_t (&w)[4], uint32_t F, uint64_t q, uint64_t qb,
+                                             uint64_t r64, uint64_t r64s, uint64_t two_f) {
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int keep = (int)F + 1 - 64 * i;
+    if (keep <= 0) w[i] = 0;
+    else if (keep < 64) w[i] &= (1ull << keep) - 1;
+  }
+  uint64_t r = mod_t64(w[3], q, qb);
+#pragma unroll
+  for (int i = 2; i >= 0; --i) r = add_mod(mul_shoup(r, r64, r64s, q), mod_t64(w[i], q, qb), q);
+  return sub_mod(r, two_f, q);
+}
+
 // (hi 2^64 + lo) mod q for any q < 2^63 (not on the hot path).
 __device__ __forceinline__ uint64_t mod_q128(uint64_t lo, uint64_t hi, uint64_t q) {
   u128 v = ((u128)hi << 64) | lo;

@@ -24,6 +24,7 @@ struct sanns_ctx {
   uint64_t* d_pk_shoup;
   uint32_t flood_bits;
   sanns::PrivacyConsts privacy;
+  bool ntt_responses;       // responses in NTT form (server finish and client decryption)
 };
 
 struct sanns_sk {
@@ -84,6 +85,10 @@ cudaError_t launch_rerandomize(const PrimeSet& P, uint64_t* ct, uint32_t B, uint
 cudaError_t launch_flood(const PrimeSet& P, uint64_t* ct, uint32_t B, uint64_t K, uint64_t pos0,
                          uint64_t seed, const uint64_t* qids, uint32_t F, const PrivacyConsts& C,
                          cudaStream_t st);
+cudaError_t launch_mask_ntt(const PrimeSet& P, uint64_t* ct_out, const uint32_t* norms, uint32_t B,
+                            uint64_t K, uint64_t n, uint64_t pos0, uint64_t mask_seed, const uint64_t* qids,
+                            uint32_t* srv_share, bool privacy, uint32_t F, const PrivacyConsts& C,
+                            cudaStream_t st);
 cudaError_t launch_topk(const uint32_t* cli, const uint32_t* srv, uint32_t B, uint64_t n, uint64_t t,
                         uint32_t k, uint64_t bins, uint32_t* dist, uint64_t* pos, cudaStream_t st);
 cudaError_t launch_keygen(const PrimeSet& P, uint64_t seed, int8_t* s, uint64_t* s_hat,
@@ -122,6 +127,6 @@ cudaError_t launch_batched_mac(const PrimeSet& P, const void* map, const uint16_
 cudaError_t launch_decrypt(const PrimeSet& P, const uint64_t* ct_out, const int8_t* s,
                            const uint64_t* s_hat, const uint64_t* s_hat_shoup, uint32_t B,
                            uint64_t K, uint64_t n, const uint8_t* qv, uint32_t d,
-                           uint64_t* scratch, uint32_t* cli_share, cudaStream_t st);
+                           uint64_t* scratch, uint32_t* cli_share, bool ntt_form, cudaStream_t st);
 
 }  // namespace sanns

@@ -64,7 +64,8 @@ extern "C" int sanns_decrypt_shares_noalloc(sanns_ctx* ctx, const sanns_sk* sk, 
   // every scratch word the second phase reads is written by the first phase
   // of the same call, so nothing needs clearing between calls
   e = launch_decrypt(ctx->P, ct_out, sk->d_s, sk->d_s_hat, sk->d_s_hat_shoup, B, K, n, qv,
-                     ctx->params.d, scratch, cli_share, reinterpret_cast<cudaStream_t>(stream));
+                     ctx->params.d, scratch, cli_share, ctx->ntt_responses,
+                     reinterpret_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) return cuda_fail(e, "decrypt kernels");
   return SANNS_OK;
 }

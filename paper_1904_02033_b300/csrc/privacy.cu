@@ -18,11 +18,6 @@ namespace {
 
 __host__ __device__ inline uint32_t pv_threads(uint32_t N) { return N / 16 < 32 ? 32 : (N / 16 > 256 ? 256 : N / 16); }
 
-__device__ __forceinline__ int cbd21(uint64_t lo) {
-  const uint64_t m21 = (1ull << 21) - 1;
-  return __popcll(lo & m21) - __popcll((lo >> 21) & m21);
-}
-
 // One block per prime j: e (centred binomial, stream (seed, E_PK, 0)) lifted
 // and transformed; a uniform mod q_j drawn in NTT form from (seed, A_PK, j);
 // pk1 = a, pk0 = -a s_hat + e_hat slot by slot; layout pk[c][j][s].
@@ -39,7 +34,7 @@ __global__ void __launch_bounds__(256) public_key_kernel(PrimeSet P, const uint6
     for (int v = 0; v < 4; ++v) {
       uint64_t lo, hi;
       draw_pair(blk, v, lo, hi);
-      const int e = cbd21(lo);
+      const int e = cbd21_of(lo);
       sa[SP(4 * u + v)] = e < 0 ? q - (uint64_t)(-e) : (uint64_t)e;
     }
   }
@@ -142,23 +137,13 @@ __global__ void flood_kernel(PrimeSet P, uint64_t* __restrict__ ct, uint32_t B, 
     uint64_t w[4], lo, hi;
     draw_pair(ba, v, w[0], w[1]);
     draw_pair(bb, v, w[2], w[3]);
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const int keep = (int)F + 1 - 64 * i;
-      if (keep <= 0) w[i] = 0;
-      else if (keep < 64) w[i] &= (1ull << keep) - 1;
-    }
     draw_pair(be, v, lo, hi);
-    const int e2 = cbd21(lo);
+    const int e2 = cbd21_of(lo);
     const uint32_t x = x0 + v;
     for (uint32_t j = 0; j < L; ++j) {
-      const uint64_t q = P.q[j], qb = C.q_barrett[j];
-      // v mod q by Horner over the 64-bit words: r <- r 2^64 + w
-      uint64_t r = mod_t64(w[3], q, qb);
-#pragma unroll
-      for (int i = 2; i >= 0; --i)
-        r = add_mod(mul_shoup(r, P.r64[j], P.r64_shoup[j], q), mod_t64(w[i], q, qb), q);
-      const uint64_t e1 = sub_mod(r, C.two_f[j], q);
+      const uint64_t q = P.q[j];
+      uint64_t wj[4] = {w[0], w[1], w[2], w[3]};
+      const uint64_t e1 = flood_e1(wj, F, q, C.q_barrett[j], P.r64[j], P.r64_shoup[j], C.two_f[j]);
       uint64_t* c0 = ct + ((bk * 2 + 0) * L + j) * N + x;
       uint64_t* c1 = ct + ((bk * 2 + 1) * L + j) * N + x;
       *c0 = add_mod(*c0, e1, q);

@@ -315,6 +315,86 @@ __global__ void __launch_bounds__(256, 3) intt_mask_short_kernel(PrimeSet P, uin
   store_poly(g, sa, N);
 }
 
+// NTT-form responses: the response is the NTT of the coefficient-form one.
+// Since the transform is linear, c0 = acc0 + NTT(Delta_j v) with v = (||p||^2
+// + r) mod t per position, and c1 = acc1: one forward transform per (b, k, j)
+// instead of two inverse ones.  With circuit privacy (after the
+// re-randomisation in the NTT domain) e1 joins c0's transform and c1 gets
+// NTT(e2).  One block per (b, k, c, j), c < comps (1 without privacy, 2 with).
+__global__ void __launch_bounds__(256, 3) mask_ntt_kernel(PrimeSet P, uint64_t* __restrict__ ct_out,
+                                const uint32_t* __restrict__ norms, uint64_t K, uint64_t n,
+                                uint64_t pos0g, uint64_t mask_seed, const uint64_t* __restrict__ qids,
+                                const uint32_t* __restrict__ srv_share, uint32_t comps, int privacy,
+                                uint32_t F, PrivacyConsts C) {
+  extern __shared__ uint64_t sa[];
+  const uint32_t N = P.N, L = P.L;
+  const uint64_t idx = blockIdx.x;                  // ((b K + k) comps + c) L + j
+  const uint32_t j = (uint32_t)(idx % L);
+  const uint32_t c = (uint32_t)((idx / L) % comps);
+  const uint64_t bk = idx / ((uint64_t)L * comps);
+  const uint64_t k = bk % K, b = bk / K;
+  const uint64_t q = P.q[j], t = P.t;
+  const uint64_t qid = qids[b];
+  const uint32_t* sh = srv_share + b * n;
+  for (uint32_t u = threadIdx.x; u < N / 4; u += blockDim.x) {
+    const uint64_t p4 = k * N + 4 * u;             // first of four positions
+    uint64_t val[4] = {0, 0, 0, 0};
+    if (c == 0) {
+      uint64_t r[4];
+      if (p4 + 3 < n) {
+#pragma unroll
+        for (int v = 0; v < 4; ++v) r[v] = sh[p4 + v] == 0 ? 0 : t - sh[p4 + v];
+      } else {
+        uint32_t blk[16];
+        chacha20_block(mask_seed, kPurposeMask, qid, (uint32_t)((pos0g + p4) / 4), blk);
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+          uint64_t lo, hi;
+          draw_pair(blk, v, lo, hi);
+          r[v] = mod_t128(lo, hi, P);
+        }
+      }
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        const uint64_t m = mod_t64((uint64_t)norms[p4 + v] + r[v], t, P.t_barrett);
+        val[v] = mul_shoup(m, P.delta[j], P.delta_shoup[j], q);
+      }
+    }
+    if (privacy) {
+      const uint32_t ctr = (uint32_t)((pos0g + p4) / 4);
+      if (c == 0) {
+        uint32_t ba[16], bb[16];
+        chacha20_block(mask_seed, kPurposeFloodLo, qid, ctr, ba);
+        chacha20_block(mask_seed, kPurposeFloodHi, qid, ctr, bb);
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+          uint64_t w[4];
+          draw_pair(ba, v, w[0], w[1]);
+          draw_pair(bb, v, w[2], w[3]);
+          val[v] = add_mod(val[v], flood_e1(w, F, q, C.q_barrett[j], P.r64[j], P.r64_shoup[j], C.two_f[j]), q);
+        }
+      } else {
+        uint32_t be[16];
+        chacha20_block(mask_seed, kPurposeE2, qid, ctr, be);
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+          uint64_t lo, hi;
+          draw_pair(be, v, lo, hi);
+          const int e2 = cbd21_of(lo);
+          val[v] = e2 < 0 ? q - (uint64_t)(-e2) : (uint64_t)e2;
+        }
+      }
+    }
+#pragma unroll
+    for (int v = 0; v < 4; ++v) sa[SP(4 * u + v)] = val[v];
+  }
+  __syncthreads();
+  ntt_forward_smem(sa, P, j);
+  __syncthreads();
+  uint64_t* g = ct_out + ((bk * 2 + c) * L + j) * N;
+  for (uint32_t x = threadIdx.x; x < N; x += blockDim.x) g[x] = add_mod(g[x], sa[SP(x)], q);
+}
+
 }  // namespace
 
 cudaError_t launch_ntt(const PrimeSet& P, uint64_t* data, uint64_t count, bool inverse,
@@ -375,6 +455,32 @@ cudaError_t launch_intt_mask(const PrimeSet& P, uint64_t* ct_out, const uint32_t
   else
     intt_mask_kernel<<<(unsigned)polys, ntt_threads(P.N), smem, st>>>(P, ct_out, norms, K, n, pos0,
                                                                       mask_seed, qids, srv_share);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mask_ntt(const PrimeSet& P, uint64_t* ct_out, const uint32_t* norms, uint32_t B,
+                            uint64_t K, uint64_t n, uint64_t pos0, uint64_t mask_seed, const uint64_t* qids,
+                            uint32_t* srv_share, bool privacy, uint32_t F, const PrivacyConsts& C,
+                            cudaStream_t st) {
+  const uint32_t comps = privacy ? 2 : 1;
+  const uint64_t polys = (uint64_t)B * K * comps * P.L;
+  if (polys == 0) return cudaSuccess;
+  const uint64_t groups = (uint64_t)B * ((n + 3) / 4);
+  mask_share_kernel<<<(unsigned)((groups + 255) / 256), 256, 0, st>>>(P, B, n, pos0, mask_seed,
+                                                                     qids, srv_share);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const size_t smem = sizeof(uint64_t) * ntt_smem_words(P.N);
+  static bool configured = false;
+  if (!configured) {
+    e = cudaFuncSetAttribute(mask_ntt_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(sizeof(uint64_t) * ntt_smem_words(kMaxN)));
+    if (e != cudaSuccess) return e;
+    configured = true;
+  }
+  mask_ntt_kernel<<<(unsigned)polys, ntt_threads(P.N), smem, st>>>(P, ct_out, norms, K, n, pos0, mask_seed,
+                                                                   qids, srv_share, comps, privacy ? 1 : 0,
+                                                                   F, C);
   return cudaGetLastError();
 }
 

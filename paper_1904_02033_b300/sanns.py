@@ -63,6 +63,7 @@ _SIGS = {
     "sanns_autotune_mac": ([_VP, _VP, _VP, C.c_uint32, _VP, C.c_int, _VP, _VP], C.c_int),
     "sanns_autotune_batched": ([_VP, _VP, _VP, C.c_uint32, _VP, C.c_int, _VP, _VP], C.c_int),
     "sanns_public_key": ([_VP, _VP, C.c_uint64, _VP, _VP], C.c_int),
+    "sanns_set_response_form": ([_VP, C.c_int], C.c_int),
     "sanns_topk": ([_VP, _VP, _VP, C.c_uint32, C.c_uint64, C.c_uint32, C.c_uint64, _VP, _VP, _VP],
                    C.c_int),
     "sanns_circuit_privacy_max_flood_bits": ([_VP], C.c_int),
@@ -377,6 +378,11 @@ def sanns_autotune_mac(ctx: Context, db: Database, ct_in: torch.Tensor, ct_out: 
     if rc < 0:
         _check(rc)
     return rc, list(ms)
+
+
+def sanns_set_response_form(ctx: Context, ntt: bool):
+    """Responses in NTT form (True) or coefficient form (False, default)."""
+    _check(load().sanns_set_response_form(ctx.handle, 1 if ntt else 0))
 
 
 def sanns_topk(ctx: Context, cli_share: torch.Tensor, srv_share: torch.Tensor, k: int,
