@@ -61,12 +61,15 @@ static_assert(kProdThreads == kQG * 8, "one (row group, dimension) item per prod
 constexpr int kEpiWarp0 = kProdWarp0 + kProdWarps;    // 10
 constexpr int kEpiWarps = 8;                          // two per TMEM lane quarter
 constexpr int kThreads = 32 * (kEpiWarp0 + kEpiWarps);  // 576
+// stages + the epilogue's held first slot of a pair (16 outputs per thread)
+constexpr int kSmem1 = kStages * kStageBytes + 16 * 32 * kEpiWarps * 8 + 1024;
 constexpr unsigned long long kWaitCycles = 4ull << 30;  // ~2 s at 2 GHz
 
 struct BatchArgs {
   const uint64_t* xm;     // query multiples of the slot range, layout of expand_query_kernel
   uint32_t s_begin, s_count;
   uint64_t* out;          // [B][K][2][L][N]
+  uint32_t out16;         // out is 16-byte aligned (paired stores)
   int* err;               // device error word
   uint32_t B, d, dpad, K;
   uint32_t QT, KT, chunks;
@@ -230,10 +233,9 @@ __device__ __forceinline__ void store_digit_rows(uint8_t* at, uint32_t bcl, uint
 // One 32-column TMEM load of the epilogue: columns (bc, a) with a fastest hold
 // the 8 digit sums of 4 outputs.  Exact combination: lo = sum_{a<4} S_a 256^a
 // and hi = sum_{a>=4} S_a 256^(a-4) (both below 2^49 in magnitude), acc = lo +
-// hi 2^32 mod q; bc0 = the (b, c) row of the first of the 4 outputs.
-__device__ __forceinline__ void epilogue_chunk(uint32_t taddr, const BatchArgs& A, const PrimeSet& P,
-                                               const Decoded& D, uint32_t k, bool k_ok,
-                                               uint32_t bc0) {
+// hi 2^32 mod q, returned in res[0 .. 3].
+__device__ __forceinline__ void epilogue_values(uint32_t taddr, const BatchArgs& A, const PrimeSet& P,
+                                                const Decoded& D, uint64_t (&res)[4]) {
   uint32_t v[32];
   asm volatile(
       "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, "
@@ -250,7 +252,6 @@ __device__ __forceinline__ void epilogue_chunk(uint32_t taddr, const BatchArgs& 
   const uint64_t q = P.q[D.j], mu = A.mu64[D.j];
   const int64_t bias = (int64_t)A.lo_bias[D.j];
   const uint64_t w32 = A.w32[D.j], w32s = A.w32_shoup[D.j];
-  const uint32_t N = P.N, L = P.L;
 #pragma unroll
   for (int o = 0; o < 4; ++o) {
     int32_t sa[8];
@@ -263,13 +264,46 @@ __device__ __forceinline__ void epilogue_chunk(uint32_t taddr, const BatchArgs& 
     // |lo|, |hi| < 2^49 <= bias: both biased values are positive and below
     // 2^50 + q; hi 2^32 lazily below 2q, the sum below 2^64
     const uint64_t hs = mul_shoup_lazy((uint64_t)(hi + bias), w32, w32s, q);
-    const uint64_t res = mod_t64(hs + (uint64_t)(lo + bias), q, mu);
+    res[o] = mod_t64(hs + (uint64_t)(lo + bias), q, mu);
+  }
+}
+
+// epilogue_values, then one 8-byte store per output of slot D.s; bc0 = the
+// (b, c) row of the first of the 4 outputs.
+__device__ __forceinline__ void epilogue_chunk(uint32_t taddr, const BatchArgs& A, const PrimeSet& P,
+                                               const Decoded& D, uint32_t k, bool k_ok,
+                                               uint32_t bc0) {
+  uint64_t res[4];
+  epilogue_values(taddr, A, P, D, res);
+  const uint32_t N = P.N, L = P.L;
+#pragma unroll
+  for (int o = 0; o < 4; ++o) {
     const uint32_t bc = bc0 + o;
     if (k_ok && bc < 2 * A.B) {
       const uint32_t b = bc >> 1, c = bc & 1;
-      A.out[((((uint64_t)b * A.K + k) * 2 + c) * L + D.j) * N + D.s] = res;
+      A.out[((((uint64_t)b * A.K + k) * 2 + c) * L + D.j) * N + D.s] = res[o];
     }
   }
+}
+
+// Unit m of this CTA for the single-SM tile: pairs of slots, both halves back
+// to back, so the epilogue can store both slots of an output as one 16-byte
+// word.  Pair p = blockIdx.x + (m / 2) gridDim.x over A.units pairs, decoded
+// as ((j S/2 + s'/2) KT + kt) QT + qt; half m % 2 gives slot s' = 2 (s'/2) +
+// m % 2.  False past the last pair.
+__device__ __forceinline__ bool unit_of(uint32_t m, const BatchArgs& A, Decoded& D) {
+  const uint64_t p = blockIdx.x + (uint64_t)(m >> 1) * gridDim.x;
+  if (p >= A.units) return false;
+  const uint32_t half = A.s_count >> 1;
+  uint32_t r = (uint32_t)p;
+  D.qt = r % A.QT;
+  r /= A.QT;
+  D.kt = r % A.KT;
+  r /= A.KT;
+  D.sl = 2 * (r % half) + (m & 1);
+  D.s = A.s_begin + D.sl;
+  D.j = r / half;
+  return true;
 }
 
 __global__ void __launch_bounds__(kThreads, 1)
@@ -312,13 +346,12 @@ batched_mac_kernel(const __grid_constant__ CUtensorMap pmap, PrimeSet P, BatchAr
     // the whole warp walks the loop (converged); lane 0 waits and issues
     uint64_t g = 0;
     bool ok = true;
-    for (uint64_t u = blockIdx.x; u < A.units && ok; u += gridDim.x) {
-      const Decoded D = decode_unit((uint32_t)u, P.logN, A);
-      const uint64_t pu = u + (uint64_t)A.prefetch_units * gridDim.x;
-      if (lane == 0 && A.prefetch_units && pu < A.units) {
+    for (uint32_t m = 0; ok; ++m) {
+      Decoded D, F;
+      if (!unit_of(m, A, D)) break;
+      if (lane == 0 && A.prefetch_units && unit_of(m + 2 * A.prefetch_units, A, F)) {
         // database tile (rows kt*128 .. of slot (j, s)) and query multiples
         // (row groups qt*32 .. of slot (j, s')) of a later unit of this CTA
-        const Decoded F = decode_unit((uint32_t)pu, P.logN, A);
         const uint32_t rows = A.K - F.kt * kBM < (uint32_t)kBM ? A.K - F.kt * kBM : (uint32_t)kBM;
         prefetch_l2(A.plimb + (((uint64_t)F.j * N + F.s) * A.K + (uint64_t)F.kt * kBM) * 8 * A.dpad,
                     rows * 16u * A.dpad);
@@ -355,10 +388,12 @@ batched_mac_kernel(const __grid_constant__ CUtensorMap pmap, PrimeSet P, BatchAr
   } else if (warp == 1) {
     // ---------------- MMA issuer ----------------
     // the whole warp walks the loop (converged); lane 0 waits and issues
-    uint64_t g = 0, r = 0;
+    uint64_t g = 0;
     bool ok = true;
-    for (uint64_t u = blockIdx.x; u < A.units && ok; u += gridDim.x, ++r) {
-      const uint32_t slot = (uint32_t)(r & 1), aph = (uint32_t)((r >> 1) & 1);
+    for (uint32_t m = 0; ok; ++m) {
+      Decoded D;
+      if (!unit_of(m, A, D)) break;
+      const uint32_t slot = m & 1, aph = (m >> 1) & 1;
       bool ready = true;
       if (lane == 0) ready = mbar_wait(smem_u32(&bar_tempty[slot]), aph ^ 1, &abort_flag, A.err, A.sleep_mma);
       if (!__shfl_sync(0xffffffffu, (int)ready, 0)) break;
@@ -394,13 +429,13 @@ batched_mac_kernel(const __grid_constant__ CUtensorMap pmap, PrimeSet P, BatchAr
     // v, exact) and one f16x2 subtraction of 1152 leaves the digits.
     const uint32_t pt = threadIdx.x - 32 * kProdWarp0;   // one (b, c, dim) item per thread
     const uint32_t bcl = pt >> 3, il = pt & 7;             // (b, c) row group in tile, dim in chunk
-    const uint32_t units = (uint32_t)A.units, chunks = A.chunks;
+    const uint32_t chunks = A.chunks;
     const uint32_t twoB = 2 * A.B;
-    // this thread's item in dimension block 0 of unit u (null past the units
-    // or past 2B: such an item reads Y_b = 0x80.., all digits zero)
-    auto unit_base = [&](uint32_t u) -> const ulonglong2* {
-      if (u >= units) return nullptr;
-      const Decoded D = decode_unit(u, P.logN, A);
+    // this thread's item in dimension block 0 of the CTA's unit m (null past
+    // the units or past 2B: such an item reads Y_b = 0x80.., all digits zero)
+    auto unit_base = [&](uint32_t m) -> const ulonglong2* {
+      Decoded D;
+      if (!unit_of(m, A, D)) return nullptr;
       const uint32_t bc = D.qt * kQG + bcl;
       if (bc >= twoB) return nullptr;
       return reinterpret_cast<const ulonglong2*>(A.xm) +
@@ -415,10 +450,10 @@ batched_mac_kernel(const __grid_constant__ CUtensorMap pmap, PrimeSet P, BatchAr
     // Each warp fills its own 32 items (4 row groups x 8 dims) of every stage
     // and arrives on the stage's barrier itself, so warps run ahead of one
     // another; values are prefetched two chunks ahead.
-    uint32_t fu = blockIdx.x, fk = 0;
-    const ulonglong2* fb = unit_base(fu);
+    uint32_t fm = 0, fk = 0;
+    const ulonglong2* fb = unit_base(fm);
     auto advance = [&]() {
-      if (++fk == chunks) { fk = 0; fu += gridDim.x; fb = unit_base(fu); }
+      if (++fk == chunks) { fk = 0; ++fm; fb = unit_base(fm); }
     };
     ulonglong2 nx0[4], nx1[4];
     load_item(fb, fk, nx0);
@@ -426,8 +461,10 @@ batched_mac_kernel(const __grid_constant__ CUtensorMap pmap, PrimeSet P, BatchAr
     load_item(fb, fk, nx1);
     advance();
     uint64_t g = 0;
-    uint32_t cu = blockIdx.x, ck = 0;
-    while (cu < units) {
+    uint32_t cm = 0, ck = 0;
+    Decoded Dc;
+    bool have = unit_of(0, A, Dc);
+    while (have) {
       ulonglong2 cur[4];
 #pragma unroll
       for (int h = 0; h < 4; ++h) { cur[h] = nx0[h]; nx0[h] = nx1[h]; }
@@ -443,26 +480,56 @@ batched_mac_kernel(const __grid_constant__ CUtensorMap pmap, PrimeSet P, BatchAr
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       __syncwarp();
       if (lane == 0) mbar_arrive(smem_u32(&bar_full[st]));
-      if (++ck == chunks) { ck = 0; cu += gridDim.x; }
+      if (++ck == chunks) { ck = 0; ++cm; have = unit_of(cm, A, Dc); }
     }
   } else {
     // ---------------- epilogue ----------------
-    // Lane = database block k of the tile (see epilogue_chunk).
+    // Lane = database block k of the tile (see epilogue_values).  The first
+    // slot of a pair is held in registers until the second one is done, then
+    // both go out as one 16-byte word per output.
     const uint32_t quarter = warp & 3;            // TMEM lanes 32 quarter ..
     const uint32_t chalf = (warp - kEpiWarp0) >> 2;  // column half of the tile
-    uint64_t r = 0;
-    for (uint64_t u = blockIdx.x; u < A.units && !abort_flag; u += gridDim.x, ++r) {
-      const uint32_t slot = (uint32_t)(r & 1), aph = (uint32_t)((r >> 1) & 1);
+    const uint32_t N = P.N, L = P.L;
+    // the pair's first slot, [output i][epilogue thread] (conflict-free)
+    uint64_t* held = reinterpret_cast<uint64_t*>(base + kStages * kStageBytes);
+    const uint32_t et = threadIdx.x - 32 * kEpiWarp0;
+    for (uint32_t m = 0; !abort_flag; ++m) {
+      Decoded D;
+      if (!unit_of(m, A, D)) break;
+      const uint32_t slot = m & 1, aph = (m >> 1) & 1;
       // lane 0 waits for the accumulator, the warp follows its decision
       bool ready = true;
       if (lane == 0) ready = mbar_wait(smem_u32(&bar_tfull[slot]), aph, &abort_flag, A.err, A.sleep_epi);
       if (!__shfl_sync(0xffffffffu, (int)ready, 0)) break;
       tc_fence_after();
-      const Decoded D = decode_unit((uint32_t)u, P.logN, A);
       const uint32_t k = D.kt * kBM + quarter * 32 + lane;
-      for (uint32_t cc = chalf * (kBN / 64); cc < (chalf + 1) * (kBN / 64); ++cc)
-        epilogue_chunk(tmem + ((quarter * 32) << 16) + slot * kBN + cc * 32, A, P, D, k, k < A.K,
-                       D.qt * kQG + cc * 4);
+      const bool k_ok = k < A.K;
+#pragma unroll
+      for (uint32_t ci = 0; ci < 4; ++ci) {
+        const uint32_t cc = chalf * 4 + ci;
+        uint64_t res[4];
+        epilogue_values(tmem + ((quarter * 32) << 16) + slot * kBN + cc * 32, A, P, D, res);
+        if (slot == 0) {
+#pragma unroll
+          for (int o = 0; o < 4; ++o) held[(ci * 4 + o) * (32 * kEpiWarps) + et] = res[o];
+        } else {
+#pragma unroll
+          for (int o = 0; o < 4; ++o) {
+            const uint32_t bc = D.qt * kQG + cc * 4 + o;
+            if (k_ok && bc < 2 * A.B) {
+              const uint32_t b = bc >> 1, c = bc & 1;
+              uint64_t* dst = A.out + ((((uint64_t)b * A.K + k) * 2 + c) * L + D.j) * N + D.s - 1;
+              const uint64_t h = held[(ci * 4 + o) * (32 * kEpiWarps) + et];
+              if (A.out16) {
+                *reinterpret_cast<ulonglong2*>(dst) = make_ulonglong2(h, res[o]);
+              } else {
+                dst[0] = h;
+                dst[1] = res[o];
+              }
+            }
+          }
+        }
+      }
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(smem_u32(&bar_tempty[slot]));
@@ -981,6 +1048,7 @@ cudaError_t launch_batched_mac(const PrimeSet& P, const void* map, const uint16_
   A.prefetch_units = tune[4];
   A.plimb = plimb;
   A.out = out;
+  A.out16 = (reinterpret_cast<uintptr_t>(out) & 15) == 0 ? 1u : 0u;
   A.err = err;
   A.B = B;
   A.d = d;
@@ -1011,9 +1079,10 @@ cudaError_t launch_batched_mac(const PrimeSet& P, const void* map, const uint16_
   // least one slot)
   const uint64_t per_slot = (uint64_t)P.L * 2 * B * A.dpad * 8 * sizeof(uint64_t);
   uint64_t S = ((uint64_t)tune[5] << 20) / per_slot;
-  if (S < 1) S = 1;
+  S &= ~1ull;                 // the single-SM tile takes slots in pairs
+  if (S < 2) S = 2;
   if (S > P.N) S = P.N;
-  const size_t smem = use_pair ? (size_t)pair::kSmem : (size_t)kStages * kStageBytes + 1024;
+  const size_t smem = use_pair ? (size_t)pair::kSmem : (size_t)kSmem1;
   // kernel attributes and the number of co-resident CTA pairs (clusters of 2
   // need two SMs of one GPC) are set up once per device, outside any capture
   int dev = 0;
@@ -1031,7 +1100,7 @@ cudaError_t launch_batched_mac(const PrimeSet& P, const void* map, const uint16_
                                (int)pair::kSmem);
       if (e == cudaSuccess)
         e = cudaFuncSetAttribute(batched_mac_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)((size_t)kStages * kStageBytes + 1024));
+                                 (int)kSmem1);
       if (e != cudaSuccess) return e;
       cudaLaunchConfig_t cfg = {};
       cfg.gridDim = dim3(2 * (unsigned)(sms > 0 ? sms / 2 : 74));
@@ -1054,7 +1123,8 @@ cudaError_t launch_batched_mac(const PrimeSet& P, const void* map, const uint16_
     A.s_begin = (uint32_t)s0;
     A.s_count = cnt;
     A.xm = scratch;
-    A.units = (uint64_t)P.L * cnt * A.KT * A.QT;
+    // tile 0 counts slot pairs (both halves in one CTA), tile 1 single slots
+    A.units = (uint64_t)P.L * (use_pair ? cnt : cnt / 2) * A.KT * A.QT;
     if (A.units >= (1ull << 31)) { e = cudaErrorInvalidValue; break; }
     expand_query_kernel<<<dim3((cnt + 31) / 32, A.dpad / 8, P.L * 2 * B), 256, 0, st>>>(
         P, ct, B, d, A.dpad, (uint32_t)s0, cnt, W,
