@@ -288,19 +288,24 @@ int sanns_set_response_form(sanns_ctx *ctx, int form);
  * Plaintext meaning of the selection step (Sec. 4, Algorithms 1 and 2; the
  * paper evaluates it inside garbled circuits, which this library does not):
  * for every query b the k smallest reconstructed distances
- * (cli_dev[b][x] + srv_dev[b][x]) mod t over positions x < n.
+ * ((cli_dev[b][x] + srv_dev[b][x]) mod t) >> shift over positions x < n
+ * (shift <= 31: Algorithm 4 truncates distances by 2^r_c or 2^r_p before
+ * selecting).
  *   bins = 0:  exact, the k smallest (distance, position) pairs in that order,
  *              which is the result Algorithm 1 (NaiveTopk) produces.
  *   bins = l:  Algorithm 2 (ApproxTopk): position x falls in bin
  *              floor(x l / n); the minimum of every bin (the earlier position
  *              on ties), then the k smallest of the l minima.
  * Output (device, caller-owned): dist_dev [B][k] u32 ascending, pos_dev
- * [B][k] u64 positions (in the server's permuted order).  Needs 1 <= k <= 32,
- * k <= n < 2^32 and, for l > 0, k <= l <= n; SANNS_EINVAL otherwise.
+ * [B][k] u64 positions (in the server's permuted order).  Needs 1 <= k <=
+ * 1024, B <= 65535, k <= n < 2^32 and, for l > 0, k <= l <= n; SANNS_EINVAL
+ * otherwise.  k <= 32 keeps per-thread register lists; larger k sorts chunks
+ * of 4096 keys in shared memory.
  * Asynchronous on stream (stream-ordered scratch).
  */
 int sanns_topk(sanns_ctx *ctx, const uint32_t *cli_dev, const uint32_t *srv_dev, uint32_t B, uint64_t n,
-               uint32_t k, uint64_t bins, uint32_t *dist_dev, uint64_t *pos_dev, void *stream);
+               uint32_t k, uint64_t bins, uint32_t shift, uint32_t *dist_dev, uint64_t *pos_dev,
+               void *stream);
 
 /*
  * Circuit privacy (Sec. 2, "Additive Homomorphic Encryption": the AHE scheme

@@ -349,16 +349,18 @@ int sanns_set_response_form(sanns_ctx* ctx, int form) {
 }
 
 int sanns_topk(sanns_ctx* ctx, const uint32_t* cli, const uint32_t* srv, uint32_t B, uint64_t n,
-               uint32_t k, uint64_t bins, uint32_t* dist, uint64_t* pos, void* stream) {
+               uint32_t k, uint64_t bins, uint32_t shift, uint32_t* dist, uint64_t* pos, void* stream) {
   if (!ctx) return fail(SANNS_EINVAL, "ctx is NULL");
   if (B == 0) return SANNS_OK;
   if (!cli || !srv || !dist || !pos) return fail(SANNS_EINVAL, "NULL buffer");
-  if (k < 1 || k > 32) return fail(SANNS_EINVAL, "k must be in [1, 32]");
+  if (k < 1 || k > kTopkLarge) return fail(SANNS_EINVAL, "k must be in [1, 1024]");
+  if (B > 65535) return fail(SANNS_EINVAL, "B must be <= 65535");
   if (n < k || n >= (1ull << 32)) return fail(SANNS_EINVAL, "need k <= n < 2^32");
   if (bins && (bins < k || bins > n)) return fail(SANNS_EINVAL, "need k <= bins <= n");
+  if (shift > 31) return fail(SANNS_EINVAL, "shift must be <= 31");
   int rc = check_device(ctx);
   if (rc) return rc;
-  SANNS_CUDA(launch_topk(cli, srv, B, n, ctx->P.t, k, bins, dist, pos, as_stream(stream)));
+  SANNS_CUDA(launch_topk(cli, srv, B, n, ctx->P.t, k, bins, shift, dist, pos, as_stream(stream)));
   return SANNS_OK;
 }
 

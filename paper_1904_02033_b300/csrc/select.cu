@@ -1,6 +1,8 @@
 // Plaintext meaning of the selection step (the paper evaluates it inside
 // garbled circuits, which stay out of scope): the k smallest reconstructed
-// distances dist = (client share + server share) mod t of every query.
+// distances dist = ((client share + server share) mod t) >> r of every query
+// (r: the paper's truncation of distances before selection, r_c for cluster
+// centres and r_p for points, Algorithm 4).
 //   exact:        the k smallest (value, position) pairs (the order of
 //                 Algorithm 1, NaiveTopk, which never lets a later equal value
 //                 displace an earlier one)
@@ -15,9 +17,12 @@ namespace sanns {
 
 namespace {
 
-constexpr int kTopkMax = 32;
+constexpr int kTopkMax = 32;     // register lists (k <= kTopkMax)
 constexpr int kTopkThreads = 256;
 constexpr uint64_t kNoKey = ~0ull;
+constexpr int kSortKeys = 4096;   // keys a block sorts in shared memory (larger k)
+constexpr int kSortThreads = 512;
+static_assert(kTopkLarge * 4 <= kSortKeys, "a sort pass must shrink the keys at least 4x");
 
 // A thread keeps its kTopkMax smallest keys, ascending (at least the k the
 // block needs, k <= kTopkMax; static indices keep the list in registers).
@@ -75,7 +80,8 @@ __device__ void topk_block_merge(uint64_t (&best)[kTopkMax], int k, uint64_t* ou
 __global__ void __launch_bounds__(kTopkThreads) topk_shares_kernel(const uint32_t* __restrict__ cli,
                                                                    const uint32_t* __restrict__ srv,
                                                                    uint64_t n, uint64_t t, int k,
-                                                                   uint64_t chunk, uint64_t* part) {
+                                                                   uint64_t chunk, uint32_t shift,
+                                                                   uint64_t* part) {
   const uint64_t b = blockIdx.y, c = blockIdx.x;
   uint64_t best[kTopkMax];
 #pragma unroll
@@ -85,7 +91,7 @@ __global__ void __launch_bounds__(kTopkThreads) topk_shares_kernel(const uint32_
   const uint32_t* ss = srv + b * n;
   for (uint64_t p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
     uint64_t v = (uint64_t)cs[p] + ss[p];
-    v = v >= t ? v - t : v;
+    v = (v >= t ? v - t : v) >> shift;
     const uint64_t key = (v << 32) | p;
     if (key < best[kTopkMax - 1]) topk_insert(best, key);
   }
@@ -97,7 +103,7 @@ __global__ void __launch_bounds__(kTopkThreads) topk_shares_kernel(const uint32_
 __global__ void __launch_bounds__(kTopkThreads) bin_min_kernel(const uint32_t* __restrict__ cli,
                                                                const uint32_t* __restrict__ srv,
                                                                uint64_t n, uint64_t t, uint64_t l,
-                                                               uint64_t* mins) {
+                                                               uint32_t shift, uint64_t* mins) {
   const uint64_t b = blockIdx.y;
   const uint64_t i = blockIdx.x * (uint64_t)(blockDim.x / 32) + (threadIdx.x >> 5);
   const uint32_t lane = threadIdx.x & 31;
@@ -108,7 +114,7 @@ __global__ void __launch_bounds__(kTopkThreads) bin_min_kernel(const uint32_t* _
   uint64_t m = kNoKey;
   for (uint64_t p = p0 + lane; p < p1; p += 32) {
     uint64_t v = (uint64_t)cs[p] + ss[p];
-    v = v >= t ? v - t : v;
+    v = (v >= t ? v - t : v) >> shift;
     const uint64_t key = (v << 32) | p;
     m = key < m ? key : m;
   }
@@ -138,6 +144,54 @@ __global__ void __launch_bounds__(kTopkThreads) topk_keys_kernel(const uint64_t*
   topk_block_merge(best, k, part + (b * gridDim.x + c) * k);
 }
 
+// Larger k (kTopkMax < k <= kTopkLarge): block (chunk c, query b) sorts
+// kSortKeys keys in shared memory (bitonic network, ascending) and keeps the
+// first k in part[b][c][0 .. k-1].  The keys come from the shares
+// (kFromShares, positions [c kSortKeys, (c + 1) kSortKeys) of n) or from a
+// key array of m keys per query; missing keys past the end sort last.
+template <bool kFromShares>
+__global__ void __launch_bounds__(kSortThreads) topk_sort_kernel(const uint64_t* __restrict__ keys,
+                                                                 const uint32_t* __restrict__ cli,
+                                                                 const uint32_t* __restrict__ srv,
+                                                                 uint64_t m, uint64_t t,
+                                                                 uint32_t shift, int k,
+                                                                 uint64_t* part) {
+  __shared__ uint64_t s[kSortKeys];
+  const uint64_t b = blockIdx.y, c = blockIdx.x;
+  const uint64_t p0 = c * kSortKeys;
+  for (int i = threadIdx.x; i < kSortKeys; i += kSortThreads) {
+    const uint64_t p = p0 + i;
+    uint64_t key = kNoKey;
+    if (p < m) {
+      if (kFromShares) {
+        uint64_t v = (uint64_t)cli[b * m + p] + srv[b * m + p];
+        v = (v >= t ? v - t : v) >> shift;
+        key = (v << 32) | p;
+      } else {
+        key = keys[b * m + p];
+      }
+    }
+    s[i] = key;
+  }
+  __syncthreads();
+  for (int size = 2; size <= kSortKeys; size <<= 1) {
+    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+      for (int i = threadIdx.x; i < kSortKeys / 2; i += kSortThreads) {
+        const int lo = 2 * i - (i & (stride - 1));  // the pair (lo, lo + stride), lo's stride bit clear
+        const int hi = lo + stride;
+        const bool up = (lo & size) == 0;
+        const uint64_t x = s[lo], y = s[hi];
+        if ((x > y) == up) {
+          s[lo] = y;
+          s[hi] = x;
+        }
+      }
+      __syncthreads();
+    }
+  }
+  for (int r = threadIdx.x; r < k; r += kSortThreads) part[(b * gridDim.x + c) * k + r] = s[r];
+}
+
 // Split the keys: dist[b][r] = key >> 32, pos[b][r] = key & (2^32 - 1).
 __global__ void topk_split_kernel(const uint64_t* __restrict__ keys, uint64_t count,
                                   uint32_t* __restrict__ dist, uint64_t* __restrict__ pos) {
@@ -145,6 +199,26 @@ __global__ void topk_split_kernel(const uint64_t* __restrict__ keys, uint64_t co
   if (e >= count) return;
   dist[e] = (uint32_t)(keys[e] >> 32);
   pos[e] = keys[e] & 0xffffffffull;
+}
+
+// The same with the shared-memory sort passes (k > kTopkMax).
+cudaError_t reduce_keys_sorted(const uint64_t* keys, uint32_t B, uint64_t m, int k, uint64_t* a,
+                               uint64_t* b, const uint64_t** res, cudaStream_t st) {
+  const uint64_t* src = keys;
+  uint64_t* dst = a;
+  while (true) {
+    const uint64_t chunks = (m + kSortKeys - 1) / kSortKeys;
+    topk_sort_kernel<false><<<dim3((unsigned)chunks, B), kSortThreads, 0, st>>>(src, nullptr, nullptr,
+                                                                              m, 0, 0, k, dst);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    m = chunks * (uint64_t)k;
+    src = dst;
+    dst = dst == a ? b : a;
+    if (chunks == 1) break;
+  }
+  *res = src;
+  return cudaSuccess;
 }
 
 // k smallest of m keys per query, B queries, through chunked passes into
@@ -171,8 +245,10 @@ cudaError_t reduce_keys(const uint64_t* keys, uint32_t B, uint64_t m, int k, uin
 }  // namespace
 
 cudaError_t launch_topk(const uint32_t* cli, const uint32_t* srv, uint32_t B, uint64_t n, uint64_t t,
-                        uint32_t k, uint64_t bins, uint32_t* dist, uint64_t* pos, cudaStream_t st) {
-  const uint64_t chunk = 1 << 16;
+                        uint32_t k, uint64_t bins, uint32_t shift, uint32_t* dist, uint64_t* pos,
+                        cudaStream_t st) {
+  const bool large = k > (uint32_t)kTopkMax;
+  const uint64_t chunk = large ? kSortKeys : 1 << 16;
   const uint64_t first = bins ? bins : (n + chunk - 1) / chunk * k;  // keys per query after pass 1
   const uint64_t words = 2 * (uint64_t)B * (first + 64);
   uint64_t* scratch = nullptr;
@@ -183,15 +259,20 @@ cudaError_t launch_topk(const uint32_t* cli, const uint32_t* srv, uint32_t B, ui
   if (bins) {
     const unsigned per_block = kTopkThreads / 32;
     bin_min_kernel<<<dim3((unsigned)((bins + per_block - 1) / per_block), B), kTopkThreads, 0, st>>>(
-        cli, srv, n, t, bins, a);
+        cli, srv, n, t, bins, shift, a);
+  } else if (large) {
+    topk_sort_kernel<true><<<dim3((unsigned)((n + chunk - 1) / chunk), B), kSortThreads, 0, st>>>(
+        nullptr, cli, srv, n, t, shift, (int)k, a);
   } else {
     topk_shares_kernel<<<dim3((unsigned)((n + chunk - 1) / chunk), B), kTopkThreads, 0, st>>>(
-        cli, srv, n, t, (int)k, chunk, a);
+        cli, srv, n, t, (int)k, chunk, shift, a);
   }
   e = cudaGetLastError();
   const uint64_t* res = nullptr;
   // the first pass's keys sit in a; later passes alternate b, a, ..
-  if (e == cudaSuccess) e = reduce_keys(a, B, first, (int)k, b, a, &res, st);
+  if (e == cudaSuccess)
+    e = large ? reduce_keys_sorted(a, B, first, (int)k, b, a, &res, st)
+              : reduce_keys(a, B, first, (int)k, b, a, &res, st);
   if (e == cudaSuccess) {
     const uint64_t count = (uint64_t)B * k;
     topk_split_kernel<<<(unsigned)((count + 255) / 256), 256, 0, st>>>(res, count, dist, pos);

@@ -64,8 +64,8 @@ _SIGS = {
     "sanns_autotune_batched": ([_VP, _VP, _VP, C.c_uint32, _VP, C.c_int, _VP, _VP], C.c_int),
     "sanns_public_key": ([_VP, _VP, C.c_uint64, _VP, _VP], C.c_int),
     "sanns_set_response_form": ([_VP, C.c_int], C.c_int),
-    "sanns_topk": ([_VP, _VP, _VP, C.c_uint32, C.c_uint64, C.c_uint32, C.c_uint64, _VP, _VP, _VP],
-                   C.c_int),
+    "sanns_topk": ([_VP, _VP, _VP, C.c_uint32, C.c_uint64, C.c_uint32, C.c_uint64, C.c_uint32, _VP,
+                    _VP, _VP], C.c_int),
     "sanns_circuit_privacy_max_flood_bits": ([_VP], C.c_int),
     "sanns_set_circuit_privacy": ([_VP, _VP, C.c_uint32, _VP], C.c_int),
     "sanns_db_prepare_batched": ([_VP, _VP, _VP], C.c_int),
@@ -386,15 +386,16 @@ def sanns_set_response_form(ctx: Context, ntt: bool):
 
 
 def sanns_topk(ctx: Context, cli_share: torch.Tensor, srv_share: torch.Tensor, k: int,
-               bins: int = 0, stream=None):
-    """The k smallest reconstructed distances per query: exact (bins = 0) or
-    ApproxTopk over `bins` bins.  Returns (dist [B][k] uint32, pos [B][k] int64)."""
+               bins: int = 0, shift: int = 0, stream=None):
+    """The k smallest reconstructed distances >> shift per query: exact
+    (bins = 0) or ApproxTopk over `bins` bins.  Returns (dist [B][k] uint32,
+    pos [B][k] int64)."""
     assert cli_share.dtype == torch.uint32 and srv_share.dtype == torch.uint32
     assert cli_share.shape == srv_share.shape and cli_share.dim() == 2
     B, n = cli_share.shape
     dist = torch.empty((B, k), dtype=torch.uint32, device="cuda")
     pos = torch.empty((B, k), dtype=torch.int64, device="cuda")
-    _check(load().sanns_topk(ctx.handle, _ptr(cli_share), _ptr(srv_share), B, n, k, bins,
+    _check(load().sanns_topk(ctx.handle, _ptr(cli_share), _ptr(srv_share), B, n, k, bins, shift,
                              _ptr(dist), _ptr(pos), _stream(stream)))
     return dist, pos
 

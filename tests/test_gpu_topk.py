@@ -23,7 +23,7 @@ def ctx():
 
 
 @pytest.mark.parametrize("n,spread", [(100_003, 50), (70_000, 1 << 24), (33, 5)])
-@pytest.mark.parametrize("k", [1, 10, 32])
+@pytest.mark.parametrize("k", [1, 10, 32, 33, 88, 1024])   # > 32: the shared-memory sort path
 def test_topk_matches_oracle(ctx, n, spread, k):
     if k > n:
         pytest.skip("k > n")
@@ -36,22 +36,25 @@ def test_topk_matches_oracle(ctx, n, spread, k):
     cli_d, srv_d = cu(cli.astype(np.uint32)), cu(srv.astype(np.uint32))
     pos = np.arange(n)
     for bins in sorted({0, max(k, n // 128), max(k, n // 7), n}):
-        gd, gp = S.sanns_topk(ctx, cli_d, srv_d, k, bins)
-        gd, gp = gd.cpu().numpy(), gp.cpu().numpy()
-        for b in range(B):
-            if bins:
-                ov, oi = select.approx_topk_by_position(dist[b], pos, k, bins)
-                assert ov == select.approx_topk(dist[b], pos, k, bins)[0]
-            else:
-                ov, oi = select.exact_topk(dist[b], pos, k)
-            assert gd[b].tolist() == ov and gp[b].tolist() == oi, (bins, b)
+        for shift in (0, 3):
+            gd, gp = S.sanns_topk(ctx, cli_d, srv_d, k, bins, shift)
+            gd, gp = gd.cpu().numpy(), gp.cpu().numpy()
+            for b in range(B):
+                ds = dist[b] >> shift
+                if bins:
+                    ov, oi = select.approx_topk_by_position(ds, pos, k, bins)
+                    if bins * k <= 4_000_000:   # Algorithm 2 written out is O(l k)
+                        assert ov == select.approx_topk(ds, pos, k, bins)[0]
+                else:
+                    ov, oi = select.exact_topk(ds, pos, k)
+                assert gd[b].tolist() == ov and gp[b].tolist() == oi, (bins, shift, b)
 
 
 def test_topk_rejects_bad_arguments(ctx):
     z = torch.zeros((1, 100), dtype=torch.uint32, device="cuda")
-    for k, bins in [(0, 0), (33, 0), (10, 5), (10, 101), (101, 0)]:
+    for k, bins, shift in [(0, 0, 0), (1025, 0, 0), (10, 5, 0), (10, 101, 0), (101, 0, 0), (10, 0, 32)]:
         with pytest.raises(S.SannsError):
-            S.sanns_topk(ctx, z, z, k, bins)
+            S.sanns_topk(ctx, z, z, k, bins, shift)
 
 
 def test_first_configuration_end_to_end_top10():

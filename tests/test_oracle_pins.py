@@ -384,3 +384,85 @@ def test_approx_topk_by_position_selects_algorithm_2_values(seed):
         assert set(pos_i) <= minpos and set(lit_i) <= minpos   # both pick bin minima
         assert len(set(pos_i)) == k
         assert pos_i == sorted(pos_i, key=lambda x: (vals[x], x))
+
+
+# ---------------------------------------------------------------- Algorithm 4
+def _toy_layout(n, d, C, seed, stash_n=0):
+    """A hand-made layout: C clusters of a random assignment (some points kept
+    back as the stash), one group per two thirds / one third of the clusters,
+    centres = rounded member means in a seeded shuffled order."""
+    rnd = np.random.default_rng(seed)
+    coords = inputs.mixture_coords(n, d, 6, 25.0, seed)
+    order = rnd.permutation(n)
+    stash = np.sort(order[:stash_n]).astype(np.int64)
+    rest = np.sort(order[stash_n:])
+    assign = rnd.integers(0, C, size=len(rest))
+    assign[:C] = np.arange(C)          # no empty cluster
+    members = [rest[assign == c] for c in range(C)]
+    offs = np.zeros(C + 1, dtype=np.uint64)
+    offs[1:] = np.cumsum([len(m) for m in members])
+    cl_members = np.concatenate(members).astype(np.int64)
+    cut = (2 * C) // 3
+    groups = [np.arange(cut), np.arange(cut, C)]
+    group_offsets, centre_cluster, centres = [0], [], []
+    for g in groups:
+        for c in rnd.permutation(g):
+            centre_cluster.append(int(c))
+            centres.append(np.rint(coords[members[c]].mean(0)).astype(np.uint8))
+        group_offsets.append(group_offsets[-1] + len(g))
+    stash_perm = rnd.permutation(stash)
+    return coords, dict(group_offsets=np.array(group_offsets), centre_cluster=np.array(centre_cluster),
+                        centres=np.array(centres), cl_offsets=offs, cl_members=cl_members,
+                        stash=stash_perm)
+
+
+def test_clustering_knns_all_clusters_is_brute_force():
+    # retrieving every cluster with exact selections (and bins of one centre
+    # each, where ApproxTopk degenerates to exact) finds the true k nearest
+    from oracle import clustering
+    coords, lay = _toy_layout(3000, 12, 30, 1, stash_n=400)
+    k = 10
+    u = [20, 10]
+    for q in inputs.mixture_coords(6, 12, 6, 25.0, 2, means_seed=1):
+        bd = clustering.sq_dist(coords, q)
+        want = np.sort(bd)[:k]
+        for l, l_s in [([0, 0], 0), ([20, 10], 400)]:
+            ids = clustering.clustering_knns(q, coords, **lay, k=k, u=u, l=l, l_s=l_s, r_c=0, r_p=0,
+                                             maxval=2 ** 31)
+            assert np.array_equal(np.sort(bd[ids]), want)
+            assert len(set(ids.tolist())) == k
+
+
+def test_clustering_knns_stash_only_and_truncation():
+    # most points in the stash (a linear scan), every cluster retrieved: with
+    # r_p > 0 the result holds the k smallest truncated distances
+    from oracle import clustering
+    coords, lay = _toy_layout(2000, 8, 6, 3, stash_n=1500)
+    k = 8
+    for r_p in (0, 4):
+        for q in inputs.mixture_coords(4, 8, 6, 25.0, 4, means_seed=3):
+            ids = clustering.clustering_knns(q, coords, **lay, k=k, u=[4, 2], l=[0, 0], l_s=0, r_c=3,
+                                             r_p=r_p, maxval=2 ** 31)
+            bd = clustering.sq_dist(coords, q) >> r_p
+            assert np.array_equal(np.sort(bd[ids]), np.sort(bd)[:k])
+
+
+def test_clustering_knns_one_probe_finds_own_cluster_points():
+    # u = 1 per group, no stash: the result lies in the union of each group's
+    # nearest-centre cluster, and is the exact top-k of that union
+    from oracle import clustering
+    coords, lay = _toy_layout(1500, 6, 12, 5)
+    k = 5
+    for q in inputs.mixture_coords(5, 6, 6, 25.0, 6, means_seed=5):
+        ids = clustering.clustering_knns(q, coords, **lay, k=k, u=[1, 1], l=[0, 0], l_s=0, r_c=0,
+                                         r_p=0, maxval=2 ** 31)
+        union = []
+        go = lay["group_offsets"]
+        for i in range(2):
+            cd = clustering.sq_dist(lay["centres"][go[i]:go[i + 1]], q)
+            c = lay["centre_cluster"][go[i] + int(np.argmin(cd))]
+            union += lay["cl_members"][int(lay["cl_offsets"][c]):int(lay["cl_offsets"][c + 1])].tolist()
+        union = np.array(union)
+        bd = clustering.sq_dist(coords[union], q)
+        assert set(ids.tolist()) <= set(union.tolist())
+        assert np.array_equal(np.sort(clustering.sq_dist(coords[ids], q)), np.sort(bd)[:k])
