@@ -235,6 +235,7 @@ def query(server: ClusteringServer, sk: S.SecretKey, q: torch.Tensor, qids: torc
     blk = np.concatenate([[0], np.cumsum(k_b.astype(np.int64))])
     pts = np.concatenate([[0], np.cumsum(n_b.astype(np.int64))])
     maxv = ctx.query()["t"] - 1
+    ids_h = ids_g.cpu().numpy() if ids_g is not None else None
     for b in range(B):
         nb = int(n_b[b])
         cand_v[b, :k] = maxv
@@ -246,7 +247,7 @@ def query(server: ClusteringServer, sk: S.SecretKey, q: torch.Tensor, qids: torc
             dv, dp = S.sanns_topk(ctx, cli_g, _contig(srv_g[pts[b]:pts[b] + nb].unsqueeze(0)), kk,
                                   0, prm.r_p)
             cand_v[b, :kk] = dv[0].cpu().numpy()
-            cand_i[b, :kk] = ids_g[pts[b] + dp[0]].cpu().numpy()
+            cand_i[b, :kk] = ids_h[pts[b] + dp[0].cpu().numpy()]
     # 4. the stash: linear scan, ApproxTopk
     ns = len(lay.stash_perm)
     if ns:
