@@ -347,7 +347,7 @@ def run_gpu(args) -> None:
     cpu = None
     if rank == 0:
         cpu = cpu_baseline(quick=args.quick_cpu)
-    batched = cluster = serving = None
+    batched = cluster = serving = alg4 = None
     if rank == 0 and not args.no_batched:
         del ct_all
         torch.cuda.empty_cache()
@@ -355,6 +355,8 @@ def run_gpu(args) -> None:
         torch.cuda.empty_cache()
     if rank == 0 and not args.no_extra:
         cluster = run_cluster_section()
+        torch.cuda.empty_cache()
+        alg4 = run_alg4_section()
         torch.cuda.empty_cache()
         serving = run_serving_section()
         torch.cuda.empty_cache()
@@ -398,6 +400,7 @@ def run_gpu(args) -> None:
             "cpu_baseline": cpu,
             "batched": batched,
             "clustering": cluster,
+            "clustering_knns": alg4,
             "serving": serving,
         }
         print(json.dumps(line), flush=True)
@@ -578,6 +581,86 @@ def run_cluster_section() -> dict:
     }
 
 
+ALG4 = dict(n=1_000_000, d=128, N=8192, L=3, prime_bits=60, t_rule=0, n_comp=64, sigma=20.0,
+            m=20, alpha=0.56, s_max=31412, k=10, u=(50, 31, 19, 13), l=(458, 270, 178, 84),
+            l_s=262, r_c=5, r_p=8, iters=6, B_lat=16, B_batch=64, seed=31)
+
+
+def run_alg4_section() -> dict:
+    """Algorithm 4 (clustering-based k-NNS) end to end through the library:
+    balanced clustering (m = 20, alpha = 0.56) and a stash of at most 31,412
+    points over n = 10^6, d = 128 mixture data, the SIFT row of the paper's
+    hyperparameters (u^i, l^i, l_s, r_c, r_p); per-query latency, batched
+    throughput and 10-NN accuracy against brute force."""
+    import time
+
+    import numpy as np
+    import torch
+
+    from paper_1904_02033_b300 import cluster, inputs
+    from paper_1904_02033_b300 import sanns as S
+
+    W = ALG4
+    n, d = W["n"], W["d"]
+    coords = inputs.mixture_coords_device(n, d, W["n_comp"], W["sigma"], W["seed"])
+    t0 = time.perf_counter()
+    groups = cluster.balanced_clustering(coords, W["m"], W["alpha"], iters=W["iters"], seed=W["seed"],
+                                         max_search=5)
+    kept, stash = cluster.split_stash(groups, W["s_max"])
+    lay = cluster.make_layout(kept, stash, d, seed=W["seed"] + 1)
+    t_cluster = time.perf_counter() - t0
+    T = len(kept)
+    u = tuple((list(W["u"]) + [W["u"][-1]] * T)[:T])
+    l = tuple((list(W["l"]) + [W["l"][-1]] * T)[:T])
+    ctx = S.sanns_ctx_create(W["N"], W["L"], W["prime_bits"], W["t_rule"], d)
+    srv = cluster.ClusteringServer(ctx, coords, lay)
+    sk = S.sanns_keygen(ctx, W["seed"] + 2)
+    prm = cluster.Params(W["k"], u, l, W["l_s"], W["r_c"], W["r_p"])
+    Bb = W["B_batch"]
+    q_all = inputs.mixture_coords_device(Bb, d, W["n_comp"], W["sigma"], W["seed"] + 3,
+                                         means_seed=W["seed"])
+    qids = torch.arange(Bb, dtype=torch.int64).to(torch.uint64).cuda()
+    cluster.query(srv, sk, q_all[:2], qids[:2], prm)       # warm-up
+    torch.cuda.synchronize()
+    lat = []
+    for b in range(W["B_lat"]):
+        t1 = time.perf_counter()
+        cluster.query(srv, sk, q_all[b:b + 1], qids[b:b + 1], prm)
+        lat.append((time.perf_counter() - t1) * 1e3)
+    t1 = time.perf_counter()
+    ids = cluster.query(srv, sk, q_all, qids, prm)
+    batch_ms = (time.perf_counter() - t1) * 1e3
+    # 10-NN accuracy against brute force (exact integer distances)
+    xf = coords.to(torch.int64)
+    acc = 0.0
+    for b in range(Bb):
+        dq = ((xf - q_all[b].to(torch.int64)[None, :]) ** 2).sum(1)
+        kth = torch.kthvalue(dq, W["k"]).values
+        got = torch.from_numpy(ids[b]).cuda()
+        acc += float(((dq[got.clamp(min=0)] <= kth) & (got >= 0)).sum()) / W["k"]
+    acc /= Bb
+    S.sanns_device_status(ctx)
+    N = W["N"]
+    sizes = np.diff(lay.cl_offsets.astype(np.int64))
+    blocks = (-(-int(lay.group_offsets[-1]) // N) + -(-len(lay.stash_perm) // N)
+              + -(-int(sum(u) * sizes.max()) // N))
+    lat.sort()
+    return {
+        "workload": "Algorithm 4 (clustering-based k-NNS): n=1,000,000 d=128 uint8 64-component "
+                    "Gaussian mixture (sigma 20); balanced clustering m=20 alpha=0.56 with stash; "
+                    "u, l, l_s, r_c, r_p of the paper's SIFT row; BFV N=8192, three 60-bit primes",
+        "groups": T, "centres_per_group": np.diff(lay.group_offsets).tolist(),
+        "stash": len(lay.stash_perm), "cluster_size_max": int(sizes.max()),
+        "u": list(u), "l": list(l), "clustering_s": t_cluster,
+        "latency_ms_B1": {"p50": lat[len(lat) // 2], "max": lat[-1], "queries": len(lat)},
+        "batch": {"queries": Bb, "ms": batch_ms, "queries_per_s": Bb / (batch_ms * 1e-3)},
+        "response_blocks_per_query_at_most": blocks,
+        "linear_scan_blocks_per_query": -(-n // N),
+        "accuracy_10nn": acc,
+        "timing": "host wall clock per call (the pipeline reads selections back to plan the gather)",
+    }
+
+
 SERVE = dict(rate=2000.0, duration=3.0, max_batch=128, slots=3, seed=21, sample_frac=0.02)
 
 
@@ -737,7 +820,7 @@ def main():
     ap.add_argument("--quick-cpu", action="store_true", help="smaller CPU baseline sample")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched section")
     ap.add_argument("--no-extra", action="store_true", help="skip the clustering and serving sections")
-    ap.add_argument("--only", choices=["cluster", "serving"], default=None,
+    ap.add_argument("--only", choices=["cluster", "serving", "alg4"], default=None,
                     help="run only one of the extra sections")
     ap.add_argument("--quick-batched", action="store_true", help="batched section at n = 10^6")
     ap.add_argument("--only-batched", type=int, default=None, metavar="N_POINTS",
@@ -759,7 +842,8 @@ def main():
     if args.only:
         import torch
         torch.cuda.set_device(0)
-        fn = run_cluster_section if args.only == "cluster" else run_serving_section
+        fn = {"cluster": run_cluster_section, "serving": run_serving_section,
+              "alg4": run_alg4_section}[args.only]
         print(json.dumps({args.only: fn()}), flush=True)
     elif args.only_batched:
         import torch

@@ -308,6 +308,24 @@ int sanns_topk(sanns_ctx *ctx, const uint32_t *cli_dev, const uint32_t *srv_dev,
                void *stream);
 
 /*
+ * The same selection over B ragged lists (Algorithm 4: the points gathered
+ * for each query, the centres of one group): list b is positions x <
+ * len[b] of cli_dev + cli_off[b] and srv_dev + srv_off[b]; positions in the
+ * output count from the list's start.  With bins = l, list b uses
+ * min(l, len[b]) bins (every position its own bin, i.e. exact, when len[b]
+ * <= l).  A list shorter than k fills its last k - len[b] outputs with dist
+ * 2^32 - 1 and pos 2^64 - 1 (also the uniform call's convention, which never
+ * produces them).  cli_off, srv_off and len are HOST arrays of B entries,
+ * read before the call returns; the device shares must hold every listed
+ * element.  Needs 1 <= k <= 1024, B <= 65535, len[b] < 2^32, bins = 0 or
+ * bins >= k, shift <= 31; SANNS_EINVAL otherwise.  Stream-ordered scratch;
+ * the host arrays are copied (pageable) on stream.
+ */
+int sanns_topk_segments(sanns_ctx *ctx, const uint32_t *cli_dev, const uint32_t *srv_dev, uint32_t B,
+                        const uint64_t *cli_off, const uint64_t *srv_off, const uint64_t *len, uint32_t k,
+                        uint64_t bins, uint32_t shift, uint32_t *dist_dev, uint64_t *pos_dev, void *stream);
+
+/*
  * Circuit privacy (Sec. 2, "Additive Homomorphic Encryption": the AHE scheme
  * must not reveal the server's operations beyond the decrypted message; the
  * paper obtains this by noise flooding, with 108 bits of statistical circuit

@@ -50,8 +50,9 @@ def kmeans(x: torch.Tensor, k: int, iters: int, seed: int):
     def assign(c):
         cn = (c * c).sum(1)
         out = torch.empty(x.shape[0], dtype=torch.int64, device=x.device)
-        for s in range(0, x.shape[0], 1 << 17):
-            e = min(x.shape[0], s + (1 << 17))
+        rows = max(1024, (1 << 27) // c.shape[0])     # a distance tile of at most 512 MB
+        for s in range(0, x.shape[0], rows):
+            e = min(x.shape[0], s + rows)
             out[s:e] = (xn[s:e, None] - 2.0 * (xf[s:e] @ c.T) + cn[None, :]).argmin(1)
         return out
 
@@ -202,69 +203,75 @@ class ClusteringServer:
                          if len(layout.stash_perm) else None)
 
 
-def _contig(t: torch.Tensor) -> torch.Tensor:
-    return t.contiguous()
-
-
 def query(server: ClusteringServer, sk: S.SecretKey, q: torch.Tensor, qids: torch.Tensor,
-          prm: Params, seeds=(101, 102, 103, 104)) -> np.ndarray:
+          prm: Params, seeds=(101, 102, 103, 104), stream=None) -> np.ndarray:
     """Algorithm 4 for B queries (uint8 [B][d] on the GPU); returns the k
-    neighbour ids per query [B][k] (host)."""
+    neighbour ids per query [B][k] (host; -1 where fewer than k points were
+    searched)."""
     ctx, lay = server.ctx, server.layout
-    B = q.shape[0]
-    k = prm.k
-    ct = S.sanns_encrypt_query(ctx, sk, q, seeds[0], qids)
+    B, k, N = q.shape[0], prm.k, ctx.N
+    ar = np.arange(B, dtype=np.uint64)
+    ct = S.sanns_encrypt_query(ctx, sk, q, seeds[0], qids, stream=stream)
     # 2. centres: encrypted distances, client shares, ApproxTopk per group
     nc = int(lay.group_offsets[-1])
-    out_c, srv_c = S.sanns_distances(ctx, server.centres_db, ct, seeds[1], qids)
-    cli_c = S.sanns_decrypt_shares(ctx, sk, out_c, nc, q)
-    probes = []
+    out_c, srv_c = S.sanns_distances(ctx, server.centres_db, ct, seeds[1], qids, stream=stream)
+    cli_c = S.sanns_decrypt_shares(ctx, sk, out_c, nc, q, stream=stream)
+    picks = []
     for i in range(len(lay.group_offsets) - 1):
         g0, g1 = int(lay.group_offsets[i]), int(lay.group_offsets[i + 1])
         u = min(prm.u[i], g1 - g0)
-        bins = min(prm.l[i], g1 - g0) if prm.l[i] else 0
-        _, pos = S.sanns_topk(ctx, _contig(cli_c[:, g0:g1]), _contig(srv_c[:, g0:g1]), u,
-                              max(bins, u) if bins else 0, prm.r_c)
-        probes.append(lay.centre_cluster[g0 + pos.cpu().numpy()])
-    probes = np.concatenate(probes, axis=1).astype(np.uint32)
-    # 3. the selected clusters' points in one persistent launch; exact top-k
+        bins = max(min(prm.l[i], g1 - g0), u) if prm.l[i] else 0
+        off = ar * nc + g0
+        _, pos = S.sanns_topk_segments(ctx, cli_c, srv_c, off, off, np.full(B, g1 - g0), u, bins,
+                                       prm.r_c, stream=stream)
+        picks.append((g0, pos))
+    probes = np.concatenate([lay.centre_cluster[g0 + pos.cpu().numpy()] for g0, pos in picks],
+                            axis=1).astype(np.uint32)
+    # 3. the selected clusters' points in one persistent launch; every
+    #    response block decrypted in one call (block j of query b carries
+    #    query b's norm); exact top-k over the B ragged lists
     out_g, srv_g, ids_g, n_b, k_b = S.sanns_distances_gather(ctx, server.clusters, ct, probes,
-                                                            seeds[2], qids)
-    cand_v = np.zeros((B, 2 * k), dtype=np.uint32)
-    cand_i = np.zeros((B, 2 * k), dtype=np.int64)
-    blk = np.concatenate([[0], np.cumsum(k_b.astype(np.int64))])
+                                                            seeds[2], qids, stream=stream)
+    kb = k_b.astype(np.int64)
+    blk = np.concatenate([[0], np.cumsum(kb)])
     pts = np.concatenate([[0], np.cumsum(n_b.astype(np.int64))])
-    maxv = ctx.query()["t"] - 1
-    ids_h = ids_g.cpu().numpy() if ids_g is not None else None
-    for b in range(B):
-        nb = int(n_b[b])
-        cand_v[b, :k] = maxv
-        cand_i[b, :k] = -1
-        if nb:
-            cli_g = S.sanns_decrypt_shares(ctx, sk, out_g[blk[b]:blk[b + 1]].unsqueeze(0), nb,
-                                           q[b:b + 1])
-            kk = min(k, nb)
-            dv, dp = S.sanns_topk(ctx, cli_g, _contig(srv_g[pts[b]:pts[b] + nb].unsqueeze(0)), kk,
-                                  0, prm.r_p)
-            cand_v[b, :kk] = dv[0].cpu().numpy()
-            cand_i[b, :kk] = ids_h[pts[b] + dp[0].cpu().numpy()]
-    # 4. the stash: linear scan, ApproxTopk
+    if blk[-1]:
+        owner = torch.from_numpy(np.repeat(np.arange(B), kb)).to(q.device)
+        cli_g = S.sanns_decrypt_shares(ctx, sk, out_g.unsqueeze(1), N, q.index_select(0, owner),
+                                       stream=stream)
+    else:   # nothing gathered (only empty clusters selected)
+        cli_g = srv_g = torch.zeros(1, dtype=torch.uint32, device=q.device)
+    dv_c, dp_c = S.sanns_topk_segments(ctx, cli_g, srv_g, blk[:-1] * N, pts[:-1], n_b, k, 0, prm.r_p,
+                                       stream=stream)
+    # 4. the stash: linear scan, ApproxTopk (fills past the stash's size)
     ns = len(lay.stash_perm)
     if ns:
-        out_s, srv_s = S.sanns_distances(ctx, server.stash_db, ct, seeds[3], qids)
-        cli_s = S.sanns_decrypt_shares(ctx, sk, out_s, ns, q)
-        kk = min(k, ns)
-        bins = max(min(prm.l_s, ns), kk) if prm.l_s else 0
-        sv, sp = S.sanns_topk(ctx, cli_s, srv_s, kk, bins, prm.r_p)
-        cand_v[:, k:k + kk] = sv.cpu().numpy()
-        cand_i[:, k:k + kk] = lay.stash_perm[sp.cpu().numpy()]
-        cand_v[:, k + kk:] = maxv
-        cand_i[:, k + kk:] = -1
+        out_s, srv_s = S.sanns_distances(ctx, server.stash_db, ct, seeds[3], qids, stream=stream)
+        cli_s = S.sanns_decrypt_shares(ctx, sk, out_s, ns, q, stream=stream)
+        bins = max(min(prm.l_s, ns), min(k, ns)) if prm.l_s else 0
+        bins = bins if bins >= k else 0     # fewer than k bins: every stash point is a candidate
+        off = ar * ns
+        dv_s, dp_s = S.sanns_topk_segments(ctx, cli_s, srv_s, off, off, np.full(B, ns), k, bins,
+                                           prm.r_p, stream=stream)
     else:
-        cand_v[:, k:] = maxv
-        cand_i[:, k:] = -1
-    # 5. the k smallest of the 2k candidates, those of step 3 first on ties
-    zeros = torch.zeros((B, 2 * k), dtype=torch.uint32, device="cuda")
-    _, fp = S.sanns_topk(ctx, torch.from_numpy(cand_v).cuda(), zeros, k)
+        z = torch.zeros(1, dtype=torch.uint32, device=q.device)
+        dv_s, dp_s = S.sanns_topk_segments(ctx, z, z, np.zeros(B), np.zeros(B), np.zeros(B), k,
+                                           stream=stream)
+    # 5. the k smallest of the 2k candidates (cluster candidates first on
+    #    ties), as shares (candidate value, 0).  A fill value 2^32 - 1
+    #    reconstructs to 2^32 - 1 - t, above every distance (t < 2^31).
+    cand = torch.cat([dv_c, dv_s], dim=1).contiguous()
+    zeros = torch.zeros_like(cand)
+    _, fp = S.sanns_topk(ctx, cand, zeros, k, stream=stream)
     fp = fp.cpu().numpy()
-    return np.take_along_axis(cand_i, fp, axis=1)
+    pc, ps = dp_c.cpu().numpy(), dp_s.cpu().numpy()
+    ids_h = ids_g.cpu().numpy().astype(np.int64) if ids_g is not None else None
+    out = np.full((B, k), -1, dtype=np.int64)
+    for b in range(B):
+        for r in range(k):
+            j = int(fp[b, r])
+            p = int(pc[b, j]) if j < k else int(ps[b, j - k])
+            if p < 0:
+                continue
+            out[b, r] = ids_h[pts[b] + p] if j < k else int(lay.stash_perm[p])
+    return out

@@ -364,6 +364,32 @@ int sanns_topk(sanns_ctx* ctx, const uint32_t* cli, const uint32_t* srv, uint32_
   return SANNS_OK;
 }
 
+int sanns_topk_segments(sanns_ctx* ctx, const uint32_t* cli, const uint32_t* srv, uint32_t B,
+                        const uint64_t* cli_off, const uint64_t* srv_off, const uint64_t* len,
+                        uint32_t k, uint64_t bins, uint32_t shift, uint32_t* dist, uint64_t* pos,
+                        void* stream) {
+  if (!ctx) return fail(SANNS_EINVAL, "ctx is NULL");
+  if (B == 0) return SANNS_OK;
+  if (!cli || !srv || !dist || !pos || !cli_off || !srv_off || !len)
+    return fail(SANNS_EINVAL, "NULL buffer");
+  if (k < 1 || k > kTopkLarge) return fail(SANNS_EINVAL, "k must be in [1, 1024]");
+  if (B > 65535) return fail(SANNS_EINVAL, "B must be <= 65535");
+  if (shift > 31) return fail(SANNS_EINVAL, "shift must be <= 31");
+  if (bins && bins < k) return fail(SANNS_EINVAL, "need bins = 0 or bins >= k");
+  std::vector<uint64_t> seg(3 * (size_t)B);
+  for (uint32_t b = 0; b < B; ++b) {
+    if (len[b] >= (1ull << 32)) return fail(SANNS_EINVAL, "segment longer than 2^32 - 1");
+    seg[b] = cli_off[b];
+    seg[B + b] = srv_off[b];
+    seg[2 * (size_t)B + b] = len[b];
+  }
+  int rc = check_device(ctx);
+  if (rc) return rc;
+  SANNS_CUDA(launch_topk_segments(cli, srv, B, seg.data(), ctx->P.t, k, bins, shift, dist, pos,
+                                  as_stream(stream)));
+  return SANNS_OK;
+}
+
 int sanns_public_key(sanns_ctx* ctx, const sanns_sk* sk, uint64_t seed, uint64_t* pk, void* stream) {
   if (!ctx || !sk || !pk) return fail(SANNS_EINVAL, "ctx, sk or pk is NULL");
   if (sk->ctx != ctx) return fail(SANNS_EINVAL, "key belongs to another context");

@@ -93,6 +93,9 @@ constexpr uint32_t kTopkLarge = 1024;  // largest k of a selection
 cudaError_t launch_topk(const uint32_t* cli, const uint32_t* srv, uint32_t B, uint64_t n, uint64_t t,
                         uint32_t k, uint64_t bins, uint32_t shift, uint32_t* dist, uint64_t* pos,
                         cudaStream_t st);
+cudaError_t launch_topk_segments(const uint32_t* cli, const uint32_t* srv, uint32_t B,
+                                 const uint64_t* seg_host, uint64_t t, uint32_t k, uint64_t bins,
+                                 uint32_t shift, uint32_t* dist, uint64_t* pos, cudaStream_t st);
 cudaError_t launch_keygen(const PrimeSet& P, uint64_t seed, int8_t* s, uint64_t* s_hat,
                           uint64_t* s_hat_shoup, cudaStream_t st);
 cudaError_t launch_encrypt(const PrimeSet& P, const uint64_t* s_hat, const uint64_t* s_hat_shoup,

@@ -11,6 +11,10 @@
 //                 position on ties), then the k smallest of the l minima.
 // A (value, position) pair is one 64-bit key, value << 32 | position, so
 // every comparison is a plain integer comparison and the result is unique.
+// Selection runs per segment: a query's whole share vector (uniform: segment
+// b = positions [b n, (b + 1) n) of both shares), or one of B ragged lists at
+// its own offsets into the client and server shares (the per-query lists of
+// the clustering protocol).  A segment shorter than k leaves missing keys.
 #include "internal.h"
 
 namespace sanns {
@@ -23,6 +27,33 @@ constexpr uint64_t kNoKey = ~0ull;
 constexpr int kSortKeys = 4096;   // keys a block sorts in shared memory (larger k)
 constexpr int kSortThreads = 512;
 static_assert(kTopkLarge * 4 <= kSortKeys, "a sort pass must shrink the keys at least 4x");
+
+// Where segment b lies: uniform (len == NULL) or from device arrays.
+struct Segs {
+  const uint64_t* cli_off;
+  const uint64_t* srv_off;
+  const uint64_t* len;
+  uint64_t n;
+};
+
+__device__ __forceinline__ void seg_of(const Segs& sg, uint64_t b, uint64_t& co, uint64_t& so,
+                                       uint64_t& ln) {
+  if (sg.len == nullptr) {
+    co = so = b * sg.n;
+    ln = sg.n;
+  } else {
+    co = sg.cli_off[b];
+    so = sg.srv_off[b];
+    ln = sg.len[b];
+  }
+}
+
+__device__ __forceinline__ uint64_t key_of(const uint32_t* cs, const uint32_t* ss, uint64_t p, uint64_t t,
+                                           uint32_t shift) {
+  uint64_t v = (uint64_t)cs[p] + ss[p];
+  v = (v >= t ? v - t : v) >> shift;
+  return (v << 32) | p;
+}
 
 // A thread keeps its kTopkMax smallest keys, ascending (at least the k the
 // block needs, k <= kTopkMax; static indices keep the list in registers).
@@ -75,48 +106,50 @@ __device__ void topk_block_merge(uint64_t (&best)[kTopkMax], int k, uint64_t* ou
   }
 }
 
-// Pass 1, from the shares: block (chunk c, query b) keeps the k smallest keys
-// of positions [c chunk, (c + 1) chunk) in part[b][c][0 .. k-1].
+// Pass 1, from the shares: block (chunk c, segment b) keeps the k smallest
+// keys of positions [c chunk, (c + 1) chunk) of the segment in
+// part[b][c][0 .. k-1].
 __global__ void __launch_bounds__(kTopkThreads) topk_shares_kernel(const uint32_t* __restrict__ cli,
                                                                    const uint32_t* __restrict__ srv,
-                                                                   uint64_t n, uint64_t t, int k,
+                                                                   Segs sg, uint64_t t, int k,
                                                                    uint64_t chunk, uint32_t shift,
                                                                    uint64_t* part) {
   const uint64_t b = blockIdx.y, c = blockIdx.x;
+  uint64_t co, so, n;
+  seg_of(sg, b, co, so, n);
   uint64_t best[kTopkMax];
 #pragma unroll
   for (int j = 0; j < kTopkMax; ++j) best[j] = kNoKey;
   const uint64_t p0 = c * chunk, p1 = p0 + chunk < n ? p0 + chunk : n;
-  const uint32_t* cs = cli + b * n;
-  const uint32_t* ss = srv + b * n;
   for (uint64_t p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
-    uint64_t v = (uint64_t)cs[p] + ss[p];
-    v = (v >= t ? v - t : v) >> shift;
-    const uint64_t key = (v << 32) | p;
+    const uint64_t key = key_of(cli + co, srv + so, p, t, shift);
     if (key < best[kTopkMax - 1]) topk_insert(best, key);
   }
   topk_block_merge(best, k, part + (b * gridDim.x + c) * k);
 }
 
-// Bin minima for ApproxTopk: one warp per bin i = positions [ceil(i n / l),
-// ceil((i + 1) n / l)); mins[b][i] = the smallest key of the bin.
+// Bin minima for ApproxTopk: one warp per bin i of segment b, l_b =
+// min(l, length) bins, bin i = positions [ceil(i n / l_b), ceil((i + 1) n / l_b));
+// mins[b][i] = the smallest key of the bin (missing for i >= l_b).  l_b = n
+// puts every position in a bin of its own: the selection is then exact.
 __global__ void __launch_bounds__(kTopkThreads) bin_min_kernel(const uint32_t* __restrict__ cli,
                                                                const uint32_t* __restrict__ srv,
-                                                               uint64_t n, uint64_t t, uint64_t l,
+                                                               Segs sg, uint64_t t, uint64_t l,
                                                                uint32_t shift, uint64_t* mins) {
   const uint64_t b = blockIdx.y;
   const uint64_t i = blockIdx.x * (uint64_t)(blockDim.x / 32) + (threadIdx.x >> 5);
   const uint32_t lane = threadIdx.x & 31;
   if (i >= l) return;
-  const uint64_t p0 = (i * n + l - 1) / l, p1 = ((i + 1) * n + l - 1) / l;
-  const uint32_t* cs = cli + b * n;
-  const uint32_t* ss = srv + b * n;
+  uint64_t co, so, n;
+  seg_of(sg, b, co, so, n);
+  const uint64_t lb = l < n ? l : n;
   uint64_t m = kNoKey;
-  for (uint64_t p = p0 + lane; p < p1; p += 32) {
-    uint64_t v = (uint64_t)cs[p] + ss[p];
-    v = (v >= t ? v - t : v) >> shift;
-    const uint64_t key = (v << 32) | p;
-    m = key < m ? key : m;
+  if (i < lb) {
+    const uint64_t p0 = (i * n + lb - 1) / lb, p1 = ((i + 1) * n + lb - 1) / lb;
+    for (uint64_t p = p0 + lane; p < p1; p += 32) {
+      const uint64_t key = key_of(cli + co, srv + so, p, t, shift);
+      m = key < m ? key : m;
+    }
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
@@ -144,33 +177,27 @@ __global__ void __launch_bounds__(kTopkThreads) topk_keys_kernel(const uint64_t*
   topk_block_merge(best, k, part + (b * gridDim.x + c) * k);
 }
 
-// Larger k (kTopkMax < k <= kTopkLarge): block (chunk c, query b) sorts
+// Larger k (kTopkMax < k <= kTopkLarge): block (chunk c, segment b) sorts
 // kSortKeys keys in shared memory (bitonic network, ascending) and keeps the
 // first k in part[b][c][0 .. k-1].  The keys come from the shares
-// (kFromShares, positions [c kSortKeys, (c + 1) kSortKeys) of n) or from a
-// key array of m keys per query; missing keys past the end sort last.
+// (kFromShares, positions [c kSortKeys, (c + 1) kSortKeys) of the segment)
+// or from a key array of m keys per segment; missing keys sort last.
 template <bool kFromShares>
 __global__ void __launch_bounds__(kSortThreads) topk_sort_kernel(const uint64_t* __restrict__ keys,
                                                                  const uint32_t* __restrict__ cli,
                                                                  const uint32_t* __restrict__ srv,
-                                                                 uint64_t m, uint64_t t,
+                                                                 Segs sg, uint64_t m, uint64_t t,
                                                                  uint32_t shift, int k,
                                                                  uint64_t* part) {
   __shared__ uint64_t s[kSortKeys];
   const uint64_t b = blockIdx.y, c = blockIdx.x;
   const uint64_t p0 = c * kSortKeys;
+  uint64_t co = 0, so = 0;
+  if (kFromShares) seg_of(sg, b, co, so, m);
   for (int i = threadIdx.x; i < kSortKeys; i += kSortThreads) {
     const uint64_t p = p0 + i;
     uint64_t key = kNoKey;
-    if (p < m) {
-      if (kFromShares) {
-        uint64_t v = (uint64_t)cli[b * m + p] + srv[b * m + p];
-        v = (v >= t ? v - t : v) >> shift;
-        key = (v << 32) | p;
-      } else {
-        key = keys[b * m + p];
-      }
-    }
+    if (p < m) key = kFromShares ? key_of(cli + co, srv + so, p, t, shift) : keys[b * m + p];
     s[i] = key;
   }
   __syncthreads();
@@ -192,13 +219,15 @@ __global__ void __launch_bounds__(kSortThreads) topk_sort_kernel(const uint64_t*
   for (int r = threadIdx.x; r < k; r += kSortThreads) part[(b * gridDim.x + c) * k + r] = s[r];
 }
 
-// Split the keys: dist[b][r] = key >> 32, pos[b][r] = key & (2^32 - 1).
+// Split the keys: dist[b][r] = key >> 32, pos[b][r] = key & (2^32 - 1); a
+// missing key gives dist 2^32 - 1, pos 2^64 - 1.
 __global__ void topk_split_kernel(const uint64_t* __restrict__ keys, uint64_t count,
                                   uint32_t* __restrict__ dist, uint64_t* __restrict__ pos) {
   const uint64_t e = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
   if (e >= count) return;
-  dist[e] = (uint32_t)(keys[e] >> 32);
-  pos[e] = keys[e] & 0xffffffffull;
+  const uint64_t key = keys[e];
+  dist[e] = (uint32_t)(key >> 32);
+  pos[e] = key == kNoKey ? kNoKey : (key & 0xffffffffull);
 }
 
 // The same with the shared-memory sort passes (k > kTopkMax).
@@ -208,8 +237,8 @@ cudaError_t reduce_keys_sorted(const uint64_t* keys, uint32_t B, uint64_t m, int
   uint64_t* dst = a;
   while (true) {
     const uint64_t chunks = (m + kSortKeys - 1) / kSortKeys;
-    topk_sort_kernel<false><<<dim3((unsigned)chunks, B), kSortThreads, 0, st>>>(src, nullptr, nullptr,
-                                                                              m, 0, 0, k, dst);
+    topk_sort_kernel<false><<<dim3((unsigned)chunks, B), kSortThreads, 0, st>>>(
+        src, nullptr, nullptr, Segs{}, m, 0, 0, k, dst);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     m = chunks * (uint64_t)k;
@@ -244,30 +273,44 @@ cudaError_t reduce_keys(const uint64_t* keys, uint32_t B, uint64_t m, int k, uin
 
 }  // namespace
 
-cudaError_t launch_topk(const uint32_t* cli, const uint32_t* srv, uint32_t B, uint64_t n, uint64_t t,
-                        uint32_t k, uint64_t bins, uint32_t shift, uint32_t* dist, uint64_t* pos,
-                        cudaStream_t st) {
+// Selection over B segments; n is the longest segment (uniform: every
+// segment), sg tells where they lie (seg_host: host copy of the offsets and
+// lengths, staged into the scratch).
+static cudaError_t run_topk(const uint32_t* cli, const uint32_t* srv, uint32_t B, uint64_t n, Segs sg,
+                            const uint64_t* seg_host, uint64_t t, uint32_t k, uint64_t bins,
+                            uint32_t shift, uint32_t* dist, uint64_t* pos, cudaStream_t st) {
   const bool large = k > (uint32_t)kTopkMax;
   const uint64_t chunk = large ? kSortKeys : 1 << 16;
-  const uint64_t first = bins ? bins : (n + chunk - 1) / chunk * k;  // keys per query after pass 1
+  const uint64_t chunks = n ? (n + chunk - 1) / chunk : 1;
+  const uint64_t first = bins ? bins : chunks * k;  // keys per segment after pass 1
   const uint64_t words = 2 * (uint64_t)B * (first + 64);
+  const uint64_t seg_words = seg_host ? 3 * (uint64_t)B : 0;
   uint64_t* scratch = nullptr;
-  cudaError_t e = cudaMallocAsync(&scratch, sizeof(uint64_t) * words, st);
+  cudaError_t e = cudaMallocAsync(&scratch, sizeof(uint64_t) * (words + seg_words), st);
   if (e != cudaSuccess) return e;
   uint64_t* a = scratch;
   uint64_t* b = scratch + words / 2;
-  if (bins) {
-    const unsigned per_block = kTopkThreads / 32;
-    bin_min_kernel<<<dim3((unsigned)((bins + per_block - 1) / per_block), B), kTopkThreads, 0, st>>>(
-        cli, srv, n, t, bins, shift, a);
-  } else if (large) {
-    topk_sort_kernel<true><<<dim3((unsigned)((n + chunk - 1) / chunk), B), kSortThreads, 0, st>>>(
-        nullptr, cli, srv, n, t, shift, (int)k, a);
-  } else {
-    topk_shares_kernel<<<dim3((unsigned)((n + chunk - 1) / chunk), B), kTopkThreads, 0, st>>>(
-        cli, srv, n, t, (int)k, chunk, shift, a);
+  if (seg_host) {
+    uint64_t* d_seg = scratch + words;
+    e = cudaMemcpyAsync(d_seg, seg_host, sizeof(uint64_t) * seg_words, cudaMemcpyHostToDevice, st);
+    sg.cli_off = d_seg;
+    sg.srv_off = d_seg + B;
+    sg.len = d_seg + 2 * (uint64_t)B;
   }
-  e = cudaGetLastError();
+  if (e == cudaSuccess) {
+    if (bins) {
+      const unsigned per_block = kTopkThreads / 32;
+      bin_min_kernel<<<dim3((unsigned)((bins + per_block - 1) / per_block), B), kTopkThreads, 0, st>>>(
+          cli, srv, sg, t, bins, shift, a);
+    } else if (large) {
+      topk_sort_kernel<true><<<dim3((unsigned)chunks, B), kSortThreads, 0, st>>>(nullptr, cli, srv, sg, 0,
+                                                                                t, shift, (int)k, a);
+    } else {
+      topk_shares_kernel<<<dim3((unsigned)chunks, B), kTopkThreads, 0, st>>>(cli, srv, sg, t, (int)k,
+                                                                            chunk, shift, a);
+    }
+    e = cudaGetLastError();
+  }
   const uint64_t* res = nullptr;
   // the first pass's keys sit in a; later passes alternate b, a, ..
   if (e == cudaSuccess)
@@ -280,6 +323,22 @@ cudaError_t launch_topk(const uint32_t* cli, const uint32_t* srv, uint32_t B, ui
   }
   cudaError_t e2 = cudaFreeAsync(scratch, st);
   return e != cudaSuccess ? e : e2;
+}
+
+cudaError_t launch_topk(const uint32_t* cli, const uint32_t* srv, uint32_t B, uint64_t n, uint64_t t,
+                        uint32_t k, uint64_t bins, uint32_t shift, uint32_t* dist, uint64_t* pos,
+                        cudaStream_t st) {
+  Segs sg{nullptr, nullptr, nullptr, n};
+  return run_topk(cli, srv, B, n, sg, nullptr, t, k, bins, shift, dist, pos, st);
+}
+
+cudaError_t launch_topk_segments(const uint32_t* cli, const uint32_t* srv, uint32_t B,
+                                 const uint64_t* seg_host, uint64_t t, uint32_t k, uint64_t bins,
+                                 uint32_t shift, uint32_t* dist, uint64_t* pos, cudaStream_t st) {
+  uint64_t n = 0;
+  for (uint32_t b = 0; b < B; ++b) n = seg_host[2 * (uint64_t)B + b] > n ? seg_host[2 * (uint64_t)B + b] : n;
+  Segs sg{nullptr, nullptr, nullptr, 0};
+  return run_topk(cli, srv, B, n, sg, seg_host, t, k, bins, shift, dist, pos, st);
 }
 
 }  // namespace sanns

@@ -79,3 +79,51 @@ def test_first_configuration_end_to_end_top10():
     ids = perm[gp.cpu().numpy()[0]]
     assert np.array_equal(np.sort(np.sum((coords[ids].astype(np.int64) - q[0]) ** 2, axis=1)),
                           np.array(ev))
+
+
+@pytest.mark.parametrize("k,bins", [(10, 0), (10, 40), (40, 0), (40, 64)])
+def test_topk_segments_matches_oracle(ctx, k, bins):
+    # ragged lists: empty, shorter than k, shorter than the bins, long ones;
+    # increasing offsets with gaps in the client shares, a shuffled order in
+    # the server shares
+    t = ctx.query()["t"]
+    rnd = np.random.default_rng(k * 7 + bins)
+    lens = np.array([0, 3, k - 1, k, bins + 5, 999, 70_001, 5, 20_000], dtype=np.int64)
+    B = len(lens)
+    gaps = rnd.integers(0, 50, size=B)
+    co = np.concatenate([[0], np.cumsum(lens + gaps)[:-1]]) + gaps
+    order = rnd.permutation(B)
+    so = np.zeros(B, dtype=np.int64)
+    so[order] = np.concatenate([[0], np.cumsum(lens[order] + 3)[:-1]])
+    srv = rnd.integers(0, t, size=int(so.max() + lens.max() + 10)).astype(np.int64)
+    cli = rnd.integers(0, t, size=int(co[-1] + lens[-1] + 10)).astype(np.int64)
+    want = []
+    for b in range(B):
+        v = rnd.integers(0, 300, size=lens[b]).astype(np.int64)       # many ties
+        cli[co[b]:co[b] + lens[b]] = (v - srv[so[b]:so[b] + lens[b]]) % t
+        want.append(v)
+    for shift in (0, 2):
+        gd, gp = S.sanns_topk_segments(ctx, cu(cli.astype(np.uint32)), cu(srv.astype(np.uint32)),
+                                       co, so, lens, k, bins, shift)
+        gd, gp = gd.cpu().numpy(), gp.cpu().numpy()
+        for b in range(B):
+            ds = want[b] >> shift
+            n = int(lens[b])
+            pos = np.arange(n)
+            lb = min(bins, n)
+            if bins and lb >= 1:
+                ov, oi = select.approx_topk_by_position(ds, pos, min(k, lb), lb)
+            else:
+                ov, oi = select.exact_topk(ds, pos, min(k, n))
+            fill = k - len(ov)
+            assert gd[b].tolist() == ov + [2 ** 32 - 1] * fill, (b, shift)
+            assert gp[b].tolist() == oi + [-1] * fill, (b, shift)
+
+
+def test_topk_segments_rejects_bad_arguments(ctx):
+    z = torch.zeros(100, dtype=torch.uint32, device="cuda")
+    one = np.array([0])
+    for k, bins, shift, ln in [(0, 0, 0, 10), (1025, 0, 0, 10), (10, 5, 0, 10), (10, 0, 32, 10),
+                               (10, 0, 0, 2 ** 32)]:
+        with pytest.raises((S.SannsError, AssertionError)):
+            S.sanns_topk_segments(ctx, z, z, one, one, np.array([ln]), k, bins, shift)
