@@ -583,7 +583,7 @@ def run_cluster_section() -> dict:
 
 ALG4 = dict(n=1_000_000, d=128, N=8192, L=3, prime_bits=60, t_rule=0, n_comp=64, sigma=20.0,
             m=20, alpha=0.56, s_max=31412, k=10, u=(50, 31, 19, 13), l=(458, 270, 178, 84),
-            l_s=262, r_c=5, r_p=8, iters=6, B_lat=16, B_batch=64, seed=31)
+            l_s=262, r_c=5, r_p=8, iters=4, B_lat=16, B_batch=64, seed=31)
 
 
 def run_alg4_section() -> dict:
@@ -630,6 +630,13 @@ def run_alg4_section() -> dict:
     t1 = time.perf_counter()
     ids = cluster.query(srv, sk, q_all, qids, prm)
     batch_ms = (time.perf_counter() - t1) * 1e3
+    # stage split (separate runs: each stage ends in a device synchronisation)
+    st1, st64 = {}, {}
+    for b in range(4):
+        cluster.query(srv, sk, q_all[b:b + 1], qids[b:b + 1], prm, timings=st1)
+    cluster.query(srv, sk, q_all, qids, prm, timings=st64)
+    st1 = {key: round(v / 4, 3) for key, v in st1.items()}
+    st64 = {key: round(v, 3) for key, v in st64.items()}
     # 10-NN accuracy against brute force (exact integer distances)
     xf = coords.to(torch.int64)
     acc = 0.0
@@ -654,6 +661,7 @@ def run_alg4_section() -> dict:
         "u": list(u), "l": list(l), "clustering_s": t_cluster,
         "latency_ms_B1": {"p50": lat[len(lat) // 2], "max": lat[-1], "queries": len(lat)},
         "batch": {"queries": Bb, "ms": batch_ms, "queries_per_s": Bb / (batch_ms * 1e-3)},
+        "stages_ms_B1": st1, "stages_ms_B64": st64,
         "response_blocks_per_query_at_most": blocks,
         "linear_scan_blocks_per_query": -(-n // N),
         "accuracy_10nn": acc,

@@ -28,6 +28,7 @@ from __future__ import annotations
 
 import dataclasses
 import math
+import time
 
 import numpy as np
 import torch
@@ -39,9 +40,17 @@ from . import sanns as S
 # preprocessing
 # ---------------------------------------------------------------------------
 def kmeans(x: torch.Tensor, k: int, iters: int, seed: int):
-    """Lloyd iterations on the GPU: initial centres = the first k points of a
+    """Lloyd iterations (on the GPU in TF32): initial centres = the first k points of a
     seeded permutation; assignment by smallest squared distance (lower centre
     id on ties).  Returns float centres [k][d] and the assignment [n]."""
+    if x.is_cuda and not torch.backends.cuda.matmul.allow_tf32:
+        # the assignment products on the tensor cores in TF32 (uint8 inputs
+        # are exact; the centres round to 10 mantissa bits)
+        torch.backends.cuda.matmul.allow_tf32 = True
+        try:
+            return kmeans(x, k, iters, seed)
+        finally:
+            torch.backends.cuda.matmul.allow_tf32 = False
     xf = x.float()
     g = torch.Generator(device=x.device).manual_seed(seed)
     c = xf[torch.randperm(x.shape[0], generator=g, device=x.device)[:k]].clone()
@@ -203,19 +212,40 @@ class ClusteringServer:
                          if len(layout.stash_perm) else None)
 
 
+class _Stages:
+    """Optional per-stage wall clock (device synchronised at each mark)."""
+
+    def __init__(self, out):
+        self.out = out
+        self.t = time.perf_counter() if out is not None else 0.0
+
+    def mark(self, name):
+        if self.out is None:
+            return
+        torch.cuda.synchronize()
+        now = time.perf_counter()
+        self.out[name] = self.out.get(name, 0.0) + (now - self.t) * 1e3
+        self.t = now
+
+
 def query(server: ClusteringServer, sk: S.SecretKey, q: torch.Tensor, qids: torch.Tensor,
-          prm: Params, seeds=(101, 102, 103, 104), stream=None) -> np.ndarray:
+          prm: Params, seeds=(101, 102, 103, 104), stream=None, timings: dict | None = None) -> np.ndarray:
     """Algorithm 4 for B queries (uint8 [B][d] on the GPU); returns the k
     neighbour ids per query [B][k] (host; -1 where fewer than k points were
-    searched)."""
+    searched).  A dict passed as `timings` accumulates milliseconds per stage
+    (the device is synchronised between stages)."""
+    st_ = _Stages(timings)
     ctx, lay = server.ctx, server.layout
     B, k, N = q.shape[0], prm.k, ctx.N
     ar = np.arange(B, dtype=np.uint64)
     ct = S.sanns_encrypt_query(ctx, sk, q, seeds[0], qids, stream=stream)
+    st_.mark("encrypt")
     # 2. centres: encrypted distances, client shares, ApproxTopk per group
     nc = int(lay.group_offsets[-1])
     out_c, srv_c = S.sanns_distances(ctx, server.centres_db, ct, seeds[1], qids, stream=stream)
+    st_.mark("centres_distances")
     cli_c = S.sanns_decrypt_shares(ctx, sk, out_c, nc, q, stream=stream)
+    st_.mark("centres_decrypt")
     picks = []
     for i in range(len(lay.group_offsets) - 1):
         g0, g1 = int(lay.group_offsets[i]), int(lay.group_offsets[i + 1])
@@ -227,11 +257,13 @@ def query(server: ClusteringServer, sk: S.SecretKey, q: torch.Tensor, qids: torc
         picks.append((g0, pos))
     probes = np.concatenate([lay.centre_cluster[g0 + pos.cpu().numpy()] for g0, pos in picks],
                             axis=1).astype(np.uint32)
+    st_.mark("centres_select")
     # 3. the selected clusters' points in one persistent launch; every
     #    response block decrypted in one call (block j of query b carries
     #    query b's norm); exact top-k over the B ragged lists
     out_g, srv_g, ids_g, n_b, k_b = S.sanns_distances_gather(ctx, server.clusters, ct, probes,
                                                             seeds[2], qids, stream=stream)
+    st_.mark("gather")
     kb = k_b.astype(np.int64)
     blk = np.concatenate([[0], np.cumsum(kb)])
     pts = np.concatenate([[0], np.cumsum(n_b.astype(np.int64))])
@@ -241,8 +273,10 @@ def query(server: ClusteringServer, sk: S.SecretKey, q: torch.Tensor, qids: torc
                                        stream=stream)
     else:   # nothing gathered (only empty clusters selected)
         cli_g = srv_g = torch.zeros(1, dtype=torch.uint32, device=q.device)
+    st_.mark("gather_decrypt")
     dv_c, dp_c = S.sanns_topk_segments(ctx, cli_g, srv_g, blk[:-1] * N, pts[:-1], n_b, k, 0, prm.r_p,
                                        stream=stream)
+    st_.mark("gather_select")
     # 4. the stash: linear scan, ApproxTopk (fills past the stash's size)
     ns = len(lay.stash_perm)
     if ns:
@@ -257,6 +291,7 @@ def query(server: ClusteringServer, sk: S.SecretKey, q: torch.Tensor, qids: torc
         z = torch.zeros(1, dtype=torch.uint32, device=q.device)
         dv_s, dp_s = S.sanns_topk_segments(ctx, z, z, np.zeros(B), np.zeros(B), np.zeros(B), k,
                                            stream=stream)
+    st_.mark("stash")
     # 5. the k smallest of the 2k candidates (cluster candidates first on
     #    ties), as shares (candidate value, 0).  A fill value 2^32 - 1
     #    reconstructs to 2^32 - 1 - t, above every distance (t < 2^31).
@@ -274,4 +309,5 @@ def query(server: ClusteringServer, sk: S.SecretKey, q: torch.Tensor, qids: torc
             if p < 0:
                 continue
             out[b, r] = ids_h[pts[b] + p] if j < k else int(lay.stash_perm[p])
+    st_.mark("final")
     return out

@@ -9,13 +9,21 @@
 // secret shares through DORAM; here the server holds them in the clear.
 //
 // Two launches:
-//   pack       one thread per gathered position: finds the probe segment by
-//              binary search, copies the point's d bytes into a
-//              coordinate-major tile [item][i][x] and its ||p||^2;
-//   persistent one block per multiprocessor walks the (query, block) work
-//              items of every query -- uneven per-query counts included --
-//              and runs encode (NTT) -> MAC -> INTT -> mask for each item,
-//              with the polynomial and both accumulators in shared memory.
+//   pack        one thread per gathered position: finds the probe segment by
+//               binary search, copies the point's d bytes into a
+//               coordinate-major tile [item][i][x] and its ||p||^2;
+//   persistent  one block per multiprocessor walks the units (work item,
+//               prime j, slice of the dimensions) of every query -- uneven
+//               per-query counts included: the slice's encodings (NTT of the
+//               coordinate polynomials) times the query's c0 and c1, summed
+//               mod q_j into a partial accumulator.  The block that completes
+//               the last slice of an (item, prime) (a ticket counter after a
+//               memory fence; nobody waits) sums the partials mod q_j (the
+//               order does not matter, so the result is exact), runs the
+//               INTT, adds Delta (||p||^2 + r) to c0, stores both components
+//               and the server share t - r.  Slices are sized so that even a
+//               single work item spreads over every multiprocessor.
+// A work item is one block of N positions of one query's gathered list.
 #include <vector>
 
 #include "internal.h"
@@ -85,72 +93,107 @@ __device__ __forceinline__ uint64_t mont_mul(uint64_t c, uint64_t p_mont, uint64
   return csub(redc128((u128)c * p_mont, q, qn), q);
 }
 
-// One block per work item at a time; shared memory holds the polynomial being
-// transformed and the two accumulators (c0, c1) of the current prime.
+// Back to coefficient form and mask (c = 0), store: one component of one
+// (item, prime) held in a (padded shared memory).
+__device__ void gather_finish(uint64_t* a, const PrimeSet& P, uint32_t j, uint32_t c, uint64_t w,
+                              const GatherItem& it, const GatherQuery& Q, const uint32_t* gnorm,
+                              uint64_t mask_seed, uint64_t qid, uint64_t* ct_out, uint32_t* srv_share) {
+  const uint32_t N = P.N, L = P.L;
+  const uint64_t q = P.q[j];
+  __syncthreads();
+  ntt_inverse_smem(a, P, (int)j);
+  __syncthreads();
+  if (c == 0) {
+    const uint64_t dl = P.delta[j], dls = P.delta_shoup[j];
+    for (uint32_t t4 = threadIdx.x; t4 < N / 4; t4 += blockDim.x) {
+      const uint64_t pos0 = (uint64_t)it.kb * N + 4 * t4;
+      uint32_t blk[16];
+      chacha20_block(mask_seed, kPurposeMask, qid, (uint32_t)(pos0 / 4), blk);
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        uint64_t lo, hi;
+        draw_pair(blk, v, lo, hi);
+        const uint64_t rr = mod_t128(lo, hi, P);
+        const uint32_t x = 4 * t4 + v;
+        const uint64_t val = mod_t64((uint64_t)gnorm[w * N + x] + rr, P.t, P.t_barrett);
+        a[SP(x)] = add_mod(a[SP(x)], mul_shoup(val, dl, dls, q), q);
+        const uint64_t pos = pos0 + v;
+        if (j == 0 && pos < Q.n) srv_share[Q.pos_off + pos] = (uint32_t)(rr == 0 ? 0 : P.t - rr);
+      }
+    }
+    __syncthreads();
+  }
+  uint64_t* dst = ct_out + ((it.blk * 2 + c) * L + j) * N;
+  for (uint32_t x = threadIdx.x; x < N; x += blockDim.x) dst[x] = a[SP(x)];
+}
+
+// Persistent: block k takes units k, k + grid, ..; unit u = (w L + j) S + s.
+// Shared memory holds the polynomial being transformed and the unit's two
+// accumulators (c0, c1).
 __global__ void __launch_bounds__(512, 1)
-gather_kernel(PrimeSet P, uint32_t d, uint64_t W, const GatherItem* __restrict__ items,
-              const GatherQuery* __restrict__ qs, const uint8_t* __restrict__ gco,
-              const uint32_t* __restrict__ gnorm, const uint64_t* __restrict__ ct_in,
-              uint64_t mask_seed, const uint64_t* __restrict__ qids,
-              uint64_t* __restrict__ ct_out, uint32_t* __restrict__ srv_share) {
+gather_kernel(PrimeSet P, uint32_t d, uint64_t W, uint32_t S, uint32_t ds,
+              const GatherItem* __restrict__ items, const GatherQuery* __restrict__ qs,
+              const uint8_t* __restrict__ gco, const uint32_t* __restrict__ gnorm,
+              const uint64_t* __restrict__ ct_in, uint64_t mask_seed, const uint64_t* __restrict__ qids,
+              uint64_t* __restrict__ part, uint32_t* __restrict__ tickets, uint64_t* __restrict__ ct_out,
+              uint32_t* __restrict__ srv_share) {
   extern __shared__ uint64_t smem[];
+  __shared__ uint32_t ticket;
   const uint32_t N = P.N, L = P.L;
   const uint32_t PW = ntt_smem_words(N);
   uint64_t* poly = smem;
   uint64_t* acc0 = smem + PW;
   uint64_t* acc1 = smem + 2 * PW;
-  for (uint64_t w = blockIdx.x; w < W; w += gridDim.x) {
+  const uint64_t units = W * L * S;
+  for (uint64_t u = blockIdx.x; u < units; u += gridDim.x) {
+    const uint32_t sl = (uint32_t)(u % S);
+    const uint64_t wj = u / S;
+    const uint32_t j = (uint32_t)(wj % L);
+    const uint64_t w = wj / L;
     const GatherItem it = items[w];
-    const GatherQuery Q = qs[it.b];
     const uint8_t* g = gco + w * (uint64_t)d * N;
-    for (uint32_t j = 0; j < L; ++j) {
-      const uint64_t q = P.q[j], qn = P.q_neg_inv[j];
-      for (uint32_t s = threadIdx.x; s < N; s += blockDim.x) acc0[SP(s)] = acc1[SP(s)] = 0;
-      for (uint32_t i = 0; i < d; ++i) {
-        __syncthreads();
-        for (uint32_t x = threadIdx.x; x < N; x += blockDim.x) poly[SP(x)] = g[(uint64_t)i * N + x];
-        __syncthreads();
-        ntt_forward_smem(poly, P, (int)j);
-        __syncthreads();
-        const uint64_t* c0 = ct_in + ((((uint64_t)it.b * d + i) * 2 + 0) * L + j) * N;
-        const uint64_t* c1 = ct_in + ((((uint64_t)it.b * d + i) * 2 + 1) * L + j) * N;
-        for (uint32_t s = threadIdx.x; s < N; s += blockDim.x) {
-          const uint64_t pm = mul_shoup(poly[SP(s)], P.r64[j], P.r64_shoup[j], q);
-          acc0[SP(s)] = add_mod(acc0[SP(s)], mont_mul(__ldg(c0 + s), pm, q, qn), q);
-          acc1[SP(s)] = add_mod(acc1[SP(s)], mont_mul(__ldg(c1 + s), pm, q, qn), q);
-        }
+    const uint64_t q = P.q[j], qn = P.q_neg_inv[j];
+    const uint32_t i0 = sl * ds, i1 = i0 + ds < d ? i0 + ds : d;
+    __syncthreads();
+    for (uint32_t x = threadIdx.x; x < N; x += blockDim.x) acc0[SP(x)] = acc1[SP(x)] = 0;
+    for (uint32_t i = i0; i < i1; ++i) {
+      __syncthreads();
+      for (uint32_t x = threadIdx.x; x < N; x += blockDim.x) poly[SP(x)] = g[(uint64_t)i * N + x];
+      __syncthreads();
+      ntt_forward_smem(poly, P, (int)j);
+      __syncthreads();
+      const uint64_t* c0 = ct_in + ((((uint64_t)it.b * d + i) * 2 + 0) * L + j) * N;
+      const uint64_t* c1 = ct_in + ((((uint64_t)it.b * d + i) * 2 + 1) * L + j) * N;
+      for (uint32_t x = threadIdx.x; x < N; x += blockDim.x) {
+        const uint64_t pm = mul_shoup(poly[SP(x)], P.r64[j], P.r64_shoup[j], q);
+        acc0[SP(x)] = add_mod(acc0[SP(x)], mont_mul(__ldg(c0 + x), pm, q, qn), q);
+        acc1[SP(x)] = add_mod(acc1[SP(x)], mont_mul(__ldg(c1 + x), pm, q, qn), q);
       }
-      // back to coefficient form, mask, store
-      for (uint32_t c = 0; c < 2; ++c) {
-        uint64_t* a = c == 0 ? acc0 : acc1;
-        __syncthreads();
-        ntt_inverse_smem(a, P, (int)j);
-        __syncthreads();
-        if (c == 0) {
-          const uint64_t dl = P.delta[j], dls = P.delta_shoup[j];
-          const uint64_t qid = qids[it.b];
-          for (uint32_t u = threadIdx.x; u < N / 4; u += blockDim.x) {
-            const uint64_t pos0 = (uint64_t)it.kb * N + 4 * u;
-            uint32_t blk[16];
-            chacha20_block(mask_seed, kPurposeMask, qid, (uint32_t)(pos0 / 4), blk);
-#pragma unroll
-            for (int v = 0; v < 4; ++v) {
-              uint64_t lo, hi;
-              draw_pair(blk, v, lo, hi);
-              const uint64_t rr = mod_t128(lo, hi, P);
-              const uint32_t x = 4 * u + v;
-              const uint64_t val = mod_t64((uint64_t)gnorm[w * N + x] + rr, P.t, P.t_barrett);
-              a[SP(x)] = add_mod(a[SP(x)], mul_shoup(val, dl, dls, q), q);
-              const uint64_t pos = pos0 + v;
-              if (j == 0 && pos < Q.n)
-                srv_share[Q.pos_off + pos] = (uint32_t)(rr == 0 ? 0 : P.t - rr);
-            }
-          }
-          __syncthreads();
-        }
-        uint64_t* dst = ct_out + ((it.blk * 2 + c) * L + j) * N;
-        for (uint32_t x = threadIdx.x; x < N; x += blockDim.x) dst[x] = a[SP(x)];
+    }
+    __syncthreads();
+    // publish the partial, then take a ticket; the last slice finishes
+    uint64_t* mine = part + u * 2 * N;
+    for (uint32_t x = threadIdx.x; x < N; x += blockDim.x) {
+      mine[x] = acc0[SP(x)];
+      mine[N + x] = acc1[SP(x)];
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) ticket = atomicAdd(tickets + wj, 1u);
+    __syncthreads();
+    if (ticket != S - 1) continue;
+    __threadfence();
+    const GatherQuery Q = qs[it.b];
+    const uint64_t qid = qids[it.b];
+    const uint64_t* all = part + wj * S * 2 * N;
+    for (uint32_t c = 0; c < 2; ++c) {
+      uint64_t* a = c == 0 ? acc0 : acc1;
+      for (uint32_t x = threadIdx.x; x < N; x += blockDim.x) {
+        uint64_t v = 0;
+        for (uint32_t s2 = 0; s2 < S; ++s2) v = add_mod(v, __ldcg(all + ((uint64_t)s2 * 2 + c) * N + x), q);
+        a[SP(x)] = v;
       }
+      gather_finish(a, P, j, c, w, it, Q, gnorm, mask_seed, qid, ct_out, srv_share);
     }
   }
 }
@@ -198,8 +241,17 @@ cudaError_t launch_gather(const PrimeSet& P, uint32_t d, const sanns_clusters* c
   const size_t sz_seg = sizeof(uint64_t) * seg.size(), sz_pr = sizeof(uint32_t) * (size_t)B * Pr;
   auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
   const size_t o_items = 0, o_qs = up(sz_items), o_seg = o_qs + up(sz_qs), o_pr = o_seg + up(sz_seg);
+  // dimension slices per (item, prime): about four units per multiprocessor
+  // in all, at least one dimension per slice
+  const uint64_t nsm = (uint64_t)(sms > 0 ? sms : 148);
+  const uint64_t want = (4 * nsm + W * P.L - 1) / (W * P.L);
+  const uint32_t S0 = (uint32_t)(want < d ? want : d);
+  const uint32_t ds = (d + S0 - 1) / S0;
+  const uint32_t S = (d + ds - 1) / ds;
   const size_t o_norm = o_pr + up(sz_pr), o_gco = o_norm + up(sizeof(uint32_t) * W * N);
-  const size_t total = o_gco + up((size_t)W * d * N);
+  const size_t o_part = o_gco + up((size_t)W * d * N);
+  const size_t o_tick = o_part + up(sizeof(uint64_t) * (size_t)W * P.L * S * 2 * N);
+  const size_t total = o_tick + up(sizeof(uint32_t) * (size_t)W * P.L);
   uint8_t* scratch = nullptr;
   cudaError_t e = cudaMallocAsync(&scratch, total, st);
   if (e != cudaSuccess) return e;
@@ -219,16 +271,19 @@ cudaError_t launch_gather(const PrimeSet& P, uint32_t d, const sanns_clusters* c
         cl->d_coords, scratch + o_gco, reinterpret_cast<uint32_t*>(scratch + o_norm), ids);
     e = cudaGetLastError();
   }
+  uint64_t* part = reinterpret_cast<uint64_t*>(scratch + o_part);
+  uint32_t* tickets = reinterpret_cast<uint32_t*>(scratch + o_tick);
+  if (e == cudaSuccess) e = cudaMemsetAsync(tickets, 0, sizeof(uint32_t) * (size_t)W * P.L, st);
   if (e == cudaSuccess) {
     const int th = gather_threads(N);
     const size_t smem = sizeof(uint64_t) * 3 * ntt_smem_words(N);
-    const uint64_t nsm = (uint64_t)(sms > 0 ? sms : 148);
-    const unsigned grid = (unsigned)(W < nsm ? W : nsm);
+    const uint64_t units = W * P.L * S;
+    const unsigned grid = (unsigned)(units < nsm ? units : nsm);
     e = cudaFuncSetAttribute(gather_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e == cudaSuccess) {
-      gather_kernel<<<grid, th, smem, st>>>(P, d, W, d_items, d_qs, scratch + o_gco,
-                                            reinterpret_cast<const uint32_t*>(scratch + o_norm),
-                                            ct_in, mask_seed, qids, ct_out, srv_share);
+      gather_kernel<<<grid, th, smem, st>>>(P, d, W, S, ds, d_items, d_qs, scratch + o_gco,
+                                            reinterpret_cast<const uint32_t*>(scratch + o_norm), ct_in,
+                                            mask_seed, qids, part, tickets, ct_out, srv_share);
       e = cudaGetLastError();
     }
   }
