@@ -627,9 +627,13 @@ def run_alg4_section() -> dict:
         t1 = time.perf_counter()
         cluster.query(srv, sk, q_all[b:b + 1], qids[b:b + 1], prm)
         lat.append((time.perf_counter() - t1) * 1e3)
+    ids = cluster.query(srv, sk, q_all, qids, prm)            # warm-up at the batch size
+    torch.cuda.synchronize()
+    reps = 3
     t1 = time.perf_counter()
-    ids = cluster.query(srv, sk, q_all, qids, prm)
-    batch_ms = (time.perf_counter() - t1) * 1e3
+    for _ in range(reps):
+        ids = cluster.query(srv, sk, q_all, qids, prm)
+    batch_ms = (time.perf_counter() - t1) * 1e3 / reps
     # stage split (separate runs: each stage ends in a device synchronisation)
     st1, st64 = {}, {}
     for b in range(4):

@@ -311,18 +311,23 @@ int sanns_topk(sanns_ctx *ctx, const uint32_t *cli_dev, const uint32_t *srv_dev,
  * The same selection over B ragged lists (Algorithm 4: the points gathered
  * for each query, the centres of one group): list b is positions x <
  * len[b] of cli_dev + cli_off[b] and srv_dev + srv_off[b]; positions in the
- * output count from the list's start.  With bins = l, list b uses
- * min(l, len[b]) bins (every position its own bin, i.e. exact, when len[b]
- * <= l).  A list shorter than k fills its last k - len[b] outputs with dist
- * 2^32 - 1 and pos 2^64 - 1 (also the uniform call's convention, which never
- * produces them).  cli_off, srv_off and len are HOST arrays of B entries,
- * read before the call returns; the device shares must hold every listed
- * element.  Needs 1 <= k <= 1024, B <= 65535, len[b] < 2^32, bins = 0 or
- * bins >= k, shift <= 31; SANNS_EINVAL otherwise.  Stream-ordered scratch;
- * the host arrays are copied (pageable) on stream.
+ * output count from the list's start.  List b selects k_b = k_seg[b]
+ * winners (k_seg NULL: k for every list; 1 <= k_b <= k).  With bins = 0 every
+ * list is exact; otherwise list b is ApproxTopk over l_b = bins_seg[b]
+ * (bins_seg NULL: bins; k_b <= l_b <= bins) bins, of which it uses
+ * min(l_b, len[b]) (every position its own bin, i.e. exact, when len[b] <=
+ * l_b).  Outputs are [B][k]: list b's k_b winners, then fill entries with
+ * dist 2^32 - 1 and pos 2^64 - 1 (also where a list holds fewer than k_b
+ * elements; the uniform call never produces them).  cli_off, srv_off, len,
+ * k_seg and bins_seg are HOST arrays of B entries, read before the call
+ * returns; the device shares must hold every listed element.  Needs 1 <= k <=
+ * 1024, B <= 65535, len[b] < 2^32, bins = 0 or bins >= k_b, shift <= 31;
+ * SANNS_EINVAL otherwise.  Stream-ordered scratch; the host arrays are copied
+ * (pageable) on stream.
  */
 int sanns_topk_segments(sanns_ctx *ctx, const uint32_t *cli_dev, const uint32_t *srv_dev, uint32_t B,
-                        const uint64_t *cli_off, const uint64_t *srv_off, const uint64_t *len, uint32_t k,
+                        const uint64_t *cli_off, const uint64_t *srv_off, const uint64_t *len,
+                        const uint32_t *k_seg, const uint64_t *bins_seg, uint32_t k,
                         uint64_t bins, uint32_t shift, uint32_t *dist_dev, uint64_t *pos_dev, void *stream);
 
 /*

@@ -202,7 +202,10 @@ class ClusteringServer:
     """The server's encoded state: centre list, clusters (gather path) and
     stash (linear scan), all resident on the GPU."""
 
-    def __init__(self, ctx: S.Context, coords: torch.Tensor, layout: Layout):
+    def __init__(self, ctx: S.Context, coords: torch.Tensor, layout: Layout, batched_min: int = 16):
+        """batched_min: from this many queries per call on, the centre and
+        stash distances run on the tensor-core batched path (bit-identical
+        results; needs d <= 128, else the per-query path always runs)."""
         self.ctx, self.layout = ctx, layout
         self.coords = coords
         self.centres_db = S.sanns_encode_db(ctx, torch.from_numpy(layout.centres).cuda())
@@ -210,6 +213,17 @@ class ClusteringServer:
                                                 torch.from_numpy(layout.cl_members).cuda())
         self.stash_db = (S.sanns_encode_db(ctx, coords, torch.from_numpy(layout.stash_perm).cuda())
                          if len(layout.stash_perm) else None)
+        self.batched_min = batched_min if ctx.d <= 128 else 0
+        if self.batched_min:
+            for db in (self.centres_db, self.stash_db):
+                if db is not None:
+                    S.sanns_db_prepare_batched(ctx, db)
+
+    def distances(self, db, ct, seed, qids, stream=None):
+        B = ct.shape[0]
+        if self.batched_min and B >= self.batched_min:
+            return S.sanns_distances_batched(self.ctx, db, ct, seed, qids, stream=stream)
+        return S.sanns_distances(self.ctx, db, ct, seed, qids, stream=stream)
 
 
 class _Stages:
@@ -242,21 +256,34 @@ def query(server: ClusteringServer, sk: S.SecretKey, q: torch.Tensor, qids: torc
     st_.mark("encrypt")
     # 2. centres: encrypted distances, client shares, ApproxTopk per group
     nc = int(lay.group_offsets[-1])
-    out_c, srv_c = S.sanns_distances(ctx, server.centres_db, ct, seeds[1], qids, stream=stream)
+    out_c, srv_c = server.distances(server.centres_db, ct, seeds[1], qids, stream=stream)
     st_.mark("centres_distances")
     cli_c = S.sanns_decrypt_shares(ctx, sk, out_c, nc, q, stream=stream)
     st_.mark("centres_decrypt")
-    picks = []
-    for i in range(len(lay.group_offsets) - 1):
-        g0, g1 = int(lay.group_offsets[i]), int(lay.group_offsets[i + 1])
-        u = min(prm.u[i], g1 - g0)
-        bins = max(min(prm.l[i], g1 - g0), u) if prm.l[i] else 0
-        off = ar * nc + g0
-        _, pos = S.sanns_topk_segments(ctx, cli_c, srv_c, off, off, np.full(B, g1 - g0), u, bins,
-                                       prm.r_c, stream=stream)
-        picks.append((g0, pos))
-    probes = np.concatenate([lay.centre_cluster[g0 + pos.cpu().numpy()] for g0, pos in picks],
-                            axis=1).astype(np.uint32)
+    # every (group, query) list in one call per selection mode (ApproxTopk
+    # where the group has bins, exact where it has none)
+    T = len(lay.group_offsets) - 1
+    g0s, g1s = lay.group_offsets[:-1].astype(np.int64), lay.group_offsets[1:].astype(np.int64)
+    us = np.minimum(np.asarray(prm.u[:T], dtype=np.int64), g1s - g0s)
+    ls = np.array([max(min(int(prm.l[i]), int(g1s[i] - g0s[i])), int(us[i])) if prm.l[i] else 0
+                   for i in range(T)], dtype=np.int64)
+    cols = [None] * T
+    for approx in (True, False):
+        grp = [i for i in range(T) if (ls[i] > 0) == approx]
+        if not grp:
+            continue
+        gi = np.repeat(np.array(grp), B)                      # segment = (group, query)
+        bi = np.tile(np.arange(B, dtype=np.int64), len(grp))
+        off = bi * nc + g0s[gi]
+        kmax = int(us[grp].max())
+        _, pos = S.sanns_topk_segments(ctx, cli_c, srv_c, off, off, (g1s - g0s)[gi], kmax,
+                                       int(ls[grp].max()) if approx else 0, prm.r_c,
+                                       k_seg=us[gi], bins_seg=ls[gi] if approx else None,
+                                       stream=stream)
+        pos = pos.cpu().numpy().reshape(len(grp), B, kmax)
+        for r, i in enumerate(grp):
+            cols[i] = lay.centre_cluster[g0s[i] + pos[r, :, :us[i]]]
+    probes = np.concatenate(cols, axis=1).astype(np.uint32)
     st_.mark("centres_select")
     # 3. the selected clusters' points in one persistent launch; every
     #    response block decrypted in one call (block j of query b carries
@@ -280,7 +307,7 @@ def query(server: ClusteringServer, sk: S.SecretKey, q: torch.Tensor, qids: torc
     # 4. the stash: linear scan, ApproxTopk (fills past the stash's size)
     ns = len(lay.stash_perm)
     if ns:
-        out_s, srv_s = S.sanns_distances(ctx, server.stash_db, ct, seeds[3], qids, stream=stream)
+        out_s, srv_s = server.distances(server.stash_db, ct, seeds[3], qids, stream=stream)
         cli_s = S.sanns_decrypt_shares(ctx, sk, out_s, ns, q, stream=stream)
         bins = max(min(prm.l_s, ns), min(k, ns)) if prm.l_s else 0
         bins = bins if bins >= k else 0     # fewer than k bins: every stash point is a candidate

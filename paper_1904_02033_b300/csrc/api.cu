@@ -366,8 +366,8 @@ int sanns_topk(sanns_ctx* ctx, const uint32_t* cli, const uint32_t* srv, uint32_
 
 int sanns_topk_segments(sanns_ctx* ctx, const uint32_t* cli, const uint32_t* srv, uint32_t B,
                         const uint64_t* cli_off, const uint64_t* srv_off, const uint64_t* len,
-                        uint32_t k, uint64_t bins, uint32_t shift, uint32_t* dist, uint64_t* pos,
-                        void* stream) {
+                        const uint32_t* k_seg, const uint64_t* bins_seg, uint32_t k, uint64_t bins,
+                        uint32_t shift, uint32_t* dist, uint64_t* pos, void* stream) {
   if (!ctx) return fail(SANNS_EINVAL, "ctx is NULL");
   if (B == 0) return SANNS_OK;
   if (!cli || !srv || !dist || !pos || !cli_off || !srv_off || !len)
@@ -376,12 +376,18 @@ int sanns_topk_segments(sanns_ctx* ctx, const uint32_t* cli, const uint32_t* srv
   if (B > 65535) return fail(SANNS_EINVAL, "B must be <= 65535");
   if (shift > 31) return fail(SANNS_EINVAL, "shift must be <= 31");
   if (bins && bins < k) return fail(SANNS_EINVAL, "need bins = 0 or bins >= k");
-  std::vector<uint64_t> seg(3 * (size_t)B);
+  std::vector<uint64_t> seg(5 * (size_t)B);
   for (uint32_t b = 0; b < B; ++b) {
     if (len[b] >= (1ull << 32)) return fail(SANNS_EINVAL, "segment longer than 2^32 - 1");
+    const uint64_t kb = k_seg ? k_seg[b] : k;
+    const uint64_t lb = bins_seg ? bins_seg[b] : bins;
+    if (kb < 1 || kb > k) return fail(SANNS_EINVAL, "need 1 <= k_seg[b] <= k");
+    if (bins && (lb < kb || lb > bins)) return fail(SANNS_EINVAL, "need k_seg[b] <= bins_seg[b] <= bins");
     seg[b] = cli_off[b];
     seg[B + b] = srv_off[b];
     seg[2 * (size_t)B + b] = len[b];
+    seg[3 * (size_t)B + b] = kb;
+    seg[4 * (size_t)B + b] = lb;
   }
   int rc = check_device(ctx);
   if (rc) return rc;

@@ -34,6 +34,8 @@ struct Segs {
   const uint64_t* srv_off;
   const uint64_t* len;
   uint64_t n;
+  const uint64_t* kseg;  // winners per segment (NULL: k for all)
+  const uint64_t* lseg;  // bins per segment (NULL: l for all)
 };
 
 __device__ __forceinline__ void seg_of(const Segs& sg, uint64_t b, uint64_t& co, uint64_t& so,
@@ -129,7 +131,7 @@ __global__ void __launch_bounds__(kTopkThreads) topk_shares_kernel(const uint32_
 }
 
 // Bin minima for ApproxTopk: one warp per bin i of segment b, l_b =
-// min(l, length) bins, bin i = positions [ceil(i n / l_b), ceil((i + 1) n / l_b));
+// min(l, length) bins (l per segment where given), bin i = positions [ceil(i n / l_b), ceil((i + 1) n / l_b));
 // mins[b][i] = the smallest key of the bin (missing for i >= l_b).  l_b = n
 // puts every position in a bin of its own: the selection is then exact.
 __global__ void __launch_bounds__(kTopkThreads) bin_min_kernel(const uint32_t* __restrict__ cli,
@@ -142,7 +144,8 @@ __global__ void __launch_bounds__(kTopkThreads) bin_min_kernel(const uint32_t* _
   if (i >= l) return;
   uint64_t co, so, n;
   seg_of(sg, b, co, so, n);
-  const uint64_t lb = l < n ? l : n;
+  const uint64_t ls = sg.lseg ? sg.lseg[b] : l;
+  const uint64_t lb = ls < n ? ls : n;
   uint64_t m = kNoKey;
   if (i < lb) {
     const uint64_t p0 = (i * n + lb - 1) / lb, p1 = ((i + 1) * n + lb - 1) / lb;
@@ -220,12 +223,13 @@ __global__ void __launch_bounds__(kSortThreads) topk_sort_kernel(const uint64_t*
 }
 
 // Split the keys: dist[b][r] = key >> 32, pos[b][r] = key & (2^32 - 1); a
-// missing key gives dist 2^32 - 1, pos 2^64 - 1.
-__global__ void topk_split_kernel(const uint64_t* __restrict__ keys, uint64_t count,
+// missing key, or r past segment b's own k, gives dist 2^32 - 1, pos 2^64 - 1.
+__global__ void topk_split_kernel(const uint64_t* __restrict__ keys, uint64_t count, uint32_t k, Segs sg,
                                   uint32_t* __restrict__ dist, uint64_t* __restrict__ pos) {
   const uint64_t e = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
   if (e >= count) return;
-  const uint64_t key = keys[e];
+  uint64_t key = keys[e];
+  if (sg.kseg && e % k >= sg.kseg[e / k]) key = kNoKey;  // past the segment's own k
   dist[e] = (uint32_t)(key >> 32);
   pos[e] = key == kNoKey ? kNoKey : (key & 0xffffffffull);
 }
@@ -274,8 +278,8 @@ cudaError_t reduce_keys(const uint64_t* keys, uint32_t B, uint64_t m, int k, uin
 }  // namespace
 
 // Selection over B segments; n is the longest segment (uniform: every
-// segment), sg tells where they lie (seg_host: host copy of the offsets and
-// lengths, staged into the scratch).
+// segment), sg tells where they lie (seg_host: host copy of [5][B]: client
+// offsets, server offsets, lengths, winners, bins; staged into the scratch).
 static cudaError_t run_topk(const uint32_t* cli, const uint32_t* srv, uint32_t B, uint64_t n, Segs sg,
                             const uint64_t* seg_host, uint64_t t, uint32_t k, uint64_t bins,
                             uint32_t shift, uint32_t* dist, uint64_t* pos, cudaStream_t st) {
@@ -284,7 +288,7 @@ static cudaError_t run_topk(const uint32_t* cli, const uint32_t* srv, uint32_t B
   const uint64_t chunks = n ? (n + chunk - 1) / chunk : 1;
   const uint64_t first = bins ? bins : chunks * k;  // keys per segment after pass 1
   const uint64_t words = 2 * (uint64_t)B * (first + 64);
-  const uint64_t seg_words = seg_host ? 3 * (uint64_t)B : 0;
+  const uint64_t seg_words = seg_host ? 5 * (uint64_t)B : 0;
   uint64_t* scratch = nullptr;
   cudaError_t e = cudaMallocAsync(&scratch, sizeof(uint64_t) * (words + seg_words), st);
   if (e != cudaSuccess) return e;
@@ -296,6 +300,8 @@ static cudaError_t run_topk(const uint32_t* cli, const uint32_t* srv, uint32_t B
     sg.cli_off = d_seg;
     sg.srv_off = d_seg + B;
     sg.len = d_seg + 2 * (uint64_t)B;
+    sg.kseg = d_seg + 3 * (uint64_t)B;
+    sg.lseg = bins ? d_seg + 4 * (uint64_t)B : nullptr;
   }
   if (e == cudaSuccess) {
     if (bins) {
@@ -318,7 +324,7 @@ static cudaError_t run_topk(const uint32_t* cli, const uint32_t* srv, uint32_t B
               : reduce_keys(a, B, first, (int)k, b, a, &res, st);
   if (e == cudaSuccess) {
     const uint64_t count = (uint64_t)B * k;
-    topk_split_kernel<<<(unsigned)((count + 255) / 256), 256, 0, st>>>(res, count, dist, pos);
+    topk_split_kernel<<<(unsigned)((count + 255) / 256), 256, 0, st>>>(res, count, k, sg, dist, pos);
     e = cudaGetLastError();
   }
   cudaError_t e2 = cudaFreeAsync(scratch, st);
@@ -328,7 +334,7 @@ static cudaError_t run_topk(const uint32_t* cli, const uint32_t* srv, uint32_t B
 cudaError_t launch_topk(const uint32_t* cli, const uint32_t* srv, uint32_t B, uint64_t n, uint64_t t,
                         uint32_t k, uint64_t bins, uint32_t shift, uint32_t* dist, uint64_t* pos,
                         cudaStream_t st) {
-  Segs sg{nullptr, nullptr, nullptr, n};
+  Segs sg{nullptr, nullptr, nullptr, n, nullptr, nullptr};
   return run_topk(cli, srv, B, n, sg, nullptr, t, k, bins, shift, dist, pos, st);
 }
 
@@ -337,7 +343,7 @@ cudaError_t launch_topk_segments(const uint32_t* cli, const uint32_t* srv, uint3
                                  uint32_t shift, uint32_t* dist, uint64_t* pos, cudaStream_t st) {
   uint64_t n = 0;
   for (uint32_t b = 0; b < B; ++b) n = seg_host[2 * (uint64_t)B + b] > n ? seg_host[2 * (uint64_t)B + b] : n;
-  Segs sg{nullptr, nullptr, nullptr, 0};
+  Segs sg{nullptr, nullptr, nullptr, 0, nullptr, nullptr};
   return run_topk(cli, srv, B, n, sg, seg_host, t, k, bins, shift, dist, pos, st);
 }
 

@@ -66,8 +66,8 @@ _SIGS = {
     "sanns_set_response_form": ([_VP, C.c_int], C.c_int),
     "sanns_topk": ([_VP, _VP, _VP, C.c_uint32, C.c_uint64, C.c_uint32, C.c_uint64, C.c_uint32, _VP,
                     _VP, _VP], C.c_int),
-    "sanns_topk_segments": ([_VP, _VP, _VP, C.c_uint32, _VP, _VP, _VP, C.c_uint32, C.c_uint64,
-                             C.c_uint32, _VP, _VP, _VP], C.c_int),
+    "sanns_topk_segments": ([_VP, _VP, _VP, C.c_uint32, _VP, _VP, _VP, _VP, _VP, C.c_uint32,
+                             C.c_uint64, C.c_uint32, _VP, _VP, _VP], C.c_int),
     "sanns_circuit_privacy_max_flood_bits": ([_VP], C.c_int),
     "sanns_set_circuit_privacy": ([_VP, _VP, C.c_uint32, _VP], C.c_int),
     "sanns_db_prepare_batched": ([_VP, _VP, _VP], C.c_int),
@@ -403,26 +403,34 @@ def sanns_topk(ctx: Context, cli_share: torch.Tensor, srv_share: torch.Tensor, k
 
 
 def sanns_topk_segments(ctx: Context, cli_share: torch.Tensor, srv_share: torch.Tensor, cli_off,
-                        srv_off, lengths, k: int, bins: int = 0, shift: int = 0, stream=None):
+                        srv_off, lengths, k: int, bins: int = 0, shift: int = 0, k_seg=None,
+                        bins_seg=None, stream=None):
     """Selection over ragged lists: list b is lengths[b] elements at cli_off[b]
-    (client shares) and srv_off[b] (server shares); offsets and lengths are
+    (client shares) and srv_off[b] (server shares), k_seg[b] winners over
+    bins_seg[b] bins where given; offsets, lengths, k_seg and bins_seg are
     host sequences.  Returns (dist [B][k] uint32, pos [B][k] int64, positions
-    from the list's start; a list shorter than k ends in dist 2^32 - 1, pos -1)."""
+    from the list's start; entries past a list's winners hold dist 2^32 - 1,
+    pos -1)."""
     import numpy as np
+    ks = None if k_seg is None else np.ascontiguousarray(k_seg, dtype=np.uint32)
+    bs = None if bins_seg is None else np.ascontiguousarray(bins_seg, dtype=np.uint64)
     assert cli_share.dtype == torch.uint32 and srv_share.dtype == torch.uint32
     co = np.ascontiguousarray(cli_off, dtype=np.uint64)
     so = np.ascontiguousarray(srv_off, dtype=np.uint64)
     ln = np.ascontiguousarray(lengths, dtype=np.uint64)
     B = len(ln)
     assert len(co) == B and len(so) == B
+    assert (ks is None or len(ks) == B) and (bs is None or len(bs) == B)
     assert int((co + ln).max(initial=0)) <= cli_share.numel()
     assert int((so + ln).max(initial=0)) <= srv_share.numel()
     dist = torch.empty((B, k), dtype=torch.uint32, device="cuda")
     pos = torch.empty((B, k), dtype=torch.int64, device="cuda")
     _check(load().sanns_topk_segments(ctx.handle, _ptr(cli_share), _ptr(srv_share), B,
                                       co.ctypes.data_as(C.c_void_p), so.ctypes.data_as(C.c_void_p),
-                                      ln.ctypes.data_as(C.c_void_p), k, bins, shift, _ptr(dist),
-                                      _ptr(pos), _stream(stream)))
+                                      ln.ctypes.data_as(C.c_void_p),
+                                      None if ks is None else ks.ctypes.data_as(C.c_void_p),
+                                      None if bs is None else bs.ctypes.data_as(C.c_void_p),
+                                      k, bins, shift, _ptr(dist), _ptr(pos), _stream(stream)))
     return dist, pos
 
 

@@ -14,14 +14,14 @@ from paper_1904_02033_b300 import sanns as S
 pytestmark = pytest.mark.gpu
 
 
-def _setup(cfg, n, d, s_max, seed=5):
+def _setup(cfg, n, d, s_max, seed=5, batched_min=16):
     coords = inputs.mixture_coords(n, d, 16, 20.0, seed)
     # the layout is the server's preprocessing, built here on CPU tensors
     groups = cluster.balanced_clustering(torch.from_numpy(coords), 300, 0.3, iters=8, seed=1)
     kept, stash = cluster.split_stash(groups, s_max)
     lay = cluster.make_layout(kept, stash, d, seed=7)
     ctx = S.sanns_ctx_create(*cfg)
-    srv = cluster.ClusteringServer(ctx, torch.from_numpy(coords).cuda(), lay)
+    srv = cluster.ClusteringServer(ctx, torch.from_numpy(coords).cuda(), lay, batched_min=batched_min)
     return coords, lay, ctx, srv
 
 
@@ -32,10 +32,12 @@ def _oracle_ids(coords, lay, q, prm, t):
                                       prm.r_c, prm.r_p, t - 1)
 
 
-@pytest.mark.parametrize("cfg,s_max", [((4096, 2, 54, 0, 32), 2000), ((8192, 3, 60, 0, 32), 0)])
-def test_clustering_query_matches_oracle(cfg, s_max):
+@pytest.mark.parametrize("cfg,s_max,batched_min", [((4096, 2, 54, 0, 32), 2000, 16),
+                                                   ((8192, 3, 60, 0, 32), 0, 16),
+                                                   ((8192, 3, 60, 0, 32), 3000, 1)])   # tensor-core path
+def test_clustering_query_matches_oracle(cfg, s_max, batched_min):
     n, d, B = 20000, 32, 6
-    coords, lay, ctx, srv = _setup(cfg, n, d, s_max)
+    coords, lay, ctx, srv = _setup(cfg, n, d, s_max, batched_min=batched_min)
     T = len(lay.group_offsets) - 1
     sizes = np.diff(lay.group_offsets)
     t = ctx.query()["t"]
@@ -49,6 +51,7 @@ def test_clustering_query_matches_oracle(cfg, s_max):
     prms = [
         cluster.Params(k=10, u=pad([8, 4], 2), l=pad([24, 12], 4), l_s=300, r_c=0, r_p=0),
         cluster.Params(k=10, u=pad([8, 4], 2), l=pad([0, 0], 0), l_s=0, r_c=2, r_p=3),
+        cluster.Params(k=10, u=pad([8, 4], 3), l=pad([0, 12], 0), l_s=50, r_c=1, r_p=2),
         # more than 32 winners per group: the shared-memory sort selection
         cluster.Params(k=40, u=pad([min(40, sizes[0]), 4], 2), l=pad([min(60, sizes[0]), 0], 0),
                        l_s=100, r_c=1, r_p=0),

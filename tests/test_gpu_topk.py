@@ -127,3 +127,37 @@ def test_topk_segments_rejects_bad_arguments(ctx):
                                (10, 0, 0, 2 ** 32)]:
         with pytest.raises((S.SannsError, AssertionError)):
             S.sanns_topk_segments(ctx, z, z, one, one, np.array([ln]), k, bins, shift)
+
+
+def test_topk_segments_per_list_k_and_bins(ctx):
+    # every list its own winners and bins (the centre groups of Algorithm 4)
+    t = ctx.query()["t"]
+    rnd = np.random.default_rng(5)
+    lens = np.array([500, 37, 9000, 3, 0, 64], dtype=np.int64)
+    ks = np.array([7, 33, 50, 2, 4, 1])
+    for approx in (False, True):
+        ls = np.array([40, 33, 300, 2, 8, 64]) if approx else None
+        co = np.concatenate([[0], np.cumsum(lens)[:-1]])
+        v = rnd.integers(0, 100, size=int(lens.sum())).astype(np.int64)
+        srv = rnd.integers(0, t, size=len(v)).astype(np.int64)
+        cli = (v - srv) % t
+        kmax = int(ks.max())
+        gd, gp = S.sanns_topk_segments(ctx, cu(cli.astype(np.uint32)), cu(srv.astype(np.uint32)), co, co,
+                                       lens, kmax, int(ls.max()) if approx else 0, 1, k_seg=ks,
+                                       bins_seg=ls)
+        gd, gp = gd.cpu().numpy(), gp.cpu().numpy()
+        for b in range(len(lens)):
+            ds = v[co[b]:co[b] + lens[b]] >> 1
+            n = int(lens[b])
+            kb = min(int(ks[b]), n)
+            if approx and n:
+                lb = min(int(ls[b]), n)
+                ov, oi = select.approx_topk_by_position(ds, np.arange(n), min(int(ks[b]), lb), lb)
+            else:
+                ov, oi = select.exact_topk(ds, np.arange(n), kb)
+            fill = kmax - len(ov)
+            assert gd[b].tolist() == ov + [2 ** 32 - 1] * fill, (approx, b)
+            assert gp[b].tolist() == oi + [-1] * fill, (approx, b)
+    with pytest.raises(S.SannsError):   # a list's k above the call's k
+        S.sanns_topk_segments(ctx, cu(cli.astype(np.uint32)), cu(srv.astype(np.uint32)), co, co, lens, 10,
+                              0, 0, k_seg=ks)
