@@ -583,7 +583,7 @@ def run_cluster_section() -> dict:
 
 ALG4 = dict(n=1_000_000, d=128, N=8192, L=3, prime_bits=60, t_rule=0, n_comp=64, sigma=20.0,
             m=20, alpha=0.56, s_max=31412, k=10, u=(50, 31, 19, 13), l=(458, 270, 178, 84),
-            l_s=262, r_c=5, r_p=8, iters=4, B_lat=16, B_batch=64, seed=31)
+            l_s=262, r_c=5, r_p=8, iters=3, B_lat=16, B_batch=64, seed=31)
 
 
 def run_alg4_section() -> dict:
@@ -605,7 +605,7 @@ def run_alg4_section() -> dict:
     coords = inputs.mixture_coords_device(n, d, W["n_comp"], W["sigma"], W["seed"])
     t0 = time.perf_counter()
     groups = cluster.balanced_clustering(coords, W["m"], W["alpha"], iters=W["iters"], seed=W["seed"],
-                                         max_search=5)
+                                         max_search=3)
     kept, stash = cluster.split_stash(groups, W["s_max"])
     lay = cluster.make_layout(kept, stash, d, seed=W["seed"] + 1)
     t_cluster = time.perf_counter() - t0

@@ -202,10 +202,13 @@ class ClusteringServer:
     """The server's encoded state: centre list, clusters (gather path) and
     stash (linear scan), all resident on the GPU."""
 
-    def __init__(self, ctx: S.Context, coords: torch.Tensor, layout: Layout, batched_min: int = 16):
-        """batched_min: from this many queries per call on, the centre and
-        stash distances run on the tensor-core batched path (bit-identical
-        results; needs d <= 128, else the per-query path always runs)."""
+    def __init__(self, ctx: S.Context, coords: torch.Tensor, layout: Layout, batched_min: int = 16,
+                 batched_min_blocks: int = 128):
+        """From batched_min queries per call on, the centre and stash
+        distances of a list of at least batched_min_blocks blocks run on the
+        tensor-core batched path (bit-identical results; needs d <= 128).  Its
+        per-call expansion of the queries (proportional to B d N L) pays back
+        only over many blocks, so short lists stay on the per-query path."""
         self.ctx, self.layout = ctx, layout
         self.coords = coords
         self.centres_db = S.sanns_encode_db(ctx, torch.from_numpy(layout.centres).cuda())
@@ -214,14 +217,16 @@ class ClusteringServer:
         self.stash_db = (S.sanns_encode_db(ctx, coords, torch.from_numpy(layout.stash_perm).cuda())
                          if len(layout.stash_perm) else None)
         self.batched_min = batched_min if ctx.d <= 128 else 0
+        self.batched_dbs = set()
         if self.batched_min:
             for db in (self.centres_db, self.stash_db):
-                if db is not None:
+                if db is not None and db.K >= batched_min_blocks:
                     S.sanns_db_prepare_batched(ctx, db)
+                    self.batched_dbs.add(id(db))
 
     def distances(self, db, ct, seed, qids, stream=None):
         B = ct.shape[0]
-        if self.batched_min and B >= self.batched_min:
+        if id(db) in self.batched_dbs and B >= self.batched_min:
             return S.sanns_distances_batched(self.ctx, db, ct, seed, qids, stream=stream)
         return S.sanns_distances(self.ctx, db, ct, seed, qids, stream=stream)
 

@@ -14,14 +14,15 @@ from paper_1904_02033_b300 import sanns as S
 pytestmark = pytest.mark.gpu
 
 
-def _setup(cfg, n, d, s_max, seed=5, batched_min=16):
+def _setup(cfg, n, d, s_max, seed=5, batched_min=16, batched_min_blocks=128):
     coords = inputs.mixture_coords(n, d, 16, 20.0, seed)
     # the layout is the server's preprocessing, built here on CPU tensors
     groups = cluster.balanced_clustering(torch.from_numpy(coords), 300, 0.3, iters=8, seed=1)
     kept, stash = cluster.split_stash(groups, s_max)
     lay = cluster.make_layout(kept, stash, d, seed=7)
     ctx = S.sanns_ctx_create(*cfg)
-    srv = cluster.ClusteringServer(ctx, torch.from_numpy(coords).cuda(), lay, batched_min=batched_min)
+    srv = cluster.ClusteringServer(ctx, torch.from_numpy(coords).cuda(), lay, batched_min=batched_min,
+                                   batched_min_blocks=batched_min_blocks)
     return coords, lay, ctx, srv
 
 
@@ -37,7 +38,7 @@ def _oracle_ids(coords, lay, q, prm, t):
                                                    ((8192, 3, 60, 0, 32), 3000, 1)])   # tensor-core path
 def test_clustering_query_matches_oracle(cfg, s_max, batched_min):
     n, d, B = 20000, 32, 6
-    coords, lay, ctx, srv = _setup(cfg, n, d, s_max, batched_min=batched_min)
+    coords, lay, ctx, srv = _setup(cfg, n, d, s_max, batched_min=batched_min, batched_min_blocks=1)
     T = len(lay.group_offsets) - 1
     sizes = np.diff(lay.group_offsets)
     t = ctx.query()["t"]
