@@ -571,7 +571,7 @@ def run_cluster_section() -> dict:
     S.sanns_device_status(ctx)
     return {
         "workload": "clustering: n=1,000,000 d=128 uint8 mixture of 1024 Zipf(1.1)-weighted "
-                    "components (sigma 20); seeded Lloyd k-means to 1024 clusters; 256 queries x "
+                    f"components (sigma 20); seeded Lloyd k-means to 1024 clusters; {B} queries x "
                     "32 probes; one persistent launch per batch; BFV N=8192, three 60-bit primes",
         "qp_per_s": total_pts / (ms * 1e-3),
         "ms_per_batch": ms, "queries": B, "gathered_points": total_pts,
@@ -844,11 +844,15 @@ def main():
     ap.add_argument("--n", type=int, default=None,
                     help="smaller database (profiling captures); the line then names it")
     ap.add_argument("--queries", type=int, default=None, help="number of distinct queries")
+    ap.add_argument("--cluster-B", type=int, default=None,
+                    help="queries per batch in the clustering section (profiling captures)")
     args = ap.parse_args()
     if args.n is not None:
         WORKLOAD["n"] = args.n
     if args.queries is not None:
         WORKLOAD["n_queries"] = args.queries
+    if args.cluster_B is not None:
+        CLUSTER["B"] = args.cluster_B
     if args.warmup < 3:
         args.warmup = 3
     if args.only:
