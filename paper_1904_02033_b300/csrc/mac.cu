@@ -18,11 +18,6 @@
 //
 // Launch variants (slots per lane, dimensions per load batch, threads, CTAs
 // per SM) trade registers for loads in flight; sanns_autotune_mac times them.
-// The async variants keep no loads in registers: each warp streams its
-// blocks' database rows through a private ring of shared-memory chunks with
-// 16-byte asynchronous copies (cp.async), several chunks in flight while it
-// multiplies the current one, so the loads in flight no longer cost
-// registers.
 #include "internal.h"
 
 namespace sanns {
@@ -181,135 +176,17 @@ __global__ void __launch_bounds__(THREADS, MINB) mac_kernel(PrimeSet P, MacArgs 
   }
 }
 
-__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
-  const uint32_t sa = (uint32_t)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-template <int NPEND>
-__device__ __forceinline__ void cp_async_wait() {
-  asm volatile("cp.async.wait_group %0;\n" ::"n"(NPEND) : "memory");
-}
-
-// One slot per lane (tile of 32 slots).  Warp w takes blocks k_first + w,
-// k_first + w + WARPS, ..; their rows, CH dimensions at a time (CH x 256 B),
-// flow through the warp's ring of ST chunks: chunk e + ST - 1 is copied while
-// chunk e is multiplied.  Shared memory: the ct tile [d][32] uint4, then the
-// rings [WARPS][ST][CH][32] u64.
-template <int THREADS, int CH, int ST, int MINB>
-__global__ void __launch_bounds__(THREADS, MINB) mac_async_kernel(PrimeSet P, MacArgs A) {
-  extern __shared__ uint4 cts[];
-  constexpr int WARPS = THREADS / 32;
-  constexpr uint32_t TILE = 32;
-  static_assert(CH == 8 || CH == 16, "the 16-dimension fold needs CH | 16");
-  const uint32_t N = P.N, L = P.L, d = A.d;
-  const uint32_t tiles = N / TILE;
-  const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  uint64_t* ring = reinterpret_cast<uint64_t*>(cts + (size_t)d * 32) + (size_t)warp * ST * CH * 32;
-  const uint32_t nch = (d + CH - 1) / CH;
-  const uint64_t w_begin = blockIdx.x * A.total / gridDim.x;
-  const uint64_t w_end = (blockIdx.x + 1) * A.total / gridDim.x;
-
-  uint64_t w = w_begin;
-  while (w < w_end) {
-    const uint64_t u = w / A.K;
-    const uint64_t k_first = w - u * A.K;
-    const uint64_t run_end = min(w_end, (u + 1) * A.K);
-    const uint32_t nk = (uint32_t)(run_end - w);
-    const uint32_t st = (uint32_t)(u % tiles);
-    const uint32_t j = (uint32_t)((u / tiles) % L);
-    const uint64_t b = u / ((uint64_t)tiles * L);
-    const uint64_t q = P.q[j];
-
-    __syncthreads();  // previous tile fully consumed
-    for (uint32_t e = threadIdx.x; e < d * 2 * 32; e += THREADS) {
-      const uint32_t l = e & 31, ci = e >> 5, c = ci & 1, i = ci >> 1;
-      const uint64_t* src = A.ct + ((((b * d + i) * 2 + c) * L + j) * N) + st * TILE + l;
-      const uint64_t m = mul_shoup(*src, P.r64[j], P.r64_shoup[j], q);
-      uint32_t* dst = reinterpret_cast<uint32_t*>(&cts[i * 32 + l]) + 2 * c;
-      dst[0] = (uint32_t)m & kMask30;
-      dst[1] = (uint32_t)(m >> 30);
-    }
-    __syncthreads();
-
-    const uint32_t nblk = nk > warp ? (nk - warp + WARPS - 1) / WARPS : 0;
-    const uint32_t E = nblk * nch;  // chunks this warp consumes in this run
-    const uint64_t* pbase = A.pt + (uint64_t)j * d * N + st * TILE + (lane & 15) * 2;
-    auto issue = [&](uint32_t e) {
-      const uint32_t r = e / nch, c = e - r * nch;
-      const uint64_t k = k_first + warp + (uint64_t)WARPS * r;
-      const uint64_t* src = pbase + k * L * (uint64_t)d * N;
-      uint64_t* dst = ring + (e % ST) * CH * 32 + (lane & 15) * 2;
-#pragma unroll
-      for (int m = 0; m < CH / 2; ++m) {
-        const uint32_t il = 2 * m + (lane >> 4);  // two 256-byte rows per warp instruction
-        const uint32_t i = c * CH + il;
-        if (i < d) cp_async16(dst + il * 32, src + (uint64_t)i * N);
-      }
-    };
-#pragma unroll
-    for (int e = 0; e < ST - 1; ++e) {
-      if ((uint32_t)e < E) issue(e);
-      cp_async_commit();
-    }
-    u128 R0 = 0, R1 = 0;
-    uint64_t aL0 = 0, aM10 = 0, aM20 = 0, aH0 = 0, aL1 = 0, aM11 = 0, aM21 = 0, aH1 = 0;
-    for (uint32_t e = 0; e < E; ++e) {
-      if (e + ST - 1 < E) issue(e + ST - 1);
-      cp_async_commit();
-      cp_async_wait<ST - 1>();  // chunk e has landed (this lane's copies) ..
-      __syncwarp();             // .. and every lane's
-      const uint32_t r = e / nch, c = e - r * nch;
-      const uint64_t* buf = ring + (e % ST) * CH * 32;
-#pragma unroll
-      for (int il = 0; il < CH; ++il) {
-        const uint32_t i = c * CH + il;
-        if (i < d) {
-          const uint64_t y = buf[il * 32 + lane];
-          const uint32_t yl = (uint32_t)y & kMask30, yh = (uint32_t)(y >> 30);
-          const uint4 x = cts[i * 32 + lane];
-          mac4(aL0, aM10, aM20, aH0, x.x, x.y, yl, yh);  // c0
-          mac4(aL1, aM11, aM21, aH1, x.z, x.w, yl, yh);  // c1
-        }
-      }
-      const uint32_t iend = c * CH + CH;
-      if ((iend & 15) == 0 || iend >= d) {  // at most 16 products per partial
-        const u128 m0 = (u128)aM10 + aM20, m1 = (u128)aM11 + aM21;
-        R0 += (u128)aL0 + (m0 << 30) + ((u128)aH0 << 60);
-        R1 += (u128)aL1 + (m1 << 30) + ((u128)aH1 << 60);
-        aL0 = aM10 = aM20 = aH0 = aL1 = aM11 = aM21 = aH1 = 0;
-      }
-      if (c == nch - 1) {
-        const uint64_t k = k_first + warp + (uint64_t)WARPS * r;
-        const uint64_t qn = P.q_neg_inv[j];
-        A.out[(((b * A.K + k) * 2 + 0) * L + j) * N + st * TILE + lane] =
-            reduce_below_16q(redc128(R0, q, qn), q);
-        A.out[(((b * A.K + k) * 2 + 1) * L + j) * N + st * TILE + lane] =
-            reduce_below_16q(redc128(R1, q, qn), q);
-        R0 = R1 = 0;
-      }
-      __syncwarp();  // every lane done with chunk e before its slot is refilled
-    }
-    cp_async_wait<0>();
-    w = run_end;
-  }
-}
-
 struct MacVariant {
   void (*fn)(PrimeSet, MacArgs);
   int spl, threads, ctas_per_sm;
-  uint32_t ring_bytes;  // async variants: the warps' shared-memory rings per CTA
   const char* name;
 };
 
 const MacVariant kVariants[] = {
-    {mac_kernel<2, 8, 512, 1>, 2, 512, 1, 0, "spl2_unr8_512x1"},
-    {mac_kernel<1, 16, 256, 3>, 1, 256, 3, 0, "spl1_unr16_256x3"},
-    {mac_kernel<1, 8, 256, 3>, 1, 256, 3, 0, "spl1_unr8_256x3"},
-    {mac_kernel<1, 16, 384, 2>, 1, 384, 2, 0, "spl1_unr16_384x2"},
-    {mac_async_kernel<512, 8, 3, 1>, 1, 512, 1, 16 * 3 * 8 * 256, "async_512x1_ch8_st3"},
-    {mac_async_kernel<256, 16, 3, 1>, 1, 256, 1, 8 * 3 * 16 * 256, "async_256x1_ch16_st3"},
-    {mac_async_kernel<256, 8, 2, 2>, 1, 256, 2, 8 * 2 * 8 * 256, "async_256x2_ch8_st2"},
+    {mac_kernel<2, 8, 512, 1>, 2, 512, 1, "spl2_unr8_512x1"},
+    {mac_kernel<1, 16, 256, 3>, 1, 256, 3, "spl1_unr16_256x3"},
+    {mac_kernel<1, 8, 256, 3>, 1, 256, 3, "spl1_unr8_256x3"},
+    {mac_kernel<1, 16, 384, 2>, 1, 384, 2, "spl1_unr16_384x2"},
 };
 constexpr int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
 
@@ -332,7 +209,7 @@ cudaError_t launch_mac(const PrimeSet& P, const uint64_t* ct, const uint64_t* pt
   A.d = d;
   A.total = (uint64_t)B * P.L * (P.N / tile) * K;
   if (A.total == 0) return cudaSuccess;
-  const size_t smem = sizeof(uint4) * 32 * d * V.spl + V.ring_bytes;
+  const size_t smem = sizeof(uint4) * 32 * d * V.spl;
   // shared-memory opt-in once per variant (the attribute is per function)
   static bool configured[kNumVariants] = {};
   static size_t configured_smem[kNumVariants] = {};
