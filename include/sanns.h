@@ -272,6 +272,29 @@ int sanns_autotune_batched(sanns_ctx *ctx, const sanns_db *db, const uint64_t *c
                            uint64_t *ct_out_dev, int reps, float *ms_out, void *stream);
 
 /*
+ * Plaintext encoding of the database (Sec. 5.3 packs N points per
+ * plaintext; Sec. 7.1 picks t; SEAL's batching puts values in the CRT slots
+ * mod t when t = 1 mod 2N).
+ *   0 (default)  coefficient encoding: point x of a block is coefficient x.
+ *   1            slot encoding: point x of a block is CRT slot x mod t.  The
+ *                plaintext of a coordinate row is the inverse negacyclic
+ *                transform mod t (psi_t = the smallest primitive 2N-th root
+ *                of unity mod t) of the row, with coefficients in [0, t); the
+ *                norms are encoded the same way; the server's mask is a
+ *                polynomial R whose coefficients are drawn as in coefficient
+ *                encoding (padding included), and its share of slot x is
+ *                t - NTT_t(R)[x]; the client's share is NTT_t(m)[x] +
+ *                ||q||^2.  Shares are identical in meaning to coefficient
+ *                encoding: they add up to ||q - p||^2 mod t.
+ * A database keeps the encoding the context had when it was encoded; the
+ * distance calls reject a database whose encoding differs from the context's,
+ * and slot encoding rejects NTT-form responses and the gather path.
+ * sanns_decrypt_shares (and its no-allocation variant) decode in the
+ * context's encoding.  SANNS_EINVAL for slots when t != 1 mod 2N.
+ */
+int sanns_set_encoding(sanns_ctx *ctx, int slots);
+
+/*
  * Response form.  0 (default): coefficient form, as the paper's protocol
  * returns (the server transforms every response polynomial back).  1: NTT
  * form, the NTT (per prime, the same negacyclic transform as the queries') of

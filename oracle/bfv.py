@@ -15,7 +15,7 @@ import ctypes as C
 import numpy as np
 
 from . import build as _build
-from .params import Params, make_params
+from .params import Params, make_params, min_primitive_root_2n
 
 _lib = None
 
@@ -81,6 +81,15 @@ class Oracle:
                                     v.ctypes.data_as(C.POINTER(C.c_uint64)))
         self._c = _CParams(N, L, d, 0, P.t, _p(self.q).value, _p(self.fwd).value,
                            _p(self.inv).value, _p(self.delta).value)
+        # slot encoding: the negacyclic transform mod t (t = 1 mod 2N)
+        self.slots_ok = (P.t - 1) % (2 * N) == 0
+        if self.slots_ok:
+            self.psi_t = min_primitive_root_2n(P.t, N)
+            self.fwd_t = np.zeros(N, dtype=np.uint64)
+            self.inv_t = np.zeros(N, dtype=np.uint64)
+            lib().oracle_ntt_tables(N, P.t, self.psi_t,
+                                    self.fwd_t.ctypes.data_as(C.POINTER(C.c_uint64)),
+                                    self.inv_t.ctypes.data_as(C.POINTER(C.c_uint64)))
 
     # ---------------- transforms ----------------
     def ntt(self, a: np.ndarray, j: int) -> np.ndarray:
@@ -94,6 +103,28 @@ class Oracle:
         lib().oracle_intt(a.ctypes.data_as(C.POINTER(C.c_uint64)), self.N, int(self.q[j]),
                           self.inv[j].ctypes.data_as(C.POINTER(C.c_uint64)))
         return a
+
+    def ntt_t(self, a: np.ndarray) -> np.ndarray:
+        """Slot values of a plaintext: the negacyclic NTT mod t."""
+        a = np.ascontiguousarray(a, dtype=np.uint64).copy()
+        lib().oracle_ntt(a.ctypes.data_as(C.POINTER(C.c_uint64)), self.N, self.t,
+                         self.fwd_t.ctypes.data_as(C.POINTER(C.c_uint64)))
+        return a
+
+    def intt_t(self, a: np.ndarray) -> np.ndarray:
+        """The plaintext (coefficients in [0, t)) whose slots are a."""
+        a = np.ascontiguousarray(a, dtype=np.uint64).copy()
+        lib().oracle_intt(a.ctypes.data_as(C.POINTER(C.c_uint64)), self.N, self.t,
+                          self.inv_t.ctypes.data_as(C.POINTER(C.c_uint64)))
+        return a
+
+    def schoolbook_mod(self, a: np.ndarray, b: np.ndarray, m: int) -> np.ndarray:
+        """Negacyclic product mod (x^N + 1, m) by the schoolbook loop."""
+        a = np.ascontiguousarray(a, dtype=np.uint64)
+        b = np.ascontiguousarray(b, dtype=np.uint64)
+        out = np.zeros(self.N, dtype=np.uint64)
+        lib().oracle_negacyclic_schoolbook(_p(a), _p(b), self.N, int(m), _p(out))
+        return out
 
     def schoolbook(self, a: np.ndarray, b: np.ndarray, j: int) -> np.ndarray:
         a = np.ascontiguousarray(a, dtype=np.uint64)
@@ -121,7 +152,12 @@ class Oracle:
         return (n + self.N - 1) // self.N
 
     def encode_db(self, coords: np.ndarray, perm: np.ndarray | None, k0: int = 0,
-                  k1: int | None = None):
+                  k1: int | None = None, slots: bool = False):
+        """Coefficient encoding (the C loops), or slot encoding: each
+        coordinate row (and the norm row) of a block becomes the plaintext
+        whose CRT slots mod t it is, then its NTT per prime."""
+        if slots:
+            return self._encode_db_slots(coords, perm, k0, k1)
         coords = np.ascontiguousarray(coords, dtype=np.uint8)
         n = coords.shape[0] if perm is None else len(perm)
         if perm is None:
@@ -134,6 +170,46 @@ class Oracle:
         lib().oracle_encode_db(C.byref(self._c), _p(coords), _p(perm), n, k0, k1,
                                _p(pt), _p(norms))
         return pt, norms
+
+    def _encode_db_slots(self, coords, perm, k0, k1):
+        assert self.slots_ok
+        coords = np.ascontiguousarray(coords, dtype=np.uint8)
+        n = coords.shape[0] if perm is None else len(perm)
+        perm = np.arange(n) if perm is None else np.asarray(perm, dtype=np.int64)
+        k1 = self.blocks(n) if k1 is None else k1
+        N, d = self.N, self.d
+        pt = np.zeros((k1 - k0, self.L, d, N), dtype=np.uint64)
+        norms = np.zeros((k1 - k0) * N, dtype=np.uint32)
+        for kk, k in enumerate(range(k0, k1)):
+            rows = np.zeros((N, d), dtype=np.int64)
+            cnt = max(0, min(n - k * N, N))
+            rows[:cnt] = coords[perm[k * N:k * N + cnt]]
+            for i in range(d):
+                poly = self.intt_t(rows[:, i].astype(np.uint64))
+                for j in range(self.L):
+                    pt[kk, j, i] = self.ntt(poly, j)
+            nrm = np.sum(rows * rows, axis=1).astype(np.uint64)
+            norms[kk * N:(kk + 1) * N] = self.intt_t(nrm).astype(np.uint32)
+        return pt, norms
+
+    def mask_r(self, mask_seed: int, qid: int, gpos: int) -> int:
+        """The server's mask value at global position gpos: the 128-bit draw
+        (stream mask_seed, purpose 4, object qid) reduced mod t."""
+        lo, hi = self.draw128(mask_seed, 4, qid, gpos)
+        return ((hi << 64) | lo) % self.t
+
+    def slot_shares(self, n: int, k0: int, k1: int, mask_seed: int, qid: int) -> np.ndarray:
+        """Slot encoding, the server's shares of blocks k0 .. k1: t - the
+        slots of the mask polynomial R (coefficients = the mask draws of
+        the block's positions, padding included)."""
+        N, t = self.N, self.t
+        out = []
+        for k in range(k0, k1):
+            R = np.array([self.mask_r(mask_seed, qid, k * N + x) for x in range(N)], dtype=np.uint64)
+            Rh = self.ntt_t(R).astype(np.int64)
+            cnt = max(0, min(n - k * N, N))
+            out.append(((t - Rh[:cnt]) % t).astype(np.uint32))
+        return np.concatenate(out) if out else np.zeros(0, dtype=np.uint32)
 
     def mac(self, ct: np.ndarray, pt: np.ndarray) -> np.ndarray:
         nk = pt.shape[0]
@@ -154,19 +230,22 @@ class Oracle:
 
     def distances(self, ct: np.ndarray, coords: np.ndarray, perm, mask_seed: int, qid: int,
                   k0: int = 0, k1: int | None = None, pk: np.ndarray | None = None,
-                  flood_bits: int = 0):
+                  flood_bits: int = 0, slots: bool = False):
         """Pi_ls step 3 for blocks [k0, k1): encode, MAC, INTT, mask; with a
         public key also the circuit-privacy terms (re-randomisation before the
-        INTT, flooding after it)."""
+        INTT, flooding after it).  With slot encoding the server's shares are
+        those of the mask polynomial's slots."""
         n = coords.shape[0] if perm is None else len(perm)
         k1 = self.blocks(n) if k1 is None else k1
-        pt, norms = self.encode_db(coords, perm, k0, k1)
+        pt, norms = self.encode_db(coords, perm, k0, k1, slots=slots)
         acc = self.mac(ct, pt)
         if pk is not None:
             self.rerandomize(acc, pk, mask_seed, qid, k0)
         out, share = self.intt_mask(acc, norms, n, k0, k1, mask_seed, qid)
         if pk is not None:
             self.flood(out, mask_seed, qid, k0, flood_bits)
+        if slots:
+            share = self.slot_shares(n, k0, k1, mask_seed, qid)
         return out, share
 
     # ---------------- response form ----------------
@@ -268,11 +347,16 @@ class Oracle:
                     return False
         return True
 
-    def decrypt_shares(self, ct_out: np.ndarray, s: np.ndarray, qv: np.ndarray, n: int):
+    def decrypt_shares(self, ct_out: np.ndarray, s: np.ndarray, qv: np.ndarray, n: int,
+                       slots: bool = False):
         """Pi_ls step 4 plus the client's local term: sigma_C = m + ||q||^2 mod t
-        for the first n positions."""
+        for the first n positions (with slot encoding, m's slots)."""
         v = self.decrypt_phase(ct_out, s)
-        m = self.scale_round(v)[:n]
+        m = self.scale_round(v)
+        if slots:
+            m = np.concatenate([self.ntt_t(m[k * self.N:(k + 1) * self.N].astype(np.uint64))
+                                for k in range(len(m) // self.N)]).astype(np.int64)
+        m = m[:n]
         qn = int(np.sum(np.asarray(qv, dtype=np.int64) ** 2))
         return ((m + qn) % self.t).astype(np.uint32)
 

@@ -125,7 +125,56 @@ int sanns_ctx_create(const sanns_params* p, sanns_ctx** out) {
   e = cudaMalloc(&c->d_err, sizeof(int));
   if (e == cudaSuccess) e = cudaMemset(c->d_err, 0, sizeof(int));
   if (e != cudaSuccess) { cudaFree(c->d_tables); delete c; return cuda_fail(e, "cudaMalloc(err)"); }
+  // slot encoding needs a primitive 2N-th root of unity mod t (t = 1 mod 2N)
+  memset(&c->PT, 0, sizeof(c->PT));
+  if (t % (2ull * N) == 1) {
+    PrimeSet& T = c->PT;
+    T.N = N;
+    T.logN = logN;
+    T.L = 1;
+    T.t = t;
+    T.q[0] = t;
+    c->psi_t = smallest_psi(t, N);
+    std::vector<uint64_t> tf(N), tfs(N), ti(N), tis(N);
+    fill_twiddles(N, t, c->psi_t, tf.data(), tfs.data(), ti.data(), tis.data());
+    // N^-1 mod t by Fermat (t prime)
+    uint64_t ninv = 1, base = N % t, ex = t - 2;
+    while (ex) {
+      if (ex & 1) ninv = (uint64_t)((u128)ninv * base % t);
+      base = (uint64_t)((u128)base * base % t);
+      ex >>= 1;
+    }
+    T.n_inv[0] = ninv;
+    T.n_inv_shoup[0] = shoup_of(ninv, t);
+    std::vector<uint64_t> th(4 * (size_t)N);
+    for (uint32_t x = 0; x < N; ++x) {
+      th[2 * x] = tf[x];
+      th[2 * x + 1] = tfs[x];
+      th[2 * N + 2 * x] = ti[x];
+      th[2 * N + 2 * x + 1] = tis[x];
+    }
+    e = cudaMalloc(&c->d_tables_t, sizeof(uint64_t) * 4 * N);
+    if (e == cudaSuccess)
+      e = cudaMemcpy(c->d_tables_t, th.data(), sizeof(uint64_t) * 4 * N, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+      cudaFree(c->d_tables_t);
+      cudaFree(c->d_tables);
+      cudaFree(c->d_err);
+      delete c;
+      return cuda_fail(e, "cudaMalloc(slot tables)");
+    }
+    T.tw = reinterpret_cast<const ulonglong2*>(c->d_tables_t);
+    T.itw = reinterpret_cast<const ulonglong2*>(c->d_tables_t + 2 * N);
+  }
   *out = c;
+  return SANNS_OK;
+}
+
+int sanns_set_encoding(sanns_ctx* ctx, int slots) {
+  if (!ctx) return fail(SANNS_EINVAL, "ctx is NULL");
+  if (slots != 0 && slots != 1) return fail(SANNS_EINVAL, "encoding must be 0 (coefficients) or 1 (slots)");
+  if (slots && !ctx->d_tables_t) return fail(SANNS_EINVAL, "slot encoding needs t = 1 mod 2N");
+  ctx->slots = slots == 1;
   return SANNS_OK;
 }
 
@@ -134,6 +183,7 @@ void sanns_ctx_free(sanns_ctx* ctx) {
   cudaFree(ctx->d_pk);
   cudaFree(ctx->d_pk_shoup);
   cudaFree(ctx->d_tables);
+  cudaFree(ctx->d_tables_t);
   cudaFree(ctx->d_err);
   delete ctx;
 }
@@ -220,13 +270,15 @@ int sanns_encode_db(sanns_ctx* ctx, const uint8_t* coords, uint64_t n_points, co
   db->ctx = ctx;
   db->n = n;
   db->K = K;
+  db->slots = ctx->slots;
   int* d_bad = nullptr;
   cudaError_t e = cudaMalloc(&db->d_pt, sizeof(uint64_t) * K * L * d * N);
   if (e == cudaSuccess) e = cudaMalloc(&db->d_norms, sizeof(uint32_t) * K * N);
   if (e == cudaSuccess) e = cudaMalloc(&d_bad, sizeof(int));
   if (e == cudaSuccess) e = cudaMemsetAsync(d_bad, 0, sizeof(int), st);
   if (e == cudaSuccess)
-    e = launch_encode(ctx->P, coords, n_points, perm, n, d, K, db->d_pt, db->d_norms, d_bad, st);
+    e = launch_encode(ctx->P, db->slots ? &ctx->PT : nullptr, coords, n_points, perm, n, d, K, db->d_pt,
+                      db->d_norms, d_bad, st);
   int bad = 0;
   if (e == cudaSuccess) e = cudaMemcpyAsync(&bad, d_bad, sizeof(int), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
@@ -302,6 +354,8 @@ int check_distance_args(sanns_ctx* ctx, const sanns_db* db, uint32_t B) {
   if (!ctx || !db) return fail(SANNS_EINVAL, "ctx or db is NULL");
   if (db->ctx != ctx) return fail(SANNS_EINVAL, "db belongs to another context");
   if ((uint64_t)B * db->K * 2 * ctx->P.L > 0x7fffffffull) return fail(SANNS_EINVAL, "batch too large");
+  if (db->slots != ctx->slots)
+    return fail(SANNS_EINVAL, "the database was encoded in the other encoding than the context's");
   return check_device(ctx);
 }
 }  // namespace
@@ -324,6 +378,8 @@ int sanns_distances_finish(sanns_ctx* ctx, const sanns_db* db, uint32_t B, uint6
   if (rc) return rc;
   if (B == 0) return SANNS_OK;
   if (!qids || !ct_out || !srv_share) return fail(SANNS_EINVAL, "NULL buffer");
+  if (ctx->slots && ctx->ntt_responses)
+    return fail(SANNS_EINVAL, "slot encoding returns coefficient-form responses only");
   cudaStream_t st = as_stream(stream);
   if (ctx->d_pk)
     SANNS_CUDA(launch_rerandomize(ctx->P, ct_out, B, db->K, db->pos0, mask_seed, qids, ctx->d_pk,
@@ -338,6 +394,8 @@ int sanns_distances_finish(sanns_ctx* ctx, const sanns_db* db, uint32_t B, uint6
   if (ctx->d_pk)
     SANNS_CUDA(launch_flood(ctx->P, ct_out, B, db->K, db->pos0, mask_seed, qids, ctx->flood_bits,
                             ctx->privacy, st));
+  if (ctx->slots)
+    SANNS_CUDA(launch_slot_share(ctx->P, ctx->PT, B, db->K, db->n, db->pos0, mask_seed, qids, srv_share, st));
   return SANNS_OK;
 }
 
@@ -607,6 +665,7 @@ int sanns_distances_gather(sanns_ctx* ctx, const sanns_clusters* cl, const uint6
   if (ctx->P.N > 8192) return fail(SANNS_EINVAL, "the gather path supports N <= 8192");
   if (ctx->d_pk) return fail(SANNS_EINVAL, "circuit privacy is not available on the gather path");
   if (ctx->ntt_responses) return fail(SANNS_EINVAL, "the gather path returns coefficient-form responses only");
+  if (ctx->slots) return fail(SANNS_EINVAL, "the gather path uses coefficient encoding only");
   if (B == 0) return SANNS_OK;
   if (!ct_in || !qids || !ct_out || !srv_share || !probes) return fail(SANNS_EINVAL, "NULL buffer");
   std::vector<uint64_t> nb(B), kb(B);
@@ -762,7 +821,8 @@ int sanns_decrypt_shares(sanns_ctx* ctx, const sanns_sk* sk, const uint64_t* ct_
   uint64_t* scratch = nullptr;
   SANNS_CUDA(cudaMallocAsync(&scratch, sizeof(uint64_t) * B * K * ctx->P.L * ctx->P.N, st));
   cudaError_t e = launch_decrypt(ctx->P, ct_out, sk->d_s, sk->d_s_hat, sk->d_s_hat_shoup, B, K, n, qv,
-                                 ctx->params.d, scratch, cli_share, ctx->ntt_responses, st);
+                                 ctx->params.d, scratch, cli_share, ctx->ntt_responses,
+                                 ctx->slots ? &ctx->PT : nullptr, st);
   cudaError_t e2 = cudaFreeAsync(scratch, st);
   if (e != cudaSuccess) return cuda_fail(e, "decrypt kernels");
   if (e2 != cudaSuccess) return cuda_fail(e2, "cudaFreeAsync");

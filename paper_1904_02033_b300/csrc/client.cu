@@ -140,9 +140,12 @@ __global__ void __launch_bounds__(512) decrypt_phase_kernel(PrimeSet P, const ui
 // fraction lies within t (|e| + t) / Q of an integer -- far from 1/2 whenever
 // decryption is correct at all -- and the truncation cannot change the
 // rounding.
-__global__ void scale_round_kernel(PrimeSet P, const uint64_t* __restrict__ v, uint64_t K,
+// With slot encoding (slots != 0) every coefficient of every block is
+// decoded (n is then K N) and m is written over v[b][k][0][x], which only this
+// thread reads; slot_decode_kernel takes it from there.
+__global__ void scale_round_kernel(PrimeSet P, uint64_t* __restrict__ v, uint64_t K,
                                    uint64_t n, uint32_t B, const uint8_t* __restrict__ qv,
-                                   uint32_t d, uint32_t* __restrict__ cli_share) {
+                                   uint32_t d, uint32_t* __restrict__ cli_share, int slots) {
   const uint64_t gid = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
   if (gid >= (uint64_t)B * n) return;
   const uint64_t b = gid / n, pos = gid % n;
@@ -164,10 +167,42 @@ __global__ void scale_round_kernel(PrimeSet P, const uint64_t* __restrict__ v, u
   const uint64_t whole = (uint64_t)(fsum >> 64);
   const uint64_t frac = (uint64_t)fsum;
   uint64_t m = (isum + whole + (frac >> 63)) % t;
+  if (slots) {
+    v[((b * K + k) * L + 0) * N + x] = m;
+    return;
+  }
   uint32_t qn = 0;
   const uint8_t* qq = qv + b * d;
   for (uint32_t i = 0; i < d; ++i) qn += (uint32_t)qq[i] * qq[i];
   cli_share[gid] = (uint32_t)((m + qn) % t);
+}
+
+// Slot encoding, the client's shares: one block per (b, k), the slots of the
+// decrypted plaintext m (NTT_t of its coefficients) plus ||q||^2.
+__global__ void __launch_bounds__(512) slot_decode_kernel(PrimeSet P, PrimeSet PT,
+                                                          const uint64_t* __restrict__ v, uint64_t K,
+                                                          uint64_t n, const uint8_t* __restrict__ qv,
+                                                          uint32_t d, uint32_t* __restrict__ cli_share) {
+  extern __shared__ uint64_t sa[];
+  __shared__ uint32_t qn;
+  const uint32_t N = P.N, L = P.L;
+  const uint64_t bk = blockIdx.x, b = bk / K, k = bk % K;
+  const uint64_t* m = v + (bk * L + 0) * N;
+  for (uint32_t x = threadIdx.x; x < N; x += blockDim.x) sa[SP(x)] = m[x];
+  if (threadIdx.x == 0) {
+    uint32_t acc = 0;
+    for (uint32_t i = 0; i < d; ++i) acc += (uint32_t)qv[b * d + i] * qv[b * d + i];
+    qn = acc;
+  }
+  __syncthreads();
+  ntt_forward_smem(sa, PT, 0);
+  __syncthreads();
+  const uint64_t t = P.t;
+  for (uint32_t x = threadIdx.x; x < N; x += blockDim.x) {
+    const uint64_t pos = k * N + x;
+    if (pos >= n) break;
+    cli_share[b * n + pos] = (uint32_t)((sa[SP(x)] + qn) % t);
+  }
 }
 
 }  // namespace
@@ -199,7 +234,8 @@ cudaError_t launch_encrypt(const PrimeSet& P, const uint64_t* s_hat, const uint6
 cudaError_t launch_decrypt(const PrimeSet& P, const uint64_t* ct_out, const int8_t* s,
                            const uint64_t* s_hat, const uint64_t* s_hat_shoup, uint32_t B,
                            uint64_t K, uint64_t n, const uint8_t* qv, uint32_t d,
-                           uint64_t* scratch, uint32_t* cli_share, bool ntt_form, cudaStream_t st) {
+                           uint64_t* scratch, uint32_t* cli_share, bool ntt_form, const PrimeSet* PT,
+                           cudaStream_t st) {
   (void)s;
   if (B == 0 || n == 0) return cudaSuccess;
   const size_t smem = sizeof(uint64_t) * ntt_smem_words(P.N);
@@ -210,9 +246,21 @@ cudaError_t launch_decrypt(const PrimeSet& P, const uint64_t* ct_out, const int8
       P, ct_out, s_hat, s_hat_shoup, K, scratch, ntt_form ? 1 : 0);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  const uint64_t total = (uint64_t)B * n;
-  scale_round_kernel<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(P, scratch, K, n, B, qv, d,
-                                                                      cli_share);
+  if (!PT) {
+    const uint64_t total = (uint64_t)B * n;
+    scale_round_kernel<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(P, scratch, K, n, B, qv, d,
+                                                                        cli_share, 0);
+    return cudaGetLastError();
+  }
+  const uint64_t total = (uint64_t)B * K * P.N;
+  scale_round_kernel<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(P, scratch, K, K * P.N, B, qv, d,
+                                                                      cli_share, 1);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(slot_decode_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  slot_decode_kernel<<<(unsigned)((uint64_t)B * K), blk_threads(P.N), smem, st>>>(P, *PT, scratch, K, n, qv, d,
+                                                                                   cli_share);
   return cudaGetLastError();
 }
 

@@ -25,6 +25,13 @@ struct sanns_ctx {
   uint32_t flood_bits;
   sanns::PrivacyConsts privacy;
   bool ntt_responses;       // responses in NTT form (server finish and client decryption)
+  // slot encoding (t = 1 mod 2N): the negacyclic transform mod t as a
+  // one-prime set (its tables in d_tables_t), and whether new databases and
+  // decryptions use it
+  sanns::PrimeSet PT;
+  uint64_t psi_t;
+  uint64_t* d_tables_t;
+  bool slots;
 };
 
 struct sanns_sk {
@@ -38,6 +45,7 @@ struct sanns_db {
   const sanns_ctx* ctx;
   uint64_t n, K;
   uint64_t pos0;            // global position of local position 0 (shards), multiple of N
+  bool slots;               // encoded with slot encoding (points in the CRT slots mod t)
   uint64_t* d_pt;           // [K][L][d][N]
   uint32_t* d_norms;        // [K N]
   uint16_t* d_plimb;        // [L][N][K][8 dpad] fp16 digits (batched path), or NULL
@@ -68,6 +76,7 @@ int cuda_fail(cudaError_t e, const char* what);
 
 // parameter derivation (params.cpp)
 int derive_params(const sanns_params& in, uint64_t q[], uint64_t psi[], uint64_t* t);
+uint64_t smallest_psi(uint64_t q, uint64_t N);
 void fill_prime_constants(PrimeSet& P, const uint64_t q[], uint64_t t, uint32_t L);
 void fill_twiddles(uint32_t N, uint64_t q, uint64_t psi, uint64_t* tw, uint64_t* tws, uint64_t* itw,
                    uint64_t* itws);
@@ -101,9 +110,12 @@ cudaError_t launch_keygen(const PrimeSet& P, uint64_t seed, int8_t* s, uint64_t*
 cudaError_t launch_encrypt(const PrimeSet& P, const uint64_t* s_hat, const uint64_t* s_hat_shoup,
                            const uint8_t* qv, uint32_t B, uint32_t d, uint64_t seed,
                            const uint64_t* qids, uint64_t* ct, cudaStream_t st);
-cudaError_t launch_encode(const PrimeSet& P, const uint8_t* coords, uint64_t n_points,
+cudaError_t launch_encode(const PrimeSet& P, const PrimeSet* PT, const uint8_t* coords, uint64_t n_points,
                           const uint32_t* perm, uint64_t n, uint32_t d, uint64_t K, uint64_t* pt,
                           uint32_t* norms, int* bad, cudaStream_t st);
+cudaError_t launch_slot_share(const PrimeSet& P, const PrimeSet& PT, uint32_t B, uint64_t K, uint64_t n,
+                              uint64_t pos0, uint64_t mask_seed, const uint64_t* qids,
+                              uint32_t* srv_share, cudaStream_t st);
 int mac_num_variants();
 const char* mac_variant_name(int v);
 cudaError_t launch_mac(const PrimeSet& P, const uint64_t* ct, const uint64_t* pt, uint32_t B,
@@ -132,6 +144,7 @@ cudaError_t launch_batched_mac(const PrimeSet& P, const void* map, const uint16_
 cudaError_t launch_decrypt(const PrimeSet& P, const uint64_t* ct_out, const int8_t* s,
                            const uint64_t* s_hat, const uint64_t* s_hat_shoup, uint32_t B,
                            uint64_t K, uint64_t n, const uint8_t* qv, uint32_t d,
-                           uint64_t* scratch, uint32_t* cli_share, bool ntt_form, cudaStream_t st);
+                           uint64_t* scratch, uint32_t* cli_share, bool ntt_form, const PrimeSet* PT,
+                           cudaStream_t st);
 
 }  // namespace sanns

@@ -65,7 +65,7 @@ extern "C" int sanns_decrypt_shares_noalloc(sanns_ctx* ctx, const sanns_sk* sk, 
   // of the same call, so nothing needs clearing between calls
   e = launch_decrypt(ctx->P, ct_out, sk->d_s, sk->d_s_hat, sk->d_s_hat_shoup, B, K, n, qv,
                      ctx->params.d, scratch, cli_share, ctx->ntt_responses,
-                     reinterpret_cast<cudaStream_t>(stream));
+                     ctx->slots ? &ctx->PT : nullptr, reinterpret_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) return cuda_fail(e, "decrypt kernels");
   return SANNS_OK;
 }

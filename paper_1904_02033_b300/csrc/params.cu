@@ -60,6 +60,22 @@ uint32_t bitrev(uint32_t x, uint32_t bits) {
 
 uint64_t shoup_of(uint64_t w, uint64_t q) { return (uint64_t)(((u128)w << 64) / q); }
 
+uint64_t smallest_psi(uint64_t q, uint64_t N) {
+  const uint64_t m = 2 * N;
+  // psi0 of order exactly 2N, then the smallest of its odd powers
+  uint64_t psi0 = 0;
+  for (uint64_t g = 2;; ++g) {
+    psi0 = powmod(g, (q - 1) / m, q);
+    if (powmod(psi0, N, q) == q - 1) break;
+  }
+  uint64_t sq = mulmod(psi0, psi0, q), cur = psi0, best = psi0;
+  for (uint64_t k = 1; k < N; ++k) {
+    cur = mulmod(cur, sq, q);
+    if (cur < best) best = cur;
+  }
+  return best;
+}
+
 int derive_params(const sanns_params& in, uint64_t q[], uint64_t psi[], uint64_t* t_out) {
   const uint64_t N = in.N, m = 2 * N;
   if (in.prime_bits < 20 || in.prime_bits > 60) return fail(SANNS_EINVAL, "prime_bits must be in [20, 60]");
@@ -73,20 +89,7 @@ int derive_params(const sanns_params& in, uint64_t q[], uint64_t psi[], uint64_t
     if (is_prime_u64(x)) q[found++] = x;
     x -= m;
   }
-  for (uint32_t j = 0; j < in.L; ++j) {
-    // psi0 of order exactly 2N, then the smallest of its odd powers
-    uint64_t psi0 = 0;
-    for (uint64_t g = 2;; ++g) {
-      psi0 = powmod(g, (q[j] - 1) / m, q[j]);
-      if (powmod(psi0, N, q[j]) == q[j] - 1) break;
-    }
-    uint64_t sq = mulmod(psi0, psi0, q[j]), cur = psi0, best = psi0;
-    for (uint64_t k = 1; k < N; ++k) {
-      cur = mulmod(cur, sq, q[j]);
-      if (cur < best) best = cur;
-    }
-    psi[j] = best;
-  }
+  for (uint32_t j = 0; j < in.L; ++j) psi[j] = smallest_psi(q[j], N);
   uint64_t t;
   if (in.t_rule == 0) {
     t = ((1ull << 24) / m) * m + 1;

@@ -27,8 +27,13 @@ __global__ void __launch_bounds__(512) ntt_kernel(PrimeSet P, uint64_t* data, in
 }
 
 // Encoding: block (k, i) builds coordinate i of positions kN .. kN+N-1 and
-// writes its NTT for every prime into pt[k][j][i][:].
-__global__ void __launch_bounds__(512) encode_kernel(PrimeSet P, const uint8_t* __restrict__ coords, uint64_t n_points,
+// writes its NTT for every prime into pt[k][j][i][:].  Coefficient encoding
+// puts point x's coordinate in coefficient x; slot encoding (slots != 0)
+// puts it in CRT slot x mod t: the plaintext is the inverse negacyclic
+// transform mod t of the coordinates (coefficients in [0, t)), whose NTT is
+// then taken for every prime.
+__global__ void __launch_bounds__(512) encode_kernel(PrimeSet P, PrimeSet PT, int slots,
+                              const uint8_t* __restrict__ coords, uint64_t n_points,
                               const uint32_t* __restrict__ perm, uint64_t n, uint32_t d,
                               uint64_t* __restrict__ pt, int* bad) {
   extern __shared__ uint64_t sa[];
@@ -47,6 +52,10 @@ __global__ void __launch_bounds__(512) encode_kernel(PrimeSet P, const uint8_t* 
       sa[SP(x)] = v;
     }
     __syncthreads();
+    if (slots) {
+      ntt_inverse_smem(sa, PT, 0);
+      __syncthreads();
+    }
     ntt_forward_smem(sa, P, j);
     __syncthreads();
     uint64_t* dst = pt + ((k * P.L + j) * d + i) * N;
@@ -69,6 +78,54 @@ __global__ void norms_kernel(const uint8_t* __restrict__ coords, uint64_t n_poin
     }
   }
   norms[pos] = s;
+}
+
+// Slot encoding of the norms, in place: block k's ||p||^2 values (zero at
+// padding positions) become the coefficients of the plaintext whose slots
+// they are, so the epilogue adds Delta (that plaintext + the mask polynomial).
+__global__ void __launch_bounds__(512) norms_slot_kernel(PrimeSet PT, uint32_t* __restrict__ norms) {
+  extern __shared__ uint64_t sa[];
+  const uint32_t N = PT.N;
+  uint32_t* g = norms + blockIdx.x * (uint64_t)N;
+  for (uint32_t x = threadIdx.x; x < N; x += blockDim.x) sa[SP(x)] = g[x];
+  __syncthreads();
+  ntt_inverse_smem(sa, PT, 0);
+  __syncthreads();
+  for (uint32_t x = threadIdx.x; x < N; x += blockDim.x) g[x] = (uint32_t)sa[SP(x)];
+}
+
+// Slot encoding, the server's shares: the mask is a polynomial R (its
+// coefficients drawn as in coefficient encoding, padding positions included),
+// so the server's share of slot s is t - NTT_t(R)[s].  One block per (b, k);
+// runs after the epilogue, which reads the coefficient shares t - R.
+__global__ void __launch_bounds__(512) slot_share_kernel(PrimeSet P, PrimeSet PT, uint64_t K, uint64_t n,
+                                                         uint64_t pos0, uint64_t mask_seed,
+                                                         const uint64_t* __restrict__ qids,
+                                                         uint32_t* __restrict__ srv_share) {
+  extern __shared__ uint64_t sa[];
+  const uint32_t N = P.N;
+  const uint64_t bk = blockIdx.x, b = bk / K, k = bk % K;
+  const uint64_t qid = qids[b];
+  for (uint32_t u = threadIdx.x; u < N / 4; u += blockDim.x) {
+    const uint64_t g0 = pos0 + k * N + 4 * u;
+    uint32_t blk[16];
+    chacha20_block(mask_seed, kPurposeMask, qid, (uint32_t)(g0 / 4), blk);
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      uint64_t lo, hi;
+      draw_pair(blk, v, lo, hi);
+      sa[SP(4 * u + v)] = mod_t128(lo, hi, P);
+    }
+  }
+  __syncthreads();
+  ntt_forward_smem(sa, PT, 0);
+  __syncthreads();
+  for (uint32_t x = threadIdx.x; x < N; x += blockDim.x) {
+    const uint64_t pos = k * N + x;
+    if (pos >= n) break;
+    const uint64_t r = sa[SP(x)];
+    srv_share[b * n + pos] = (uint32_t)(r == 0 ? 0 : P.t - r);
+  }
 }
 
 // The server's mask, drawn once per position: r = uniform mod t from ChaCha20
@@ -409,7 +466,7 @@ cudaError_t launch_ntt(const PrimeSet& P, uint64_t* data, uint64_t count, bool i
   return cudaGetLastError();
 }
 
-cudaError_t launch_encode(const PrimeSet& P, const uint8_t* coords, uint64_t n_points,
+cudaError_t launch_encode(const PrimeSet& P, const PrimeSet* PT, const uint8_t* coords, uint64_t n_points,
                           const uint32_t* perm, uint64_t n, uint32_t d, uint64_t K, uint64_t* pt,
                           uint32_t* norms, int* bad, cudaStream_t st) {
   const size_t smem = sizeof(uint64_t) * ntt_smem_words(P.N);
@@ -417,12 +474,31 @@ cudaError_t launch_encode(const PrimeSet& P, const uint8_t* coords, uint64_t n_p
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   dim3 grid((unsigned)K, d);
-  encode_kernel<<<grid, ntt_threads(P.N), smem, st>>>(P, coords, n_points, perm, n, d, pt, bad);
+  encode_kernel<<<grid, ntt_threads(P.N), smem, st>>>(P, PT ? *PT : P, PT ? 1 : 0, coords, n_points, perm,
+                                                      n, d, pt, bad);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const uint64_t total = K * P.N;
   norms_kernel<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(coords, n_points, perm, n, d,
                                                                  total, norms);
+  e = cudaGetLastError();
+  if (e != cudaSuccess || !PT) return e;
+  e = cudaFuncSetAttribute(norms_slot_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  norms_slot_kernel<<<(unsigned)K, ntt_threads(P.N), smem, st>>>(*PT, norms);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_slot_share(const PrimeSet& P, const PrimeSet& PT, uint32_t B, uint64_t K, uint64_t n,
+                              uint64_t pos0, uint64_t mask_seed, const uint64_t* qids,
+                              uint32_t* srv_share, cudaStream_t st) {
+  if ((uint64_t)B * K == 0) return cudaSuccess;
+  const size_t smem = sizeof(uint64_t) * ntt_smem_words(P.N);
+  cudaError_t e = cudaFuncSetAttribute(slot_share_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  slot_share_kernel<<<(unsigned)((uint64_t)B * K), ntt_threads(P.N), smem, st>>>(P, PT, K, n, pos0, mask_seed,
+                                                                                  qids, srv_share);
   return cudaGetLastError();
 }
 

@@ -63,6 +63,7 @@ _SIGS = {
     "sanns_autotune_mac": ([_VP, _VP, _VP, C.c_uint32, _VP, C.c_int, _VP, _VP], C.c_int),
     "sanns_autotune_batched": ([_VP, _VP, _VP, C.c_uint32, _VP, C.c_int, _VP, _VP], C.c_int),
     "sanns_public_key": ([_VP, _VP, C.c_uint64, _VP, _VP], C.c_int),
+    "sanns_set_encoding": ([_VP, C.c_int], C.c_int),
     "sanns_set_response_form": ([_VP, C.c_int], C.c_int),
     "sanns_topk": ([_VP, _VP, _VP, C.c_uint32, C.c_uint64, C.c_uint32, C.c_uint64, C.c_uint32, _VP,
                     _VP, _VP], C.c_int),
@@ -380,6 +381,12 @@ def sanns_autotune_mac(ctx: Context, db: Database, ct_in: torch.Tensor, ct_out: 
     if rc < 0:
         _check(rc)
     return rc, list(ms)
+
+
+def sanns_set_encoding(ctx: Context, slots: bool):
+    """Slot encoding (True, needs t = 1 mod 2N) or coefficient encoding
+    (False, default) for databases encoded from now on and for decryption."""
+    _check(load().sanns_set_encoding(ctx.handle, 1 if slots else 0))
 
 
 def sanns_set_response_form(ctx: Context, ntt: bool):

@@ -466,3 +466,58 @@ def test_clustering_knns_one_probe_finds_own_cluster_points():
         bd = clustering.sq_dist(coords[union], q)
         assert set(ids.tolist()) <= set(union.tolist())
         assert np.array_equal(np.sort(clustering.sq_dist(coords[ids], q)), np.sort(bd)[:k])
+
+
+# ---------------------------------------------------------------- slot encoding
+@pytest.mark.parametrize("N", [64, 256])
+def test_slot_transform_definition_and_ring_isomorphism(N):
+    # NTT_t follows the same O(N^2) definition as the RNS transforms, with the
+    # smallest primitive 2N-th root mod t; it maps negacyclic products mod t
+    # to slot-wise products and constants to constant slots
+    O = Oracle(N, 2, 40, 0, 4)
+    t = O.t
+    assert O.slots_ok and (t - 1) % (2 * N) == 0
+    assert pow(O.psi_t, N, t) == t - 1
+    rnd = np.random.default_rng(N + 1)
+    a = rnd.integers(0, t, size=N, dtype=np.uint64)
+    b = rnd.integers(0, t, size=N, dtype=np.uint64)
+    fa, fb = O.ntt_t(a), O.ntt_t(b)
+    assert [int(v) for v in fa] == _ntt_definition(a, t, O.psi_t)
+    assert np.array_equal(O.intt_t(fa), a)
+    prod = O.schoolbook_mod(a, b, t)
+    assert np.array_equal(O.ntt_t(prod), (fa.astype(object) * fb.astype(object) % t).astype(np.uint64))
+    c = np.zeros(N, dtype=np.uint64)
+    c[0] = 12345
+    assert np.all(O.ntt_t(c) == 12345)
+
+
+def test_mask_draw_matches_coefficient_shares():
+    # the per-position mask value used by the slot shares is the one the
+    # coefficient-encoding epilogue draws (share = t - r)
+    O = Oracle(256, 2, 40, 0, 5)
+    coords = inputs.uniform_coords(600, 5, 3)
+    s, s_hat = O.keygen(1)
+    ct = O.encrypt(s_hat, inputs.uniform_coords(1, 5, 4)[0], 2, 7)
+    _, share = O.distances(ct, coords, None, 9, 7)
+    r = np.array([O.mask_r(9, 7, x) for x in range(600)], dtype=np.int64)
+    assert np.array_equal(share.astype(np.int64), (O.t - r) % O.t)
+
+
+@pytest.mark.parametrize("cfg,n", [((256, 2, 40, 0, 5), 700), ((64, 3, 50, 0, 3), 64)])
+def test_slot_encoding_shares_reconstruct_brute_force(cfg, n):
+    # the whole path in slot encoding: encrypted distances, slot shares on both
+    # sides, the sum equals the integer squared distance of every point
+    O = Oracle(*cfg)
+    d = cfg[4]
+    coords = inputs.uniform_coords(n, d, 11)
+    perm = inputs.permutation(n, 12)
+    qv = inputs.uniform_coords(1, d, 13)[0]
+    s, s_hat = O.keygen(5)
+    ct = O.encrypt(s_hat, qv, 6, 3)
+    out, srv = O.distances(ct, coords, perm, 8, 3, slots=True)
+    cli = O.decrypt_shares(out, s, qv, n, slots=True)
+    brute = np.sum((coords[perm].astype(np.int64) - qv.astype(np.int64)) ** 2, axis=1)
+    assert np.array_equal((cli.astype(np.int64) + srv) % O.t, brute)
+    # decrypting slot-encoded responses as coefficients does not give the distances
+    cli_coef = O.decrypt_shares(out, s, qv, n)
+    assert not np.array_equal((cli_coef.astype(np.int64) + srv) % O.t, brute)
