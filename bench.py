@@ -288,6 +288,31 @@ def run_gpu(args) -> None:
     nf_ms = c0.elapsed_time(c1) / cp_steps
     S.sanns_set_response_form(ctx, False)
 
+    # slot encoding (points in the CRT slots mod t): the same database encoded
+    # through the inverse transform mod t; the step adds the server's slot
+    # shares (one forward transform mod t per block); one query checked
+    # against brute force through the client's slot decoding
+    S.sanns_set_encoding(ctx, True)
+    db_s = S.sanns_encode_db(ctx, torch.from_numpy(coords).cuda(), torch.from_numpy(perm).cuda())
+    for s in range(3):
+        S.sanns_distances(ctx, db_s, ct_all[s:s + 1], mask_seed, qids[s:s + 1], ct_out, srv)
+    torch.cuda.synchronize()
+    c0.record(stream)
+    for s in range(cp_steps):
+        qi = s % W["n_queries"]
+        S.sanns_distances(ctx, db_s, ct_all[qi:qi + 1], mask_seed, qids[qi:qi + 1], ct_out, srv)
+    c1.record(stream)
+    torch.cuda.synchronize()
+    sl_ms = c0.elapsed_time(c1) / cp_steps
+    S.sanns_distances(ctx, db_s, ct_all[0:1], mask_seed, qids[0:1], ct_out, srv)
+    cli_s = S.sanns_decrypt_shares(ctx, sk, ct_out, n, qdev[0:1])
+    pts = torch.from_numpy(coords).cuda()[torch.from_numpy(perm.astype(np.int64)).cuda()]
+    brute = ((pts.int() - qdev[0].int()) ** 2).sum(1)
+    t_mod = ctx.query()["t"]
+    slot_exact = bool(torch.equal((cli_s[0].long() + srv[0].long()) % t_mod, brute.long()))
+    del db_s, cli_s, pts, brute
+    S.sanns_set_encoding(ctx, False)
+
     # end-to-end through the C ABI: each step copies its query ciphertext from
     # pinned host memory, runs sanns_distances and copies the response
     # ciphertexts and the server share back; three streams overlap step s's
@@ -389,6 +414,9 @@ def run_gpu(args) -> None:
             "selection": selection,
             "ntt_form_responses": {"ms_per_step": nf_ms, "steps": cp_steps,
                                    "value": world * n / (nf_ms * 1e-3), "unit": UNIT},
+            "slot_encoding": {"ms_per_step": sl_ms, "steps": cp_steps,
+                              "value": world * n / (sl_ms * 1e-3), "unit": UNIT,
+                              "shares_equal_brute_force": slot_exact},
             "circuit_privacy": {"ms_per_step": cp_ms, "flood_bits": flood, "steps": cp_steps,
                                 "value": world * n / (cp_ms * 1e-3), "unit": UNIT,
                                 "what": "public-key re-randomisation (one NTT per block per "
