@@ -18,9 +18,6 @@
 //
 // Launch variants (slots per lane, dimensions per load batch, threads, CTAs
 // per SM) trade registers for loads in flight; sanns_autotune_mac times them.
-// With PF, each warp asks for its next block's rows to be brought into L2
-// (bulk L2 prefetch, one request per row) when it starts a block, so that
-// its register loads of that block find them there.
 #include "internal.h"
 
 namespace sanns {
@@ -70,11 +67,7 @@ struct PtVec<2> {
 // ct tile in shared memory, per (dimension i, lane): for SPL = 1 one uint4
 // {c0 lo, c0 hi, c1 lo, c1 hi}; for SPL = 2 two uint4 (c0, c1), each
 // {lo(s0), hi(s0), lo(s1), hi(s1)}.
-__device__ __forceinline__ void prefetch_l2(const void* p, uint32_t bytes) {
-  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
-}
-
-template <int SPL, int UNR, int THREADS, int MINB, int PF = 0>
+template <int SPL, int UNR, int THREADS, int MINB>
 __global__ void __launch_bounds__(THREADS, MINB) mac_kernel(PrimeSet P, MacArgs A) {
   extern __shared__ uint4 cts[];
   constexpr int WARPS = THREADS / 32;
@@ -120,11 +113,6 @@ __global__ void __launch_bounds__(THREADS, MINB) mac_kernel(PrimeSet P, MacArgs 
     for (uint32_t kk = warp; kk < nk; kk += WARPS) {
       const uint64_t k = k_first + kk;
       const uint64_t* p = A.pt + ((k * L + j) * d) * N + st * TILE + SPL * lane;
-      if (PF && kk + WARPS < nk) {
-        // rows of block k + WARPS, this tile's 32 SPL slots each (16-byte aligned)
-        const uint64_t* nx = A.pt + (((k + WARPS) * L + j) * d) * N + st * TILE;
-        for (uint32_t i = lane; i < d; i += 32) prefetch_l2(nx + (uint64_t)i * N, 8 * TILE);
-      }
       u128 R[NOUT];
       uint64_t aL[NOUT], aM1[NOUT], aM2[NOUT], aH[NOUT];
 #pragma unroll
@@ -199,8 +187,6 @@ const MacVariant kVariants[] = {
     {mac_kernel<1, 16, 256, 3>, 1, 256, 3, "spl1_unr16_256x3"},
     {mac_kernel<1, 8, 256, 3>, 1, 256, 3, "spl1_unr8_256x3"},
     {mac_kernel<1, 16, 384, 2>, 1, 384, 2, "spl1_unr16_384x2"},
-    {mac_kernel<2, 8, 512, 1, 1>, 2, 512, 1, "spl2_unr8_512x1_pf"},
-    {mac_kernel<1, 16, 256, 3, 1>, 1, 256, 3, "spl1_unr16_256x3_pf"},
 };
 constexpr int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
 
