@@ -197,13 +197,17 @@ int sanns_gather_plan(const sanns_clusters *cl, const uint32_t *probes_host, uin
  * For query b the gathered list plays the role of the permuted database of
  * sanns_distances: position pos of the list is a point, blocks of N
  * positions are encoded, multiplied with ct_in[b], transformed back and
- * masked with r drawn from stream (mask_seed, 4, qids[b]) at pos.
+ * masked with r drawn from stream (mask_seed, 4, qids[b]) at pos.  The
+ * context's circuit privacy and encoding apply as in sanns_distances, with
+ * the list positions (from 0) as positions: each query's result is that of
+ * sanns_distances on its gathered list as a database.
  * Outputs are concatenated query by query: ct_out_dev [sum_b blocks_b][2][L][N]
- * (coefficient form), srv_share_dev uint32 [sum_b n_b], ids_dev uint32
- * [sum_b n_b] = the point index at each gathered position (may be NULL).
- * Requires N <= 8192.  Uses a stream-ordered scratch allocation of about
- * sum_b blocks_b (d + 4) N bytes and synchronises the stream once after
- * uploading the plan.
+ * (coefficient form; NTT-form responses are rejected), srv_share_dev uint32
+ * [sum_b n_b], ids_dev uint32 [sum_b n_b] = the point index at each gathered
+ * position (may be NULL).  Requires N <= 8192.  Uses a stream-ordered scratch
+ * allocation of about sum_b blocks_b (d + 4 + 16 L S) N bytes (S dimension
+ * slices, sized for about four units per SM) and synchronises the stream
+ * once after uploading the plan.
  */
 int sanns_distances_gather(sanns_ctx *ctx, const sanns_clusters *cl, const uint64_t *ct_in_dev,
                            uint32_t B, const uint32_t *probes_host, uint32_t P, uint64_t mask_seed,
@@ -288,7 +292,7 @@ int sanns_autotune_batched(sanns_ctx *ctx, const sanns_db *db, const uint64_t *c
  *                encoding: they add up to ||q - p||^2 mod t.
  * A database keeps the encoding the context had when it was encoded; the
  * distance calls reject a database whose encoding differs from the context's,
- * and slot encoding rejects NTT-form responses and the gather path.
+ * and slot encoding rejects NTT-form responses.
  * sanns_decrypt_shares (and its no-allocation variant) decode in the
  * context's encoding.  SANNS_EINVAL for slots when t != 1 mod 2N.
  */
@@ -377,8 +381,7 @@ int sanns_topk_segments(sanns_ctx *ctx, const uint32_t *cli_dev, const uint32_t 
  *                         pk_dev = NULL turns it off.  F above
  *                         sanns_circuit_privacy_max_flood_bits (2^F <= Delta /
  *                         4, so decryption stays correct) returns SANNS_EINVAL.
- *                         Synchronous.  The gather path rejects calls while it
- *                         is on.
+ *                         Synchronous.
  */
 int sanns_public_key(sanns_ctx *ctx, const sanns_sk *sk, uint64_t seed, uint64_t *pk_dev, void *stream);
 int sanns_circuit_privacy_max_flood_bits(const sanns_ctx *ctx);

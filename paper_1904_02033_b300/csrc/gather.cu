@@ -24,6 +24,12 @@
 //               and the server share t - r.  Slices are sized so that even a
 //               single work item spreads over every multiprocessor.
 // A work item is one block of N positions of one query's gathered list.
+// Each query's list is treated as a database of its own (positions from 0),
+// so with circuit privacy the finishing block adds pk * NTT(u) before the
+// INTT and the flooding terms e1, e2 after it, drawn at the list positions;
+// with slot encoding the coordinates and norms go through the inverse
+// transform mod t first and a last pass writes the slot shares.
+#include <cstring>
 #include <vector>
 
 #include "internal.h"
@@ -93,11 +99,23 @@ __device__ __forceinline__ uint64_t mont_mul(uint64_t c, uint64_t p_mont, uint64
   return csub(redc128((u128)c * p_mont, q, qn), q);
 }
 
-// Back to coefficient form and mask (c = 0), store: one component of one
-// (item, prime) held in a (padded shared memory).
+// Options of the gather: slot encoding (PT) and circuit privacy (pk and its
+// Shoup companions in NTT form, flooding exponent F).
+struct GatherOpts {
+  PrimeSet PT;
+  int slots;
+  const uint64_t* pk;
+  const uint64_t* pks;
+  uint32_t F;
+  PrivacyConsts C;
+};
+
+// Back to coefficient form and mask (c = 0), flooding (with privacy), store:
+// one component of one (item, prime) held in a (padded shared memory).
 __device__ void gather_finish(uint64_t* a, const PrimeSet& P, uint32_t j, uint32_t c, uint64_t w,
                               const GatherItem& it, const GatherQuery& Q, const uint32_t* gnorm,
-                              uint64_t mask_seed, uint64_t qid, uint64_t* ct_out, uint32_t* srv_share) {
+                              uint64_t mask_seed, uint64_t qid, const GatherOpts& O, uint64_t* ct_out,
+                              uint32_t* srv_share) {
   const uint32_t N = P.N, L = P.L;
   const uint64_t q = P.q[j];
   __syncthreads();
@@ -123,6 +141,37 @@ __device__ void gather_finish(uint64_t* a, const PrimeSet& P, uint32_t j, uint32
     }
     __syncthreads();
   }
+  if (O.pk) {
+    // flooding: e1 on c0 (uniform in [-2^F, 2^F)), e2 on c1 (CBD 21)
+    for (uint32_t t4 = threadIdx.x; t4 < N / 4; t4 += blockDim.x) {
+      const uint32_t ctr = (uint32_t)(((uint64_t)it.kb * N + 4 * t4) / 4);
+      uint32_t ba[16], bb[16];
+      if (c == 0) {
+        chacha20_block(mask_seed, kPurposeFloodLo, qid, ctr, ba);
+        chacha20_block(mask_seed, kPurposeFloodHi, qid, ctr, bb);
+      } else {
+        chacha20_block(mask_seed, kPurposeE2, qid, ctr, ba);
+      }
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        const uint32_t x = 4 * t4 + v;
+        uint64_t e;
+        if (c == 0) {
+          uint64_t wv[4];
+          draw_pair(ba, v, wv[0], wv[1]);
+          draw_pair(bb, v, wv[2], wv[3]);
+          e = flood_e1(wv, O.F, q, O.C.q_barrett[j], P.r64[j], P.r64_shoup[j], O.C.two_f[j]);
+        } else {
+          uint64_t lo, hi;
+          draw_pair(ba, v, lo, hi);
+          const int e2 = cbd21_of(lo);
+          e = e2 < 0 ? q - (uint64_t)(-e2) : (uint64_t)e2;
+        }
+        a[SP(x)] = add_mod(a[SP(x)], e, q);
+      }
+    }
+    __syncthreads();
+  }
   uint64_t* dst = ct_out + ((it.blk * 2 + c) * L + j) * N;
   for (uint32_t x = threadIdx.x; x < N; x += blockDim.x) dst[x] = a[SP(x)];
 }
@@ -136,7 +185,7 @@ gather_kernel(PrimeSet P, uint32_t d, uint64_t W, uint32_t S, uint32_t ds,
               const uint8_t* __restrict__ gco, const uint32_t* __restrict__ gnorm,
               const uint64_t* __restrict__ ct_in, uint64_t mask_seed, const uint64_t* __restrict__ qids,
               uint64_t* __restrict__ part, uint32_t* __restrict__ tickets, uint64_t* __restrict__ ct_out,
-              uint32_t* __restrict__ srv_share) {
+              uint32_t* __restrict__ srv_share, GatherOpts O) {
   extern __shared__ uint64_t smem[];
   __shared__ uint32_t ticket;
   const uint32_t N = P.N, L = P.L;
@@ -160,6 +209,10 @@ gather_kernel(PrimeSet P, uint32_t d, uint64_t W, uint32_t S, uint32_t ds,
       __syncthreads();
       for (uint32_t x = threadIdx.x; x < N; x += blockDim.x) poly[SP(x)] = g[(uint64_t)i * N + x];
       __syncthreads();
+      if (O.slots) {
+        ntt_inverse_smem(poly, O.PT, 0);
+        __syncthreads();
+      }
       ntt_forward_smem(poly, P, (int)j);
       __syncthreads();
       const uint64_t* c0 = ct_in + ((((uint64_t)it.b * d + i) * 2 + 0) * L + j) * N;
@@ -186,15 +239,69 @@ gather_kernel(PrimeSet P, uint32_t d, uint64_t W, uint32_t S, uint32_t ds,
     const GatherQuery Q = qs[it.b];
     const uint64_t qid = qids[it.b];
     const uint64_t* all = part + wj * S * 2 * N;
+    if (O.pk) {
+      // re-randomisation: u ternary at the list positions, transformed
+      for (uint32_t u4 = threadIdx.x; u4 < N / 4; u4 += blockDim.x) {
+        uint32_t blk[16];
+        chacha20_block(mask_seed, kPurposeU, qid, (uint32_t)(((uint64_t)it.kb * N) / 4 + u4), blk);
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+          uint64_t lo, hi;
+          draw_pair(blk, v, lo, hi);
+          const int uv = (int)(lo % 3) - 1;
+          poly[SP(4 * u4 + v)] = uv < 0 ? q - 1 : (uint64_t)uv;
+        }
+      }
+      __syncthreads();
+      ntt_forward_smem(poly, P, (int)j);
+      __syncthreads();
+    }
     for (uint32_t c = 0; c < 2; ++c) {
       uint64_t* a = c == 0 ? acc0 : acc1;
+      const uint64_t* pkc = O.pk ? O.pk + ((size_t)c * L + j) * N : nullptr;
+      const uint64_t* pksc = O.pk ? O.pks + ((size_t)c * L + j) * N : nullptr;
       for (uint32_t x = threadIdx.x; x < N; x += blockDim.x) {
         uint64_t v = 0;
         for (uint32_t s2 = 0; s2 < S; ++s2) v = add_mod(v, __ldcg(all + ((uint64_t)s2 * 2 + c) * N + x), q);
+        if (pkc) v = add_mod(v, mul_shoup(poly[SP(x)], pkc[x], pksc[x], q), q);
         a[SP(x)] = v;
       }
-      gather_finish(a, P, j, c, w, it, Q, gnorm, mask_seed, qid, ct_out, srv_share);
+      gather_finish(a, P, j, c, w, it, Q, gnorm, mask_seed, qid, O, ct_out, srv_share);
     }
+  }
+}
+
+// Slot encoding: one block per work item; the mask polynomial R of the item
+// (coefficient draws at the list positions, padding included) to slots,
+// srv_share = t - NTT_t(R) at the query's positions.
+__global__ void __launch_bounds__(512) gather_slot_share_kernel(PrimeSet P, PrimeSet PT,
+                                                                const GatherItem* __restrict__ items,
+                                                                const GatherQuery* __restrict__ qs,
+                                                                uint64_t mask_seed, const uint64_t* __restrict__ qids,
+                                                                uint32_t* __restrict__ srv_share) {
+  extern __shared__ uint64_t sa[];
+  const uint32_t N = P.N;
+  const GatherItem it = items[blockIdx.x];
+  const GatherQuery Q = qs[it.b];
+  const uint64_t qid = qids[it.b];
+  for (uint32_t u = threadIdx.x; u < N / 4; u += blockDim.x) {
+    uint32_t blk[16];
+    chacha20_block(mask_seed, kPurposeMask, qid, (uint32_t)(((uint64_t)it.kb * N) / 4 + u), blk);
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      uint64_t lo, hi;
+      draw_pair(blk, v, lo, hi);
+      sa[SP(4 * u + v)] = mod_t128(lo, hi, P);
+    }
+  }
+  __syncthreads();
+  ntt_forward_smem(sa, PT, 0);
+  __syncthreads();
+  for (uint32_t x = threadIdx.x; x < N; x += blockDim.x) {
+    const uint64_t pos = (uint64_t)it.kb * N + x;
+    if (pos >= Q.n) break;
+    const uint64_t r = sa[SP(x)];
+    srv_share[Q.pos_off + pos] = (uint32_t)(r == 0 ? 0 : P.t - r);
   }
 }
 
@@ -212,7 +319,8 @@ cudaError_t launch_gather(const PrimeSet& P, uint32_t d, const sanns_clusters* c
                           const uint64_t* ct_in, uint32_t B, const uint32_t* probes_host,
                           uint32_t Pr, const uint64_t* n_b, uint64_t mask_seed,
                           const uint64_t* qids, uint64_t* ct_out, uint32_t* srv_share,
-                          uint32_t* ids, int sms, cudaStream_t st) {
+                          uint32_t* ids, int sms, const PrimeSet* PT, const uint64_t* pk,
+                          const uint64_t* pks, uint32_t F, const PrivacyConsts& C, cudaStream_t st) {
   const uint32_t N = P.N;
   // host plan: items (query-major), per-query offsets, probe segments
   std::vector<GatherItem> items;
@@ -271,6 +379,19 @@ cudaError_t launch_gather(const PrimeSet& P, uint32_t d, const sanns_clusters* c
         cl->d_coords, scratch + o_gco, reinterpret_cast<uint32_t*>(scratch + o_norm), ids);
     e = cudaGetLastError();
   }
+  if (e == cudaSuccess && PT) e = launch_norms_slot(*PT, reinterpret_cast<uint32_t*>(scratch + o_norm), W, st);
+  GatherOpts O;
+  memset(&O, 0, sizeof(O));
+  if (PT) {
+    O.PT = *PT;
+    O.slots = 1;
+  } else {
+    O.PT = P;
+  }
+  O.pk = pk;
+  O.pks = pks;
+  O.F = F;
+  O.C = C;
   uint64_t* part = reinterpret_cast<uint64_t*>(scratch + o_part);
   uint32_t* tickets = reinterpret_cast<uint32_t*>(scratch + o_tick);
   if (e == cudaSuccess) e = cudaMemsetAsync(tickets, 0, sizeof(uint32_t) * (size_t)W * P.L, st);
@@ -283,7 +404,16 @@ cudaError_t launch_gather(const PrimeSet& P, uint32_t d, const sanns_clusters* c
     if (e == cudaSuccess) {
       gather_kernel<<<grid, th, smem, st>>>(P, d, W, S, ds, d_items, d_qs, scratch + o_gco,
                                             reinterpret_cast<const uint32_t*>(scratch + o_norm), ct_in,
-                                            mask_seed, qids, part, tickets, ct_out, srv_share);
+                                            mask_seed, qids, part, tickets, ct_out, srv_share, O);
+      e = cudaGetLastError();
+    }
+  }
+  if (e == cudaSuccess && PT) {
+    const size_t smem = sizeof(uint64_t) * ntt_smem_words(N);
+    e = cudaFuncSetAttribute(gather_slot_share_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) {
+      gather_slot_share_kernel<<<(unsigned)W, gather_threads(N), smem, st>>>(P, *PT, d_items, d_qs, mask_seed,
+                                                                             qids, srv_share);
       e = cudaGetLastError();
     }
   }

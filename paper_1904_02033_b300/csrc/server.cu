@@ -489,6 +489,15 @@ cudaError_t launch_encode(const PrimeSet& P, const PrimeSet* PT, const uint8_t* 
   return cudaGetLastError();
 }
 
+cudaError_t launch_norms_slot(const PrimeSet& PT, uint32_t* norms, uint64_t K, cudaStream_t st) {
+  if (K == 0) return cudaSuccess;
+  const size_t smem = sizeof(uint64_t) * ntt_smem_words(PT.N);
+  cudaError_t e = cudaFuncSetAttribute(norms_slot_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  norms_slot_kernel<<<(unsigned)K, ntt_threads(PT.N), smem, st>>>(PT, norms);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_slot_share(const PrimeSet& P, const PrimeSet& PT, uint32_t B, uint64_t K, uint64_t n,
                               uint64_t pos0, uint64_t mask_seed, const uint64_t* qids,
                               uint32_t* srv_share, cudaStream_t st) {

@@ -1,6 +1,7 @@
 """GPU parity of the clustering-protocol gather path (one persistent launch
 over uneven per-query cluster gathers) against the oracle, which treats each
-query's gathered list as a permuted database."""
+query's gathered list as a permuted database; also with circuit privacy and
+with slot encoding."""
 import numpy as np
 import pytest
 import torch
@@ -21,12 +22,15 @@ def gathered_list(offsets, members, probes_b):
                           + [np.zeros(0, dtype=np.uint32)]).astype(np.uint32)
 
 
-@pytest.mark.parametrize("cfg,n,C,B,P", [
-    ((256, 2, 40, 0, 5), 3000, 20, 3, 4),
-    ((64, 2, 50, 0, 3), 500, 7, 2, 7),       # probes covering every cluster, tiny N
-    ((8192, 3, 60, 0, 4), 30000, 9, 2, 3),   # N = 8192, three 60-bit primes
+@pytest.mark.parametrize("cfg,n,C,B,P,F,slots", [
+    ((256, 2, 40, 0, 5), 3000, 20, 3, 4, 0, False),
+    ((64, 2, 50, 0, 3), 500, 7, 2, 7, 0, False),       # probes covering every cluster, tiny N
+    ((8192, 3, 60, 0, 4), 30000, 9, 2, 3, 0, False),   # N = 8192, three 60-bit primes
+    ((256, 3, 60, 0, 5), 3000, 20, 3, 4, 100, False),  # circuit privacy
+    ((256, 2, 40, 0, 5), 3000, 20, 3, 4, 0, True),     # slot encoding
+    ((8192, 3, 60, 0, 4), 30000, 9, 2, 3, 148, True),  # both, N = 8192
 ])
-def test_gather_matches_oracle(cfg, n, C, B, P):
+def test_gather_matches_oracle(cfg, n, C, B, P, F, slots):
     N, L, bits, rule, d = cfg
     rnd = np.random.default_rng(n)
     coords = inputs.uniform_coords(n, d, 1)
@@ -43,6 +47,12 @@ def test_gather_matches_oracle(cfg, n, C, B, P):
 
     ctx = S.sanns_ctx_create(*cfg)
     sk = S.sanns_keygen(ctx, 3)
+    S.sanns_set_encoding(ctx, slots)
+    pk = None
+    if F:
+        pk_d = S.sanns_public_key(ctx, sk, 8)
+        S.sanns_set_circuit_privacy(ctx, pk_d, F)
+        pk = pk_d.cpu().numpy()
     cl = S.sanns_clusters_create(ctx, cu(coords), offsets, cu(members))
     ct_in = S.sanns_encrypt_query(ctx, sk, cu(q), 4, cu(qids))
     ct_out, srv, ids, n_b, k_b = S.sanns_distances_gather(ctx, cl, ct_in, probes, 6, cu(qids))
@@ -58,10 +68,11 @@ def test_gather_matches_oracle(cfg, n, C, B, P):
         assert int(n_b[b]) == len(g) and int(k_b[b]) == -(-len(g) // N)
         assert np.array_equal(ids[nb0:nb0 + len(g)], g)
         if len(g):
-            want_out, want_srv = O.distances(ct_np[b], coords, g, 6, int(qids[b]))
+            want_out, want_srv = O.distances(ct_np[b], coords, g, 6, int(qids[b]), pk=pk, flood_bits=F,
+                                             slots=slots)
             assert np.array_equal(ct_out[kb0:kb0 + int(k_b[b])], want_out)
             assert np.array_equal(srv[nb0:nb0 + len(g)], want_srv)
-            cli = O.decrypt_shares(want_out, s, q[b], len(g))
+            cli = O.decrypt_shares(want_out, s, q[b], len(g), slots=slots)
             brute = np.sum((coords[g].astype(np.int64) - q[b].astype(np.int64)) ** 2, axis=1)
             assert np.array_equal((cli.astype(np.int64) + want_srv) % O.t, brute)
         kb0 += int(k_b[b])

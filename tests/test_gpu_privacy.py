@@ -80,7 +80,7 @@ def test_private_distances_match_oracle(cfg, n, B, F, batched):
     assert torch.equal(again, plain_out)
 
 
-def test_flood_bits_bound_and_gather_rejected():
+def test_flood_bits_bound():
     cfg = (256, 2, 40, 0, 4)
     ctx = S.sanns_ctx_create(*cfg)
     sk = S.sanns_keygen(ctx, 1)
@@ -91,12 +91,3 @@ def test_flood_bits_bound_and_gather_rejected():
         S.sanns_set_circuit_privacy(ctx, pk, fmax + 1)
     assert e.value.code == -1
     S.sanns_set_circuit_privacy(ctx, pk, fmax)
-    coords = inputs.uniform_coords(300, 4, 3)
-    offsets = np.array([0, 150, 300], dtype=np.uint64)
-    members = np.arange(300, dtype=np.uint32)
-    cl = S.sanns_clusters_create(ctx, cu(coords), offsets, cu(members))
-    q = inputs.uniform_coords(1, 4, 4)
-    ct = S.sanns_encrypt_query(ctx, sk, cu(q), 5, cu(np.array([1], dtype=np.uint64)))
-    with pytest.raises(S.SannsError):
-        S.sanns_distances_gather(ctx, cl, ct, np.array([[0]], dtype=np.uint32), 6,
-                                 cu(np.array([1], dtype=np.uint64)))
