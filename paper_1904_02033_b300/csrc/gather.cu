@@ -217,10 +217,23 @@ gather_kernel(PrimeSet P, uint32_t d, uint64_t W, uint32_t S, uint32_t ds,
       __syncthreads();
       const uint64_t* c0 = ct_in + ((((uint64_t)it.b * d + i) * 2 + 0) * L + j) * N;
       const uint64_t* c1 = ct_in + ((((uint64_t)it.b * d + i) * 2 + 1) * L + j) * N;
-      for (uint32_t x = threadIdx.x; x < N; x += blockDim.x) {
-        const uint64_t pm = mul_shoup(poly[SP(x)], P.r64[j], P.r64_shoup[j], q);
-        acc0[SP(x)] = add_mod(acc0[SP(x)], mont_mul(__ldg(c0 + x), pm, q, qn), q);
-        acc1[SP(x)] = add_mod(acc1[SP(x)], mont_mul(__ldg(c1 + x), pm, q, qn), q);
+      // four slots' ciphertext words requested before any is used
+      for (uint32_t x0 = threadIdx.x; x0 < N; x0 += 4 * blockDim.x) {
+        uint64_t v0[4], v1[4];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+          const uint32_t x = x0 + r * blockDim.x;
+          v0[r] = x < N ? __ldg(c0 + x) : 0;
+          v1[r] = x < N ? __ldg(c1 + x) : 0;
+        }
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+          const uint32_t x = x0 + r * blockDim.x;
+          if (x >= N) break;
+          const uint64_t pm = mul_shoup(poly[SP(x)], P.r64[j], P.r64_shoup[j], q);
+          acc0[SP(x)] = add_mod(acc0[SP(x)], mont_mul(v0[r], pm, q, qn), q);
+          acc1[SP(x)] = add_mod(acc1[SP(x)], mont_mul(v1[r], pm, q, qn), q);
+        }
       }
     }
     __syncthreads();
