@@ -3,6 +3,8 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <map>
+#include <mutex>
 #include <vector>
 
 #include "internal.h"
@@ -11,6 +13,21 @@ namespace sanns {
 
 namespace {
 thread_local std::string g_last_error;
+std::mutex g_attr_mu;
+std::map<std::pair<const void*, int>, size_t> g_attr_done;
+}
+
+cudaError_t ensure_smem_attr(const void* kernel, size_t bytes) {
+  int dev = -1;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lock(g_attr_mu);
+  const auto key = std::make_pair(kernel, dev);
+  auto it = g_attr_done.find(key);
+  if (it != g_attr_done.end() && it->second >= bytes) return cudaSuccess;
+  e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e == cudaSuccess) g_attr_done[key] = bytes;
+  return e;
 }
 
 int fail(int code, const std::string& msg) {

@@ -74,6 +74,10 @@ int cuda_fail(cudaError_t e, const char* what);
     if (_e != cudaSuccess) return sanns::cuda_fail(_e, #call); \
   } while (0)
 
+// The dynamic shared-memory opt-in of a kernel, set once per (kernel, device)
+// for at least `bytes` (thread-safe; a process may drive several devices).
+cudaError_t ensure_smem_attr(const void* kernel, size_t bytes);
+
 // parameter derivation (params.cpp)
 int derive_params(const sanns_params& in, uint64_t q[], uint64_t psi[], uint64_t* t);
 uint64_t smallest_psi(uint64_t q, uint64_t N);

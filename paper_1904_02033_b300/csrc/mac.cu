@@ -210,16 +210,9 @@ cudaError_t launch_mac(const PrimeSet& P, const uint64_t* ct, const uint64_t* pt
   A.total = (uint64_t)B * P.L * (P.N / tile) * K;
   if (A.total == 0) return cudaSuccess;
   const size_t smem = sizeof(uint4) * 32 * d * V.spl;
-  // shared-memory opt-in once per variant (the attribute is per function)
-  static bool configured[kNumVariants] = {};
-  static size_t configured_smem[kNumVariants] = {};
-  if (!configured[variant] || configured_smem[variant] < smem) {
-    cudaError_t e = cudaFuncSetAttribute(V.fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)(smem > 48 * 1024 ? smem : 48 * 1024));
-    if (e != cudaSuccess) return e;
-    configured[variant] = true;
-    configured_smem[variant] = smem > 48 * 1024 ? smem : 48 * 1024;
-  }
+  // shared-memory opt-in, once per (variant, device)
+  cudaError_t e = ensure_smem_attr((const void*)V.fn, smem > 48 * 1024 ? smem : 48 * 1024);
+  if (e != cudaSuccess) return e;
   int per_sm = V.ctas_per_sm;
   // fewer co-resident CTAs when the ct tile is large
   while (per_sm > 1 && smem * per_sm > 220 * 1024) --per_sm;

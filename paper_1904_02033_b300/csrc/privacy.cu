@@ -176,13 +176,8 @@ cudaError_t launch_rerandomize(const PrimeSet& P, uint64_t* ct, uint32_t B, uint
   const uint64_t blocks = (uint64_t)B * K * P.L;
   if (blocks == 0) return cudaSuccess;
   const size_t smem = sizeof(uint64_t) * ntt_smem_words(P.N);
-  static bool configured = false;
-  if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(rerandomize_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)(sizeof(uint64_t) * ntt_smem_words(kMaxN)));
-    if (e != cudaSuccess) return e;
-    configured = true;
-  }
+  cudaError_t e = ensure_smem_attr((const void*)rerandomize_kernel, smem);
+  if (e != cudaSuccess) return e;
   rerandomize_kernel<<<(unsigned)blocks, pv_threads(P.N), smem, st>>>(P, ct, K, pos0, seed, qids, pk, pks);
   return cudaGetLastError();
 }

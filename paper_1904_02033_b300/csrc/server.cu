@@ -522,16 +522,9 @@ cudaError_t launch_intt_mask(const PrimeSet& P, uint64_t* ct_out, const uint32_t
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const size_t smem = sizeof(uint64_t) * ntt_smem_words(P.N);
-  static bool configured = false;
-  if (!configured) {
-    e = cudaFuncSetAttribute(intt_mask_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)(sizeof(uint64_t) * ntt_smem_words(kMaxN)));
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(intt_mask_short_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)(sizeof(uint64_t) * ntt_smem_words(kMaxN)));
-    if (e != cudaSuccess) return e;
-    configured = true;
-  }
+  e = ensure_smem_attr((const void*)intt_mask_kernel, smem);
+  if (e == cudaSuccess) e = ensure_smem_attr((const void*)intt_mask_short_kernel, smem);
+  if (e != cudaSuccess) return e;
   // three blocks per SM; up to two waves the per-block latency decides, past
   // that the throughput of the fused kernel
   if (polys <= 2ull * 3 * (uint64_t)(sms > 0 ? sms : 148))
@@ -556,13 +549,8 @@ cudaError_t launch_mask_ntt(const PrimeSet& P, uint64_t* ct_out, const uint32_t*
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const size_t smem = sizeof(uint64_t) * ntt_smem_words(P.N);
-  static bool configured = false;
-  if (!configured) {
-    e = cudaFuncSetAttribute(mask_ntt_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)(sizeof(uint64_t) * ntt_smem_words(kMaxN)));
-    if (e != cudaSuccess) return e;
-    configured = true;
-  }
+  e = ensure_smem_attr((const void*)mask_ntt_kernel, smem);
+  if (e != cudaSuccess) return e;
   mask_ntt_kernel<<<(unsigned)polys, ntt_threads(P.N), smem, st>>>(P, ct_out, norms, K, n, pos0, mask_seed,
                                                                    qids, srv_share, comps, privacy ? 1 : 0,
                                                                    F, C);
