@@ -671,13 +671,34 @@ def run_alg4_section() -> dict:
     st64 = {key: round(v, 3) for key, v in st64.items()}
     # 10-NN accuracy against brute force (exact integer distances)
     xf = coords.to(torch.int64)
-    acc = 0.0
+    kths = []
     for b in range(Bb):
         dq = ((xf - q_all[b].to(torch.int64)[None, :]) ** 2).sum(1)
-        kth = torch.kthvalue(dq, W["k"]).values
-        got = torch.from_numpy(ids[b]).cuda()
-        acc += float(((dq[got.clamp(min=0)] <= kth) & (got >= 0)).sum()) / W["k"]
-    acc /= Bb
+        kths.append((dq, torch.kthvalue(dq, W["k"]).values))
+
+    def accuracy(ids):
+        a = 0.0
+        for b in range(Bb):
+            dq, kth = kths[b]
+            got = torch.from_numpy(ids[b]).cuda()
+            a += float(((dq[got.clamp(min=0)] <= kth) & (got >= 0)).sum()) / W["k"]
+        return a / Bb
+
+    acc = accuracy(ids)
+    # the cost / accuracy trade-off: more clusters and bins per group
+    sizes_g = np.diff(lay.group_offsets)
+    tradeoff = []
+    for scale in (2, 4):
+        us = tuple(int(min(x * scale, sizes_g[i])) for i, x in enumerate(u))
+        ls = tuple(int(max(min(x * scale, sizes_g[i]), us[i])) for i, x in enumerate(l))
+        p2 = cluster.Params(W["k"], us, ls, W["l_s"] * scale, W["r_c"], W["r_p"])
+        cluster.query(srv, sk, q_all, qids, p2)
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
+        ids2 = cluster.query(srv, sk, q_all, qids, p2)
+        ms2 = (time.perf_counter() - t2) * 1e3
+        tradeoff.append({"u_l_scale": scale, "u": list(us), "ms_B64": ms2,
+                         "queries_per_s": Bb / (ms2 * 1e-3), "accuracy_10nn": accuracy(ids2)})
     S.sanns_device_status(ctx)
     N = W["N"]
     sizes = np.diff(lay.cl_offsets.astype(np.int64))
@@ -697,6 +718,7 @@ def run_alg4_section() -> dict:
         "response_blocks_per_query_at_most": blocks,
         "linear_scan_blocks_per_query": -(-n // N),
         "accuracy_10nn": acc,
+        "tradeoff": tradeoff,
         "timing": "host wall clock per call (the pipeline reads selections back to plan the gather)",
     }
 
