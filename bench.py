@@ -688,7 +688,7 @@ def run_alg4_section() -> dict:
     # the cost / accuracy trade-off: more clusters and bins per group
     sizes_g = np.diff(lay.group_offsets)
     tradeoff = []
-    for scale in (2, 4):
+    for scale in (2, 4, 8):
         us = tuple(int(min(x * scale, sizes_g[i])) for i, x in enumerate(u))
         ls = tuple(int(max(min(x * scale, sizes_g[i]), us[i])) for i, x in enumerate(l))
         p2 = cluster.Params(W["k"], us, ls, W["l_s"] * scale, W["r_c"], W["r_p"])
