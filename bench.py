@@ -359,6 +359,19 @@ def run_gpu(args) -> None:
     last.synchronize()
     torch.cuda.synchronize()
     e2e_ms = (time.perf_counter() - t_start) * 1e3 / e2e_steps
+    # the host link alone: the same uploads and downloads, both directions at
+    # once on their own streams, no compute
+    link_reps = 20
+    torch.cuda.synchronize()
+    t_l = time.perf_counter()
+    for r in range(link_reps):
+        with torch.cuda.stream(s_up):
+            ct_dev[r % 2].copy_(ct_host[r % nh:r % nh + 1], non_blocking=True)
+        with torch.cuda.stream(s_dn):
+            out_host[r % 2].copy_(out_dev[r % 2], non_blocking=True)
+            srv_host[r % 2].copy_(srv_dev[r % 2], non_blocking=True)
+    torch.cuda.synchronize()
+    link_ms = (time.perf_counter() - t_l) * 1e3 / link_reps
     if dist:
         tt = torch.tensor([e2e_ms], device="cuda")
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
@@ -409,6 +422,8 @@ def run_gpu(args) -> None:
             "e2e": {"value": world * n / (e2e_ms * 1e-3), "unit": UNIT,
                     "h2d_bytes_per_step": d * 2 * L * N * 8,
                     "d2h_bytes_per_step": K * 2 * L * N * 8 + n * 4, "ms_per_step": e2e_ms,
+                    "link_only_ms_per_step": link_ms,
+                    "link_bound_frac": link_ms / e2e_ms,
                     "timing": "host wall clock over pipelined steps (3 streams: upload, "
                               "compute, download)"},
             "selection": selection,
