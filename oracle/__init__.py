@@ -13,13 +13,19 @@ Contents
                   keygen, encrypt, DB encoding, ct x pt MAC, INTT + mask,
                   the c0 + c1 s step of decryption, schoolbook products.
   params.py       exact-integer parameter derivation (primes, psi, t, Delta).
-  bfv.py          ctypes wrappers + exact big-integer CRT scale-and-round.
+  bfv.py          ctypes wrappers + exact big-integer CRT scale-and-round;
+                  circuit privacy (public key, re-randomisation, flooding);
+                  slot encoding (the negacyclic transform mod t, slot shares).
   select.py       Algorithms 1 and 2 (NaiveTopk, ApproxTopk) in plaintext.
+  clustering.py   Algorithm 4 (ClusteringKNNS) in plaintext on a given server
+                  layout (groups of clusters with shuffled centres, stash).
 
 Parity pins: every function above is pinned by a -m "not gpu" test against
 something other than itself (O(N^2) NTT definition, schoolbook products,
 RFC 8439 test vectors, decrypt(encrypt(m)) = m, brute-force distances,
-sympy primality, closed forms for ApproxTopk).  The concrete ciphertext bits
+sympy primality, closed forms for ApproxTopk, the mod-t transform as a ring
+isomorphism, Algorithm 4 reducing to brute force when every cluster is
+retrieved).  The concrete ciphertext bits
 depend on conventions the paper leaves open (RNG layout, NTT order); those
 are pinned only through the conventions and the round-trip identities --
 "parity unpinned" by a printed value from the paper.
