@@ -18,6 +18,9 @@
 //
 // Launch variants (slots per lane, dimensions per load batch, threads, CTAs
 // per SM) trade registers for loads in flight; sanns_autotune_mac times them.
+// Pair variants (QN = 2) hold two queries' ct tiles and use every database
+// word they load for both, halving the database traffic of a multi-query
+// call; calls with B >= 2 run the pair sibling of the selected variant.
 #include "internal.h"
 
 namespace sanns {
@@ -31,8 +34,9 @@ struct MacArgs {
   const uint64_t* pt;  // [K][L][d][N], NTT form
   uint64_t* out;       // [B][K][2][L][N]
   uint64_t K;
-  uint64_t total;      // B L (N / tile) K work items (tile, block)
+  uint64_t total;      // ceil(B / QN) L (N / tile) K work items (tile, block)
   uint32_t d;
+  uint32_t B;
 };
 
 __device__ __forceinline__ void mac4(uint64_t& aL, uint64_t& aM1, uint64_t& aM2, uint64_t& aH,
@@ -65,14 +69,15 @@ struct PtVec<2> {
 };
 
 // ct tile in shared memory, per (dimension i, lane): for SPL = 1 one uint4
-// {c0 lo, c0 hi, c1 lo, c1 hi}; for SPL = 2 two uint4 (c0, c1), each
-// {lo(s0), hi(s0), lo(s1), hi(s1)}.
-template <int SPL, int UNR, int THREADS, int MINB>
+// {c0 lo, c0 hi, c1 lo, c1 hi} per query of the pass (QN of them); for
+// SPL = 2 two uint4 (c0, c1), each {lo(s0), hi(s0), lo(s1), hi(s1)}.
+template <int SPL, int UNR, int THREADS, int MINB, int QN = 1>
 __global__ void __launch_bounds__(THREADS, MINB) mac_kernel(PrimeSet P, MacArgs A) {
+  static_assert(QN == 1 || SPL == 1, "query pairs use one slot per lane");
   extern __shared__ uint4 cts[];
   constexpr int WARPS = THREADS / 32;
   constexpr uint32_t TILE = 32 * SPL;
-  constexpr int NOUT = 2 * SPL;  // (c, slot) pairs per lane
+  constexpr int NOUT = 2 * SPL * QN;  // (query, c, slot) outputs per lane
   typedef PtVec<SPL> V;
   const uint32_t N = P.N, L = P.L, d = A.d;
   const uint32_t tiles = N / TILE;
@@ -88,18 +93,20 @@ __global__ void __launch_bounds__(THREADS, MINB) mac_kernel(PrimeSet P, MacArgs 
     const uint32_t nk = (uint32_t)(run_end - w);
     const uint32_t st = (uint32_t)(u % tiles);
     const uint32_t j = (uint32_t)((u / tiles) % L);
-    const uint64_t b = u / ((uint64_t)tiles * L);
+    const uint64_t b = u / ((uint64_t)tiles * L) * QN;  // first query of the pass
+    const bool pair = QN == 2 && b + 1 < A.B;            // a second query exists
     const uint64_t q = P.q[j];
 
     __syncthreads();  // previous tile fully consumed
-    for (uint32_t e = threadIdx.x; e < d * 2 * 32; e += THREADS) {
-      const uint32_t l = e & 31, ci = e >> 5, c = ci & 1, i = ci >> 1;
-      const uint64_t* src = A.ct + ((((b * d + i) * 2 + c) * L + j) * N) + st * TILE + SPL * l;
+    for (uint32_t e = threadIdx.x; e < d * 2 * 32 * QN; e += THREADS) {
+      const uint32_t l = e & 31, ci = e >> 5, c = ci & 1, qi = (ci >> 1) % QN, i = (ci >> 1) / QN;
+      const uint64_t bq = b + (pair ? qi : 0);
+      const uint64_t* src = A.ct + ((((bq * d + i) * 2 + c) * L + j) * N) + st * TILE + SPL * l;
       uint64_t m[SPL];
 #pragma unroll
       for (int s = 0; s < SPL; ++s) m[s] = mul_shoup(src[s], P.r64[j], P.r64_shoup[j], q);
       if (SPL == 1) {
-        uint32_t* dst = reinterpret_cast<uint32_t*>(&cts[i * 32 + l]) + 2 * c;
+        uint32_t* dst = reinterpret_cast<uint32_t*>(&cts[(i * QN + qi) * 32 + l]) + 2 * c;
         dst[0] = (uint32_t)m[0] & kMask30;
         dst[1] = (uint32_t)(m[0] >> 30);
       } else {
@@ -136,9 +143,13 @@ __global__ void __launch_bounds__(THREADS, MINB) mac_kernel(PrimeSet P, MacArgs 
               const uint64_t y = V::get(pv[v], s);
               const uint32_t yl = (uint32_t)y & kMask30, yh = (uint32_t)(y >> 30);
               if (SPL == 1) {
-                const uint4 x = cts[ii * 32 + lane];
-                mac4(aL[0], aM1[0], aM2[0], aH[0], x.x, x.y, yl, yh);  // c0
-                mac4(aL[1], aM1[1], aM2[1], aH[1], x.z, x.w, yl, yh);  // c1
+#pragma unroll
+                for (int qi = 0; qi < QN; ++qi) {
+                  const uint4 x = cts[(ii * QN + qi) * 32 + lane];
+                  mac4(aL[2 * qi], aM1[2 * qi], aM2[2 * qi], aH[2 * qi], x.x, x.y, yl, yh);  // c0
+                  mac4(aL[2 * qi + 1], aM1[2 * qi + 1], aM2[2 * qi + 1], aH[2 * qi + 1], x.z, x.w, yl,
+                       yh);  // c1
+                }
               } else {
                 const uint4 x0 = cts[(ii * 2 + 0) * 32 + lane];
                 const uint4 x1 = cts[(ii * 2 + 1) * 32 + lane];
@@ -164,9 +175,14 @@ __global__ void __launch_bounds__(THREADS, MINB) mac_kernel(PrimeSet P, MacArgs 
       uint64_t* o0 = A.out + (((b * A.K + k) * 2 + 0) * L + j) * N + st * TILE + SPL * lane;
       uint64_t* o1 = A.out + (((b * A.K + k) * 2 + 1) * L + j) * N + st * TILE + SPL * lane;
       if (SPL == 1) {
-        // c0 at o[0], c1 at o[1] (layout of the SPL = 1 accumulators)
+        // query qi's c0 at r[2 qi], c1 at r[2 qi + 1]
         *o0 = r[0];
         *o1 = r[1];
+        if (QN == 2 && pair) {
+          const uint64_t step = A.K * 2 * L * N;  // the next query's outputs
+          o0[step] = r[2 % NOUT];
+          o1[step] = r[3 % NOUT];
+        }
       } else {
         *reinterpret_cast<ulonglong2*>(o0) = make_ulonglong2(r[0], r[1]);
         *reinterpret_cast<ulonglong2*>(o1) = make_ulonglong2(r[2 % NOUT], r[3 % NOUT]);
@@ -178,15 +194,18 @@ __global__ void __launch_bounds__(THREADS, MINB) mac_kernel(PrimeSet P, MacArgs 
 
 struct MacVariant {
   void (*fn)(PrimeSet, MacArgs);
-  int spl, threads, ctas_per_sm;
+  int spl, threads, ctas_per_sm, qn;
+  int pair_sibling;  // the variant run for calls with B >= 2 (-1: itself)
   const char* name;
 };
 
 const MacVariant kVariants[] = {
-    {mac_kernel<2, 8, 512, 1>, 2, 512, 1, "spl2_unr8_512x1"},
-    {mac_kernel<1, 16, 256, 3>, 1, 256, 3, "spl1_unr16_256x3"},
-    {mac_kernel<1, 8, 256, 3>, 1, 256, 3, "spl1_unr8_256x3"},
-    {mac_kernel<1, 16, 384, 2>, 1, 384, 2, "spl1_unr16_384x2"},
+    {mac_kernel<2, 8, 512, 1>, 2, 512, 1, 1, 4, "spl2_unr8_512x1"},
+    {mac_kernel<1, 16, 256, 3>, 1, 256, 3, 1, 5, "spl1_unr16_256x3"},
+    {mac_kernel<1, 8, 256, 3>, 1, 256, 3, 1, 5, "spl1_unr8_256x3"},
+    {mac_kernel<1, 16, 384, 2>, 1, 384, 2, 1, 4, "spl1_unr16_384x2"},
+    {mac_kernel<1, 8, 512, 1, 2>, 1, 512, 1, 2, -1, "pair_unr8_512x1"},
+    {mac_kernel<1, 8, 256, 2, 2>, 1, 256, 2, 2, -1, "pair_unr8_256x2"},
 };
 constexpr int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
 
@@ -199,6 +218,7 @@ cudaError_t launch_mac(const PrimeSet& P, const uint64_t* ct, const uint64_t* pt
                        uint32_t d, uint64_t K, uint64_t* out, int sms, int variant,
                        cudaStream_t st) {
   if (variant < 0 || variant >= kNumVariants) return cudaErrorInvalidValue;
+  if (B >= 2 && kVariants[variant].pair_sibling >= 0) variant = kVariants[variant].pair_sibling;
   const MacVariant& V = kVariants[variant];
   const uint32_t tile = 32u * V.spl;
   MacArgs A;
@@ -207,9 +227,10 @@ cudaError_t launch_mac(const PrimeSet& P, const uint64_t* ct, const uint64_t* pt
   A.out = out;
   A.K = K;
   A.d = d;
-  A.total = (uint64_t)B * P.L * (P.N / tile) * K;
+  A.B = B;
+  A.total = (uint64_t)((B + V.qn - 1) / V.qn) * P.L * (P.N / tile) * K;
   if (A.total == 0) return cudaSuccess;
-  const size_t smem = sizeof(uint4) * 32 * d * V.spl;
+  const size_t smem = sizeof(uint4) * 32 * d * V.spl * V.qn;
   // shared-memory opt-in, once per (variant, device)
   cudaError_t e = ensure_smem_attr((const void*)V.fn, smem > 48 * 1024 ? smem : 48 * 1024);
   if (e != cudaSuccess) return e;

@@ -211,3 +211,27 @@ def test_every_mac_variant_matches_oracle(cfg, n):
         assert np.array_equal(np_(acc)[0], want), names[v]
     best, ms = S.sanns_autotune_mac(ctx, db, ct_in, acc, reps=1)
     assert 0 <= best < len(names) and all(m > 0 for m in ms)
+
+
+@pytest.mark.parametrize("cfg,n,B", [((8192, 3, 60, 0, 7), 8192 * 2 + 5, 3), ((256, 2, 40, 0, 200), 700, 4),
+                                     ((256, 2, 40, 0, 224), 300, 5)])
+def test_multi_query_mac_matches_oracle(cfg, n, B):
+    # calls with B >= 2 run the pair variants (two queries per pass over the
+    # database, a lone last query for odd B), also at the largest d
+    ctx = S.sanns_ctx_create(*cfg)
+    O = oracle(*cfg)
+    d = cfg[4]
+    coords = inputs.uniform_coords(n, d, 8)
+    sk = S.sanns_keygen(ctx, 2)
+    q = inputs.uniform_coords(B, d, 9)
+    qids = cu(np.arange(B, dtype=np.uint64) + 11)
+    db = S.sanns_encode_db(ctx, cu(coords))
+    ct_in = S.sanns_encrypt_query(ctx, sk, cu(q), 3, qids)
+    pt, _ = O.encode_db(coords, None)
+    ct_np = np_(ct_in)
+    want = [O.mac(ct_np[b], pt) for b in range(B)]
+    for v in range(len(S.sanns_mac_variants())):
+        S.sanns_set_mac_variant(ctx, v)
+        acc = np_(S.sanns_distances_mac(ctx, db, ct_in))
+        for b in range(B):
+            assert np.array_equal(acc[b], want[b]), (S.sanns_mac_variants()[v], b)
