@@ -342,9 +342,17 @@ int sanns_db_export(const sanns_db* db, uint64_t k0, uint64_t k1, uint64_t* pt, 
   const sanns_ctx* ctx = db->ctx;
   const size_t per_block = (size_t)ctx->P.L * ctx->params.d * ctx->P.N;
   cudaStream_t st = as_stream(stream);
-  if (pt)
-    SANNS_CUDA(cudaMemcpyAsync(pt, db->d_pt + k0 * per_block, sizeof(uint64_t) * (k1 - k0) * per_block,
-                               cudaMemcpyDefault, st));
+  if (pt && k1 > k0) {
+    // canonical values from the split storage format, through a device copy
+    const uint64_t count = (k1 - k0) * per_block;
+    uint64_t* tmp = nullptr;
+    SANNS_CUDA(cudaMallocAsync(&tmp, sizeof(uint64_t) * count, st));
+    cudaError_t e = launch_join30(db->d_pt + k0 * per_block, tmp, count, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(pt, tmp, sizeof(uint64_t) * count, cudaMemcpyDefault, st);
+    cudaError_t e2 = cudaFreeAsync(tmp, st);
+    if (e != cudaSuccess) return cuda_fail(e, "db export");
+    if (e2 != cudaSuccess) return cuda_fail(e2, "cudaFreeAsync");
+  }
   if (norms)
     SANNS_CUDA(cudaMemcpyAsync(norms, db->d_norms + k0 * ctx->P.N,
                                sizeof(uint32_t) * (k1 - k0) * ctx->P.N, cudaMemcpyDefault, st));

@@ -902,7 +902,7 @@ __global__ void prepare_limbs_kernel(const uint64_t* __restrict__ pt, uint32_t K
   const uint32_t k = blockIdx.x, j = blockIdx.y, s0 = blockIdx.z * 32;
   for (uint32_t e = threadIdx.x; e < dpad * 32; e += blockDim.x) {
     const uint32_t i = e >> 5, s = e & 31;
-    tile[e] = i < d ? pt[(((uint64_t)k * L + j) * d + i) * N + s0 + s] : 0;
+    tile[e] = i < d ? join30(pt[(((uint64_t)k * L + j) * d + i) * N + s0 + s]) : 0;
   }
   __syncthreads();
   for (uint32_t e = threadIdx.x; e < dpad * 32; e += blockDim.x) {

@@ -212,6 +212,16 @@ __device__ __forceinline__ void draw_pair(const uint32_t blk[16], int u, uint64_
 // Shared-memory polynomials are stored padded, one spare word after every
 // 16, so that the stride-16 accesses of the radix-16 passes hit distinct banks.
 __host__ __device__ __forceinline__ uint32_t SP(uint32_t x) { return x + (x >> 4); }
+
+// Storage format of the encoded database (values below 2^60): bits 0..29 in
+// the low 32-bit word, bits 30..59 in the high word, so that the MAC reads
+// the 30-bit halves it multiplies without splitting them.
+__host__ __device__ __forceinline__ uint64_t split30(uint64_t y) {
+  return (y & ((1ull << 30) - 1)) | ((y >> 30) << 32);
+}
+__host__ __device__ __forceinline__ uint64_t join30(uint64_t v) {
+  return (v & 0xffffffffull) | ((v >> 32) << 30);
+}
 __host__ __device__ __forceinline__ uint32_t ntt_smem_words(uint32_t N) { return N + N / 16; }
 
 // Global <-> padded shared-memory copies of one polynomial by the whole block,

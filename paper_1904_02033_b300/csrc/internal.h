@@ -46,7 +46,7 @@ struct sanns_db {
   uint64_t n, K;
   uint64_t pos0;            // global position of local position 0 (shards), multiple of N
   bool slots;               // encoded with slot encoding (points in the CRT slots mod t)
-  uint64_t* d_pt;           // [K][L][d][N]
+  uint64_t* d_pt;           // [K][L][d][N], NTT form in the split30 format (common.cuh)
   uint32_t* d_norms;        // [K N]
   uint16_t* d_plimb;        // [L][N][K][8 dpad] fp16 digits (batched path), or NULL
   alignas(64) unsigned char limb_map[128];  // TMA descriptor of d_plimb
@@ -138,6 +138,7 @@ cudaError_t launch_gather(const PrimeSet& P, uint32_t d, const sanns_clusters* c
                           uint32_t* ids, int sms, const PrimeSet* PT, const uint64_t* pk,
                           const uint64_t* pks, uint32_t F, const PrivacyConsts& C, cudaStream_t st);
 cudaError_t launch_norms_slot(const PrimeSet& PT, uint32_t* norms, uint64_t K, cudaStream_t st);
+cudaError_t launch_join30(const uint64_t* src, uint64_t* dst, uint64_t count, cudaStream_t st);
 size_t batched_limb_bytes(uint32_t L, uint32_t N, uint64_t K, uint32_t d);
 cudaError_t launch_prepare_limbs(const PrimeSet& P, const uint64_t* pt, uint64_t K, uint32_t d,
                                  uint16_t* plimb, cudaStream_t st);

@@ -9,7 +9,9 @@
 // different k).
 //
 // Arithmetic: the query values are put in Montgomery form (x 2^64 mod q) and
-// both operands are split into 30-bit halves x = x1 2^30 + x0.  The four
+// both operands are split into 30-bit halves x = x1 2^30 + x0 (the database
+// is stored with its halves in separate 32-bit words, so only the query tile
+// is split, once per tile).  The four
 // partial products go into four 64-bit accumulators with one 32x32->64
 // multiply-add each; 16 products of (2^30 - 1)^2 fit in 64 bits, so every 16
 // dimensions the partials are folded into an exact 128-bit sum R.  R < d q^2
@@ -31,7 +33,7 @@ constexpr uint32_t kMask30 = (1u << 30) - 1;
 
 struct MacArgs {
   const uint64_t* ct;  // [B][d][2][L][N], NTT form
-  const uint64_t* pt;  // [K][L][d][N], NTT form
+  const uint64_t* pt;  // [K][L][d][N], NTT form, split30 format (30-bit halves in the two words)
   uint64_t* out;       // [B][K][2][L][N]
   uint64_t K;
   uint64_t total;      // ceil(B / QN) L (N / tile) K work items (tile, block)
@@ -141,7 +143,7 @@ __global__ void __launch_bounds__(THREADS, MINB) mac_kernel(PrimeSet P, MacArgs 
 #pragma unroll
             for (int s = 0; s < SPL; ++s) {
               const uint64_t y = V::get(pv[v], s);
-              const uint32_t yl = (uint32_t)y & kMask30, yh = (uint32_t)(y >> 30);
+              const uint32_t yl = (uint32_t)y, yh = (uint32_t)(y >> 32);  // stored split
               if (SPL == 1) {
 #pragma unroll
                 for (int qi = 0; qi < QN; ++qi) {

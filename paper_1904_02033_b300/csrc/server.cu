@@ -59,7 +59,7 @@ __global__ void __launch_bounds__(512) encode_kernel(PrimeSet P, PrimeSet PT, in
     ntt_forward_smem(sa, P, j);
     __syncthreads();
     uint64_t* dst = pt + ((k * P.L + j) * d + i) * N;
-    for (uint32_t x = threadIdx.x; x < N; x += blockDim.x) dst[x] = sa[SP(x)];
+    for (uint32_t x = threadIdx.x; x < N; x += blockDim.x) dst[x] = split30(sa[SP(x)]);
     __syncthreads();
   }
 }
@@ -486,6 +486,17 @@ cudaError_t launch_encode(const PrimeSet& P, const PrimeSet* PT, const uint8_t* 
   e = cudaFuncSetAttribute(norms_slot_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   norms_slot_kernel<<<(unsigned)K, ntt_threads(P.N), smem, st>>>(*PT, norms);
+  return cudaGetLastError();
+}
+
+__global__ void join30_kernel(const uint64_t* __restrict__ src, uint64_t* __restrict__ dst, uint64_t count) {
+  const uint64_t e = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+  if (e < count) dst[e] = join30(src[e]);
+}
+
+cudaError_t launch_join30(const uint64_t* src, uint64_t* dst, uint64_t count, cudaStream_t st) {
+  if (count == 0) return cudaSuccess;
+  join30_kernel<<<(unsigned)((count + 255) / 256), 256, 0, st>>>(src, dst, count);
   return cudaGetLastError();
 }
 
