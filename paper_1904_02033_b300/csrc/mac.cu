@@ -41,12 +41,24 @@ struct MacArgs {
   uint32_t B;
 };
 
+// acc += a b for a 64-bit sum that cannot overflow: the low product word
+// added with a carry out, the high word with that carry in.
+__device__ __forceinline__ void mad_acc(uint64_t& acc, uint32_t a, uint32_t b) {
+  asm("{\n\t.reg .u32 lo, hi;\n\t"
+      "mov.b64 {lo, hi}, %0;\n\t"
+      "mad.lo.cc.u32 lo, %1, %2, lo;\n\t"
+      "madc.hi.u32 hi, %1, %2, hi;\n\t"
+      "mov.b64 %0, {lo, hi};\n\t}"
+      : "+l"(acc)
+      : "r"(a), "r"(b));
+}
+
 __device__ __forceinline__ void mac4(uint64_t& aL, uint64_t& aM1, uint64_t& aM2, uint64_t& aH,
                                      uint32_t xl, uint32_t xh, uint32_t yl, uint32_t yh) {
-  aL += (uint64_t)xl * yl;
-  aM1 += (uint64_t)xh * yl;
-  aM2 += (uint64_t)xl * yh;
-  aH += (uint64_t)xh * yh;
+  mad_acc(aL, xl, yl);
+  mad_acc(aM1, xh, yl);
+  mad_acc(aM2, xl, yh);
+  mad_acc(aH, xh, yh);
 }
 
 template <int SPL>
