@@ -72,20 +72,10 @@ __device__ __forceinline__ uint64_t csub(uint64_t x, uint64_t m) { return x >= m
 // value), so the estimate is at most 2 below it and the remainder below 4q.
 __device__ __forceinline__ uint64_t mul_shoup_lazy4(uint64_t y, uint64_t w, uint64_t w_shoup,
                                                     uint64_t q) {
-  // the quotient estimate y1 s1 + hi(y0 s1) + hi(y1 s0) with explicit carries
-  uint64_t qt;
-  asm("{\n\t.reg .u32 y0, y1, s0, s1, t0, t1, l, h;\n\t"
-      "mov.b64 {y0, y1}, %1;\n\t"
-      "mov.b64 {s0, s1}, %2;\n\t"
-      "mul.hi.u32 t0, y0, s1;\n\t"
-      "mul.hi.u32 t1, y1, s0;\n\t"
-      "mad.lo.cc.u32 l, y1, s1, t0;\n\t"
-      "madc.hi.u32 h, y1, s1, 0;\n\t"
-      "add.cc.u32 l, l, t1;\n\t"
-      "addc.u32 h, h, 0;\n\t"
-      "mov.b64 %0, {l, h};\n\t}"
-      : "=l"(qt)
-      : "l"(y), "l"(w_shoup));
+  const uint32_t y0 = (uint32_t)y, y1 = (uint32_t)(y >> 32);
+  const uint32_t s0 = (uint32_t)w_shoup, s1 = (uint32_t)(w_shoup >> 32);
+  uint64_t qt = (uint64_t)y1 * s1 + __umulhi(y0, s1);
+  qt += __umulhi(y1, s0);
   return w * y - qt * q;
 }
 
