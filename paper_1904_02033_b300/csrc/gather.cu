@@ -274,8 +274,18 @@ gather_kernel(PrimeSet P, uint32_t d, uint64_t W, uint32_t S, uint32_t ds,
       const uint64_t* pkc = O.pk ? O.pk + ((size_t)c * L + j) * N : nullptr;
       const uint64_t* pksc = O.pk ? O.pks + ((size_t)c * L + j) * N : nullptr;
       for (uint32_t x = threadIdx.x; x < N; x += blockDim.x) {
+        // eight slices' partials requested before any is added (one query's
+        // gather spreads over up to d slices)
         uint64_t v = 0;
-        for (uint32_t s2 = 0; s2 < S; ++s2) v = add_mod(v, __ldcg(all + ((uint64_t)s2 * 2 + c) * N + x), q);
+        uint32_t s2 = 0;
+        for (; s2 + 8 <= S; s2 += 8) {
+          uint64_t t8[8];
+#pragma unroll
+          for (int r = 0; r < 8; ++r) t8[r] = __ldcg(all + ((uint64_t)(s2 + r) * 2 + c) * N + x);
+#pragma unroll
+          for (int r = 0; r < 8; ++r) v = add_mod(v, t8[r], q);
+        }
+        for (; s2 < S; ++s2) v = add_mod(v, __ldcg(all + ((uint64_t)s2 * 2 + c) * N + x), q);
         if (pkc) v = add_mod(v, mul_shoup(poly[SP(x)], pkc[x], pksc[x], q), q);
         a[SP(x)] = v;
       }
@@ -363,9 +373,13 @@ cudaError_t launch_gather(const PrimeSet& P, uint32_t d, const sanns_clusters* c
   auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
   const size_t o_items = 0, o_qs = up(sz_items), o_seg = o_qs + up(sz_qs), o_pr = o_seg + up(sz_seg);
   // dimension slices per (item, prime): about four units per multiprocessor
-  // in all, at least one dimension per slice
+  // in all, at least one dimension per slice, and at most kMaxSlices: the
+  // finishing block reads every slice's partial (2 N words each), so more
+  // slices than that cost more in the finish than they save in the MAC
+  constexpr uint64_t kMaxSlices = 32;
   const uint64_t nsm = (uint64_t)(sms > 0 ? sms : 148);
-  const uint64_t want = (4 * nsm + W * P.L - 1) / (W * P.L);
+  uint64_t want = (4 * nsm + W * P.L - 1) / (W * P.L);
+  if (want > kMaxSlices) want = kMaxSlices;
   const uint32_t S0 = (uint32_t)(want < d ? want : d);
   const uint32_t ds = (d + S0 - 1) / S0;
   const uint32_t S = (d + ds - 1) / ds;
