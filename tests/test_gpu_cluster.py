@@ -82,3 +82,30 @@ def test_clustering_accuracy_against_brute_force():
         assert np.all(got[b] >= 0) and len(set(got[b].tolist())) == k
         acc += np.sum(bd[got[b]] <= kth) / k
     assert acc / B >= 0.9, acc / B
+
+
+@pytest.mark.parametrize("F,slots", [(100, False), (0, True), (148, True)])
+def test_clustering_query_with_privacy_and_slots(F, slots):
+    # circuit privacy and slot encoding change the ciphertexts, not the
+    # reconstructed distances: the returned ids are the oracle's
+    n, d, B = 20000, 32, 4
+    cfg = (8192, 3, 60, 0, 32)
+    coords = inputs.mixture_coords(n, d, 16, 20.0, 5)
+    groups = cluster.balanced_clustering(torch.from_numpy(coords), 300, 0.3, iters=8, seed=1)
+    kept, stash = cluster.split_stash(groups, 2000)
+    lay = cluster.make_layout(kept, stash, d, seed=7)
+    ctx = S.sanns_ctx_create(*cfg)
+    S.sanns_set_encoding(ctx, slots)
+    sk = S.sanns_keygen(ctx, 13)
+    if F:
+        S.sanns_set_circuit_privacy(ctx, S.sanns_public_key(ctx, sk, 14), F)
+    srv = cluster.ClusteringServer(ctx, torch.from_numpy(coords).cuda(), lay)
+    T = len(lay.group_offsets) - 1
+    prm = cluster.Params(k=10, u=tuple(([8, 4] + [2] * T)[:T]), l=tuple(([24, 12] + [4] * T)[:T]),
+                         l_s=300, r_c=1, r_p=2)
+    q = inputs.mixture_coords(B, d, 16, 20.0, 9, means_seed=5)
+    qids = torch.from_numpy(np.arange(B, dtype=np.uint64) + 50).cuda()
+    got = cluster.query(srv, sk, torch.from_numpy(q).cuda(), qids, prm)
+    t = ctx.query()["t"]
+    for b in range(B):
+        assert np.array_equal(got[b], _oracle_ids(coords, lay, q[b], prm, t)), b
