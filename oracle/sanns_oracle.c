@@ -16,7 +16,7 @@
  *     coordinates, f_k = sum_i CMult(c_i, p_ik) + r[kN:(k+1)N], decryption.
  *   - Sec. 2.3 (AHE): BFV [FV12]; R_t = Z_t[x]/(x^N + 1).
  * The BFV conventions the paper leaves to SEAL (NTT order, RNG, sampling,
- * Delta) are the readings written down in the design doc; each function states the
+ * Delta) are fixed here as readings of the paper; each function states the
  * one it implements.
  *
  * Arithmetic: all residues are canonical uint64 in [0, q); every product is a
