@@ -120,6 +120,23 @@ def _roofline_bytes(W) -> dict:
     return {"pt": pt, "ct": ct, "out": out, "total": pt + ct + out, "K": K}
 
 
+# DRAM bytes of one mac_kernel launch (spl2_unr8_512x1) from the ncu capture
+# of the small case n = 200,000 (K = 25 blocks, d = 128, N = 8192, L = 3;
+# profiles/mac_kernel_linear_scan_n200k.md): dram__bytes_read.sum +
+# dram__bytes_write.sum.  The query ciphertext is read once per launch; the
+# rest grows with the blocks, so a full launch's traffic is that rest scaled
+# by the block count plus the query ciphertext.
+MAC_CAPTURE = dict(K=25, d=128, N=8192, L=3, dram_bytes=680_013_312 + 3_469_568)
+
+
+def _mac_traffic(rb: dict, W) -> float | None:
+    C = MAC_CAPTURE
+    if (W["d"], W["N"], W["L"]) != (C["d"], C["N"], C["L"]):
+        return None
+    ct = C["d"] * 2 * C["L"] * C["N"] * 8
+    return (C["dram_bytes"] - ct) * rb["K"] / C["K"] + ct
+
+
 def run_gpu(args) -> None:
     import torch
 
@@ -417,7 +434,9 @@ def run_gpu(args) -> None:
             "roofline": {"kernel": "mac_kernel (K2 ct x pt MAC)", "bound": "hbm",
                          "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "peak_source": peak_kind,
-                         "traffic": None, "algorithmic_bytes": rb["total"],
+                         "traffic": _mac_traffic(rb, W),
+                         "traffic_source": "ncu capture at n = 200,000 scaled by blocks",
+                         "algorithmic_bytes": rb["total"],
                          "launch_ms": mac_avg},
             "e2e": {"value": world * n / (e2e_ms * 1e-3), "unit": UNIT,
                     "h2d_bytes_per_step": d * 2 * L * N * 8,
