@@ -252,6 +252,16 @@ int sanns_distances_batched(sanns_ctx *ctx, const sanns_db *db, const uint64_t *
 int sanns_distances_batched_mac(sanns_ctx *ctx, const sanns_db *db, const uint64_t *ct_in_dev,
                                 uint32_t B, uint64_t *ct_out_dev, void *stream);
 int sanns_device_status(sanns_ctx *ctx, void *stream);
+/*
+ * Self-test of the failure path of the bounded device-side waits (no
+ * counterpart in the paper): one thread waits, with the batched kernel's own
+ * bounded-wait routine, on a shared-memory barrier that nothing completes;
+ * after limit_ms (1 .. 1000) the wait gives up, raises the context's device
+ * error word and the kernel returns, so the next sanns_device_status returns
+ * SANNS_ETIMEOUT (and clears it) and the context stays usable.  It faults
+ * nothing and always ends.  Asynchronous on stream.
+ */
+int sanns_selftest_wait_timeout(sanns_ctx *ctx, uint32_t limit_ms, void *stream);
 /* Tuning of the batched kernel: back-off sleep (ns, <= 100000) of the TMA
  * thread, the MMA thread, the digit producers and the epilogue when their
  * barrier is not ready yet; how many of its own work units ahead each CTA

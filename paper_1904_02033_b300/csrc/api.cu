@@ -814,6 +814,15 @@ int sanns_autotune_batched(sanns_ctx* ctx, const sanns_db* db, const uint64_t* c
   return best;
 }
 
+int sanns_selftest_wait_timeout(sanns_ctx* ctx, uint32_t limit_ms, void* stream) {
+  if (!ctx) return fail(SANNS_EINVAL, "ctx is NULL");
+  if (limit_ms < 1 || limit_ms > 1000) return fail(SANNS_EINVAL, "limit_ms must be in [1, 1000]");
+  int rc = check_device(ctx);
+  if (rc) return rc;
+  SANNS_CUDA(launch_wait_selftest(ctx->d_err, limit_ms, ctx->device, as_stream(stream)));
+  return SANNS_OK;
+}
+
 int sanns_device_status(sanns_ctx* ctx, void* stream) {
   if (!ctx) return fail(SANNS_EINVAL, "ctx is NULL");
   int rc = check_device(ctx);

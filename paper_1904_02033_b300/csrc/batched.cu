@@ -125,23 +125,40 @@ __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
   return ok != 0;
 }
 
-// Bounded wait; false when the CTA is aborting or the wait timed out (which
-// also raises the abort flag and the device error word).
+// Bounded wait; false when the CTA is aborting or the wait timed out after
+// limit_cycles (which also raises the abort flag and the device error word).
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag,
-                                          int* err, uint32_t sleep_ns = 0) {
+                                          int* err, uint32_t sleep_ns = 0,
+                                          unsigned long long limit_cycles = kWaitCycles) {
   const unsigned long long t0 = clock64();
   for (uint32_t it = 0;; ++it) {
     if (mbar_try(bar, parity)) return true;
     if (sleep_ns && it > 2) __nanosleep(sleep_ns);
     if ((it & 255) == 255) {
       if (*abort_flag) return false;
-      if (clock64() - t0 > kWaitCycles) {
+      if (clock64() - t0 > limit_cycles) {
         *abort_flag = 1;
         atomicExch(err, SANNS_ETIMEOUT);
         return false;
       }
     }
   }
+}
+
+// Self-test of the time-out path: one thread waits, through mbar_wait, on a
+// barrier that nothing arrives on, so the wait gives up after limit_cycles,
+// raises the device error word and the kernel returns.
+__global__ void wait_selftest_kernel(int* err, unsigned long long limit_cycles) {
+  __shared__ alignas(8) uint64_t bar;
+  __shared__ int abort_flag;
+  if (threadIdx.x == 0) {
+    mbar_init(smem_u32(&bar), 1);
+    abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) mbar_wait(smem_u32(&bar), 0, &abort_flag, err, 1000, limit_cycles);
+  __syncthreads();
 }
 
 __device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, int x, int y,
@@ -1004,6 +1021,15 @@ cudaError_t get_encode(PFN_cuTensorMapEncodeTiled_v12000* out) {
 size_t batched_limb_bytes(uint32_t L, uint32_t N, uint64_t K, uint32_t d) {
   const uint32_t dpad = (d + 7) / 8 * 8;
   return (size_t)L * N * K * 8ull * dpad * 2;
+}
+
+cudaError_t launch_wait_selftest(int* err, uint32_t limit_ms, int device, cudaStream_t st) {
+  int khz = 0;
+  cudaError_t e = cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, device);
+  if (e != cudaSuccess) return e;
+  const unsigned long long cycles = (unsigned long long)limit_ms * (unsigned long long)(khz > 0 ? khz : 2000000);
+  wait_selftest_kernel<<<1, 32, 0, st>>>(err, cycles);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_prepare_limbs(const PrimeSet& P, const uint64_t* pt, uint64_t K, uint32_t d,

@@ -64,6 +64,7 @@ _SIGS = {
     "sanns_autotune_batched": ([_VP, _VP, _VP, C.c_uint32, _VP, C.c_int, _VP, _VP], C.c_int),
     "sanns_public_key": ([_VP, _VP, C.c_uint64, _VP, _VP], C.c_int),
     "sanns_set_encoding": ([_VP, C.c_int], C.c_int),
+    "sanns_selftest_wait_timeout": ([_VP, C.c_uint32, _VP], C.c_int),
     "sanns_set_response_form": ([_VP, C.c_int], C.c_int),
     "sanns_topk": ([_VP, _VP, _VP, C.c_uint32, C.c_uint64, C.c_uint32, C.c_uint64, C.c_uint32, _VP,
                     _VP, _VP], C.c_int),
@@ -381,6 +382,12 @@ def sanns_autotune_mac(ctx: Context, db: Database, ct_in: torch.Tensor, ct_out: 
     if rc < 0:
         _check(rc)
     return rc, list(ms)
+
+
+def sanns_selftest_wait_timeout(ctx: Context, limit_ms: int = 20, stream=None):
+    """Runs one bounded device-side wait that must time out after limit_ms;
+    the next sanns_device_status then raises SannsError with SANNS_ETIMEOUT."""
+    _check(load().sanns_selftest_wait_timeout(ctx.handle, limit_ms, _stream(stream)))
 
 
 def sanns_set_encoding(ctx: Context, slots: bool):

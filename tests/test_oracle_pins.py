@@ -521,3 +521,21 @@ def test_slot_encoding_shares_reconstruct_brute_force(cfg, n):
     # decrypting slot-encoded responses as coefficients does not give the distances
     cli_coef = O.decrypt_shares(out, s, qv, n)
     assert not np.array_equal((cli_coef.astype(np.int64) + srv) % O.t, brute)
+
+
+def test_corrupted_response_coefficient_breaks_exactly_its_share():
+    # a flipped residue bit of c0 at coefficient x changes the decrypted
+    # plaintext at x only: the share reconstruction catches it there
+    O = Oracle(256, 2, 40, 0, 5)
+    n, x = 600, 137
+    coords = inputs.uniform_coords(n, 5, 11)
+    qv = inputs.uniform_coords(1, 5, 12)[0]
+    s, s_hat = O.keygen(11)
+    ct = O.encrypt(s_hat, qv, 13, 11)
+    out, srv = O.distances(ct, coords, None, 14, 11)
+    brute = np.sum((coords.astype(np.int64) - qv.astype(np.int64)) ** 2, axis=1)
+    assert np.array_equal((O.decrypt_shares(out, s, qv, n).astype(np.int64) + srv) % O.t, brute)
+    bad = out.copy()
+    bad[0, 0, 0, x] ^= np.uint64(1 << 30)
+    rec = (O.decrypt_shares(bad, s, qv, n).astype(np.int64) + srv) % O.t
+    assert np.flatnonzero(rec != brute).tolist() == [x]
