@@ -177,9 +177,11 @@ __device__ void gather_finish(uint64_t* a, const PrimeSet& P, uint32_t j, uint32
 }
 
 // Persistent: block k takes units k, k + grid, ..; unit u = (w L + j) S + s.
-// Shared memory holds the polynomial being transformed and the unit's two
-// accumulators (c0, c1).
-__global__ void __launch_bounds__(512, 1)
+// Shared memory holds only the polynomial being transformed; the unit's two
+// accumulators (c0, c1) are its partial-sum slab part[u] in global memory
+// (L2-resident), which each thread reads back and updates only at its own
+// slots.  So three blocks fit on a multiprocessor.
+__global__ void __launch_bounds__(256, 3)
 gather_kernel(PrimeSet P, uint32_t d, uint64_t W, uint32_t S, uint32_t ds,
               const GatherItem* __restrict__ items, const GatherQuery* __restrict__ qs,
               const uint8_t* __restrict__ gco, const uint32_t* __restrict__ gnorm,
@@ -189,10 +191,7 @@ gather_kernel(PrimeSet P, uint32_t d, uint64_t W, uint32_t S, uint32_t ds,
   extern __shared__ uint64_t smem[];
   __shared__ uint32_t ticket;
   const uint32_t N = P.N, L = P.L;
-  const uint32_t PW = ntt_smem_words(N);
   uint64_t* poly = smem;
-  uint64_t* acc0 = smem + PW;
-  uint64_t* acc1 = smem + 2 * PW;
   const uint64_t units = W * L * S;
   for (uint64_t u = blockIdx.x; u < units; u += gridDim.x) {
     const uint32_t sl = (uint32_t)(u % S);
@@ -203,8 +202,7 @@ gather_kernel(PrimeSet P, uint32_t d, uint64_t W, uint32_t S, uint32_t ds,
     const uint8_t* g = gco + w * (uint64_t)d * N;
     const uint64_t q = P.q[j], qn = P.q_neg_inv[j];
     const uint32_t i0 = sl * ds, i1 = i0 + ds < d ? i0 + ds : d;
-    __syncthreads();
-    for (uint32_t x = threadIdx.x; x < N; x += blockDim.x) acc0[SP(x)] = acc1[SP(x)] = 0;
+    uint64_t* mine = part + u * 2 * N;  // this unit's accumulators: c0 at [0, N), c1 at [N, 2N)
     for (uint32_t i = i0; i < i1; ++i) {
       __syncthreads();
       for (uint32_t x = threadIdx.x; x < N; x += blockDim.x) poly[SP(x)] = g[(uint64_t)i * N + x];
@@ -217,32 +215,30 @@ gather_kernel(PrimeSet P, uint32_t d, uint64_t W, uint32_t S, uint32_t ds,
       __syncthreads();
       const uint64_t* c0 = ct_in + ((((uint64_t)it.b * d + i) * 2 + 0) * L + j) * N;
       const uint64_t* c1 = ct_in + ((((uint64_t)it.b * d + i) * 2 + 1) * L + j) * N;
-      // four slots' ciphertext words requested before any is used
+      const bool first = i == i0;
+      // four slots' ciphertext words and accumulators requested before any is used
       for (uint32_t x0 = threadIdx.x; x0 < N; x0 += 4 * blockDim.x) {
-        uint64_t v0[4], v1[4];
+        uint64_t v0[4], v1[4], a0[4], a1[4];
 #pragma unroll
         for (int r = 0; r < 4; ++r) {
           const uint32_t x = x0 + r * blockDim.x;
-          v0[r] = x < N ? __ldg(c0 + x) : 0;
-          v1[r] = x < N ? __ldg(c1 + x) : 0;
+          const bool in = x < N;
+          v0[r] = in ? __ldg(c0 + x) : 0;
+          v1[r] = in ? __ldg(c1 + x) : 0;
+          a0[r] = in && !first ? __ldcg(mine + x) : 0;
+          a1[r] = in && !first ? __ldcg(mine + N + x) : 0;
         }
 #pragma unroll
         for (int r = 0; r < 4; ++r) {
           const uint32_t x = x0 + r * blockDim.x;
           if (x >= N) break;
           const uint64_t pm = mul_shoup(poly[SP(x)], P.r64[j], P.r64_shoup[j], q);
-          acc0[SP(x)] = add_mod(acc0[SP(x)], mont_mul(v0[r], pm, q, qn), q);
-          acc1[SP(x)] = add_mod(acc1[SP(x)], mont_mul(v1[r], pm, q, qn), q);
+          mine[x] = add_mod(a0[r], mont_mul(v0[r], pm, q, qn), q);
+          mine[N + x] = add_mod(a1[r], mont_mul(v1[r], pm, q, qn), q);
         }
       }
     }
-    __syncthreads();
     // publish the partial, then take a ticket; the last slice finishes
-    uint64_t* mine = part + u * 2 * N;
-    for (uint32_t x = threadIdx.x; x < N; x += blockDim.x) {
-      mine[x] = acc0[SP(x)];
-      mine[N + x] = acc1[SP(x)];
-    }
     __threadfence();
     __syncthreads();
     if (threadIdx.x == 0) ticket = atomicAdd(tickets + wj, 1u);
@@ -251,9 +247,11 @@ gather_kernel(PrimeSet P, uint32_t d, uint64_t W, uint32_t S, uint32_t ds,
     __threadfence();
     const GatherQuery Q = qs[it.b];
     const uint64_t qid = qids[it.b];
-    const uint64_t* all = part + wj * S * 2 * N;
+    uint64_t* all = part + wj * S * 2 * N;
     if (O.pk) {
-      // re-randomisation: u ternary at the list positions, transformed
+      // re-randomisation: u ternary at the list positions, transformed, and
+      // pk_c * u_hat added into slice 0's partial (which only this block reads)
+      __syncthreads();
       for (uint32_t u4 = threadIdx.x; u4 < N / 4; u4 += blockDim.x) {
         uint32_t blk[16];
         chacha20_block(mask_seed, kPurposeU, qid, (uint32_t)(((uint64_t)it.kb * N) / 4 + u4), blk);
@@ -268,14 +266,18 @@ gather_kernel(PrimeSet P, uint32_t d, uint64_t W, uint32_t S, uint32_t ds,
       __syncthreads();
       ntt_forward_smem(poly, P, (int)j);
       __syncthreads();
+      for (uint32_t c = 0; c < 2; ++c) {
+        const uint64_t* pkc = O.pk + ((size_t)c * L + j) * N;
+        const uint64_t* pksc = O.pks + ((size_t)c * L + j) * N;
+        for (uint32_t x = threadIdx.x; x < N; x += blockDim.x)
+          all[(uint64_t)c * N + x] = add_mod(__ldcg(all + (uint64_t)c * N + x),
+                                             mul_shoup(poly[SP(x)], pkc[x], pksc[x], q), q);
+      }
     }
     for (uint32_t c = 0; c < 2; ++c) {
-      uint64_t* a = c == 0 ? acc0 : acc1;
-      const uint64_t* pkc = O.pk ? O.pk + ((size_t)c * L + j) * N : nullptr;
-      const uint64_t* pksc = O.pk ? O.pks + ((size_t)c * L + j) * N : nullptr;
+      __syncthreads();  // the polynomial buffer is free again
       for (uint32_t x = threadIdx.x; x < N; x += blockDim.x) {
-        // eight slices' partials requested before any is added (one query's
-        // gather spreads over up to d slices)
+        // eight slices' partials requested before any is added
         uint64_t v = 0;
         uint32_t s2 = 0;
         for (; s2 + 8 <= S; s2 += 8) {
@@ -286,10 +288,9 @@ gather_kernel(PrimeSet P, uint32_t d, uint64_t W, uint32_t S, uint32_t ds,
           for (int r = 0; r < 8; ++r) v = add_mod(v, t8[r], q);
         }
         for (; s2 < S; ++s2) v = add_mod(v, __ldcg(all + ((uint64_t)s2 * 2 + c) * N + x), q);
-        if (pkc) v = add_mod(v, mul_shoup(poly[SP(x)], pkc[x], pksc[x], q), q);
-        a[SP(x)] = v;
+        poly[SP(x)] = v;
       }
-      gather_finish(a, P, j, c, w, it, Q, gnorm, mask_seed, qid, O, ct_out, srv_share);
+      gather_finish(poly, P, j, c, w, it, Q, gnorm, mask_seed, qid, O, ct_out, srv_share);
     }
   }
 }
@@ -336,7 +337,7 @@ cudaError_t launch_check_indices(const uint32_t* idx, uint64_t m, uint64_t bound
   return cudaGetLastError();
 }
 
-int gather_threads(uint32_t N) { return N >= 1024 ? 512 : (int)(N / 2); }
+int gather_threads(uint32_t N) { return N >= 512 ? 256 : (int)(N / 2); }
 
 cudaError_t launch_gather(const PrimeSet& P, uint32_t d, const sanns_clusters* cl,
                           const uint64_t* ct_in, uint32_t B, const uint32_t* probes_host,
@@ -424,9 +425,10 @@ cudaError_t launch_gather(const PrimeSet& P, uint32_t d, const sanns_clusters* c
   if (e == cudaSuccess) e = cudaMemsetAsync(tickets, 0, sizeof(uint32_t) * (size_t)W * P.L, st);
   if (e == cudaSuccess) {
     const int th = gather_threads(N);
-    const size_t smem = sizeof(uint64_t) * 3 * ntt_smem_words(N);
+    const size_t smem = sizeof(uint64_t) * ntt_smem_words(N);
     const uint64_t units = W * P.L * S;
-    const unsigned grid = (unsigned)(units < nsm ? units : nsm);
+    const uint64_t slots = 3 * nsm;  // three blocks per multiprocessor
+    const unsigned grid = (unsigned)(units < slots ? units : slots);
     e = cudaFuncSetAttribute(gather_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e == cudaSuccess) {
       gather_kernel<<<grid, th, smem, st>>>(P, d, W, S, ds, d_items, d_qs, scratch + o_gco,
