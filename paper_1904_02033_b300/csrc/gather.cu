@@ -12,11 +12,12 @@
 //   pack        one thread per gathered position: finds the probe segment by
 //               binary search, copies the point's d bytes into a
 //               coordinate-major tile [item][i][x] and its ||p||^2;
-//   persistent  one block per multiprocessor walks the units (work item,
+//   persistent  three blocks per multiprocessor walk the units (work item,
 //               prime j, slice of the dimensions) of every query -- uneven
 //               per-query counts included: the slice's encodings (NTT of the
 //               coordinate polynomials) times the query's c0 and c1, summed
-//               mod q_j into a partial accumulator.  The block that completes
+//               mod q_j into the unit's partial-sum slab in global memory
+//               (at most 32 slices per item and prime).  The block that completes
 //               the last slice of an (item, prime) (a ticket counter after a
 //               memory fence; nobody waits) sums the partials mod q_j (the
 //               order does not matter, so the result is exact), runs the
