@@ -137,6 +137,61 @@ def _mac_traffic(rb: dict, W) -> float | None:
     return (C["dram_bytes"] - ct) * rb["K"] / C["K"] + ct
 
 
+def _ntt_report(polys: int, N: int, ms: float, what: str) -> dict:
+    """The epilogue's transforms (one inverse NTT per block, component and
+    prime, with the mask): polynomials per second and the fraction of the HBM
+    copy peak that 16 N bytes per polynomial (read and written once) would
+    use.  The transforms are bound by the integer multiply pipe instead
+    (profiles/intt_mask_kernel_linear_scan_n1M.md)."""
+    peak, _ = _peaks()
+    gbs = 16.0 * N * polys / (ms * 1e-3) / 1e9
+    return {"what": what, "polys": polys, "ms": ms, "polys_per_s": polys / (ms * 1e-3),
+            "hbm_gbs": gbs, "hbm_frac": gbs / peak, "bound": "integer multiply pipe"}
+
+
+def run_small_section() -> dict:
+    """Configuration 1: n = 4096, d = 32 uniform uint8, N = 4096, two 54-bit
+    primes, one query; latency-bound, so p50/p99 of the distance step, and
+    the exact top-10 checked against brute force."""
+    import numpy as np
+    import torch
+
+    from paper_1904_02033_b300 import inputs
+    from paper_1904_02033_b300 import sanns as S
+
+    n, d = 4096, 32
+    ctx = S.sanns_ctx_create(4096, 2, 54, 0, d)
+    coords = inputs.uniform_coords(n, d, 0)
+    perm = inputs.permutation(n, 0)
+    q = inputs.uniform_coords(1, d, 0)
+    qids = torch.from_numpy(np.array([0], dtype=np.uint64)).cuda()
+    sk = S.sanns_keygen(ctx, 0)
+    db = S.sanns_encode_db(ctx, torch.from_numpy(coords).cuda(), torch.from_numpy(perm).cuda())
+    ct = S.sanns_encrypt_query(ctx, sk, torch.from_numpy(q).cuda(), 0, qids)
+    out, srv = S.sanns_distances(ctx, db, ct, 0, qids)
+    st = torch.cuda.current_stream()
+    reps = 500
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+    for _ in range(10):
+        S.sanns_distances(ctx, db, ct, 0, qids, out, srv)
+    torch.cuda.synchronize()
+    for a, b in ev:
+        a.record(st)
+        S.sanns_distances(ctx, db, ct, 0, qids, out, srv)
+        b.record(st)
+    torch.cuda.synchronize()
+    lat = sorted(a.elapsed_time(b) for a, b in ev)
+    cli = S.sanns_decrypt_shares(ctx, sk, out, n, torch.from_numpy(q).cuda())
+    dist_k, pos_k = S.sanns_topk(ctx, cli, srv, 10)
+    brute = np.sum((coords[perm].astype(np.int64) - q[0].astype(np.int64)) ** 2, axis=1)
+    exact = sorted(brute.tolist())[:10] == dist_k.cpu().numpy()[0].tolist()
+    return {"workload": "configuration 1: n=4,096 d=32 uniform uint8; BFV N=4096, two 54-bit primes; "
+                        "one query per step",
+            "latency_ms": {"p50": lat[len(lat) // 2], "p99": lat[int(0.99 * (len(lat) - 1))]},
+            "qp_per_s": n / (lat[len(lat) // 2] * 1e-3), "steps": reps,
+            "exact_top10_equals_brute_force": bool(exact)}
+
+
 def run_gpu(args) -> None:
     import torch
 
@@ -211,6 +266,8 @@ def run_gpu(args) -> None:
     lat = sorted(starts[s].elapsed_time(ends[s]) for s in timed)
     mac_ms = [starts[s].elapsed_time(mac_end[s]) for s in timed]
     mac_avg = sum(mac_ms) / len(mac_ms)
+    fin_ms = [mac_end[s].elapsed_time(ends[s]) for s in timed]
+    fin_avg = sum(fin_ms) / len(fin_ms)
 
     # the same steps replayed from one captured CUDA graph (MAC, mask draw and
     # INTT + mask of G consecutive queries as graph nodes)
@@ -402,13 +459,14 @@ def run_gpu(args) -> None:
     cpu = None
     if rank == 0:
         cpu = cpu_baseline(quick=args.quick_cpu)
-    batched = cluster = serving = alg4 = None
+    batched = cluster = serving = alg4 = small = None
     if rank == 0 and not args.no_batched:
         del ct_all
         torch.cuda.empty_cache()
         batched = run_batched_section(quick=args.quick_batched)
         torch.cuda.empty_cache()
     if rank == 0 and not args.no_extra:
+        small = run_small_section()
         cluster = run_cluster_section()
         torch.cuda.empty_cache()
         alg4 = run_alg4_section()
@@ -446,6 +504,10 @@ def run_gpu(args) -> None:
                     "timing": "host wall clock over pipelined steps (3 streams: upload, "
                               "compute, download)"},
             "selection": selection,
+            "ntt": _ntt_report(K * 2 * L, N, fin_avg,
+                               "INTT + mask of one query (mask draw, intt_mask_short_kernel), "
+                               "the step minus its MAC stage"),
+            "small_config": small,
             "ntt_form_responses": {"ms_per_step": nf_ms, "steps": cp_steps,
                                    "value": world * n / (nf_ms * 1e-3), "unit": UNIT},
             "slot_encoding": {"ms_per_step": sl_ms, "steps": cp_steps,
@@ -561,6 +623,8 @@ def run_batched_section(quick: bool = False, n_override: int | None = None,
         "qp_per_s_plain_per_query": B * n / (t_plain * 1e-3),
         "speedup_vs_plain": t_plain / t_batch,
         "ms_per_batch": t_batch, "ms_batched_mac": t_bmac, "ms_plain_for_B_queries": t_plain,
+        "ntt_epilogue": _ntt_report(B * K * 2 * L, N, t_batch - t_bmac,
+                                    "fused INTT + mask (intt_mask_kernel), the batch's step minus its MAC stage"),
         "ntt_form_responses": {"ms_per_batch": t_batch_ntt, "ms_plain_for_B_queries": t_plain_ntt,
                                "speedup_vs_plain": t_plain_ntt / t_batch_ntt,
                                "qp_per_s_batched": B * n / (t_batch_ntt * 1e-3)},
