@@ -301,8 +301,9 @@ int sanns_autotune_batched(sanns_ctx *ctx, const sanns_db *db, const uint64_t *c
  *                ||q||^2.  Shares are identical in meaning to coefficient
  *                encoding: they add up to ||q - p||^2 mod t.
  * A database keeps the encoding the context had when it was encoded; the
- * distance calls reject a database whose encoding differs from the context's,
- * and slot encoding rejects NTT-form responses.
+ * distance calls reject a database whose encoding differs from the context's.
+ * Slot encoding combines with NTT-form responses (the NTT of the slot-encoded
+ * coefficient response) and with circuit privacy.
  * sanns_decrypt_shares (and its no-allocation variant) decode in the
  * context's encoding.  SANNS_EINVAL for slots when t != 1 mod 2N.
  */

@@ -403,8 +403,6 @@ int sanns_distances_finish(sanns_ctx* ctx, const sanns_db* db, uint32_t B, uint6
   if (rc) return rc;
   if (B == 0) return SANNS_OK;
   if (!qids || !ct_out || !srv_share) return fail(SANNS_EINVAL, "NULL buffer");
-  if (ctx->slots && ctx->ntt_responses)
-    return fail(SANNS_EINVAL, "slot encoding returns coefficient-form responses only");
   cudaStream_t st = as_stream(stream);
   if (ctx->d_pk)
     SANNS_CUDA(launch_rerandomize(ctx->P, ct_out, B, db->K, db->pos0, mask_seed, qids, ctx->d_pk,
@@ -412,6 +410,8 @@ int sanns_distances_finish(sanns_ctx* ctx, const sanns_db* db, uint32_t B, uint6
   if (ctx->ntt_responses) {
     SANNS_CUDA(launch_mask_ntt(ctx->P, ct_out, db->d_norms, B, db->K, db->n, db->pos0, mask_seed, qids,
                                srv_share, ctx->d_pk != nullptr, ctx->flood_bits, ctx->privacy, st));
+    if (ctx->slots)
+      SANNS_CUDA(launch_slot_share(ctx->P, ctx->PT, B, db->K, db->n, db->pos0, mask_seed, qids, srv_share, st));
     return SANNS_OK;
   }
   SANNS_CUDA(launch_intt_mask(ctx->P, ct_out, db->d_norms, B, db->K, db->n, db->pos0, mask_seed, qids,

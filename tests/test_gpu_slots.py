@@ -91,8 +91,37 @@ def test_slot_encoding_rejections():
     with pytest.raises(S.SannsError):          # the database's encoding differs
         S.sanns_distances(ctx, db_slots, ct, 4, qids)
     S.sanns_set_encoding(ctx, True)
-    S.sanns_set_response_form(ctx, True)
-    with pytest.raises(S.SannsError):          # slot encoding: coefficient-form responses only
-        S.sanns_distances(ctx, db_slots, ct, 4, qids)
-    S.sanns_set_response_form(ctx, False)
     S.sanns_distances(ctx, db_slots, ct, 4, qids)   # the matching setting works
+
+
+@pytest.mark.parametrize("cfg,n,F", [((256, 2, 40, 0, 5), 700, 0), ((8192, 3, 60, 0, 7), 8192 + 100, 148)])
+def test_slot_encoding_with_ntt_form_responses(cfg, n, F):
+    # the NTT-form response is the NTT of the slot-encoded coefficient
+    # response, and NTT-form decryption decodes the slots
+    O = oracle(cfg)
+    d = cfg[4]
+    ctx = S.sanns_ctx_create(*cfg)
+    S.sanns_set_encoding(ctx, True)
+    S.sanns_set_response_form(ctx, True)
+    coords = inputs.uniform_coords(n, d, 21)
+    perm = inputs.permutation(n, 22)
+    q = inputs.uniform_coords(1, d, 23)
+    qids = np.array([9], dtype=np.uint64)
+    sk = S.sanns_keygen(ctx, 24)
+    s, s_hat = O.keygen(24)
+    db = S.sanns_encode_db(ctx, cu(coords), cu(perm))
+    ct_in = S.sanns_encrypt_query(ctx, sk, cu(q), 25, cu(qids))
+    pk = None
+    if F:
+        pk_d = S.sanns_public_key(ctx, sk, 26)
+        S.sanns_set_circuit_privacy(ctx, pk_d, F)
+        pk = pk_d.cpu().numpy()
+    out, srv = S.sanns_distances(ctx, db, ct_in, 27, cu(qids))
+    cli = S.sanns_decrypt_shares(ctx, sk, out, n, cu(q)).cpu().numpy()[0]
+    want_out, want_srv = O.distances(ct_in.cpu().numpy()[0], coords, perm, 27, 9, pk=pk, flood_bits=F,
+                                     slots=True)
+    assert np.array_equal(out.cpu().numpy()[0], O.to_ntt_form(want_out))
+    assert np.array_equal(srv.cpu().numpy()[0], want_srv)
+    assert np.array_equal(cli, O.decrypt_shares(want_out, s, q[0], n, slots=True))
+    brute = np.sum((coords[perm].astype(np.int64) - q[0].astype(np.int64)) ** 2, axis=1)
+    assert np.array_equal((cli.astype(np.int64) + srv.cpu().numpy()[0]) % O.t, brute)
