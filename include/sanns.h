@@ -202,7 +202,7 @@ int sanns_gather_plan(const sanns_clusters *cl, const uint32_t *probes_host, uin
  * the list positions (from 0) as positions: each query's result is that of
  * sanns_distances on its gathered list as a database.
  * Outputs are concatenated query by query: ct_out_dev [sum_b blocks_b][2][L][N]
- * (coefficient form; NTT-form responses are rejected), srv_share_dev uint32
+ * (in the context's response form), srv_share_dev uint32
  * [sum_b n_b], ids_dev uint32 [sum_b n_b] = the point index at each gathered
  * position (may be NULL).  Requires N <= 8192.  Uses a stream-ordered scratch
  * allocation of about sum_b blocks_b (d + 4 + 16 L S) N bytes (S dimension

@@ -688,7 +688,6 @@ int sanns_distances_gather(sanns_ctx* ctx, const sanns_clusters* cl, const uint6
   if (!ctx || !cl) return fail(SANNS_EINVAL, "ctx or clusters is NULL");
   if (cl->ctx != ctx) return fail(SANNS_EINVAL, "clusters belong to another context");
   if (ctx->P.N > 8192) return fail(SANNS_EINVAL, "the gather path supports N <= 8192");
-  if (ctx->ntt_responses) return fail(SANNS_EINVAL, "the gather path returns coefficient-form responses only");
   if (B == 0) return SANNS_OK;
   if (!ct_in || !qids || !ct_out || !srv_share || !probes) return fail(SANNS_EINVAL, "NULL buffer");
   std::vector<uint64_t> nb(B), kb(B);
@@ -701,7 +700,8 @@ int sanns_distances_gather(sanns_ctx* ctx, const sanns_clusters* cl, const uint6
   if (rc) return rc;
   SANNS_CUDA(launch_gather(ctx->P, ctx->params.d, cl, ct_in, B, probes, P, nb.data(), mask_seed, qids,
                            ct_out, srv_share, ids, ctx->sms, ctx->slots ? &ctx->PT : nullptr, ctx->d_pk,
-                           ctx->d_pk_shoup, ctx->flood_bits, ctx->privacy, as_stream(stream)));
+                           ctx->d_pk_shoup, ctx->flood_bits, ctx->privacy, ctx->ntt_responses,
+                           as_stream(stream)));
   return SANNS_OK;
 }
 

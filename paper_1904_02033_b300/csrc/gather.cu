@@ -105,23 +105,40 @@ __device__ __forceinline__ uint64_t mont_mul(uint64_t c, uint64_t p_mont, uint64
 struct GatherOpts {
   PrimeSet PT;
   int slots;
+  int ntt_form;  // responses in NTT form
   const uint64_t* pk;
   const uint64_t* pks;
   uint32_t F;
   PrivacyConsts C;
 };
 
-// Back to coefficient form and mask (c = 0), flooding (with privacy), store:
-// one component of one (item, prime) held in a (padded shared memory).
-__device__ void gather_finish(uint64_t* a, const PrimeSet& P, uint32_t j, uint32_t c, uint64_t w,
-                              const GatherItem& it, const GatherQuery& Q, const uint32_t* gnorm,
-                              uint64_t mask_seed, uint64_t qid, const GatherOpts& O, uint64_t* ct_out,
-                              uint32_t* srv_share) {
+// One component of one (item, prime), its NTT-domain sum held in a (padded
+// shared memory): back to coefficient form, mask (c = 0), flooding (with
+// privacy), store.  For NTT-form responses the sum stays in the NTT domain:
+// it is kept in save (global, owned by this block), the coefficient-domain
+// terms are built in a, transformed and added.
+__device__ void gather_finish(uint64_t* a, uint64_t* save, const PrimeSet& P, uint32_t j, uint32_t c,
+                              uint64_t w, const GatherItem& it, const GatherQuery& Q,
+                              const uint32_t* gnorm, uint64_t mask_seed, uint64_t qid, const GatherOpts& O,
+                              uint64_t* ct_out, uint32_t* srv_share) {
   const uint32_t N = P.N, L = P.L;
   const uint64_t q = P.q[j];
+  uint64_t* dst = ct_out + ((it.blk * 2 + c) * L + j) * N;
   __syncthreads();
-  ntt_inverse_smem(a, P, (int)j);
-  __syncthreads();
+  if (O.ntt_form) {
+    if (c == 1 && !O.pk) {  // nothing to add to c1
+      for (uint32_t x = threadIdx.x; x < N; x += blockDim.x) dst[x] = a[SP(x)];
+      return;
+    }
+    for (uint32_t x = threadIdx.x; x < N; x += blockDim.x) {
+      save[x] = a[SP(x)];
+      a[SP(x)] = 0;
+    }
+    __syncthreads();
+  } else {
+    ntt_inverse_smem(a, P, (int)j);
+    __syncthreads();
+  }
   if (c == 0) {
     const uint64_t dl = P.delta[j], dls = P.delta_shoup[j];
     for (uint32_t t4 = threadIdx.x; t4 < N / 4; t4 += blockDim.x) {
@@ -173,8 +190,13 @@ __device__ void gather_finish(uint64_t* a, const PrimeSet& P, uint32_t j, uint32
     }
     __syncthreads();
   }
-  uint64_t* dst = ct_out + ((it.blk * 2 + c) * L + j) * N;
-  for (uint32_t x = threadIdx.x; x < N; x += blockDim.x) dst[x] = a[SP(x)];
+  if (O.ntt_form) {
+    ntt_forward_smem(a, P, (int)j);
+    __syncthreads();
+    for (uint32_t x = threadIdx.x; x < N; x += blockDim.x) dst[x] = add_mod(save[x], a[SP(x)], q);
+  } else {
+    for (uint32_t x = threadIdx.x; x < N; x += blockDim.x) dst[x] = a[SP(x)];
+  }
 }
 
 // Persistent: block k takes units k, k + grid, ..; unit u = (w L + j) S + s.
@@ -291,7 +313,8 @@ gather_kernel(PrimeSet P, uint32_t d, uint64_t W, uint32_t S, uint32_t ds,
         for (; s2 < S; ++s2) v = add_mod(v, __ldcg(all + ((uint64_t)s2 * 2 + c) * N + x), q);
         poly[SP(x)] = v;
       }
-      gather_finish(poly, P, j, c, w, it, Q, gnorm, mask_seed, qid, O, ct_out, srv_share);
+      gather_finish(poly, all + (uint64_t)c * N, P, j, c, w, it, Q, gnorm, mask_seed, qid, O, ct_out,
+                    srv_share);
     }
   }
 }
@@ -345,7 +368,8 @@ cudaError_t launch_gather(const PrimeSet& P, uint32_t d, const sanns_clusters* c
                           uint32_t Pr, const uint64_t* n_b, uint64_t mask_seed,
                           const uint64_t* qids, uint64_t* ct_out, uint32_t* srv_share,
                           uint32_t* ids, int sms, const PrimeSet* PT, const uint64_t* pk,
-                          const uint64_t* pks, uint32_t F, const PrivacyConsts& C, cudaStream_t st) {
+                          const uint64_t* pks, uint32_t F, const PrivacyConsts& C, bool ntt_form,
+                          cudaStream_t st) {
   const uint32_t N = P.N;
   // host plan: items (query-major), per-query offsets, probe segments
   std::vector<GatherItem> items;
@@ -417,6 +441,7 @@ cudaError_t launch_gather(const PrimeSet& P, uint32_t d, const sanns_clusters* c
   } else {
     O.PT = P;
   }
+  O.ntt_form = ntt_form ? 1 : 0;
   O.pk = pk;
   O.pks = pks;
   O.F = F;

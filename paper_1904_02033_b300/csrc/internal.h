@@ -136,7 +136,8 @@ cudaError_t launch_gather(const PrimeSet& P, uint32_t d, const sanns_clusters* c
                           uint32_t Pr, const uint64_t* n_b, uint64_t mask_seed,
                           const uint64_t* qids, uint64_t* ct_out, uint32_t* srv_share,
                           uint32_t* ids, int sms, const PrimeSet* PT, const uint64_t* pk,
-                          const uint64_t* pks, uint32_t F, const PrivacyConsts& C, cudaStream_t st);
+                          const uint64_t* pks, uint32_t F, const PrivacyConsts& C, bool ntt_form,
+                          cudaStream_t st);
 cudaError_t launch_norms_slot(const PrimeSet& PT, uint32_t* norms, uint64_t K, cudaStream_t st);
 cudaError_t launch_join30(const uint64_t* src, uint64_t* dst, uint64_t count, cudaStream_t st);
 size_t batched_limb_bytes(uint32_t L, uint32_t N, uint64_t K, uint32_t d);

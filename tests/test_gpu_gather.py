@@ -22,15 +22,18 @@ def gathered_list(offsets, members, probes_b):
                           + [np.zeros(0, dtype=np.uint32)]).astype(np.uint32)
 
 
-@pytest.mark.parametrize("cfg,n,C,B,P,F,slots", [
-    ((256, 2, 40, 0, 5), 3000, 20, 3, 4, 0, False),
-    ((64, 2, 50, 0, 3), 500, 7, 2, 7, 0, False),       # probes covering every cluster, tiny N
-    ((8192, 3, 60, 0, 4), 30000, 9, 2, 3, 0, False),   # N = 8192, three 60-bit primes
-    ((256, 3, 60, 0, 5), 3000, 20, 3, 4, 100, False),  # circuit privacy
-    ((256, 2, 40, 0, 5), 3000, 20, 3, 4, 0, True),     # slot encoding
-    ((8192, 3, 60, 0, 4), 30000, 9, 2, 3, 148, True),  # both, N = 8192
+@pytest.mark.parametrize("cfg,n,C,B,P,F,slots,ntt", [
+    ((256, 2, 40, 0, 5), 3000, 20, 3, 4, 0, False, False),
+    ((64, 2, 50, 0, 3), 500, 7, 2, 7, 0, False, False),       # probes covering every cluster, tiny N
+    ((8192, 3, 60, 0, 4), 30000, 9, 2, 3, 0, False, False),   # N = 8192, three 60-bit primes
+    ((256, 3, 60, 0, 5), 3000, 20, 3, 4, 100, False, False),  # circuit privacy
+    ((256, 2, 40, 0, 5), 3000, 20, 3, 4, 0, True, False),     # slot encoding
+    ((8192, 3, 60, 0, 4), 30000, 9, 2, 3, 148, True, False),  # both, N = 8192
+    ((256, 2, 40, 0, 5), 3000, 20, 3, 4, 0, False, True),     # NTT-form responses
+    ((256, 3, 60, 0, 5), 3000, 20, 3, 4, 100, True, True),    # all three
+    ((8192, 3, 60, 0, 4), 30000, 9, 2, 3, 148, False, True),  # NTT form and privacy, N = 8192
 ])
-def test_gather_matches_oracle(cfg, n, C, B, P, F, slots):
+def test_gather_matches_oracle(cfg, n, C, B, P, F, slots, ntt):
     N, L, bits, rule, d = cfg
     rnd = np.random.default_rng(n)
     coords = inputs.uniform_coords(n, d, 1)
@@ -48,6 +51,7 @@ def test_gather_matches_oracle(cfg, n, C, B, P, F, slots):
     ctx = S.sanns_ctx_create(*cfg)
     sk = S.sanns_keygen(ctx, 3)
     S.sanns_set_encoding(ctx, slots)
+    S.sanns_set_response_form(ctx, ntt)
     pk = None
     if F:
         pk_d = S.sanns_public_key(ctx, sk, 8)
@@ -70,7 +74,7 @@ def test_gather_matches_oracle(cfg, n, C, B, P, F, slots):
         if len(g):
             want_out, want_srv = O.distances(ct_np[b], coords, g, 6, int(qids[b]), pk=pk, flood_bits=F,
                                              slots=slots)
-            assert np.array_equal(ct_out[kb0:kb0 + int(k_b[b])], want_out)
+            assert np.array_equal(ct_out[kb0:kb0 + int(k_b[b])], O.to_ntt_form(want_out) if ntt else want_out)
             assert np.array_equal(srv[nb0:nb0 + len(g)], want_srv)
             cli = O.decrypt_shares(want_out, s, q[b], len(g), slots=slots)
             brute = np.sum((coords[g].astype(np.int64) - q[b].astype(np.int64)) ** 2, axis=1)

@@ -61,18 +61,3 @@ def test_ntt_form_responses(cfg, n, B, privacy, batched):
     assert torch.equal(cli, cli_c)
     brute = np.sum((coords[perm].astype(np.int64)[None] - q.astype(np.int64)[:, None]) ** 2, axis=2)
     assert np.array_equal((cli.cpu().numpy().astype(np.int64) + srv.cpu().numpy()) % O.t, brute)
-
-
-def test_gather_rejects_ntt_form():
-    cfg = (256, 2, 40, 0, 4)
-    ctx = S.sanns_ctx_create(*cfg)
-    sk = S.sanns_keygen(ctx, 1)
-    coords = inputs.uniform_coords(300, 4, 3)
-    cl = S.sanns_clusters_create(ctx, cu(coords), np.array([0, 150, 300], dtype=np.uint64),
-                                 cu(np.arange(300, dtype=np.uint32)))
-    ct = S.sanns_encrypt_query(ctx, sk, cu(inputs.uniform_coords(1, 4, 4)), 5,
-                               cu(np.array([1], dtype=np.uint64)))
-    S.sanns_set_response_form(ctx, True)
-    with pytest.raises(S.SannsError):
-        S.sanns_distances_gather(ctx, cl, ct, np.array([[0]], dtype=np.uint32), 6,
-                                 cu(np.array([1], dtype=np.uint64)))
