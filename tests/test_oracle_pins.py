@@ -539,3 +539,60 @@ def test_corrupted_response_coefficient_breaks_exactly_its_share():
     bad[0, 0, 0, x] ^= np.uint64(1 << 30)
     rec = (O.decrypt_shares(bad, s, qv, n).astype(np.int64) + srv) % O.t
     assert np.flatnonzero(rec != brute).tolist() == [x]
+
+
+def test_response_equals_textbook_rederivation():
+    # The oracle's response blocks re-derived in pure Python from the
+    # definition (Sec. 5.3, Pi_ls step 3): c_c = sum_i c_{i,c} * g_i by the
+    # schoolbook negacyclic product mod q_j (no NTT), then c_0 += Delta
+    # (||p||^2 + r) with Delta = floor(Q / t) and r the mask draw of each
+    # position (padding included).  Shares only the coefficient transform
+    # (pinned against its O(N^2) definition) and the ChaCha20 draws (RFC 8439).
+    N, L, bits, d, n = 64, 2, 40, 3, 100
+    O = Oracle(N, L, bits, 0, d)
+    qs = [int(x) for x in O.q]
+    t = O.t
+    Q = 1
+    for qj in qs:
+        Q *= qj
+    Delta = Q // t
+    coords = inputs.uniform_coords(n, d, 31)
+    perm = inputs.permutation(n, 32)
+    qv = inputs.uniform_coords(1, d, 33)[0]
+    s, s_hat = O.keygen(34)
+    ct = O.encrypt(s_hat, qv, 35, 5)
+    out, srv = O.distances(ct, coords, perm, 36, 5)
+
+    def negacyclic(a, b, m):
+        res = [0] * N
+        for u in range(N):
+            if a[u] == 0:
+                continue
+            for v in range(N):
+                w = u + v
+                if w < N:
+                    res[w] += a[u] * b[v]
+                else:
+                    res[w - N] -= a[u] * b[v]
+        return [x % m for x in res]
+
+    K = -(-n // N)
+    for k in range(K):
+        pts = [int(perm[k * N + x]) if k * N + x < n else None for x in range(N)]
+        for j, qj in enumerate(qs):
+            for c in range(2):
+                acc = [0] * N
+                for i in range(d):
+                    a = [int(v) for v in O.intt(ct[i, c, j], j)]
+                    g = [int(coords[p][i]) if p is not None else 0 for p in pts]
+                    acc = [(x + y) % qj for x, y in zip(acc, negacyclic(a, g, qj))]
+                if c == 0:
+                    for x in range(N):
+                        p = pts[x]
+                        nrm = int(np.sum(coords[p].astype(np.int64) ** 2)) if p is not None else 0
+                        r = O.mask_r(36, 5, k * N + x)
+                        acc[x] = (acc[x] + (Delta % qj) * ((nrm + r) % t)) % qj
+                assert [int(v) for v in out[k, c, j]] == acc, (k, j, c)
+    # and the server's share is t - r at every database position
+    r_all = np.array([O.mask_r(36, 5, x) for x in range(n)], dtype=np.int64)
+    assert np.array_equal(srv.astype(np.int64), (t - r_all) % t)
