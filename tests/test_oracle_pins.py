@@ -596,3 +596,51 @@ def test_response_equals_textbook_rederivation():
     # and the server's share is t - r at every database position
     r_all = np.array([O.mask_r(36, 5, x) for x in range(n)], dtype=np.int64)
     assert np.array_equal(srv.astype(np.int64), (t - r_all) % t)
+
+
+def test_decryption_equals_textbook_rederivation():
+    # the client's share re-derived in pure Python: w_j = c0 + c1 s by the
+    # schoolbook negacyclic product mod q_j, w by CRT, m = round(t w / Q)
+    # mod t, share = m + ||q||^2 mod t
+    N, L, bits, d, n = 64, 2, 40, 3, 100
+    O = Oracle(N, L, bits, 0, d)
+    qs = [int(x) for x in O.q]
+    t = O.t
+    Q = 1
+    for qj in qs:
+        Q *= qj
+    coords = inputs.uniform_coords(n, d, 41)
+    qv = inputs.uniform_coords(1, d, 42)[0]
+    s, s_hat = O.keygen(43)
+    ct = O.encrypt(s_hat, qv, 44, 6)
+    out, _ = O.distances(ct, coords, None, 45, 6)
+    got = O.decrypt_shares(out, s, qv, n)
+    sv = [int(v) for v in s]
+    qn = int(np.sum(qv.astype(np.int64) ** 2))
+    want = []
+    for k in range(out.shape[0]):
+        w_res = []
+        for j, qj in enumerate(qs):
+            c0 = [int(v) for v in out[k, 0, j]]
+            c1 = [int(v) for v in out[k, 1, j]]
+            prod = [0] * N
+            for u in range(N):
+                if sv[u] == 0:
+                    continue
+                for v in range(N):
+                    w = u + v
+                    term = sv[u] * c1[v]
+                    if w < N:
+                        prod[w] += term
+                    else:
+                        prod[w - N] -= term
+            w_res.append([(c0[x] + prod[x]) % qj for x in range(N)])
+        for x in range(N):
+            w = 0
+            for j, qj in enumerate(qs):
+                Qj = Q // qj
+                w += w_res[j][x] * Qj * pow(Qj, -1, qj)
+            w %= Q
+            m = ((t * w + Q // 2) // Q) % t
+            want.append((m + qn) % t)
+    assert got.tolist() == want[:n]
