@@ -644,3 +644,34 @@ def test_decryption_equals_textbook_rederivation():
             m = ((t * w + Q // 2) // Q) % t
             want.append((m + qn) % t)
     assert got.tolist() == want[:n]
+
+
+def test_encryption_phase_is_the_documented_error_plus_message():
+    # c0 + c1 s (back in coefficient form) is exactly e + Delta m_i: e the
+    # centred binomial (eta = 21) of the low 42 bits of draw (seed, 3, qid
+    # 2^16 + i) at each coefficient, m_i = (t - 2 q_i) mod t on coefficient 0
+    N, L, bits, d = 64, 2, 40, 3
+    O = Oracle(N, L, bits, 0, d)
+    qs = [int(x) for x in O.q]
+    t = O.t
+    Q = 1
+    for qj in qs:
+        Q *= qj
+    Delta = Q // t
+    qv = inputs.uniform_coords(1, d, 51)[0]
+    seed, qid = 52, 7
+    s, s_hat = O.keygen(53)
+    ct = O.encrypt(s_hat, qv, seed, qid)
+    m21 = (1 << 21) - 1
+    for i in range(d):
+        e = []
+        for x in range(N):
+            lo, _ = O.draw128(seed, 3, (qid << 16) | i, x)
+            e.append(bin(lo & m21).count("1") - bin((lo >> 21) & m21).count("1"))
+        m = (t - 2 * int(qv[i])) % t
+        for j, qj in enumerate(qs):
+            phase = (ct[i, 0, j].astype(object) + ct[i, 1, j].astype(object) * s_hat[j].astype(object)) % qj
+            v = [int(a) for a in O.intt(np.array(phase, dtype=np.uint64), j)]
+            want = [ex % qj for ex in e]
+            want[0] = (want[0] + (Delta % qj) * m) % qj
+            assert v == want, (i, j)
