@@ -25,10 +25,10 @@ something other than itself (O(N^2) NTT definition, schoolbook products,
 RFC 8439 test vectors, decrypt(encrypt(m)) = m, brute-force distances,
 sympy primality, closed forms for ApproxTopk, the mod-t transform as a ring
 isomorphism, Algorithm 4 reducing to brute force when every cluster is
-retrieved).  The concrete ciphertext bits
-depend on conventions the paper leaves open (RNG layout, NTT order); those
-are pinned only through the conventions and the round-trip identities --
-"parity unpinned" by a printed value from the paper.
+retrieved).  The concrete ciphertext bits depend on conventions the paper
+leaves open (RNG layout, NTT order), so the paper prints none; encryption,
+the response blocks, circuit privacy and decryption are each re-derived at
+N = 64 from their definitions with schoolbook products and exact integers.
 """
 from .bfv import Oracle, chacha20_block  # noqa: F401
 from .params import make_params  # noqa: F401

@@ -675,3 +675,60 @@ def test_encryption_phase_is_the_documented_error_plus_message():
             want = [ex % qj for ex in e]
             want[0] = (want[0] + (Delta % qj) * m) % qj
             assert v == want, (i, j)
+
+
+@pytest.mark.parametrize("F", [0, 40, 200])
+def test_circuit_privacy_terms_equal_textbook_rederivation(F):
+    # Sec. 2, circuit privacy, re-derived in pure Python at N = 64 with
+    # schoolbook products (no NTT): the public key's phase pk0 + pk1 s is its
+    # error draw (CBD eta = 21, stream 6); the privacy response minus the plain
+    # one is pk_c u in coefficient form, u ternary ((lo mod 3) - 1, stream 7,
+    # position k N + x), plus e1 = (low F + 1 bits of the 256-bit value of
+    # streams 9 and 10) - 2^F on c0 and e2 = CBD of stream 8 on c1
+    N, L, bits, d, n = 64, 2, 40, 2, 100
+    O = Oracle(N, L, bits, 0, d)
+    qs = [int(x) for x in O.q]
+    m21 = (1 << 21) - 1
+
+    def cbd(lo):
+        return bin(lo & m21).count("1") - bin((lo >> 21) & m21).count("1")
+
+    def negacyclic(a, b, m):
+        res = [0] * N
+        for u in range(N):
+            for v in range(N):
+                w = u + v
+                res[w % N] += a[u] * b[v] if w < N else -a[u] * b[v]
+        return [x % m for x in res]
+
+    coords = inputs.uniform_coords(n, d, 60)
+    qv = inputs.uniform_coords(1, d, 61)[0]
+    s, s_hat = O.keygen(62)
+    pk = O.public_key(s_hat, 63)
+    e_pk = [cbd(O.draw128(63, 6, 0, x)[0]) for x in range(N)]
+    for j, qj in enumerate(qs):
+        p0 = [int(v) for v in O.intt(pk[0, j], j)]
+        p1 = [int(v) for v in O.intt(pk[1, j], j)]
+        ph = [(a + b) % qj for a, b in zip(p0, negacyclic(p1, [int(v) % qj for v in s], qj))]
+        assert ph == [e % qj for e in e_pk], j
+    seed, qid = 64, 9
+    ct = O.encrypt(s_hat, qv, 65, qid)
+    plain, srv0 = O.distances(ct, coords, None, seed, qid)
+    priv, srv = O.distances(ct, coords, None, seed, qid, pk=pk, flood_bits=F)
+    assert np.array_equal(srv, srv0)
+    for k in range(-(-n // N)):
+        pos = [k * N + x for x in range(N)]
+        u = [O.draw128(seed, 7, qid, p)[0] % 3 - 1 for p in pos]
+        e1, e2 = [], []
+        for p in pos:
+            a, b = O.draw128(seed, 9, qid, p), O.draw128(seed, 10, qid, p)
+            v = a[0] | (a[1] << 64) | (b[0] << 128) | (b[1] << 192)
+            e1.append((v & ((1 << (F + 1)) - 1)) - (1 << F))
+            e2.append(cbd(O.draw128(seed, 8, qid, p)[0]))
+        assert all(-(1 << F) <= e < (1 << F) for e in e1)
+        for j, qj in enumerate(qs):
+            for c, e in ((0, e1), (1, e2)):
+                pkc = [int(v) for v in O.intt(pk[c, j], j)]
+                want = [(x + y) % qj for x, y in zip(negacyclic(pkc, [w % qj for w in u], qj), e)]
+                diff = [(int(a) - int(b)) % qj for a, b in zip(priv[k, c, j], plain[k, c, j])]
+                assert diff == want, (F, k, c, j)
