@@ -109,6 +109,33 @@ def test_chacha20_rfc8439_block_vector():
     assert out.astype("<u4").tobytes().hex() == kv["block"][0]
 
 
+
+def test_draw128_layout_over_the_rfc_block():
+    # The 128-bit draw of coefficient c of stream (seed, purpose, object):
+    # key = seed as two little-endian words, nonce = (purpose, object low,
+    # object high), block counter c / 4, words 4 (c mod 4) .. + 3 of the block.
+    # With seed = purpose = object = 0 the eight draws c = 0 .. 7 are the RFC
+    # 8439 A.1 zero-key keystream (block counters 0 and 1) read in order.
+    g = {}
+    for line in open(os.path.join(GOLD, "chacha20_rfc8439_zero_key.txt")):
+        if line.strip() and not line.startswith("#"):
+            k, v = line.split()
+            g[k] = v
+    O = Oracle(64, 1, 40, 0, 1)
+    stream = bytes.fromhex(g["block0"] + g["block1"])
+    for c in range(8):
+        lo, hi = O.draw128(0, 0, 0, c)
+        assert ((hi << 64) | lo).to_bytes(16, "little") == stream[16 * c:16 * c + 16], c
+    rnd = random.Random(7)
+    for _ in range(40):
+        seed, purpose = rnd.getrandbits(64), rnd.randrange(1, 11)
+        obj, c = rnd.getrandbits(40), rnd.getrandbits(33)
+        blk = chacha20_block([seed & 0xFFFFFFFF, seed >> 32, 0, 0, 0, 0, 0, 0], c // 4,
+                             [purpose, obj & 0xFFFFFFFF, obj >> 32])
+        w = [int(x) for x in blk[4 * (c % 4):4 * (c % 4) + 4]]
+        assert O.draw128(seed, purpose, obj, c) == (w[0] | w[1] << 32, w[2] | w[3] << 32)
+
+
 # ---------------------------------------------------------------- NTT
 def _ntt_definition(a, q, psi):
     """O(N^2) definition of the convention: slot s holds a(psi^(2 brv(s)+1))."""
