@@ -341,6 +341,33 @@ def test_approx_topk_expected_hits_closed_forms():
     assert abs(np.mean(hits) - want) < 4 * np.std(hits) / math.sqrt(len(hits)) + 0.02
 
 
+
+@pytest.mark.parametrize("n,k,l", [(7, 3, 3), (7, 2, 4), (6, 3, 5)])
+def test_expected_hits_equals_brute_force_over_all_permutations(n, k, l):
+    # E|I| of Algorithm 2 by enumeration: every ordering of n distinct values
+    # run through ApproxTopk, the true top k counted among its output
+    import itertools
+    v = np.arange(n)
+    tot, cnt = 0, 0
+    for pm in itertools.permutations(range(n)):
+        pm = np.array(pm)
+        _, got = select.approx_topk(v[pm], pm, k, l)
+        tot += len(set(got) & set(range(k)))
+        cnt += 1
+    assert abs(tot / cnt - select.expected_hits(n, k, l)) < 1e-12
+
+
+@pytest.mark.parametrize("k", [5, 10, 20, 50, 100])
+@pytest.mark.parametrize("delta", [0.01, 0.02, 0.05, 0.1])
+def test_theorem_1_bins_k_over_delta_meet_the_bound(k, delta):
+    # Theorem 1: with l = k / delta bins the expected number of true top-k
+    # entries returned is at least (1 - delta) k; checked on the Sec. 7
+    # selection grid (n = 10^6 values, k and delta as evaluated there)
+    n = 10 ** 6
+    l = math.ceil(k / delta)
+    assert select.expected_hits(n, k, l) >= (1 - delta) * k
+
+
 # ---------------------------------------------------------------------------
 # circuit privacy (Sec. 2 "Additive Homomorphic Encryption": circuit privacy by
 # noise flooding; a public key lets the server re-randomise c1)
