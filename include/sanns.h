@@ -21,6 +21,14 @@
  *   last failure on the calling thread is sanns_last_error().  Arguments are
  *   validated on the host before anything is launched; an invalid argument
  *   launches nothing.
+ * - Host threads: the computing calls keep no state in a handle (their
+ *   scratch is allocated stream-ordered per call), so several threads may
+ *   call them on one context and database at once, each with its own stream
+ *   and output buffers.  Calls that change a handle's settings or contents
+ *   (sanns_set_*, sanns_autotune_*, sanns_batched_tune,
+ *   sanns_db_prepare_batched, sanns_db_set_position_base, the *_free calls)
+ *   must not overlap any other call on that handle.  The device error word
+ *   read by sanns_device_status is shared by all calls on a context.
  *
  * Readings of the paper that fix the exact bits (the paper leaves them to
  * SEAL): primes = the L largest primes below 2^prime_bits that are 1 mod 2N;
