@@ -81,6 +81,11 @@ static int log2_exact(uint32_t n)
 /* NTT over Z_q[x]/(x^N + 1)                                             */
 /* ------------------------------------------------------------------ */
 /*
+ * Products in the BFV ring R_q = Z_q[x]/(x^N + 1) (Sec. 2.3, Sec. 5.3).  The
+ * paper leaves the multiplication algorithm to SEAL; this is the textbook
+ * negacyclic number-theoretic transform.
+ */
+/*
  * Twiddle tables: fwd[m] = psi^brv(m), inv[m] = psi^-brv(m), m in [0, N),
  * brv over log2(N) bits.
  */
@@ -146,8 +151,13 @@ void oracle_intt(uint64_t *a, uint32_t N, uint64_t q, const uint64_t *inv)
 }
 
 /* ------------------------------------------------------------------ */
-/* ChaCha20 block function (RFC 8439, Sec. 2.3)                         */
+/* ChaCha20 block function (RFC 8439, its section 2.3)                  */
 /* ------------------------------------------------------------------ */
+/*
+ * The randomness of keygen, encryption, the server's masks and circuit
+ * privacy (Sec. 2.3, Sec. 5.3).  The paper leaves its source to SEAL; every
+ * draw here comes from a ChaCha20 stream.
+ */
 static uint32_t rotl32(uint32_t x, int n) { return (x << n) | (x >> (32 - n)); }
 
 static void quarter_round(uint32_t *s, int a, int b, int c, int d)
@@ -434,7 +444,7 @@ void oracle_intt_mask(const oracle_params *P, const uint64_t *acc,
 /* ------------------------------------------------------------------ */
 /*
  * The paper asks the AHE scheme for circuit privacy and obtains it by noise
- * flooding (Sec. 2, "Additive Homomorphic Encryption"; 108 bits of
+ * flooding (Sec. 2.3, "Additive Homomorphic Encryption"; 108 bits of
  * statistical circuit privacy with its parameters, Sec. 7.1).  With
  * private-key BFV the server cannot re-randomise c1 = sum_i a_i g_i on its
  * own, so the client also publishes a public key and the server adds a fresh
@@ -476,9 +486,9 @@ void oracle_public_key(const oracle_params *P, const uint64_t *s_hat, uint64_t s
 }
 
 /*
- * Re-randomisation in the NTT domain, before the inverse transform: for
- * blocks k in [k0, k0 + nk) (global block index, positions k N + x) of one
- * query,
+ * Re-randomisation (circuit privacy, Sec. 2.3) in the NTT domain, before the
+ * inverse transform: for blocks k in [k0, k0 + nk) (global block index,
+ * positions k N + x) of one query,
  *   u  ternary, (lo mod 3) - 1 of draw (seed, U, qid) at position k N + x,
  *   acc[k][c][j] += pk_c[j] * NTT(u)   (slot-wise), c = 0, 1.
  * acc is [nk][2][L][N], NTT form, modified in place.
@@ -511,7 +521,8 @@ void oracle_rerandomize(const oracle_params *P, uint64_t *acc, const uint64_t *p
 }
 
 /*
- * Flooding, in coefficient form after the inverse transform and the mask:
+ * Flooding (circuit privacy by noise flooding, Sec. 2.3), in coefficient form
+ * after the inverse transform and the mask:
  * at position k N + x of one query
  *   e1 = v - 2^F, v = the low F + 1 bits of the 256-bit integer
  *        lo_a + hi_a 2^64 + lo_b 2^128 + hi_b 2^192, (lo_a, hi_a) the draw
@@ -586,7 +597,10 @@ void oracle_decrypt_phase(const oracle_params *P, const uint64_t *ct,
     free(b);
 }
 
-/* Schoolbook negacyclic product mod q, for the tests' cross-checks. */
+/*
+ * Schoolbook negacyclic product mod q: the definition of the product in
+ * R_q = Z_q[x]/(x^N + 1) (Sec. 5.3), for the tests' cross-checks.
+ */
 void oracle_negacyclic_schoolbook(const uint64_t *a, const uint64_t *b,
                                   uint32_t N, uint64_t q, uint64_t *out)
 {

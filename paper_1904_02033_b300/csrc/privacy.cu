@@ -1,5 +1,5 @@
 // Circuit privacy of the distance responses.  The paper requires the AHE
-// scheme to be circuit private and obtains it by noise flooding (Sec. 2,
+// scheme to be circuit private and obtains it by noise flooding (Sec. 2.3,
 // "Additive Homomorphic Encryption"; 108 bits of statistical circuit privacy
 // with its parameters, Sec. 7.1).  With private-key BFV the server cannot
 // re-randomise c1 = sum_i a_i g_i by itself, so the client publishes a public

@@ -369,7 +369,7 @@ def test_theorem_1_bins_k_over_delta_meet_the_bound(k, delta):
 
 
 # ---------------------------------------------------------------------------
-# circuit privacy (Sec. 2 "Additive Homomorphic Encryption": circuit privacy by
+# circuit privacy (Sec. 2.3 "Additive Homomorphic Encryption": circuit privacy by
 # noise flooding; a public key lets the server re-randomise c1)
 # ---------------------------------------------------------------------------
 def test_public_key_is_an_encryption_of_zero():
@@ -733,7 +733,7 @@ def test_encryption_phase_is_the_documented_error_plus_message():
 
 @pytest.mark.parametrize("F", [0, 40, 200])
 def test_circuit_privacy_terms_equal_textbook_rederivation(F):
-    # Sec. 2, circuit privacy, re-derived in pure Python at N = 64 with
+    # Sec. 2.3, circuit privacy, re-derived in pure Python at N = 64 with
     # schoolbook products (no NTT): the public key's phase pk0 + pk1 s is its
     # error draw (CBD eta = 21, stream 6); the privacy response minus the plain
     # one is pk_c u in coefficient form, u ternary ((lo mod 3) - 1, stream 7,
