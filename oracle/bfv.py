@@ -21,6 +21,7 @@ _lib = None
 
 
 def lib():
+    """The oracle's compiled C loops (built on first use)."""
     global _lib
     if _lib is None:
         _lib = C.CDLL(_build.build())
@@ -93,12 +94,15 @@ class Oracle:
 
     # ---------------- transforms ----------------
     def ntt(self, a: np.ndarray, j: int) -> np.ndarray:
+        """Negacyclic NTT mod q_j (products in R_q = Z_q[x]/(x^N + 1), Sec. 2.3):
+        slot s = a(psi_j^(2 brv(s) + 1))."""
         a = np.ascontiguousarray(a, dtype=np.uint64).copy()
         lib().oracle_ntt(a.ctypes.data_as(C.POINTER(C.c_uint64)), self.N, int(self.q[j]),
                          self.fwd[j].ctypes.data_as(C.POINTER(C.c_uint64)))
         return a
 
     def intt(self, a: np.ndarray, j: int) -> np.ndarray:
+        """Inverse of ntt: NTT form back to coefficients mod q_j (Sec. 2.3)."""
         a = np.ascontiguousarray(a, dtype=np.uint64).copy()
         lib().oracle_intt(a.ctypes.data_as(C.POINTER(C.c_uint64)), self.N, int(self.q[j]),
                           self.inv[j].ctypes.data_as(C.POINTER(C.c_uint64)))
@@ -127,6 +131,8 @@ class Oracle:
         return out
 
     def schoolbook(self, a: np.ndarray, b: np.ndarray, j: int) -> np.ndarray:
+        """Negacyclic product in R_q mod q_j by the schoolbook loop (the
+        definition of the ring product, Sec. 5.3)."""
         a = np.ascontiguousarray(a, dtype=np.uint64)
         b = np.ascontiguousarray(b, dtype=np.uint64)
         out = np.zeros(self.N, dtype=np.uint64)
@@ -135,12 +141,17 @@ class Oracle:
 
     # ---------------- protocol steps ----------------
     def keygen(self, seed: int):
+        """AHE.Keygen (Pi_ls step 1): ternary s from stream (seed, 1) and its NTT
+        s_hat per prime; returns (s int8 [N], s_hat [L][N])."""
         s = np.zeros(self.N, dtype=np.int8)
         s_hat = np.zeros((self.L, self.N), dtype=np.uint64)
         lib().oracle_keygen(C.byref(self._c), seed, _p(s), _p(s_hat))
         return s, s_hat
 
     def encrypt(self, s_hat: np.ndarray, qv: np.ndarray, seed: int, qid: int) -> np.ndarray:
+        """AHE.Enc of one query (Pi_ls step 2, Sec. 5.3): coordinate i as the
+        constant plaintext m_i = (t - 2 q_i) mod t, private-key BFV; returns
+        ct [d][2][L][N] in NTT form."""
         qv = np.ascontiguousarray(qv, dtype=np.uint8)
         assert qv.shape == (self.d,)
         ct = np.zeros((self.d, 2, self.L, self.N), dtype=np.uint64)
@@ -149,6 +160,8 @@ class Oracle:
         return ct
 
     def blocks(self, n: int) -> int:
+        """Number of N-point blocks covering n points (Sec. 5.3 packs N points
+        per plaintext)."""
         return (n + self.N - 1) // self.N
 
     def encode_db(self, coords: np.ndarray, perm: np.ndarray | None, k0: int = 0,
@@ -212,6 +225,8 @@ class Oracle:
         return np.concatenate(out) if out else np.zeros(0, dtype=np.uint32)
 
     def mac(self, ct: np.ndarray, pt: np.ndarray) -> np.ndarray:
+        """Pi_ls step 3, sum_i CMult(c_i, g_ik) per block, slot-wise in the NTT
+        domain; returns acc [nk][2][L][N]."""
         nk = pt.shape[0]
         acc = np.zeros((nk, 2, self.L, self.N), dtype=np.uint64)
         lib().oracle_mac(C.byref(self._c), _p(np.ascontiguousarray(ct)),
@@ -220,6 +235,8 @@ class Oracle:
 
     def intt_mask(self, acc: np.ndarray, norms: np.ndarray, n: int, k0: int, k1: int,
                   mask_seed: int, qid: int):
+        """Pi_ls step 3, "+ r": each block back to coefficient form plus
+        Delta (||p||^2 + r) on c0; returns (responses, server shares t - r)."""
         out = np.zeros_like(acc)
         cnt = max(0, min(n, k1 * self.N) - k0 * self.N)
         share = np.zeros(cnt, dtype=np.uint32)
@@ -259,6 +276,7 @@ class Oracle:
         return out
 
     def from_ntt_form(self, ct_ntt: np.ndarray) -> np.ndarray:
+        """Inverse of to_ntt_form: every polynomial back to coefficient form."""
         out = np.empty_like(ct_ntt)
         for k in range(ct_ntt.shape[0]):
             for c in range(2):
@@ -268,6 +286,8 @@ class Oracle:
 
     # ---------------- circuit privacy ----------------
     def public_key(self, s_hat: np.ndarray, seed: int) -> np.ndarray:
+        """The client's public key for circuit privacy (Sec. 2.3): pk1 = a,
+        pk0 = -a s + e, layout [2][L][N], NTT form."""
         pk = np.zeros((2, self.L, self.N), dtype=np.uint64)
         lib().oracle_public_key(C.byref(self._c), _p(np.ascontiguousarray(s_hat)), seed, _p(pk))
         return pk
@@ -304,6 +324,8 @@ class Oracle:
         return out
 
     def decrypt_phase(self, ct_out: np.ndarray, s: np.ndarray) -> np.ndarray:
+        """First half of AHE.Dec (Pi_ls step 4): c0 + c1 s mod q_j, coefficient
+        form, [nk][L][N]."""
         nk = ct_out.shape[0]
         v = np.zeros((nk, self.L, self.N), dtype=np.uint64)
         lib().oracle_decrypt_phase(C.byref(self._c), _p(np.ascontiguousarray(ct_out)),
@@ -361,12 +383,15 @@ class Oracle:
         return ((m + qn) % self.t).astype(np.uint32)
 
     def draw128(self, seed: int, purpose: int, obj: int, c: int):
+        """The 128-bit draw of coefficient c of ChaCha20 stream (seed, purpose,
+        object): the randomness of every protocol step (Sec. 2.3, 5.3)."""
         out = np.zeros(2, dtype=np.uint64)
         lib().oracle_draw128(seed, purpose, obj, c, _p(out))
         return int(out[0]), int(out[1])
 
 
 def chacha20_block(key_words, counter: int, nonce_words):
+    """The ChaCha20 block function (RFC 8439, its section 2.3), as 16 words."""
     key = np.array(key_words, dtype=np.uint32)
     nonce = np.array(nonce_words, dtype=np.uint32)
     out = np.zeros(16, dtype=np.uint32)

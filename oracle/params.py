@@ -107,10 +107,15 @@ class Params:
 
     @property
     def delta_mod_q(self) -> list[int]:
+        """Delta = floor(Q / t) (BFV, Sec. 2.3) reduced mod each q_j."""
         return [self.delta % qj for qj in self.q]
 
 
 def make_params(N: int, L: int, prime_bits: int, t_rule: int, d: int) -> Params:
+    """The BFV parameters of Sec. 7.1 ("Parameters": N, a three-word q, t) as
+    exact integers: the L largest primes below 2^prime_bits that are 1 mod 2N,
+    the smallest primitive 2N-th root psi of each, t by its rule, and
+    Delta = floor(Q / t)."""
     if N & (N - 1) or N < 2:
         raise ValueError("N must be a power of two")
     q = ntt_primes(N, L, prime_bits)
