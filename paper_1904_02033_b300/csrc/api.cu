@@ -1,5 +1,7 @@
 // The extern "C" entry points of sanns.h: host-side validation, handle
-// management and the launch sequences.
+// management and the launch sequences of the linear-scan protocol's steps
+// 1-4 (Sec. 5.3), the clustering protocol's gathers (Algorithm 4) and the
+// selections (Algorithms 1 and 2).
 #include <cstdio>
 #include <cstring>
 #include <string>

@@ -1,5 +1,6 @@
 // K5: the batched ct x pt MAC on the tensor cores (tcgen05, kind::f16, fp16
-// operands, fp32 accumulation in TMEM), exact.
+// operands, fp32 accumulation in TMEM), exact: the sum_i CMult(c_i, g_ik) of
+// the linear-scan protocol's step 3 (Sec. 5.3) for many queries at once.
 //
 // With B queries, every (prime j, slot s) is the contraction
 //     C[(b, c)][k] = sum_i A[(b, c)][i] P[k][i]  mod q_j,

@@ -1,4 +1,5 @@
-// sanns_decrypt_shares_noalloc: client decryption for callers that cannot
+// sanns_decrypt_shares_noalloc: client decryption (the linear-scan protocol's
+// step 4, Sec. 5.3; the paper has no allocation-free form) for callers that cannot
 // allocate device memory at call time -- for instance code running inside a
 // CUDA graph capture, a real-time loop that must not call cudaMalloc (it can
 // synchronise the device and its latency is unbounded), or a host that runs
