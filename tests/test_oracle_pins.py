@@ -786,3 +786,32 @@ def test_circuit_privacy_terms_equal_textbook_rederivation(F):
                 want = [(x + y) % qj for x, y in zip(negacyclic(pkc, [w % qj for w in u], qj), e)]
                 diff = [(int(a) - int(b)) % qj for a, b in zip(priv[k, c, j], plain[k, c, j])]
                 assert diff == want, (F, k, c, j)
+
+
+@pytest.mark.parametrize("cfg", [(64, 2, 40, 0, 4), (256, 3, 60, 0, 8)])
+def test_maximum_flooding_still_decrypts_worst_case_distances(cfg):
+    # Sec. 2.3 noise flooding at the largest exponent allowed, F = floor(log2
+    # Delta) - 2 (2^F <= Delta / 4, the rest of the Delta / 2 margin left to
+    # the structured noise): extreme coordinates (0 against 255, the largest
+    # distance d 255^2 and the largest plaintext overflow) still reconstruct
+    # exactly, and the phase noise is the flooding term
+    O = Oracle(*cfg)
+    N, d = cfg[0], cfg[4]
+    n = 2 * N - 3
+    coords = np.full((n, d), 255, dtype=np.uint8)
+    coords[1::3] = 0
+    rnd = np.random.default_rng(cfg[0])
+    coords[2::3] = rnd.integers(0, 256, size=coords[2::3].shape, dtype=np.uint8)
+    F = O.max_flood_bits()
+    assert 2 ** F <= O.P.delta // 4 < 2 ** (F + 1)
+    s, s_hat = O.keygen(71)
+    pk = O.public_key(s_hat, 72)
+    for qv in (np.zeros(d, dtype=np.uint8), np.full(d, 255, dtype=np.uint8)):
+        ct = O.encrypt(s_hat, qv, 73, 4)
+        out, srv = O.distances(ct, coords, None, 74, 4, pk=pk, flood_bits=F)
+        cli = O.decrypt_shares(out, s, qv, n)
+        brute = np.sum((coords.astype(np.int64) - qv.astype(np.int64)) ** 2, axis=1)
+        assert np.array_equal((cli.astype(np.int64) + srv) % O.t, brute)
+        m = O.scale_round(O.decrypt_phase(out, s))
+        noise = max(O.phase_noise(out, s, m))
+        assert 2 ** (F - 2) <= noise < O.P.delta // 2
