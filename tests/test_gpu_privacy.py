@@ -91,3 +91,35 @@ def test_flood_bits_bound():
         S.sanns_set_circuit_privacy(ctx, pk, fmax + 1)
     assert e.value.code == -1
     S.sanns_set_circuit_privacy(ctx, pk, fmax)
+
+
+@pytest.mark.parametrize("cfg", [(256, 2, 40, 0, 4), (256, 3, 60, 0, 8)])
+def test_maximum_flooding_extreme_coordinates(cfg):
+    # the largest allowed flooding exponent with the extreme coordinates (0
+    # against 255): bit-identical to the oracle, and the GPU decryption still
+    # reconstructs every distance
+    O = oracle(cfg)
+    ctx = S.sanns_ctx_create(*cfg)
+    N, d = cfg[0], cfg[4]
+    n = 2 * N - 3
+    coords = np.full((n, d), 255, dtype=np.uint8)
+    coords[1::3] = 0
+    q = np.stack([np.zeros(d, dtype=np.uint8), np.full(d, 255, dtype=np.uint8)])
+    qids = np.array([9, 10], dtype=np.uint64)
+    sk = S.sanns_keygen(ctx, 81)
+    pk = S.sanns_public_key(ctx, sk, 82)
+    F = S.sanns_circuit_privacy_max_flood_bits(ctx)
+    S.sanns_set_circuit_privacy(ctx, pk, F)
+    db = S.sanns_encode_db(ctx, cu(coords))
+    ct_in = S.sanns_encrypt_query(ctx, sk, cu(q), 83, cu(qids))
+    out, srv = S.sanns_distances(ctx, db, ct_in, 84, cu(qids))
+    cli = S.sanns_decrypt_shares(ctx, sk, out, n, cu(q)).cpu().numpy()
+    out, srv = out.cpu().numpy(), srv.cpu().numpy()
+    s, s_hat = O.keygen(81)
+    opk = O.public_key(s_hat, 82)
+    cti = ct_in.cpu().numpy()
+    for b in range(2):
+        oo, os_ = O.distances(cti[b], coords, None, 84, int(qids[b]), pk=opk, flood_bits=F)
+        assert np.array_equal(out[b], oo) and np.array_equal(srv[b], os_)
+        brute = np.sum((coords.astype(np.int64) - q[b].astype(np.int64)) ** 2, axis=1)
+        assert np.array_equal((cli[b].astype(np.int64) + srv[b]) % O.t, brute)
