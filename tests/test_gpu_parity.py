@@ -37,6 +37,7 @@ CONFIGS = [
     (256, 3, 60, 1, 17),
     (4096, 2, 54, 0, 32),
     (8192, 3, 60, 0, 7),
+    (16384, 4, 60, 0, 5),   # the largest ring and prime count the API accepts
 ]
 
 
@@ -149,6 +150,7 @@ def _pipeline(cfg, n, B, seed, perm=True):
     # INTT + mask kernel, with the padding positions of the last block
     (CONFIGS[1], 256 * 60 - 17, 8),
     (CONFIGS[4], 8192 * 38 - 1000, 4),
+    (CONFIGS[5], 16384 + 77, 2),    # N = 16384, four 60-bit primes, ragged, a query pair
 ])
 def test_distances_match_oracle_bit_exact(cfg, n, B):
     r = _pipeline(cfg, n, B, seed=n % 97)
