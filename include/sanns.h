@@ -377,7 +377,7 @@ int sanns_topk_segments(sanns_ctx *ctx, const uint32_t *cli_dev, const uint32_t 
                         uint64_t bins, uint32_t shift, uint32_t *dist_dev, uint64_t *pos_dev, void *stream);
 
 /*
- * Circuit privacy (Sec. 2, "Additive Homomorphic Encryption": the AHE scheme
+ * Circuit privacy (Sec. 2.3, "Additive Homomorphic Encryption": the AHE scheme
  * must not reveal the server's operations beyond the decrypted message; the
  * paper obtains this by noise flooding, with 108 bits of statistical circuit
  * privacy at its parameters, Sec. 7.1).  Private-key BFV leaves the server

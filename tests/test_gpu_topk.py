@@ -25,8 +25,6 @@ def ctx():
 @pytest.mark.parametrize("n,spread", [(100_003, 50), (70_000, 1 << 24), (33, 5)])
 @pytest.mark.parametrize("k", [1, 10, 32, 33, 88, 1024])   # > 32: the shared-memory sort path
 def test_topk_matches_oracle(ctx, n, spread, k):
-    if k > n:
-        pytest.skip("k > n")
     t = ctx.query()["t"]
     rnd = np.random.default_rng(n + k)
     B = 3
@@ -34,6 +32,12 @@ def test_topk_matches_oracle(ctx, n, spread, k):
     srv = rnd.integers(0, t, size=(B, n)).astype(np.int64)
     cli = (dist - srv) % t
     cli_d, srv_d = cu(cli.astype(np.uint32)), cu(srv.astype(np.uint32))
+    if k > n:   # fewer elements than winners: rejected on the host, nothing launched
+        for bins in (0, n):
+            with pytest.raises(S.SannsError) as e:
+                S.sanns_topk(ctx, cli_d, srv_d, k, bins)
+            assert e.value.code == -1
+        return
     pos = np.arange(n)
     for bins in sorted({0, max(k, n // 128), max(k, n // 7), n}):
         for shift in (0, 3):
