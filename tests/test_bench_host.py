@@ -44,3 +44,10 @@ def test_roofline_helpers():
     rep = b._ntt_report(738, 8192, 0.5, "x")
     assert abs(rep["polys_per_s"] - 738 / 0.5e-3) < 1e-6
     assert abs(rep["hbm_gbs"] - 16 * 8192 * 738 / 0.5e-3 / 1e9) < 1e-9
+
+
+def test_all_cores_baseline_uses_every_core():
+    b = _bench_module()
+    r = b.cpu_baseline_all_cores(quick=True)
+    assert r["kind"] == "oracle" and r["value"] > 0
+    assert r["cores"] == max(1, min(len(os.sched_getaffinity(0)), 64))
