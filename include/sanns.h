@@ -143,6 +143,21 @@ int sanns_encrypt_query(sanns_ctx *ctx, const sanns_sk *sk, const uint8_t *q_dev
                         void *stream);
 
 /*
+ * Seeded query ciphertexts (the paper has no counterpart: its client sends
+ * both components).  c1 = a of sanns_encrypt_query is the output of the
+ * stream (seed, 2, qid << 16 | j << 12 | i), so a client may send c0 alone
+ * with the seed and the query ids, halving the upload, and the server
+ * rebuilds the ciphertext: ct_in_dev[b][i][0] = c0_dev[b][i] and
+ * ct_in_dev[b][i][1] = a, bit-identical to sanns_encrypt_query's output for
+ * the same (seed, qids).  c0_dev: [B][d][L][N] (component 0 of each
+ * coordinate, NTT form); qids_dev: uint64 [B]; ct_in_dev output
+ * [B][d][2][L][N].  The two buffers must not overlap; B <= 65535; SANNS_EINVAL
+ * otherwise.  Asynchronous on stream.
+ */
+int sanns_expand_query(sanns_ctx *ctx, const uint64_t *c0_dev, uint32_t B, uint64_t seed,
+                       const uint64_t *qids_dev, uint64_t *ct_in_dev, void *stream);
+
+/*
  * The server's distance step (Pi_ls step 3) for B queries against one
  * encoded database:
  *   acc[b][k][c][j][s] = sum_i ct_in[b][i][c][j][s] pt[k][j][i][s]  mod q_j

@@ -376,6 +376,22 @@ int sanns_encrypt_query(sanns_ctx* ctx, const sanns_sk* sk, const uint8_t* qv, u
   return SANNS_OK;
 }
 
+int sanns_expand_query(sanns_ctx* ctx, const uint64_t* c0, uint32_t B, uint64_t seed,
+                       const uint64_t* qids, uint64_t* ct, void* stream) {
+  if (!ctx) return fail(SANNS_EINVAL, "ctx is NULL");
+  if (B == 0) return SANNS_OK;
+  if (!c0 || !qids || !ct) return fail(SANNS_EINVAL, "NULL buffer");
+  if (B > 65535) return fail(SANNS_EINVAL, "B must be <= 65535");
+  const uint64_t words = (uint64_t)B * ctx->params.d * ctx->P.L * ctx->P.N;
+  const uintptr_t a0 = reinterpret_cast<uintptr_t>(c0), a1 = a0 + 8 * words;
+  const uintptr_t b0 = reinterpret_cast<uintptr_t>(ct), b1 = b0 + 16 * words;
+  if (a0 < b1 && b0 < a1) return fail(SANNS_EINVAL, "c0 and ct_in overlap");
+  int rc = check_device(ctx);
+  if (rc) return rc;
+  SANNS_CUDA(launch_seeded_query(ctx->P, c0, B, ctx->params.d, seed, qids, ct, as_stream(stream)));
+  return SANNS_OK;
+}
+
 namespace {
 int check_distance_args(sanns_ctx* ctx, const sanns_db* db, uint32_t B) {
   if (!ctx || !db) return fail(SANNS_EINVAL, "ctx or db is NULL");

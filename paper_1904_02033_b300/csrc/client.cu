@@ -91,6 +91,33 @@ __global__ void __launch_bounds__(512) encrypt_kernel(PrimeSet P, const uint64_t
   }
 }
 
+// Seeded query ciphertexts: the server rebuilds c1 = a from the same stream
+// as encrypt_kernel and places the received c0 beside it.  One block per
+// (i, j, b); c0_in is [B][d][L][N], ct is [B][d][2][L][N].
+__global__ void __launch_bounds__(256) seeded_query_kernel(PrimeSet P, const uint64_t* __restrict__ c0_in,
+                                                           uint32_t d, uint64_t seed,
+                                                           const uint64_t* __restrict__ qids,
+                                                           uint64_t* __restrict__ ct) {
+  const uint32_t N = P.N, L = P.L;
+  const uint32_t i = blockIdx.x, j = blockIdx.y, b = blockIdx.z;
+  const uint64_t q = P.q[j];
+  const uint64_t a_obj = (qids[b] << 16) | ((uint64_t)j << 12) | i;
+  const uint64_t* src = c0_in + (((size_t)b * d + i) * L + j) * N;
+  uint64_t* c0 = ct + ((((size_t)b * d + i) * 2 + 0) * L + j) * N;
+  uint64_t* c1 = ct + ((((size_t)b * d + i) * 2 + 1) * L + j) * N;
+  for (uint32_t x = threadIdx.x; x < N; x += blockDim.x) c0[x] = src[x];
+  for (uint32_t u = threadIdx.x; u < N / 4; u += blockDim.x) {
+    uint32_t blk[16];
+    chacha20_block(seed, kPurposeA, a_obj, u, blk);
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      uint64_t lo, hi;
+      draw_pair(blk, v, lo, hi);
+      c1[4 * u + v] = mod_q128(lo, hi, q);
+    }
+  }
+}
+
 // Decryption, first half: one block per (b, k, j): v = c0 + INTT(NTT(c1) s_hat)
 // for coefficient-form responses, v = INTT(c0 + c1 s_hat) for NTT-form ones.
 __global__ void __launch_bounds__(512) decrypt_phase_kernel(PrimeSet P, const uint64_t* __restrict__ ct_out,
@@ -228,6 +255,14 @@ cudaError_t launch_encrypt(const PrimeSet& P, const uint64_t* s_hat, const uint6
   dim3 grid(d, P.L, B);
   encrypt_kernel<<<grid, blk_threads(P.N), smem, st>>>(P, s_hat, s_hat_shoup, qv, d, seed, qids,
                                                        ct);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_seeded_query(const PrimeSet& P, const uint64_t* c0, uint32_t B, uint32_t d,
+                                uint64_t seed, const uint64_t* qids, uint64_t* ct, cudaStream_t st) {
+  if (B == 0) return cudaSuccess;
+  dim3 grid(d, P.L, B);
+  seeded_query_kernel<<<grid, 256, 0, st>>>(P, c0, d, seed, qids, ct);
   return cudaGetLastError();
 }
 

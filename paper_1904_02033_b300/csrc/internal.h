@@ -114,6 +114,8 @@ cudaError_t launch_keygen(const PrimeSet& P, uint64_t seed, int8_t* s, uint64_t*
 cudaError_t launch_encrypt(const PrimeSet& P, const uint64_t* s_hat, const uint64_t* s_hat_shoup,
                            const uint8_t* qv, uint32_t B, uint32_t d, uint64_t seed,
                            const uint64_t* qids, uint64_t* ct, cudaStream_t st);
+cudaError_t launch_seeded_query(const PrimeSet& P, const uint64_t* c0, uint32_t B, uint32_t d,
+                                uint64_t seed, const uint64_t* qids, uint64_t* ct, cudaStream_t st);
 cudaError_t launch_encode(const PrimeSet& P, const PrimeSet* PT, const uint8_t* coords, uint64_t n_points,
                           const uint32_t* perm, uint64_t n, uint32_t d, uint64_t K, uint64_t* pt,
                           uint32_t* norms, int* bad, cudaStream_t st);

@@ -45,6 +45,7 @@ _SIGS = {
     "sanns_db_set_position_base": ([_VP, C.c_uint64], C.c_int),
     "sanns_db_export": ([_VP, C.c_uint64, C.c_uint64, _VP, _VP, _VP], C.c_int),
     "sanns_encrypt_query": ([_VP, _VP, _VP, C.c_uint32, C.c_uint64, _VP, _VP, _VP], C.c_int),
+    "sanns_expand_query": ([_VP, _VP, C.c_uint32, C.c_uint64, _VP, _VP, _VP], C.c_int),
     "sanns_distances": ([_VP, _VP, _VP, C.c_uint32, C.c_uint64, _VP, _VP, _VP, _VP], C.c_int),
     "sanns_distances_mac": ([_VP, _VP, _VP, C.c_uint32, _VP, _VP], C.c_int),
     "sanns_distances_finish": ([_VP, _VP, C.c_uint32, C.c_uint64, _VP, _VP, _VP, _VP], C.c_int),
@@ -242,6 +243,21 @@ def sanns_encrypt_query(ctx: Context, sk: SecretKey, q: torch.Tensor, seed: int,
         out = torch.empty((B, ctx.d, 2, ctx.L, ctx.N), dtype=torch.uint64, device="cuda")
     _check(load().sanns_encrypt_query(ctx.handle, sk.handle, _ptr(q), B, seed, _ptr(qids),
                                       _ptr(out), _stream(stream)))
+    return out
+
+
+def sanns_expand_query(ctx: Context, c0: torch.Tensor, seed: int, qids: torch.Tensor,
+                       out: torch.Tensor | None = None, stream=None):
+    """Rebuild query ciphertexts [B][d][2][L][N] from their c0 components
+    [B][d][L][N] and the encryption seed (c1 is the seed's stream)."""
+    assert c0.dtype == torch.uint64 and c0.is_contiguous()
+    B = c0.shape[0]
+    assert c0.shape == (B, ctx.d, ctx.L, ctx.N)
+    assert qids.dtype == torch.uint64 and qids.numel() == B
+    if out is None:
+        out = torch.empty((B, ctx.d, 2, ctx.L, ctx.N), dtype=torch.uint64, device="cuda")
+    _check(load().sanns_expand_query(ctx.handle, _ptr(c0), B, seed, _ptr(qids), _ptr(out),
+                                     _stream(stream)))
     return out
 
 

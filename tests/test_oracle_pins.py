@@ -815,3 +815,20 @@ def test_maximum_flooding_still_decrypts_worst_case_distances(cfg):
         m = O.scale_round(O.decrypt_phase(out, s))
         noise = max(O.phase_noise(out, s, m))
         assert 2 ** (F - 2) <= noise < O.P.delta // 2
+
+
+def test_encryption_c1_is_the_documented_stream():
+    # c1 = a, drawn directly in NTT form: slot s of prime j, coordinate i is
+    # (hi 2^64 + lo) mod q_j of draw s of stream (seed, 2, qid 2^16 + j 2^12 + i)
+    N, L, bits, d = 64, 2, 40, 3
+    O = Oracle(N, L, bits, 0, d)
+    s, s_hat = O.keygen(91)
+    seed, qid = 92, 6
+    ct = O.encrypt(s_hat, inputs.uniform_coords(1, d, 93)[0], seed, qid)
+    for i in range(d):
+        for j, qj in enumerate(int(x) for x in O.q):
+            want = []
+            for x in range(N):
+                lo, hi = O.draw128(seed, 2, (qid << 16) | (j << 12) | i, x)
+                want.append(((hi << 64) | lo) % qj)
+            assert [int(v) for v in ct[i, 1, j]] == want, (i, j)
