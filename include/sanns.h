@@ -9,8 +9,9 @@
  * - Buffers named *_dev are device memory of the current CUDA device (for
  *   instance a torch tensor's data_ptr()); *_host are host memory; "any" means
  *   either (copied with cudaMemcpyDefault).  The caller owns every buffer it
- *   passes; opaque handles (sanns_ctx, sanns_sk, sanns_db, sanns_clusters) are
- *   owned by the library and released with the matching sanns_*_free.
+ *   passes; opaque handles (sanns_ctx, sanns_sk, sanns_db, sanns_clusters,
+ *   sanns_gather_batch) are owned by the library and released with the
+ *   matching sanns_*_free.
  * - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
  *   Calls enqueue work on it and return without synchronising unless stated;
  *   buffers must stay alive until the stream has passed the call.
@@ -55,6 +56,7 @@ typedef struct sanns_ctx sanns_ctx;
 typedef struct sanns_sk sanns_sk;
 typedef struct sanns_db sanns_db;
 typedef struct sanns_clusters sanns_clusters;
+typedef struct sanns_gather_batch sanns_gather_batch;
 
 /*
  * BFV parameters (Sec. 7.1 "Parameter choices": N = 2^13, 180-bit q as three
@@ -236,6 +238,27 @@ int sanns_distances_gather(sanns_ctx *ctx, const sanns_clusters *cl, const uint6
                            uint32_t B, const uint32_t *probes_host, uint32_t P, uint64_t mask_seed,
                            const uint64_t *qids_dev, uint64_t *ct_out_dev, uint32_t *srv_share_dev,
                            uint32_t *ids_dev, void *stream);
+
+/*
+ * The same gather in two steps, for batches whose probes repeat and for CUDA
+ * graph capture (the paper has no counterpart: its server handles one query
+ * at a time).  sanns_gather_prepare plans the batch of probes_host (B x P,
+ * host) and uploads the plan once (synchronous; the clusters must outlive
+ * the batch).  sanns_distances_gather_prepared then computes exactly what
+ * sanns_distances_gather computes for those probes, with the same output
+ * layout (sizes from sanns_gather_plan); it only enqueues kernels and
+ * stream-ordered scratch on stream, so it may be captured into a graph and
+ * replayed (with new ciphertexts and query ids in the same buffers).  B in
+ * 1..65535 and the other bounds of sanns_distances_gather; SANNS_EINVAL
+ * otherwise.
+ */
+int sanns_gather_prepare(sanns_ctx *ctx, const sanns_clusters *cl, const uint32_t *probes_host,
+                         uint32_t B, uint32_t P, sanns_gather_batch **out);
+void sanns_gather_batch_free(sanns_gather_batch *batch);
+int sanns_distances_gather_prepared(sanns_ctx *ctx, const sanns_gather_batch *batch,
+                                    const uint64_t *ct_in_dev, uint64_t mask_seed,
+                                    const uint64_t *qids_dev, uint64_t *ct_out_dev,
+                                    uint32_t *srv_share_dev, uint32_t *ids_dev, void *stream);
 
 /*
  * Launch variants of the MAC kernel (slots per lane, loads in flight, CTAs

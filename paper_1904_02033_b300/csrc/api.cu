@@ -723,6 +723,60 @@ int sanns_distances_gather(sanns_ctx* ctx, const sanns_clusters* cl, const uint6
   return SANNS_OK;
 }
 
+int sanns_gather_prepare(sanns_ctx* ctx, const sanns_clusters* cl, const uint32_t* probes, uint32_t B,
+                         uint32_t P, sanns_gather_batch** out) {
+  if (!out) return fail(SANNS_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!ctx || !cl) return fail(SANNS_EINVAL, "ctx or clusters is NULL");
+  if (cl->ctx != ctx) return fail(SANNS_EINVAL, "clusters belong to another context");
+  if (ctx->P.N > 8192) return fail(SANNS_EINVAL, "the gather path supports N <= 8192");
+  if (B == 0 || B > 65535) return fail(SANNS_EINVAL, "B must be in 1..65535");
+  if (!probes) return fail(SANNS_EINVAL, "probes is NULL");
+  sanns_gather_batch* gb = new sanns_gather_batch();
+  gb->ctx = ctx;
+  gb->cl = cl;
+  gb->B = B;
+  gb->P = P;
+  gb->n_b.assign(B, 0);
+  gb->k_b.assign(B, 0);
+  int rc = sanns_gather_plan(cl, probes, B, P, gb->n_b.data(), gb->k_b.data());
+  uint64_t W = 0;
+  for (uint32_t b = 0; rc == 0 && b < B; ++b) W += gb->k_b[b];
+  if (rc == 0 && (W * 2 * ctx->P.L > 0x7fffffffull || W * ctx->P.N > (1ull << 40)))
+    rc = fail(SANNS_EINVAL, "batch too large");
+  if (rc == 0) rc = check_device(ctx);
+  if (rc == 0) {
+    const cudaError_t e = gather_prepare(ctx->P.N, probes, gb);
+    if (e != cudaSuccess) rc = cuda_fail(e, "upload the gather plan");
+  }
+  if (rc) {
+    delete gb;
+    return rc;
+  }
+  *out = gb;
+  return SANNS_OK;
+}
+
+void sanns_gather_batch_free(sanns_gather_batch* gb) {
+  if (!gb) return;
+  if (gb->d_tables) cudaFree(gb->d_tables);
+  delete gb;
+}
+
+int sanns_distances_gather_prepared(sanns_ctx* ctx, const sanns_gather_batch* gb, const uint64_t* ct_in,
+                                    uint64_t mask_seed, const uint64_t* qids, uint64_t* ct_out,
+                                    uint32_t* srv_share, uint32_t* ids, void* stream) {
+  if (!ctx || !gb) return fail(SANNS_EINVAL, "ctx or batch is NULL");
+  if (gb->ctx != ctx) return fail(SANNS_EINVAL, "the batch belongs to another context");
+  if (!ct_in || !qids || !ct_out || !srv_share) return fail(SANNS_EINVAL, "NULL buffer");
+  int rc = check_device(ctx);
+  if (rc) return rc;
+  SANNS_CUDA(launch_gather_prepared(ctx->P, ctx->params.d, gb, ct_in, mask_seed, qids, ct_out, srv_share, ids,
+                                    ctx->sms, ctx->slots ? &ctx->PT : nullptr, ctx->d_pk, ctx->d_pk_shoup,
+                                    ctx->flood_bits, ctx->privacy, ctx->ntt_responses, as_stream(stream)));
+  return SANNS_OK;
+}
+
 int sanns_db_prepare_batched(sanns_ctx* ctx, sanns_db* db, void* stream) {
   if (!ctx || !db) return fail(SANNS_EINVAL, "ctx or db is NULL");
   if (db->ctx != ctx) return fail(SANNS_EINVAL, "db belongs to another context");

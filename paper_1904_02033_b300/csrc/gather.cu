@@ -363,41 +363,76 @@ cudaError_t launch_check_indices(const uint32_t* idx, uint64_t m, uint64_t bound
 
 int gather_threads(uint32_t N) { return N >= 512 ? 256 : (int)(N / 2); }
 
-cudaError_t launch_gather(const PrimeSet& P, uint32_t d, const sanns_clusters* cl,
-                          const uint64_t* ct_in, uint32_t B, const uint32_t* probes_host,
-                          uint32_t Pr, const uint64_t* n_b, uint64_t mask_seed,
-                          const uint64_t* qids, uint64_t* ct_out, uint32_t* srv_share,
-                          uint32_t* ids, int sms, const PrimeSet* PT, const uint64_t* pk,
-                          const uint64_t* pks, uint32_t F, const PrivacyConsts& C, bool ntt_form,
-                          cudaStream_t st) {
-  const uint32_t N = P.N;
-  // host plan: items (query-major), per-query offsets, probe segments
+namespace {
+
+// Host plan of one gather: items (query-major), per-query offsets and the
+// probe segments of every query's list.
+struct PlanHost {
   std::vector<GatherItem> items;
-  std::vector<GatherQuery> qs(B);
-  std::vector<uint64_t> seg((size_t)B * (Pr + 1));
+  std::vector<GatherQuery> qs;
+  std::vector<uint64_t> seg;
+};
+
+void build_plan(uint32_t N, const sanns_clusters* cl, const uint32_t* probes_host, uint32_t B,
+                uint32_t Pr, const uint64_t* n_b, PlanHost& H) {
+  H.qs.assign(B, GatherQuery{0, 0});
+  H.seg.assign((size_t)B * (Pr + 1), 0);
   uint64_t blk = 0, pos = 0;
   for (uint32_t b = 0; b < B; ++b) {
     uint64_t acc = 0;
     for (uint32_t p = 0; p < Pr; ++p) {
-      seg[(size_t)b * (Pr + 1) + p] = acc;
+      H.seg[(size_t)b * (Pr + 1) + p] = acc;
       const uint32_t c = probes_host[(size_t)b * Pr + p];
       acc += cl->h_offsets[c + 1] - cl->h_offsets[c];
     }
-    seg[(size_t)b * (Pr + 1) + Pr] = acc;
-    qs[b].n = n_b[b];
-    qs[b].pos_off = pos;
+    H.seg[(size_t)b * (Pr + 1) + Pr] = acc;
+    H.qs[b].n = n_b[b];
+    H.qs[b].pos_off = pos;
     const uint64_t Kb = (n_b[b] + N - 1) / N;
-    for (uint64_t k = 0; k < Kb; ++k) items.push_back(GatherItem{b, (uint32_t)k, blk + k});
+    for (uint64_t k = 0; k < Kb; ++k) H.items.push_back(GatherItem{b, (uint32_t)k, blk + k});
     blk += Kb;
     pos += n_b[b];
   }
-  const uint64_t W = items.size();
-  if (W == 0) return cudaSuccess;
-  // one stream-ordered scratch allocation: tables + packed coordinates + norms
-  const size_t sz_items = sizeof(GatherItem) * W, sz_qs = sizeof(GatherQuery) * B;
-  const size_t sz_seg = sizeof(uint64_t) * seg.size(), sz_pr = sizeof(uint32_t) * (size_t)B * Pr;
-  auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
-  const size_t o_items = 0, o_qs = up(sz_items), o_seg = o_qs + up(sz_qs), o_pr = o_seg + up(sz_seg);
+}
+
+size_t up256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// Offsets of the plan tables in one allocation; returns its size.
+size_t plan_layout(uint64_t W, uint32_t B, uint32_t Pr, size_t& o_items, size_t& o_qs, size_t& o_seg,
+                   size_t& o_pr) {
+  o_items = 0;
+  o_qs = up256(sizeof(GatherItem) * W);
+  o_seg = o_qs + up256(sizeof(GatherQuery) * B);
+  o_pr = o_seg + up256(sizeof(uint64_t) * (size_t)B * (Pr + 1));
+  return o_pr + up256(sizeof(uint32_t) * (size_t)B * Pr);
+}
+
+cudaError_t upload_plan(uint8_t* tables, const PlanHost& H, const uint32_t* probes_host, uint32_t B,
+                        uint32_t Pr, size_t o_items, size_t o_qs, size_t o_seg, size_t o_pr,
+                        cudaStream_t st) {
+  cudaError_t e = cudaMemcpyAsync(tables + o_items, H.items.data(), sizeof(GatherItem) * H.items.size(),
+                                  cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(tables + o_qs, H.qs.data(), sizeof(GatherQuery) * B, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(tables + o_seg, H.seg.data(), sizeof(uint64_t) * H.seg.size(), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(tables + o_pr, probes_host, sizeof(uint32_t) * (size_t)B * Pr, cudaMemcpyHostToDevice, st);
+  // the host vectors must outlive the copies
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  return e;
+}
+
+// The launches of one gather over an uploaded plan: a stream-ordered scratch
+// allocation (packed coordinates, norms, partial sums, tickets) and the
+// kernels, nothing that waits on the host.
+cudaError_t gather_kernels(const PrimeSet& P, uint32_t d, const sanns_clusters* cl, const uint8_t* tables,
+                           size_t o_items, size_t o_qs, size_t o_seg, size_t o_pr, uint64_t W,
+                           uint32_t Pr, const uint64_t* ct_in, uint64_t mask_seed, const uint64_t* qids,
+                           uint64_t* ct_out, uint32_t* srv_share, uint32_t* ids, int sms, const PrimeSet* PT,
+                           const uint64_t* pk, const uint64_t* pks, uint32_t F, const PrivacyConsts& C,
+                           bool ntt_form, cudaStream_t st) {
+  const uint32_t N = P.N;
   // dimension slices per (item, prime): about four units per multiprocessor
   // in all, at least one dimension per slice, and at most kMaxSlices: the
   // finishing block reads every slice's partial (2 N words each), so more
@@ -409,26 +444,24 @@ cudaError_t launch_gather(const PrimeSet& P, uint32_t d, const sanns_clusters* c
   const uint32_t S0 = (uint32_t)(want < d ? want : d);
   const uint32_t ds = (d + S0 - 1) / S0;
   const uint32_t S = (d + ds - 1) / ds;
-  const size_t o_norm = o_pr + up(sz_pr), o_gco = o_norm + up(sizeof(uint32_t) * W * N);
-  const size_t o_part = o_gco + up((size_t)W * d * N);
-  const size_t o_tick = o_part + up(sizeof(uint64_t) * (size_t)W * P.L * S * 2 * N);
-  const size_t total = o_tick + up(sizeof(uint32_t) * (size_t)W * P.L);
-  uint8_t* scratch = nullptr;
-  cudaError_t e = cudaMallocAsync(&scratch, total, st);
+  const size_t o_norm = 0, o_gco = up256(sizeof(uint32_t) * W * N);
+  const size_t o_part = o_gco + up256((size_t)W * d * N);
+  const size_t o_tick = o_part + up256(sizeof(uint64_t) * (size_t)W * P.L * S * 2 * N);
+  const size_t total = o_tick + up256(sizeof(uint32_t) * (size_t)W * P.L);
+  const size_t smem = sizeof(uint64_t) * ntt_smem_words(N);
+  cudaError_t e = ensure_smem_attr((const void*)gather_kernel, smem);
+  if (e == cudaSuccess && PT) e = ensure_smem_attr((const void*)gather_slot_share_kernel, smem);
   if (e != cudaSuccess) return e;
-  e = cudaMemcpyAsync(scratch + o_items, items.data(), sz_items, cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(scratch + o_qs, qs.data(), sz_qs, cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(scratch + o_seg, seg.data(), sz_seg, cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(scratch + o_pr, probes_host, sz_pr, cudaMemcpyHostToDevice, st);
-  // the host vectors must outlive the copies
-  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-  const GatherItem* d_items = reinterpret_cast<const GatherItem*>(scratch + o_items);
-  const GatherQuery* d_qs = reinterpret_cast<const GatherQuery*>(scratch + o_qs);
-  if (e == cudaSuccess) {
+  uint8_t* scratch = nullptr;
+  e = cudaMallocAsync(&scratch, total, st);
+  if (e != cudaSuccess) return e;
+  const GatherItem* d_items = reinterpret_cast<const GatherItem*>(tables + o_items);
+  const GatherQuery* d_qs = reinterpret_cast<const GatherQuery*>(tables + o_qs);
+  {
     const uint64_t threads = W * N;
     pack_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(
-        N, d, W, d_items, d_qs, reinterpret_cast<const uint64_t*>(scratch + o_seg),
-        reinterpret_cast<const uint32_t*>(scratch + o_pr), Pr, cl->d_offsets, cl->d_members,
+        N, d, W, d_items, d_qs, reinterpret_cast<const uint64_t*>(tables + o_seg),
+        reinterpret_cast<const uint32_t*>(tables + o_pr), Pr, cl->d_offsets, cl->d_members,
         cl->d_coords, scratch + o_gco, reinterpret_cast<uint32_t*>(scratch + o_norm), ids);
     e = cudaGetLastError();
   }
@@ -451,29 +484,78 @@ cudaError_t launch_gather(const PrimeSet& P, uint32_t d, const sanns_clusters* c
   if (e == cudaSuccess) e = cudaMemsetAsync(tickets, 0, sizeof(uint32_t) * (size_t)W * P.L, st);
   if (e == cudaSuccess) {
     const int th = gather_threads(N);
-    const size_t smem = sizeof(uint64_t) * ntt_smem_words(N);
     const uint64_t units = W * P.L * S;
     const uint64_t slots = 3 * nsm;  // three blocks per multiprocessor
     const unsigned grid = (unsigned)(units < slots ? units : slots);
-    e = cudaFuncSetAttribute(gather_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e == cudaSuccess) {
-      gather_kernel<<<grid, th, smem, st>>>(P, d, W, S, ds, d_items, d_qs, scratch + o_gco,
-                                            reinterpret_cast<const uint32_t*>(scratch + o_norm), ct_in,
-                                            mask_seed, qids, part, tickets, ct_out, srv_share, O);
-      e = cudaGetLastError();
-    }
+    gather_kernel<<<grid, th, smem, st>>>(P, d, W, S, ds, d_items, d_qs, scratch + o_gco,
+                                          reinterpret_cast<const uint32_t*>(scratch + o_norm), ct_in,
+                                          mask_seed, qids, part, tickets, ct_out, srv_share, O);
+    e = cudaGetLastError();
   }
   if (e == cudaSuccess && PT) {
-    const size_t smem = sizeof(uint64_t) * ntt_smem_words(N);
-    e = cudaFuncSetAttribute(gather_slot_share_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e == cudaSuccess) {
-      gather_slot_share_kernel<<<(unsigned)W, gather_threads(N), smem, st>>>(P, *PT, d_items, d_qs, mask_seed,
-                                                                             qids, srv_share);
-      e = cudaGetLastError();
-    }
+    gather_slot_share_kernel<<<(unsigned)W, gather_threads(N), smem, st>>>(P, *PT, d_items, d_qs, mask_seed,
+                                                                           qids, srv_share);
+    e = cudaGetLastError();
   }
   cudaError_t e2 = cudaFreeAsync(scratch, st);
   return e != cudaSuccess ? e : e2;
+}
+
+}  // namespace
+
+cudaError_t launch_gather(const PrimeSet& P, uint32_t d, const sanns_clusters* cl,
+                          const uint64_t* ct_in, uint32_t B, const uint32_t* probes_host,
+                          uint32_t Pr, const uint64_t* n_b, uint64_t mask_seed,
+                          const uint64_t* qids, uint64_t* ct_out, uint32_t* srv_share,
+                          uint32_t* ids, int sms, const PrimeSet* PT, const uint64_t* pk,
+                          const uint64_t* pks, uint32_t F, const PrivacyConsts& C, bool ntt_form,
+                          cudaStream_t st) {
+  PlanHost H;
+  build_plan(P.N, cl, probes_host, B, Pr, n_b, H);
+  const uint64_t W = H.items.size();
+  if (W == 0) return cudaSuccess;
+  size_t o_items, o_qs, o_seg, o_pr;
+  const size_t bytes = plan_layout(W, B, Pr, o_items, o_qs, o_seg, o_pr);
+  uint8_t* tables = nullptr;
+  cudaError_t e = cudaMallocAsync(&tables, bytes, st);
+  if (e != cudaSuccess) return e;
+  e = upload_plan(tables, H, probes_host, B, Pr, o_items, o_qs, o_seg, o_pr, st);
+  if (e == cudaSuccess)
+    e = gather_kernels(P, d, cl, tables, o_items, o_qs, o_seg, o_pr, W, Pr, ct_in, mask_seed, qids, ct_out,
+                       srv_share, ids, sms, PT, pk, pks, F, C, ntt_form, st);
+  cudaError_t e2 = cudaFreeAsync(tables, st);
+  return e != cudaSuccess ? e : e2;
+}
+
+cudaError_t gather_prepare(uint32_t N, const uint32_t* probes_host, sanns_gather_batch* gb) {
+  PlanHost H;
+  build_plan(N, gb->cl, probes_host, gb->B, gb->P, gb->n_b.data(), H);
+  gb->W = H.items.size();
+  gb->d_tables = nullptr;
+  if (gb->W == 0) return cudaSuccess;
+  const size_t bytes = plan_layout(gb->W, gb->B, gb->P, gb->o_items, gb->o_qs, gb->o_seg, gb->o_pr);
+  cudaError_t e = cudaMalloc(&gb->d_tables, bytes);
+  if (e != cudaSuccess) {
+    gb->d_tables = nullptr;
+    return e;
+  }
+  e = upload_plan(gb->d_tables, H, probes_host, gb->B, gb->P, gb->o_items, gb->o_qs, gb->o_seg, gb->o_pr,
+                  nullptr);
+  if (e != cudaSuccess) {
+    cudaFree(gb->d_tables);
+    gb->d_tables = nullptr;
+  }
+  return e;
+}
+
+cudaError_t launch_gather_prepared(const PrimeSet& P, uint32_t d, const sanns_gather_batch* gb,
+                                   const uint64_t* ct_in, uint64_t mask_seed, const uint64_t* qids,
+                                   uint64_t* ct_out, uint32_t* srv_share, uint32_t* ids, int sms,
+                                   const PrimeSet* PT, const uint64_t* pk, const uint64_t* pks, uint32_t F,
+                                   const PrivacyConsts& C, bool ntt_form, cudaStream_t st) {
+  if (gb->W == 0) return cudaSuccess;
+  return gather_kernels(P, d, gb->cl, gb->d_tables, gb->o_items, gb->o_qs, gb->o_seg, gb->o_pr, gb->W, gb->P,
+                        ct_in, mask_seed, qids, ct_out, srv_share, ids, sms, PT, pk, pks, F, C, ntt_form, st);
 }
 
 }  // namespace sanns

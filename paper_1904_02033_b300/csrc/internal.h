@@ -62,6 +62,19 @@ struct sanns_clusters {
   std::vector<uint64_t> h_offsets;
 };
 
+// A prepared gather batch: the plan of one sanns_distances_gather call (work
+// items, per-query offsets, probe segments and the probes) uploaded once, so
+// that the launches over it are kernels and stream-ordered scratch only.
+struct sanns_gather_batch {
+  const sanns_ctx* ctx;
+  const sanns_clusters* cl;
+  uint32_t B, P;
+  uint64_t W;               // work items (blocks of the gathered lists)
+  std::vector<uint64_t> n_b, k_b;  // gathered points and blocks per query
+  uint8_t* d_tables;        // items | queries | segments | probes, or NULL when W = 0
+  size_t o_items, o_qs, o_seg, o_pr;
+};
+
 namespace sanns {
 
 // error reporting (thread-local message)
@@ -140,6 +153,12 @@ cudaError_t launch_gather(const PrimeSet& P, uint32_t d, const sanns_clusters* c
                           uint32_t* ids, int sms, const PrimeSet* PT, const uint64_t* pk,
                           const uint64_t* pks, uint32_t F, const PrivacyConsts& C, bool ntt_form,
                           cudaStream_t st);
+cudaError_t gather_prepare(uint32_t N, const uint32_t* probes_host, sanns_gather_batch* gb);
+cudaError_t launch_gather_prepared(const PrimeSet& P, uint32_t d, const sanns_gather_batch* gb,
+                                   const uint64_t* ct_in, uint64_t mask_seed, const uint64_t* qids,
+                                   uint64_t* ct_out, uint32_t* srv_share, uint32_t* ids, int sms,
+                                   const PrimeSet* PT, const uint64_t* pk, const uint64_t* pks, uint32_t F,
+                                   const PrivacyConsts& C, bool ntt_form, cudaStream_t st);
 cudaError_t launch_norms_slot(const PrimeSet& PT, uint32_t* norms, uint64_t K, cudaStream_t st);
 cudaError_t launch_join30(const uint64_t* src, uint64_t* dst, uint64_t count, cudaStream_t st);
 size_t batched_limb_bytes(uint32_t L, uint32_t N, uint64_t K, uint32_t d);

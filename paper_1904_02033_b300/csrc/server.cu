@@ -503,7 +503,7 @@ cudaError_t launch_join30(const uint64_t* src, uint64_t* dst, uint64_t count, cu
 cudaError_t launch_norms_slot(const PrimeSet& PT, uint32_t* norms, uint64_t K, cudaStream_t st) {
   if (K == 0) return cudaSuccess;
   const size_t smem = sizeof(uint64_t) * ntt_smem_words(PT.N);
-  cudaError_t e = cudaFuncSetAttribute(norms_slot_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = ensure_smem_attr((const void*)norms_slot_kernel, smem);
   if (e != cudaSuccess) return e;
   norms_slot_kernel<<<(unsigned)K, ntt_threads(PT.N), smem, st>>>(PT, norms);
   return cudaGetLastError();

@@ -55,6 +55,9 @@ _SIGS = {
     "sanns_gather_plan": ([_VP, _VP, C.c_uint32, C.c_uint32, _VP, _VP], C.c_int),
     "sanns_distances_gather": ([_VP, _VP, _VP, C.c_uint32, _VP, C.c_uint32, C.c_uint64, _VP, _VP,
                                 _VP, _VP, _VP], C.c_int),
+    "sanns_gather_prepare": ([_VP, _VP, _VP, C.c_uint32, C.c_uint32, C.POINTER(_VP)], C.c_int),
+    "sanns_gather_batch_free": ([_VP], None),
+    "sanns_distances_gather_prepared": ([_VP, _VP, _VP, C.c_uint64, _VP, _VP, _VP, _VP, _VP], C.c_int),
     "sanns_decrypt_shares_noalloc": ([_VP, _VP, _VP, C.c_uint32, C.c_uint64, _VP, _VP, _VP],
                                      C.c_int),
     "sanns_decrypt_noalloc_max_words": ([], C.c_uint64),
@@ -358,6 +361,45 @@ def sanns_distances_gather(ctx: Context, cl: Clusters, ct_in: torch.Tensor, prob
                                          pr.ctypes.data_as(C.c_void_p), P, mask_seed, _ptr(qids),
                                          _ptr(ct_out), _ptr(srv), _ptr(ids), _stream(stream)))
     return ct_out[:tot_k], srv[:tot_n], (ids[:tot_n] if with_ids else None), n_b, k_b
+
+
+class GatherBatch:
+    def __init__(self, handle, ctx, cl, n_b, k_b):
+        self.handle, self.ctx, self.cl, self.n_b, self.k_b = handle, ctx, cl, n_b, k_b
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _LIB is not None:
+            _LIB.sanns_gather_batch_free(self.handle)
+            self.handle = None
+
+
+def sanns_gather_prepare(ctx: Context, cl: Clusters, probes) -> GatherBatch:
+    """Plan and upload one batch of probes (B x P, host) once."""
+    import numpy as np
+    pr = np.ascontiguousarray(probes, dtype=np.uint32)
+    B, P = pr.shape
+    n_b, k_b = sanns_gather_plan(cl, pr)
+    h = _VP()
+    _check(load().sanns_gather_prepare(ctx.handle, cl.handle, pr.ctypes.data_as(C.c_void_p), B, P,
+                                       C.byref(h)))
+    return GatherBatch(h, ctx, cl, n_b, k_b)
+
+
+def sanns_distances_gather_prepared(ctx: Context, batch: GatherBatch, ct_in: torch.Tensor,
+                                    mask_seed: int, qids: torch.Tensor, ct_out: torch.Tensor,
+                                    srv_share: torch.Tensor, ids: torch.Tensor | None = None,
+                                    stream=None):
+    """sanns_distances_gather over a prepared batch, into caller-allocated
+    outputs sized by the batch (kernels and stream-ordered scratch only, so
+    the call can be captured into a CUDA graph)."""
+    B = len(batch.n_b)
+    assert ct_in.dtype == torch.uint64 and ct_in.shape == (B, ctx.d, 2, ctx.L, ctx.N)
+    assert qids.dtype == torch.uint64 and qids.numel() == B
+    assert ct_out.shape[0] >= int(batch.k_b.sum()) and srv_share.numel() >= int(batch.n_b.sum())
+    _check(load().sanns_distances_gather_prepared(ctx.handle, batch.handle, _ptr(ct_in), mask_seed,
+                                                  _ptr(qids), _ptr(ct_out), _ptr(srv_share), _ptr(ids),
+                                                  _stream(stream)))
+    return ct_out, srv_share, ids
 
 
 def sanns_decrypt_shares_noalloc(ctx: Context, sk: SecretKey, ct_out: torch.Tensor, n: int,

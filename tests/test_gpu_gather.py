@@ -90,3 +90,70 @@ def test_gather_rejects_bad_probe():
     cl = S.sanns_clusters_create(ctx, cu(coords), offsets, cu(members))
     with pytest.raises(S.SannsError):
         S.sanns_gather_plan(cl, np.array([[0, 4]], dtype=np.uint32))
+
+
+def _capture(fn):
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        fn()
+    torch.cuda.current_stream().wait_stream(side)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        fn()
+    return g
+
+
+@pytest.mark.parametrize("cfg,n,C,B,P,slots", [
+    ((256, 2, 40, 0, 5), 3000, 20, 3, 4, False),
+    ((8192, 3, 60, 0, 4), 30000, 9, 2, 3, False),
+    ((256, 2, 40, 0, 5), 3000, 20, 3, 4, True),
+])
+def test_prepared_gather_equals_one_shot_and_replays_in_a_graph(cfg, n, C, B, P, slots):
+    # the plan uploaded once: eager calls equal the one-shot gather, and the
+    # call captured into a CUDA graph and replayed with another batch of
+    # ciphertexts in the same buffer equals the one-shot gather of that batch
+    N, L, bits, rule, d = cfg
+    rnd = np.random.default_rng(n + 1)
+    coords = inputs.uniform_coords(n, d, 11)
+    assign = rnd.choice(C, size=n, p=inputs.zipf_weights(C, 1.1))
+    offsets, members = inputs.clusters_csr(assign, C)
+    probes = np.stack([rnd.permutation(C)[:P] for _ in range(B)]).astype(np.uint32)
+    qids = cu(np.arange(9, 9 + B, dtype=np.uint64))
+    ctx = S.sanns_ctx_create(*cfg)
+    sk = S.sanns_keygen(ctx, 12)
+    S.sanns_set_encoding(ctx, slots)
+    cl = S.sanns_clusters_create(ctx, cu(coords), offsets, cu(members))
+    ct_a = S.sanns_encrypt_query(ctx, sk, cu(inputs.uniform_coords(B, d, 13)), 14, qids)
+    ct_b = S.sanns_encrypt_query(ctx, sk, cu(inputs.uniform_coords(B, d, 15)), 16, qids)
+    ref_a = S.sanns_distances_gather(ctx, cl, ct_a, probes, 6, qids)
+    ref_b = S.sanns_distances_gather(ctx, cl, ct_b, probes, 6, qids)
+    batch = S.sanns_gather_prepare(ctx, cl, probes)
+    assert np.array_equal(batch.n_b, ref_a[3]) and np.array_equal(batch.k_b, ref_a[4])
+    tk, tn = int(batch.k_b.sum()), int(batch.n_b.sum())
+    ct_in = ct_a.clone()
+    out = torch.empty((max(tk, 1), 2, L, N), dtype=torch.uint64, device="cuda")
+    srv = torch.empty(max(tn, 1), dtype=torch.uint32, device="cuda")
+    ids = torch.empty(max(tn, 1), dtype=torch.uint32, device="cuda")
+    S.sanns_distances_gather_prepared(ctx, batch, ct_in, 6, qids, out, srv, ids)
+    torch.cuda.synchronize()
+    assert torch.equal(out[:tk], ref_a[0]) and torch.equal(srv[:tn], ref_a[1])
+    assert torch.equal(ids[:tn], ref_a[2])
+    g = _capture(lambda: S.sanns_distances_gather_prepared(ctx, batch, ct_in, 6, qids, out, srv, ids))
+    for ct, ref in ((ct_b, ref_b), (ct_a, ref_a)):
+        ct_in.copy_(ct)
+        out.zero_()
+        srv.zero_()
+        g.replay()
+        torch.cuda.synchronize()
+        assert torch.equal(out[:tk], ref[0]) and torch.equal(srv[:tn], ref[1])
+
+
+def test_prepare_rejects_a_probe_past_the_clusters():
+    ctx = S.sanns_ctx_create(256, 2, 40, 0, 5)
+    offsets, members = inputs.clusters_csr(np.zeros(10, dtype=np.int64), 2)
+    cl = S.sanns_clusters_create(ctx, cu(inputs.uniform_coords(10, 5, 1)), offsets, cu(members))
+    with pytest.raises(S.SannsError) as e:
+        S.sanns_gather_prepare(ctx, cl, np.array([[0, 2]], dtype=np.uint32))
+    assert e.value.code == -1
