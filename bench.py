@@ -641,8 +641,7 @@ def run_batched_section(quick: bool = False, n_override: int | None = None,
     t_plain_ntt = timed(plain, 1)
     S.sanns_device_status(ctx)
     S.sanns_set_response_form(ctx, False)
-    dpad = (d + 7) // 8 * 8
-    flops = 2.0 * (2 * B * 8) * K * (8 * dpad) * L * N
+    flops = _batched_flops(B, K, d, L, N)
     peak = _peaks_tensor()
     return {
         "workload": f"batched: n={n:,} d={d} uint8 256-component Gaussian mixture (sigma 12); "
@@ -916,6 +915,15 @@ def run_serving_section() -> dict:
         "deferred_for_memory": stats.deferred,
         "sample_bit_exact": f"{exact}/{len(sample)}",
     }
+
+
+def _batched_flops(B: int, K: int, d: int, L: int, N: int) -> float:
+    """Algorithmic FLOPs of one batched MAC: per (prime, slot) a GEMM with
+    rows (query, component, query digit) = 2 B 8, columns the K blocks and a
+    contraction over (dimension padded to a multiple of 8, database digit) =
+    8 ceil(d / 8) 8, at 2 FLOPs per multiply-add."""
+    dpad = (d + 7) // 8 * 8
+    return 2.0 * (2 * B * 8) * K * (8 * dpad) * L * N
 
 
 def _peaks_tensor():

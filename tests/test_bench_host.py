@@ -41,6 +41,9 @@ def test_roofline_helpers():
     tr = b._mac_traffic(rb, W)
     assert 0.98 < tr / rb["total"] < 1.0            # the capture's DRAM bytes scaled by blocks
     assert b._mac_traffic(rb, dict(W, d=96)) is None  # another shape: no scaled figure
+    # the batched GEMM at 64 queries, n = 10^7 (K = 1221), d = 96, L = 3
+    assert abs(b._batched_flops(64, 1221, 96, 3, 8192) - 4.72e13) < 0.005e13
+    assert b._batched_flops(1, 1, 90, 1, 64) == 2.0 * 16 * 1 * (8 * 96) * 1 * 64
     rep = b._ntt_report(738, 8192, 0.5, "x")
     assert abs(rep["polys_per_s"] - 738 / 0.5e-3) < 1e-6
     assert abs(rep["hbm_gbs"] - 16 * 8192 * 738 / 0.5e-3 / 1e9) < 1e-9
