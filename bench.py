@@ -916,6 +916,7 @@ def run_serving_section() -> dict:
         "latency_ms": {"p50": stats.percentile(50) * 1e3, "p99": stats.percentile(99) * 1e3},
         "batches": len(sizes), "mean_batch": float(np.mean(sizes)), "max_batch": int(max(sizes)),
         "deferred_for_memory": stats.deferred,
+        "rejected_for_memory": stats.rejected,
         "sample_bit_exact": f"{exact}/{len(sample)}",
     }
 

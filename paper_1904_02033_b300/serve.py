@@ -31,6 +31,7 @@ class Request:
     start: float | None = None
     done: float | None = None
     result: object = None
+    error: str | None = None    # set when the request cannot be served
 
     @property
     def latency(self) -> float | None:
@@ -49,6 +50,7 @@ class Stats:
     latencies: list = dataclasses.field(default_factory=list)
     batches: list = dataclasses.field(default_factory=list)   # (db, size, t_launch)
     deferred: int = 0                                          # admissions held back for memory
+    rejected: int = 0                                          # requests larger than the whole budget
 
     def percentile(self, p: float) -> float:
         xs = sorted(self.latencies)
@@ -113,6 +115,14 @@ class Scheduler:
             nq = min(len(q), self.max_batch)
             while nq > 0 and self.mem_used + self.ex.bytes_for(db, nq) > self.mem_budget:
                 nq //= 2
+            if nq == 0 and not self.inflight:
+                # nothing in flight will free memory: this request alone is
+                # larger than the budget, so it is rejected rather than held
+                r = q.popleft()
+                r.done = self.clock()
+                r.error = "needs more device memory than the admission budget"
+                self.stats.rejected += 1
+                continue
             if nq == 0:
                 self.stats.deferred += 1
                 break

@@ -99,3 +99,25 @@ def test_oldest_request_picks_the_database():
     s.submit(Request(rid=2, db="B", arrival=3.0))
     s.poll()
     assert ex.launched[0][0] == "B" and ex.launched[0][1] == [0, 2]
+
+
+def test_request_larger_than_the_budget_is_rejected_not_held():
+    # with nothing in flight no retirement can free memory, so a request that
+    # alone exceeds the budget is rejected; the others are still served
+    clock = FakeClock()
+
+    class PerDb(FakeExecutor):
+        def bytes_for(self, db, n):
+            return n * (100 if db == "A" else 1000)
+
+    ex = PerDb(clock)
+    sched = Scheduler(ex, max_batch=8, slots=2, mem_budget=500, clock=clock)
+    reqs = _arrivals(60, 2000.0, 5)
+    stats = run_open_loop(sched, reqs, clock=clock)
+    big = [r for r in reqs if r.db == "B"]
+    small = [r for r in reqs if r.db == "A"]
+    assert big and small
+    assert all(r.error and r.result is None for r in big)
+    assert all(r.error is None and r.result == ("done", r.rid) for r in small)
+    assert stats.rejected == len(big) and len(stats.latencies) == len(small)
+    assert sched.idle() and ex.max_active_bytes <= 500
