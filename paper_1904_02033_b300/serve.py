@@ -112,17 +112,17 @@ class Scheduler:
                 break
             _, db = min(cands)
             q = self.waiting[db]
-            nq = min(len(q), self.max_batch)
-            while nq > 0 and self.mem_used + self.ex.bytes_for(db, nq) > self.mem_budget:
-                nq //= 2
-            if nq == 0 and not self.inflight:
-                # nothing in flight will free memory: this request alone is
-                # larger than the budget, so it is rejected rather than held
+            if self.ex.bytes_for(db, 1) > self.mem_budget:
+                # no amount of retiring frees enough memory for this request
+                # alone: it is rejected rather than held at the queue's head
                 r = q.popleft()
                 r.done = self.clock()
                 r.error = "needs more device memory than the admission budget"
                 self.stats.rejected += 1
                 continue
+            nq = min(len(q), self.max_batch)
+            while nq > 0 and self.mem_used + self.ex.bytes_for(db, nq) > self.mem_budget:
+                nq //= 2
             if nq == 0:
                 self.stats.deferred += 1
                 break

@@ -102,8 +102,8 @@ def test_oldest_request_picks_the_database():
 
 
 def test_request_larger_than_the_budget_is_rejected_not_held():
-    # with nothing in flight no retirement can free memory, so a request that
-    # alone exceeds the budget is rejected; the others are still served
+    # a request that alone exceeds the budget can never be admitted: it is
+    # rejected at once instead of holding up the queue; the others are served
     clock = FakeClock()
 
     class PerDb(FakeExecutor):
