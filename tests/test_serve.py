@@ -121,3 +121,43 @@ def test_request_larger_than_the_budget_is_rejected_not_held():
     assert all(r.error is None and r.result == ("done", r.rid) for r in small)
     assert stats.rejected == len(big) and len(stats.latencies) == len(small)
     assert sched.idle() and ex.max_active_bytes <= 500
+
+
+from hypothesis import given, settings, strategies as st  # noqa: E402
+
+
+@settings(max_examples=60, deadline=None)
+@given(n=st.integers(1, 80), rate=st.floats(100.0, 1e6), seed=st.integers(0, 2 ** 16),
+       slots=st.integers(1, 4), max_batch=st.integers(1, 32), budget=st.integers(50, 5000),
+       bytes_a=st.integers(1, 400), bytes_b=st.integers(1, 6000))
+def test_scheduler_invariants(n, rate, seed, slots, max_batch, budget, bytes_a, bytes_b):
+    # whatever the arrivals, sizes and budget: every request ends served or
+    # rejected (rejected exactly when it alone exceeds the budget), the bytes
+    # in flight never exceed the budget, batches stay within max_batch and one
+    # database, and each database's requests start in arrival order
+    clock = FakeClock()
+    per = {"A": bytes_a, "B": bytes_b}
+
+    class PerDb(FakeExecutor):
+        def bytes_for(self, db, k):
+            return k * per[db]
+
+    ex = PerDb(clock)
+    sched = Scheduler(ex, max_batch=max_batch, slots=slots, mem_budget=budget, clock=clock)
+    reqs = _arrivals(n, rate, seed)
+    stats = run_open_loop(sched, reqs, clock=clock)
+    assert sched.idle()
+    for r in reqs:
+        if per[r.db] > budget:
+            assert r.error and r.result is None
+        else:
+            assert r.error is None and r.result == ("done", r.rid)
+    assert stats.rejected == sum(per[r.db] > budget for r in reqs)
+    assert ex.max_active_bytes <= budget
+    by_rid = {r.rid: r for r in reqs}
+    for db, ids, _ in ex.launched:
+        assert 1 <= len(ids) <= max_batch and all(by_rid[i].db == db for i in ids)
+    for db in per:
+        starts = [(by_rid[i].arrival, by_rid[i].start) for _, ids, _ in ex.launched for i in ids
+                  if by_rid[i].db == db]
+        assert [a for a, _ in starts] == sorted(a for a, _ in starts)
