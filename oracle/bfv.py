@@ -2,7 +2,7 @@
 exact big-integer CRT decryption.
 
 TEST INFRASTRUCTURE ONLY (the oracle): only tests/, __graft_entry__.smoke()
-and bench.py's cpu_baseline leg may import this module.  It never imports the
+and bench.py's cpu_baseline and reference legs may import this module.  It never imports the
 CUDA package.
 
 Follows SANNS (arxiv 1904.02033) Sec. 5.3 and Fig. "SANNS linear-scan

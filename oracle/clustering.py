@@ -2,7 +2,7 @@
 on a server layout given as input.
 
 TEST INFRASTRUCTURE ONLY (the oracle): only tests/, __graft_entry__.smoke()
-and bench.py's cpu_baseline leg may import this module.  It never imports the
+and bench.py's cpu_baseline and reference legs may import this module.  It never imports the
 CUDA package.
 
 The server's layout is what Algorithm 4 receives: T groups of clusters with

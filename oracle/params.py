@@ -1,7 +1,7 @@
 """BFV parameter derivation with exact Python integers.
 
 TEST INFRASTRUCTURE ONLY (the oracle): only tests/, __graft_entry__.smoke()
-and bench.py's cpu_baseline leg may import this package.
+and bench.py's cpu_baseline and reference legs may import this package.
 
 The paper fixes N = 2^13 and a 180-bit ciphertext modulus made of three
 machine words (Sec. 7.1, "Parameters") and a plaintext modulus t = 2^b_d with

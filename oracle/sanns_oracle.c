@@ -2,7 +2,7 @@
  * sanns_oracle.c -- plain, slow CPU oracle for the encrypted-distance path.
  *
  * TEST INFRASTRUCTURE ONLY.  Only tests/, __graft_entry__.smoke() and the
- * cpu_baseline leg of bench.py may load this library.  It shares no code,
+ * cpu_baseline and reference legs of bench.py may load this library.  It shares no code,
  * header, table or constant generator with the CUDA library: every routine
  * below is written out directly from its definition, with no lazy reduction,
  * no blocking and no fusion.
