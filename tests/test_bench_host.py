@@ -54,3 +54,12 @@ def test_all_cores_baseline_uses_every_core():
     r = b.cpu_baseline_all_cores(quick=True)
     assert r["kind"] == "oracle" and r["value"] > 0
     assert r["cores"] == max(1, min(len(os.sched_getaffinity(0)), 64))
+
+
+def test_reference_arm_other_ranks_exit_without_work():
+    # under torchrun only rank 0 runs and prints the reference line
+    env = dict(os.environ, RANK="1", WORLD_SIZE="2", LOCAL_RANK="1")
+    r = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--steps", "1", "--warmup", "3"],
+                       cwd=ROOT, capture_output=True, text=True, timeout=600, env=env)
+    assert r.returncode == 0, r.stderr[-2000:]
+    assert not [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
