@@ -3,7 +3,8 @@ a 64-component Gaussian mixture, d = 128, N = 8192, three 60-bit primes, one
 query, every MAC launch variant (the autotuned one first, as the benchmark
 runs it).  The oracle computes sampled blocks one by one (the first, a middle
 one and the ragged last, with their server and client shares); every
-position's shares reconstruct the brute-force squared distance."""
+position's shares reconstruct the brute-force squared distance.  The file
+sorts after the other GPU tests, so the small cases report first."""
 import numpy as np
 import pytest
 import torch
