@@ -77,3 +77,19 @@ def test_null_handles_rejected(lib):
     assert lib.sanns_distances(None, None, None, 1, 0, None, None, None, None) == -1
     lib.sanns_keygen.argtypes = [C.c_void_p, C.c_uint64, C.c_void_p, C.c_void_p]
     assert lib.sanns_keygen(None, 0, None, None) == -1
+
+
+def test_null_handles_rejected_by_the_seeded_and_prepared_calls(lib):
+    # validated on the host before any device work, so no GPU is needed
+    lib.sanns_expand_query.argtypes = [C.c_void_p, C.c_void_p, C.c_uint32, C.c_uint64, C.c_void_p,
+                                       C.c_void_p, C.c_void_p]
+    assert lib.sanns_expand_query(None, None, 1, 0, None, None, None) == -1
+    lib.sanns_gather_prepare.argtypes = [C.c_void_p] * 3 + [C.c_uint32, C.c_uint32, C.c_void_p]
+    assert lib.sanns_gather_prepare(None, None, None, 1, 1, None) == -1      # out is NULL
+    out = C.c_void_p(1)
+    assert lib.sanns_gather_prepare(None, None, None, 1, 1, C.byref(out)) == -1
+    assert out.value is None                                                # cleared on failure
+    lib.sanns_distances_gather_prepared.argtypes = [C.c_void_p] * 3 + [C.c_uint64] + [C.c_void_p] * 5
+    assert lib.sanns_distances_gather_prepared(None, None, None, 0, None, None, None, None, None) == -1
+    lib.sanns_gather_batch_free.argtypes = [C.c_void_p]
+    lib.sanns_gather_batch_free(None)                                       # a no-op
