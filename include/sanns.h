@@ -29,7 +29,11 @@
  *   (sanns_set_*, sanns_autotune_*, sanns_batched_tune,
  *   sanns_db_prepare_batched, sanns_db_set_position_base, the *_free calls)
  *   must not overlap any other call on that handle.  The device error word
- *   read by sanns_device_status is shared by all calls on a context.
+ *   read by sanns_device_status is shared by all calls on a context.  The
+ *   one exception to the no-shared-state rule is
+ *   sanns_decrypt_shares_noalloc: its scratch is one process-wide array per
+ *   device, shared by every context on that device, so its calls on one
+ *   device must be ordered (one stream, or events between streams).
  *
  * Readings of the paper that fix the exact bits (the paper leaves them to
  * SEAL): primes = the L largest primes below 2^prime_bits that are 1 mod 2N;
@@ -308,6 +312,20 @@ int sanns_device_status(sanns_ctx *ctx, void *stream);
  * nothing and always ends.  Asynchronous on stream.
  */
 int sanns_selftest_wait_timeout(sanns_ctx *ctx, uint32_t limit_ms, void *stream);
+/*
+ * Measured dense tensor-core rates of the current GPU (no counterpart in the
+ * paper; the denominators of the batched path's roofline).  Runs three
+ * throughput probes on every SM and writes, to rates_host[0..2]:
+ *   [0] tcgen05.mma kind::f16, M128 N256 K16, fp16 in, fp32 out (TFLOP/s);
+ *       the instruction family of the batched MAC;
+ *   [1] legacy mma.sync m16n8k16, fp16 in, fp32 out (TFLOP/s);
+ *   [2] legacy mma.sync m16n8k32, s8 in, s32 out (TOP/s), the only INT8
+ *       tensor instruction on sm_103a: ptxas rejects tcgen05.mma kind::i8
+ *       for that target.
+ * Synchronous, about 10 ms of GPU time.  SANNS_ETIMEOUT if the probe's
+ * bounded completion wait gave up (nothing is written then).
+ */
+int sanns_measure_mma_rates(sanns_ctx *ctx, double *rates_host, void *stream);
 /* Tuning of the batched kernel: back-off sleep (ns, <= 100000) of the TMA
  * thread, the MMA thread, the digit producers and the epilogue when their
  * barrier is not ready yet; how many of its own work units ahead each CTA
@@ -470,7 +488,9 @@ int sanns_decrypt_shares(sanns_ctx *ctx, const sanns_sk *sk, const uint64_t *ct_
  *     query fits up to n = 1,392,640 points).
  *   - The first call on a device looks up the array's device address
  *     (cudaGetSymbolAddress) with that device current; make that first call
- *     before any stream capture.
+ *     before any stream capture.  The address is kept for the life of the
+ *     process: resetting the device (cudaDeviceReset) and calling again is
+ *     not supported.
  *   - All calls share the one array and it keeps the last call's contents;
  *     each call writes every word it later reads, so nothing is cleared, but
  *     calls that overlap on the GPU (different streams, no ordering between

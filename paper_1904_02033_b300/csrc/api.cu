@@ -895,6 +895,18 @@ int sanns_selftest_wait_timeout(sanns_ctx* ctx, uint32_t limit_ms, void* stream)
   return SANNS_OK;
 }
 
+int sanns_measure_mma_rates(sanns_ctx* ctx, double* rates_host, void* stream) {
+  if (!ctx || !rates_host) return fail(SANNS_EINVAL, "ctx or rates_host is NULL");
+  int rc = check_device(ctx);
+  if (rc) return rc;
+  double r[3] = {0, 0, 0};
+  SANNS_CUDA(measure_mma_rates(ctx->sms, ctx->d_err, r, as_stream(stream)));
+  rc = sanns_device_status(ctx, stream);
+  if (rc) return rc;
+  for (int i = 0; i < 3; ++i) rates_host[i] = r[i];
+  return SANNS_OK;
+}
+
 int sanns_device_status(sanns_ctx* ctx, void* stream) {
   if (!ctx) return fail(SANNS_EINVAL, "ctx is NULL");
   int rc = check_device(ctx);

@@ -163,6 +163,7 @@ cudaError_t launch_norms_slot(const PrimeSet& PT, uint32_t* norms, uint64_t K, c
 cudaError_t launch_join30(const uint64_t* src, uint64_t* dst, uint64_t count, cudaStream_t st);
 size_t batched_limb_bytes(uint32_t L, uint32_t N, uint64_t K, uint32_t d);
 cudaError_t launch_wait_selftest(int* err, uint32_t limit_ms, int device, cudaStream_t st);
+cudaError_t measure_mma_rates(int sms, int* d_err, double out[3], cudaStream_t st);
 cudaError_t launch_prepare_limbs(const PrimeSet& P, const uint64_t* pt, uint64_t K, uint32_t d,
                                  uint16_t* plimb, cudaStream_t st);
 constexpr int kBatchedConfigs = 4;  // (tile shape, L2 prefetch) pairs timed by the autotuner

@@ -81,6 +81,7 @@ _SIGS = {
                                 C.c_int),
     "sanns_distances_batched_mac": ([_VP, _VP, _VP, C.c_uint32, _VP, _VP], C.c_int),
     "sanns_device_status": ([_VP, _VP], C.c_int),
+    "sanns_measure_mma_rates": ([_VP, _VP, _VP], C.c_int),
     "sanns_batched_tune": ([_VP, C.c_uint32, C.c_uint32, C.c_uint32, C.c_uint32, C.c_uint32,
                             C.c_uint32, C.c_uint32], C.c_int),
     "sanns_decrypt_shares": ([_VP, _VP, _VP, C.c_uint32, C.c_uint64, _VP, _VP, _VP], C.c_int),
@@ -577,6 +578,14 @@ def sanns_distances_batched_mac(ctx: Context, db: Database, ct_in: torch.Tensor,
 
 def sanns_device_status(ctx: Context, stream=None):
     _check(load().sanns_device_status(ctx.handle, _stream(stream)))
+
+
+def sanns_measure_mma_rates(ctx: Context, stream=None) -> dict:
+    """Measured dense tensor-core rates of this GPU: tcgen05 kind::f16 and
+    legacy mma.sync f16 (TFLOP/s), legacy mma.sync s8 (TOP/s)."""
+    r = (C.c_double * 3)()
+    _check(load().sanns_measure_mma_rates(ctx.handle, r, _stream(stream)))
+    return {"tcgen05_f16_tflops": r[0], "mma_sync_f16_tflops": r[1], "mma_sync_s8_tops": r[2]}
 
 
 def sanns_batched_tune(ctx: Context, tma_ns: int = 0, mma_ns: int = 0, producer_ns: int = 32,

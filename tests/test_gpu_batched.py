@@ -86,3 +86,14 @@ def test_batched_autotune_keeps_results_identical():
     acc_b = S.sanns_distances_batched_mac(ctx, db, ct_in)
     S.sanns_device_status(ctx)
     assert torch.equal(acc_b.cpu(), acc_plain.cpu())
+
+
+def test_measured_tensor_rates_rank_the_instruction_families():
+    """The library's rate probe: the tcgen05 fp16 MMA the batched kernel uses
+    is faster than the legacy fp16 mma.sync, which is faster per operation
+    than the legacy s8 mma.sync (the only INT8 tensor instruction on sm_103a)."""
+    ctx = S.sanns_ctx_create(256, 2, 40, 0, 8)
+    r = S.sanns_measure_mma_rates(ctx)
+    assert r["tcgen05_f16_tflops"] > r["mma_sync_f16_tflops"] > r["mma_sync_s8_tops"] > 0
+    # sanity bound: no more than the nominal dense fp16 peak plus margin
+    assert r["tcgen05_f16_tflops"] < 3000

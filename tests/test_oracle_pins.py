@@ -211,6 +211,15 @@ def test_keygen_is_ternary_and_ntt_of_s():
     assert set(np.unique(s)).issubset({-1, 0, 1})
     counts = np.bincount(s.astype(np.int64) + 1, minlength=3)
     assert counts.min() > 256 / 3 * 0.6
+    # the secret's stream: s_x = (lo mod 3) - 1 of the 128-bit draw x of
+    # (seed, purpose 1, object 0), read from the RFC-pinned block function
+    # with the documented key / nonce / counter / word layout
+    for seed in (3, 0xFEDCBA9876543210):
+        sx = O.keygen(seed=seed)[0]
+        for x in range(O.N):
+            blk = chacha20_block([seed & 0xFFFFFFFF, seed >> 32, 0, 0, 0, 0, 0, 0], x // 4, [1, 0, 0])
+            lo = int(blk[4 * (x % 4)]) | int(blk[4 * (x % 4) + 1]) << 32
+            assert int(sx[x]) == lo % 3 - 1, (seed, x)
     for j in range(O.L):
         q = int(O.q[j])
         lifted = [(int(v) % q) for v in s]
