@@ -583,7 +583,7 @@ BATCHED = dict(n=10_000_000, d=96, N=8192, L=3, prime_bits=60, t_rule=0, n_comp=
 
 def run_batched_section(quick: bool = False, n_override: int | None = None,
                         d_override: int | None = None, b_override: int | None = None,
-                        scratch_mib: int | None = None) -> dict:
+                        scratch_mib: int | None = None, tile: int | None = None) -> dict:
     """The batched configuration: n = 10^7, d = 96 (Deep1B-10M-shaped), 64
     queries per launch on the tensor-core path, against the same queries run
     one at a time on the per-query path; outputs compared in full."""
@@ -620,10 +620,15 @@ def run_batched_section(quick: bool = False, n_override: int | None = None,
     out_p = torch.empty((1, K, 2, L, N), dtype=torch.uint64, device="cuda")
     srv_p = torch.empty((1, n), dtype=torch.uint32, device="cuda")
     S.sanns_autotune_mac(ctx, db, ct[0:1], out_p, reps=2)
-    if scratch_mib:
-        S.sanns_batched_tune(ctx, scratch_mib=scratch_mib)
-    tuned, tune_ms = S.sanns_autotune_batched(ctx, db, ct, out_b, reps=1)
-    tile, prefetch = S.BATCHED_CONFIGS[tuned]
+    if tile is not None:
+        # a fixed tile shape (profiling captures), no autotuning
+        S.sanns_batched_tune(ctx, scratch_mib=scratch_mib or 4096, tile=tile, prefetch_units=0)
+        prefetch, tune_ms = 0, []
+    else:
+        if scratch_mib:
+            S.sanns_batched_tune(ctx, scratch_mib=scratch_mib)
+        tuned, tune_ms = S.sanns_autotune_batched(ctx, db, ct, out_b, reps=1)
+        tile, prefetch = S.BATCHED_CONFIGS[tuned]
 
     def timed(fn, reps):
         fn()
@@ -673,8 +678,15 @@ def run_batched_section(quick: bool = False, n_override: int | None = None,
                                "speedup_vs_plain": t_plain_ntt / t_batch_ntt,
                                "qp_per_s_batched": B * n / (t_batch_ntt * 1e-3)},
         "bit_identical_to_per_query_path": same,
-        "autotuned": {"tile": ["128 blocks x 256 query rows per SM",
-                               "256 blocks x 256 query rows per SM pair"][tile],
+        "autotuned": {"tile": ["128 blocks x 256 query rows per SM, producer-fed digits",
+                               "256 blocks x 256 query rows per SM pair, producer-fed digits",
+                               "128 blocks x 256 query rows per SM, TMA-fed fp16 digits",
+                               "256 blocks x 256 query rows per SM pair, TMA-fed fp16 digits",
+                               "128 blocks x 256 query rows per SM, TMA-fed, clusters of 2 sharing the query tile",
+                               "128 blocks x 256 query rows per SM, TMA-fed, clusters of 4 sharing the query tile",
+                               "128 blocks x 256 query rows per SM, TMA-fed, four slots per CTA, 32-byte stores",
+                               "128 blocks x 256 query rows per SM, TMA-fed, four slots per CTA, 32-byte stores, "
+                               "clusters of 2 sharing the query tile"][tile],
                       "l2_prefetch_units": prefetch,
                       "ms_per_config": {f"tile{t}_prefetch{p}": round(m, 3)
                                         for (t, p), m in zip(S.BATCHED_CONFIGS, tune_ms)}},
@@ -1102,6 +1114,8 @@ def main():
                     help="run only the batched section on N_POINTS points (profiling)")
     ap.add_argument("--batched-d", type=int, default=None, help="dimension for --only-batched")
     ap.add_argument("--batched-B", type=int, default=None, help="queries per launch for --only-batched")
+    ap.add_argument("--batched-tile", type=int, default=None, choices=list(range(8)),
+                    help="fixed tile shape of the batched MAC for --only-batched (no autotuning)")
     ap.add_argument("--batched-scratch-mib", type=int, default=None,
                     help="cap on the batched path's query-multiple scratch (smaller launches)")
     ap.add_argument("--n", type=int, default=None,
@@ -1130,7 +1144,8 @@ def main():
         print(json.dumps({"batched": run_batched_section(n_override=args.only_batched,
                                                          d_override=args.batched_d,
                                                          b_override=args.batched_B,
-                                                         scratch_mib=args.batched_scratch_mib)}),
+                                                         scratch_mib=args.batched_scratch_mib,
+                                                         tile=args.batched_tile)}),
               flush=True)
     elif args.impl == "reference":
         run_reference(args)

@@ -132,6 +132,15 @@ int sanns_db_info(const sanns_db *db, uint64_t *n, uint64_t *K);
  * ||p||^2 of their (k1 - k0) N positions, to `any` memory (NULL skips). */
 int sanns_db_export(const sanns_db *db, uint64_t k0, uint64_t k1, uint64_t *pt_any,
                     uint32_t *norms_any, void *stream);
+/* The inverse of sanns_db_export over a whole database: a new encoded
+ * database of n points (K = ceil(n / N) blocks) from its plaintexts pt_any
+ * ([K][L][d][N], NTT form, canonical residues) and norms_any ([K N] uint32)
+ * in `any` memory, for a server that encodes once (Pi_ls step 1, offline)
+ * and loads the result later.  The context's current encoding setting is
+ * recorded with it; position base 0.  SANNS_EINVAL if a residue is not below
+ * its prime (nothing is created).  Synchronous. */
+int sanns_db_import(sanns_ctx *ctx, uint64_t n, const uint64_t *pt_any, const uint32_t *norms_any,
+                    sanns_db **out, void *stream);
 
 /*
  * AHE.Enc (Pi_ls step 2) of B queries, private-key BFV.  Coordinate i of
@@ -330,21 +339,34 @@ int sanns_measure_mma_rates(sanns_ctx *ctx, double *rates_host, void *stream);
  * thread, the MMA thread, the digit producers and the epilogue when their
  * barrier is not ready yet; how many of its own work units ahead each CTA
  * prefetches the database-digit and query tiles into L2 (0 = no prefetch,
- * <= 8; default 1); the cap (MiB, default 4096) on the stream-ordered
+ * <= 8; default 0); the cap (MiB, default 4096) on the stream-ordered
  * scratch that holds the query multiples of one range of slots (a smaller cap
  * means more, shorter launches; at least one slot's worth is always used);
- * and the tile shape: 0 (default) = 128 database blocks x 256 query rows per
- * SM, 1 = 256 x 256 per pair of SMs (cluster of two CTAs sharing one MMA).
+ * and the tile shape, two bits: bit 0 clear = 128 database blocks x 256 query
+ * rows per SM, set = 256 x 256 per pair of SMs (cluster of two CTAs sharing
+ * one MMA); bit 1 clear = producer warps turn byte-interleaved query
+ * multiples into fp16 digit rows in shared memory, set = a pre-kernel writes
+ * the fp16 digit rows to the scratch once per slot range (twice the scratch
+ * per slot) and they arrive by TMA like the database tile; 4 and 5 = the
+ * one-SM, TMA-fed tile run by clusters of 2 or 4 CTAs that take consecutive
+ * database tiles of one slot and query tile and share the query tile by
+ * multicast (each CTA loads a 1/2 or 1/4 of it for all); 6 and 7 = the
+ * one-SM, TMA-fed tile with four consecutive slots per CTA, whose epilogue
+ * holds three slots in registers and writes each output's four slots as one
+ * 32-byte store (a whole sector), alone (6) or in clusters of 2 sharing the
+ * query tile (7; as 6 when the number of 128-block database tiles is odd).
+ * Defaults: tile 7, no L2 prefetch (the fastest on the n = 10^7, d = 96,
+ * 64-query workload).
  * Results never depend on these values.  Returns SANNS_EINVAL for
  * out-of-range values. */
 int sanns_batched_tune(sanns_ctx *ctx, uint32_t tma_ns, uint32_t mma_ns, uint32_t producer_ns,
                        uint32_t epilogue_ns, uint32_t prefetch_units, uint32_t scratch_mib,
                        uint32_t tile);
-/* Autotuner of the batched MAC: times the four configurations cfg = 2 tile +
- * prefetch_units (tile 0 or 1, L2 prefetch 0 or 1 unit ahead) `reps` times
+/* Autotuner of the batched MAC: times the sixteen configurations cfg = 2 tile +
+ * prefetch_units (tile 0..7, L2 prefetch 0 or 1 unit ahead) `reps` times
  * each on the given inputs (writing ct_out_dev as sanns_distances_batched_mac
  * would), keeps the fastest in the context and returns its index (>= 0) or an
- * error code; ms_out (host, 4 floats, may be NULL) receives the mean time per
+ * error code; ms_out (host, 16 floats, may be NULL) receives the mean time per
  * launch.  Synchronous.  Every configuration computes identical results. */
 int sanns_autotune_batched(sanns_ctx *ctx, const sanns_db *db, const uint64_t *ct_in_dev, uint32_t B,
                            uint64_t *ct_out_dev, int reps, float *ms_out, void *stream);

@@ -115,9 +115,9 @@ int sanns_ctx_create(const sanns_params* p, sanns_ctx** out) {
   c->batched_tune[1] = 0;
   c->batched_tune[2] = 32;
   c->batched_tune[3] = 128;
-  c->batched_tune[4] = 1;
+  c->batched_tune[4] = 0;
   c->batched_tune[5] = 4096;
-  c->batched_tune[6] = 0;
+  c->batched_tune[6] = 7;
 
   const size_t per = (size_t)p->L * N;
   std::vector<uint64_t> fw(per), fws(per), iw(per), iws(per);
@@ -309,6 +309,50 @@ int sanns_encode_db(sanns_ctx* ctx, const uint8_t* coords, uint64_t n_points, co
   if (bad) {
     sanns_db_free(db);
     return fail(SANNS_EINVAL, "perm holds an index >= n_points");
+  }
+  *out = db;
+  return SANNS_OK;
+}
+
+int sanns_db_import(sanns_ctx* ctx, uint64_t n, const uint64_t* pt, const uint32_t* norms, sanns_db** out,
+                    void* stream) {
+  if (!out) return fail(SANNS_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!ctx) return fail(SANNS_EINVAL, "ctx is NULL");
+  if (n == 0) return fail(SANNS_EINVAL, "n must be positive");
+  if (!pt || !norms) return fail(SANNS_EINVAL, "pt or norms is NULL");
+  int rc = check_device(ctx);
+  if (rc) return rc;
+  const uint32_t N = ctx->P.N, L = ctx->P.L, d = ctx->params.d;
+  const uint64_t K = (n + N - 1) / N;
+  if (K > 0x7fffffffull) return fail(SANNS_EINVAL, "too many blocks");
+  cudaStream_t st = as_stream(stream);
+  sanns_db* db = new sanns_db();
+  db->ctx = ctx;
+  db->n = n;
+  db->K = K;
+  db->slots = ctx->slots;
+  const uint64_t count = K * L * d * N;
+  int* d_bad = nullptr;
+  cudaError_t e = cudaMalloc(&db->d_pt, sizeof(uint64_t) * count);
+  if (e == cudaSuccess) e = cudaMalloc(&db->d_norms, sizeof(uint32_t) * K * N);
+  if (e == cudaSuccess) e = cudaMalloc(&d_bad, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemsetAsync(d_bad, 0, sizeof(int), st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(db->d_pt, pt, sizeof(uint64_t) * count, cudaMemcpyDefault, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(db->d_norms, norms, sizeof(uint32_t) * K * N, cudaMemcpyDefault, st);
+  if (e == cudaSuccess) e = launch_import_pt(ctx->P, db->d_pt, count, d, d_bad, st);
+  int bad = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&bad, d_bad, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (d_bad) cudaFree(d_bad);
+  if (e != cudaSuccess) {
+    sanns_db_free(db);
+    return cuda_fail(e, "db import");
+  }
+  if (bad) {
+    sanns_db_free(db);
+    return fail(SANNS_EINVAL, "a plaintext residue is not below its prime");
   }
   *out = db;
   return SANNS_OK;
@@ -828,7 +872,11 @@ int sanns_batched_tune(sanns_ctx* ctx, uint32_t tma_ns, uint32_t mma_ns, uint32_
     return fail(SANNS_EINVAL, "back-off above 100 us");
   if (prefetch_units > 8) return fail(SANNS_EINVAL, "prefetch distance above 8 units");
   if (scratch_mib < 1 || scratch_mib > (1u << 20)) return fail(SANNS_EINVAL, "scratch cap outside 1 MiB .. 1 TiB");
-  if (tile > 1) return fail(SANNS_EINVAL, "tile must be 0 (128 blocks, one SM) or 1 (256 blocks, SM pair)");
+  if (tile > 7)
+    return fail(SANNS_EINVAL,
+                "tile must be 0..7 (0..3: bit 0 = 256 blocks on an SM pair, bit 1 = query digits by TMA; "
+                "4, 5: TMA-fed, clusters of 2 or 4 sharing the query tile; 6, 7: TMA-fed, four slots per "
+                "CTA with 32-byte stores, alone or in clusters of 2)");
   ctx->batched_tune[0] = tma_ns;
   ctx->batched_tune[1] = mma_ns;
   ctx->batched_tune[2] = producer_ns;

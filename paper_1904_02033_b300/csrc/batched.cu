@@ -86,6 +86,9 @@ struct BatchArgs {
   uint32_t sleep_tma, sleep_mma, sleep_prod, sleep_epi, prefetch_units;
   const uint16_t* plimb;  // [L][N][K][8 dpad] database digits (prefetch addresses)
   uint64_t lo_bias[kMaxPrimes];  // a multiple of q_j at or above 2^49
+  // TMA-fed query digits: [L S'][16 B][8 dpad] fp16 rows (bc, a) of the slot
+  // range (see expand_query_f16_kernel), for the prefetch addresses
+  const uint16_t* xh;
 };
 
 // L2 prefetch of [p, p + bytes) in pieces of at most 32 KB (16-byte aligned
@@ -309,23 +312,97 @@ __device__ __forceinline__ void epilogue_chunk(uint32_t taddr, const BatchArgs& 
 // word.  Pair p = blockIdx.x + (m / 2) gridDim.x over A.units pairs, decoded
 // as ((j S/2 + s'/2) KT + kt) QT + qt; half m % 2 gives slot s' = 2 (s'/2) +
 // m % 2.  False past the last pair.
+//
+// With clusters of CL CTAs (CL > 1), pairs are counted per cluster: pair p =
+// cluster + (m / 2) (clusters in the grid) over A.units pairs, whose database
+// tile index counts groups of CL tiles; the CTA of rank r takes tile
+// CL group + r, so the CTAs of a cluster share the slot and the query tile.
+template <int CL>
 __device__ __forceinline__ bool unit_of(uint32_t m, const BatchArgs& A, Decoded& D) {
-  const uint64_t p = blockIdx.x + (uint64_t)(m >> 1) * gridDim.x;
+  const uint32_t cid = blockIdx.x / CL, rank = blockIdx.x % CL, ncl = gridDim.x / CL;
+  const uint64_t p = cid + (uint64_t)(m >> 1) * ncl;
   if (p >= A.units) return false;
   const uint32_t half = A.s_count >> 1;
+  const uint32_t ktg = A.KT / CL;
   uint32_t r = (uint32_t)p;
   D.qt = r % A.QT;
   r /= A.QT;
-  D.kt = r % A.KT;
-  r /= A.KT;
+  D.kt = (r % ktg) * CL + rank;
+  r /= ktg;
   D.sl = 2 * (r % half) + (m & 1);
   D.s = A.s_begin + D.sl;
   D.j = r / half;
   return true;
 }
 
+__device__ __forceinline__ void tma_load_3d_mc(uint32_t dst, const CUtensorMap* map, int x, int y, int z,
+                                               uint32_t bar, uint16_t mask) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster"
+      " [%0], [%1, {%2, %3, %4}], [%5], %6;" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(bar), "h"(mask)
+      : "memory");
+}
+
+// completion of this thread's prior MMAs arrives on the barrier at the same
+// offset in every CTA of `mask` (single-CTA MMAs)
+__device__ __forceinline__ void mma_commit_mc1(uint32_t bar, uint16_t mask) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64"
+      " [%0], %1;" ::"r"(bar), "h"(mask)
+      : "memory");
+}
+
+__device__ __forceinline__ void cluster_barrier() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\nbarrier.cluster.wait.acquire.aligned;" ::
+                   : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_acq_cluster(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait on a barrier that other CTAs of the cluster arrive on
+// (cluster-scope acquire), otherwise as mbar_wait.
+__device__ __forceinline__ bool mbar_wait_cluster(uint32_t bar, uint32_t parity, volatile int* abort_flag,
+                                                  int* err, uint32_t sleep_ns = 0) {
+  const unsigned long long t0 = clock64();
+  for (uint32_t it = 0;; ++it) {
+    if (mbar_try_acq_cluster(bar, parity)) return true;
+    if (sleep_ns && it > 2) __nanosleep(sleep_ns);
+    if ((it & 255) == 255) {
+      if (*abort_flag) return false;
+      if (clock64() - t0 > kWaitCycles) {
+        *abort_flag = 1;
+        atomicExch(err, SANNS_ETIMEOUT);
+        return false;
+      }
+    }
+  }
+}
+
+// TMA_B: the query-digit tile of every stage arrives by TMA from the fp16
+// rows written by expand_query_f16_kernel (xmap), and the producer warps stay
+// idle; otherwise they generate it from the byte-interleaved multiples.
+//
+// CL > 1 (with TMA_B): clusters of CL CTAs take CL consecutive database tiles
+// of the same slot and query tile; each CTA loads 256 / CL of the query-digit
+// rows with cluster multicast, so every CTA receives the whole query tile
+// while the cluster reads it from L2 once.  A stage is then free only once
+// every CTA of the cluster has consumed it: the MMA completion arrives on the
+// stage-empty barrier of all CL CTAs.
+template <bool TMA_B, int CL>
 __global__ void __launch_bounds__(kThreads, 1)
-batched_mac_kernel(const __grid_constant__ CUtensorMap pmap, PrimeSet P, BatchArgs A) {
+batched_mac_kernel(const __grid_constant__ CUtensorMap pmap, const __grid_constant__ CUtensorMap xmap,
+                   PrimeSet P, BatchArgs A) {
+  static_assert(CL == 1 || TMA_B, "clusters share TMA-fed query tiles");
   extern __shared__ __align__(1024) uint8_t dsmem[];
   __shared__ __align__(8) uint64_t bar_full[kStages], bar_empty[kStages];
   __shared__ __align__(8) uint64_t bar_tfull[2], bar_tempty[2];
@@ -339,8 +416,8 @@ batched_mac_kernel(const __grid_constant__ CUtensorMap pmap, PrimeSet P, BatchAr
   if (threadIdx.x == 0) {
     abort_flag = 0;
     for (int s = 0; s < kStages; ++s) {
-      mbar_init(smem_u32(&bar_full[s]), 1 + kProdWarps);
-      mbar_init(smem_u32(&bar_empty[s]), 1);
+      mbar_init(smem_u32(&bar_full[s]), TMA_B ? 1 : 1 + kProdWarps);
+      mbar_init(smem_u32(&bar_empty[s]), CL);
     }
     for (int a = 0; a < 2; ++a) {
       mbar_init(smem_u32(&bar_tfull[a]), 1);
@@ -355,9 +432,12 @@ batched_mac_kernel(const __grid_constant__ CUtensorMap pmap, PrimeSet P, BatchAr
   }
   tc_fence_before();
   __syncthreads();
+  if (CL > 1) cluster_barrier();  // every CTA's barriers exist before any multicast
   tc_fence_after();
   const uint32_t tmem = tmem_base_slot;
   const uint32_t N = P.N;
+  const uint32_t crank = blockIdx.x % CL;
+  constexpr uint16_t kMask = (uint16_t)((1u << CL) - 1);
 
   if (warp == 0) {
     // ---------------- TMA producer ----------------
@@ -366,8 +446,9 @@ batched_mac_kernel(const __grid_constant__ CUtensorMap pmap, PrimeSet P, BatchAr
     bool ok = true;
     for (uint32_t m = 0; ok; ++m) {
       Decoded D, F;
-      if (!unit_of(m, A, D)) break;
-      if (lane == 0 && A.prefetch_units && unit_of(m + 2 * A.prefetch_units, A, F)) {
+      if (!unit_of<CL>(m, A, D)) break;
+      if (lane == 0 && A.prefetch_units && unit_of<CL>(m + 2 * A.prefetch_units, A, F) &&
+          F.kt * kBM < A.K) {
         // database tile (rows kt*128 .. of slot (j, s)) and query multiples
         // (row groups qt*32 .. of slot (j, s')) of a later unit of this CTA
         const uint32_t rows = A.K - F.kt * kBM < (uint32_t)kBM ? A.K - F.kt * kBM : (uint32_t)kBM;
@@ -375,19 +456,33 @@ batched_mac_kernel(const __grid_constant__ CUtensorMap pmap, PrimeSet P, BatchAr
                     rows * 16u * A.dpad);
         const uint32_t twoB = 2 * A.B, bc0 = F.qt * kQG;
         const uint32_t groups = twoB - bc0 < (uint32_t)kQG ? twoB - bc0 : (uint32_t)kQG;
-        prefetch_l2(A.xm + (((uint64_t)F.j * A.s_count + F.sl) * twoB + bc0) * A.dpad * 8,
-                    groups * 64u * A.dpad);
+        if (TMA_B)
+          prefetch_l2(A.xh + (((uint64_t)F.j * A.s_count + F.sl) * 8 * twoB + 8 * bc0) * 8 * A.dpad,
+                      groups * 128u * A.dpad);
+        else
+          prefetch_l2(A.xm + (((uint64_t)F.j * A.s_count + F.sl) * twoB + bc0) * A.dpad * 8,
+                      groups * 64u * A.dpad);
       }
       for (uint32_t kc = 0; kc < A.chunks; ++kc, ++g) {
         const uint32_t st = (uint32_t)(g % kStages), ph = (uint32_t)((g / kStages) & 1);
         bool ready = true;
-        if (lane == 0) ready = mbar_wait(smem_u32(&bar_empty[st]), ph ^ 1, &abort_flag, A.err, A.sleep_tma);
+        if (lane == 0)
+          ready = CL > 1 ? mbar_wait_cluster(smem_u32(&bar_empty[st]), ph ^ 1, &abort_flag, A.err, A.sleep_tma)
+                         : mbar_wait(smem_u32(&bar_empty[st]), ph ^ 1, &abort_flag, A.err, A.sleep_tma);
         if (!__shfl_sync(0xffffffffu, (int)ready, 0)) { ok = false; break; }
         if (lane == 0) {
           const uint32_t full = smem_u32(&bar_full[st]);
-          mbar_arrive_tx(full, kATile);
+          mbar_arrive_tx(full, TMA_B ? kStageBytes : kATile);
           tma_load_3d(sbase + st * kStageBytes, &pmap, (int)(kc * kBK), (int)(D.kt * kBM),
                       (int)(D.j * N + D.s), full);
+          if (TMA_B && CL == 1)
+            tma_load_3d(sbase + st * kStageBytes + kATile, &xmap, (int)(kc * kBK), (int)(D.qt * kBN),
+                        (int)(D.j * A.s_count + D.sl), full);
+          if (TMA_B && CL > 1)
+            // rows [crank kBN / CL, ..) of the query tile, into every CTA of the cluster
+            tma_load_3d_mc(sbase + st * kStageBytes + kATile + crank * (kBTile / CL), &xmap, (int)(kc * kBK),
+                           (int)(D.qt * kBN + crank * (kBN / CL)), (int)(D.j * A.s_count + D.sl), full,
+                           kMask);
         }
         __syncwarp();
       }
@@ -410,7 +505,7 @@ batched_mac_kernel(const __grid_constant__ CUtensorMap pmap, PrimeSet P, BatchAr
     bool ok = true;
     for (uint32_t m = 0; ok; ++m) {
       Decoded D;
-      if (!unit_of(m, A, D)) break;
+      if (!unit_of<CL>(m, A, D)) break;
       const uint32_t slot = m & 1, aph = (m >> 1) & 1;
       bool ready = true;
       if (lane == 0) ready = mbar_wait(smem_u32(&bar_tempty[slot]), aph ^ 1, &abort_flag, A.err, A.sleep_mma);
@@ -428,7 +523,8 @@ batched_mac_kernel(const __grid_constant__ CUtensorMap pmap, PrimeSet P, BatchAr
 #pragma unroll
           for (int k = 0; k < kBK / 16; ++k)
             mma_f16(dt, ad + 2 * k, bd + 2 * k, (kc > 0 || k > 0) ? 1u : 0u);
-          mma_commit(smem_u32(&bar_empty[st]));
+          if (CL > 1) mma_commit_mc1(smem_u32(&bar_empty[st]), kMask);
+          else mma_commit(smem_u32(&bar_empty[st]));
         }
         __syncwarp();
       }
@@ -437,6 +533,9 @@ batched_mac_kernel(const __grid_constant__ CUtensorMap pmap, PrimeSet P, BatchAr
       __syncwarp();
     }
   } else if (warp < kEpiWarp0) {
+    if (TMA_B) {
+      // the query-digit tiles arrive by TMA: nothing to produce
+    } else {
     // ---------------- query-digit producers ----------------
     // The pre-kernel stored, for every query value, Y_b = X 256^b mod q +
     // 0x8080808080808080 (b = 0..7), whose bytes are the balanced base-256
@@ -453,7 +552,7 @@ batched_mac_kernel(const __grid_constant__ CUtensorMap pmap, PrimeSet P, BatchAr
     // the units or past 2B: such an item reads Y_b = 0x80.., all digits zero)
     auto unit_base = [&](uint32_t m) -> const ulonglong2* {
       Decoded D;
-      if (!unit_of(m, A, D)) return nullptr;
+      if (!unit_of<CL>(m, A, D)) return nullptr;
       const uint32_t bc = D.qt * kQG + bcl;
       if (bc >= twoB) return nullptr;
       return reinterpret_cast<const ulonglong2*>(A.xm) +
@@ -481,7 +580,7 @@ batched_mac_kernel(const __grid_constant__ CUtensorMap pmap, PrimeSet P, BatchAr
     uint64_t g = 0;
     uint32_t cm = 0, ck = 0;
     Decoded Dc;
-    bool have = unit_of(0, A, Dc);
+    bool have = unit_of<CL>(0, A, Dc);
     while (have) {
       ulonglong2 cur[4];
 #pragma unroll
@@ -498,7 +597,8 @@ batched_mac_kernel(const __grid_constant__ CUtensorMap pmap, PrimeSet P, BatchAr
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       __syncwarp();
       if (lane == 0) mbar_arrive(smem_u32(&bar_full[st]));
-      if (++ck == chunks) { ck = 0; ++cm; have = unit_of(cm, A, Dc); }
+      if (++ck == chunks) { ck = 0; ++cm; have = unit_of<CL>(cm, A, Dc); }
+    }
     }
   } else {
     // ---------------- epilogue ----------------
@@ -513,7 +613,7 @@ batched_mac_kernel(const __grid_constant__ CUtensorMap pmap, PrimeSet P, BatchAr
     const uint32_t et = threadIdx.x - 32 * kEpiWarp0;
     for (uint32_t m = 0; !abort_flag; ++m) {
       Decoded D;
-      if (!unit_of(m, A, D)) break;
+      if (!unit_of<CL>(m, A, D)) break;
       const uint32_t slot = m & 1, aph = (m >> 1) & 1;
       // lane 0 waits for the accumulator, the warp follows its decision
       bool ready = true;
@@ -556,6 +656,246 @@ batched_mac_kernel(const __grid_constant__ CUtensorMap pmap, PrimeSet P, BatchAr
 
   tc_fence_before();
   __syncthreads();
+  if (CL > 1) cluster_barrier();  // no CTA leaves while a peer may still reach its memory
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem));
+  }
+}
+
+// ------------------------------------------------------------------------
+// The TMA-fed single-SM tile with whole-sector output stores.  The outputs of
+// one unit (one slot) are 128 blocks x 32 (b, c) words, every one of them in
+// a different 393 KB-apart row of the [B][K][2][L][N] response layout, so
+// one slot alone can only write 8 bytes (or 16 for a slot pair) per row.
+// Here a CTA takes four consecutive slots of the same (prime, database tile,
+// query tile) back to back; the epilogue keeps the first two slots' results
+// in registers and the third in shared memory, and writes each output row's
+// four slots as one 32-byte store (a whole DRAM sector).  Both operands
+// arrive by TMA, so the CTA has no producer warps: 10 warps (TMA, MMA, 8
+// epilogue).  CL > 1: clusters that share each query tile by multicast, as in
+// batched_mac_kernel.
+// ------------------------------------------------------------------------
+namespace quad {
+constexpr int kEpiWarp0 = 2;
+constexpr int kEpiWarps = 8;
+constexpr int kThreads = 32 * (kEpiWarp0 + kEpiWarps);  // 320
+// stages + the third held slot (16 outputs per epilogue thread)
+constexpr int kHeldBytes = 16 * 32 * kEpiWarps * 8;
+constexpr int kSmem = kStages * kStageBytes + kHeldBytes + 1024;
+}  // namespace quad
+
+// Unit m of this CTA: quad p = cluster + (m / 4) (clusters in the grid) over
+// A.units quads, decoded as ((j S/4 + s'/4) KTG + ktg) QT + qt; slot s' = 4
+// (s'/4) + m % 4; database tile CL ktg + rank.
+template <int CL>
+__device__ __forceinline__ bool unit_of_quad(uint32_t m, const BatchArgs& A, Decoded& D) {
+  const uint32_t cid = blockIdx.x / CL, rank = blockIdx.x % CL, ncl = gridDim.x / CL;
+  const uint64_t p = cid + (uint64_t)(m >> 2) * ncl;
+  if (p >= A.units) return false;
+  const uint32_t quarter = A.s_count >> 2;
+  const uint32_t ktg = A.KT / CL;
+  uint32_t r = (uint32_t)p;
+  D.qt = r % A.QT;
+  r /= A.QT;
+  D.kt = (r % ktg) * CL + rank;
+  r /= ktg;
+  D.sl = 4 * (r % quarter) + (m & 3);
+  D.s = A.s_begin + D.sl;
+  D.j = r / quarter;
+  return true;
+}
+
+__device__ __forceinline__ void st_global_v4_b64(uint64_t* p, uint64_t a, uint64_t b, uint64_t c,
+                                                 uint64_t d) {
+  asm volatile("st.global.v4.b64 [%0], {%1, %2, %3, %4};" ::"l"(p), "l"(a), "l"(b), "l"(c), "l"(d)
+               : "memory");
+}
+
+template <int CL>
+__global__ void __launch_bounds__(quad::kThreads, 1)
+batched_mac_quad_kernel(const __grid_constant__ CUtensorMap pmap, const __grid_constant__ CUtensorMap xmap,
+                        PrimeSet P, BatchArgs A) {
+  constexpr int kEpiWarp0 = quad::kEpiWarp0;
+  constexpr int kEpiWarps = quad::kEpiWarps;
+  extern __shared__ __align__(1024) uint8_t dsmem[];
+  __shared__ __align__(8) uint64_t bar_full[kStages], bar_empty[kStages];
+  __shared__ __align__(8) uint64_t bar_tfull[2], bar_tempty[2];
+  __shared__ uint32_t tmem_base_slot;
+  __shared__ volatile int abort_flag;
+
+  const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  uint8_t* base = dsmem + ((1024 - (smem_u32(dsmem) & 1023)) & 1023);
+  const uint32_t sbase = smem_u32(base);
+
+  if (threadIdx.x == 0) {
+    abort_flag = 0;
+    for (int s = 0; s < kStages; ++s) {
+      mbar_init(smem_u32(&bar_full[s]), 1);
+      mbar_init(smem_u32(&bar_empty[s]), CL);
+    }
+    for (int a = 0; a < 2; ++a) {
+      mbar_init(smem_u32(&bar_tfull[a]), 1);
+      mbar_init(smem_u32(&bar_tempty[a]), kEpiWarps);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(
+                     smem_u32(&tmem_base_slot)));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (CL > 1) cluster_barrier();  // every CTA's barriers exist before any multicast
+  tc_fence_after();
+  const uint32_t tmem = tmem_base_slot;
+  const uint32_t N = P.N;
+  const uint32_t crank = blockIdx.x % CL;
+  constexpr uint16_t kMask = (uint16_t)((1u << CL) - 1);
+
+  if (warp == 0) {
+    // ---------------- TMA producer: database tile + query tile ----------------
+    uint64_t g = 0;
+    bool ok = true;
+    for (uint32_t m = 0; ok; ++m) {
+      Decoded D;
+      if (!unit_of_quad<CL>(m, A, D)) break;
+      for (uint32_t kc = 0; kc < A.chunks; ++kc, ++g) {
+        const uint32_t st = (uint32_t)(g % kStages), ph = (uint32_t)((g / kStages) & 1);
+        bool ready = true;
+        if (lane == 0)
+          ready = CL > 1 ? mbar_wait_cluster(smem_u32(&bar_empty[st]), ph ^ 1, &abort_flag, A.err, A.sleep_tma)
+                         : mbar_wait(smem_u32(&bar_empty[st]), ph ^ 1, &abort_flag, A.err, A.sleep_tma);
+        if (!__shfl_sync(0xffffffffu, (int)ready, 0)) { ok = false; break; }
+        if (lane == 0) {
+          const uint32_t full = smem_u32(&bar_full[st]);
+          mbar_arrive_tx(full, kStageBytes);
+          tma_load_3d(sbase + st * kStageBytes, &pmap, (int)(kc * kBK), (int)(D.kt * kBM),
+                      (int)(D.j * N + D.s), full);
+          if (CL == 1)
+            tma_load_3d(sbase + st * kStageBytes + kATile, &xmap, (int)(kc * kBK), (int)(D.qt * kBN),
+                        (int)(D.j * A.s_count + D.sl), full);
+          else
+            tma_load_3d_mc(sbase + st * kStageBytes + kATile + crank * (kBTile / CL), &xmap, (int)(kc * kBK),
+                           (int)(D.qt * kBN + crank * (kBN / CL)), (int)(D.j * A.s_count + D.sl), full,
+                           kMask);
+        }
+        __syncwarp();
+      }
+    }
+    // drain: every issued copy completes before the CTA may exit
+    if (!ok && lane == 0) {
+      const uint64_t first = g > kStages ? g - kStages : 0;
+      for (uint64_t h = first; h < g; ++h) {
+        const uint32_t st = (uint32_t)(h % kStages), ph = (uint32_t)((h / kStages) & 1);
+        const unsigned long long t0 = clock64();
+        while (!mbar_try(smem_u32(&bar_full[st]), ph) && clock64() - t0 < kWaitCycles) {
+        }
+      }
+    }
+    __syncwarp();
+  } else if (warp == 1) {
+    // ---------------- MMA issuer ----------------
+    uint64_t g = 0;
+    bool ok = true;
+    for (uint32_t m = 0; ok; ++m) {
+      Decoded D;
+      if (!unit_of_quad<CL>(m, A, D)) break;
+      const uint32_t slot = m & 1, aph = (m >> 1) & 1;
+      bool ready = true;
+      if (lane == 0) ready = mbar_wait(smem_u32(&bar_tempty[slot]), aph ^ 1, &abort_flag, A.err, A.sleep_mma);
+      if (!__shfl_sync(0xffffffffu, (int)ready, 0)) break;
+      tc_fence_after();
+      const uint32_t dt = tmem + slot * kBN;
+      for (uint32_t kc = 0; kc < A.chunks; ++kc, ++g) {
+        const uint32_t st = (uint32_t)(g % kStages), ph = (uint32_t)((g / kStages) & 1);
+        if (lane == 0) ready = mbar_wait(smem_u32(&bar_full[st]), ph, &abort_flag, A.err, A.sleep_mma);
+        if (!__shfl_sync(0xffffffffu, (int)ready, 0)) { ok = false; break; }
+        tc_fence_after();
+        if (lane == 0) {
+          const uint32_t a_addr = sbase + st * kStageBytes, b_addr = a_addr + kATile;
+          const uint64_t ad = smem_desc(a_addr), bd = smem_desc(b_addr);
+#pragma unroll
+          for (int k = 0; k < kBK / 16; ++k)
+            mma_f16(dt, ad + 2 * k, bd + 2 * k, (kc > 0 || k > 0) ? 1u : 0u);
+          if (CL > 1) mma_commit_mc1(smem_u32(&bar_empty[st]), kMask);
+          else mma_commit(smem_u32(&bar_empty[st]));
+        }
+        __syncwarp();
+      }
+      if (!ok) break;
+      if (lane == 0) mma_commit(smem_u32(&bar_tfull[slot]));
+      __syncwarp();
+    }
+  } else {
+    // ---------------- epilogue ----------------
+    // Lane = database block k of the tile; each thread owns 16 outputs (4
+    // column chunks x 4 (b, c) rows) of its block per slot.  Slots 0..2 of a
+    // quad are held in registers, slot 3 writes all four.
+    const uint32_t quarter = warp & 3;                 // TMEM lanes 32 quarter ..
+    const uint32_t chalf = (warp - kEpiWarp0) >> 2;    // column half of the tile
+    const uint32_t L = P.L;
+    const uint32_t et = threadIdx.x - 32 * kEpiWarp0;
+    // slots 0, 1 of a quad in registers; slot 2 in shared memory, [output
+    // i][epilogue thread] (conflict-free)
+    uint64_t held[2][16];
+    uint64_t* held2 = reinterpret_cast<uint64_t*>(base + kStages * kStageBytes);
+    bool live = true;
+    for (uint32_t m = 0; live && !abort_flag; m += 4) {
+#pragma unroll
+      for (int sub = 0; sub < 4; ++sub) {
+        Decoded D;
+        if (!live || !unit_of_quad<CL>(m + sub, A, D)) { live = false; break; }
+        const uint32_t u = m + sub;
+        const uint32_t slot = u & 1, aph = (u >> 1) & 1;
+        bool ready = true;
+        if (lane == 0) ready = mbar_wait(smem_u32(&bar_tfull[slot]), aph, &abort_flag, A.err, A.sleep_epi);
+        if (!__shfl_sync(0xffffffffu, (int)ready, 0)) { live = false; break; }
+        tc_fence_after();
+        const uint32_t k = D.kt * kBM + quarter * 32 + lane;
+        const bool k_ok = k < A.K;
+#pragma unroll
+        for (uint32_t ci = 0; ci < 4; ++ci) {
+          const uint32_t cc = chalf * 4 + ci;
+          uint64_t res[4];
+          epilogue_values(tmem + ((quarter * 32) << 16) + slot * kBN + cc * 32, A, P, D, res);
+          if (sub < 2) {
+#pragma unroll
+            for (int o = 0; o < 4; ++o) held[sub][ci * 4 + o] = res[o];
+          } else if (sub == 2) {
+#pragma unroll
+            for (int o = 0; o < 4; ++o) held2[(ci * 4 + o) * (32 * kEpiWarps) + et] = res[o];
+          } else {
+#pragma unroll
+            for (int o = 0; o < 4; ++o) {
+              const uint32_t bc = D.qt * kQG + cc * 4 + o;
+              if (k_ok && bc < 2 * A.B) {
+                const uint32_t b = bc >> 1, c = bc & 1;
+                uint64_t* dst = A.out + ((((uint64_t)b * A.K + k) * 2 + c) * L + D.j) * N + D.s - 3;
+                const uint64_t h2 = held2[(ci * 4 + o) * (32 * kEpiWarps) + et];
+                if (A.out16 == 2) {
+                  st_global_v4_b64(dst, held[0][ci * 4 + o], held[1][ci * 4 + o], h2, res[o]);
+                } else {
+                  dst[0] = held[0][ci * 4 + o];
+                  dst[1] = held[1][ci * 4 + o];
+                  dst[2] = h2;
+                  dst[3] = res[o];
+                }
+              }
+            }
+          }
+        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(smem_u32(&bar_tempty[slot]));
+      }
+    }
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  if (CL > 1) cluster_barrier();  // no CTA leaves while a peer may still reach its memory
   if (warp == 1) {
     tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem));
@@ -686,6 +1026,11 @@ __device__ __forceinline__ void mma_commit_mc(uint32_t bar, uint16_t mask) {
       : "memory");
 }
 
+// TMA_B: each CTA's half of the query-digit tile arrives by TMA from the fp16
+// rows of expand_query_f16_kernel (xmap, boxes of 128 rows) and the producer
+// warps stay idle; otherwise xmap holds the byte-interleaved multiples and the
+// producers generate the digits.
+template <bool TMA_B>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(pair::kThreads, 1)
 batched_mac_pair_kernel(const __grid_constant__ CUtensorMap pmap, const __grid_constant__ CUtensorMap xmap,
                         PrimeSet P, BatchArgs A) {
@@ -725,7 +1070,7 @@ batched_mac_pair_kernel(const __grid_constant__ CUtensorMap pmap, const __grid_c
     }
     for (int s = 0; s < kStages; ++s) {
       // leader: its TMA thread (expecting both CTAs' bytes) + both CTAs' producers
-      mbar_init(smem_u32(&bar_full[s]), 1 + 2 * kProdWarps);
+      mbar_init(smem_u32(&bar_full[s]), TMA_B ? 1 : 1 + 2 * kProdWarps);
       mbar_init(smem_u32(&bar_empty[s]), 1);
     }
     for (int a = 0; a < 2; ++a) {
@@ -766,32 +1111,42 @@ batched_mac_pair_kernel(const __grid_constant__ CUtensorMap pmap, const __grid_c
         const uint32_t twoB = 2 * A.B, bc0 = F.qt * kQG + rank * kQGh;
         if (bc0 < twoB) {
           const uint32_t groups = twoB - bc0 < (uint32_t)kQGh ? twoB - bc0 : (uint32_t)kQGh;
-          prefetch_l2(A.xm + (((uint64_t)F.j * A.s_count + F.sl) * twoB + bc0) * A.dpad * 8,
-                      groups * 64u * A.dpad);
+          if (TMA_B)
+            prefetch_l2(A.xh + (((uint64_t)F.j * A.s_count + F.sl) * 8 * twoB + 8 * bc0) * 8 * A.dpad,
+                        groups * 128u * A.dpad);
+          else
+            prefetch_l2(A.xm + (((uint64_t)F.j * A.s_count + F.sl) * twoB + bc0) * A.dpad * 8,
+                        groups * 64u * A.dpad);
         }
       }
       for (uint32_t kc = 0; kc < A.chunks; ++kc, ++g) {
         const uint32_t st = (uint32_t)(g % kStages), ph = (uint32_t)((g / kStages) & 1);
         const uint32_t xs = (uint32_t)(g % kXStages), xph = (uint32_t)((g / kXStages) & 1);
         bool ready = true;
-        // this CTA's query multiples of the stage: 16 row groups x 8 dimensions
-        if (lane == 0) ready = mbar_wait_cl(smem_u32(&bar_xempty[xs]), xph ^ 1, &abort_flag, A.err, A.sleep_tma);
-        if (!__shfl_sync(0xffffffffu, (int)ready, 0)) { ok = false; break; }
-        if (lane == 0) {
-          const uint32_t xf = smem_u32(&bar_xfull[xs]);
-          mbar_arrive_tx(xf, kXTile);
-          tma_load_4d(xbase + xs * kXTile, &xmap, 0, (int)kc, (int)(D.qt * kQG + rank * kQGh),
-                      (int)(D.j * A.s_count + D.sl), xf);
+        if (!TMA_B) {
+          // this CTA's query multiples of the stage: 16 row groups x 8 dimensions
+          if (lane == 0) ready = mbar_wait_cl(smem_u32(&bar_xempty[xs]), xph ^ 1, &abort_flag, A.err, A.sleep_tma);
+          if (!__shfl_sync(0xffffffffu, (int)ready, 0)) { ok = false; break; }
+          if (lane == 0) {
+            const uint32_t xf = smem_u32(&bar_xfull[xs]);
+            mbar_arrive_tx(xf, kXTile);
+            tma_load_4d(xbase + xs * kXTile, &xmap, 0, (int)kc, (int)(D.qt * kQG + rank * kQGh),
+                        (int)(D.j * A.s_count + D.sl), xf);
+          }
+          __syncwarp();
         }
-        __syncwarp();
         if (lane == 0) ready = mbar_wait_cl(smem_u32(&bar_empty[st]), ph ^ 1, &abort_flag, A.err, A.sleep_tma);
         if (!__shfl_sync(0xffffffffu, (int)ready, 0)) { ok = false; break; }
         if (lane == 0) {
           const uint32_t full = smem_u32(&bar_full[st]);
-          if (rank == 0) mbar_arrive_tx(full, 2 * kATile);
+          if (rank == 0) mbar_arrive_tx(full, TMA_B ? 2 * kStageBytes : 2 * kATile);
           tma_load_3d_pair(sbase + st * kStageBytes, &pmap, (int)(kc * kBK),
                            (int)(D.kt * 2 * kBM + rank * kBM), (int)(D.j * N + D.s),
                            map_rank(full, 0));
+          if (TMA_B)
+            tma_load_3d_pair(sbase + st * kStageBytes + kATile, &xmap, (int)(kc * kBK),
+                             (int)(D.qt * kBN + rank * pair::kBNh), (int)(D.j * A.s_count + D.sl),
+                             map_rank(full, 0));
         }
         __syncwarp();
       }
@@ -845,6 +1200,9 @@ batched_mac_pair_kernel(const __grid_constant__ CUtensorMap pmap, const __grid_c
       __syncwarp();
     }
   } else if (warp < kEpiWarp0) {
+    if (TMA_B) {
+      // the query-digit halves arrive by TMA: nothing to produce
+    } else {
     // ---------------- query-digit producers (both CTAs) ----------------
     // this CTA's half of the tile's query rows: row groups rank 16 .. rank 16
     // + 15; their multiples arrive by TMA (rows past 2B read as zero, whose
@@ -876,6 +1234,7 @@ batched_mac_pair_kernel(const __grid_constant__ CUtensorMap pmap, const __grid_c
         if (lane == 0) mbar_arrive_cluster(map_rank(smem_u32(&bar_full[st]), 0));
       }
       if (!ok) break;
+    }
     }
   } else {
     // ---------------- epilogue (both CTAs) ----------------
@@ -999,6 +1358,66 @@ __global__ void __launch_bounds__(256) expand_query_kernel(PrimeSet P, const uin
   }
 }
 
+// The query-digit rows of the TMA-fed tiles, fp16, for the slots [s_begin,
+// s_begin + S): xh[j][s'][8 bc + a][8 i + b] = digit a of X_b = ct[bc][i]
+// 256^b mod q_j (balanced base-256 digits in [-128, 127]: the bytes of X_b +
+// 0x80..80, minus 128), zero for i >= d; bc = 2 b_query + c.  This is the
+// B operand of the contraction exactly as the MMA reads it (rows (bc, a),
+// contraction (i, b)), so the MAC kernel moves it with plain tile copies.  A
+// block takes (j, bc, 8 dimensions, 32 slots): coalesced ciphertext reads
+// along the slots, a shared-memory transpose, then 128 contiguous bytes per
+// (slot, digit row).
+__global__ void __launch_bounds__(256) expand_query_f16_kernel(PrimeSet P, const uint64_t* __restrict__ ct,
+                                    uint32_t B, uint32_t d, uint32_t dpad, uint32_t s_begin, uint32_t S,
+                                    const W256 W, uint4* __restrict__ xh) {
+  __shared__ uint4 tile[32][8][8];  // [slot][digit a][dim in block], 8 fp16 (b = 0..7) each
+  const uint32_t s0 = blockIdx.x * 32, ib = blockIdx.y;
+  const uint32_t j = blockIdx.z / (2 * B), bc = blockIdx.z % (2 * B);
+  const uint32_t b = bc >> 1, c = bc & 1;
+  const uint32_t N = P.N, L = P.L;
+  const uint64_t q = P.q[j];
+  {
+    const uint32_t il = threadIdx.x >> 5, sl = threadIdx.x & 31;
+    const uint32_t i = ib * 8 + il;
+    uint64_t v[8];
+    if (i < d && s0 + sl < S) {
+      const uint64_t X = ct[((((uint64_t)b * d + i) * 2 + c) * L + j) * N + s_begin + s0 + sl];
+      v[0] = X;
+#pragma unroll
+      for (int k = 1; k < 8; ++k) v[k] = mul_shoup(X, W.w[j][k], W.ws[j][k], q);
+    } else {
+#pragma unroll
+      for (int k = 0; k < 8; ++k) v[k] = 0;
+    }
+#pragma unroll
+    for (int k = 0; k < 8; ++k) v[k] += 0x8080808080808080ull;  // bytes = digits + 128
+#pragma unroll
+    for (int a = 0; a < 8; ++a) {
+      uint32_t h[4];
+#pragma unroll
+      for (int m = 0; m < 4; ++m) {
+        // fp16 of (byte - 128) for b = 2m, 2m + 1: 0x64vv = 1024 + v exactly,
+        // minus 1152
+        const uint32_t lo = (uint32_t)(v[2 * m] >> (8 * a)) & 255u;
+        const uint32_t hi = (uint32_t)(v[2 * m + 1] >> (8 * a)) & 255u;
+        const uint32_t hv = 0x64006400u | lo | (hi << 16);
+        uint32_t r;
+        asm("sub.rn.f16x2 %0, %1, %2;" : "=r"(r) : "r"(hv), "r"(0x64806480u));
+        h[m] = r;
+      }
+      tile[sl][a][il] = make_uint4(h[0], h[1], h[2], h[3]);
+    }
+  }
+  __syncthreads();
+  // (slot, a) rows of 128 bytes: 8 sixteen-byte words, word il = dims 8 ib + il
+  const uint32_t wpr = dpad;  // sixteen-byte words per digit row (8 dpad fp16)
+  for (uint32_t e = threadIdx.x; e < 32 * 8 * 8; e += blockDim.x) {
+    const uint32_t sl = e >> 6, a = (e >> 3) & 7, il = e & 7;
+    if (s0 + sl >= S) continue;
+    xh[(((uint64_t)j * S + s0 + sl) * 16 * B + 8 * bc + a) * wpr + ib * 8 + il] = tile[sl][a][il];
+  }
+}
+
 std::mutex g_encode_mu;
 PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
 
@@ -1075,15 +1494,29 @@ cudaError_t launch_batched_mac(const PrimeSet& P, const void* map, const uint16_
   A.prefetch_units = tune[4];
   A.plimb = plimb;
   A.out = out;
-  A.out16 = (reinterpret_cast<uintptr_t>(out) & 15) == 0 ? 1u : 0u;
+  // 2: 32-byte aligned, 1: 16-byte aligned (paired / quad stores)
+  A.out16 = (reinterpret_cast<uintptr_t>(out) & 31) == 0 ? 2u : (reinterpret_cast<uintptr_t>(out) & 15) == 0 ? 1u : 0u;
   A.err = err;
   A.B = B;
   A.d = d;
   A.dpad = (d + 7) / 8 * 8;
   A.K = (uint32_t)K;
-  const bool use_pair = tune[6] == 1;   // 256-block tiles on SM pairs
+  // tile shape: 0..3: bit 0 = SM pair (256 blocks) instead of one SM (128
+  // blocks); bit 1 = query digits by TMA from fp16 rows instead of producer
+  // warps.  4, 5: one SM per tile, TMA-fed, in clusters of 2 or 4 CTAs that
+  // share each query tile by multicast.
+  // 6, 7: one SM per tile, TMA-fed, four slots per CTA with 32-byte output
+  // stores (batched_mac_quad_kernel), alone or in clusters of 2.
+  const uint32_t tile = tune[6];
+  const bool use_pair = tile < 4 && (tile & 1) != 0;
+  const bool tma_b = tile >= 2;
+  const bool quads = tile >= 6;
   A.QT = (2 * B + kQG - 1) / kQG;
   A.KT = (uint32_t)(use_pair ? (K + 2 * pair::kBM - 1) / (2 * pair::kBM) : (K + kBM - 1) / kBM);
+  // tile 7 on an odd number of database tiles runs as tile 6 rather than
+  // padding a whole tile of zeros per cluster
+  const int CL = tile == 4 ? 2 : tile == 5 ? 4 : (tile == 7 && A.KT % 2 == 0) ? 2 : 1;
+  A.KT = (A.KT + CL - 1) / CL * CL;  // whole clusters (tiles past K load zeros and store nothing)
   A.chunks = A.dpad / 8;
   W256 W;
   memset(&W, 0, sizeof(W));
@@ -1103,13 +1536,14 @@ cudaError_t launch_batched_mac(const PrimeSet& P, const void* map, const uint16_
     A.lo_bias[j] = ((1ull << 49) + P.q[j] - 1) / P.q[j] * P.q[j];
   }
   // slot ranges bound the scratch of the query multiples (tune[5] MiB, at
-  // least one slot)
-  const uint64_t per_slot = (uint64_t)P.L * 2 * B * A.dpad * 8 * sizeof(uint64_t);
+  // least one slot): byte-interleaved multiples (8 bytes per digit row and
+  // dimension) or fp16 digit rows (16 bytes)
+  const uint64_t per_slot = (uint64_t)P.L * 2 * B * A.dpad * 8 * (tma_b ? 16 : 8);
   uint64_t S = ((uint64_t)tune[5] << 20) / per_slot;
-  S &= ~1ull;                 // the single-SM tile takes slots in pairs
-  if (S < 2) S = 2;
+  S &= quads ? ~3ull : ~1ull;   // the single-SM tiles take slots in pairs or quads
+  if (S < (quads ? 4u : 2u)) S = quads ? 4 : 2;
   if (S > P.N) S = P.N;
-  const size_t smem = use_pair ? (size_t)pair::kSmem : (size_t)kSmem1;
+  const size_t smem = use_pair ? (size_t)pair::kSmem : quads ? (size_t)quad::kSmem : (size_t)kSmem1;
   // kernel attributes and the number of co-resident CTA pairs (clusters of 2
   // need two SMs of one GPC) are set up once per device, outside any capture
   int dev = 0;
@@ -1117,29 +1551,80 @@ cudaError_t launch_batched_mac(const PrimeSet& P, const void* map, const uint16_
   if (e != cudaSuccess) return e;
   static std::mutex setup_mu;
   static int pairs_resident_dev[64] = {};
+  static int clusters_resident_dev[64][3] = {};   // clusters of 2 and of 4 (tiles 4, 5), quad clusters of 2 (7)
   static bool configured_dev[64] = {};
   if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
-  int pairs_resident = 0;
+  int pairs_resident = 0, clusters_resident = 0;
   {
     std::lock_guard<std::mutex> lock(setup_mu);
     if (!configured_dev[dev]) {
-      e = cudaFuncSetAttribute(batched_mac_pair_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+      const void* cluster_kernels[2] = {(const void*)batched_mac_kernel<true, 2>,
+                                        (const void*)batched_mac_kernel<true, 4>};
+      for (int c = 0; c < 2 && e == cudaSuccess; ++c) {
+        e = cudaFuncSetAttribute(cluster_kernels[c], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem1);
+        if (e != cudaSuccess) break;
+        cudaLaunchConfig_t cfg = {};
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = 2u << c;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.gridDim = dim3((unsigned)((sms > 0 ? sms : 148) / (2 << c) * (2 << c)));
+        cfg.blockDim = dim3(kThreads);
+        cfg.dynamicSmemBytes = kSmem1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        e = cudaOccupancyMaxActiveClusters(&clusters_resident_dev[dev][c], cluster_kernels[c], &cfg);
+      }
+      if (e != cudaSuccess) return e;
+      e = cudaFuncSetAttribute(batched_mac_pair_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)pair::kSmem);
       if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(batched_mac_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        e = cudaFuncSetAttribute(batched_mac_pair_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)pair::kSmem);
+      if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(batched_mac_kernel<false, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)kSmem1);
+      if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(batched_mac_kernel<true, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)kSmem1);
+      if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(batched_mac_quad_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)quad::kSmem);
+      if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(batched_mac_quad_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)quad::kSmem);
+      if (e == cudaSuccess) {
+        cudaLaunchConfig_t cfg = {};
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = 2;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.gridDim = dim3((unsigned)((sms > 0 ? sms : 148) / 2 * 2));
+        cfg.blockDim = dim3(quad::kThreads);
+        cfg.dynamicSmemBytes = quad::kSmem;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        e = cudaOccupancyMaxActiveClusters(&clusters_resident_dev[dev][2], batched_mac_quad_kernel<2>, &cfg);
+      }
       if (e != cudaSuccess) return e;
       cudaLaunchConfig_t cfg = {};
       cfg.gridDim = dim3(2 * (unsigned)(sms > 0 ? sms / 2 : 74));
       cfg.blockDim = dim3(pair::kThreads);
       cfg.dynamicSmemBytes = pair::kSmem;
-      e = cudaOccupancyMaxActiveClusters(&pairs_resident_dev[dev], batched_mac_pair_kernel, &cfg);
+      e = cudaOccupancyMaxActiveClusters(&pairs_resident_dev[dev], batched_mac_pair_kernel<false>, &cfg);
       if (e != cudaSuccess) return e;
       configured_dev[dev] = true;
     }
     pairs_resident = pairs_resident_dev[dev];
+    if (CL > 1) clusters_resident = clusters_resident_dev[dev][quads ? 2 : CL == 2 ? 0 : 1];
   }
   if (use_pair && pairs_resident < 1) return cudaErrorInvalidConfiguration;
+  if (CL > 1 && clusters_resident < 1) return cudaErrorInvalidConfiguration;
+  PFN_cuTensorMapEncodeTiled_v12000 enc = nullptr;
+  e = get_encode(&enc);
+  if (e != cudaSuccess) return e;
   uint64_t* scratch = nullptr;
   e = cudaMallocAsync(&scratch, per_slot * S, st);
   if (e != cudaSuccess) return e;
@@ -1150,38 +1635,96 @@ cudaError_t launch_batched_mac(const PrimeSet& P, const void* map, const uint16_
     A.s_begin = (uint32_t)s0;
     A.s_count = cnt;
     A.xm = scratch;
-    // tile 0 counts slot pairs (both halves in one CTA), tile 1 single slots
-    A.units = (uint64_t)P.L * (use_pair ? cnt : cnt / 2) * A.KT * A.QT;
+    A.xh = reinterpret_cast<const uint16_t*>(scratch);
+    // one-SM tiles count slot pairs or quads (all in one CTA; per cluster of
+    // CL database tiles), SM pairs single slots
+    A.units = (uint64_t)P.L * (use_pair ? cnt : quads ? cnt / 4 : cnt / 2) * (A.KT / CL) * A.QT;
     if (A.units >= (1ull << 31)) { e = cudaErrorInvalidValue; break; }
-    expand_query_kernel<<<dim3((cnt + 31) / 32, A.dpad / 8, P.L * 2 * B), 256, 0, st>>>(
-        P, ct, B, d, A.dpad, (uint32_t)s0, cnt, W,
-        reinterpret_cast<ulonglong2*>(scratch));
-    e = cudaGetLastError();
-    if (e != cudaSuccess) break;
-    if (use_pair) {
-      // query multiples of this range as a tensor: [L S'][2B][dpad / 8][64 u64],
-      // boxes of 16 row groups x one 8-dimension block (8 KB)
-      CUtensorMap xmap;
-      {
-        PFN_cuTensorMapEncodeTiled_v12000 enc = nullptr;
-        e = get_encode(&enc);
-        if (e != cudaSuccess) break;
+    const dim3 xgrid((cnt + 31) / 32, A.dpad / 8, P.L * 2 * B);
+    CUtensorMap xmap;
+    CUresult cr = CUDA_SUCCESS;
+    if (tma_b) {
+      expand_query_f16_kernel<<<xgrid, 256, 0, st>>>(P, ct, B, d, A.dpad, (uint32_t)s0, cnt, W,
+                                                     reinterpret_cast<uint4*>(scratch));
+      // fp16 digit rows as a tensor [L S'][16 B][8 dpad]; boxes of 64
+      // contraction columns x 256 rows (one SM) or 128 rows (each CTA of a pair)
+      const cuuint64_t dims[3] = {8ull * A.dpad, 16ull * B, (cuuint64_t)P.L * cnt};
+      const cuuint64_t strides[2] = {16ull * A.dpad, 16ull * B * 16ull * A.dpad};
+      const cuuint32_t box[3] = {(cuuint32_t)kBK, (cuuint32_t)(use_pair ? pair::kBNh : kBN / CL), 1};
+      const cuuint32_t estr[3] = {1, 1, 1};
+      cr = enc(&xmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 3, scratch, dims, strides, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    } else {
+      expand_query_kernel<<<xgrid, 256, 0, st>>>(P, ct, B, d, A.dpad, (uint32_t)s0, cnt, W,
+                                                 reinterpret_cast<ulonglong2*>(scratch));
+      if (use_pair) {
+        // query multiples of this range as a tensor: [L S'][2B][dpad / 8][64 u64],
+        // boxes of 16 row groups x one 8-dimension block (8 KB)
         const cuuint64_t dims[4] = {64, A.dpad / 8, 2ull * B, (cuuint64_t)P.L * cnt};
         const cuuint64_t strides[3] = {512, 64ull * A.dpad, 128ull * B * A.dpad};
         const cuuint32_t box[4] = {64, 1, (cuuint32_t)pair::kQGh, 1};
         const cuuint32_t estr[4] = {1, 1, 1, 1};
-        CUresult cr = enc(&xmap, CU_TENSOR_MAP_DATA_TYPE_UINT64, 4, scratch, dims, strides, box, estr,
-                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-        if (cr != CUDA_SUCCESS) { e = cudaErrorInvalidValue; break; }
+        cr = enc(&xmap, CU_TENSOR_MAP_DATA_TYPE_UINT64, 4, scratch, dims, strides, box, estr,
+                 CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                 CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+      } else {
+        memcpy(&xmap, &m, sizeof(m));   // unused by the producer-fed tile
       }
+    }
+    e = cudaGetLastError();
+    if (e != cudaSuccess) break;
+    if (cr != CUDA_SUCCESS) { e = cudaErrorInvalidValue; break; }
+    if (use_pair) {
       uint64_t clusters = (uint64_t)pairs_resident;
       if (clusters > A.units) clusters = A.units;
-      batched_mac_pair_kernel<<<(unsigned)(2 * clusters), pair::kThreads, smem, st>>>(m, xmap, P, A);
+      if (tma_b)
+        batched_mac_pair_kernel<true><<<(unsigned)(2 * clusters), pair::kThreads, smem, st>>>(m, xmap, P, A);
+      else
+        batched_mac_pair_kernel<false><<<(unsigned)(2 * clusters), pair::kThreads, smem, st>>>(m, xmap, P, A);
+    } else if (quads) {
+      uint64_t clusters = CL > 1 ? (uint64_t)clusters_resident : (uint64_t)(sms > 0 ? sms : 148);
+      if (clusters > A.units) clusters = A.units;
+      cudaLaunchConfig_t cfg = {};
+      cudaLaunchAttribute at[1];
+      at[0].id = cudaLaunchAttributeClusterDimension;
+      at[0].val.clusterDim.x = (unsigned)CL;
+      at[0].val.clusterDim.y = 1;
+      at[0].val.clusterDim.z = 1;
+      cfg.gridDim = dim3((unsigned)(clusters * CL));
+      cfg.blockDim = dim3(quad::kThreads);
+      cfg.dynamicSmemBytes = smem;
+      cfg.stream = st;
+      cfg.attrs = at;
+      cfg.numAttrs = CL > 1 ? 1 : 0;
+      if (CL == 2) e = cudaLaunchKernelEx(&cfg, batched_mac_quad_kernel<2>, m, xmap, P, A);
+      else e = cudaLaunchKernelEx(&cfg, batched_mac_quad_kernel<1>, m, xmap, P, A);
+      if (e != cudaSuccess) break;
+    } else if (CL > 1) {
+      uint64_t clusters = (uint64_t)clusters_resident;
+      if (clusters > A.units) clusters = A.units;
+      cudaLaunchConfig_t cfg = {};
+      cudaLaunchAttribute at[1];
+      at[0].id = cudaLaunchAttributeClusterDimension;
+      at[0].val.clusterDim.x = (unsigned)CL;
+      at[0].val.clusterDim.y = 1;
+      at[0].val.clusterDim.z = 1;
+      cfg.gridDim = dim3((unsigned)(clusters * CL));
+      cfg.blockDim = dim3(kThreads);
+      cfg.dynamicSmemBytes = smem;
+      cfg.stream = st;
+      cfg.attrs = at;
+      cfg.numAttrs = 1;
+      if (CL == 2) e = cudaLaunchKernelEx(&cfg, batched_mac_kernel<true, 2>, m, xmap, P, A);
+      else e = cudaLaunchKernelEx(&cfg, batched_mac_kernel<true, 4>, m, xmap, P, A);
+      if (e != cudaSuccess) break;
     } else {
       uint64_t grid = (uint64_t)(sms > 0 ? sms : 148);
       if (grid > A.units) grid = A.units;
-      batched_mac_kernel<<<(unsigned)grid, kThreads, smem, st>>>(m, P, A);
+      if (tma_b)
+        batched_mac_kernel<true, 1><<<(unsigned)grid, kThreads, smem, st>>>(m, xmap, P, A);
+      else
+        batched_mac_kernel<false, 1><<<(unsigned)grid, kThreads, smem, st>>>(m, xmap, P, A);
     }
     e = cudaGetLastError();
   }

@@ -16,8 +16,10 @@ struct sanns_ctx {
   int mac_variant;          // launch variant of the MAC kernel (autotuned)
   int* d_err;               // device error word raised by bounded waits
   uint32_t batched_tune[7]; // batched kernel: back-off ns (TMA, MMA, producers, epilogue), L2 prefetch
-                            // units, scratch cap (MiB) of the query multiples, tile (0: 128 blocks
-                            // on one SM, 1: 256 blocks on an SM pair)
+                            // units, scratch cap (MiB) of the query multiples, tile (0..3: bit 0 =
+                            // 256 blocks on an SM pair instead of 128 on one SM, bit 1 = query
+                            // digits by TMA from fp16 rows instead of producer warps; 4, 5: one
+                            // SM, TMA-fed, clusters of 2 or 4 sharing the query tile by multicast)
   // circuit privacy: the client's public key (library copy, [2][L][N] NTT
   // form) and its Shoup companions, or NULL; flooding exponent F
   uint64_t* d_pk;
@@ -161,12 +163,14 @@ cudaError_t launch_gather_prepared(const PrimeSet& P, uint32_t d, const sanns_ga
                                    const PrivacyConsts& C, bool ntt_form, cudaStream_t st);
 cudaError_t launch_norms_slot(const PrimeSet& PT, uint32_t* norms, uint64_t K, cudaStream_t st);
 cudaError_t launch_join30(const uint64_t* src, uint64_t* dst, uint64_t count, cudaStream_t st);
+cudaError_t launch_import_pt(const PrimeSet& P, uint64_t* pt, uint64_t count, uint32_t d, int* bad,
+                             cudaStream_t st);
 size_t batched_limb_bytes(uint32_t L, uint32_t N, uint64_t K, uint32_t d);
 cudaError_t launch_wait_selftest(int* err, uint32_t limit_ms, int device, cudaStream_t st);
 cudaError_t measure_mma_rates(int sms, int* d_err, double out[3], cudaStream_t st);
 cudaError_t launch_prepare_limbs(const PrimeSet& P, const uint64_t* pt, uint64_t K, uint32_t d,
                                  uint16_t* plimb, cudaStream_t st);
-constexpr int kBatchedConfigs = 4;  // (tile shape, L2 prefetch) pairs timed by the autotuner
+constexpr int kBatchedConfigs = 16;  // (tile shape 0..7, L2 prefetch 0/1) pairs timed by the autotuner
 int make_limb_map(const PrimeSet& P, const uint16_t* plimb, uint64_t K, uint32_t d, void* map_out);
 cudaError_t launch_batched_mac(const PrimeSet& P, const void* map, const uint16_t* plimb,
                                const uint64_t* ct, uint32_t B,

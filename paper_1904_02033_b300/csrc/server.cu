@@ -494,6 +494,29 @@ __global__ void join30_kernel(const uint64_t* __restrict__ src, uint64_t* __rest
   if (e < count) dst[e] = join30(src[e]);
 }
 
+// Imported plaintexts, in place: canonical residues [K][L][d][N] -> the
+// split30 storage format; a value >= q_j of its prime raises *bad.
+__global__ void import_pt_kernel(PrimeSet P, uint64_t* __restrict__ pt, uint64_t count, uint32_t d,
+                                 int* bad) {
+  const uint64_t e = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+  if (e >= count) return;
+  const uint32_t j = (uint32_t)((e / ((uint64_t)d * P.N)) % P.L);
+  const uint64_t v = pt[e];
+  if (v >= P.q[j]) {
+    atomicExch(bad, 1);
+    pt[e] = 0;
+  } else {
+    pt[e] = split30(v);
+  }
+}
+
+cudaError_t launch_import_pt(const PrimeSet& P, uint64_t* pt, uint64_t count, uint32_t d, int* bad,
+                             cudaStream_t st) {
+  if (count == 0) return cudaSuccess;
+  import_pt_kernel<<<(unsigned)((count + 255) / 256), 256, 0, st>>>(P, pt, count, d, bad);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_join30(const uint64_t* src, uint64_t* dst, uint64_t count, cudaStream_t st) {
   if (count == 0) return cudaSuccess;
   join30_kernel<<<(unsigned)((count + 255) / 256), 256, 0, st>>>(src, dst, count);

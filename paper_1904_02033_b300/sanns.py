@@ -44,6 +44,7 @@ _SIGS = {
     "sanns_db_info": ([_VP, _VP, _VP], C.c_int),
     "sanns_db_set_position_base": ([_VP, C.c_uint64], C.c_int),
     "sanns_db_export": ([_VP, C.c_uint64, C.c_uint64, _VP, _VP, _VP], C.c_int),
+    "sanns_db_import": ([_VP, C.c_uint64, _VP, _VP, C.POINTER(_VP), _VP], C.c_int),
     "sanns_encrypt_query": ([_VP, _VP, _VP, C.c_uint32, C.c_uint64, _VP, _VP, _VP], C.c_int),
     "sanns_expand_query": ([_VP, _VP, C.c_uint32, C.c_uint64, _VP, _VP, _VP], C.c_int),
     "sanns_distances": ([_VP, _VP, _VP, C.c_uint32, C.c_uint64, _VP, _VP, _VP, _VP], C.c_int),
@@ -236,6 +237,18 @@ def sanns_db_export(db: Database, k0: int = 0, k1: int | None = None, stream=Non
     norms = torch.empty((k1 - k0) * ctx.N, dtype=torch.uint32, device="cuda")
     _check(load().sanns_db_export(db.handle, k0, k1, _ptr(pt), _ptr(norms), _stream(stream)))
     return pt, norms
+
+
+def sanns_db_import(ctx: Context, n: int, pt: torch.Tensor, norms: torch.Tensor,
+                    stream=None) -> Database:
+    """A database from exported plaintexts [K][L][d][N] (canonical residues,
+    NTT form) and norms [K N] (CUDA tensors), K = ceil(n / N)."""
+    K = (n + ctx.N - 1) // ctx.N
+    assert pt.dtype == torch.uint64 and tuple(pt.shape) == (K, ctx.L, ctx.d, ctx.N)
+    assert norms.dtype == torch.uint32 and norms.numel() == K * ctx.N
+    h = _VP()
+    _check(load().sanns_db_import(ctx.handle, n, _ptr(pt), _ptr(norms), C.byref(h), _stream(stream)))
+    return Database(h, ctx, n, K)
 
 
 def sanns_encrypt_query(ctx: Context, sk: SecretKey, q: torch.Tensor, seed: int,
@@ -529,7 +542,7 @@ def sanns_set_circuit_privacy(ctx: Context, pk: torch.Tensor | None, flood_bits:
     _check(load().sanns_set_circuit_privacy(ctx.handle, _ptr(pk), flood_bits, _stream(stream)))
 
 
-BATCHED_CONFIGS = [(tile, pf) for tile in (0, 1) for pf in (0, 1)]  # index = 2 tile + prefetch
+BATCHED_CONFIGS = [(tile, pf) for tile in range(8) for pf in (0, 1)]  # index = 2 tile + prefetch
 
 
 def sanns_autotune_batched(ctx: Context, db: Database, ct_in: torch.Tensor, ct_out: torch.Tensor,
@@ -589,8 +602,8 @@ def sanns_measure_mma_rates(ctx: Context, stream=None) -> dict:
 
 
 def sanns_batched_tune(ctx: Context, tma_ns: int = 0, mma_ns: int = 0, producer_ns: int = 32,
-                       epilogue_ns: int = 128, prefetch_units: int = 1, scratch_mib: int = 4096,
-                       tile: int = 0):
+                       epilogue_ns: int = 128, prefetch_units: int = 0, scratch_mib: int = 4096,
+                       tile: int = 7):
     _check(load().sanns_batched_tune(ctx.handle, tma_ns, mma_ns, producer_ns, epilogue_ns,
                                      prefetch_units, scratch_mib, tile))
 

@@ -237,3 +237,32 @@ def test_multi_query_mac_matches_oracle(cfg, n, B):
         acc = np_(S.sanns_distances_mac(ctx, db, ct_in))
         for b in range(B):
             assert np.array_equal(acc[b], want[b]), (S.sanns_mac_variants()[v], b)
+
+
+def test_db_import_of_the_oracle_encoding_equals_encode_db():
+    """A database imported from the oracle's plaintexts and norms computes
+    the same responses as the one the library encodes itself; a residue not
+    below its prime is rejected and nothing is created."""
+    cfg = (256, 2, 40, 0, 5)
+    N, L, bits, rule, d = cfg
+    n = 3 * N - 11
+    ctx = S.sanns_ctx_create(*cfg)
+    O = oracle(*cfg)
+    coords = inputs.uniform_coords(n, d, 71)
+    perm = inputs.permutation(n, 72)
+    pt, norms = O.encode_db(coords, perm)
+    db_imp = S.sanns_db_import(ctx, n, cu(pt), cu(norms))
+    db_enc = S.sanns_encode_db(ctx, cu(coords), cu(perm))
+    sk = S.sanns_keygen(ctx, 73)
+    qids = cu(np.array([5], dtype=np.uint64))
+    ct = S.sanns_encrypt_query(ctx, sk, cu(inputs.uniform_coords(1, d, 74)), 75, qids)
+    a_out, a_srv = S.sanns_distances(ctx, db_imp, ct, 76, qids)
+    b_out, b_srv = S.sanns_distances(ctx, db_enc, ct, 76, qids)
+    assert torch.equal(a_out, b_out) and torch.equal(a_srv, b_srv)
+    ept, enorms = S.sanns_db_export(db_imp)
+    assert np.array_equal(np_(ept), pt) and np.array_equal(np_(enorms), norms)
+    bad = pt.copy()
+    bad[1, 1, 2, 7] = O.q[1]
+    with pytest.raises(S.SannsError) as e:
+        S.sanns_db_import(ctx, n, cu(bad), cu(norms))
+    assert e.value.code == -1
