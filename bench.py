@@ -327,9 +327,10 @@ def run_gpu(args) -> None:
                      and bool(torch.equal(brute[ep[0]].long(), ed[0].long()))
                      and bool(torch.equal(brute[ap[0]].long(), ad[0].long())))
         hits.append(len(set(ep[0].tolist()) & set(ap[0].tolist())))
-        dk = int(ed[0].max())
+        ev = ed[0].long()
+        dk = int(ev.max())
         av = ad[0].long()
-        hits_ties.append(int((av < dk).sum()) + min(int((av == dk).sum()), int((ed[0].long() == dk).sum())))
+        hits_ties.append(int((av < dk).sum()) + min(int((av == dk).sum()), int((ev == dk).sum())))
         del out1, srv1, cli1, brute
     selection = {
         "k": k_sel, "bins": l_sel, "queries": W["n_queries"],
@@ -575,6 +576,142 @@ def run_gpu(args) -> None:
     if dist:
         dist.barrier()
         dist.destroy_process_group()
+
+
+def run_gpu_sharded(args) -> None:
+    """The linear-scan workload split across the ranks by block ranges
+    (strong scaling: the total work is fixed).  Each rank encodes only its
+    shard of the permuted point list (position base k0 N); per step rank 0's
+    query ciphertext is broadcast over NCCL, every rank runs the distance step
+    on its shard, and the response blocks and server shares are gathered back
+    to rank 0, where they equal the single-GPU result bit for bit (checked on
+    one step).  `e2e` adds rank 0's upload of the query from pinned host
+    memory and its download of the gathered result."""
+    import socket
+
+    import torch
+    import torch.distributed as dist
+
+    from paper_1904_02033_b300 import inputs
+    from paper_1904_02033_b300 import sanns as S
+    from paper_1904_02033_b300.shard import ShardDatabase, distances_sharded, shard_blocks
+
+    rank, world, local = _env_rank()
+    torch.cuda.set_device(local)
+    if world == 1 and "MASTER_PORT" not in os.environ:
+        sk_ = socket.socket()
+        sk_.bind(("127.0.0.1", 0))
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        os.environ["MASTER_PORT"] = str(sk_.getsockname()[1])
+        sk_.close()
+        os.environ.setdefault("RANK", "0")
+        os.environ.setdefault("WORLD_SIZE", "1")
+    dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    W = WORKLOAD
+    n, d, N, L = W["n"], W["d"], W["N"], W["L"]
+    ctx = S.sanns_ctx_create(N, L, W["prime_bits"], W["t_rule"], d)
+    coords = torch.from_numpy(inputs.mixture_coords(n, d, W["n_comp"], W["sigma"], W["seed"] + 1,
+                                                    means_seed=W["seed"])).cuda()
+    perm = torch.from_numpy(inputs.permutation(n, W["seed"] + 2)).cuda()
+    K = -(-n // N)
+    k0, k1 = shard_blocks(K, world, rank)
+    shard = ShardDatabase(ctx, coords, perm, n, k0, k1)
+    nq = W["n_queries"]
+    qids = torch.arange(nq, dtype=torch.int64).to(torch.uint64).cuda()
+    sk = S.sanns_keygen(ctx, W["seed"] + 3)
+    queries = torch.from_numpy(inputs.mixture_coords(nq, d, W["n_comp"], W["sigma"], W["seed"] + 1001,
+                                                     means_seed=W["seed"])).cuda()
+    ct_all = S.sanns_encrypt_query(ctx, sk, queries, W["seed"] + 4, qids)   # used on rank 0 only
+    buf = torch.empty((1, d, 2, L, N), dtype=torch.uint64, device="cuda")
+    mask_seed = W["seed"] + 5
+    state = {"qi": 0}
+
+    def compute(ct_in, a, b):
+        qi = state["qi"]
+        return shard.distances(ct_in, mask_seed, qids[qi:qi + 1])
+
+    def step(s):
+        state["qi"] = s % nq
+        if rank == 0:
+            buf.copy_(ct_all[s % nq:s % nq + 1])
+        return distances_sharded(compute, buf, n, N, L)
+
+    # one step checked against the single-GPU run on rank 0
+    res = step(0)
+    exact = None
+    if rank == 0:
+        full = S.sanns_encode_db(ctx, coords, perm)
+        o, sv = S.sanns_distances(ctx, full, ct_all[0:1], mask_seed, qids[0:1])
+        exact = bool(torch.equal(res[0], o) and torch.equal(res[1], sv))
+        del full, o, sv
+    del res
+    torch.cuda.empty_cache()
+    for s in range(args.warmup):
+        step(s)
+    torch.cuda.synchronize()
+    dist.barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.4)
+    stream = torch.cuda.current_stream()
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    t0.record(stream)
+    for s in range(args.steps):
+        step(args.warmup + s)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    ck = clocks.stop()
+    ms = t0.elapsed_time(t1)
+    tt = torch.tensor([ms], device="cuda")
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    ms = float(tt.item())
+    # end to end: rank 0 uploads the query from pinned memory and downloads
+    # the gathered result every step
+    ct_host = ct_all[:4].cpu().pin_memory() if rank == 0 else None
+    out_host = torch.empty((1, K, 2, L, N), dtype=torch.uint64).pin_memory() if rank == 0 else None
+    srv_host = torch.empty((1, n), dtype=torch.uint32).pin_memory() if rank == 0 else None
+    e2e_steps = max(10, min(args.steps, 100))
+    dist.barrier()
+    torch.cuda.synchronize()
+    tw = time.perf_counter()
+    for s in range(e2e_steps):
+        state["qi"] = s % nq
+        if rank == 0:
+            buf.copy_(ct_host[s % 4:s % 4 + 1], non_blocking=True)
+        r = distances_sharded(compute, buf, n, N, L)
+        if rank == 0:
+            out_host.copy_(r[0], non_blocking=True)
+            srv_host.copy_(r[1], non_blocking=True)
+    torch.cuda.synchronize()
+    e2e_ms = (time.perf_counter() - tw) * 1e3 / e2e_steps
+    tt = torch.tensor([e2e_ms], device="cuda")
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    e2e_ms = float(tt.item())
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": n * args.steps / (ms * 1e-3), "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+            "higher_is_better": True, "scaling": "strong", "vs_baseline": None, "dtype": "u64",
+            "data": "synthetic",
+            "config": {"workload": f"linear scan, 1 query per step, split over {world} GPU(s) by "
+                                   f"block ranges: n={n:,} d=128 uint8 64-component Gaussian "
+                                   "mixture (sigma 20); BFV N=8192, three 60-bit primes",
+                       "n": n, "d": d, "N": N, "L": L, "K": K, "parallelism": f"blocks{world}",
+                       "collectives": "NCCL broadcast of the query ciphertext from rank 0, gather "
+                                      "of response blocks and server shares to rank 0",
+                       "l2": "inputs larger than L2: each shard's encoded database is streamed "
+                             "from HBM every step"},
+            "gathered_result_equals_single_gpu": exact,
+            "e2e": {"value": n / (e2e_ms * 1e-3), "unit": UNIT, "ms_per_step": e2e_ms,
+                    "h2d_bytes_per_step": d * 2 * L * N * 8,
+                    "d2h_bytes_per_step": K * 2 * L * N * 8 + n * 4},
+            "gpu_launches": 3 * args.steps,
+            "clocks": ck,
+        }
+        print(json.dumps(line), flush=True)
+    dist.barrier()
+    dist.destroy_process_group()
 
 
 BATCHED = dict(n=10_000_000, d=96, N=8192, L=3, prime_bits=60, t_rule=0, n_comp=256, sigma=12.0,
@@ -1105,6 +1242,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="sanns", choices=["sanns", "reference"])
     ap.add_argument("--quick-cpu", action="store_true", help="smaller CPU baseline sample")
+    ap.add_argument("--shard", action="store_true",
+                    help="split the linear-scan database across the ranks by block ranges "
+                         "(broadcast + gather) instead of running replicas")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched section")
     ap.add_argument("--no-extra", action="store_true", help="skip the clustering and serving sections")
     ap.add_argument("--only", choices=["cluster", "serving", "alg4"], default=None,
@@ -1149,6 +1289,8 @@ def main():
               flush=True)
     elif args.impl == "reference":
         run_reference(args)
+    elif args.shard:
+        run_gpu_sharded(args)
     else:
         run_gpu(args)
 
