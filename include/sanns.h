@@ -335,6 +335,17 @@ int sanns_selftest_wait_timeout(sanns_ctx *ctx, uint32_t limit_ms, void *stream)
  * bounded completion wait gave up (nothing is written then).
  */
 int sanns_measure_mma_rates(sanns_ctx *ctx, double *rates_host, void *stream);
+/*
+ * Device memory a distance call allocates for itself, beyond the caller's
+ * buffers (no counterpart in the paper; for admission control by device
+ * memory): *bytes = the stream-ordered scratch of one sanns_distances call
+ * (batched = 0: none, the per-query path writes the caller's buffers only)
+ * or one sanns_distances_batched call with B queries under the context's
+ * current tuning (batched != 0: the query multiples of one slot range,
+ * bounded by the scratch cap of sanns_batched_tune).  It is freed on the
+ * call's stream when the call's work is done.
+ */
+int sanns_distances_scratch_bytes(const sanns_ctx *ctx, uint32_t B, int batched, uint64_t *bytes);
 /* Tuning of the batched kernel: back-off sleep (ns, <= 100000) of the TMA
  * thread, the MMA thread, the digit producers and the epilogue when their
  * barrier is not ready yet; how many of its own work units ahead each CTA

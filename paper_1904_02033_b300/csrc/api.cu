@@ -864,6 +864,15 @@ int sanns_distances_batched(sanns_ctx* ctx, const sanns_db* db, const uint64_t* 
   return sanns_distances_finish(ctx, db, B, mask_seed, qids, ct_out, srv_share, stream);
 }
 
+int sanns_distances_scratch_bytes(const sanns_ctx* ctx, uint32_t B, int batched, uint64_t* bytes) {
+  if (!ctx || !bytes) return fail(SANNS_EINVAL, "ctx or bytes is NULL");
+  *bytes = 0;
+  if (B == 0 || !batched) return SANNS_OK;   // the per-query path allocates nothing
+  if (B > 4096) return fail(SANNS_EINVAL, "B must be <= 4096");
+  *bytes = batched_scratch_bytes(ctx->P, B, ctx->params.d, ctx->batched_tune);
+  return SANNS_OK;
+}
+
 int sanns_batched_tune(sanns_ctx* ctx, uint32_t tma_ns, uint32_t mma_ns, uint32_t producer_ns,
                        uint32_t epilogue_ns, uint32_t prefetch_units, uint32_t scratch_mib,
                        uint32_t tile) {

@@ -1438,6 +1438,30 @@ cudaError_t get_encode(PFN_cuTensorMapEncodeTiled_v12000* out) {
 
 }  // namespace
 
+// Scratch per slot of the query multiples and the slots per launch range:
+// byte-interleaved multiples (8 bytes per digit row and dimension) for tiles
+// 0, 1, fp16 digit rows (16 bytes) for the TMA-fed tiles 2..7; the range is
+// capped by tune[5] MiB, a multiple of 2 (slot pairs) or 4 (slot quads,
+// tiles 6, 7), at least that and at most N.
+void batched_slot_range(const PrimeSet& P, uint32_t B, uint32_t d, const uint32_t tune[7],
+                        uint64_t* per_slot, uint64_t* slots) {
+  const uint32_t dpad = (d + 7) / 8 * 8;
+  const bool tma_b = tune[6] >= 2, quads = tune[6] >= 6;
+  const uint64_t ps = (uint64_t)P.L * 2 * B * dpad * 8 * (tma_b ? 16 : 8);
+  uint64_t S = ((uint64_t)tune[5] << 20) / ps;
+  S &= quads ? ~3ull : ~1ull;
+  if (S < (quads ? 4u : 2u)) S = quads ? 4 : 2;
+  if (S > P.N) S = P.N;
+  *per_slot = ps;
+  *slots = S;
+}
+
+size_t batched_scratch_bytes(const PrimeSet& P, uint32_t B, uint32_t d, const uint32_t tune[7]) {
+  uint64_t ps = 0, S = 0;
+  batched_slot_range(P, B, d, tune, &ps, &S);
+  return (size_t)(ps * S);
+}
+
 size_t batched_limb_bytes(uint32_t L, uint32_t N, uint64_t K, uint32_t d) {
   const uint32_t dpad = (d + 7) / 8 * 8;
   return (size_t)L * N * K * 8ull * dpad * 2;
@@ -1536,13 +1560,9 @@ cudaError_t launch_batched_mac(const PrimeSet& P, const void* map, const uint16_
     A.lo_bias[j] = ((1ull << 49) + P.q[j] - 1) / P.q[j] * P.q[j];
   }
   // slot ranges bound the scratch of the query multiples (tune[5] MiB, at
-  // least one slot): byte-interleaved multiples (8 bytes per digit row and
-  // dimension) or fp16 digit rows (16 bytes)
-  const uint64_t per_slot = (uint64_t)P.L * 2 * B * A.dpad * 8 * (tma_b ? 16 : 8);
-  uint64_t S = ((uint64_t)tune[5] << 20) / per_slot;
-  S &= quads ? ~3ull : ~1ull;   // the single-SM tiles take slots in pairs or quads
-  if (S < (quads ? 4u : 2u)) S = quads ? 4 : 2;
-  if (S > P.N) S = P.N;
+  // least one slot's worth)
+  uint64_t per_slot = 0, S = 0;
+  batched_slot_range(P, B, d, tune, &per_slot, &S);
   const size_t smem = use_pair ? (size_t)pair::kSmem : quads ? (size_t)quad::kSmem : (size_t)kSmem1;
   // kernel attributes and the number of co-resident CTA pairs (clusters of 2
   // need two SMs of one GPC) are set up once per device, outside any capture

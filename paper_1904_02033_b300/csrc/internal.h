@@ -166,6 +166,9 @@ cudaError_t launch_join30(const uint64_t* src, uint64_t* dst, uint64_t count, cu
 cudaError_t launch_import_pt(const PrimeSet& P, uint64_t* pt, uint64_t count, uint32_t d, int* bad,
                              cudaStream_t st);
 size_t batched_limb_bytes(uint32_t L, uint32_t N, uint64_t K, uint32_t d);
+void batched_slot_range(const PrimeSet& P, uint32_t B, uint32_t d, const uint32_t tune[7],
+                        uint64_t* per_slot, uint64_t* slots);
+size_t batched_scratch_bytes(const PrimeSet& P, uint32_t B, uint32_t d, const uint32_t tune[7]);
 cudaError_t launch_wait_selftest(int* err, uint32_t limit_ms, int device, cudaStream_t st);
 cudaError_t measure_mma_rates(int sms, int* d_err, double out[3], cudaStream_t st);
 cudaError_t launch_prepare_limbs(const PrimeSet& P, const uint64_t* pt, uint64_t K, uint32_t d,

@@ -83,6 +83,7 @@ _SIGS = {
     "sanns_distances_batched_mac": ([_VP, _VP, _VP, C.c_uint32, _VP, _VP], C.c_int),
     "sanns_device_status": ([_VP, _VP], C.c_int),
     "sanns_measure_mma_rates": ([_VP, _VP, _VP], C.c_int),
+    "sanns_distances_scratch_bytes": ([_VP, C.c_uint32, C.c_int, C.POINTER(C.c_uint64)], C.c_int),
     "sanns_batched_tune": ([_VP, C.c_uint32, C.c_uint32, C.c_uint32, C.c_uint32, C.c_uint32,
                             C.c_uint32, C.c_uint32], C.c_int),
     "sanns_decrypt_shares": ([_VP, _VP, _VP, C.c_uint32, C.c_uint64, _VP, _VP, _VP], C.c_int),
@@ -591,6 +592,13 @@ def sanns_distances_batched_mac(ctx: Context, db: Database, ct_in: torch.Tensor,
 
 def sanns_device_status(ctx: Context, stream=None):
     _check(load().sanns_device_status(ctx.handle, _stream(stream)))
+
+
+def sanns_distances_scratch_bytes(ctx: Context, B: int, batched: bool) -> int:
+    """Stream-ordered scratch one distance call with B queries allocates."""
+    v = C.c_uint64()
+    _check(load().sanns_distances_scratch_bytes(ctx.handle, B, 1 if batched else 0, C.byref(v)))
+    return v.value
 
 
 def sanns_measure_mma_rates(ctx: Context, stream=None) -> dict:

@@ -64,12 +64,16 @@ class Scheduler:
     """Admission by free execution slots and a device-memory budget."""
 
     def __init__(self, executor: Executor, max_batch: int = 128, slots: int = 3,
-                 mem_budget: int = 1 << 40, clock: Callable[[], float] = time.perf_counter):
+                 mem_budget: int = 1 << 40, clock: Callable[[], float] = time.perf_counter,
+                 batch_window: float = 0.0):
         self.ex = executor
         self.max_batch = max_batch
         self.slots = slots
         self.mem_budget = mem_budget
         self.clock = clock
+        # a database's queue is admitted once it holds max_batch requests or
+        # its oldest request has waited batch_window seconds (0: at once)
+        self.batch_window = batch_window
         self.waiting: dict[str, collections.deque] = collections.defaultdict(collections.deque)
         self.inflight: list[tuple[object, list[Request], int, int]] = []  # handle, reqs, bytes, slot
         self.mem_used = 0
@@ -106,8 +110,12 @@ class Scheduler:
             slot = self._free_slot()
             if slot is None:
                 break
-            # oldest waiting request decides which database goes next
-            cands = [(q[0].arrival, db) for db, q in self.waiting.items() if q]
+            # oldest waiting request decides which database goes next, among
+            # the queues that are full or have waited out the batching window
+            now = self.clock()
+            cands = [(q[0].arrival, db) for db, q in self.waiting.items()
+                     if q and (self.batch_window <= 0 or len(q) >= self.max_batch
+                               or now - q[0].arrival >= self.batch_window)]
             if not cands:
                 break
             _, db = min(cands)
@@ -177,11 +185,21 @@ class GpuExecutor:
         self.mask_seed = mask_seed
         self.streams = [torch.cuda.Stream() for _ in range(slots)]
         self.max_batch = max_batch
+        self.tensor_batches = 0             # batches launched on the tensor-core path
+
+    def uses_tensor_path(self, db: str, n_queries: int) -> bool:
+        return n_queries >= self.batched_min and getattr(self.dbs[db][1], "batched", False)
 
     def bytes_for(self, db: str, n_queries: int) -> int:
+        """Device memory one batch holds while in flight: its responses and
+        server shares, the concatenated query ciphertexts, and the scratch
+        the library allocates for the call (the tensor-core path's query
+        multiples)."""
         ctx, d = self.dbs[db]
         per_q = d.K * 2 * ctx.L * ctx.N * 8 + d.n * 4 + ctx.d * 2 * ctx.L * ctx.N * 8
-        return n_queries * per_q
+        scratch = self.S.sanns_distances_scratch_bytes(ctx, n_queries,
+                                                       self.uses_tensor_path(db, n_queries))
+        return n_queries * per_q + scratch
 
     def launch(self, db: str, reqs: list[Request], slot: int):
         torch, S = self.torch, self.S
@@ -190,7 +208,8 @@ class GpuExecutor:
         with torch.cuda.stream(st):
             ct = torch.cat([r.payload[0] for r in reqs]) if len(reqs) > 1 else reqs[0].payload[0]
             qids = torch.cat([r.payload[1] for r in reqs]) if len(reqs) > 1 else reqs[0].payload[1]
-            if len(reqs) >= self.batched_min and getattr(d, "batched", False):
+            if self.uses_tensor_path(db, len(reqs)):
+                self.tensor_batches += 1
                 out, srv = S.sanns_distances_batched(ctx, d, ct, self.mask_seed, qids, stream=st)
             else:
                 out, srv = S.sanns_distances(ctx, d, ct, self.mask_seed, qids, stream=st)

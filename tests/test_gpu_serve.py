@@ -47,3 +47,42 @@ def test_results_identical_alone_and_in_the_mix():
         torch.cuda.synchronize()
         assert torch.equal(r.result[0].cpu(), solo_out.cpu()), r.rid
         assert torch.equal(r.result[1].cpu(), solo_srv.cpu()), r.rid
+
+
+def test_memory_budget_binds_defers_then_admits_with_identical_results():
+    """A device-memory budget that holds one small batch at a time (library
+    scratch of the tensor-core path included): admissions are deferred while a
+    batch is in flight, every request is served once memory frees up, and
+    each result equals the query computed alone."""
+    ctx = S.sanns_ctx_create(256, 2, 40, 0, 8)
+    db = S.sanns_encode_db(ctx, torch.from_numpy(inputs.uniform_coords(3000, 8, 1)).cuda())
+    S.sanns_db_prepare_batched(ctx, db)
+    db.batched = True
+    sk = S.sanns_keygen(ctx, 2)
+    dbs = {"A": (ctx, db)}
+    ex = GpuExecutor(dbs, slots=3, max_batch=16, batched_min=4, mask_seed=5)
+    # the library reports the tensor path's scratch, and the executor counts it
+    assert S.sanns_distances_scratch_bytes(ctx, 4, True) > 0
+    assert S.sanns_distances_scratch_bytes(ctx, 4, False) == 0
+    assert ex.bytes_for("A", 4) == 4 * ex.bytes_for("A", 1) + S.sanns_distances_scratch_bytes(ctx, 4, True)
+    budget = ex.bytes_for("A", 4) + ex.bytes_for("A", 1) // 2   # one batch of 4 fits, two do not
+    sched = Scheduler(ex, max_batch=16, slots=3, mem_budget=budget)
+    reqs = []
+    for rid in range(40):
+        q = torch.from_numpy(inputs.uniform_coords(1, 8, 200 + rid)).cuda()
+        qid = torch.tensor([rid], dtype=torch.int64).to(torch.uint64).cuda()
+        reqs.append(Request(rid=rid, db="A", arrival=0.0,
+                            payload=(S.sanns_encrypt_query(ctx, sk, q, 9, qid), qid)))
+    torch.cuda.synchronize()
+    stats = run_open_loop(sched, reqs)
+    torch.cuda.synchronize()
+    S.sanns_device_status(ctx)
+    assert len(stats.latencies) == 40 and stats.rejected == 0
+    assert stats.deferred > 0                          # memory, not slots, was the limit
+    assert max(n for _, n, _ in stats.batches) <= 4
+    assert ex.tensor_batches > 0                       # batches of 4 took the tensor-core path
+    for r in reqs:
+        solo_out, solo_srv = S.sanns_distances(ctx, db, r.payload[0], 5, r.payload[1])
+        torch.cuda.synchronize()
+        assert torch.equal(r.result[0].cpu(), solo_out.cpu()), r.rid
+        assert torch.equal(r.result[1].cpu(), solo_srv.cpu()), r.rid

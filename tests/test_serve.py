@@ -161,3 +161,29 @@ def test_scheduler_invariants(n, rate, seed, slots, max_batch, budget, bytes_a, 
         starts = [(by_rid[i].arrival, by_rid[i].start) for _, ids, _ in ex.launched for i in ids
                   if by_rid[i].db == db]
         assert [a for a, _ in starts] == sorted(a for a, _ in starts)
+
+
+def test_batching_window_holds_a_queue_until_full_or_waited_out():
+    # with a window, a database's queue is admitted only once it holds
+    # max_batch requests or its oldest request has waited the window: batches
+    # grow, and no request waits much longer than the window plus service
+    clk = FakeClock()
+    ex = FakeExecutor(clk)
+    window = 2e-3
+    s = Scheduler(ex, max_batch=16, slots=3, clock=clk, batch_window=window)
+    reqs = _arrivals(400, 4000.0, 7)
+    stats = run_open_loop(s, reqs, clock=clk)
+    served = sorted(rid for _, ids, _ in ex.launched for rid in ids)
+    assert served == list(range(400))
+    sizes = [len(ids) for _, ids, _ in ex.launched]
+    assert max(sizes) <= 16 and np.mean(sizes) > 3
+    # every launched batch was full or its oldest member had waited the window
+    by_rid = {r.rid: r for r in reqs}
+    for (db, ids, _), (_, n, t) in zip(ex.launched, stats.batches):
+        oldest = min(by_rid[i].arrival for i in ids)
+        assert n == 16 or t - oldest >= window - 1e-9
+    # without the window the same arrivals are admitted at once, in smaller batches
+    clk2 = FakeClock()
+    ex2 = FakeExecutor(clk2)
+    run_open_loop(Scheduler(ex2, max_batch=16, slots=3, clock=clk2), _arrivals(400, 4000.0, 7), clock=clk2)
+    assert np.mean([len(ids) for _, ids, _ in ex2.launched]) < np.mean(sizes)
