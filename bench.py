@@ -137,6 +137,18 @@ def _mac_traffic(rb: dict, W) -> float | None:
     return (C["dram_bytes"] - ct) * rb["K"] / C["K"] + ct
 
 
+def _ntt_roofline(rates: dict, polys: int, N: int, ms: float) -> dict:
+    """The INTT + mask epilogue against the measured register-resident
+    inverse-butterfly rate (integer pipes): N/2 log2 N butterflies per
+    polynomial."""
+    bf = polys * (N // 2) * (N.bit_length() - 1)
+    achieved = bf / (ms * 1e-3)
+    return {"bound": "alu", "achieved": achieved, "peak": rates["inv_butterflies_per_s"],
+            "unit": "butterflies/s", "frac": achieved / rates["inv_butterflies_per_s"],
+            "peak_source": "library probe: register-resident inverse butterflies on this GPU "
+                           "(sanns_measure_int_rates)"}
+
+
 def _ntt_report(polys: int, N: int, ms: float, what: str) -> dict:
     """The epilogue's transforms (one inverse NTT per block, component and
     prime, with the mask): polynomials per second and the fraction of the HBM
@@ -802,6 +814,7 @@ def run_batched_section(quick: bool = False, n_override: int | None = None,
     flops = _batched_flops(B, K, d, L, N)
     peak = _peaks_tensor()
     rates = S.sanns_measure_mma_rates(ctx)
+    int_rates = S.sanns_measure_int_rates(ctx)
     return {
         "workload": f"batched: n={n:,} d={d} uint8 256-component Gaussian mixture (sigma 12); "
                     f"{B} queries per launch; BFV N=8192, three 60-bit primes",
@@ -809,8 +822,9 @@ def run_batched_section(quick: bool = False, n_override: int | None = None,
         "qp_per_s_plain_per_query": B * n / (t_plain * 1e-3),
         "speedup_vs_plain": t_plain / t_batch,
         "ms_per_batch": t_batch, "ms_batched_mac": t_bmac, "ms_plain_for_B_queries": t_plain,
-        "ntt_epilogue": _ntt_report(B * K * 2 * L, N, t_batch - t_bmac,
-                                    "fused INTT + mask (intt_mask_kernel), the batch's step minus its MAC stage"),
+        "ntt_epilogue": dict(_ntt_report(B * K * 2 * L, N, t_batch - t_bmac,
+                                         "fused INTT + mask (intt_mask_kernel), the batch's step minus its MAC stage"),
+                             roofline=_ntt_roofline(int_rates, B * K * 2 * L, N, t_batch - t_bmac)),
         "ntt_form_responses": {"ms_per_batch": t_batch_ntt, "ms_plain_for_B_queries": t_plain_ntt,
                                "speedup_vs_plain": t_plain_ntt / t_batch_ntt,
                                "qp_per_s_batched": B * n / (t_batch_ntt * 1e-3)},
@@ -892,7 +906,26 @@ def run_cluster_section() -> dict:
     same = bool(torch.equal(ref_out[0], ct_out[: int(k_b[0])])) and bool(
         torch.equal(ref_srv[0], srv[: int(n_b[0])]))
     S.sanns_device_status(ctx)
+    # integer-pipe roofline: per work item d L forward transforms of the
+    # gathered coordinates, 2 d L N modular multiply-adds (c0 and c1) and 2 L
+    # inverse transforms, each transform N/2 log2 N butterflies; the ideal
+    # time charges the forward butterflies and the multiply-adds at the
+    # measured forward-butterfly rate and the inverse ones at the inverse rate
+    rates = S.sanns_measure_int_rates(ctx)
+    bf = N // 2 * (N.bit_length() - 1)
+    fwd = total_blocks * W["d"] * W["L"] * bf
+    macs = total_blocks * 2 * W["d"] * W["L"] * N
+    inv = total_blocks * 2 * W["L"] * bf
+    ideal_ms = ((fwd + macs) / rates["fwd_butterflies_per_s"] + inv / rates["inv_butterflies_per_s"]) * 1e3
     return {
+        "roofline": {"kernel": "gather_kernel (K4: forward NTTs + MAC + INTT per work item)",
+                     "bound": "alu", "achieved": (fwd + macs + inv) / (ms * 1e-3),
+                     "peak": rates["fwd_butterflies_per_s"], "unit": "butterflies/s",
+                     "frac": ideal_ms / ms, "ideal_ms": ideal_ms,
+                     "peak_source": "library probe: register-resident butterflies on this GPU "
+                                    "(sanns_measure_int_rates)",
+                     "work": {"fwd_butterflies": fwd, "mac": macs, "inv_butterflies": inv},
+                     "probe": rates},
         "workload": "clustering: n=1,000,000 d=128 uint8 mixture of 1024 Zipf(1.1)-weighted "
                     f"components (sigma 20); seeded Lloyd k-means to 1024 clusters; {B} queries x "
                     "32 probes; one persistent launch per batch; BFV N=8192, three 60-bit primes",

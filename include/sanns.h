@@ -336,6 +336,15 @@ int sanns_selftest_wait_timeout(sanns_ctx *ctx, uint32_t limit_ms, void *stream)
  */
 int sanns_measure_mma_rates(sanns_ctx *ctx, double *rates_host, void *stream);
 /*
+ * Measured integer-pipe ceiling of the transforms (no counterpart in the
+ * paper; the denominator of the INTT and gather rooflines): radix-2
+ * butterflies per second on every SM, values in registers, the context's
+ * first prime, written to rates_host[0] (inverse, Gentleman-Sande, the fused
+ * INTT's lazy arithmetic) and rates_host[1] (forward, Cooley-Tukey).
+ * Synchronous, a few milliseconds of GPU time.
+ */
+int sanns_measure_int_rates(sanns_ctx *ctx, double *rates_host, void *stream);
+/*
  * Device memory a distance call allocates for itself, beyond the caller's
  * buffers (no counterpart in the paper; for admission control by device
  * memory): *bytes = the stream-ordered scratch of one sanns_distances call

@@ -964,6 +964,17 @@ int sanns_measure_mma_rates(sanns_ctx* ctx, double* rates_host, void* stream) {
   return SANNS_OK;
 }
 
+int sanns_measure_int_rates(sanns_ctx* ctx, double* rates_host, void* stream) {
+  if (!ctx || !rates_host) return fail(SANNS_EINVAL, "ctx or rates_host is NULL");
+  int rc = check_device(ctx);
+  if (rc) return rc;
+  double r[2] = {0, 0};
+  SANNS_CUDA(measure_int_rates(ctx->P, ctx->sms, r, as_stream(stream)));
+  rates_host[0] = r[0];
+  rates_host[1] = r[1];
+  return SANNS_OK;
+}
+
 int sanns_device_status(sanns_ctx* ctx, void* stream) {
   if (!ctx) return fail(SANNS_EINVAL, "ctx is NULL");
   int rc = check_device(ctx);

@@ -171,6 +171,7 @@ void batched_slot_range(const PrimeSet& P, uint32_t B, uint32_t d, const uint32_
 size_t batched_scratch_bytes(const PrimeSet& P, uint32_t B, uint32_t d, const uint32_t tune[7]);
 cudaError_t launch_wait_selftest(int* err, uint32_t limit_ms, int device, cudaStream_t st);
 cudaError_t measure_mma_rates(int sms, int* d_err, double out[3], cudaStream_t st);
+cudaError_t measure_int_rates(const PrimeSet& P, int sms, double out[2], cudaStream_t st);
 cudaError_t launch_prepare_limbs(const PrimeSet& P, const uint64_t* pt, uint64_t K, uint32_t d,
                                  uint16_t* plimb, cudaStream_t st);
 constexpr int kBatchedConfigs = 16;  // (tile shape 0..7, L2 prefetch 0/1) pairs timed by the autotuner

@@ -1,6 +1,8 @@
-// Measured dense tensor-core rates of the current GPU (no counterpart in the
-// paper): the denominators of the batched path's roofline.  The batched MAC
-// contracts exact small integers; the candidate instruction families are
+// Measured peak rates of the current GPU (no counterpart in the paper): the
+// denominators of the rooflines.
+//
+// Tensor cores, for the batched path.  The batched MAC contracts exact small
+// integers; the candidate instruction families are
 //   - tcgen05.mma kind::f16 (fp16 operands, fp32 accumulation in TMEM), the
 //     one the batched kernel uses;
 //   - the legacy warp-level mma.sync with fp16 operands;
@@ -140,6 +142,65 @@ __global__ void __launch_bounds__(128, 1) tc_f16_rate_kernel(uint32_t iters, int
   }
 }
 
+// Integer-pipe probes: the radix-2 butterflies of the transforms (inverse:
+// Gentleman-Sande with values below 4q and the three-product Shoup quotient,
+// as in the fused INTT; forward: Cooley-Tukey with values below 4q and the
+// exact Shoup quotient, as in the forward transforms) on 16 values per thread
+// in registers, four stages per round like one radix-16 pass, twiddles read
+// once from the context's table.  No memory traffic in the loop: the rate is
+// the arithmetic ceiling of one butterfly.
+constexpr uint32_t kIntThreads = 256;
+
+__global__ void __launch_bounds__(kIntThreads) inv_bfly_rate_kernel(PrimeSet P, uint32_t iters, uint64_t* out) {
+  const uint64_t q = P.q[0], q4 = 4 * q;
+  ulonglong2 w[4];
+#pragma unroll
+  for (int s = 0; s < 4; ++s) w[s] = P.itw[1 + ((threadIdx.x + s) & 31)];
+  uint64_t v[16];
+#pragma unroll
+  for (int k = 0; k < 16; ++k) v[k] = (threadIdx.x * 16ull + k + blockIdx.x) % q;
+  for (uint32_t it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int s = 0; s < 4; ++s) {
+      const int hk = 1 << s;
+#pragma unroll
+      for (int k = 0; k < 16; ++k) {
+        if (k & hk) continue;
+        inv_bfly4(v[k], v[k + hk], w[s].x, w[s].y, q, q4);
+      }
+    }
+  }
+  uint64_t acc = 0;
+#pragma unroll
+  for (int k = 0; k < 16; ++k) acc ^= v[k];
+  out[blockIdx.x * blockDim.x + threadIdx.x] = acc;
+}
+
+__global__ void __launch_bounds__(kIntThreads) fwd_bfly_rate_kernel(PrimeSet P, uint32_t iters, uint64_t* out) {
+  const uint64_t q = P.q[0], q2 = 2 * q;
+  ulonglong2 w[4];
+#pragma unroll
+  for (int s = 0; s < 4; ++s) w[s] = P.tw[1 + ((threadIdx.x + s) & 31)];
+  uint64_t v[16];
+#pragma unroll
+  for (int k = 0; k < 16; ++k) v[k] = (threadIdx.x * 16ull + k + blockIdx.x) % q;
+  for (uint32_t it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int s = 0; s < 4; ++s) {
+      const int hk = 8 >> s;
+#pragma unroll
+      for (int k = 0; k < 16; ++k) {
+        if (k & hk) continue;
+        fwd_bfly(v[k], v[k + hk], w[s].x, w[s].y, q, q2);
+      }
+    }
+  }
+  uint64_t acc = 0;
+#pragma unroll
+  for (int k = 0; k < 16; ++k) acc ^= v[k];
+  out[blockIdx.x * blockDim.x + threadIdx.x] = acc;
+}
+
 template <typename F>
 cudaError_t time_launch(cudaStream_t st, F launch, float* ms) {
   cudaEvent_t e0, e1;
@@ -160,6 +221,26 @@ cudaError_t time_launch(cudaStream_t st, F launch, float* ms) {
 }
 
 }  // namespace
+
+cudaError_t measure_int_rates(const PrimeSet& P, int sms, double out[2], cudaStream_t st) {
+  const uint32_t blocks = (uint32_t)sms * 8;   // 2048 threads per SM
+  uint64_t* d_out = nullptr;
+  cudaError_t e = cudaMallocAsync(&d_out, sizeof(uint64_t) * blocks * kIntThreads, st);
+  if (e != cudaSuccess) return e;
+  const uint32_t iters = 256;
+  // 4 stages x 8 butterflies per round and thread
+  const double bflies = (double)blocks * kIntThreads * iters * 32;
+  float ms = 0.f;
+  e = time_launch(st, [&] { inv_bfly_rate_kernel<<<blocks, kIntThreads, 0, st>>>(P, iters, d_out); }, &ms);
+  if (e == cudaSuccess) out[0] = bflies / (ms * 1e-3);
+  if (e == cudaSuccess)
+    e = time_launch(st, [&] { fwd_bfly_rate_kernel<<<blocks, kIntThreads, 0, st>>>(P, iters, d_out); }, &ms);
+  if (e == cudaSuccess) out[1] = bflies / (ms * 1e-3);
+  cudaError_t e2 = cudaFreeAsync(d_out, st);
+  if (e == cudaSuccess) e = e2;
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  return e;
+}
 
 cudaError_t measure_mma_rates(int sms, int* d_err, double out[3], cudaStream_t st) {
   const uint32_t blocks_sync = (uint32_t)sms * 4;

@@ -84,6 +84,7 @@ _SIGS = {
     "sanns_device_status": ([_VP, _VP], C.c_int),
     "sanns_measure_mma_rates": ([_VP, _VP, _VP], C.c_int),
     "sanns_distances_scratch_bytes": ([_VP, C.c_uint32, C.c_int, C.POINTER(C.c_uint64)], C.c_int),
+    "sanns_measure_int_rates": ([_VP, _VP, _VP], C.c_int),
     "sanns_batched_tune": ([_VP, C.c_uint32, C.c_uint32, C.c_uint32, C.c_uint32, C.c_uint32,
                             C.c_uint32, C.c_uint32], C.c_int),
     "sanns_decrypt_shares": ([_VP, _VP, _VP, C.c_uint32, C.c_uint64, _VP, _VP, _VP], C.c_int),
@@ -599,6 +600,14 @@ def sanns_distances_scratch_bytes(ctx: Context, B: int, batched: bool) -> int:
     v = C.c_uint64()
     _check(load().sanns_distances_scratch_bytes(ctx.handle, B, 1 if batched else 0, C.byref(v)))
     return v.value
+
+
+def sanns_measure_int_rates(ctx: Context, stream=None) -> dict:
+    """Register-resident butterflies per second (inverse and forward) on the
+    context's first prime: the integer-pipe ceiling of the transforms."""
+    r = (C.c_double * 2)()
+    _check(load().sanns_measure_int_rates(ctx.handle, r, _stream(stream)))
+    return {"inv_butterflies_per_s": r[0], "fwd_butterflies_per_s": r[1]}
 
 
 def sanns_measure_mma_rates(ctx: Context, stream=None) -> dict:

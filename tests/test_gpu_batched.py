@@ -218,3 +218,13 @@ def test_batched_c3_shape_equals_oracle():
             assert np.array_equal(out_h[b], want[b][0]), (tile, b)
             assert np.array_equal(srv_h[b], want[b][1]), (tile, b)
         assert torch.equal(po, out) and torch.equal(ps, srv), tile
+
+
+def test_measured_butterfly_rates_are_plausible():
+    """The integer-pipe probe: register-resident butterflies per second are
+    positive and below what 148 SMs could issue at one butterfly per lane and
+    clock (an upper bound far above any real 64-bit modular butterfly)."""
+    ctx = S.sanns_ctx_create(8192, 3, 60, 0, 8)
+    r = S.sanns_measure_int_rates(ctx)
+    for k in ("inv_butterflies_per_s", "fwd_butterflies_per_s"):
+        assert 0 < r[k] < 148 * 128 * 2.1e9, (k, r[k])
