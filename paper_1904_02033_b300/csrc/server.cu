@@ -452,6 +452,136 @@ __global__ void __launch_bounds__(256, 3) mask_ntt_kernel(PrimeSet P, uint64_t* 
   for (uint32_t x = threadIdx.x; x < N; x += blockDim.x) g[x] = add_mod(g[x], sa[SP(x)], q);
 }
 
+// NTT-form responses without circuit privacy, fused: c0 = acc0 + NTT(Delta_j
+// v) with v = (||p||^2 + r) mod t per position; c1 is acc1 untouched, so one
+// block per (b, k, j) and c = 0 only.  The mask values are built straight
+// into the first butterfly stage (distance N/2), values stay lazily below 4q
+// between passes, and the last radix-16 pass (16 consecutive slots per
+// thread) adds the canonical transform to acc0 in global memory: two
+// shared-memory passes and two block barriers fewer than building, then
+// transforming, then adding.
+__global__ void __launch_bounds__(256, 3) mask_ntt_fused_kernel(PrimeSet P, uint64_t* __restrict__ ct_out,
+                                      const uint32_t* __restrict__ norms, uint64_t K, uint64_t n,
+                                      uint64_t pos0g, uint64_t mask_seed,
+                                      const uint64_t* __restrict__ qids,
+                                      const uint32_t* __restrict__ srv_share) {
+  extern __shared__ uint64_t sa[];
+  const uint32_t N = P.N, L = P.L, logN = P.logN;
+  const uint64_t idx = blockIdx.x;                  // (b K + k) L + j
+  const uint32_t j = (uint32_t)(idx % L);
+  const uint64_t bk = idx / L;
+  const uint64_t k = bk % K, b = bk / K;
+  const uint64_t q = P.q[j], q2 = 2 * q, t = P.t;
+  const uint64_t qid = qids[b];
+  const uint32_t* sh = srv_share + b * n;
+  const ulonglong2* tw = P.tw + (size_t)j * N;
+  const uint64_t dl = P.delta[j], dls = P.delta_shoup[j];
+  if (threadIdx.x == 0) {
+    // the accumulator row is read only at the end: start pulling it into L2
+    const uintptr_t a0 = reinterpret_cast<uintptr_t>(ct_out + (bk * 2 * L + j) * N);
+    for (uint32_t off = 0; off < N * 8u; off += 32768u) {
+      const uint32_t len = N * 8u - off < 32768u ? N * 8u - off : 32768u;
+      asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a0 + off), "r"(len) : "memory");
+    }
+  }
+  auto value = [&](uint32_t x) -> uint64_t {
+    const uint64_t pos = k * N + x;
+    uint64_t r;
+    if (pos < n) {
+      const uint32_t sv = sh[pos];
+      r = sv == 0 ? 0 : t - sv;
+    } else {
+      r = mask_draw(P, pos0g + pos, mask_seed, qid);
+    }
+    const uint64_t m = mod_t64((uint64_t)norms[pos] + r, t, P.t_barrett);
+    return mul_shoup(m, dl, dls, q);
+  };
+  const uint32_t r2 = logN & 3;  // leading radix-2 stages
+  if (r2) {
+    // stage 0: distance N/2, twiddle psi^brv(1) for every pair
+    const ulonglong2 w = __ldg(tw + 1);
+    for (uint32_t x = threadIdx.x; x < N / 2; x += blockDim.x) {
+      uint64_t X = value(x), Y = value(x + N / 2);
+      fwd_bfly(X, Y, w.x, w.y, q, q2);
+      sa[SP(x)] = X;
+      sa[SP(x + N / 2)] = Y;
+    }
+  } else {
+    for (uint32_t x = threadIdx.x; x < N; x += blockDim.x) sa[SP(x)] = value(x);
+  }
+  __syncthreads();
+  uint32_t lt = logN - 1 - (r2 ? 1 : 0);
+  for (uint32_t st = 1; st < r2; ++st, --lt) {
+    const uint32_t tt = 1u << lt, m = 1u << st;
+    for (uint32_t bf = threadIdx.x; bf < N / 2; bf += blockDim.x) {
+      const uint32_t i = bf >> lt, x = (i << (lt + 1)) + (bf & (tt - 1));
+      uint64_t X = sa[SP(x)], Y = sa[SP(x + tt)];
+      const ulonglong2 w = __ldg(tw + m + i);
+      fwd_bfly(X, Y, w.x, w.y, q, q2);
+      sa[SP(x)] = X;
+      sa[SP(x + tt)] = Y;
+    }
+    __syncthreads();
+  }
+  // radix-16 passes but the last (stages t, t/2, t/4, t/8 with t = 2^lt)
+  for (; lt > 3; lt -= 4) {
+    const uint32_t ls = lt - 3, S = 1u << ls;
+    const uint32_t m0 = 1u << (logN - 1 - lt);
+    for (uint32_t th = threadIdx.x; th < N / 16; th += blockDim.x) {
+      const uint32_t g = th >> ls, bb = th & (S - 1);
+      const uint32_t x0 = (g << (lt + 1)) + bb;
+      uint64_t v[16];
+#pragma unroll
+      for (int kk = 0; kk < 16; ++kk) v[kk] = sa[SP(x0 + (kk << ls))];
+#pragma unroll
+      for (int s = 0; s < 4; ++s) {
+        const int hk = 8 >> s;
+        const uint32_t base = (m0 << s) + (g << s);
+#pragma unroll
+        for (int kk = 0; kk < 16; ++kk) {
+          if (kk & hk) continue;
+          const ulonglong2 w = __ldg(tw + base + (kk >> (4 - s)));
+          fwd_bfly(v[kk], v[kk + hk], w.x, w.y, q, q2);
+        }
+      }
+#pragma unroll
+      for (int kk = 0; kk < 16; ++kk) sa[SP(x0 + (kk << ls))] = v[kk];
+    }
+    __syncthreads();
+  }
+  // last pass, lt = 3: a thread owns the 16 consecutive slots x0 = 16 th ..,
+  // written back canonical; then the add to acc0 with coalesced 16-byte
+  // accesses (consecutive threads, consecutive slot pairs)
+  const uint32_t m0 = 1u << (logN - 4);
+  for (uint32_t th = threadIdx.x; th < N / 16; th += blockDim.x) {
+    const uint32_t x0 = th << 4;
+    uint64_t v[16];
+#pragma unroll
+    for (int kk = 0; kk < 16; ++kk) v[kk] = sa[SP(x0 + kk)];
+#pragma unroll
+    for (int s = 0; s < 4; ++s) {
+      const int hk = 8 >> s;
+      const uint32_t base = (m0 << s) + (th << s);
+#pragma unroll
+      for (int kk = 0; kk < 16; ++kk) {
+        if (kk & hk) continue;
+        const ulonglong2 w = __ldg(tw + base + (kk >> (4 - s)));
+        fwd_bfly(v[kk], v[kk + hk], w.x, w.y, q, q2);
+      }
+    }
+#pragma unroll
+    for (int kk = 0; kk < 16; ++kk) sa[SP(x0 + kk)] = csub(csub(v[kk], q2), q);
+  }
+  __syncthreads();
+  ulonglong2* gv = reinterpret_cast<ulonglong2*>(ct_out + (bk * 2 * L + j) * N);   // component 0
+  for (uint32_t i = threadIdx.x; i < N / 2; i += blockDim.x) {
+    ulonglong2 a = gv[i];
+    a.x = add_mod(a.x, sa[SP(2 * i)], q);
+    a.y = add_mod(a.y, sa[SP(2 * i + 1)], q);
+    gv[i] = a;
+  }
+}
+
 }  // namespace
 
 cudaError_t launch_ntt(const PrimeSet& P, uint64_t* data, uint64_t count, bool inverse,
@@ -583,6 +713,13 @@ cudaError_t launch_mask_ntt(const PrimeSet& P, uint64_t* ct_out, const uint32_t*
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const size_t smem = sizeof(uint64_t) * ntt_smem_words(P.N);
+  if (!privacy) {
+    e = ensure_smem_attr((const void*)mask_ntt_fused_kernel, smem);
+    if (e != cudaSuccess) return e;
+    mask_ntt_fused_kernel<<<(unsigned)polys, ntt_threads(P.N), smem, st>>>(P, ct_out, norms, K, n, pos0,
+                                                                           mask_seed, qids, srv_share);
+    return cudaGetLastError();
+  }
   e = ensure_smem_attr((const void*)mask_ntt_kernel, smem);
   if (e != cudaSuccess) return e;
   mask_ntt_kernel<<<(unsigned)polys, ntt_threads(P.N), smem, st>>>(P, ct_out, norms, K, n, pos0, mask_seed,

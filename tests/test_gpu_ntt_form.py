@@ -22,6 +22,12 @@ def cu(a):
     ((256, 3, 60, 0, 5), 256 * 3 + 1, 2, True, False),
     ((256, 2, 60, 0, 16), 256 * 9 - 1, 3, False, True),
     ((256, 2, 60, 0, 16), 256 * 5 + 7, 3, True, True),
+    # every count of leading radix-2 stages of the fused mask transform
+    # (log2 N mod 4 = 0, 1, 2, 3), ragged last blocks
+    ((4096, 2, 54, 0, 8), 4096 * 2 - 5, 2, False, False),
+    ((64, 2, 50, 0, 3), 64 * 5 - 3, 2, False, False),
+    ((16384, 2, 60, 0, 4), 16384 + 77, 1, False, False),
+    ((2048, 2, 50, 0, 4), 2048 * 3 - 1, 2, False, True),
 ])
 def test_ntt_form_responses(cfg, n, B, privacy, batched):
     O = Oracle(*cfg)
