@@ -241,20 +241,74 @@ def run_gpu(args) -> None:
     variant, variant_ms = S.sanns_autotune_mac(ctx, db, ct_all[0:1], ct_out, reps=3)
     variant_names = S.sanns_mac_variants()
 
-    def step(s):
+    # Steps are pipelined over two streams: query s's MAC (HBM-bound) runs on
+    # stream A while query s-1's INTT + mask (integer-bound) runs on stream B,
+    # with the responses double-buffered; the MAC's persistent grid is capped
+    # at `mac_sms` SMs so that the other SMs take the INTT meanwhile.
+    s_mac, s_fin = torch.cuda.Stream(), torch.cuda.Stream()
+    outs = [ct_out, torch.empty_like(ct_out)]
+    srvs = [srv, torch.empty_like(srv)]
+
+    def run_steps(first, count, starts=None, mac_end=None, ends=None):
+        fin = [None] * count
+        for i in range(count):
+            s = first + i
+            qi, u = s % W["n_queries"], s % 2
+            if i >= 2:
+                s_mac.wait_event(fin[i - 2])
+            if starts is not None:
+                starts[s].record(s_mac)
+            S.sanns_distances_mac(ctx, db, ct_all[qi:qi + 1], outs[u], stream=s_mac)
+            me = mac_end[s] if mac_end is not None else torch.cuda.Event()
+            me.record(s_mac)
+            s_fin.wait_event(me)
+            S.sanns_distances_finish(ctx, db, outs[u], mask_seed, qids[qi:qi + 1], srvs[u],
+                                     stream=s_fin)
+            fin[i] = ends[s] if ends is not None else torch.cuda.Event()
+            fin[i].record(s_fin)
+        s_mac.wait_event(fin[count - 1])
+
+    def time_steps(count):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(s_mac)
+        run_steps(0, count)
+        e1.record(s_mac)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / count
+
+    # the SM cap, tuned on short pipelined runs (0 = all SMs)
+    sms_ms = {}
+    for cap in (0, 144, 140, 136, 132, 128, 124, 120):
+        S.sanns_set_mac_sms(ctx, cap)
+        time_steps(20)
+        sms_ms[cap] = time_steps(100)
+    mac_sms = min(sms_ms, key=sms_ms.get)
+    # the same steps one after another on one stream with every SM, for
+    # reference; its INTT + mask times are the stage's own (the pipelined
+    # loop's overlap with the next MAC)
+    S.sanns_set_mac_sms(ctx, 0)
+    serial_n = min(args.steps, 200)
+    torch.cuda.synchronize()
+    sev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(serial_n)]
+    for s in range(serial_n):
         qi = s % W["n_queries"]
+        sev[s][0].record(stream)
         S.sanns_distances_mac(ctx, db, ct_all[qi:qi + 1], ct_out, stream=stream)
-        mac_end[s].record(stream)
+        sev[s][1].record(stream)
         S.sanns_distances_finish(ctx, db, ct_out, mask_seed, qids[qi:qi + 1], srv, stream=stream)
+        sev[s][2].record(stream)
+    torch.cuda.synchronize()
+    serial_ms = sev[0][0].elapsed_time(sev[-1][2]) / serial_n
+    serial_mac_ms = sum(e[0].elapsed_time(e[1]) for e in sev) / serial_n
+    serial_fin_ms = sum(e[1].elapsed_time(e[2]) for e in sev) / serial_n
+    S.sanns_set_mac_sms(ctx, mac_sms)
 
     total_steps = args.warmup + args.steps
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(total_steps)]
     mac_end = [torch.cuda.Event(enable_timing=True) for _ in range(total_steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(total_steps)]
-    for s in range(args.warmup):
-        starts[s].record(stream)
-        step(s)
-        ends[s].record(stream)
+    run_steps(0, args.warmup, starts, mac_end, ends)
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
@@ -264,15 +318,13 @@ def run_gpu(args) -> None:
     t0 = torch.cuda.Event(enable_timing=True)
     t1 = torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
-    t0.record(stream)
-    for s in range(args.warmup, total_steps):
-        starts[s].record(stream)
-        step(s)
-        ends[s].record(stream)
-    t1.record(stream)
+    t0.record(s_mac)
+    run_steps(args.warmup, args.steps, starts, mac_end, ends)
+    t1.record(s_mac)
     torch.cuda.synchronize()
     ck = clocks.stop()
     ms = t0.elapsed_time(t1)
+    S.sanns_set_mac_sms(ctx, 0)   # the single-stream sections below use every SM
     if dist:
         tt = torch.tensor([ms], device="cuda")
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
@@ -534,6 +586,13 @@ def run_gpu(args) -> None:
                        "parallelism": f"replicas{world}" if world > 1 else "single",
                        "mac_variant": variant_names[variant],
                        "mac_variant_ms": dict(zip(variant_names, [round(x, 4) for x in variant_ms])),
+                       "pipelining": "query s's MAC on stream A overlaps query s-1's INTT + mask "
+                                     "on stream B (responses double-buffered); the MAC's grid "
+                                     f"capped at {mac_sms or 'all'} SMs (tuned)",
+                       "mac_sms_ms_per_step": {str(k): round(v, 4) for k, v in sms_ms.items()},
+                       "serial_ms_per_step": serial_ms,
+                       "serial_mac_ms": serial_mac_ms,
+                       "serial_mac_hbm_frac": rb["total"] / (serial_mac_ms * 1e-3) / 1e9 / peak,
                        "l2": "inputs larger than L2: the 3.1 GB encoded database is streamed "
                              "from HBM every step"},
             "latency_ms": {"p50": lat[len(lat) // 2],
@@ -561,9 +620,10 @@ def run_gpu(args) -> None:
                         "the encryption seed (sanns_expand_query): an option beyond the paper, "
                         "whose client sends both components"},
             "selection": selection,
-            "ntt": _ntt_report(K * 2 * L, N, fin_avg,
-                               "INTT + mask of one query (mask draw, intt_mask_short_kernel), "
-                               "the step minus its MAC stage"),
+            "ntt": dict(_ntt_report(K * 2 * L, N, serial_fin_ms,
+                                    "INTT + mask of one query (mask draw, intt_mask_short_kernel), "
+                                    "on its own in the serial reference loop"),
+                        overlapped_ms=fin_avg),
             "small_config": small,
             "ntt_form_responses": {"ms_per_step": nf_ms, "steps": cp_steps,
                                    "value": world * n / (nf_ms * 1e-3), "unit": UNIT},

@@ -111,6 +111,7 @@ int sanns_ctx_create(const sanns_params* p, sanns_ctx** out) {
     }
   }
   c->mac_variant = 0;
+  c->mac_sms = 0;
   c->batched_tune[0] = 0;
   c->batched_tune[1] = 0;
   c->batched_tune[2] = 32;
@@ -454,7 +455,8 @@ int sanns_distances_mac(sanns_ctx* ctx, const sanns_db* db, const uint64_t* ct_i
   if (B == 0) return SANNS_OK;
   if (!ct_in || !ct_out) return fail(SANNS_EINVAL, "NULL buffer");
   if (!aligned16(ct_in) || !aligned16(ct_out)) return fail(SANNS_EINVAL, "ct buffers must be 16-byte aligned");
-  SANNS_CUDA(launch_mac(ctx->P, ct_in, db->d_pt, B, ctx->params.d, db->K, ct_out, ctx->sms,
+  const int sms = ctx->mac_sms > 0 && ctx->mac_sms < ctx->sms ? ctx->mac_sms : ctx->sms;
+  SANNS_CUDA(launch_mac(ctx->P, ct_in, db->d_pt, B, ctx->params.d, db->K, ct_out, sms,
                         ctx->mac_variant, as_stream(stream)));
   return SANNS_OK;
 }
@@ -612,6 +614,13 @@ int sanns_set_circuit_privacy(sanns_ctx* ctx, const uint64_t* pk, uint32_t flood
 int sanns_mac_variants(void) { return mac_num_variants(); }
 
 const char* sanns_mac_variant_name(int v) { return mac_variant_name(v); }
+
+int sanns_set_mac_sms(sanns_ctx* ctx, int sms) {
+  if (!ctx) return fail(SANNS_EINVAL, "ctx is NULL");
+  if (sms < 0) return fail(SANNS_EINVAL, "sms must be >= 0");
+  ctx->mac_sms = sms;
+  return SANNS_OK;
+}
 
 int sanns_set_mac_variant(sanns_ctx* ctx, int v) {
   if (!ctx) return fail(SANNS_EINVAL, "ctx is NULL");

@@ -14,6 +14,7 @@ struct sanns_ctx {
   int device;
   int sms;
   int mac_variant;          // launch variant of the MAC kernel (autotuned)
+  int mac_sms;              // SMs the MAC kernel's persistent grid uses (0: all)
   int* d_err;               // device error word raised by bounded waits
   uint32_t batched_tune[7]; // batched kernel: back-off ns (TMA, MMA, producers, epilogue), L2 prefetch
                             // units, scratch cap (MiB) of the query multiples, tile (0..3: bit 0 =

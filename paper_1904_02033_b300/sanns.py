@@ -65,6 +65,7 @@ _SIGS = {
     "sanns_mac_variants": ([], C.c_int),
     "sanns_mac_variant_name": ([C.c_int], C.c_char_p),
     "sanns_set_mac_variant": ([_VP, C.c_int], C.c_int),
+    "sanns_set_mac_sms": ([_VP, C.c_int], C.c_int),
     "sanns_autotune_mac": ([_VP, _VP, _VP, C.c_uint32, _VP, C.c_int, _VP, _VP], C.c_int),
     "sanns_autotune_batched": ([_VP, _VP, _VP, C.c_uint32, _VP, C.c_int, _VP, _VP], C.c_int),
     "sanns_public_key": ([_VP, _VP, C.c_uint64, _VP, _VP], C.c_int),
@@ -443,6 +444,12 @@ def sanns_mac_variants() -> list[str]:
 
 def sanns_set_mac_variant(ctx: Context, variant: int):
     _check(load().sanns_set_mac_variant(ctx.handle, variant))
+
+
+def sanns_set_mac_sms(ctx: Context, sms: int):
+    """SMs the MAC kernel uses (0: all); the rest stay free for concurrent
+    work on other streams."""
+    _check(load().sanns_set_mac_sms(ctx.handle, sms))
 
 
 def sanns_autotune_mac(ctx: Context, db: Database, ct_in: torch.Tensor, ct_out: torch.Tensor,
