@@ -325,6 +325,13 @@ def run_gpu(args) -> None:
     ck = clocks.stop()
     ms = t0.elapsed_time(t1)
     S.sanns_set_mac_sms(ctx, 0)   # the single-stream sections below use every SM
+    # the last two pipelined steps against the same queries run alone
+    pipe_exact = True
+    for s in (total_steps - 2, total_steps - 1):
+        qi, u = s % W["n_queries"], s % 2
+        o1, s1 = S.sanns_distances(ctx, db, ct_all[qi:qi + 1], mask_seed, qids[qi:qi + 1])
+        pipe_exact &= bool(torch.equal(o1, outs[u]) and torch.equal(s1, srvs[u]))
+    del o1, s1
     if dist:
         tt = torch.tensor([ms], device="cuda")
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
@@ -590,6 +597,7 @@ def run_gpu(args) -> None:
                                      "on stream B (responses double-buffered); the MAC's grid "
                                      f"capped at {mac_sms or 'all'} SMs (tuned)",
                        "mac_sms_ms_per_step": {str(k): round(v, 4) for k, v in sms_ms.items()},
+                       "pipelined_steps_bit_identical": pipe_exact,
                        "serial_ms_per_step": serial_ms,
                        "serial_mac_ms": serial_mac_ms,
                        "serial_mac_hbm_frac": rb["total"] / (serial_mac_ms * 1e-3) / 1e9 / peak,

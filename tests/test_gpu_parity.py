@@ -266,3 +266,45 @@ def test_db_import_of_the_oracle_encoding_equals_encode_db():
     with pytest.raises(S.SannsError) as e:
         S.sanns_db_import(ctx, n, cu(bad), cu(norms))
     assert e.value.code == -1
+
+
+def test_mac_sm_cap_and_two_stream_pipeline_keep_results():
+    """The MAC's grid capped to fewer SMs, and consecutive queries pipelined
+    over two streams (MAC of one query beside the INTT + mask of the
+    previous, responses double-buffered), give the single-stream results."""
+    cfg = (4096, 2, 54, 0, 16)
+    N, L, bits, rule, d = cfg
+    n = 4096 * 7 - 5
+    ctx = S.sanns_ctx_create(*cfg)
+    db = S.sanns_encode_db(ctx, cu(inputs.uniform_coords(n, d, 81)), cu(inputs.permutation(n, 82)))
+    sk = S.sanns_keygen(ctx, 83)
+    B = 6
+    qids = cu(np.arange(B, dtype=np.uint64))
+    ct = S.sanns_encrypt_query(ctx, sk, cu(inputs.uniform_coords(B, d, 84)), 85, qids)
+    want = [S.sanns_distances(ctx, db, ct[b:b + 1], 86, qids[b:b + 1]) for b in range(B)]
+    with pytest.raises(S.SannsError):
+        S.sanns_set_mac_sms(ctx, -1)
+    for cap in (7, 100):
+        S.sanns_set_mac_sms(ctx, cap)
+        s_mac, s_fin = torch.cuda.Stream(), torch.cuda.Stream()
+        outs = [torch.empty_like(want[0][0]) for _ in range(2)]
+        srvs = [torch.empty_like(want[0][1]) for _ in range(2)]
+        got = []
+        fin = [None] * B
+        for b in range(B):
+            if b >= 2:
+                s_mac.wait_event(fin[b - 2])
+                torch.cuda.current_stream().wait_event(fin[b - 2])
+            S.sanns_distances_mac(ctx, db, ct[b:b + 1], outs[b % 2], stream=s_mac)
+            ev = torch.cuda.Event()
+            ev.record(s_mac)
+            s_fin.wait_event(ev)
+            S.sanns_distances_finish(ctx, db, outs[b % 2], 86, qids[b:b + 1], srvs[b % 2], stream=s_fin)
+            fin[b] = torch.cuda.Event()
+            fin[b].record(s_fin)
+            s_fin.synchronize()
+            got.append((outs[b % 2].clone(), srvs[b % 2].clone()))
+        torch.cuda.synchronize()
+        for b in range(B):
+            assert torch.equal(got[b][0], want[b][0]) and torch.equal(got[b][1], want[b][1]), (cap, b)
+    S.sanns_set_mac_sms(ctx, 0)
