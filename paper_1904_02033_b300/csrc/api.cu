@@ -166,6 +166,9 @@ int sanns_ctx_create(const sanns_params* p, sanns_ctx** out) {
     }
     T.n_inv[0] = ninv;
     T.n_inv_shoup[0] = shoup_of(ninv, t);
+    // psi_t^-brv(1) N^-1: the last inverse stage with N^-1 folded in
+    T.last_inv[0] = (uint64_t)((u128)ti[1] * ninv % t);
+    T.last_inv_shoup[0] = shoup_of(T.last_inv[0], t);
     std::vector<uint64_t> th(4 * (size_t)N);
     for (uint32_t x = 0; x < N; ++x) {
       th[2 * x] = tf[x];

@@ -325,8 +325,15 @@ __device__ __forceinline__ void ntt_forward_smem(uint64_t* a, const PrimeSet& P,
           fwd_bfly(v[k], v[k + hk], w.x, w.y, q, q2);
         }
       }
+      // values stay lazily below 4q between passes; the last pass (lt = 3)
+      // stores them canonical
+      if (lt == 3) {
 #pragma unroll
-      for (int k = 0; k < 16; ++k) a[SP(x0 + (k << ls))] = csub(csub(v[k], q2), q);
+        for (int k = 0; k < 16; ++k) a[SP(x0 + (k << ls))] = csub(csub(v[k], q2), q);
+      } else {
+#pragma unroll
+        for (int k = 0; k < 16; ++k) a[SP(x0 + (k << ls))] = v[k];
+      }
     }
     __syncthreads();
     if (lt < 4) break;
@@ -392,11 +399,24 @@ __device__ __forceinline__ void ntt_inverse_smem(uint64_t* a, const PrimeSet& P,
     inv_pass16(a, tw, N, logN, lt, q, q2);
     __syncthreads();
   }
-  for (; lt < logN; ++lt) {
+  if (lt == logN) {
+    // log2 N a multiple of 4: N^-1 in a pass of its own
+    for (uint32_t x = threadIdx.x; x < N; x += blockDim.x) a[SP(x)] = mul_shoup(a[SP(x)], ni, nis, q);
+    return;
+  }
+  for (; lt + 1 < logN; ++lt) {
     inv_pass2(a, tw, N, logN, lt, q, q2);
     __syncthreads();
   }
-  for (uint32_t x = threadIdx.x; x < N; x += blockDim.x) a[SP(x)] = mul_shoup(a[SP(x)], ni, nis, q);
+  // the last stage (distance N/2, one twiddle psi^-brv(1)) with N^-1 folded
+  // in: the sum side times N^-1, the difference side times psi^-brv(1) N^-1;
+  // both canonical
+  const uint64_t wl = P.last_inv[j], wls = P.last_inv_shoup[j];
+  for (uint32_t x = threadIdx.x; x < N / 2; x += blockDim.x) {
+    const uint64_t X = a[SP(x)], Y = a[SP(x + N / 2)];
+    a[SP(x)] = mul_shoup(csub(X + Y, q2), ni, nis, q);
+    a[SP(x + N / 2)] = mul_shoup(X - Y + q2, wl, wls, q);
+  }
 }
 
 }  // namespace sanns
