@@ -1150,6 +1150,19 @@ def run_serving_section() -> dict:
         sk = S.sanns_keygen(ctx, 400 + i)
         pools[name] = (S.sanns_encrypt_query(ctx, sk, q, 500 + i, qids), qids)
     times = inputs.poisson_arrivals(W["rate"], W["duration"], W["seed"])
+    # warm-up: one call per database on each path at the largest batch, so
+    # the stream-ordered memory pool has grown before the timed runs
+    for name, (ctx, db) in dbs.items():
+        ct, qids = pools[name]
+        reps = -(-W["max_batch"] // ct.shape[0])
+        big = ct.repeat(reps, 1, 1, 1, 1)[:W["max_batch"]].contiguous()
+        bq = torch.arange(W["max_batch"], dtype=torch.int64).to(torch.uint64).cuda()
+        o, sv = S.sanns_distances_batched(ctx, db, big, 5, bq)
+        del o, sv, big
+        o, sv = S.sanns_distances(ctx, db, ct[0:1], 5, qids[0:1])
+        del o, sv
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
 
     def serve_once(window: float) -> dict:
         rnd = np.random.default_rng(W["seed"])
@@ -1161,6 +1174,7 @@ def run_serving_section() -> dict:
             reqs.append(Request(rid=rid, db=name, arrival=float(t),
                                 payload=(ct[k:k + 1], qids[k:k + 1])))
         ex = GpuExecutor(dbs, slots=W["slots"], max_batch=W["max_batch"], batched_min=8)
+        torch.cuda.empty_cache()
         free, _ = torch.cuda.mem_get_info()
         sched = Scheduler(ex, max_batch=W["max_batch"], slots=W["slots"], mem_budget=int(free * 0.5),
                           batch_window=window)
