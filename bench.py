@@ -1383,7 +1383,7 @@ def main():
                     help="run only the batched section on N_POINTS points (profiling)")
     ap.add_argument("--batched-d", type=int, default=None, help="dimension for --only-batched")
     ap.add_argument("--batched-B", type=int, default=None, help="queries per launch for --only-batched")
-    ap.add_argument("--batched-tile", type=int, default=None, choices=list(range(8)),
+    ap.add_argument("--batched-tile", type=int, default=None, choices=list(range(9)),
                     help="fixed tile shape of the batched MAC for --only-batched (no autotuning)")
     ap.add_argument("--batched-scratch-mib", type=int, default=None,
                     help="cap on the batched path's query-multiple scratch (smaller launches)")

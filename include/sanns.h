@@ -381,7 +381,10 @@ int sanns_distances_scratch_bytes(const sanns_ctx *ctx, uint32_t B, int batched,
  * one-SM, TMA-fed tile with four consecutive slots per CTA, whose epilogue
  * holds three slots in registers and writes each output's four slots as one
  * 32-byte store (a whole sector), alone (6) or in clusters of 2 sharing the
- * query tile (7; as 6 when the number of 128-block database tiles is odd).
+ * query tile (7; as 6 when the number of 128-block database tiles is odd);
+ * 8 = the four-slot epilogue on pairs of SMs (256 database blocks x 256
+ * query rows per pair, each CTA loading its 128 blocks and half of the query
+ * tile by TMA).
  * Defaults: tile 7, no L2 prefetch (the fastest on the n = 10^7, d = 96,
  * 64-query workload).
  * Results never depend on these values.  Returns SANNS_EINVAL for
@@ -389,11 +392,11 @@ int sanns_distances_scratch_bytes(const sanns_ctx *ctx, uint32_t B, int batched,
 int sanns_batched_tune(sanns_ctx *ctx, uint32_t tma_ns, uint32_t mma_ns, uint32_t producer_ns,
                        uint32_t epilogue_ns, uint32_t prefetch_units, uint32_t scratch_mib,
                        uint32_t tile);
-/* Autotuner of the batched MAC: times the sixteen configurations cfg = 2 tile +
- * prefetch_units (tile 0..7, L2 prefetch 0 or 1 unit ahead) `reps` times
+/* Autotuner of the batched MAC: times the eighteen configurations cfg = 2 tile +
+ * prefetch_units (tile 0..8, L2 prefetch 0 or 1 unit ahead) `reps` times
  * each on the given inputs (writing ct_out_dev as sanns_distances_batched_mac
  * would), keeps the fastest in the context and returns its index (>= 0) or an
- * error code; ms_out (host, 16 floats, may be NULL) receives the mean time per
+ * error code; ms_out (host, 18 floats, may be NULL) receives the mean time per
  * launch.  Synchronous.  Every configuration computes identical results. */
 int sanns_autotune_batched(sanns_ctx *ctx, const sanns_db *db, const uint64_t *ct_in_dev, uint32_t B,
                            uint64_t *ct_out_dev, int reps, float *ms_out, void *stream);

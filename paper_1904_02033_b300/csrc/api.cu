@@ -893,11 +893,11 @@ int sanns_batched_tune(sanns_ctx* ctx, uint32_t tma_ns, uint32_t mma_ns, uint32_
     return fail(SANNS_EINVAL, "back-off above 100 us");
   if (prefetch_units > 8) return fail(SANNS_EINVAL, "prefetch distance above 8 units");
   if (scratch_mib < 1 || scratch_mib > (1u << 20)) return fail(SANNS_EINVAL, "scratch cap outside 1 MiB .. 1 TiB");
-  if (tile > 7)
+  if (tile > 8)
     return fail(SANNS_EINVAL,
-                "tile must be 0..7 (0..3: bit 0 = 256 blocks on an SM pair, bit 1 = query digits by TMA; "
+                "tile must be 0..8 (0..3: bit 0 = 256 blocks on an SM pair, bit 1 = query digits by TMA; "
                 "4, 5: TMA-fed, clusters of 2 or 4 sharing the query tile; 6, 7: TMA-fed, four slots per "
-                "CTA with 32-byte stores, alone or in clusters of 2)");
+                "CTA with 32-byte stores, alone or in clusters of 2; 8: four slots per SM pair)");
   ctx->batched_tune[0] = tma_ns;
   ctx->batched_tune[1] = mma_ns;
   ctx->batched_tune[2] = producer_ns;

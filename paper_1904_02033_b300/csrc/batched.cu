@@ -1269,6 +1269,246 @@ batched_mac_pair_kernel(const __grid_constant__ CUtensorMap pmap, const __grid_c
   }
 }
 
+// ------------------------------------------------------------------------
+// Tile 8: the four-slot epilogue on CTA pairs.  One tcgen05 MMA of M = 256
+// (128 database blocks in each CTA) by N = 256 query rows (128 held by each
+// CTA) by K = 16; both operands arrive by TMA.  A stage is 32 KB per CTA
+// instead of the single-SM tile's 48 KB for the same MMA work per SM, so six
+// stages fit beside the epilogue's held slot: half again as much work in
+// flight to cover the load latency and the stage hand-off, and a third less
+// traffic from L2 and into shared memory per product.
+// Roles as in batched_mac_quad_kernel; the even CTA's MMA thread issues for
+// both, its stage-full barrier counts both CTAs' bytes, and the MMA
+// completions are multicast to the stage-empty and accumulator-full barriers
+// of both CTAs.  Each CTA's epilogue reads its own 128 TMEM lanes and arrives
+// on the even CTA's accumulator-empty barrier.
+// ------------------------------------------------------------------------
+namespace pq {
+constexpr int kStages = 6;
+constexpr int kBM = 128;                  // database blocks per CTA (M = 256 per pair)
+constexpr int kBN = 256;                  // query rows per pair tile (N)
+constexpr int kBNh = 128;                 // query rows held per CTA
+constexpr int kATile = kBM * kBK * 2;     // 16 KB
+constexpr int kBTile = kBNh * kBK * 2;    // 16 KB
+constexpr int kStageBytes = kATile + kBTile;
+constexpr int kEpiWarp0 = 2;
+constexpr int kEpiWarps = 8;
+constexpr int kThreads = 32 * (kEpiWarp0 + kEpiWarps);  // 320
+constexpr int kHeldBytes = 16 * 32 * kEpiWarps * 8;
+constexpr int kSmem = kStages * kStageBytes + kHeldBytes + 1024;
+static_assert(kSmem <= 227 * 1024, "stages + held slot fit one CTA's shared memory");
+}  // namespace pq
+
+// Unit m of this pair: quad p = pair + (m / 4) (pairs in the grid) over
+// A.units quads, decoded as ((j S/4 + s'/4) KT + kt) QT + qt with kt a
+// 256-block pair tile; slot s' = 4 (s'/4) + m % 4.  Both CTAs decode the same
+// unit; rank r takes blocks 256 kt + 128 r .. + 127.
+__device__ __forceinline__ bool unit_of_pq(uint32_t m, const BatchArgs& A, Decoded& D) {
+  const uint32_t cid = blockIdx.x >> 1, ncl = gridDim.x >> 1;
+  const uint64_t p = cid + (uint64_t)(m >> 2) * ncl;
+  if (p >= A.units) return false;
+  const uint32_t quarter = A.s_count >> 2;
+  uint32_t r = (uint32_t)p;
+  D.qt = r % A.QT;
+  r /= A.QT;
+  D.kt = r % A.KT;
+  r /= A.KT;
+  D.sl = 4 * (r % quarter) + (m & 3);
+  D.s = A.s_begin + D.sl;
+  D.j = r / quarter;
+  return true;
+}
+
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(pq::kThreads, 1)
+batched_mac_pairq_kernel(const __grid_constant__ CUtensorMap pmap, const __grid_constant__ CUtensorMap xmap,
+                         PrimeSet P, BatchArgs A) {
+  constexpr int kStages = pq::kStages;
+  constexpr int kEpiWarp0 = pq::kEpiWarp0;
+  constexpr int kEpiWarps = pq::kEpiWarps;
+  constexpr int kStageBytes = pq::kStageBytes;
+  extern __shared__ __align__(1024) uint8_t dsmem[];
+  __shared__ __align__(8) uint64_t bar_full[kStages], bar_empty[kStages];
+  __shared__ __align__(8) uint64_t bar_tfull[2], bar_tempty[2], bar_done;
+  __shared__ uint32_t tmem_base_slot;
+  __shared__ volatile int abort_flag;
+
+  const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t rank = cluster_rank();
+  uint8_t* base = dsmem + ((1024 - (smem_u32(dsmem) & 1023)) & 1023);
+  const uint32_t sbase = smem_u32(base);
+
+  if (threadIdx.x == 0) {
+    abort_flag = 0;
+    for (int s = 0; s < kStages; ++s) {
+      mbar_init(smem_u32(&bar_full[s]), 1);    // even CTA: its TMA thread, both CTAs' bytes
+      mbar_init(smem_u32(&bar_empty[s]), 1);   // the even CTA's multicast commit
+    }
+    for (int a = 0; a < 2; ++a) {
+      mbar_init(smem_u32(&bar_tfull[a]), 1);
+      mbar_init(smem_u32(&bar_tempty[a]), 2 * kEpiWarps);
+    }
+    mbar_init(smem_u32(&bar_done), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(
+                     smem_u32(&tmem_base_slot)));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;");
+  }
+  tc_fence_before();
+  __syncthreads();
+  cluster_sync_all();  // barriers of both CTAs initialised before any remote arrival
+  tc_fence_after();
+  const uint32_t tmem = tmem_base_slot;
+  const uint32_t N = P.N;
+
+  if (warp == 0) {
+    // ---------------- TMA producer (both CTAs) ----------------
+    uint64_t g = 0;
+    bool ok = true;
+    for (uint32_t m = 0; ok; ++m) {
+      Decoded D;
+      if (!unit_of_pq(m, A, D)) break;
+      for (uint32_t kc = 0; kc < A.chunks; ++kc, ++g) {
+        const uint32_t st = (uint32_t)(g % kStages), ph = (uint32_t)((g / kStages) & 1);
+        bool ready = true;
+        if (lane == 0) ready = mbar_wait_cl(smem_u32(&bar_empty[st]), ph ^ 1, &abort_flag, A.err, A.sleep_tma);
+        if (!__shfl_sync(0xffffffffu, (int)ready, 0)) { ok = false; break; }
+        if (lane == 0) {
+          const uint32_t full = smem_u32(&bar_full[st]);
+          if (rank == 0) mbar_arrive_tx(full, 2 * kStageBytes);
+          const uint32_t full0 = map_rank(full, 0);
+          tma_load_3d_pair(sbase + st * kStageBytes, &pmap, (int)(kc * kBK),
+                           (int)(D.kt * 2 * pq::kBM + rank * pq::kBM), (int)(D.j * N + D.s), full0);
+          tma_load_3d_pair(sbase + st * kStageBytes + pq::kATile, &xmap, (int)(kc * kBK),
+                           (int)(D.qt * pq::kBN + rank * pq::kBNh), (int)(D.j * A.s_count + D.sl), full0);
+        }
+        __syncwarp();
+      }
+    }
+    if (!ok && lane == 0) {
+      // copies in flight complete on the even CTA's barriers: give them a
+      // bounded moment before the CTA may leave
+      const unsigned long long t0 = clock64();
+      while (clock64() - t0 < (1ull << 22)) {
+      }
+    }
+    __syncwarp();
+  } else if (warp == 1) {
+    // ---------------- MMA issuer (even CTA) ----------------
+    if (rank == 0) {
+      uint64_t g = 0;
+      bool ok = true;
+      for (uint32_t m = 0; ok; ++m) {
+        Decoded D;
+        if (!unit_of_pq(m, A, D)) break;
+        const uint32_t slot = m & 1, aph = (m >> 1) & 1;
+        bool ready = true;
+        if (lane == 0) ready = mbar_wait_cl(smem_u32(&bar_tempty[slot]), aph ^ 1, &abort_flag, A.err, A.sleep_mma);
+        if (!__shfl_sync(0xffffffffu, (int)ready, 0)) break;
+        tc_fence_after();
+        const uint32_t dt = tmem + slot * pq::kBN;
+        for (uint32_t kc = 0; kc < A.chunks; ++kc, ++g) {
+          const uint32_t st = (uint32_t)(g % kStages), ph = (uint32_t)((g / kStages) & 1);
+          if (lane == 0) ready = mbar_wait_cl(smem_u32(&bar_full[st]), ph, &abort_flag, A.err, A.sleep_mma);
+          if (!__shfl_sync(0xffffffffu, (int)ready, 0)) { ok = false; break; }
+          tc_fence_after();
+          if (lane == 0) {
+            const uint32_t a_addr = sbase + st * kStageBytes, b_addr = a_addr + pq::kATile;
+            const uint64_t ad = smem_desc(a_addr), bd = smem_desc(b_addr);
+#pragma unroll
+            for (int k = 0; k < kBK / 16; ++k)
+              mma_f16_pair(dt, ad + 2 * k, bd + 2 * k, (kc > 0 || k > 0) ? 1u : 0u);
+            mma_commit_mc(smem_u32(&bar_empty[st]), 0x3);
+          }
+          __syncwarp();
+        }
+        if (!ok) break;
+        if (lane == 0) mma_commit_mc(smem_u32(&bar_tfull[slot]), 0x3);
+        __syncwarp();
+      }
+      // every MMA issued has completed before the pair may tear down
+      if (lane == 0) {
+        mma_commit_mc(smem_u32(&bar_done), 0x1);
+        const unsigned long long t0 = clock64();
+        while (!mbar_try_cluster(smem_u32(&bar_done), 0) && clock64() - t0 < kWaitCycles) {
+        }
+      }
+      __syncwarp();
+    }
+  } else {
+    // ---------------- epilogue (both CTAs) ----------------
+    // Lane = database block of this CTA's 128; each thread owns 16 outputs
+    // (4 column chunks x 4 (b, c) rows) per slot.  Slots 0, 1 of a quad are
+    // held in registers, slot 2 in shared memory, slot 3 writes all four as
+    // one 32-byte store per output.
+    const uint32_t quarter = warp & 3;
+    const uint32_t chalf = (warp - kEpiWarp0) >> 2;
+    const uint32_t L = P.L;
+    const uint32_t et = threadIdx.x - 32 * kEpiWarp0;
+    uint64_t held[2][16];
+    uint64_t* held2 = reinterpret_cast<uint64_t*>(base + kStages * kStageBytes);
+    bool live = true;
+    for (uint32_t m = 0; live && !abort_flag; m += 4) {
+#pragma unroll
+      for (int sub = 0; sub < 4; ++sub) {
+        Decoded D;
+        if (!live || !unit_of_pq(m + sub, A, D)) { live = false; break; }
+        const uint32_t u = m + sub;
+        const uint32_t slot = u & 1, aph = (u >> 1) & 1;
+        bool ready = true;
+        if (lane == 0) ready = mbar_wait_cl(smem_u32(&bar_tfull[slot]), aph, &abort_flag, A.err, A.sleep_epi);
+        if (!__shfl_sync(0xffffffffu, (int)ready, 0)) { live = false; break; }
+        tc_fence_after();
+        const uint32_t k = D.kt * 2 * pq::kBM + rank * pq::kBM + quarter * 32 + lane;
+        const bool k_ok = k < A.K;
+#pragma unroll
+        for (uint32_t ci = 0; ci < 4; ++ci) {
+          const uint32_t cc = chalf * 4 + ci;
+          uint64_t res[4];
+          epilogue_values(tmem + ((quarter * 32) << 16) + slot * pq::kBN + cc * 32, A, P, D, res);
+          if (sub < 2) {
+#pragma unroll
+            for (int o = 0; o < 4; ++o) held[sub][ci * 4 + o] = res[o];
+          } else if (sub == 2) {
+#pragma unroll
+            for (int o = 0; o < 4; ++o) held2[(ci * 4 + o) * (32 * kEpiWarps) + et] = res[o];
+          } else {
+#pragma unroll
+            for (int o = 0; o < 4; ++o) {
+              const uint32_t bc = D.qt * kQG + cc * 4 + o;
+              if (k_ok && bc < 2 * A.B) {
+                const uint32_t b = bc >> 1, c = bc & 1;
+                uint64_t* dst = A.out + ((((uint64_t)b * A.K + k) * 2 + c) * L + D.j) * N + D.s - 3;
+                const uint64_t h2 = held2[(ci * 4 + o) * (32 * kEpiWarps) + et];
+                if (A.out16 == 2) {
+                  st_global_v4_b64(dst, held[0][ci * 4 + o], held[1][ci * 4 + o], h2, res[o]);
+                } else {
+                  dst[0] = held[0][ci * 4 + o];
+                  dst[1] = held[1][ci * 4 + o];
+                  dst[2] = h2;
+                  dst[3] = res[o];
+                }
+              }
+            }
+          }
+        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive_cluster(map_rank(smem_u32(&bar_tempty[slot]), 0));
+      }
+    }
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  cluster_sync_all();  // no CTA leaves while its peer may still reach its memory
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, 512;" ::"r"(tmem));
+  }
+}
+
 // Database digits: pt [K][L][d][N] u64 -> plimb [L][N][K][8 dpad] fp16, column
 // 8 i + b = digit b of pt[k][j][i][s] (zero for i >= d).  One block per
 // (k, j, 32-slot group) transposes through shared memory.
@@ -1363,58 +1603,63 @@ __global__ void __launch_bounds__(256) expand_query_kernel(PrimeSet P, const uin
 // 256^b mod q_j (balanced base-256 digits in [-128, 127]: the bytes of X_b +
 // 0x80..80, minus 128), zero for i >= d; bc = 2 b_query + c.  This is the
 // B operand of the contraction exactly as the MMA reads it (rows (bc, a),
-// contraction (i, b)), so the MAC kernel moves it with plain tile copies.  A
-// block takes (j, bc, 8 dimensions, 32 slots): coalesced ciphertext reads
-// along the slots, a shared-memory transpose, then 128 contiguous bytes per
-// (slot, digit row).
+// contraction (i, b)), so the MAC kernel moves it with plain tile copies.
+// A block takes 4 consecutive slots of one prime, whose rows are 4
+// contiguous 16 B x 8 dpad x 2-byte regions, and writes them whole: a thread
+// takes (bc, i) items (i fastest) and reads the item's 4 slots as one 32-byte
+// sector; a warp then stores 512 contiguous bytes per (slot, digit row).
 __global__ void __launch_bounds__(256) expand_query_f16_kernel(PrimeSet P, const uint64_t* __restrict__ ct,
                                     uint32_t B, uint32_t d, uint32_t dpad, uint32_t s_begin, uint32_t S,
                                     const W256 W, uint4* __restrict__ xh) {
-  __shared__ uint4 tile[32][8][8];  // [slot][digit a][dim in block], 8 fp16 (b = 0..7) each
-  const uint32_t s0 = blockIdx.x * 32, ib = blockIdx.y;
-  const uint32_t j = blockIdx.z / (2 * B), bc = blockIdx.z % (2 * B);
-  const uint32_t b = bc >> 1, c = bc & 1;
+  const uint32_t s0 = blockIdx.x * 4, j = blockIdx.y;
   const uint32_t N = P.N, L = P.L;
   const uint64_t q = P.q[j];
-  {
-    const uint32_t il = threadIdx.x >> 5, sl = threadIdx.x & 31;
-    const uint32_t i = ib * 8 + il;
-    uint64_t v[8];
-    if (i < d && s0 + sl < S) {
-      const uint64_t X = ct[((((uint64_t)b * d + i) * 2 + c) * L + j) * N + s_begin + s0 + sl];
-      v[0] = X;
-#pragma unroll
-      for (int k = 1; k < 8; ++k) v[k] = mul_shoup(X, W.w[j][k], W.ws[j][k], q);
-    } else {
-#pragma unroll
-      for (int k = 0; k < 8; ++k) v[k] = 0;
-    }
-#pragma unroll
-    for (int k = 0; k < 8; ++k) v[k] += 0x8080808080808080ull;  // bytes = digits + 128
-#pragma unroll
-    for (int a = 0; a < 8; ++a) {
-      uint32_t h[4];
-#pragma unroll
-      for (int m = 0; m < 4; ++m) {
-        // fp16 of (byte - 128) for b = 2m, 2m + 1: 0x64vv = 1024 + v exactly,
-        // minus 1152
-        const uint32_t lo = (uint32_t)(v[2 * m] >> (8 * a)) & 255u;
-        const uint32_t hi = (uint32_t)(v[2 * m + 1] >> (8 * a)) & 255u;
-        const uint32_t hv = 0x64006400u | lo | (hi << 16);
-        uint32_t r;
-        asm("sub.rn.f16x2 %0, %1, %2;" : "=r"(r) : "r"(hv), "r"(0x64806480u));
-        h[m] = r;
+  const uint32_t ns = S - s0 < 4 ? S - s0 : 4;        // slots of this block in the range
+  const uint32_t items = 2 * B * dpad;
+  for (uint32_t it = threadIdx.x; it < items; it += blockDim.x) {
+    const uint32_t i = it % dpad, bc = it / dpad;
+    const uint32_t b = bc >> 1, c = bc & 1;
+    uint64_t x[4] = {0, 0, 0, 0};
+    if (i < d) {
+      const uint64_t* src = ct + ((((uint64_t)b * d + i) * 2 + c) * L + j) * N + s_begin + s0;
+      if (ns == 4 && ((reinterpret_cast<uintptr_t>(src) & 15) == 0)) {
+        const ulonglong2 u0 = __ldcs(reinterpret_cast<const ulonglong2*>(src));
+        const ulonglong2 u1 = __ldcs(reinterpret_cast<const ulonglong2*>(src) + 1);
+        x[0] = u0.x;
+        x[1] = u0.y;
+        x[2] = u1.x;
+        x[3] = u1.y;
+      } else {
+        for (uint32_t sl = 0; sl < ns; ++sl) x[sl] = src[sl];
       }
-      tile[sl][a][il] = make_uint4(h[0], h[1], h[2], h[3]);
     }
-  }
-  __syncthreads();
-  // (slot, a) rows of 128 bytes: 8 sixteen-byte words, word il = dims 8 ib + il
-  const uint32_t wpr = dpad;  // sixteen-byte words per digit row (8 dpad fp16)
-  for (uint32_t e = threadIdx.x; e < 32 * 8 * 8; e += blockDim.x) {
-    const uint32_t sl = e >> 6, a = (e >> 3) & 7, il = e & 7;
-    if (s0 + sl >= S) continue;
-    xh[(((uint64_t)j * S + s0 + sl) * 16 * B + 8 * bc + a) * wpr + ib * 8 + il] = tile[sl][a][il];
+#pragma unroll
+    for (uint32_t sl = 0; sl < 4; ++sl) {
+      if (sl >= ns) break;
+      uint64_t v[8];
+      v[0] = x[sl];
+#pragma unroll
+      for (int k = 1; k < 8; ++k) v[k] = mul_shoup(x[sl], W.w[j][k], W.ws[j][k], q);
+#pragma unroll
+      for (int k = 0; k < 8; ++k) v[k] += 0x8080808080808080ull;  // bytes = digits + 128
+      uint4* row = xh + (((uint64_t)j * S + s0 + sl) * 16 * B + 8 * bc) * dpad + i;
+#pragma unroll
+      for (int a = 0; a < 8; ++a) {
+        uint32_t h[4];
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+          // fp16 of (byte - 128) for b = 2m, 2m + 1: 0x64vv = 1024 + v exactly,
+          // minus 1152
+          const uint32_t lo = (uint32_t)(v[2 * m] >> (8 * a)) & 255u;
+          const uint32_t hi = (uint32_t)(v[2 * m + 1] >> (8 * a)) & 255u;
+          const uint32_t hv = 0x64006400u | lo | (hi << 16);
+          uint32_t r;
+          asm("sub.rn.f16x2 %0, %1, %2;" : "=r"(r) : "r"(hv), "r"(0x64806480u));
+          h[m] = r;
+        }
+        __stcs(row + (uint64_t)a * dpad, make_uint4(h[0], h[1], h[2], h[3]));
+      }
+    }
   }
 }
 
@@ -1440,9 +1685,9 @@ cudaError_t get_encode(PFN_cuTensorMapEncodeTiled_v12000* out) {
 
 // Scratch per slot of the query multiples and the slots per launch range:
 // byte-interleaved multiples (8 bytes per digit row and dimension) for tiles
-// 0, 1, fp16 digit rows (16 bytes) for the TMA-fed tiles 2..7; the range is
+// 0, 1, fp16 digit rows (16 bytes) for the TMA-fed tiles 2..8; the range is
 // capped by tune[5] MiB, a multiple of 2 (slot pairs) or 4 (slot quads,
-// tiles 6, 7), at least that and at most N.
+// tiles 6..8), at least that and at most N.
 void batched_slot_range(const PrimeSet& P, uint32_t B, uint32_t d, const uint32_t tune[7],
                         uint64_t* per_slot, uint64_t* slots) {
   const uint32_t dpad = (d + 7) / 8 * 8;
@@ -1531,12 +1776,14 @@ cudaError_t launch_batched_mac(const PrimeSet& P, const void* map, const uint16_
   // share each query tile by multicast.
   // 6, 7: one SM per tile, TMA-fed, four slots per CTA with 32-byte output
   // stores (batched_mac_quad_kernel), alone or in clusters of 2.
+  // 8: the four-slot epilogue on SM pairs (batched_mac_pairq_kernel).
   const uint32_t tile = tune[6];
   const bool use_pair = tile < 4 && (tile & 1) != 0;
+  const bool pairq = tile == 8;
   const bool tma_b = tile >= 2;
   const bool quads = tile >= 6;
   A.QT = (2 * B + kQG - 1) / kQG;
-  A.KT = (uint32_t)(use_pair ? (K + 2 * pair::kBM - 1) / (2 * pair::kBM) : (K + kBM - 1) / kBM);
+  A.KT = (uint32_t)(use_pair || pairq ? (K + 2 * pair::kBM - 1) / (2 * pair::kBM) : (K + kBM - 1) / kBM);
   // tile 7 on an odd number of database tiles runs as tile 6 rather than
   // padding a whole tile of zeros per cluster
   const int CL = tile == 4 ? 2 : tile == 5 ? 4 : (tile == 7 && A.KT % 2 == 0) ? 2 : 1;
@@ -1563,7 +1810,8 @@ cudaError_t launch_batched_mac(const PrimeSet& P, const void* map, const uint16_
   // least one slot's worth)
   uint64_t per_slot = 0, S = 0;
   batched_slot_range(P, B, d, tune, &per_slot, &S);
-  const size_t smem = use_pair ? (size_t)pair::kSmem : quads ? (size_t)quad::kSmem : (size_t)kSmem1;
+  const size_t smem = use_pair ? (size_t)pair::kSmem : pairq ? (size_t)pq::kSmem
+                    : quads ? (size_t)quad::kSmem : (size_t)kSmem1;
   // kernel attributes and the number of co-resident CTA pairs (clusters of 2
   // need two SMs of one GPC) are set up once per device, outside any capture
   int dev = 0;
@@ -1571,6 +1819,7 @@ cudaError_t launch_batched_mac(const PrimeSet& P, const void* map, const uint16_
   if (e != cudaSuccess) return e;
   static std::mutex setup_mu;
   static int pairs_resident_dev[64] = {};
+  static int pairq_resident_dev[64] = {};
   static int clusters_resident_dev[64][3] = {};   // clusters of 2 and of 4 (tiles 4, 5), quad clusters of 2 (7)
   static bool configured_dev[64] = {};
   if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
@@ -1635,12 +1884,19 @@ cudaError_t launch_batched_mac(const PrimeSet& P, const void* map, const uint16_
       cfg.dynamicSmemBytes = pair::kSmem;
       e = cudaOccupancyMaxActiveClusters(&pairs_resident_dev[dev], batched_mac_pair_kernel<false>, &cfg);
       if (e != cudaSuccess) return e;
+      e = cudaFuncSetAttribute(batched_mac_pairq_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)pq::kSmem);
+      if (e != cudaSuccess) return e;
+      cfg.blockDim = dim3(pq::kThreads);
+      cfg.dynamicSmemBytes = pq::kSmem;
+      e = cudaOccupancyMaxActiveClusters(&pairq_resident_dev[dev], batched_mac_pairq_kernel, &cfg);
+      if (e != cudaSuccess) return e;
       configured_dev[dev] = true;
     }
-    pairs_resident = pairs_resident_dev[dev];
+    pairs_resident = pairq ? pairq_resident_dev[dev] : pairs_resident_dev[dev];
     if (CL > 1) clusters_resident = clusters_resident_dev[dev][quads ? 2 : CL == 2 ? 0 : 1];
   }
-  if (use_pair && pairs_resident < 1) return cudaErrorInvalidConfiguration;
+  if ((use_pair || pairq) && pairs_resident < 1) return cudaErrorInvalidConfiguration;
   if (CL > 1 && clusters_resident < 1) return cudaErrorInvalidConfiguration;
   PFN_cuTensorMapEncodeTiled_v12000 enc = nullptr;
   e = get_encode(&enc);
@@ -1664,13 +1920,13 @@ cudaError_t launch_batched_mac(const PrimeSet& P, const void* map, const uint16_
     CUtensorMap xmap;
     CUresult cr = CUDA_SUCCESS;
     if (tma_b) {
-      expand_query_f16_kernel<<<xgrid, 256, 0, st>>>(P, ct, B, d, A.dpad, (uint32_t)s0, cnt, W,
-                                                     reinterpret_cast<uint4*>(scratch));
+      expand_query_f16_kernel<<<dim3((cnt + 3) / 4, P.L), 256, 0, st>>>(P, ct, B, d, A.dpad, (uint32_t)s0, cnt,
+                                                                      W, reinterpret_cast<uint4*>(scratch));
       // fp16 digit rows as a tensor [L S'][16 B][8 dpad]; boxes of 64
       // contraction columns x 256 rows (one SM) or 128 rows (each CTA of a pair)
       const cuuint64_t dims[3] = {8ull * A.dpad, 16ull * B, (cuuint64_t)P.L * cnt};
       const cuuint64_t strides[2] = {16ull * A.dpad, 16ull * B * 16ull * A.dpad};
-      const cuuint32_t box[3] = {(cuuint32_t)kBK, (cuuint32_t)(use_pair ? pair::kBNh : kBN / CL), 1};
+      const cuuint32_t box[3] = {(cuuint32_t)kBK, (cuuint32_t)(use_pair || pairq ? pair::kBNh : kBN / CL), 1};
       const cuuint32_t estr[3] = {1, 1, 1};
       cr = enc(&xmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 3, scratch, dims, strides, box, estr,
                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
@@ -1702,6 +1958,10 @@ cudaError_t launch_batched_mac(const PrimeSet& P, const void* map, const uint16_
         batched_mac_pair_kernel<true><<<(unsigned)(2 * clusters), pair::kThreads, smem, st>>>(m, xmap, P, A);
       else
         batched_mac_pair_kernel<false><<<(unsigned)(2 * clusters), pair::kThreads, smem, st>>>(m, xmap, P, A);
+    } else if (pairq) {
+      uint64_t clusters = (uint64_t)pairs_resident;
+      if (clusters > A.units) clusters = A.units;
+      batched_mac_pairq_kernel<<<(unsigned)(2 * clusters), pq::kThreads, smem, st>>>(m, xmap, P, A);
     } else if (quads) {
       uint64_t clusters = CL > 1 ? (uint64_t)clusters_resident : (uint64_t)(sms > 0 ? sms : 148);
       if (clusters > A.units) clusters = A.units;

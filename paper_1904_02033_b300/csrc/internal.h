@@ -175,7 +175,7 @@ cudaError_t measure_mma_rates(int sms, int* d_err, double out[3], cudaStream_t s
 cudaError_t measure_int_rates(const PrimeSet& P, int sms, double out[2], cudaStream_t st);
 cudaError_t launch_prepare_limbs(const PrimeSet& P, const uint64_t* pt, uint64_t K, uint32_t d,
                                  uint16_t* plimb, cudaStream_t st);
-constexpr int kBatchedConfigs = 16;  // (tile shape 0..7, L2 prefetch 0/1) pairs timed by the autotuner
+constexpr int kBatchedConfigs = 18;  // (tile shape 0..8, L2 prefetch 0/1) pairs timed by the autotuner
 int make_limb_map(const PrimeSet& P, const uint16_t* plimb, uint64_t K, uint32_t d, void* map_out);
 cudaError_t launch_batched_mac(const PrimeSet& P, const void* map, const uint16_t* plimb,
                                const uint64_t* ct, uint32_t B,

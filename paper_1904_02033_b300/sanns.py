@@ -551,7 +551,7 @@ def sanns_set_circuit_privacy(ctx: Context, pk: torch.Tensor | None, flood_bits:
     _check(load().sanns_set_circuit_privacy(ctx.handle, _ptr(pk), flood_bits, _stream(stream)))
 
 
-BATCHED_CONFIGS = [(tile, pf) for tile in range(8) for pf in (0, 1)]  # index = 2 tile + prefetch
+BATCHED_CONFIGS = [(tile, pf) for tile in range(9) for pf in (0, 1)]  # index = 2 tile + prefetch
 
 
 def sanns_autotune_batched(ctx: Context, db: Database, ct_in: torch.Tensor, ct_out: torch.Tensor,

@@ -15,9 +15,9 @@ def cu(a):
     return torch.from_numpy(np.ascontiguousarray(a)).cuda()
 
 
-TILES = [0, 1, 2, 3, 4, 5, 6, 7]
+TILES = [0, 1, 2, 3, 4, 5, 6, 7, 8]
 TILE_IDS = ["tile128", "tile256pair", "tile128tma", "tile256pairtma", "tile128tma_cl2",
-            "tile128tma_cl4", "tile128quad", "tile128quad_cl2"]
+            "tile128tma_cl4", "tile128quad", "tile128quad_cl2", "tile256pairquad"]
 
 
 @pytest.mark.parametrize("tile", TILES, ids=TILE_IDS)

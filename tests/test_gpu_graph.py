@@ -55,7 +55,7 @@ def test_per_query_step_replays_bit_exact(cfg, n, B):
         assert torch.equal(out, ref_out) and torch.equal(srv, ref_srv)
 
 
-@pytest.mark.parametrize("tile", list(range(8)))
+@pytest.mark.parametrize("tile", list(range(9)))
 def test_batched_step_replays_bit_exact(tile):
     cfg = (256, 2, 40, 0, 24)
     ctx, db, ct, qids = _setup(cfg, 256 * 30 + 3, 6, 41)
