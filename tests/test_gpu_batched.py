@@ -63,6 +63,37 @@ def test_batched_equals_plain_and_oracle(cfg, n, B, tile):
         assert np.array_equal((cli.astype(np.int64) + srv0) % O.t, brute)
 
 
+@pytest.mark.parametrize("tile", [2, 6, 7, 8])
+def test_many_slot_ranges_equal_one(tile):
+    """A 3 MiB scratch cap splits N = 256 slots into 22 ranges of 12 (the
+    last of 4), each with its own query expansion and MAC launch; the
+    responses equal the per-query path's, as with one range, and the scratch
+    the library reports is one range's."""
+    cfg = (256, 2, 60, 0, 24)
+    n, B = 256 * 512 - 7, 20          # four 128-block tiles: tile 7 runs in clusters of 2
+    ctx = S.sanns_ctx_create(*cfg)
+    rnd = np.random.default_rng(31)
+    coords = rnd.integers(0, 256, size=(n, cfg[4]), dtype=np.uint8)
+    q = rnd.integers(0, 256, size=(B, cfg[4]), dtype=np.uint8)
+    qids = cu(np.arange(B, dtype=np.uint64))
+    sk = S.sanns_keygen(ctx, 32)
+    db = S.sanns_encode_db(ctx, cu(coords), cu(inputs.permutation(n, 33)))
+    S.sanns_db_prepare_batched(ctx, db)
+    ct_in = S.sanns_encrypt_query(ctx, sk, cu(q), 34, qids)
+    acc_plain = S.sanns_distances_mac(ctx, db, ct_in)
+    S.sanns_batched_tune(ctx, scratch_mib=3, tile=tile)
+    per_slot = cfg[1] * 2 * B * 24 * 8 * 16     # fp16 digit rows of one slot, every prime
+    assert S.sanns_distances_scratch_bytes(ctx, B, True) == 12 * per_slot
+    acc_b = S.sanns_distances_batched_mac(ctx, db, ct_in)
+    S.sanns_device_status(ctx)
+    assert torch.equal(acc_b.cpu(), acc_plain.cpu())
+    S.sanns_batched_tune(ctx, scratch_mib=4096, tile=tile)
+    assert S.sanns_distances_scratch_bytes(ctx, B, True) == 256 * per_slot
+    acc_1 = S.sanns_distances_batched_mac(ctx, db, ct_in)
+    S.sanns_device_status(ctx)
+    assert torch.equal(acc_1.cpu(), acc_plain.cpu())
+
+
 def test_batched_needs_prepare_and_small_d():
     ctx = S.sanns_ctx_create(256, 2, 40, 0, 200)
     db = S.sanns_encode_db(ctx, cu(inputs.uniform_coords(300, 200, 1)))
