@@ -484,30 +484,63 @@ __global__ void __launch_bounds__(256, 3) mask_ntt_fused_kernel(PrimeSet P, uint
       asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a0 + off), "r"(len) : "memory");
     }
   }
-  auto value = [&](uint32_t x) -> uint64_t {
+  // the value at slot x from its raw inputs (norm, share), which the loops
+  // below load for several slots at once so that their latencies overlap
+  auto value = [&](uint32_t x, uint32_t nv, uint32_t sv) -> uint64_t {
     const uint64_t pos = k * N + x;
     uint64_t r;
-    if (pos < n) {
-      const uint32_t sv = sh[pos];
-      r = sv == 0 ? 0 : t - sv;
-    } else {
-      r = mask_draw(P, pos0g + pos, mask_seed, qid);
-    }
-    const uint64_t m = mod_t64((uint64_t)norms[pos] + r, t, P.t_barrett);
+    if (pos < n) r = sv == 0 ? 0 : t - sv;
+    else r = mask_draw(P, pos0g + pos, mask_seed, qid);
+    const uint64_t m = mod_t64((uint64_t)nv + r, t, P.t_barrett);
     return mul_shoup(m, dl, dls, q);
   };
+  const uint32_t* nk = norms + k * N;
+  const uint64_t valid = n > k * N ? n - k * N : 0;      // slots of this block with a share
   const uint32_t r2 = logN & 3;  // leading radix-2 stages
   if (r2) {
-    // stage 0: distance N/2, twiddle psi^brv(1) for every pair
+    // stage 0: distance N/2, twiddle psi^brv(1) for every pair; four pairs
+    // (eight slots) in flight per thread
     const ulonglong2 w = __ldg(tw + 1);
-    for (uint32_t x = threadIdx.x; x < N / 2; x += blockDim.x) {
-      uint64_t X = value(x), Y = value(x + N / 2);
-      fwd_bfly(X, Y, w.x, w.y, q, q2);
-      sa[SP(x)] = X;
-      sa[SP(x + N / 2)] = Y;
+    for (uint32_t x0 = threadIdx.x; x0 < N / 2; x0 += 4 * blockDim.x) {
+      uint32_t nv[8], sv[8];
+#pragma unroll
+      for (int z = 0; z < 4; ++z) {
+        const uint32_t x = x0 + z * blockDim.x;
+        if (x < N / 2) {
+          nv[z] = __ldg(nk + x);
+          nv[z + 4] = __ldg(nk + x + N / 2);
+          sv[z] = x < valid ? __ldg(sh + k * N + x) : 0;
+          sv[z + 4] = x + N / 2 < valid ? __ldg(sh + k * N + x + N / 2) : 0;
+        }
+      }
+#pragma unroll
+      for (int z = 0; z < 4; ++z) {
+        const uint32_t x = x0 + z * blockDim.x;
+        if (x < N / 2) {
+          uint64_t X = value(x, nv[z], sv[z]), Y = value(x + N / 2, nv[z + 4], sv[z + 4]);
+          fwd_bfly(X, Y, w.x, w.y, q, q2);
+          sa[SP(x)] = X;
+          sa[SP(x + N / 2)] = Y;
+        }
+      }
     }
   } else {
-    for (uint32_t x = threadIdx.x; x < N; x += blockDim.x) sa[SP(x)] = value(x);
+    for (uint32_t x0 = threadIdx.x; x0 < N; x0 += 8 * blockDim.x) {
+      uint32_t nv[8], sv[8];
+#pragma unroll
+      for (int z = 0; z < 8; ++z) {
+        const uint32_t x = x0 + z * blockDim.x;
+        if (x < N) {
+          nv[z] = __ldg(nk + x);
+          sv[z] = x < valid ? __ldg(sh + k * N + x) : 0;
+        }
+      }
+#pragma unroll
+      for (int z = 0; z < 8; ++z) {
+        const uint32_t x = x0 + z * blockDim.x;
+        if (x < N) sa[SP(x)] = value(x, nv[z], sv[z]);
+      }
+    }
   }
   __syncthreads();
   uint32_t lt = logN - 1 - (r2 ? 1 : 0);
@@ -574,11 +607,23 @@ __global__ void __launch_bounds__(256, 3) mask_ntt_fused_kernel(PrimeSet P, uint
   }
   __syncthreads();
   ulonglong2* gv = reinterpret_cast<ulonglong2*>(ct_out + (bk * 2 * L + j) * N);   // component 0
-  for (uint32_t i = threadIdx.x; i < N / 2; i += blockDim.x) {
-    ulonglong2 a = gv[i];
-    a.x = add_mod(a.x, sa[SP(2 * i)], q);
-    a.y = add_mod(a.y, sa[SP(2 * i + 1)], q);
-    gv[i] = a;
+  // four 16-byte words of the accumulator row in flight per thread
+  for (uint32_t i0 = threadIdx.x; i0 < N / 2; i0 += 4 * blockDim.x) {
+    ulonglong2 a[4];
+#pragma unroll
+    for (int z = 0; z < 4; ++z) {
+      const uint32_t i = i0 + z * blockDim.x;
+      if (i < N / 2) a[z] = gv[i];
+    }
+#pragma unroll
+    for (int z = 0; z < 4; ++z) {
+      const uint32_t i = i0 + z * blockDim.x;
+      if (i < N / 2) {
+        a[z].x = add_mod(a[z].x, sa[SP(2 * i)], q);
+        a[z].y = add_mod(a[z].y, sa[SP(2 * i + 1)], q);
+        gv[i] = a[z];
+      }
+    }
   }
 }
 
