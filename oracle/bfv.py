@@ -382,6 +382,41 @@ class Oracle:
         qn = int(np.sum(np.asarray(qv, dtype=np.int64) ** 2))
         return ((m + qn) % self.t).astype(np.uint32)
 
+    def mod_switch(self, ct_out: np.ndarray) -> np.ndarray:
+        """Modulus switching of coefficient-form responses from Q = q_0 ...
+        q_{L-1} down to q_0 (the standard BFV rescaling of [FV12]; not a step
+        of Pi_ls, which sends the responses at the full modulus): every
+        coefficient, as the integer c in [0, Q) that its residues represent,
+        becomes round(q_0 c / Q) mod q_0.  [nk][2][L][N] -> [nk][2][N]."""
+        P = self.P
+        Q, q0 = P.Q, P.q[0]
+        coef = [(Q // qj) * pow(Q // qj, -1, qj) % Q for qj in P.q]
+        nk = ct_out.shape[0]
+        out = np.zeros((nk, 2, self.N), dtype=np.uint64)
+        for k in range(nk):
+            for c in range(2):
+                cols = [ct_out[k, c, j].tolist() for j in range(self.L)]
+                row = []
+                for x in range(self.N):
+                    w = sum(int(cols[j][x]) * coef[j] for j in range(self.L)) % Q
+                    row.append(((2 * q0 * w + Q) // (2 * Q)) % q0)   # round half up
+                out[k, c] = row
+        return out
+
+    def prime0(self) -> "Oracle":
+        """The same parameters with the first prime alone: the scheme that
+        decrypts modulus-switched responses (same q_0, N and t)."""
+        O1 = Oracle(self.N, 1, self.P.prime_bits, self.P.t_rule, self.d)
+        assert O1.P.q[0] == self.P.q[0] and O1.t == self.t
+        return O1
+
+    def decrypt_shares_switched(self, ct1: np.ndarray, s: np.ndarray, qv: np.ndarray, n: int,
+                                slots: bool = False):
+        """Pi_ls step 4 on responses switched to q_0 ([nk][2][N]): the client's
+        shares by decryption modulo q_0."""
+        nk = ct1.shape[0]
+        return self.prime0().decrypt_shares(ct1.reshape(nk, 2, 1, self.N), s, qv, n, slots)
+
     def draw128(self, seed: int, purpose: int, obj: int, c: int):
         """The 128-bit draw of coefficient c of ChaCha20 stream (seed, purpose,
         object): the randomness of every protocol step (Sec. 2.3, 5.3)."""

@@ -841,3 +841,63 @@ def test_encryption_c1_is_the_documented_stream():
                 lo, hi = O.draw128(seed, 2, (qid << 16) | (j << 12) | i, x)
                 want.append(((hi << 64) | lo) % qj)
             assert [int(v) for v in ct[i, 1, j]] == want, (i, j)
+
+
+# ------------------------------------------------------- modulus switching
+
+@pytest.mark.parametrize("cfg", [(64, 2, 50, 0, 4), (64, 3, 60, 0, 4), (64, 4, 60, 0, 4)])
+def test_mod_switch_removes_errors_below_half_the_dropped_modulus(cfg):
+    # round(q_0 c / Q) for c = a (Q / q_0) + e: exactly a whenever |e| is below
+    # half of D = Q / q_0 (D is odd, so no ties), including e = 0, both
+    # extreme errors and the wrap of negative c below zero
+    O = Oracle(*cfg)
+    P = O.P
+    Q, q0 = P.Q, P.q[0]
+    D = Q // q0
+    assert D * q0 == Q and D % 2 == 1
+    N, L = cfg[0], cfg[1]
+    rnd = random.Random(L)
+    ct = np.zeros((1, 2, L, N), dtype=np.uint64)
+    want = np.zeros((1, 2, N), dtype=np.uint64)
+    half = (D - 1) // 2
+    for c in range(2):
+        for x in range(N):
+            a = rnd.randrange(q0) if x > 2 else [0, q0 - 1, 1][x]
+            e = [0, half, -half, 1, -1][x % 5] if x < 10 else rnd.randrange(-half, half + 1)
+            v = (a * D + e) % Q
+            for j, qj in enumerate(P.q):
+                ct[0, c, j, x] = v % qj
+            want[0, c, x] = a
+    assert np.array_equal(O.mod_switch(ct), want)
+
+
+@pytest.mark.parametrize("cfg,flood,slots", [
+    ((64, 2, 40, 0, 4), False, False),
+    ((256, 3, 60, 0, 8), False, False),
+    ((256, 3, 60, 0, 8), True, False),      # the largest flooding exponent
+    ((64, 4, 60, 0, 3), False, False),
+    ((256, 2, 40, 0, 5), False, True),      # slot encoding
+])
+def test_switched_responses_reconstruct_brute_force_distances(cfg, flood, slots):
+    # the responses switched down to q_0 and decrypted there: the shares still
+    # add up to ||q - p||^2 for every point, with extreme coordinates (the
+    # largest distances); the switched response is 1 / L of the bytes
+    O = Oracle(*cfg)
+    N, L, d = cfg[0], cfg[1], cfg[4]
+    n = 2 * N - 3
+    coords = np.full((n, d), 255, dtype=np.uint8)
+    coords[1::3] = 0
+    rnd = np.random.default_rng(N + L)
+    coords[2::3] = rnd.integers(0, 256, size=coords[2::3].shape, dtype=np.uint8)
+    perm = inputs.permutation(n, 3)
+    s, s_hat = O.keygen(31)
+    pk = O.public_key(s_hat, 32) if flood else None
+    F = O.max_flood_bits() if flood else 0
+    for qv in (np.zeros(d, dtype=np.uint8), np.full(d, 255, dtype=np.uint8)):
+        ct = O.encrypt(s_hat, qv, 33, 6)
+        out, srv = O.distances(ct, coords, perm, 34, 6, pk=pk, flood_bits=F, slots=slots)
+        sw = O.mod_switch(out)
+        assert sw.nbytes * L == out.nbytes
+        cli = O.decrypt_shares_switched(sw, s, qv, n, slots=slots)
+        brute = np.sum((coords[perm].astype(np.int64) - qv.astype(np.int64)) ** 2, axis=1)
+        assert np.array_equal((cli.astype(np.int64) + srv) % O.t, brute)
