@@ -493,8 +493,11 @@ def run_gpu(args) -> None:
     # the encryption seed (sanns_expand_query) before the distance step
     c0_host = ct_all[:nh, :, 0].contiguous().cpu().pin_memory()
     c0_dev = [torch.empty((1, d, L, N), dtype=torch.uint64, device="cuda") for _ in range(2)]
+    # responses switched down to q_0 (sanns_set_response_primes): the download
+    # is the compact q_0 rows, a third of the bytes
+    sw_host = [torch.empty((1, K, 2, 1, N), dtype=torch.uint64).pin_memory() for _ in range(2)]
 
-    def run_e2e(nsteps, seeded=False):
+    def run_e2e(nsteps, seeded=False, switched=False):
         up_done = [torch.cuda.Event() for _ in range(nsteps)]
         cmp_done = [torch.cuda.Event() for _ in range(nsteps)]
         dn_done = [torch.cuda.Event() for _ in range(nsteps)]
@@ -520,7 +523,10 @@ def run_gpu(args) -> None:
             cmp_done[s].record(s_cmp)
             with torch.cuda.stream(s_dn):
                 s_dn.wait_event(cmp_done[s])
-                out_host[u].copy_(out_dev[u], non_blocking=True)
+                if switched:
+                    S.sanns_copy_responses(ctx, out_dev[u], sw_host[u], stream=s_dn)
+                else:
+                    out_host[u].copy_(out_dev[u], non_blocking=True)
                 srv_host[u].copy_(srv_dev[u], non_blocking=True)
                 dn_done[s].record(s_dn)
         return dn_done[-1]
@@ -540,6 +546,26 @@ def run_gpu(args) -> None:
     e2e_seeded_ms = (time.perf_counter() - t_start) * 1e3 / e2e_steps
     seeded_exact = bool(torch.equal(
         S.sanns_expand_query(ctx, c0_host[0:1].cuda(), W["seed"] + 4, qids[0:1]), ct_all[0:1]))
+    S.sanns_set_response_primes(ctx, 1)
+    e2e_sw = {}
+    for seeded in (False, True):
+        run_e2e(4, seeded=seeded, switched=True)
+        torch.cuda.synchronize()
+        t_start = time.perf_counter()
+        run_e2e(e2e_steps, seeded=seeded, switched=True).synchronize()
+        torch.cuda.synchronize()
+        e2e_sw[seeded] = (time.perf_counter() - t_start) * 1e3 / e2e_steps
+    # the last step's downloaded switched response decrypts to shares that
+    # reconstruct the brute-force distances of its query
+    s_last = e2e_steps - 1
+    u_last, q_last = s_last % 2, s_last % nh
+    cli_sw = S.sanns_decrypt_shares(ctx, sk, sw_host[u_last].cuda(), n, qdev[q_last:q_last + 1])
+    pts_all = torch.from_numpy(coords).cuda()[torch.from_numpy(perm.astype(np.int64)).cuda()]
+    brute_sw = ((pts_all.int() - qdev[q_last].int()) ** 2).sum(1)
+    switched_exact = bool(torch.equal((cli_sw[0].long() + srv_host[u_last][0].cuda().long()) % t_mod,
+                                      brute_sw.long()))
+    del cli_sw, brute_sw, pts_all
+    S.sanns_set_response_primes(ctx, L)
     # the host link alone: the same uploads and downloads, both directions at
     # once on their own streams, no compute
     link_reps = 20
@@ -627,6 +653,19 @@ def run_gpu(args) -> None:
                 "what": "as e2e, but the client uploads c0 alone and the server rebuilds c1 from "
                         "the encryption seed (sanns_expand_query): an option beyond the paper, "
                         "whose client sends both components"},
+            "e2e_switched_responses": {
+                "value": world * n / (e2e_sw[False] * 1e-3), "unit": UNIT,
+                "h2d_bytes_per_step": d * 2 * L * N * 8,
+                "d2h_bytes_per_step": K * 2 * N * 8 + n * 4, "ms_per_step": e2e_sw[False],
+                "shares_equal_brute_force": switched_exact,
+                "seeded_queries": {"value": world * n / (e2e_sw[True] * 1e-3), "unit": UNIT,
+                                   "h2d_bytes_per_step": d * L * N * 8,
+                                   "d2h_bytes_per_step": K * 2 * N * 8 + n * 4,
+                                   "ms_per_step": e2e_sw[True]},
+                "what": "as e2e, but the server switches each response down to q_0 "
+                        "(sanns_set_response_primes; the client decrypts modulo q_0) and "
+                        "downloads a third of the bytes: an option beyond the paper, whose "
+                        "server sends the responses at the full modulus"},
             "selection": selection,
             "ntt": dict(_ntt_report(K * 2 * L, N, serial_fin_ms,
                                     "INTT + mask of one query (mask draw, intt_mask_short_kernel), "

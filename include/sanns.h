@@ -439,6 +439,39 @@ int sanns_set_encoding(sanns_ctx *ctx, int slots);
 int sanns_set_response_form(sanns_ctx *ctx, int form);
 
 /*
+ * Response modulus (an option beyond the paper, whose server sends the
+ * responses at the full modulus Q = q_0 ... q_{L-1}).  primes = L (default):
+ * as the paper.  primes = 1: after the epilogue the server switches every
+ * coefficient-form response down to q_0, the standard BFV modulus switch
+ * c -> round(q_0 c / Q) mod q_0 of each coefficient c in [0, Q), computed in
+ * RNS (Garner digits of the dropped primes, exact), so a response costs 1/L
+ * of the bytes.  After the switch the phase noise is (q_0 / Q) e plus at
+ * most (N + 1) / 2 of rounding; with e up to the largest circuit-privacy
+ * flooding (Q / (4t)) it stays below q_0 / (2t), so decryption is unchanged,
+ * whenever q_0 > 2t (N + 5) -- the call returns SANNS_EINVAL otherwise.
+ *   - sanns_distances / sanns_distances_batched then leave the switched
+ *     response in the j = 0 rows of ct_out_dev ([B][K][2][L][N], rows of N
+ *     words at a pitch of L N); the other rows are scratch.
+ *     sanns_copy_responses gathers them compact.
+ *   - sanns_decrypt_shares(_noalloc) on a context with primes = 1 takes the
+ *     compact switched responses, [B][K][2][N], and decrypts modulo q_0.
+ *   - Not with NTT-form responses (SANNS_EINVAL either way round), and the
+ *     clustering gather rejects calls while primes = 1.
+ * Both sides of a protocol run must use the same setting.
+ */
+int sanns_set_response_primes(sanns_ctx *ctx, uint32_t primes);
+
+/*
+ * Copies the responses of B queries over K blocks from ct_out_dev (as a
+ * distance call left them) to dst, compact: [B][K][2][R][N] with R the
+ * response primes (L: the whole buffer; 1: the j = 0 rows).  dst may be
+ * device memory or pinned host memory (the download of a response).
+ * Asynchronous on stream.
+ */
+int sanns_copy_responses(const sanns_ctx *ctx, const uint64_t *ct_out_dev, uint32_t B, uint64_t K,
+                         uint64_t *dst, void *stream);
+
+/*
  * Plaintext meaning of the selection step (Sec. 4, Algorithms 1 and 2; the
  * paper evaluates it inside garbled circuits, which this library does not):
  * for every query b the k smallest reconstructed distances
@@ -520,6 +553,9 @@ int sanns_set_circuit_privacy(sanns_ctx *ctx, const uint64_t *pk_dev, uint32_t f
  * primes), cli_share[b][pos] = (m + ||q_b||^2) mod t.  ct_out_dev
  * [B][K][2][L][N] with K = ceil(n / N); q_dev uint8 [B][d]; cli_share_dev
  * uint32 [B][n].  Uses a stream-ordered scratch allocation of B K L N words.
+ * With sanns_set_response_primes(ctx, 1): ct_out_dev is [B][K][2][N] modulo
+ * q_0 (sanns_copy_responses' compact form), Q is q_0, and the scratch is
+ * B K N words.
  */
 int sanns_decrypt_shares(sanns_ctx *ctx, const sanns_sk *sk, const uint64_t *ct_out_dev,
                          uint32_t B, uint64_t n, const uint8_t *q_dev, uint32_t *cli_share_dev,

@@ -142,6 +142,14 @@ int sanns_ctx_create(const sanns_params* p, sanns_ctx** out) {
   if (e != cudaSuccess) { cudaFree(c->d_tables); delete c; return cuda_fail(e, "cudaMemcpy(tables)"); }
   c->P.tw = reinterpret_cast<const ulonglong2*>(c->d_tables);
   c->P.itw = reinterpret_cast<const ulonglong2*>(c->d_tables + 2 * per);
+  // responses at every prime by default; the one-prime view (q_0 alone, its
+  // tables the first rows of the full ones) decrypts switched responses
+  c->response_primes = p->L;
+  c->P1 = c->P;
+  fill_prime_constants(c->P1, q, t, 1);
+  c->P1.last_inv[0] = c->P.last_inv[0];
+  c->P1.last_inv_shoup[0] = c->P.last_inv_shoup[0];
+  make_mod_switch_consts(c->P, &c->MS);
   e = cudaMalloc(&c->d_err, sizeof(int));
   if (e == cudaSuccess) e = cudaMemset(c->d_err, 0, sizeof(int));
   if (e != cudaSuccess) { cudaFree(c->d_tables); delete c; return cuda_fail(e, "cudaMalloc(err)"); }
@@ -488,13 +496,47 @@ int sanns_distances_finish(sanns_ctx* ctx, const sanns_db* db, uint32_t B, uint6
                             ctx->privacy, st));
   if (ctx->slots)
     SANNS_CUDA(launch_slot_share(ctx->P, ctx->PT, B, db->K, db->n, db->pos0, mask_seed, qids, srv_share, st));
+  if (ctx->response_primes == 1)
+    SANNS_CUDA(launch_mod_switch(ctx->P, ctx->MS, ct_out, (uint64_t)B * db->K * 2, st));
   return SANNS_OK;
 }
 
 int sanns_set_response_form(sanns_ctx* ctx, int form) {
   if (!ctx) return fail(SANNS_EINVAL, "ctx is NULL");
   if (form != 0 && form != 1) return fail(SANNS_EINVAL, "form must be 0 (coefficients) or 1 (NTT)");
+  if (form == 1 && ctx->response_primes != ctx->P.L)
+    return fail(SANNS_EINVAL, "NTT-form responses cannot be modulus-switched (switching needs coefficients)");
   ctx->ntt_responses = form == 1;
+  return SANNS_OK;
+}
+
+int sanns_set_response_primes(sanns_ctx* ctx, uint32_t primes) {
+  if (!ctx) return fail(SANNS_EINVAL, "ctx is NULL");
+  if (primes != 1 && primes != ctx->P.L)
+    return fail(SANNS_EINVAL, "primes must be 1 (switch to q_0) or L (every prime)");
+  if (primes != ctx->P.L && ctx->ntt_responses)
+    return fail(SANNS_EINVAL, "NTT-form responses cannot be modulus-switched (switching needs coefficients)");
+  // after the switch the phase noise is (q_0 / Q) e plus the rounding
+  // (|eps_0 + eps_1 s| <= (N + 1) / 2); decryption mod q_0 needs it below
+  // q_0 / (2t), with e up to the largest flooding, Q / (4t): q_0 > 2t (N + 5)
+  if (primes == 1 && (u128)ctx->P.q[0] <= (u128)2 * ctx->P.t * (ctx->P.N + 5))
+    return fail(SANNS_EINVAL, "q_0 too small to switch to: decryption needs q_0 > 2 t (N + 5)");
+  ctx->response_primes = primes;
+  return SANNS_OK;
+}
+
+int sanns_copy_responses(const sanns_ctx* ctx, const uint64_t* ct_out, uint32_t B, uint64_t K, uint64_t* dst,
+                         void* stream) {
+  if (!ctx) return fail(SANNS_EINVAL, "ctx is NULL");
+  if (B == 0 || K == 0) return SANNS_OK;
+  if (!ct_out || !dst) return fail(SANNS_EINVAL, "NULL buffer");
+  const uint64_t N = ctx->P.N, L = ctx->P.L, rows = (uint64_t)B * K * 2;
+  cudaStream_t st = as_stream(stream);
+  if (ctx->response_primes == L)
+    SANNS_CUDA(cudaMemcpyAsync(dst, ct_out, sizeof(uint64_t) * rows * L * N, cudaMemcpyDefault, st));
+  else
+    SANNS_CUDA(cudaMemcpy2DAsync(dst, sizeof(uint64_t) * N, ct_out, sizeof(uint64_t) * L * N,
+                                 sizeof(uint64_t) * N, rows, cudaMemcpyDefault, st));
   return SANNS_OK;
 }
 
@@ -762,6 +804,8 @@ int sanns_distances_gather(sanns_ctx* ctx, const sanns_clusters* cl, const uint6
   if (!ctx || !cl) return fail(SANNS_EINVAL, "ctx or clusters is NULL");
   if (cl->ctx != ctx) return fail(SANNS_EINVAL, "clusters belong to another context");
   if (ctx->P.N > 8192) return fail(SANNS_EINVAL, "the gather path supports N <= 8192");
+  if (ctx->response_primes != ctx->P.L)
+    return fail(SANNS_EINVAL, "the clustering gather returns responses at every prime");
   if (B == 0) return SANNS_OK;
   if (!ct_in || !qids || !ct_out || !srv_share || !probes) return fail(SANNS_EINVAL, "NULL buffer");
   std::vector<uint64_t> nb(B), kb(B);
@@ -824,6 +868,8 @@ int sanns_distances_gather_prepared(sanns_ctx* ctx, const sanns_gather_batch* gb
                                     uint32_t* srv_share, uint32_t* ids, void* stream) {
   if (!ctx || !gb) return fail(SANNS_EINVAL, "ctx or batch is NULL");
   if (gb->ctx != ctx) return fail(SANNS_EINVAL, "the batch belongs to another context");
+  if (ctx->response_primes != ctx->P.L)
+    return fail(SANNS_EINVAL, "the clustering gather returns responses at every prime");
   if (!ct_in || !qids || !ct_out || !srv_share) return fail(SANNS_EINVAL, "NULL buffer");
   int rc = check_device(ctx);
   if (rc) return rc;
@@ -1010,14 +1056,16 @@ int sanns_decrypt_shares(sanns_ctx* ctx, const sanns_sk* sk, const uint64_t* ct_
   if (B == 0 || n == 0) return SANNS_OK;
   if (!ct_out || !qv || !cli_share) return fail(SANNS_EINVAL, "NULL buffer");
   const uint64_t K = (n + ctx->P.N - 1) / ctx->P.N;
-  if ((uint64_t)B * K * ctx->P.L > 0x7fffffffull || (uint64_t)B * n > (1ull << 40))
+  // switched responses ([B][K][2][N], modulo q_0) decrypt in the one-prime view
+  const PrimeSet& PD = ctx->response_primes == 1 ? ctx->P1 : ctx->P;
+  if ((uint64_t)B * K * PD.L > 0x7fffffffull || (uint64_t)B * n > (1ull << 40))
     return fail(SANNS_EINVAL, "batch too large");
   int rc = check_device(ctx);
   if (rc) return rc;
   cudaStream_t st = as_stream(stream);
   uint64_t* scratch = nullptr;
-  SANNS_CUDA(cudaMallocAsync(&scratch, sizeof(uint64_t) * B * K * ctx->P.L * ctx->P.N, st));
-  cudaError_t e = launch_decrypt(ctx->P, ct_out, sk->d_s, sk->d_s_hat, sk->d_s_hat_shoup, B, K, n, qv,
+  SANNS_CUDA(cudaMallocAsync(&scratch, sizeof(uint64_t) * B * K * PD.L * PD.N, st));
+  cudaError_t e = launch_decrypt(PD, ct_out, sk->d_s, sk->d_s_hat, sk->d_s_hat_shoup, B, K, n, qv,
                                  ctx->params.d, scratch, cli_share, ctx->ntt_responses,
                                  ctx->slots ? &ctx->PT : nullptr, st);
   cudaError_t e2 = cudaFreeAsync(scratch, st);

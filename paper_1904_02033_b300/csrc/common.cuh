@@ -30,6 +30,20 @@ struct PrivacyConsts {
   uint64_t two_f[kMaxPrimes];       // 2^F mod q_j
 };
 
+// Modulus switching of responses from q_0 .. q_{L-1} down to q_0 (modswitch.cu):
+// Garner constants of the dropped primes q_1 .. q_{L-1}, by value.
+struct ModSwitchConsts {
+  uint64_t g[kMaxPrimes][kMaxPrimes];   // g[i][m] = q_1 .. q_{m-1} mod q_i (m < i)
+  uint64_t gs[kMaxPrimes][kMaxPrimes];
+  uint64_t ginv[kMaxPrimes];            // (q_1 .. q_{i-1})^-1 mod q_i
+  uint64_t ginvs[kMaxPrimes];
+  uint64_t h[kMaxPrimes];               // mixed-radix digits of (P - 1) / 2, P = q_1 .. q_{L-1}
+  uint64_t w0[kMaxPrimes];              // q_1 .. q_{m-1} mod q_0
+  uint64_t w0s[kMaxPrimes];
+  uint64_t p0;                          // P mod q_0
+  uint64_t pinv0, pinv0s;               // P^-1 mod q_0
+};
+
 // Per-prime constants, passed to kernels by value.
 struct PrimeSet {
   uint32_t N, logN, L, pad;

@@ -28,6 +28,12 @@ struct sanns_ctx {
   uint32_t flood_bits;
   sanns::PrivacyConsts privacy;
   bool ntt_responses;       // responses in NTT form (server finish and client decryption)
+  // responses switched down to q_0 (1) or kept at every prime (L): the
+  // one-prime view of the parameters that decrypts them, and the constants
+  // of the switch
+  uint32_t response_primes;
+  sanns::PrimeSet P1;
+  sanns::ModSwitchConsts MS;
   // slot encoding (t = 1 mod 2N): the negacyclic transform mod t as a
   // one-prime set (its tables in d_tables_t), and whether new databases and
   // decryptions use it
@@ -101,6 +107,11 @@ void fill_prime_constants(PrimeSet& P, const uint64_t q[], uint64_t t, uint32_t 
 void fill_twiddles(uint32_t N, uint64_t q, uint64_t psi, uint64_t* tw, uint64_t* tws, uint64_t* itw,
                    uint64_t* itws);
 uint64_t shoup_of(uint64_t w, uint64_t q);
+
+// modulus switching of the responses down to q_0 (modswitch.cu)
+void make_mod_switch_consts(const PrimeSet& P, ModSwitchConsts* C);
+cudaError_t launch_mod_switch(const PrimeSet& P, const ModSwitchConsts& C, uint64_t* buf, uint64_t tuples,
+                              cudaStream_t st);
 
 // kernel launchers (ntt.cu, mac.cu, client.cu)
 cudaError_t launch_ntt(const PrimeSet& P, uint64_t* data, uint64_t count, bool inverse,

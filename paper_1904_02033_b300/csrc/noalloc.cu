@@ -50,7 +50,8 @@ extern "C" int sanns_decrypt_shares_noalloc(sanns_ctx* ctx, const sanns_sk* sk, 
   if (B == 0 || n == 0) return SANNS_OK;
   if (!ct_out || !qv || !cli_share) return fail(SANNS_EINVAL, "NULL buffer");
   const uint64_t K = (n + ctx->P.N - 1) / ctx->P.N;
-  const uint64_t words = (uint64_t)B * K * ctx->P.L * ctx->P.N;
+  const PrimeSet& PD = ctx->response_primes == 1 ? ctx->P1 : ctx->P;   // switched responses: q_0 alone
+  const uint64_t words = (uint64_t)B * K * PD.L * PD.N;
   if (words > kNoAllocWords)
     return fail(SANNS_EINVAL, "decryption needs " + std::to_string(words) +
                                   " scratch words; the static scratch holds " +
@@ -64,7 +65,7 @@ extern "C" int sanns_decrypt_shares_noalloc(sanns_ctx* ctx, const sanns_sk* sk, 
   if (rc) return rc;
   // every scratch word the second phase reads is written by the first phase
   // of the same call, so nothing needs clearing between calls
-  e = launch_decrypt(ctx->P, ct_out, sk->d_s, sk->d_s_hat, sk->d_s_hat_shoup, B, K, n, qv,
+  e = launch_decrypt(PD, ct_out, sk->d_s, sk->d_s_hat, sk->d_s_hat_shoup, B, K, n, qv,
                      ctx->params.d, scratch, cli_share, ctx->ntt_responses,
                      ctx->slots ? &ctx->PT : nullptr, reinterpret_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) return cuda_fail(e, "decrypt kernels");

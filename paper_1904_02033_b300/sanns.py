@@ -72,6 +72,8 @@ _SIGS = {
     "sanns_set_encoding": ([_VP, C.c_int], C.c_int),
     "sanns_selftest_wait_timeout": ([_VP, C.c_uint32, _VP], C.c_int),
     "sanns_set_response_form": ([_VP, C.c_int], C.c_int),
+    "sanns_set_response_primes": ([_VP, C.c_uint32], C.c_int),
+    "sanns_copy_responses": ([_VP, _VP, C.c_uint32, C.c_uint64, _VP, _VP], C.c_int),
     "sanns_topk": ([_VP, _VP, _VP, C.c_uint32, C.c_uint64, C.c_uint32, C.c_uint64, C.c_uint32, _VP,
                     _VP, _VP], C.c_int),
     "sanns_topk_segments": ([_VP, _VP, _VP, C.c_uint32, _VP, _VP, _VP, _VP, _VP, C.c_uint32,
@@ -141,6 +143,7 @@ class Context:
         self.handle = handle
         self.N, self.L, self.prime_bits, self.t_rule, self.d, self.b_c = (
             N, L, prime_bits, t_rule, d, b_c)
+        self.response_primes = L
 
     def __del__(self):
         if getattr(self, "handle", None) and _LIB is not None:
@@ -480,6 +483,33 @@ def sanns_set_encoding(ctx: Context, slots: bool):
 def sanns_set_response_form(ctx: Context, ntt: bool):
     """Responses in NTT form (True) or coefficient form (False, default)."""
     _check(load().sanns_set_response_form(ctx.handle, 1 if ntt else 0))
+
+
+def sanns_set_response_primes(ctx: Context, primes: int):
+    """Responses switched down to q_0 (1) or kept at every prime (ctx.L,
+    default)."""
+    _check(load().sanns_set_response_primes(ctx.handle, primes))
+    ctx.response_primes = primes
+
+
+def sanns_copy_responses(ctx: Context, ct_out: torch.Tensor, dst: torch.Tensor | None = None,
+                         stream=None) -> torch.Tensor:
+    """The responses a distance call left in ct_out [B][K][2][L][N], compact:
+    [B][K][2][R][N] with R = ctx.response_primes, into dst (device or pinned
+    host memory; a new device tensor when None)."""
+    B, K = ct_out.shape[0], ct_out.shape[1]
+    shape = (B, K, 2, ctx.response_primes, ctx.N)
+    if dst is None:
+        dst = torch.empty(shape, dtype=torch.uint64, device="cuda")
+    assert tuple(dst.shape) == shape and dst.is_contiguous() and dst.dtype == torch.uint64
+    if dst.is_cuda:
+        dp = _ptr(dst)
+    elif dst.is_pinned():
+        dp = C.c_void_p(dst.data_ptr())
+    else:
+        raise ValueError("dst must be a CUDA tensor or pinned host memory")
+    _check(load().sanns_copy_responses(ctx.handle, _ptr(ct_out), B, K, dp, _stream(stream)))
+    return dst
 
 
 def sanns_topk(ctx: Context, cli_share: torch.Tensor, srv_share: torch.Tensor, k: int,
