@@ -476,9 +476,11 @@ def run_gpu(args) -> None:
     S.sanns_set_encoding(ctx, False)
 
     # end-to-end through the C ABI: each step copies its query ciphertext from
-    # pinned host memory, runs sanns_distances and copies the response
-    # ciphertexts and the server share back; three streams overlap step s's
-    # compute with the upload of s+1 and the download of s-1.
+    # pinned host memory, runs the distance step (sanns_distances_mac, then
+    # sanns_distances_finish) and copies the response ciphertexts and the
+    # server share back; four streams overlap step s's MAC with step s-1's
+    # finish (the MAC's grid at the tuned SM cap, as in the timed loop), the
+    # upload of s+1 and the download of s-1.
     nh = min(4, W["n_queries"])
     ct_host = ct_all[:nh].cpu().pin_memory()
     out_host = [torch.empty((1, K, 2, L, N), dtype=torch.uint64).pin_memory() for _ in range(2)]
@@ -487,6 +489,7 @@ def run_gpu(args) -> None:
     out_dev = [torch.empty((1, K, 2, L, N), dtype=torch.uint64, device="cuda") for _ in range(2)]
     srv_dev = [torch.empty((1, n), dtype=torch.uint32, device="cuda") for _ in range(2)]
     s_up, s_cmp, s_dn = torch.cuda.Stream(), torch.cuda.Stream(), torch.cuda.Stream()
+    s_fin = torch.cuda.Stream()
     e2e_steps = max(10, min(args.steps, 100))
 
     # seeded queries: the client sends c0 alone; the server rebuilds c1 from
@@ -499,6 +502,7 @@ def run_gpu(args) -> None:
 
     def run_e2e(nsteps, seeded=False, switched=False):
         up_done = [torch.cuda.Event() for _ in range(nsteps)]
+        mac_done = [torch.cuda.Event() for _ in range(nsteps)]
         cmp_done = [torch.cuda.Event() for _ in range(nsteps)]
         dn_done = [torch.cuda.Event() for _ in range(nsteps)]
         for s in range(nsteps):
@@ -506,7 +510,7 @@ def run_gpu(args) -> None:
             qi = s % nh
             with torch.cuda.stream(s_up):
                 if s >= 2:
-                    s_up.wait_event(cmp_done[s - 2])      # ct_dev[u] free again
+                    s_up.wait_event(mac_done[s - 2])      # ct_dev[u] free again
                 if seeded:
                     c0_dev[u].copy_(c0_host[qi:qi + 1], non_blocking=True)
                 else:
@@ -514,13 +518,16 @@ def run_gpu(args) -> None:
                 up_done[s].record(s_up)
             s_cmp.wait_event(up_done[s])
             if s >= 2:
-                s_cmp.wait_event(dn_done[s - 2])          # out_dev[u] downloaded
+                s_cmp.wait_event(dn_done[s - 2])          # out_dev[u], srv_dev[u] downloaded
             if seeded:
                 S.sanns_expand_query(ctx, c0_dev[u], W["seed"] + 4, qids[qi:qi + 1], out=ct_dev[u],
                                      stream=s_cmp)
-            S.sanns_distances(ctx, db, ct_dev[u], mask_seed, qids[qi:qi + 1], out_dev[u],
-                              srv_dev[u], stream=s_cmp)
-            cmp_done[s].record(s_cmp)
+            S.sanns_distances_mac(ctx, db, ct_dev[u], out_dev[u], stream=s_cmp)
+            mac_done[s].record(s_cmp)
+            s_fin.wait_event(mac_done[s])
+            S.sanns_distances_finish(ctx, db, out_dev[u], mask_seed, qids[qi:qi + 1], srv_dev[u],
+                                     stream=s_fin)
+            cmp_done[s].record(s_fin)
             with torch.cuda.stream(s_dn):
                 s_dn.wait_event(cmp_done[s])
                 if switched:
@@ -531,6 +538,7 @@ def run_gpu(args) -> None:
                 dn_done[s].record(s_dn)
         return dn_done[-1]
 
+    S.sanns_set_mac_sms(ctx, mac_sms)
     run_e2e(4)
     torch.cuda.synchronize()
     t_start = time.perf_counter()
@@ -566,6 +574,7 @@ def run_gpu(args) -> None:
                                       brute_sw.long()))
     del cli_sw, brute_sw, pts_all
     S.sanns_set_response_primes(ctx, L)
+    S.sanns_set_mac_sms(ctx, 0)
     # the host link alone: the same uploads and downloads, both directions at
     # once on their own streams, no compute
     link_reps = 20
@@ -643,8 +652,8 @@ def run_gpu(args) -> None:
                     "d2h_bytes_per_step": K * 2 * L * N * 8 + n * 4, "ms_per_step": e2e_ms,
                     "link_only_ms_per_step": link_ms,
                     "link_bound_frac": link_ms / e2e_ms,
-                    "timing": "host wall clock over pipelined steps (3 streams: upload, "
-                              "compute, download)"},
+                    "timing": "host wall clock over pipelined steps (4 streams: upload, MAC, "
+                              "finish, download)"},
             "e2e_seeded_queries": {
                 "value": world * n / (e2e_seeded_ms * 1e-3), "unit": UNIT,
                 "h2d_bytes_per_step": d * L * N * 8,
