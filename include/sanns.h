@@ -455,8 +455,10 @@ int sanns_set_response_form(sanns_ctx *ctx, int form);
  *     sanns_copy_responses gathers them compact.
  *   - sanns_decrypt_shares(_noalloc) on a context with primes = 1 takes the
  *     compact switched responses, [B][K][2][N], and decrypts modulo q_0.
- *   - Not with NTT-form responses (SANNS_EINVAL either way round), and the
- *     clustering gather rejects calls while primes = 1.
+ *   - The clustering gather does the same to each work item's response
+ *     ([W][2][L][N]: its j = 0 rows; sanns_copy_responses with B = 1,
+ *     K = W gathers them).
+ *   - Not with NTT-form responses (SANNS_EINVAL either way round).
  * Both sides of a protocol run must use the same setting.
  */
 int sanns_set_response_primes(sanns_ctx *ctx, uint32_t primes);

@@ -804,8 +804,6 @@ int sanns_distances_gather(sanns_ctx* ctx, const sanns_clusters* cl, const uint6
   if (!ctx || !cl) return fail(SANNS_EINVAL, "ctx or clusters is NULL");
   if (cl->ctx != ctx) return fail(SANNS_EINVAL, "clusters belong to another context");
   if (ctx->P.N > 8192) return fail(SANNS_EINVAL, "the gather path supports N <= 8192");
-  if (ctx->response_primes != ctx->P.L)
-    return fail(SANNS_EINVAL, "the clustering gather returns responses at every prime");
   if (B == 0) return SANNS_OK;
   if (!ct_in || !qids || !ct_out || !srv_share || !probes) return fail(SANNS_EINVAL, "NULL buffer");
   std::vector<uint64_t> nb(B), kb(B);
@@ -820,6 +818,8 @@ int sanns_distances_gather(sanns_ctx* ctx, const sanns_clusters* cl, const uint6
                            ct_out, srv_share, ids, ctx->sms, ctx->slots ? &ctx->PT : nullptr, ctx->d_pk,
                            ctx->d_pk_shoup, ctx->flood_bits, ctx->privacy, ctx->ntt_responses,
                            as_stream(stream)));
+  if (ctx->response_primes == 1)
+    SANNS_CUDA(launch_mod_switch(ctx->P, ctx->MS, ct_out, W * 2, as_stream(stream)));
   return SANNS_OK;
 }
 
@@ -868,14 +868,14 @@ int sanns_distances_gather_prepared(sanns_ctx* ctx, const sanns_gather_batch* gb
                                     uint32_t* srv_share, uint32_t* ids, void* stream) {
   if (!ctx || !gb) return fail(SANNS_EINVAL, "ctx or batch is NULL");
   if (gb->ctx != ctx) return fail(SANNS_EINVAL, "the batch belongs to another context");
-  if (ctx->response_primes != ctx->P.L)
-    return fail(SANNS_EINVAL, "the clustering gather returns responses at every prime");
   if (!ct_in || !qids || !ct_out || !srv_share) return fail(SANNS_EINVAL, "NULL buffer");
   int rc = check_device(ctx);
   if (rc) return rc;
   SANNS_CUDA(launch_gather_prepared(ctx->P, ctx->params.d, gb, ct_in, mask_seed, qids, ct_out, srv_share, ids,
                                     ctx->sms, ctx->slots ? &ctx->PT : nullptr, ctx->d_pk, ctx->d_pk_shoup,
                                     ctx->flood_bits, ctx->privacy, ctx->ntt_responses, as_stream(stream)));
+  if (ctx->response_primes == 1)
+    SANNS_CUDA(launch_mod_switch(ctx->P, ctx->MS, ct_out, gb->W * 2, as_stream(stream)));
   return SANNS_OK;
 }
 

@@ -1,9 +1,9 @@
 """Modulus-switched responses (an option beyond the paper, whose server sends
 the responses at the full modulus): the GPU's RNS switch equals the oracle's
 round(q_0 c / Q) mod q_0 of each coefficient's CRT integer, element by
-element, on both distance paths, with circuit privacy and with slot
-encoding; decryption modulo q_0 gives the oracle's client shares, which
-reconstruct the brute-force distances."""
+element, on the per-query, tensor-core and gather paths, with circuit
+privacy and slot encoding; decryption modulo q_0 gives the oracle's client
+shares, which reconstruct the brute-force distances."""
 import numpy as np
 import pytest
 import torch
@@ -118,15 +118,46 @@ def test_switching_rules():
     S.sanns_set_response_primes(ctx, 1)
     with pytest.raises(S.SannsError):
         S.sanns_set_response_form(ctx, True)
-    # the clustering gather answers at every prime only
-    coords = inputs.uniform_coords(300, 5, 1)
-    offsets, members = inputs.clusters_csr(np.arange(300) % 4, 4)
+
+
+@pytest.mark.parametrize("cfg,F", [((256, 3, 60, 0, 5), 0), ((256, 2, 40, 0, 5), 30)])
+def test_switched_gather_responses_equal_oracle(cfg, F):
+    # the clustering gather switches each work item's response the same way
+    N, L, bits, rule, d = cfg
+    n, C, B, P = 3000, 20, 3, 4
+    rnd = np.random.default_rng(n + L)
+    coords = inputs.uniform_coords(n, d, 1)
+    assign = rnd.choice(C, size=n, p=inputs.zipf_weights(C, 1.1))
+    offsets, members = inputs.clusters_csr(assign, C)
+    probes = np.stack([rnd.permutation(C)[:P] for _ in range(B)]).astype(np.uint32)
+    q = inputs.uniform_coords(B, d, 2)
+    qids = np.array([5 + 3 * b for b in range(B)], dtype=np.uint64)
+    ctx = S.sanns_ctx_create(*cfg)
+    sk = S.sanns_keygen(ctx, 3)
+    pk = None
+    if F:
+        pk_d = S.sanns_public_key(ctx, sk, 8)
+        S.sanns_set_circuit_privacy(ctx, pk_d, F)
+        pk = pk_d.cpu().numpy()
+    S.sanns_set_response_primes(ctx, 1)
     cl = S.sanns_clusters_create(ctx, cu(coords), offsets, cu(members))
-    sk = S.sanns_keygen(ctx, 2)
-    qids = cu(np.array([3], dtype=np.uint64))
-    ct_in = S.sanns_encrypt_query(ctx, sk, cu(inputs.uniform_coords(1, 5, 3)), 4, qids)
-    with pytest.raises(S.SannsError):
-        S.sanns_distances_gather(ctx, cl, ct_in, np.array([[0, 1]], dtype=np.uint32), 6, qids)
-    S.sanns_set_response_primes(ctx, 3)
-    S.sanns_distances_gather(ctx, cl, ct_in, np.array([[0, 1]], dtype=np.uint32), 6, qids)
+    ct_in = S.sanns_encrypt_query(ctx, sk, cu(q), 4, cu(qids))
+    ct_out, srv, ids, n_b, k_b = S.sanns_distances_gather(ctx, cl, ct_in, probes, 6, cu(qids))
+    W = int(k_b.sum())
+    sw = S.sanns_copy_responses(ctx, ct_out[:W].reshape(1, W, 2, L, N)).reshape(W, 2, N)
     S.sanns_device_status(ctx)
+    sw, srv, ct_np = sw.cpu().numpy(), srv.cpu().numpy(), ct_in.cpu().numpy()
+    O = oracle(*cfg)
+    s_, _ = O.keygen(3)
+    kb0 = nb0 = 0
+    for b in range(B):
+        g = np.concatenate([members[offsets[c]:offsets[c + 1]] for c in probes[b]]).astype(np.uint32)
+        full, want_srv = O.distances(ct_np[b], coords, g, 6, int(qids[b]), pk=pk, flood_bits=F)
+        want = O.mod_switch(full)
+        assert np.array_equal(sw[kb0:kb0 + int(k_b[b])], want), b
+        assert np.array_equal(srv[nb0:nb0 + len(g)], want_srv), b
+        cli = O.decrypt_shares_switched(want, s_, q[b], len(g))
+        brute = np.sum((coords[g].astype(np.int64) - q[b].astype(np.int64)) ** 2, axis=1)
+        assert np.array_equal((cli.astype(np.int64) + want_srv) % O.t, brute), b
+        kb0 += int(k_b[b])
+        nb0 += len(g)
