@@ -298,13 +298,15 @@ __device__ __forceinline__ void inv_bfly_t(uint64_t& X, uint64_t& Y, uint64_t w,
   else inv_bfly(X, Y, w, ws, q, bound);
 }
 
-__device__ __forceinline__ void ntt_forward_smem(uint64_t* a, const PrimeSet& P, int j) {
+// first_st: leading radix-2 stages the caller has already done (values then
+// lazily below 4q), at most logN & 3.
+__device__ __forceinline__ void ntt_forward_smem(uint64_t* a, const PrimeSet& P, int j, uint32_t first_st = 0) {
   const uint32_t N = P.N, logN = P.logN;
   const uint64_t q = P.q[j], q2 = 2 * q;
   const ulonglong2* tw = P.tw + (size_t)j * N;
   const uint32_t r2 = logN & 3;  // leading radix-2 stages
-  uint32_t lt = logN - 1;         // log2 of the butterfly distance t
-  for (uint32_t st = 0; st < r2; ++st, --lt) {
+  uint32_t lt = logN - 1 - first_st;  // log2 of the butterfly distance t
+  for (uint32_t st = first_st; st < r2; ++st, --lt) {
     const uint32_t t = 1u << lt, m = 1u << st;
     for (uint32_t bf = threadIdx.x; bf < N / 2; bf += blockDim.x) {
       const uint32_t i = bf >> lt, x = (i << (lt + 1)) + (bf & (t - 1));

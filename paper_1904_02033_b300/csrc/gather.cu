@@ -228,13 +228,41 @@ gather_kernel(PrimeSet P, uint32_t d, uint64_t W, uint32_t S, uint32_t ds,
     uint64_t* mine = part + u * 2 * N;  // this unit's accumulators: c0 at [0, N), c1 at [N, 2N)
     for (uint32_t i = i0; i < i1; ++i) {
       __syncthreads();
-      for (uint32_t x = threadIdx.x; x < N; x += blockDim.x) poly[SP(x)] = g[(uint64_t)i * N + x];
-      __syncthreads();
-      if (O.slots) {
-        ntt_inverse_smem(poly, O.PT, 0);
+      const uint8_t* gi = g + (uint64_t)i * N;   // 16-byte aligned: item and row offsets are multiples of N
+      if (!O.slots && (P.logN & 3)) {
+        // the coordinate bytes, 16 of each half per thread, go straight
+        // through the first forward stage (distance N/2, twiddle psi^brv(1))
+        const ulonglong2 w1 = __ldg(P.tw + (size_t)j * N + 1);
+        for (uint32_t gx = threadIdx.x; gx < N / 32; gx += blockDim.x) {
+          const uint32_t x = gx * 16;
+          const uint4 lo = __ldg(reinterpret_cast<const uint4*>(gi + x));
+          const uint4 hi = __ldg(reinterpret_cast<const uint4*>(gi + x + N / 2));
+          const uint32_t lw[4] = {lo.x, lo.y, lo.z, lo.w}, hw[4] = {hi.x, hi.y, hi.z, hi.w};
+#pragma unroll
+          for (int k = 0; k < 16; ++k) {
+            uint64_t X = (lw[k >> 2] >> (8 * (k & 3))) & 255u, Y = (hw[k >> 2] >> (8 * (k & 3))) & 255u;
+            fwd_bfly(X, Y, w1.x, w1.y, q, 2 * q);
+            poly[SP(x + k)] = X;
+            poly[SP(x + N / 2 + k)] = Y;
+          }
+        }
         __syncthreads();
+        ntt_forward_smem(poly, P, (int)j, 1);
+      } else {
+        for (uint32_t gx = threadIdx.x; gx < N / 16; gx += blockDim.x) {
+          const uint32_t x = gx * 16;
+          const uint4 v = __ldg(reinterpret_cast<const uint4*>(gi + x));
+          const uint32_t vw[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+          for (int k = 0; k < 16; ++k) poly[SP(x + k)] = (vw[k >> 2] >> (8 * (k & 3))) & 255u;
+        }
+        __syncthreads();
+        if (O.slots) {
+          ntt_inverse_smem(poly, O.PT, 0);
+          __syncthreads();
+        }
+        ntt_forward_smem(poly, P, (int)j);
       }
-      ntt_forward_smem(poly, P, (int)j);
       __syncthreads();
       const uint64_t* c0 = ct_in + ((((uint64_t)it.b * d + i) * 2 + 0) * L + j) * N;
       const uint64_t* c1 = ct_in + ((((uint64_t)it.b * d + i) * 2 + 1) * L + j) * N;
