@@ -94,6 +94,63 @@ __global__ void pack_kernel(uint32_t N, uint32_t d, uint64_t W, const GatherItem
   if (ids) ids[Q.pos_off + pos] = pt;
 }
 
+// The same packing for d a multiple of 16 and N a multiple of 128 (the
+// coordinates 16-byte aligned): a block takes 128 consecutive positions of
+// one work item; each thread finds its point, reads the point's d bytes with
+// 16-byte loads into a shared tile [dimension][position] and sums ||p||^2;
+// the block then writes the tile's d rows of 128 positions with 16-byte
+// stores, instead of one byte per thread and dimension.
+__global__ void __launch_bounds__(128) pack_tile_kernel(uint32_t N, uint32_t d, const GatherItem* __restrict__ items,
+                                                        const GatherQuery* __restrict__ qs,
+                                                        const uint64_t* __restrict__ seg,
+                                                        const uint32_t* __restrict__ probes, uint32_t P,
+                                                        const uint64_t* __restrict__ offsets,
+                                                        const uint32_t* __restrict__ members,
+                                                        const uint8_t* __restrict__ coords, uint8_t* __restrict__ gco,
+                                                        uint32_t* __restrict__ gnorm, uint32_t* __restrict__ ids) {
+  __shared__ __align__(16) uint8_t tile[kMaxD][128];
+  const uint32_t per_item = N / 128;
+  const uint64_t w = blockIdx.x / per_item;
+  const uint32_t x0 = (uint32_t)(blockIdx.x % per_item) * 128;
+  const uint32_t x = x0 + threadIdx.x;
+  const GatherItem it = items[w];
+  const uint64_t pos = (uint64_t)it.kb * N + x;
+  const GatherQuery Q = qs[it.b];
+  uint32_t nrm = 0;
+  if (pos < Q.n) {
+    const uint64_t* sg = seg + (uint64_t)it.b * (P + 1);
+    uint32_t lo = 0, hi = P;  // invariant: sg[lo] <= pos < sg[hi]
+    while (hi - lo > 1) {
+      uint32_t mid = (lo + hi) >> 1;
+      if (sg[mid] <= pos) lo = mid; else hi = mid;
+    }
+    const uint32_t c = probes[(uint64_t)it.b * P + lo];
+    const uint32_t pt = members[offsets[c] + (pos - sg[lo])];
+    const uint4* src = reinterpret_cast<const uint4*>(coords + (uint64_t)pt * d);
+    for (uint32_t k = 0; k < d / 16; ++k) {
+      const uint4 v = __ldg(src + k);
+      const uint32_t vw[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+      for (int m = 0; m < 16; ++m) {
+        const uint32_t b = (vw[m >> 2] >> (8 * (m & 3))) & 255u;
+        nrm += b * b;
+        tile[16 * k + m][threadIdx.x] = (uint8_t)b;
+      }
+    }
+    if (ids) ids[Q.pos_off + pos] = pt;
+  } else {
+    for (uint32_t i = 0; i < d; ++i) tile[i][threadIdx.x] = 0;
+  }
+  gnorm[w * N + x] = nrm;
+  __syncthreads();
+  uint8_t* dst = gco + w * (uint64_t)d * N + x0;
+  for (uint32_t e = threadIdx.x; e < d * 8; e += blockDim.x) {
+    const uint32_t i = e >> 3, c16 = e & 7;
+    *reinterpret_cast<uint4*>(dst + (uint64_t)i * N + 16 * c16) =
+        *reinterpret_cast<const uint4*>(&tile[i][16 * c16]);
+  }
+}
+
 // c * p mod q for c, p < q < 2^60 with p_mont = p 2^64 mod q: one Montgomery
 // reduction of the 120-bit product gives a value below q + 2^56 < 2q.
 __device__ __forceinline__ uint64_t mont_mul(uint64_t c, uint64_t p_mont, uint64_t q, uint64_t qn) {
@@ -485,7 +542,13 @@ cudaError_t gather_kernels(const PrimeSet& P, uint32_t d, const sanns_clusters* 
   if (e != cudaSuccess) return e;
   const GatherItem* d_items = reinterpret_cast<const GatherItem*>(tables + o_items);
   const GatherQuery* d_qs = reinterpret_cast<const GatherQuery*>(tables + o_qs);
-  {
+  if (d % 16 == 0 && N % 128 == 0 && (reinterpret_cast<uintptr_t>(cl->d_coords) & 15) == 0) {
+    pack_tile_kernel<<<(unsigned)(W * (N / 128)), 128, 0, st>>>(
+        N, d, d_items, d_qs, reinterpret_cast<const uint64_t*>(tables + o_seg),
+        reinterpret_cast<const uint32_t*>(tables + o_pr), Pr, cl->d_offsets, cl->d_members,
+        cl->d_coords, scratch + o_gco, reinterpret_cast<uint32_t*>(scratch + o_norm), ids);
+    e = cudaGetLastError();
+  } else {
     const uint64_t threads = W * N;
     pack_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(
         N, d, W, d_items, d_qs, reinterpret_cast<const uint64_t*>(tables + o_seg),
