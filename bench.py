@@ -238,8 +238,14 @@ def run_gpu(args) -> None:
     srv = torch.empty((1, n), dtype=torch.uint32, device="cuda")
     stream = torch.cuda.current_stream()
     mask_seed = W["seed"] + 5
-    variant, variant_ms = S.sanns_autotune_mac(ctx, db, ct_all[0:1], ct_out, reps=3)
     variant_names = S.sanns_mac_variants()
+    if args.mac_variant:
+        # a fixed launch variant (profiler runs, whose per-launch overhead
+        # would decide the autotuner's pick)
+        variant, variant_ms = variant_names.index(args.mac_variant), []
+        S.sanns_set_mac_variant(ctx, variant)
+    else:
+        variant, variant_ms = S.sanns_autotune_mac(ctx, db, ct_all[0:1], ct_out, reps=3)
 
     # Steps are pipelined over two streams: query s's MAC (HBM-bound) runs on
     # stream A while query s-1's INTT + mask (integer-bound) runs on stream B,
@@ -279,7 +285,7 @@ def run_gpu(args) -> None:
 
     # the SM cap, tuned on short pipelined runs (0 = all SMs)
     sms_ms = {}
-    for cap in (0, 144, 140, 136, 132, 128, 124, 120):
+    for cap in ((args.mac_sms,) if args.mac_sms is not None else (0, 144, 140, 136, 132, 128, 124, 120)):
         S.sanns_set_mac_sms(ctx, cap)
         time_steps(20)
         sms_ms[cap] = time_steps(100)
@@ -1419,6 +1425,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="sanns", choices=["sanns", "reference"])
     ap.add_argument("--quick-cpu", action="store_true", help="smaller CPU baseline sample")
+    ap.add_argument("--mac-variant", default=None, help="fixed MAC launch variant instead of the autotuner's")
+    ap.add_argument("--mac-sms", type=int, default=None, help="fixed MAC SM cap instead of the tuned one")
     ap.add_argument("--shard", action="store_true",
                     help="split the linear-scan database across the ranks by block ranges "
                          "(broadcast + gather) instead of running replicas")
