@@ -562,11 +562,14 @@ def run_gpu(args) -> None:
         S.sanns_expand_query(ctx, c0_host[0:1].cuda(), W["seed"] + 4, qids[0:1]), ct_all[0:1]))
     S.sanns_set_response_primes(ctx, 1)
     e2e_sw = {}
+    issue_sw = {}
     for seeded in (False, True):
         run_e2e(4, seeded=seeded, switched=True)
         torch.cuda.synchronize()
         t_start = time.perf_counter()
-        run_e2e(e2e_steps, seeded=seeded, switched=True).synchronize()
+        ev_last = run_e2e(e2e_steps, seeded=seeded, switched=True)
+        issue_sw[seeded] = (time.perf_counter() - t_start) * 1e3 / e2e_steps
+        ev_last.synchronize()
         torch.cuda.synchronize()
         e2e_sw[seeded] = (time.perf_counter() - t_start) * 1e3 / e2e_steps
     # the last step's downloaded switched response decrypts to shares that
@@ -579,6 +582,18 @@ def run_gpu(args) -> None:
     switched_exact = bool(torch.equal((cli_sw[0].long() + srv_host[u_last][0].cuda().long()) % t_mod,
                                       brute_sw.long()))
     del cli_sw, brute_sw, pts_all
+    # the host link alone for the switched, seeded pattern: c0 up, the q_0 rows
+    # (a pitched copy) and the shares down
+    torch.cuda.synchronize()
+    t_l = time.perf_counter()
+    for r in range(20):
+        with torch.cuda.stream(s_up):
+            c0_dev[r % 2].copy_(c0_host[r % nh:r % nh + 1], non_blocking=True)
+        with torch.cuda.stream(s_dn):
+            S.sanns_copy_responses(ctx, out_dev[r % 2], sw_host[r % 2], stream=s_dn)
+            srv_host[r % 2].copy_(srv_dev[r % 2], non_blocking=True)
+    torch.cuda.synchronize()
+    link_sw_ms = (time.perf_counter() - t_l) * 1e3 / 20
     S.sanns_set_response_primes(ctx, L)
     S.sanns_set_mac_sms(ctx, 0)
     # the host link alone: the same uploads and downloads, both directions at
@@ -676,7 +691,9 @@ def run_gpu(args) -> None:
                 "seeded_queries": {"value": world * n / (e2e_sw[True] * 1e-3), "unit": UNIT,
                                    "h2d_bytes_per_step": d * L * N * 8,
                                    "d2h_bytes_per_step": K * 2 * N * 8 + n * 4,
-                                   "ms_per_step": e2e_sw[True]},
+                                   "ms_per_step": e2e_sw[True],
+                                   "link_only_ms_per_step": link_sw_ms,
+                                   "host_issue_ms_per_step": issue_sw[True]},
                 "what": "as e2e, but the server switches each response down to q_0 "
                         "(sanns_set_response_primes; the client decrypts modulo q_0) and "
                         "downloads a third of the bytes: an option beyond the paper, whose "
