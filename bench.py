@@ -165,9 +165,9 @@ def _ntt_report(polys: int, N: int, ms: float, what: str) -> dict:
 
 
 def run_small_section() -> dict:
-    """Configuration 1: n = 4096, d = 32 uniform uint8, N = 4096, two 54-bit
-    primes, one query; latency-bound, so p50/p99 of the distance step, and
-    the exact top-10 checked against brute force."""
+    """The small linear scan: n = 4096, d = 32 uniform uint8, N = 4096, two
+    54-bit primes, one query; latency-bound, so p50/p99 of the distance step,
+    and the exact top-10 checked against brute force."""
     import numpy as np
     import torch
 
@@ -200,7 +200,7 @@ def run_small_section() -> dict:
     dist_k, pos_k = S.sanns_topk(ctx, cli, srv, 10)
     brute = np.sum((coords[perm].astype(np.int64) - q[0].astype(np.int64)) ** 2, axis=1)
     exact = sorted(brute.tolist())[:10] == dist_k.cpu().numpy()[0].tolist()
-    return {"workload": "configuration 1: n=4,096 d=32 uniform uint8; BFV N=4096, two 54-bit primes; "
+    return {"workload": "small linear scan: n=4,096 d=32 uniform uint8; BFV N=4096, two 54-bit primes; "
                         "one query per step",
             "latency_ms": {"p50": lat[len(lat) // 2], "p99": lat[int(0.99 * (len(lat) - 1))]},
             "qp_per_s": n / (lat[len(lat) // 2] * 1e-3), "steps": reps,
