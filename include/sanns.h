@@ -137,8 +137,9 @@ int sanns_db_export(const sanns_db *db, uint64_t k0, uint64_t k1, uint64_t *pt_a
  * ([K][L][d][N], NTT form, canonical residues) and norms_any ([K N] uint32)
  * in `any` memory, for a server that encodes once (Pi_ls step 1, offline)
  * and loads the result later.  The context's current encoding setting is
- * recorded with it; position base 0.  SANNS_EINVAL if a residue is not below
- * its prime (nothing is created).  Synchronous. */
+ * recorded with it; position base 0.  The norms are stored reduced mod t
+ * (the responses only ever use them mod t).  SANNS_EINVAL if a residue is
+ * not below its prime (nothing is created).  Synchronous. */
 int sanns_db_import(sanns_ctx *ctx, uint64_t n, const uint64_t *pt_any, const uint32_t *norms_any,
                     sanns_db **out, void *stream);
 

@@ -66,8 +66,9 @@ class _CParams(C.Structure):
 class Oracle:
     """One BFV parameter set with its twiddle tables, for the C loops."""
 
-    def __init__(self, N: int, L: int, prime_bits: int, t_rule: int, d: int):
-        self.P: Params = make_params(N, L, prime_bits, t_rule, d)
+    def __init__(self, N: int, L: int, prime_bits: int, t_rule: int, d: int, b_c: int = 8):
+        self.P: Params = make_params(N, L, prime_bits, t_rule, d, b_c)
+        self.b_c = b_c
         P = self.P
         self.N, self.L, self.d, self.t = N, L, d, P.t
         self.q = np.array(P.q, dtype=np.uint64)
@@ -406,7 +407,7 @@ class Oracle:
     def prime0(self) -> "Oracle":
         """The same parameters with the first prime alone: the scheme that
         decrypts modulus-switched responses (same q_0, N and t)."""
-        O1 = Oracle(self.N, 1, self.P.prime_bits, self.P.t_rule, self.d)
+        O1 = Oracle(self.N, 1, self.P.prime_bits, self.P.t_rule, self.d, self.b_c)
         assert O1.P.q[0] == self.P.q[0] and O1.t == self.t
         return O1
 

@@ -111,16 +111,16 @@ class Params:
         return [self.delta % qj for qj in self.q]
 
 
-def make_params(N: int, L: int, prime_bits: int, t_rule: int, d: int) -> Params:
+def make_params(N: int, L: int, prime_bits: int, t_rule: int, d: int, b_c: int = 8) -> Params:
     """The BFV parameters of Sec. 7.1 ("Parameters": N, a three-word q, t) as
     exact integers: the L largest primes below 2^prime_bits that are 1 mod 2N,
-    the smallest primitive 2N-th root psi of each, t by its rule, and
-    Delta = floor(Q / t)."""
+    the smallest primitive 2N-th root psi of each, t by its rule (b_c bits
+    per coordinate for the paper's rule), and Delta = floor(Q / t)."""
     if N & (N - 1) or N < 2:
         raise ValueError("N must be a power of two")
     q = ntt_primes(N, L, prime_bits)
     psi = [min_primitive_root_2n(qj, N) for qj in q]
-    t = plain_modulus(N, t_rule, d)
+    t = plain_modulus(N, t_rule, d, b_c)
     Q = reduce(lambda a, b: a * b, q, 1)
     return Params(N=N, L=L, prime_bits=prime_bits, t_rule=t_rule, d=d,
                   q=q, psi=psi, t=t, Q=Q, delta=Q // t)

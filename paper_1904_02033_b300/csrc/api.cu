@@ -96,6 +96,10 @@ int sanns_ctx_create(const sanns_params* p, sanns_ctx** out) {
   while ((1u << logN) < N) ++logN;
   c->P.logN = logN;
   fill_prime_constants(c->P, q, t, p->L);
+  // every norm encode_db stores, d 255^2 at most, is below t: the mask
+  // epilogues then reduce ||p||^2 + r mod t with one conditional subtraction
+  // (imported norms are reduced mod t on import)
+  c->P.norms_below_t = (uint64_t)p->d * 255u * 255u < t ? 1u : 0u;
   for (uint32_t j = 0; j < p->L; ++j) c->psi[j] = psi[j];
   cudaError_t e = cudaGetDevice(&c->device);
   if (e != cudaSuccess) { delete c; return cuda_fail(e, "cudaGetDevice"); }
@@ -354,6 +358,7 @@ int sanns_db_import(sanns_ctx* ctx, uint64_t n, const uint64_t* pt, const uint32
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(db->d_norms, norms, sizeof(uint32_t) * K * N, cudaMemcpyDefault, st);
   if (e == cudaSuccess) e = launch_import_pt(ctx->P, db->d_pt, count, d, d_bad, st);
+  if (e == cudaSuccess) e = launch_norms_mod_t(ctx->P, db->d_norms, K * N, st);
   int bad = 0;
   if (e == cudaSuccess) e = cudaMemcpyAsync(&bad, d_bad, sizeof(int), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);

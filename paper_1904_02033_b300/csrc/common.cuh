@@ -46,7 +46,8 @@ struct ModSwitchConsts {
 
 // Per-prime constants, passed to kernels by value.
 struct PrimeSet {
-  uint32_t N, logN, L, pad;
+  uint32_t N, logN, L;
+  uint32_t norms_below_t;           // every stored ||p||^2 is below t (d 255^2 < t)
   uint64_t t;                       // plaintext modulus
   uint64_t t_barrett;               // floor(2^64 / t)
   uint64_t two64_mod_t;             // 2^64 mod t
@@ -129,6 +130,13 @@ __device__ __forceinline__ uint64_t reduce_below_16q(uint64_t x, uint64_t q) {
 __device__ __forceinline__ uint64_t mod_t64(uint64_t x, uint64_t t, uint64_t t_barrett) {
   uint64_t qt = __umul64hi(x, t_barrett);
   return csub(x - qt * t, t);
+}
+
+// (||p||^2 + r) mod t for a stored norm and a mask value r < t: one
+// conditional subtraction when the norms are below t, else Barrett.
+__device__ __forceinline__ uint64_t norm_plus_mask_mod_t(const PrimeSet& P, uint32_t norm, uint64_t r) {
+  const uint64_t x = (uint64_t)norm + r;
+  return P.norms_below_t ? csub(x, P.t) : mod_t64(x, P.t, P.t_barrett);
 }
 
 // (hi 2^64 + lo) mod t, t < 2^32.

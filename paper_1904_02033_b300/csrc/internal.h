@@ -108,6 +108,8 @@ void fill_twiddles(uint32_t N, uint64_t q, uint64_t psi, uint64_t* tw, uint64_t*
                    uint64_t* itws);
 uint64_t shoup_of(uint64_t w, uint64_t q);
 
+cudaError_t launch_norms_mod_t(const PrimeSet& P, uint32_t* norms, uint64_t count, cudaStream_t st);
+
 // modulus switching of the responses down to q_0 (modswitch.cu)
 void make_mod_switch_consts(const PrimeSet& P, ModSwitchConsts* C);
 cudaError_t launch_mod_switch(const PrimeSet& P, const ModSwitchConsts& C, uint64_t* buf, uint64_t tuples,

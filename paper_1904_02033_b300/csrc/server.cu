@@ -269,7 +269,7 @@ __global__ void __launch_bounds__(256, 3) intt_mask_kernel(PrimeSet P, uint64_t*
         const uint64_t pos = kb * N + x0 + k * t16;
         const uint32_t sv = sh[pos];
         const uint64_t r = sv == 0 ? 0 : t - sv;
-        const uint64_t val = mod_t64((uint64_t)norms[pos] + r, t, P.t_barrett);
+        const uint64_t val = norm_plus_mask_mod_t(P, norms[pos], r);
         v[k] = add_mod(v[k], mul_shoup(val, dl, dls, q), q);
       }
     } else if (c == 0) {
@@ -287,7 +287,7 @@ __global__ void __launch_bounds__(256, 3) intt_mask_kernel(PrimeSet P, uint64_t*
         } else {
           r = mask_draw(P, pos0g + pos, mask_seed, qids[b]);
         }
-        const uint64_t val = mod_t64((uint64_t)norms[pos] + r, t, P.t_barrett);
+        const uint64_t val = norm_plus_mask_mod_t(P, norms[pos], r);
         g[x] = add_mod(sa[SP(x)], mul_shoup(val, dl, dls, q), q);
       }
       continue;
@@ -361,7 +361,7 @@ __global__ void __launch_bounds__(256, 3) intt_mask_short_kernel(PrimeSet P, uin
         const uint32_t nvv[4] = {nv[z].x, nv[z].y, nv[z].z, nv[z].w};
 #pragma unroll
         for (int v = 0; v < 4; ++v) {
-          const uint64_t val = mod_t64((uint64_t)nvv[v] + r[v], t, P.t_barrett);
+          const uint64_t val = norm_plus_mask_mod_t(P, nvv[v], r[v]);
           const uint32_t x = 4 * u + v;
           sa[SP(x)] = add_mod(sa[SP(x)], mul_shoup(val, dl, dls, q), q);
         }
@@ -413,7 +413,7 @@ __global__ void __launch_bounds__(256, 3) mask_ntt_kernel(PrimeSet P, uint64_t* 
       }
 #pragma unroll
       for (int v = 0; v < 4; ++v) {
-        const uint64_t m = mod_t64((uint64_t)norms[p4 + v] + r[v], t, P.t_barrett);
+        const uint64_t m = norm_plus_mask_mod_t(P, norms[p4 + v], r[v]);
         val[v] = mul_shoup(m, P.delta[j], P.delta_shoup[j], q);
       }
     }
@@ -491,7 +491,7 @@ __global__ void __launch_bounds__(256, 3) mask_ntt_fused_kernel(PrimeSet P, uint
     uint64_t r;
     if (pos < n) r = sv == 0 ? 0 : t - sv;
     else r = mask_draw(P, pos0g + pos, mask_seed, qid);
-    const uint64_t m = mod_t64((uint64_t)nv + r, t, P.t_barrett);
+    const uint64_t m = norm_plus_mask_mod_t(P, nv, r);
     return mul_shoup(m, dl, dls, q);
   };
   const uint32_t* nk = norms + k * N;
@@ -627,7 +627,20 @@ __global__ void __launch_bounds__(256, 3) mask_ntt_fused_kernel(PrimeSet P, uint
   }
 }
 
+// Imported norms reduced mod t in place, so that every stored norm is below t
+// (the mask epilogues rely on it when the context's norms_below_t is set).
+__global__ void norms_mod_t_kernel(PrimeSet P, uint32_t* __restrict__ norms, uint64_t count) {
+  const uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+  if (i < count) norms[i] = (uint32_t)mod_t64(norms[i], P.t, P.t_barrett);
+}
+
 }  // namespace
+
+cudaError_t launch_norms_mod_t(const PrimeSet& P, uint32_t* norms, uint64_t count, cudaStream_t st) {
+  if (count == 0) return cudaSuccess;
+  norms_mod_t_kernel<<<(unsigned)((count + 255) / 256), 256, 0, st>>>(P, norms, count);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_ntt(const PrimeSet& P, uint64_t* data, uint64_t count, bool inverse,
                        cudaStream_t st) {

@@ -261,6 +261,12 @@ def test_db_import_of_the_oracle_encoding_equals_encode_db():
     assert torch.equal(a_out, b_out) and torch.equal(a_srv, b_srv)
     ept, enorms = S.sanns_db_export(db_imp)
     assert np.array_equal(np_(ept), pt) and np.array_equal(np_(enorms), norms)
+    # norms are only ever used mod t: imported ones at or above t are stored
+    # reduced and give the same responses
+    db_big = S.sanns_db_import(ctx, n, cu(pt), cu(norms + np.uint32(O.t)))
+    c_out, c_srv = S.sanns_distances(ctx, db_big, ct, 76, qids)
+    assert torch.equal(c_out, b_out) and torch.equal(c_srv, b_srv)
+    assert np.array_equal(np_(S.sanns_db_export(db_big)[1]), norms)
     bad = pt.copy()
     bad[1, 1, 2, 7] = O.q[1]
     with pytest.raises(S.SannsError) as e:
@@ -308,3 +314,38 @@ def test_mac_sm_cap_and_two_stream_pipeline_keep_results():
         for b in range(B):
             assert torch.equal(got[b][0], want[b][0]) and torch.equal(got[b][1], want[b][1]), (cap, b)
     S.sanns_set_mac_sms(ctx, 0)
+
+
+@pytest.mark.parametrize("batched", [False, True])
+def test_norms_above_t_with_few_bits_per_coordinate(batched):
+    """The paper's t = 2^(2 b_c + ceil(log2 d)) with b_c = 6 bits per
+    coordinate is below the norms of 8-bit coordinates, so ||p||^2 + r is
+    reduced mod t the general way: responses and shares still equal the
+    oracle's (same b_c), and the shares reconstruct the distances mod t."""
+    cfg = (256, 2, 40, 1, 5)
+    n, B = 700, 2
+    ctx = S.sanns_ctx_create(*cfg, b_c=6)
+    O = Oracle(*cfg, b_c=6)
+    assert O.t == 2 ** 15 < 5 * 255 ** 2
+    coords = inputs.uniform_coords(n, cfg[4], 81)
+    coords[:9] = 255
+    perm = inputs.permutation(n, 82)
+    q = inputs.uniform_coords(B, cfg[4], 83)
+    qids = np.array([7, 8], dtype=np.uint64)
+    sk = S.sanns_keygen(ctx, 84)
+    db = S.sanns_encode_db(ctx, cu(coords), cu(perm))
+    ct = S.sanns_encrypt_query(ctx, sk, cu(q), 85, cu(qids))
+    if batched:
+        S.sanns_db_prepare_batched(ctx, db)
+        out, srv = S.sanns_distances_batched(ctx, db, ct, 86, cu(qids))
+    else:
+        out, srv = S.sanns_distances(ctx, db, ct, 86, cu(qids))
+    cli = S.sanns_decrypt_shares(ctx, sk, out, n, cu(q))
+    s_, _ = O.keygen(84)
+    for b in range(B):
+        want_out, want_srv = O.distances(np_(ct)[b], coords, perm, 86, int(qids[b]))
+        assert np.array_equal(np_(out)[b], want_out)
+        assert np.array_equal(np_(srv)[b], want_srv)
+        assert np.array_equal(np_(cli)[b], O.decrypt_shares(want_out, s_, q[b], n))
+        brute = np.sum((coords[perm].astype(np.int64) - q[b].astype(np.int64)) ** 2, axis=1)
+        assert np.array_equal((np_(cli)[b].astype(np.int64) + np_(srv)[b]) % O.t, brute % O.t)
