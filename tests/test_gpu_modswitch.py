@@ -105,6 +105,11 @@ def test_copies_and_noalloc_decryption_agree():
     cli2 = S.sanns_decrypt_shares_noalloc(ctx, sk, sw, 500, q=cu(q))
     torch.cuda.synchronize()
     assert torch.equal(cli2.cpu(), cli.cpu())
+    # at every prime the copy is the whole response buffer
+    S.sanns_set_response_primes(ctx, 3)
+    full = S.sanns_copy_responses(ctx, out)
+    torch.cuda.synchronize()
+    assert tuple(full.shape) == tuple(out.shape) and torch.equal(full, out)
 
 
 def test_switching_rules():
