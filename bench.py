@@ -196,6 +196,29 @@ def run_small_section() -> dict:
         b.record(st)
     torch.cuda.synchronize()
     lat = sorted(a.elapsed_time(b) for a, b in ev)
+    # the same step captured once into a CUDA graph and replayed: the launch
+    # gaps of the eager calls above are host time, not the step's own
+    gs = torch.cuda.Stream()
+    gs.wait_stream(st)
+    with torch.cuda.stream(gs):
+        S.sanns_distances(ctx, db, ct, 0, qids, out, srv)
+    st.wait_stream(gs)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        S.sanns_distances(ctx, db, ct, 0, qids, out, srv)
+    torch.cuda.synchronize()
+    for _ in range(10):
+        g.replay()
+    torch.cuda.synchronize()
+    gev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+    cur = torch.cuda.current_stream()
+    for a, b in gev:
+        a.record(cur)
+        g.replay()
+        b.record(cur)
+    torch.cuda.synchronize()
+    glat = sorted(a.elapsed_time(b) for a, b in gev)
     cli = S.sanns_decrypt_shares(ctx, sk, out, n, torch.from_numpy(q).cuda())
     dist_k, pos_k = S.sanns_topk(ctx, cli, srv, 10)
     brute = np.sum((coords[perm].astype(np.int64) - q[0].astype(np.int64)) ** 2, axis=1)
@@ -203,6 +226,8 @@ def run_small_section() -> dict:
     return {"workload": "small linear scan: n=4,096 d=32 uniform uint8; BFV N=4096, two 54-bit primes; "
                         "one query per step",
             "latency_ms": {"p50": lat[len(lat) // 2], "p99": lat[int(0.99 * (len(lat) - 1))]},
+            "latency_graph_ms": {"p50": glat[len(glat) // 2], "p99": glat[int(0.99 * (len(glat) - 1))],
+                                 "what": "one step captured into a CUDA graph, replayed"},
             "qp_per_s": n / (lat[len(lat) // 2] * 1e-3), "steps": reps,
             "exact_top10_equals_brute_force": bool(exact)}
 
