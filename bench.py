@@ -1001,7 +1001,9 @@ def run_batched_section(quick: bool = False, n_override: int | None = None,
                                "128 blocks x 256 query rows per SM, TMA-fed, clusters of 4 sharing the query tile",
                                "128 blocks x 256 query rows per SM, TMA-fed, four slots per CTA, 32-byte stores",
                                "128 blocks x 256 query rows per SM, TMA-fed, four slots per CTA, 32-byte stores, "
-                               "clusters of 2 sharing the query tile"][tile],
+                               "clusters of 2 sharing the query tile",
+                               "256 blocks x 256 query rows per SM pair, TMA-fed, four slots per CTA pair, "
+                               "32-byte stores"][tile],
                       "l2_prefetch_units": prefetch,
                       "ms_per_config": {f"tile{t}_prefetch{p}": round(m, 3)
                                         for (t, p), m in zip(S.BATCHED_CONFIGS, tune_ms)}},

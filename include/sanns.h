@@ -285,12 +285,15 @@ int sanns_distances_gather_prepared(sanns_ctx *ctx, const sanns_gather_batch *ba
 int sanns_mac_variants(void);
 const char *sanns_mac_variant_name(int variant);
 int sanns_set_mac_variant(sanns_ctx *ctx, int variant);
-/* SMs the MAC kernel's persistent grid spreads over (0, the default: all).
- * The MAC is bound by HBM bandwidth, which fewer SMs can still saturate; the
- * SMs left over run other work launched on other streams at the same time,
- * such as the previous query's INTT + mask (sanns_distances_finish), whose
- * integer arithmetic then overlaps the next query's database stream.
- * Results never depend on this value. */
+/* SMs the MAC kernels' persistent grids spread over (0, the default: all),
+ * for the per-query MAC and the batched tensor-core MAC alike (CTA pairs and
+ * clusters take the largest whole number of pairs or clusters within it).
+ * The per-query MAC is bound by HBM bandwidth, which fewer SMs can still
+ * saturate, and the batched MAC by the board's power limit; the SMs left over
+ * run other work launched on other streams at the same time, such as the
+ * previous query's or batch's INTT + mask (sanns_distances_finish), whose
+ * integer arithmetic then overlaps the next MAC.  Results never depend on
+ * this value. */
 int sanns_set_mac_sms(sanns_ctx *ctx, int sms);
 int sanns_autotune_mac(sanns_ctx *ctx, const sanns_db *db, const uint64_t *ct_in_dev, uint32_t B,
                        uint64_t *ct_out_dev, int reps, float *ms_out, void *stream);

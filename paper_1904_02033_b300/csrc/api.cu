@@ -464,6 +464,11 @@ int check_distance_args(sanns_ctx* ctx, const sanns_db* db, uint32_t B) {
 }
 }  // namespace
 
+// SMs the MAC kernels' persistent grids spread over (sanns_set_mac_sms)
+static int mac_grid_sms(const sanns_ctx* ctx) {
+  return ctx->mac_sms > 0 && ctx->mac_sms < ctx->sms ? ctx->mac_sms : ctx->sms;
+}
+
 int sanns_distances_mac(sanns_ctx* ctx, const sanns_db* db, const uint64_t* ct_in, uint32_t B,
                         uint64_t* ct_out, void* stream) {
   int rc = check_distance_args(ctx, db, B);
@@ -471,7 +476,7 @@ int sanns_distances_mac(sanns_ctx* ctx, const sanns_db* db, const uint64_t* ct_i
   if (B == 0) return SANNS_OK;
   if (!ct_in || !ct_out) return fail(SANNS_EINVAL, "NULL buffer");
   if (!aligned16(ct_in) || !aligned16(ct_out)) return fail(SANNS_EINVAL, "ct buffers must be 16-byte aligned");
-  const int sms = ctx->mac_sms > 0 && ctx->mac_sms < ctx->sms ? ctx->mac_sms : ctx->sms;
+  const int sms = mac_grid_sms(ctx);
   SANNS_CUDA(launch_mac(ctx->P, ct_in, db->d_pt, B, ctx->params.d, db->K, ct_out, sms,
                         ctx->mac_variant, as_stream(stream)));
   return SANNS_OK;
@@ -915,7 +920,7 @@ int sanns_distances_batched_mac(sanns_ctx* ctx, const sanns_db* db, const uint64
   if (!ct_in || !ct_out) return fail(SANNS_EINVAL, "NULL buffer");
   if (B > 4096) return fail(SANNS_EINVAL, "B must be <= 4096");
   SANNS_CUDA(launch_batched_mac(ctx->P, db->limb_map, db->d_plimb, ct_in, B, ctx->params.d, db->K, ct_out, ctx->d_err,
-                                ctx->sms, ctx->batched_tune, as_stream(stream)));
+                                mac_grid_sms(ctx), ctx->batched_tune, as_stream(stream)));
   return SANNS_OK;
 }
 
@@ -979,7 +984,7 @@ int sanns_autotune_batched(sanns_ctx* ctx, const sanns_db* db, const uint64_t* c
     ctx->batched_tune[4] = (uint32_t)(cfg & 1);    // L2 prefetch distance
     auto launch = [&]() {
       return launch_batched_mac(ctx->P, db->limb_map, db->d_plimb, ct_in, B, ctx->params.d, db->K, ct_out,
-                                ctx->d_err, ctx->sms, ctx->batched_tune, st);
+                                ctx->d_err, mac_grid_sms(ctx), ctx->batched_tune, st);
     };
     cudaError_t e = launch();
     if (e == cudaSuccess) e = cudaEventRecord(e0, st);

@@ -1827,6 +1827,10 @@ cudaError_t launch_batched_mac(const PrimeSet& P, const void* map, const uint16_
   {
     std::lock_guard<std::mutex> lock(setup_mu);
     if (!configured_dev[dev]) {
+      // residency on the whole device (the cap below applies per launch)
+      int dev_sms = 0;
+      e = cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, dev);
+      if (e != cudaSuccess) return e;
       const void* cluster_kernels[2] = {(const void*)batched_mac_kernel<true, 2>,
                                         (const void*)batched_mac_kernel<true, 4>};
       for (int c = 0; c < 2 && e == cudaSuccess; ++c) {
@@ -1838,7 +1842,7 @@ cudaError_t launch_batched_mac(const PrimeSet& P, const void* map, const uint16_
         at[0].val.clusterDim.x = 2u << c;
         at[0].val.clusterDim.y = 1;
         at[0].val.clusterDim.z = 1;
-        cfg.gridDim = dim3((unsigned)((sms > 0 ? sms : 148) / (2 << c) * (2 << c)));
+        cfg.gridDim = dim3((unsigned)(dev_sms / (2 << c) * (2 << c)));
         cfg.blockDim = dim3(kThreads);
         cfg.dynamicSmemBytes = kSmem1;
         cfg.attrs = at;
@@ -1870,7 +1874,7 @@ cudaError_t launch_batched_mac(const PrimeSet& P, const void* map, const uint16_
         at[0].val.clusterDim.x = 2;
         at[0].val.clusterDim.y = 1;
         at[0].val.clusterDim.z = 1;
-        cfg.gridDim = dim3((unsigned)((sms > 0 ? sms : 148) / 2 * 2));
+        cfg.gridDim = dim3((unsigned)(dev_sms / 2 * 2));
         cfg.blockDim = dim3(quad::kThreads);
         cfg.dynamicSmemBytes = quad::kSmem;
         cfg.attrs = at;
@@ -1879,7 +1883,7 @@ cudaError_t launch_batched_mac(const PrimeSet& P, const void* map, const uint16_
       }
       if (e != cudaSuccess) return e;
       cudaLaunchConfig_t cfg = {};
-      cfg.gridDim = dim3(2 * (unsigned)(sms > 0 ? sms / 2 : 74));
+      cfg.gridDim = dim3(2 * (unsigned)(dev_sms / 2));
       cfg.blockDim = dim3(pair::kThreads);
       cfg.dynamicSmemBytes = pair::kSmem;
       e = cudaOccupancyMaxActiveClusters(&pairs_resident_dev[dev], batched_mac_pair_kernel<false>, &cfg);
@@ -1898,6 +1902,13 @@ cudaError_t launch_batched_mac(const PrimeSet& P, const void* map, const uint16_
   }
   if ((use_pair || pairq) && pairs_resident < 1) return cudaErrorInvalidConfiguration;
   if (CL > 1 && clusters_resident < 1) return cudaErrorInvalidConfiguration;
+  // an SM cap (sms > 0) bounds the persistent grid; at least one CTA pair or
+  // cluster still runs
+  if (sms > 0) {
+    const int cap2 = sms / 2 > 0 ? sms / 2 : 1, capc = sms / CL > 0 ? sms / CL : 1;
+    if (pairs_resident > cap2) pairs_resident = cap2;
+    if (CL > 1 && clusters_resident > capc) clusters_resident = capc;
+  }
   PFN_cuTensorMapEncodeTiled_v12000 enc = nullptr;
   e = get_encode(&enc);
   if (e != cudaSuccess) return e;

@@ -94,6 +94,30 @@ def test_many_slot_ranges_equal_one(tile):
     assert torch.equal(acc_1.cpu(), acc_plain.cpu())
 
 
+@pytest.mark.parametrize("tile", TILES, ids=TILE_IDS)
+def test_sm_cap_keeps_batched_results(tile):
+    """The MAC SM cap bounds the tensor-core path's persistent grid too (one
+    CTA, pair or cluster at the smallest caps, an odd cap for the clusters of
+    2 and 4); the responses equal the per-query path's at every cap."""
+    cfg = (256, 2, 60, 0, 24)
+    n, B = 256 * 512 - 7, 12
+    ctx = S.sanns_ctx_create(*cfg)
+    rnd = np.random.default_rng(41)
+    coords = rnd.integers(0, 256, size=(n, cfg[4]), dtype=np.uint8)
+    q = rnd.integers(0, 256, size=(B, cfg[4]), dtype=np.uint8)
+    sk = S.sanns_keygen(ctx, 42)
+    db = S.sanns_encode_db(ctx, cu(coords), cu(inputs.permutation(n, 43)))
+    S.sanns_db_prepare_batched(ctx, db)
+    ct_in = S.sanns_encrypt_query(ctx, sk, cu(q), 44, cu(np.arange(B, dtype=np.uint64)))
+    acc_plain = S.sanns_distances_mac(ctx, db, ct_in).cpu()
+    S.sanns_batched_tune(ctx, tile=tile)
+    for cap in (1, 2, 7, 100, 0):
+        S.sanns_set_mac_sms(ctx, cap)
+        acc_b = S.sanns_distances_batched_mac(ctx, db, ct_in)
+        S.sanns_device_status(ctx)
+        assert torch.equal(acc_b.cpu(), acc_plain), cap
+
+
 def test_batched_needs_prepare_and_small_d():
     ctx = S.sanns_ctx_create(256, 2, 40, 0, 200)
     db = S.sanns_encode_db(ctx, cu(inputs.uniform_coords(300, 200, 1)))
