@@ -6,9 +6,12 @@ encrypted queries.  Requests that arrive while other batches are on the GPU
 wait until an execution slot and device memory free up; then every waiting
 request of one database (up to `max_batch`, FIFO) is admitted as one batch
 and launched on its own stream, so batches overlap on the device.  A batch
-of `batched_min` or more queries runs on the tensor-core path, smaller ones
-on the per-query path; both give bit-identical ciphertexts, so a request's
-result does not depend on what it was batched with.
+of `batched_min` or more queries may run on the tensor-core path, smaller
+ones run on the per-query path; once the executor is calibrated, a batch
+takes whichever path its measured service times say is faster for that
+database and batch size (the tensor path's per-call query expansion only
+pays back over enough blocks).  Both give bit-identical ciphertexts, so a
+request's result does not depend on what it was batched with.
 
 The scheduler is plain host logic over an `Executor` interface, which makes
 it testable without a GPU (tests drive it with a fake executor and a fake
@@ -170,12 +173,31 @@ def run_open_loop(sched: Scheduler, arrivals: list[Request], poll_sleep: float =
     return sched.stats
 
 
+def interpolate_ms(table: list[tuple[int, float]], n: int) -> float:
+    """Service time of a batch of n queries from measured (batch size, ms)
+    points: piecewise linear between them, linear beyond the ends."""
+    pts = sorted(table)
+    if len(pts) == 1:
+        b, ms = pts[0]
+        return ms * n / b
+    # the first segment whose right end reaches n, else the last one
+    i = next((i for i in range(1, len(pts)) if n <= pts[i][0]), len(pts) - 1)
+    (b0, m0), (b1, m1) = pts[i - 1], pts[i]
+    return m0 + (m1 - m0) * (n - b0) / (b1 - b0)
+
+
+def tensor_path_is_faster(per_query: list[tuple[int, float]], tensor: list[tuple[int, float]],
+                          n: int) -> bool:
+    """The path decision of a calibrated executor for a batch of n queries."""
+    return interpolate_ms(tensor, n) < interpolate_ms(per_query, n)
+
+
 class GpuExecutor:
     """Executor over libsanns: one CUDA stream and one output buffer set per
     slot; databases and their contexts stay resident."""
 
     def __init__(self, dbs: dict, slots: int, max_batch: int, batched_min: int = 8,
-                 mask_seed: int = 5):
+                 mask_seed: int = 5, keep: Callable[[Request], bool] | None = None):
         import torch
 
         from . import sanns as S
@@ -186,9 +208,53 @@ class GpuExecutor:
         self.streams = [torch.cuda.Stream() for _ in range(slots)]
         self.max_batch = max_batch
         self.tensor_batches = 0             # batches launched on the tensor-core path
+        # which finished requests keep their result tensors (all by default);
+        # a result is a view of its whole batch's buffers, so keeping one
+        # keeps the batch's responses in device memory
+        self.keep = keep
+        # db -> {"per_query": [(B, ms)], "tensor": [(B, ms)]} once calibrated
+        self.costs: dict = {}
 
     def uses_tensor_path(self, db: str, n_queries: int) -> bool:
-        return n_queries >= self.batched_min and getattr(self.dbs[db][1], "batched", False)
+        if n_queries < self.batched_min or not getattr(self.dbs[db][1], "batched", False):
+            return False
+        c = self.costs.get(db)
+        return c is None or tensor_path_is_faster(c["per_query"], c["tensor"], n_queries)
+
+    def calibrate(self, pools: dict, per_query_sizes=(1, 2, 4), tensor_sizes=(8, 32, 128),
+                  reps: int = 3) -> dict:
+        """Time both paths on every database at a few batch sizes (queries
+        taken cyclically from pools[db] = (ct, qids)), keep the tables and
+        route each later batch to the faster path.  Synchronous; call it
+        before serving."""
+        torch, S = self.torch, self.S
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        st = self.streams[0]
+        for name, (ctx, d) in self.dbs.items():
+            ct, qids = pools[name]
+            table = {"per_query": [], "tensor": []}
+            paths = [("per_query", per_query_sizes, S.sanns_distances)]
+            if getattr(d, "batched", False):
+                paths.append(("tensor", [b for b in tensor_sizes if b >= self.batched_min],
+                              S.sanns_distances_batched))
+            for key, sizes, fn in paths:
+                for b in sizes:
+                    idx = torch.arange(b, device=ct.device) % ct.shape[0]
+                    x, qx = ct.index_select(0, idx).contiguous(), qids.index_select(0, idx).contiguous()
+                    with torch.cuda.stream(st):
+                        out, srv = fn(ctx, d, x, self.mask_seed, qx, stream=st)
+                        ev0.record(st)
+                        for _ in range(reps):
+                            fn(ctx, d, x, self.mask_seed, qx, out, srv, stream=st)
+                        ev1.record(st)
+                    ev1.synchronize()
+                    table[key].append((b, ev0.elapsed_time(ev1) / reps))
+                    del out, srv
+            if not table["tensor"]:
+                del table["tensor"]
+                table["tensor"] = [(1, float("inf"))]
+            self.costs[name] = table
+        return self.costs
 
     def bytes_for(self, db: str, n_queries: int) -> int:
         """Device memory one batch holds while in flight: its responses and
@@ -223,4 +289,5 @@ class GpuExecutor:
     def finish(self, handle, reqs):
         _, out, srv = handle
         for i, r in enumerate(reqs):
-            r.result = (out[i:i + 1], srv[i:i + 1])
+            if self.keep is None or self.keep(r):
+                r.result = (out[i:i + 1], srv[i:i + 1])

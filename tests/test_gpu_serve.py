@@ -86,3 +86,38 @@ def test_memory_budget_binds_defers_then_admits_with_identical_results():
         torch.cuda.synchronize()
         assert torch.equal(r.result[0].cpu(), solo_out.cpu()), r.rid
         assert torch.equal(r.result[1].cpu(), solo_srv.cpu()), r.rid
+
+
+def test_calibration_tables_and_routing():
+    """Calibration times both paths on each database; the executor then routes
+    each batch size to the path its tables say is faster, and the results
+    stay identical to the query computed alone."""
+    ctx = S.sanns_ctx_create(256, 2, 40, 0, 8)
+    db = S.sanns_encode_db(ctx, torch.from_numpy(inputs.uniform_coords(3000, 8, 4)).cuda())
+    S.sanns_db_prepare_batched(ctx, db)
+    db.batched = True
+    sk = S.sanns_keygen(ctx, 2)
+    q = torch.from_numpy(inputs.uniform_coords(5, 8, 5)).cuda()
+    qids = torch.arange(5, dtype=torch.int64).to(torch.uint64).cuda()
+    ct = S.sanns_encrypt_query(ctx, sk, q, 9, qids)
+    ex = GpuExecutor({"A": (ctx, db)}, slots=2, max_batch=16, batched_min=4, mask_seed=5)
+    costs = ex.calibrate({"A": (ct, qids)}, per_query_sizes=(1, 2), tensor_sizes=(4, 16), reps=2)
+    t = costs["A"]
+    assert [b for b, _ in t["per_query"]] == [1, 2] and [b for b, _ in t["tensor"]] == [4, 16]
+    assert all(ms > 0 for _, ms in t["per_query"] + t["tensor"])
+    from paper_1904_02033_b300.serve import tensor_path_is_faster
+    for n in (1, 3, 4, 9, 16):
+        assert ex.uses_tensor_path("A", n) == (n >= 4 and tensor_path_is_faster(t["per_query"], t["tensor"], n))
+    # forced routes: the tensor path wherever allowed, then never
+    for tensor_ms in (0.0, float("inf")):
+        ex.costs["A"]["tensor"] = [(1, tensor_ms), (2, tensor_ms)]
+        before = ex.tensor_batches
+        reqs = [Request(rid=i, db="A", arrival=0.0, payload=(ct[i:i + 1], qids[i:i + 1])) for i in range(5)]
+        stats = run_open_loop(Scheduler(ex, max_batch=16, slots=1), reqs)
+        torch.cuda.synchronize()
+        S.sanns_device_status(ctx)
+        assert len(stats.latencies) == 5
+        assert (ex.tensor_batches > before) == (tensor_ms == 0.0)
+        for r in reqs:
+            solo_out, solo_srv = S.sanns_distances(ctx, db, r.payload[0], 5, r.payload[1])
+            assert torch.equal(r.result[0], solo_out) and torch.equal(r.result[1], solo_srv), r.rid

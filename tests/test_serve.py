@@ -187,3 +187,23 @@ def test_batching_window_holds_a_queue_until_full_or_waited_out():
     ex2 = FakeExecutor(clk2)
     run_open_loop(Scheduler(ex2, max_batch=16, slots=3, clock=clk2), _arrivals(400, 4000.0, 7), clock=clk2)
     assert np.mean([len(ids) for _, ids, _ in ex2.launched]) < np.mean(sizes)
+
+
+def test_interpolated_service_times():
+    from paper_1904_02033_b300.serve import interpolate_ms
+    t = [(4, 2.5), (1, 0.75), (2, 1.3)]                 # any order
+    assert interpolate_ms(t, 1) == 0.75 and interpolate_ms(t, 4) == 2.5
+    assert abs(interpolate_ms(t, 3) - 1.9) < 1e-12       # between the measured sizes
+    assert abs(interpolate_ms(t, 8) - 4.9) < 1e-12       # beyond: the last segment's slope
+    assert interpolate_ms([(8, 4.0)], 16) == 8.0         # one point: proportional
+
+
+def test_calibrated_route_takes_the_faster_path():
+    from paper_1904_02033_b300.serve import tensor_path_is_faster
+    per_query = [(1, 0.75), (2, 1.3), (4, 2.5)]           # about 0.6 ms a query
+    big_db = [(8, 3.9), (32, 12.8), (128, 48.0)]         # expansion amortised: 0.4 ms a query
+    small_db = [(8, 1.5), (32, 4.8), (128, 18.0)]
+    small_pq = [(1, 0.14), (2, 0.23), (4, 0.42)]         # about 0.1 ms a query
+    assert all(tensor_path_is_faster(per_query, big_db, n) for n in (8, 16, 64, 128))
+    assert not any(tensor_path_is_faster(small_pq, small_db, n) for n in (8, 16, 64, 128))
+    assert not tensor_path_is_faster(per_query, [(1, float("inf"))], 64)
