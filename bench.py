@@ -692,7 +692,11 @@ def run_gpu(args) -> None:
                          "traffic": _mac_traffic(rb, W),
                          "traffic_source": "ncu capture at n = 200,000 scaled by blocks",
                          "algorithmic_bytes": rb["total"],
-                         "launch_ms": mac_avg},
+                         "launch_ms": mac_avg,
+                         # in the timed loop the MAC's grid leaves SMs to the
+                         # previous query's INTT + mask; alone on every SM:
+                         "launch_sms": mac_sms or None,
+                         "frac_alone_all_sms": rb["total"] / (serial_mac_ms * 1e-3) / 1e9 / peak},
             "e2e": {"value": world * n / (e2e_ms * 1e-3), "unit": UNIT,
                     "h2d_bytes_per_step": d * 2 * L * N * 8,
                     "d2h_bytes_per_step": K * 2 * L * N * 8 + n * 4, "ms_per_step": e2e_ms,
