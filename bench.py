@@ -184,6 +184,7 @@ def run_small_section() -> dict:
     db = S.sanns_encode_db(ctx, torch.from_numpy(coords).cuda(), torch.from_numpy(perm).cuda())
     ct = S.sanns_encrypt_query(ctx, sk, torch.from_numpy(q).cuda(), 0, qids)
     out, srv = S.sanns_distances(ctx, db, ct, 0, qids)
+    variant, _ = S.sanns_autotune_mac(ctx, db, ct, out, reps=50)
     st = torch.cuda.current_stream()
     reps = 500
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
@@ -229,6 +230,8 @@ def run_small_section() -> dict:
             "latency_graph_ms": {"p50": glat[len(glat) // 2], "p99": glat[int(0.99 * (len(glat) - 1))],
                                  "what": "one step captured into a CUDA graph, replayed"},
             "qp_per_s": n / (lat[len(lat) // 2] * 1e-3), "steps": reps,
+            "mac_variant": S.sanns_mac_variants()[variant],
+            "epilogue": "four CTAs (a cluster) per response polynomial, mask drawn in the same kernel",
             "exact_top10_equals_brute_force": bool(exact)}
 
 

@@ -206,11 +206,110 @@ __global__ void __launch_bounds__(THREADS, MINB) mac_kernel(PrimeSet P, MacArgs 
   }
 }
 
+// Few work items (one query over a small database): one CTA per (tile,
+// block) item, its eight warps splitting the d dimensions, so that each warp's
+// chain of dependent loads is d/8 long instead of d.  Each lane reads its two
+// slots' ct values straight from global memory (Montgomery form and 30-bit
+// halves formed in registers) beside the database words; the warps' exact
+// 128-bit partial sums meet in shared memory and warp 0 reduces them.
+template <int SPL, int THREADS>
+__global__ void __launch_bounds__(THREADS, 1) mac_split_kernel(PrimeSet P, MacArgs A) {
+  static_assert(SPL == 2, "two slots per lane");
+  constexpr int WARPS = THREADS / 32;
+  constexpr uint32_t TILE = 32 * SPL;
+  constexpr int NOUT = 2 * SPL;
+  constexpr int BATCH = 8;                 // dimensions whose loads are in flight together
+  __shared__ ulonglong2 red[WARPS][NOUT][32];
+  const uint32_t N = P.N, L = P.L, d = A.d;
+  const uint32_t tiles = N / TILE;
+  const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (uint64_t w = blockIdx.x; w < A.total; w += gridDim.x) {
+    const uint64_t u = w / A.K, k = w - u * A.K;
+    const uint32_t st = (uint32_t)(u % tiles);
+    const uint32_t j = (uint32_t)((u / tiles) % L);
+    const uint64_t b = u / ((uint64_t)tiles * L);
+    const uint64_t q = P.q[j], r64 = P.r64[j], r64s = P.r64_shoup[j];
+    const uint32_t per = (d + WARPS - 1) / WARPS;
+    const uint32_t i_begin = warp * per, i_end = min(d, i_begin + per);
+    const uint64_t* p = A.pt + ((k * L + j) * d) * N + st * TILE + SPL * lane;
+    const uint64_t* c = A.ct + (b * d * 2 * L + j) * N + st * TILE + SPL * lane;  // dimension 0, c0
+    u128 R[NOUT];
+    uint64_t aL[NOUT], aM1[NOUT], aM2[NOUT], aH[NOUT];
+#pragma unroll
+    for (int o = 0; o < NOUT; ++o) { R[o] = 0; aL[o] = aM1[o] = aM2[o] = aH[o] = 0; }
+    uint32_t since_fold = 0;
+    for (uint32_t i0 = i_begin; i0 < i_end; i0 += BATCH) {
+      ulonglong2 pv[BATCH], c0v[BATCH], c1v[BATCH];
+#pragma unroll
+      for (int v = 0; v < BATCH; ++v) {
+        const uint32_t i = i0 + v;
+        const bool in = i < i_end;
+        pv[v] = in ? __ldcs(reinterpret_cast<const ulonglong2*>(p + (uint64_t)i * N)) : make_ulonglong2(0, 0);
+        c0v[v] = in ? __ldg(reinterpret_cast<const ulonglong2*>(c + (uint64_t)i * 2 * L * N))
+                    : make_ulonglong2(0, 0);
+        c1v[v] = in ? __ldg(reinterpret_cast<const ulonglong2*>(c + ((uint64_t)i * 2 + 1) * L * N))
+                    : make_ulonglong2(0, 0);
+      }
+#pragma unroll
+      for (int v = 0; v < BATCH; ++v) {
+        if (i0 + v >= i_end) break;
+        if (since_fold == 16) {  // 16 products of (2^30 - 1)^2 fill a 64-bit sum
+#pragma unroll
+          for (int o = 0; o < NOUT; ++o) {
+            const u128 m = (u128)aM1[o] + aM2[o];
+            R[o] += (u128)aL[o] + (m << 30) + ((u128)aH[o] << 60);
+            aL[o] = aM1[o] = aM2[o] = aH[o] = 0;
+          }
+          since_fold = 0;
+        }
+        const uint64_t y[SPL] = {pv[v].x, pv[v].y};
+        const uint64_t x0[SPL] = {mul_shoup(c0v[v].x, r64, r64s, q), mul_shoup(c0v[v].y, r64, r64s, q)};
+        const uint64_t x1[SPL] = {mul_shoup(c1v[v].x, r64, r64s, q), mul_shoup(c1v[v].y, r64, r64s, q)};
+#pragma unroll
+        for (int s = 0; s < SPL; ++s) {
+          const uint32_t yl = (uint32_t)y[s], yh = (uint32_t)(y[s] >> 32);  // stored split
+          mac4(aL[s], aM1[s], aM2[s], aH[s], (uint32_t)x0[s] & kMask30, (uint32_t)(x0[s] >> 30), yl, yh);
+          mac4(aL[2 + s], aM1[2 + s], aM2[2 + s], aH[2 + s], (uint32_t)x1[s] & kMask30,
+               (uint32_t)(x1[s] >> 30), yl, yh);
+        }
+        ++since_fold;
+      }
+    }
+#pragma unroll
+    for (int o = 0; o < NOUT; ++o) {
+      const u128 m = (u128)aM1[o] + aM2[o];
+      R[o] += (u128)aL[o] + (m << 30) + ((u128)aH[o] << 60);
+      red[warp][o][lane] = make_ulonglong2((uint64_t)R[o], (uint64_t)(R[o] >> 64));
+    }
+    __syncthreads();
+    if (warp == 0) {
+      const uint64_t qn = P.q_neg_inv[j];
+      uint64_t r[NOUT];
+#pragma unroll
+      for (int o = 0; o < NOUT; ++o) {
+        u128 S = 0;
+#pragma unroll
+        for (int wi = 0; wi < WARPS; ++wi) {
+          const ulonglong2 h = red[wi][o][lane];
+          S += ((u128)h.y << 64) | h.x;
+        }
+        r[o] = reduce_below_16q(redc128(S, q, qn), q);
+      }
+      uint64_t* o0 = A.out + (((b * A.K + k) * 2 + 0) * L + j) * N + st * TILE + SPL * lane;
+      uint64_t* o1 = A.out + (((b * A.K + k) * 2 + 1) * L + j) * N + st * TILE + SPL * lane;
+      *reinterpret_cast<ulonglong2*>(o0) = make_ulonglong2(r[0], r[1]);
+      *reinterpret_cast<ulonglong2*>(o1) = make_ulonglong2(r[2], r[3]);
+    }
+    __syncthreads();  // red[] is reused by the next item
+  }
+}
+
 struct MacVariant {
   void (*fn)(PrimeSet, MacArgs);
   int spl, threads, ctas_per_sm, qn;
   int pair_sibling;  // the variant run for calls with B >= 2 (-1: itself)
   const char* name;
+  bool split = false;  // mac_split_kernel: one CTA per item, no shared ct tile
 };
 
 const MacVariant kVariants[] = {
@@ -220,6 +319,7 @@ const MacVariant kVariants[] = {
     {mac_kernel<1, 16, 384, 2>, 1, 384, 2, 1, 4, "spl1_unr16_384x2"},
     {mac_kernel<1, 8, 512, 1, 2>, 1, 512, 1, 2, -1, "pair_unr8_512x1"},
     {mac_kernel<1, 8, 256, 2, 2>, 1, 256, 2, 2, -1, "pair_unr8_256x2"},
+    {mac_split_kernel<2, 256>, 2, 256, 1, 1, -1, "split_d_256x1", true},
 };
 constexpr int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
 
@@ -244,6 +344,13 @@ cudaError_t launch_mac(const PrimeSet& P, const uint64_t* ct, const uint64_t* pt
   A.B = B;
   A.total = (uint64_t)((B + V.qn - 1) / V.qn) * P.L * (P.N / tile) * K;
   if (A.total == 0) return cudaSuccess;
+  if (V.split) {
+    // one CTA per item up to eight per SM (the grid loops beyond that)
+    uint64_t grid = (uint64_t)(sms > 0 ? sms : 148) * 8;
+    if (grid > A.total) grid = A.total;
+    V.fn<<<(unsigned)grid, V.threads, 0, st>>>(P, A);
+    return cudaGetLastError();
+  }
   const size_t smem = sizeof(uint4) * 32 * d * V.spl * V.qn;
   // shared-memory opt-in, once per (variant, device)
   cudaError_t e = ensure_smem_attr((const void*)V.fn, smem > 48 * 1024 ? smem : 48 * 1024);

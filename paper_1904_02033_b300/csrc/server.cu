@@ -372,6 +372,216 @@ __global__ void __launch_bounds__(256, 3) intt_mask_short_kernel(PrimeSet P, uin
   store_poly(g, sa, N);
 }
 
+// ------------------------------------------------------------------------
+// Few polynomials (one query over a small database): each polynomial's
+// epilogue on a cluster of four CTAs, so that its transform spreads over four
+// SMs instead of waiting on one.  With M = N / 4, CTA r holds quarter r
+// (positions rM .. rM + M - 1) in shared memory and runs the stages of
+// distance below M on it (radix-4 register passes, the global twiddle index
+// of each pair group being r M / 2^(lt+1) + its local index).  The stages of
+// distance M and N/2 mix the quarters: after a cluster barrier, CTA r reads
+// the four quarters' values at its own offsets through distributed shared
+// memory and computes its quarter of the output,
+//   stage M:    X0' = X0 + X1, X1' = (X0 - X1) w[2], X2' = X2 + X3,
+//               X3' = (X2 - X3) w[3];
+//   stage N/2:  out0 = (X0' + X2') N^-1, out2 = (X0' - X2') psi^-brv(1) N^-1,
+//               out1, out3 likewise from X1', X3';
+// then, for c = 0, draws r itself (one ChaCha20 block per four positions, as
+// mask_share_kernel does), adds Delta ((||p||^2 + r) mod t) and writes the
+// server share from the j = 0 polynomial.  A second cluster barrier keeps
+// every CTA's shared memory alive until the others have read it.
+// ------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t cl_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+
+__device__ __forceinline__ void cl_sync() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\nbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+// The same barrier without ordering of memory accesses: enough where it only
+// has to hold a CTA until the others have consumed (used) what they loaded
+// from its shared memory.
+__device__ __forceinline__ void cl_sync_relaxed() {
+  asm volatile("barrier.cluster.arrive.relaxed.aligned;\nbarrier.cluster.wait.aligned;" ::: "memory");
+}
+
+// 64-bit load from CTA `rank`'s copy of the shared-memory word at `local`
+__device__ __forceinline__ uint64_t ld_cluster(const uint64_t* local, uint32_t rank) {
+  const uint32_t a = (uint32_t)__cvta_generic_to_shared(local);
+  uint32_t ra;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(ra) : "r"(a), "r"(rank));
+  uint64_t v;
+  asm volatile("ld.shared::cluster.u64 %0, [%1];" : "=l"(v) : "r"(ra) : "memory");
+  return v;
+}
+
+constexpr uint32_t kClusterIntt = 4;
+constexpr uint32_t kClusterThreads = 256;   // the prologue's per-thread load counts assume it
+
+// shared-memory words of the cluster kernel for a ring of N: the padded
+// quarter, the quarter's twiddle pairs of every local stage (M - 1 pairs), the
+// mask term of each of its M positions and their 32-bit server shares
+__host__ __device__ __forceinline__ uint32_t cluster_intt_smem_words(uint32_t N) {
+  const uint32_t M = N / kClusterIntt;
+  return ntt_smem_words(M) + 2 * (M - 1) + M + M / 2;
+}
+
+__global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(kClusterThreads, 1)
+    intt_mask_cluster_kernel(PrimeSet P, uint64_t* __restrict__ ct_out, const uint32_t* __restrict__ norms,
+                             uint64_t K, uint64_t n, uint64_t pos0g, uint64_t mask_seed,
+                             const uint64_t* __restrict__ qids, uint32_t* __restrict__ srv_share) {
+  extern __shared__ uint64_t sa[];
+  const uint32_t N = P.N, L = P.L, logN = P.logN;
+  const uint32_t M = N / kClusterIntt, logM = logN - 2;
+  ulonglong2* tws = reinterpret_cast<ulonglong2*>(sa + ntt_smem_words(M));  // 16-byte aligned: M + M/16 even
+  uint64_t* mval = sa + ntt_smem_words(M) + 2 * (M - 1);
+  uint32_t* shs = reinterpret_cast<uint32_t*>(mval + M);
+  const uint32_t r = cl_rank();
+  const uint64_t poly = blockIdx.x / kClusterIntt;  // ((b K + k) 2 + c) L + j
+  const uint32_t j = (uint32_t)(poly % L);
+  const uint32_t c = (uint32_t)((poly / L) % 2);
+  const uint64_t bk = poly / (2 * L);
+  const uint64_t k = bk % K, b = bk / K;
+  const uint64_t q = P.q[j], q2 = 2 * q, q4 = 4 * q;  // values stay below 4q
+  const ulonglong2* itw = P.itw + (size_t)j * N;
+  uint64_t* g = ct_out + poly * N;
+
+  // Everything this CTA reads from global memory is requested first: its
+  // quarter, the twiddles of its local stages (stage lt uses the M / 2^(lt+1)
+  // pairs from N / 2^(lt+1) + r M / 2^(lt+1), kept from word M - M / 2^lt of
+  // tws) and, for c = 0, the norms; the mask draws are computed while the
+  // loads are in flight.
+  // (all of a thread's loads are issued before any is stored: M <= 4096 gives
+  // at most 8 data pairs and 16 twiddle pairs per thread of 256)
+  constexpr int kDmax = 8, kTmax = 16;
+  ulonglong2 dv[kDmax], tv[kTmax];
+#pragma unroll
+  for (int z = 0; z < kDmax; ++z) {
+    const uint32_t x = 2 * (threadIdx.x + z * blockDim.x);
+    dv[z] = x < M ? __ldg(reinterpret_cast<const ulonglong2*>(g + (uint64_t)r * M + x)) : make_ulonglong2(0, 0);
+  }
+#pragma unroll
+  for (int z = 0; z < kTmax; ++z) {
+    // flat index f of the stage-major twiddle copy: stage lt holds words
+    // [M - M / 2^lt, M - M / 2^(lt+1)), i.e. lt = log2 M - ceil(log2 (M - f))
+    const uint32_t f = threadIdx.x + z * blockDim.x;
+    if (f + 1 < M) {
+      const uint32_t lt = logM - (32 - __clz(M - f - 1));
+      const uint32_t cnt = M >> (lt + 1), e = f - (M - (M >> lt));
+      tv[z] = __ldg(itw + (N >> (lt + 1)) + r * cnt + e);
+    }
+  }
+#pragma unroll
+  for (int z = 0; z < kDmax; ++z) {
+    const uint32_t x = 2 * (threadIdx.x + z * blockDim.x);
+    if (x < M) {
+      sa[SP(x)] = dv[z].x;
+      sa[SP(x + 1)] = dv[z].y;
+    }
+  }
+#pragma unroll
+  for (int z = 0; z < kTmax; ++z) {
+    const uint32_t f = threadIdx.x + z * blockDim.x;
+    if (f + 1 < M) tws[f] = tv[z];
+  }
+  if (c == 0) {
+    const uint64_t dl = P.delta[j], dls = P.delta_shoup[j], t = P.t;
+    for (uint32_t u0 = 4 * threadIdx.x; u0 < M; u0 += 4 * blockDim.x) {
+      const uint64_t pos = k * N + (uint64_t)r * M + u0;
+      const uint4 nv = __ldg(reinterpret_cast<const uint4*>(norms + pos));
+      uint32_t blk[16];
+      chacha20_block(mask_seed, kPurposeMask, qids[b], (uint32_t)((pos0g + pos) / 4), blk);
+      const uint32_t nvv[4] = {nv.x, nv.y, nv.z, nv.w};
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        uint64_t lo, hi;
+        draw_pair(blk, v, lo, hi);
+        const uint64_t rv = mod_t128(lo, hi, P);
+        mval[u0 + v] = mul_shoup(norm_plus_mask_mod_t(P, nvv[v], rv), dl, dls, q);
+        // the share, written after the transform's stages (a global store
+        // here would hold up the release of the first cluster barrier)
+        shs[u0 + v] = (uint32_t)(rv == 0 ? 0 : t - rv);
+      }
+    }
+  }
+  __syncthreads();
+  // stages of distance 2^lt < M on the quarter: radix-4 passes (stages lt and
+  // lt + 1), a radix-2 stage when log2 M is odd
+  uint32_t lt = 0;
+  for (; lt + 2 <= logM; lt += 2) {
+    const ulonglong2* t0 = tws + (M - (M >> lt));
+    const ulonglong2* t1 = tws + (M - (M >> (lt + 1)));
+    for (uint32_t th = threadIdx.x; th < M / 4; th += blockDim.x) {
+      const uint32_t gl = th >> lt, bl = th & ((1u << lt) - 1);
+      const uint32_t x0 = (gl << (lt + 2)) + bl;
+      uint64_t v[4];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) v[e] = sa[SP(x0 + (e << lt))];
+      const ulonglong2 wa = t0[2 * gl], wb = t0[2 * gl + 1], wc = t1[gl];
+      inv_bfly4(v[0], v[1], wa.x, wa.y, q, q4);
+      inv_bfly4(v[2], v[3], wb.x, wb.y, q, q4);
+      inv_bfly4(v[0], v[2], wc.x, wc.y, q, q4);
+      inv_bfly4(v[1], v[3], wc.x, wc.y, q, q4);
+#pragma unroll
+      for (int e = 0; e < 4; ++e) sa[SP(x0 + (e << lt))] = v[e];
+    }
+    __syncthreads();
+  }
+  if (lt < logM) {
+    const uint32_t t = 1u << lt;
+    const ulonglong2* t0 = tws + (M - (M >> lt));
+    for (uint32_t bf = threadIdx.x; bf < M / 2; bf += blockDim.x) {
+      const uint32_t i = bf >> lt, x = (i << (lt + 1)) + (bf & (t - 1));
+      uint64_t X = sa[SP(x)], Y = sa[SP(x + t)];
+      const ulonglong2 w = t0[i];
+      inv_bfly4(X, Y, w.x, w.y, q, q4);
+      sa[SP(x)] = X;
+      sa[SP(x + t)] = Y;
+    }
+  }
+  cl_sync();  // every quarter's local stages done and visible to the cluster
+
+  const ulonglong2 w2 = __ldg(itw + 2), w3 = __ldg(itw + 3);
+  const uint64_t ni = P.n_inv[j], nis = P.n_inv_shoup[j];
+  const uint64_t wl = P.last_inv[j], wls = P.last_inv_shoup[j];
+  for (uint32_t u0 = 4 * threadIdx.x; u0 < M; u0 += 4 * blockDim.x) {
+    uint64_t X[4][4];  // [quarter][offset]
+#pragma unroll
+    for (uint32_t qi = 0; qi < 4; ++qi)
+#pragma unroll
+      for (int v = 0; v < 4; ++v) X[qi][v] = ld_cluster(sa + SP(u0 + v), qi);
+    uint64_t out[4];
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      uint64_t A, B;
+      if ((r & 1) == 0) {  // sum sides of the stage of distance M
+        A = csub(X[0][v] + X[1][v], q4);
+        B = csub(X[2][v] + X[3][v], q4);
+      } else {             // difference sides
+        A = mul_shoup_lazy4(X[0][v] - X[1][v] + q4, w2.x, w2.y, q);
+        B = mul_shoup_lazy4(X[2][v] - X[3][v] + q4, w3.x, w3.y, q);
+      }
+      const uint64_t y = r < 2 ? mul_shoup_lazy4(csub(A + B, q4), ni, nis, q)
+                               : mul_shoup_lazy4(A - B + q4, wl, wls, q);
+      out[v] = csub(csub(y, q2), q);
+      if (c == 0) out[v] = add_mod(out[v], mval[u0 + v], q);
+    }
+    const uint32_t x = r * M + u0;
+    *reinterpret_cast<ulonglong2*>(g + x) = make_ulonglong2(out[0], out[1]);
+    *reinterpret_cast<ulonglong2*>(g + x + 2) = make_ulonglong2(out[2], out[3]);
+    if (c == 0 && j == 0) {
+      const uint64_t pos = k * N + x;
+#pragma unroll
+      for (int v = 0; v < 4; ++v)
+        if (pos + v < n) srv_share[b * n + pos + v] = shs[u0 + v];
+    }
+  }
+  cl_sync_relaxed();  // the other CTAs have finished reading this CTA's quarter
+}
+
 // NTT-form responses: the response is the NTT of the coefficient-form one.
 // Since the transform is linear, c0 = acc0 + NTT(Delta_j v) with v = (||p||^2
 // + r) mod t per position, and c1 = acc1: one forward transform per (b, k, j)
@@ -738,6 +948,16 @@ cudaError_t launch_intt_mask(const PrimeSet& P, uint64_t* ct_out, const uint32_t
                              const uint64_t* qids, uint32_t* srv_share, int sms, cudaStream_t st) {
   const uint64_t polys = (uint64_t)B * K * 2 * P.L;
   if (polys == 0) return cudaSuccess;
+  // few polynomials: four SMs per polynomial, the mask drawn in the same
+  // kernel (all clusters resident at once)
+  if (polys * kClusterIntt <= (uint64_t)(sms > 0 ? sms : 148) && P.N >= 1024 && P.N <= 16384) {
+    const size_t csmem = sizeof(uint64_t) * cluster_intt_smem_words(P.N);
+    cudaError_t e = ensure_smem_attr((const void*)intt_mask_cluster_kernel, csmem);
+    if (e != cudaSuccess) return e;
+    intt_mask_cluster_kernel<<<(unsigned)(polys * kClusterIntt), kClusterThreads, csmem, st>>>(
+        P, ct_out, norms, K, n, pos0, mask_seed, qids, srv_share);
+    return cudaGetLastError();
+  }
   const uint64_t groups = (uint64_t)B * ((n + 3) / 4);
   mask_share_kernel<<<(unsigned)((groups + 255) / 256), 256, 0, st>>>(P, B, n, pos0, mask_seed,
                                                                      qids, srv_share);

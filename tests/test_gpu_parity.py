@@ -172,6 +172,19 @@ def test_distances_match_oracle_bit_exact(cfg, n, B):
         assert np.array_equal((r["cli"][b].astype(np.int64) + r["srv"][b]) % O.t, brute)
 
 
+@pytest.mark.parametrize("cfg,n,B", [
+    ((1024, 2, 40, 0, 9), 1024 * 3 - 7, 2),    # quarters of 256: radix-4 passes only
+    ((2048, 3, 60, 1, 6), 2048 * 2 + 1, 1),    # quarters of 512: a radix-2 stage too; t = 2^b_d
+])
+def test_few_polynomials_on_clusters_match_oracle(cfg, n, B):
+    """At most 37 response polynomials (B K 2 L): the epilogue runs each
+    polynomial on a cluster of four CTAs and draws the mask itself; the N =
+    4096, 8192 and 16384 cases above take the same path."""
+    K = -(-n // cfg[0])
+    assert B * K * 2 * cfg[1] * 4 <= S.sanns_device_sms()
+    test_distances_match_oracle_bit_exact(cfg, n, B)
+
+
 def test_max_dimension_and_identity_perm():
     cfg = (64, 2, 40, 0, 224)
     r = _pipeline(cfg, 130, 1, seed=3, perm=False)
