@@ -220,6 +220,22 @@ def run_small_section() -> dict:
         b.record(cur)
     torch.cuda.synchronize()
     glat = sorted(a.elapsed_time(b) for a, b in gev)
+    # 50 steps in one graph: the per-step device time without the per-replay
+    # cost (back-to-back queries, as a serving loop would run them)
+    g50 = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g50):
+        for _ in range(50):
+            S.sanns_distances(ctx, db, ct, 0, qids, out, srv)
+    torch.cuda.synchronize()
+    g50.replay()
+    torch.cuda.synchronize()
+    e50 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(40)]
+    for a, b in e50:
+        a.record(cur)
+        g50.replay()
+        b.record(cur)
+    torch.cuda.synchronize()
+    l50 = sorted(a.elapsed_time(b) / 50 for a, b in e50)
     cli = S.sanns_decrypt_shares(ctx, sk, out, n, torch.from_numpy(q).cuda())
     dist_k, pos_k = S.sanns_topk(ctx, cli, srv, 10)
     brute = np.sum((coords[perm].astype(np.int64) - q[0].astype(np.int64)) ** 2, axis=1)
@@ -229,6 +245,7 @@ def run_small_section() -> dict:
             "latency_ms": {"p50": lat[len(lat) // 2], "p99": lat[int(0.99 * (len(lat) - 1))]},
             "latency_graph_ms": {"p50": glat[len(glat) // 2], "p99": glat[int(0.99 * (len(glat) - 1))],
                                  "what": "one step captured into a CUDA graph, replayed"},
+            "ms_per_step_graph_of_50": l50[len(l50) // 2],
             "qp_per_s": n / (lat[len(lat) // 2] * 1e-3), "steps": reps,
             "mac_variant": S.sanns_mac_variants()[variant],
             "epilogue": "four CTAs (a cluster) per response polynomial, mask drawn in the same kernel",
