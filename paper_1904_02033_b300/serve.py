@@ -251,8 +251,7 @@ class GpuExecutor:
                     table[key].append((b, ev0.elapsed_time(ev1) / reps))
                     del out, srv
             if not table["tensor"]:
-                del table["tensor"]
-                table["tensor"] = [(1, float("inf"))]
+                table["tensor"] = [(1, float("inf"))]   # no tensor path on this database
             self.costs[name] = table
         return self.costs
 
