@@ -132,20 +132,31 @@ int sanns_ctx_create(const sanns_params* p, sanns_ctx** out) {
     c->P.last_inv[j] = (uint64_t)(((unsigned __int128)iw[j * N + 1] * c->P.n_inv[j]) % q[j]);
     c->P.last_inv_shoup[j] = shoup_of(c->P.last_inv[j], q[j]);
   }
-  // interleave {w, w_shoup}: forward table then inverse table, [L][N] pairs each
-  std::vector<uint64_t> host(4 * per);
+  // interleave {w, w_shoup}: forward table then inverse table, [L][N] pairs
+  // each; then the Montgomery byte tables, [L][2][256]
+  const size_t mb = (size_t)p->L * 512;
+  std::vector<uint64_t> host(4 * per + mb);
   for (size_t x = 0; x < per; ++x) {
     host[2 * x] = fw[x];
     host[2 * x + 1] = fws[x];
     host[2 * per + 2 * x] = iw[x];
     host[2 * per + 2 * x + 1] = iws[x];
   }
-  e = cudaMalloc(&c->d_tables, sizeof(uint64_t) * 4 * per);
+  for (uint32_t j = 0; j < p->L; ++j) {
+    const u128 R = (((u128)1) << 64) % q[j];
+    const u128 w1R = (u128)fw[(size_t)j * N + 1] * R % q[j];
+    for (uint32_t a = 0; a < 256; ++a) {
+      host[4 * per + (size_t)j * 512 + a] = (uint64_t)(a * R % q[j]);
+      host[4 * per + (size_t)j * 512 + 256 + a] = (uint64_t)(a * w1R % q[j]);
+    }
+  }
+  e = cudaMalloc(&c->d_tables, sizeof(uint64_t) * (4 * per + mb));
   if (e != cudaSuccess) { delete c; return cuda_fail(e, "cudaMalloc(tables)"); }
-  e = cudaMemcpy(c->d_tables, host.data(), sizeof(uint64_t) * 4 * per, cudaMemcpyHostToDevice);
+  e = cudaMemcpy(c->d_tables, host.data(), sizeof(uint64_t) * (4 * per + mb), cudaMemcpyHostToDevice);
   if (e != cudaSuccess) { cudaFree(c->d_tables); delete c; return cuda_fail(e, "cudaMemcpy(tables)"); }
   c->P.tw = reinterpret_cast<const ulonglong2*>(c->d_tables);
   c->P.itw = reinterpret_cast<const ulonglong2*>(c->d_tables + 2 * per);
+  c->P.mbyte = c->d_tables + 4 * per;
   // responses at every prime by default; the one-prime view (q_0 alone, its
   // tables the first rows of the full ones) decrypts switched responses
   c->response_primes = p->L;

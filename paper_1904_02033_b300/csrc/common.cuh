@@ -66,6 +66,9 @@ struct PrimeSet {
   // twiddles, [L][N] pairs {w, Shoup companion}: psi^brv(m) and psi^-brv(m)
   const ulonglong2* tw;
   const ulonglong2* itw;
+  // Montgomery images of coordinate bytes, [L][2][256]: a 2^64 mod q and
+  // b psi^brv(1) 2^64 mod q (the first forward stage of a byte polynomial)
+  const uint64_t* mbyte;
 };
 
 // ------------------------------------------------------------------------

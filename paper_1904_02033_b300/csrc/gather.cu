@@ -286,10 +286,14 @@ gather_kernel(PrimeSet P, uint32_t d, uint64_t W, uint32_t S, uint32_t ds,
     for (uint32_t i = i0; i < i1; ++i) {
       __syncthreads();
       const uint8_t* gi = g + (uint64_t)i * N;   // 16-byte aligned: item and row offsets are multiples of N
+      // Coefficient encoding: each byte a enters as its Montgomery image
+      // a 2^64 mod q (a table lookup), so by linearity the transform comes out
+      // in Montgomery form, ready for the MAC's Montgomery products.
+      const uint64_t* mb = P.mbyte + (size_t)j * 512;
       if (!O.slots && (P.logN & 3)) {
         // the coordinate bytes, 16 of each half per thread, go straight
-        // through the first forward stage (distance N/2, twiddle psi^brv(1))
-        const ulonglong2 w1 = __ldg(P.tw + (size_t)j * N + 1);
+        // through the first forward stage (distance N/2, twiddle psi^brv(1)):
+        // X = aR + b psi^brv(1) R, Y = aR - b psi^brv(1) R, both from tables
         for (uint32_t gx = threadIdx.x; gx < N / 32; gx += blockDim.x) {
           const uint32_t x = gx * 16;
           const uint4 lo = __ldg(reinterpret_cast<const uint4*>(gi + x));
@@ -297,10 +301,10 @@ gather_kernel(PrimeSet P, uint32_t d, uint64_t W, uint32_t S, uint32_t ds,
           const uint32_t lw[4] = {lo.x, lo.y, lo.z, lo.w}, hw[4] = {hi.x, hi.y, hi.z, hi.w};
 #pragma unroll
           for (int k = 0; k < 16; ++k) {
-            uint64_t X = (lw[k >> 2] >> (8 * (k & 3))) & 255u, Y = (hw[k >> 2] >> (8 * (k & 3))) & 255u;
-            fwd_bfly(X, Y, w1.x, w1.y, q, 2 * q);
-            poly[SP(x + k)] = X;
-            poly[SP(x + N / 2 + k)] = Y;
+            const uint64_t A = __ldg(mb + ((lw[k >> 2] >> (8 * (k & 3))) & 255u));
+            const uint64_t T = __ldg(mb + 256 + ((hw[k >> 2] >> (8 * (k & 3))) & 255u));
+            poly[SP(x + k)] = A + T;              // below 2q
+            poly[SP(x + N / 2 + k)] = A - T + q;  // below 2q
           }
         }
         __syncthreads();
@@ -311,7 +315,10 @@ gather_kernel(PrimeSet P, uint32_t d, uint64_t W, uint32_t S, uint32_t ds,
           const uint4 v = __ldg(reinterpret_cast<const uint4*>(gi + x));
           const uint32_t vw[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
-          for (int k = 0; k < 16; ++k) poly[SP(x + k)] = (vw[k >> 2] >> (8 * (k & 3))) & 255u;
+          for (int k = 0; k < 16; ++k) {
+            const uint32_t a = (vw[k >> 2] >> (8 * (k & 3))) & 255u;
+            poly[SP(x + k)] = O.slots ? a : __ldg(mb + a);   // slot rows go mod t first
+          }
         }
         __syncthreads();
         if (O.slots) {
@@ -340,7 +347,8 @@ gather_kernel(PrimeSet P, uint32_t d, uint64_t W, uint32_t S, uint32_t ds,
         for (int r = 0; r < 4; ++r) {
           const uint32_t x = x0 + r * blockDim.x;
           if (x >= N) break;
-          const uint64_t pm = mul_shoup(poly[SP(x)], P.r64[j], P.r64_shoup[j], q);
+          // Montgomery form already, except for slot rows (transformed mod t)
+          const uint64_t pm = O.slots ? mul_shoup(poly[SP(x)], P.r64[j], P.r64_shoup[j], q) : poly[SP(x)];
           mine[x] = add_mod(a0[r], mont_mul(v0[r], pm, q, qn), q);
           mine[N + x] = add_mod(a1[r], mont_mul(v1[r], pm, q, qn), q);
         }
