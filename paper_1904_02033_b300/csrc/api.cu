@@ -131,6 +131,8 @@ int sanns_ctx_create(const sanns_params* p, sanns_ctx** out) {
   for (uint32_t j = 0; j < p->L; ++j) {
     c->P.last_inv[j] = (uint64_t)(((unsigned __int128)iw[j * N + 1] * c->P.n_inv[j]) % q[j]);
     c->P.last_inv_shoup[j] = shoup_of(c->P.last_inv[j], q[j]);
+    c->P.delta_w1[j] = (uint64_t)(((unsigned __int128)fw[j * N + 1] * c->P.delta[j]) % q[j]);
+    c->P.delta_w1_shoup[j] = shoup_of(c->P.delta_w1[j], q[j]);
   }
   // interleave {w, w_shoup}: forward table then inverse table, [L][N] pairs
   // each; then the Montgomery byte tables, [L][2][256]
@@ -164,6 +166,8 @@ int sanns_ctx_create(const sanns_params* p, sanns_ctx** out) {
   fill_prime_constants(c->P1, q, t, 1);
   c->P1.last_inv[0] = c->P.last_inv[0];
   c->P1.last_inv_shoup[0] = c->P.last_inv_shoup[0];
+  c->P1.delta_w1[0] = (uint64_t)(((unsigned __int128)fw[1] * c->P1.delta[0]) % q[0]);
+  c->P1.delta_w1_shoup[0] = shoup_of(c->P1.delta_w1[0], q[0]);
   make_mod_switch_consts(c->P, &c->MS);
   e = cudaMalloc(&c->d_err, sizeof(int));
   if (e == cudaSuccess) e = cudaMemset(c->d_err, 0, sizeof(int));

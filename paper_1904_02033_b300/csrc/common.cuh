@@ -63,6 +63,8 @@ struct PrimeSet {
   uint64_t crt_inv_shoup[kMaxPrimes];
   uint64_t last_inv[kMaxPrimes];    // psi^-brv(1) N^-1 mod q: last inverse stage with N^-1
   uint64_t last_inv_shoup[kMaxPrimes];
+  uint64_t delta_w1[kMaxPrimes];    // Delta psi^brv(1) mod q: first forward stage of Delta v
+  uint64_t delta_w1_shoup[kMaxPrimes];
   // twiddles, [L][N] pairs {w, Shoup companion}: psi^brv(m) and psi^-brv(m)
   const ulonglong2* tw;
   const ulonglong2* itw;
@@ -100,6 +102,20 @@ __device__ __forceinline__ uint64_t mul_shoup_lazy4(uint64_t y, uint64_t w, uint
 __device__ __forceinline__ uint64_t mul_shoup(uint64_t y, uint64_t w, uint64_t w_shoup,
                                               uint64_t q) {
   return csub(mul_shoup_lazy(y, w, w_shoup, q), q);
+}
+
+// w * v mod q lazily in [0, 2q) for a 32-bit v (values mod t): the same
+// Shoup quotient floor(v w_shoup / 2^64), exactly, from two 32-bit partial
+// products, and a quotient below 2^32.
+__device__ __forceinline__ uint64_t mul_shoup_u32_lazy(uint32_t v, uint64_t w, uint64_t w_shoup,
+                                                       uint64_t q) {
+  const uint64_t hi = (uint64_t)v * (uint32_t)(w_shoup >> 32) + __umulhi(v, (uint32_t)w_shoup);
+  const uint32_t qt = (uint32_t)(hi >> 32);
+  return (uint64_t)v * w - (uint64_t)qt * q;
+}
+
+__device__ __forceinline__ uint64_t mul_shoup_u32(uint32_t v, uint64_t w, uint64_t w_shoup, uint64_t q) {
+  return csub(mul_shoup_u32_lazy(v, w, w_shoup, q), q);
 }
 
 __device__ __forceinline__ uint64_t add_mod(uint64_t a, uint64_t b, uint64_t q) {

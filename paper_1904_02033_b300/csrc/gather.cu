@@ -209,7 +209,7 @@ __device__ void gather_finish(uint64_t* a, uint64_t* save, const PrimeSet& P, ui
         const uint64_t rr = mod_t128(lo, hi, P);
         const uint32_t x = 4 * t4 + v;
         const uint64_t val = norm_plus_mask_mod_t(P, gnorm[w * N + x], rr);
-        a[SP(x)] = add_mod(a[SP(x)], mul_shoup(val, dl, dls, q), q);
+        a[SP(x)] = add_mod(a[SP(x)], mul_shoup_u32((uint32_t)val, dl, dls, q), q);
         const uint64_t pos = pos0 + v;
         if (j == 0 && pos < Q.n) srv_share[Q.pos_off + pos] = (uint32_t)(rr == 0 ? 0 : P.t - rr);
       }

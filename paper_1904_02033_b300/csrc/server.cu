@@ -270,7 +270,7 @@ __global__ void __launch_bounds__(256, 3) intt_mask_kernel(PrimeSet P, uint64_t*
         const uint32_t sv = sh[pos];
         const uint64_t r = sv == 0 ? 0 : t - sv;
         const uint64_t val = norm_plus_mask_mod_t(P, norms[pos], r);
-        v[k] = add_mod(v[k], mul_shoup(val, dl, dls, q), q);
+        v[k] = add_mod(v[k], mul_shoup_u32((uint32_t)val, dl, dls, q), q);
       }
     } else if (c == 0) {
       // block with padding positions (the last one): element by element
@@ -288,7 +288,7 @@ __global__ void __launch_bounds__(256, 3) intt_mask_kernel(PrimeSet P, uint64_t*
           r = mask_draw(P, pos0g + pos, mask_seed, qids[b]);
         }
         const uint64_t val = norm_plus_mask_mod_t(P, norms[pos], r);
-        g[x] = add_mod(sa[SP(x)], mul_shoup(val, dl, dls, q), q);
+        g[x] = add_mod(sa[SP(x)], mul_shoup_u32((uint32_t)val, dl, dls, q), q);
       }
       continue;
     }
@@ -363,7 +363,7 @@ __global__ void __launch_bounds__(256, 3) intt_mask_short_kernel(PrimeSet P, uin
         for (int v = 0; v < 4; ++v) {
           const uint64_t val = norm_plus_mask_mod_t(P, nvv[v], r[v]);
           const uint32_t x = 4 * u + v;
-          sa[SP(x)] = add_mod(sa[SP(x)], mul_shoup(val, dl, dls, q), q);
+          sa[SP(x)] = add_mod(sa[SP(x)], mul_shoup_u32((uint32_t)val, dl, dls, q), q);
         }
       }
     }
@@ -500,7 +500,7 @@ __global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(kClusterThreads, 1)
         uint64_t lo, hi;
         draw_pair(blk, v, lo, hi);
         const uint64_t rv = mod_t128(lo, hi, P);
-        mval[u0 + v] = mul_shoup(norm_plus_mask_mod_t(P, nvv[v], rv), dl, dls, q);
+        mval[u0 + v] = mul_shoup_u32((uint32_t)norm_plus_mask_mod_t(P, nvv[v], rv), dl, dls, q);
         // the share, written after the transform's stages (a global store
         // here would hold up the release of the first cluster barrier)
         shs[u0 + v] = (uint32_t)(rv == 0 ? 0 : t - rv);
@@ -696,21 +696,21 @@ __global__ void __launch_bounds__(256, 3) mask_ntt_fused_kernel(PrimeSet P, uint
   }
   // the value at slot x from its raw inputs (norm, share), which the loops
   // below load for several slots at once so that their latencies overlap
-  auto value = [&](uint32_t x, uint32_t nv, uint32_t sv) -> uint64_t {
+  auto value = [&](uint32_t x, uint32_t nv, uint32_t sv) -> uint32_t {   // (||p||^2 + r) mod t
     const uint64_t pos = k * N + x;
     uint64_t r;
     if (pos < n) r = sv == 0 ? 0 : t - sv;
     else r = mask_draw(P, pos0g + pos, mask_seed, qid);
-    const uint64_t m = norm_plus_mask_mod_t(P, nv, r);
-    return mul_shoup(m, dl, dls, q);
+    return (uint32_t)norm_plus_mask_mod_t(P, nv, r);
   };
+  const uint64_t dw = P.delta_w1[j], dws = P.delta_w1_shoup[j];
   const uint32_t* nk = norms + k * N;
   const uint64_t valid = n > k * N ? n - k * N : 0;      // slots of this block with a share
   const uint32_t r2 = logN & 3;  // leading radix-2 stages
   if (r2) {
-    // stage 0: distance N/2, twiddle psi^brv(1) for every pair; four pairs
-    // (eight slots) in flight per thread
-    const ulonglong2 w = __ldg(tw + 1);
+    // stage 0: distance N/2, twiddle psi^brv(1) for every pair, with Delta
+    // folded in: X = Delta v_x + (Delta psi^brv(1)) v_{x+N/2}, two products
+    // of 32-bit values per pair; four pairs (eight slots) in flight per thread
     for (uint32_t x0 = threadIdx.x; x0 < N / 2; x0 += 4 * blockDim.x) {
       uint32_t nv[8], sv[8];
 #pragma unroll
@@ -727,10 +727,10 @@ __global__ void __launch_bounds__(256, 3) mask_ntt_fused_kernel(PrimeSet P, uint
       for (int z = 0; z < 4; ++z) {
         const uint32_t x = x0 + z * blockDim.x;
         if (x < N / 2) {
-          uint64_t X = value(x, nv[z], sv[z]), Y = value(x + N / 2, nv[z + 4], sv[z + 4]);
-          fwd_bfly(X, Y, w.x, w.y, q, q2);
-          sa[SP(x)] = X;
-          sa[SP(x + N / 2)] = Y;
+          const uint64_t X = mul_shoup_u32(value(x, nv[z], sv[z]), dl, dls, q);
+          const uint64_t T = mul_shoup_u32_lazy(value(x + N / 2, nv[z + 4], sv[z + 4]), dw, dws, q);
+          sa[SP(x)] = X + T;               // below 3q
+          sa[SP(x + N / 2)] = X - T + q2;  // below 3q
         }
       }
     }
@@ -748,7 +748,7 @@ __global__ void __launch_bounds__(256, 3) mask_ntt_fused_kernel(PrimeSet P, uint
 #pragma unroll
       for (int z = 0; z < 8; ++z) {
         const uint32_t x = x0 + z * blockDim.x;
-        if (x < N) sa[SP(x)] = value(x, nv[z], sv[z]);
+        if (x < N) sa[SP(x)] = mul_shoup_u32(value(x, nv[z], sv[z]), dl, dls, q);
       }
     }
   }
