@@ -474,19 +474,8 @@ __global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(kClusterThreads, 1)
       tv[z] = __ldg(itw + (N >> (lt + 1)) + r * cnt + e);
     }
   }
-#pragma unroll
-  for (int z = 0; z < kDmax; ++z) {
-    const uint32_t x = 2 * (threadIdx.x + z * blockDim.x);
-    if (x < M) {
-      sa[SP(x)] = dv[z].x;
-      sa[SP(x + 1)] = dv[z].y;
-    }
-  }
-#pragma unroll
-  for (int z = 0; z < kTmax; ++z) {
-    const uint32_t f = threadIdx.x + z * blockDim.x;
-    if (f + 1 < M) tws[f] = tv[z];
-  }
+  // the mask terms first, so that their draws run while the loads above are
+  // in flight
   if (c == 0) {
     const uint64_t dl = P.delta[j], dls = P.delta_shoup[j], t = P.t;
     for (uint32_t u0 = 4 * threadIdx.x; u0 < M; u0 += 4 * blockDim.x) {
@@ -506,6 +495,19 @@ __global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(kClusterThreads, 1)
         shs[u0 + v] = (uint32_t)(rv == 0 ? 0 : t - rv);
       }
     }
+  }
+#pragma unroll
+  for (int z = 0; z < kDmax; ++z) {
+    const uint32_t x = 2 * (threadIdx.x + z * blockDim.x);
+    if (x < M) {
+      sa[SP(x)] = dv[z].x;
+      sa[SP(x + 1)] = dv[z].y;
+    }
+  }
+#pragma unroll
+  for (int z = 0; z < kTmax; ++z) {
+    const uint32_t f = threadIdx.x + z * blockDim.x;
+    if (f + 1 < M) tws[f] = tv[z];
   }
   __syncthreads();
   // stages of distance 2^lt < M on the quarter: radix-4 passes (stages lt and
