@@ -408,25 +408,36 @@ __device__ __forceinline__ void cl_sync_relaxed() {
   asm volatile("barrier.cluster.arrive.relaxed.aligned;\nbarrier.cluster.wait.aligned;" ::: "memory");
 }
 
-// 64-bit load from CTA `rank`'s copy of the shared-memory word at `local`
-__device__ __forceinline__ uint64_t ld_cluster(const uint64_t* local, uint32_t rank) {
+// Two consecutive 64-bit words (16-byte aligned) from CTA `rank`'s copy of
+// the shared memory at `local`; issued after the cluster barrier that made
+// them visible, so the compiler may schedule these loads freely.
+__device__ __forceinline__ ulonglong2 ld_cluster2(const uint64_t* local, uint32_t rank) {
   const uint32_t a = (uint32_t)__cvta_generic_to_shared(local);
   uint32_t ra;
-  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(ra) : "r"(a), "r"(rank));
-  uint64_t v;
-  asm volatile("ld.shared::cluster.u64 %0, [%1];" : "=l"(v) : "r"(ra) : "memory");
+  asm("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(ra) : "r"(a), "r"(rank));
+  ulonglong2 v;
+  asm("ld.shared::cluster.v2.u64 {%0, %1}, [%2];" : "=l"(v.x), "=l"(v.y) : "r"(ra));
   return v;
 }
 
+// bar.sync on barrier 1 for the data warps alone (warps 0 .. 7)
+__device__ __forceinline__ void data_warps_sync() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
+
 constexpr uint32_t kClusterIntt = 4;
-constexpr uint32_t kClusterThreads = 256;   // the prologue's per-thread load counts assume it
+// warps 0 .. 7 load the quarter and run its local stages while warps 8 .. 15
+// draw the mask terms (c = 0); all sixteen run the cross-quarter stages
+constexpr uint32_t kClusterThreads = 512, kClusterDataThreads = 256;
+
+// the cluster kernel's padded quarter keeps even pairs 16-byte aligned (two
+// spare words after every 16)
+__host__ __device__ __forceinline__ uint32_t SPC(uint32_t x) { return x + 2 * (x >> 4); }
 
 // shared-memory words of the cluster kernel for a ring of N: the padded
 // quarter, the quarter's twiddle pairs of every local stage (M - 1 pairs), the
 // mask term of each of its M positions and their 32-bit server shares
 __host__ __device__ __forceinline__ uint32_t cluster_intt_smem_words(uint32_t N) {
   const uint32_t M = N / kClusterIntt;
-  return ntt_smem_words(M) + 2 * (M - 1) + M + M / 2;
+  return M + M / 8 + 2 * (M - 1) + M + M / 2;
 }
 
 __global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(kClusterThreads, 1)
@@ -436,8 +447,8 @@ __global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(kClusterThreads, 1)
   extern __shared__ uint64_t sa[];
   const uint32_t N = P.N, L = P.L, logN = P.logN;
   const uint32_t M = N / kClusterIntt, logM = logN - 2;
-  ulonglong2* tws = reinterpret_cast<ulonglong2*>(sa + ntt_smem_words(M));  // 16-byte aligned: M + M/16 even
-  uint64_t* mval = sa + ntt_smem_words(M) + 2 * (M - 1);
+  ulonglong2* tws = reinterpret_cast<ulonglong2*>(sa + M + M / 8);   // 16-byte aligned: M + M/8 even
+  uint64_t* mval = sa + M + M / 8 + 2 * (M - 1);
   uint32_t* shs = reinterpret_cast<uint32_t*>(mval + M);
   const uint32_t r = cl_rank();
   const uint64_t poly = blockIdx.x / kClusterIntt;  // ((b K + k) 2 + c) L + j
@@ -448,41 +459,87 @@ __global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(kClusterThreads, 1)
   const uint64_t q = P.q[j], q2 = 2 * q, q4 = 4 * q;  // values stay below 4q
   const ulonglong2* itw = P.itw + (size_t)j * N;
   uint64_t* g = ct_out + poly * N;
+  const uint32_t tid = threadIdx.x;
 
-  // Everything this CTA reads from global memory is requested first: its
-  // quarter, the twiddles of its local stages (stage lt uses the M / 2^(lt+1)
-  // pairs from N / 2^(lt+1) + r M / 2^(lt+1), kept from word M - M / 2^lt of
-  // tws) and, for c = 0, the norms; the mask draws are computed while the
-  // loads are in flight.
-  // (all of a thread's loads are issued before any is stored: M <= 4096 gives
-  // at most 8 data pairs and 16 twiddle pairs per thread of 256)
-  constexpr int kDmax = 8, kTmax = 16;
-  ulonglong2 dv[kDmax], tv[kTmax];
+  if (tid < kClusterDataThreads) {
+    // the quarter and the twiddles of its local stages (stage lt uses the
+    // M / 2^(lt+1) pairs from N / 2^(lt+1) + r M / 2^(lt+1), kept from pair
+    // M - M / 2^lt of tws), two data pairs and four twiddle pairs per thread
+    // requested before any is stored
+    for (uint32_t base = 0; 2 * base < M / 2 || 4 * base + 1 < M; base += kClusterDataThreads) {
+      ulonglong2 dv[2], tv[4];
 #pragma unroll
-  for (int z = 0; z < kDmax; ++z) {
-    const uint32_t x = 2 * (threadIdx.x + z * blockDim.x);
-    dv[z] = x < M ? __ldg(reinterpret_cast<const ulonglong2*>(g + (uint64_t)r * M + x)) : make_ulonglong2(0, 0);
-  }
+      for (int z = 0; z < 2; ++z) {
+        const uint32_t x = 2 * (2 * base + tid + z * kClusterDataThreads);
+        dv[z] = x < M ? __ldg(reinterpret_cast<const ulonglong2*>(g + (uint64_t)r * M + x)) : make_ulonglong2(0, 0);
+      }
 #pragma unroll
-  for (int z = 0; z < kTmax; ++z) {
-    // flat index f of the stage-major twiddle copy: stage lt holds words
-    // [M - M / 2^lt, M - M / 2^(lt+1)), i.e. lt = log2 M - ceil(log2 (M - f))
-    const uint32_t f = threadIdx.x + z * blockDim.x;
-    if (f + 1 < M) {
-      const uint32_t lt = logM - (32 - __clz(M - f - 1));
-      const uint32_t cnt = M >> (lt + 1), e = f - (M - (M >> lt));
-      tv[z] = __ldg(itw + (N >> (lt + 1)) + r * cnt + e);
+      for (int z = 0; z < 4; ++z) {
+        // flat index f of the stage-major twiddle copy: stage lt holds pairs
+        // [M - M / 2^lt, M - M / 2^(lt+1)), i.e. lt = log2 M - ceil(log2 (M - f))
+        const uint32_t f = 4 * base + tid + z * kClusterDataThreads;
+        if (f + 1 < M) {
+          const uint32_t lt = logM - (32 - __clz(M - f - 1));
+          const uint32_t cnt = M >> (lt + 1), e = f - (M - (M >> lt));
+          tv[z] = __ldg(itw + (N >> (lt + 1)) + r * cnt + e);
+        }
+      }
+#pragma unroll
+      for (int z = 0; z < 2; ++z) {
+        const uint32_t x = 2 * (2 * base + tid + z * kClusterDataThreads);
+        if (x < M) *reinterpret_cast<ulonglong2*>(sa + SPC(x)) = dv[z];
+      }
+#pragma unroll
+      for (int z = 0; z < 4; ++z) {
+        const uint32_t f = 4 * base + tid + z * kClusterDataThreads;
+        if (f + 1 < M) tws[f] = tv[z];
+      }
     }
-  }
-  // the mask terms first, so that their draws run while the loads above are
-  // in flight
-  if (c == 0) {
+    data_warps_sync();
+    // stages of distance 2^lt < M on the quarter: radix-4 passes (stages lt
+    // and lt + 1), a radix-2 stage when log2 M is odd
+    uint32_t lt = 0;
+    for (; lt + 2 <= logM; lt += 2) {
+      const ulonglong2* t0 = tws + (M - (M >> lt));
+      const ulonglong2* t1 = tws + (M - (M >> (lt + 1)));
+      for (uint32_t th = tid; th < M / 4; th += kClusterDataThreads) {
+        const uint32_t gl = th >> lt, bl = th & ((1u << lt) - 1);
+        const uint32_t x0 = (gl << (lt + 2)) + bl;
+        uint64_t v[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) v[e] = sa[SPC(x0 + (e << lt))];
+        const ulonglong2 wa = t0[2 * gl], wb = t0[2 * gl + 1], wc = t1[gl];
+        inv_bfly4(v[0], v[1], wa.x, wa.y, q, q4);
+        inv_bfly4(v[2], v[3], wb.x, wb.y, q, q4);
+        inv_bfly4(v[0], v[2], wc.x, wc.y, q, q4);
+        inv_bfly4(v[1], v[3], wc.x, wc.y, q, q4);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) sa[SPC(x0 + (e << lt))] = v[e];
+      }
+      data_warps_sync();
+    }
+    if (lt < logM) {
+      const uint32_t t = 1u << lt;
+      const ulonglong2* t0 = tws + (M - (M >> lt));
+      for (uint32_t bf = tid; bf < M / 2; bf += kClusterDataThreads) {
+        const uint32_t i = bf >> lt, x = (i << (lt + 1)) + (bf & (t - 1));
+        uint64_t X = sa[SPC(x)], Y = sa[SPC(x + t)];
+        const ulonglong2 w = t0[i];
+        inv_bfly4(X, Y, w.x, w.y, q, q4);
+        sa[SPC(x)] = X;
+        sa[SPC(x + t)] = Y;
+      }
+    }
+  } else if (c == 0) {
+    // mask terms Delta ((||p||^2 + r) mod t) and the shares t - r of the
+    // quarter's positions, four per ChaCha20 block, meanwhile
     const uint64_t dl = P.delta[j], dls = P.delta_shoup[j], t = P.t;
-    for (uint32_t u0 = 4 * threadIdx.x; u0 < M; u0 += 4 * blockDim.x) {
+    const uint64_t qid = qids[b];
+    for (uint32_t u0 = 4 * (tid - kClusterDataThreads); u0 < M; u0 += 4 * (kClusterThreads - kClusterDataThreads)) {
       const uint64_t pos = k * N + (uint64_t)r * M + u0;
       const uint4 nv = __ldg(reinterpret_cast<const uint4*>(norms + pos));
       uint32_t blk[16];
-      chacha20_block(mask_seed, kPurposeMask, qids[b], (uint32_t)((pos0g + pos) / 4), blk);
+      chacha20_block(mask_seed, kPurposeMask, qid, (uint32_t)((pos0g + pos) / 4), blk);
       const uint32_t nvv[4] = {nv.x, nv.y, nv.z, nv.w};
 #pragma unroll
       for (int v = 0; v < 4; ++v) {
@@ -490,81 +547,31 @@ __global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(kClusterThreads, 1)
         draw_pair(blk, v, lo, hi);
         const uint64_t rv = mod_t128(lo, hi, P);
         mval[u0 + v] = mul_shoup_u32((uint32_t)norm_plus_mask_mod_t(P, nvv[v], rv), dl, dls, q);
-        // the share, written after the transform's stages (a global store
-        // here would hold up the release of the first cluster barrier)
         shs[u0 + v] = (uint32_t)(rv == 0 ? 0 : t - rv);
       }
     }
   }
-#pragma unroll
-  for (int z = 0; z < kDmax; ++z) {
-    const uint32_t x = 2 * (threadIdx.x + z * blockDim.x);
-    if (x < M) {
-      sa[SP(x)] = dv[z].x;
-      sa[SP(x + 1)] = dv[z].y;
-    }
-  }
-#pragma unroll
-  for (int z = 0; z < kTmax; ++z) {
-    const uint32_t f = threadIdx.x + z * blockDim.x;
-    if (f + 1 < M) tws[f] = tv[z];
-  }
-  __syncthreads();
-  // stages of distance 2^lt < M on the quarter: radix-4 passes (stages lt and
-  // lt + 1), a radix-2 stage when log2 M is odd
-  uint32_t lt = 0;
-  for (; lt + 2 <= logM; lt += 2) {
-    const ulonglong2* t0 = tws + (M - (M >> lt));
-    const ulonglong2* t1 = tws + (M - (M >> (lt + 1)));
-    for (uint32_t th = threadIdx.x; th < M / 4; th += blockDim.x) {
-      const uint32_t gl = th >> lt, bl = th & ((1u << lt) - 1);
-      const uint32_t x0 = (gl << (lt + 2)) + bl;
-      uint64_t v[4];
-#pragma unroll
-      for (int e = 0; e < 4; ++e) v[e] = sa[SP(x0 + (e << lt))];
-      const ulonglong2 wa = t0[2 * gl], wb = t0[2 * gl + 1], wc = t1[gl];
-      inv_bfly4(v[0], v[1], wa.x, wa.y, q, q4);
-      inv_bfly4(v[2], v[3], wb.x, wb.y, q, q4);
-      inv_bfly4(v[0], v[2], wc.x, wc.y, q, q4);
-      inv_bfly4(v[1], v[3], wc.x, wc.y, q, q4);
-#pragma unroll
-      for (int e = 0; e < 4; ++e) sa[SP(x0 + (e << lt))] = v[e];
-    }
-    __syncthreads();
-  }
-  if (lt < logM) {
-    const uint32_t t = 1u << lt;
-    const ulonglong2* t0 = tws + (M - (M >> lt));
-    for (uint32_t bf = threadIdx.x; bf < M / 2; bf += blockDim.x) {
-      const uint32_t i = bf >> lt, x = (i << (lt + 1)) + (bf & (t - 1));
-      uint64_t X = sa[SP(x)], Y = sa[SP(x + t)];
-      const ulonglong2 w = t0[i];
-      inv_bfly4(X, Y, w.x, w.y, q, q4);
-      sa[SP(x)] = X;
-      sa[SP(x + t)] = Y;
-    }
-  }
-  cl_sync();  // every quarter's local stages done and visible to the cluster
+  cl_sync();  // every quarter's local stages (and mask terms) done and visible to the cluster
 
   const ulonglong2 w2 = __ldg(itw + 2), w3 = __ldg(itw + 3);
   const uint64_t ni = P.n_inv[j], nis = P.n_inv_shoup[j];
   const uint64_t wl = P.last_inv[j], wls = P.last_inv_shoup[j];
-  for (uint32_t u0 = 4 * threadIdx.x; u0 < M; u0 += 4 * blockDim.x) {
-    uint64_t X[4][4];  // [quarter][offset]
+  for (uint32_t u0 = 2 * tid; u0 < M; u0 += 2 * kClusterThreads) {
+    ulonglong2 X[4];  // the four quarters' values at offsets u0, u0 + 1
 #pragma unroll
-    for (uint32_t qi = 0; qi < 4; ++qi)
+    for (uint32_t qi = 0; qi < 4; ++qi) X[qi] = ld_cluster2(sa + SPC(u0), qi);
+    uint64_t out[2];
 #pragma unroll
-      for (int v = 0; v < 4; ++v) X[qi][v] = ld_cluster(sa + SP(u0 + v), qi);
-    uint64_t out[4];
-#pragma unroll
-    for (int v = 0; v < 4; ++v) {
+    for (int v = 0; v < 2; ++v) {
+      const uint64_t x0 = v ? X[0].y : X[0].x, x1 = v ? X[1].y : X[1].x;
+      const uint64_t x2 = v ? X[2].y : X[2].x, x3 = v ? X[3].y : X[3].x;
       uint64_t A, B;
       if ((r & 1) == 0) {  // sum sides of the stage of distance M
-        A = csub(X[0][v] + X[1][v], q4);
-        B = csub(X[2][v] + X[3][v], q4);
+        A = csub(x0 + x1, q4);
+        B = csub(x2 + x3, q4);
       } else {             // difference sides
-        A = mul_shoup_lazy4(X[0][v] - X[1][v] + q4, w2.x, w2.y, q);
-        B = mul_shoup_lazy4(X[2][v] - X[3][v] + q4, w3.x, w3.y, q);
+        A = mul_shoup_lazy4(x0 - x1 + q4, w2.x, w2.y, q);
+        B = mul_shoup_lazy4(x2 - x3 + q4, w3.x, w3.y, q);
       }
       const uint64_t y = r < 2 ? mul_shoup_lazy4(csub(A + B, q4), ni, nis, q)
                                : mul_shoup_lazy4(A - B + q4, wl, wls, q);
@@ -573,12 +580,10 @@ __global__ void __cluster_dims__(4, 1, 1) __launch_bounds__(kClusterThreads, 1)
     }
     const uint32_t x = r * M + u0;
     *reinterpret_cast<ulonglong2*>(g + x) = make_ulonglong2(out[0], out[1]);
-    *reinterpret_cast<ulonglong2*>(g + x + 2) = make_ulonglong2(out[2], out[3]);
     if (c == 0 && j == 0) {
       const uint64_t pos = k * N + x;
-#pragma unroll
-      for (int v = 0; v < 4; ++v)
-        if (pos + v < n) srv_share[b * n + pos + v] = shs[u0 + v];
+      if (pos < n) srv_share[b * n + pos] = shs[u0];
+      if (pos + 1 < n) srv_share[b * n + pos + 1] = shs[u0 + 1];
     }
   }
   cl_sync_relaxed();  // the other CTAs have finished reading this CTA's quarter
