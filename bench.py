@@ -159,7 +159,7 @@ def _ntt_report(polys: int, N: int, ms: float, what: str) -> dict:
     gbs = 16.0 * N * polys / (ms * 1e-3) / 1e9
     return {"what": what, "polys": polys, "ms": ms, "polys_per_s": polys / (ms * 1e-3),
             "hbm_gbs": gbs, "hbm_frac": gbs / peak, "bound": "integer multiply pipe",
-            "pipes_from_ncu": {"fma_heavy_pct": 78.7, "alu_pct": 48.4,
+            "pipes_from_ncu": {"fma_heavy_pct": 77.2, "alu_pct": 48.2,
                                "source": "ncu of the fused INTT + mask kernel, 5,952 polynomials "
                                          "(profiles/intt_mask_kernel_linear_scan_n1M.md)"}}
 
