@@ -386,10 +386,12 @@ __global__ void __launch_bounds__(256, 3) intt_mask_short_kernel(PrimeSet P, uin
 //               X3' = (X2 - X3) w[3];
 //   stage N/2:  out0 = (X0' + X2') N^-1, out2 = (X0' - X2') psi^-brv(1) N^-1,
 //               out1, out3 likewise from X1', X3';
-// then, for c = 0, draws r itself (one ChaCha20 block per four positions, as
-// mask_share_kernel does), adds Delta ((||p||^2 + r) mod t) and writes the
-// server share from the j = 0 polynomial.  A second cluster barrier keeps
-// every CTA's shared memory alive until the others have read it.
+// then, for c = 0, adds Delta ((||p||^2 + r) mod t) and writes the server
+// share from the j = 0 polynomial.  The mask r is drawn in the kernel (one
+// ChaCha20 block per four positions, as mask_share_kernel does) by warps of
+// its own while the other warps run the local stages.  A second cluster
+// barrier keeps every CTA's shared memory alive until the others have read
+// it.
 // ------------------------------------------------------------------------
 __device__ __forceinline__ uint32_t cl_rank() {
   uint32_t r;
