@@ -276,7 +276,9 @@ int sanns_distances_gather_prepared(sanns_ctx *ctx, const sanns_gather_batch *ba
 
 /*
  * Launch variants of the MAC kernel (slots per lane, loads in flight, CTAs
- * per SM).  sanns_autotune_mac runs every variant `reps` times on the given
+ * per SM; one, "split_d_256x1", gives each work item a CTA whose warps split
+ * the d dimensions, for launches with few items).  sanns_autotune_mac runs
+ * every variant `reps` times on the given
  * inputs (writing ct_out_dev as sanns_distances_mac would), stores the
  * fastest in the context and returns its index (>= 0) or an error code;
  * ms_out (host, sanns_mac_variants() floats, may be NULL) receives the mean
