@@ -1241,7 +1241,7 @@ def run_alg4_section() -> dict:
     }
 
 
-SERVE = dict(rate=2000.0, duration=3.0, max_batch=128, slots=2, mac_sms=128, seed=21, sample_frac=0.02)
+SERVE = dict(rate=2000.0, duration=10.0, max_batch=128, slots=2, mac_sms=128, seed=21, sample_frac=0.02)
 
 
 def run_serving_section() -> dict:
@@ -1347,7 +1347,7 @@ def run_serving_section() -> dict:
             "sample_skipped_rejected": skipped,
         }
 
-    out = {"workload": "serving: Poisson 2000 q/s for 3 s over two resident databases "
+    out = {"workload": "serving: Poisson 2000 q/s for 10 s over two resident databases "
                        "(n=220,000 d=50 and n=1,000,000 d=128), batches up to 128, 2 slots, "
                        "per-query MAC on 128 SMs, memory admission (library scratch included), "
                        "each batch on the path its calibrated service times favour"}
