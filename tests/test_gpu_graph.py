@@ -71,3 +71,50 @@ def test_batched_step_replays_bit_exact(tile):
         torch.cuda.synchronize()
         S.sanns_device_status(ctx)
         assert torch.equal(out, ref_out) and torch.equal(srv, ref_srv)
+
+
+@pytest.mark.parametrize("cfg,n,cap", [((8192, 3, 60, 0, 7), 8192 * 40 + 11, 100),
+                                       ((256, 2, 40, 0, 5), 256 * 300 - 3, 0)])
+def test_pipelined_steps_in_one_graph_equal_eager(cfg, n, cap):
+    """Consecutive queries pipelined over two streams (query s's MAC on the
+    capture stream, query s-1's INTT + mask on a side stream, responses
+    double-buffered, the MAC's grid capped) captured into one graph, as the
+    benchmark times them: after each replay the two buffers hold the last two
+    steps, equal to those queries run alone."""
+    Q = 6
+    ctx, db, ct, qids = _setup(cfg, n, Q, 21)
+    K, L, N = db.K, cfg[1], cfg[0]
+    outs = [torch.empty((1, K, 2, L, N), dtype=torch.uint64, device="cuda") for _ in range(2)]
+    srvs = [torch.empty((1, n), dtype=torch.uint32, device="cuda") for _ in range(2)]
+    want = [S.sanns_distances(ctx, db, ct[s:s + 1], 5, qids[s:s + 1]) for s in range(Q)]
+    S.sanns_set_mac_sms(ctx, cap)
+    cap_st, side = torch.cuda.Stream(), torch.cuda.Stream()
+    cap_st.wait_stream(torch.cuda.current_stream())
+    # one eager pass first (warm-up, as the benchmark does)
+    for s in range(2):
+        S.sanns_distances(ctx, db, ct[s:s + 1], 5, qids[s:s + 1], outs[s % 2], srvs[s % 2], stream=cap_st)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=cap_st):
+        fin = [None] * Q
+        for s in range(Q):
+            u = s % 2
+            if s >= 2:
+                cap_st.wait_event(fin[s - 2])
+            S.sanns_distances_mac(ctx, db, ct[s:s + 1], outs[u], stream=cap_st)
+            me = torch.cuda.Event()
+            me.record(cap_st)
+            side.wait_event(me)
+            S.sanns_distances_finish(ctx, db, outs[u], 5, qids[s:s + 1], srvs[u], stream=side)
+            fin[s] = torch.cuda.Event()
+            fin[s].record(side)
+        cap_st.wait_event(fin[Q - 1])
+    S.sanns_set_mac_sms(ctx, 0)
+    for _ in range(2):
+        for o in outs:
+            o.zero_()
+        g.replay()
+        torch.cuda.synchronize()
+        S.sanns_device_status(ctx)
+        for s in (Q - 2, Q - 1):   # the buffers hold the last two steps
+            assert torch.equal(outs[s % 2], want[s][0]) and torch.equal(srvs[s % 2], want[s][1]), s
