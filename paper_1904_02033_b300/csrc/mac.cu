@@ -96,8 +96,18 @@ __global__ void __launch_bounds__(THREADS, MINB) mac_kernel(PrimeSet P, MacArgs 
   const uint32_t N = P.N, L = P.L, d = A.d;
   const uint32_t tiles = N / TILE;
   const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const uint64_t w_begin = blockIdx.x * A.total / gridDim.x;
-  const uint64_t w_end = (blockIdx.x + 1) * A.total / gridDim.x;
+  // Work is split into rounds: a run of K blocks (one tile) is ceil(K / WARPS)
+  // rounds of at most WARPS blocks, one per warp.  Each CTA takes an even
+  // share of the rounds, so its item range starts and ends on round
+  // boundaries and no run is cut into pieces that each pay a partial round.
+  const uint64_t rounds_per_run = (A.K + WARPS - 1) / WARPS;
+  const uint64_t rounds = A.total / A.K * rounds_per_run;
+  auto item_of_round = [&](uint64_t r) -> uint64_t {
+    const uint64_t in_run = (r % rounds_per_run) * WARPS;
+    return r / rounds_per_run * A.K + (in_run < A.K ? in_run : A.K);
+  };
+  const uint64_t w_begin = item_of_round(blockIdx.x * rounds / gridDim.x);
+  const uint64_t w_end = item_of_round((blockIdx.x + 1) * rounds / gridDim.x);
 
   uint64_t w = w_begin;
   while (w < w_end) {
