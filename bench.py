@@ -126,7 +126,7 @@ def _roofline_bytes(W) -> dict:
 # dram__bytes_write.sum.  The query ciphertext is read once per launch; the
 # rest grows with the blocks, so a full launch's traffic is that rest scaled
 # by the block count plus the query ciphertext.
-MAC_CAPTURE = dict(K=25, d=128, N=8192, L=3, dram_bytes=680_013_312 + 3_469_568)
+MAC_CAPTURE = dict(K=25, d=128, N=8192, L=3, dram_bytes=679_687_680 + 2_998_272)
 
 
 def _mac_traffic(rb: dict, W) -> float | None:
