@@ -1462,6 +1462,18 @@ def cpu_baseline(quick: bool = False) -> dict:
                       f"MAC + INTT + mask, {dt:.1f} s"}
 
 
+def _cpu_model() -> str:
+    """The host CPU's model name (from /proc/cpuinfo), for the baseline's record."""
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
 def cpu_baseline_all_cores(quick: bool = False) -> dict:
     """Time the oracle, as it stands, on every host core (at most 64): one
     thread per core, each running the single-threaded C loops (ctypes releases
@@ -1499,6 +1511,7 @@ def cpu_baseline_all_cores(quick: bool = False) -> dict:
         spans = list(ex.map(work, range(T)))
     dt = max(e for _, e in spans) - min(b for b, _ in spans)
     return {"value": npts * nq / dt, "unit": UNIT, "cores": T, "kind": "oracle",
+            "cpu": _cpu_model(), "nproc": os.cpu_count(),
             "sample": f"{T} threads x {bpt} blocks of 8192 points each, {nq} queries "
                       f"(d=128, N=8192, L=3): MAC + INTT + mask, {dt:.1f} s"}
 
@@ -1543,7 +1556,7 @@ def run_reference(args) -> None:
                                "64-component Gaussian mixture (sigma 20); BFV N=8192, three "
                                "60-bit primes, t=16957441 (CPU oracle on a bounded sample)"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": T, "kind": "oracle",
-                         "sample": sample},
+                         "cpu": _cpu_model(), "nproc": os.cpu_count(), "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
