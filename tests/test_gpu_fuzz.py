@@ -1,0 +1,71 @@
+"""Seeded random configurations through the whole per-query step, each
+against the oracle: ring size, prime count and size, dimension, database
+size (ragged), queries per call, MAC launch variant and response form
+(full modulus or switched down to q_0) are drawn from a fixed stream, so the
+epilogue kernels chosen by launch size (the cluster, short and fused
+INTT + mask kernels) and every MAC variant meet shapes the hand-written
+cases do not."""
+import numpy as np
+import pytest
+import torch
+
+from oracle.bfv import Oracle
+from paper_1904_02033_b300 import inputs
+from paper_1904_02033_b300 import sanns as S
+
+pytestmark = pytest.mark.gpu
+
+CASES = 40
+
+
+def _case(i):
+    rnd = np.random.default_rng(1000 + i)
+    N = int(rnd.choice([256, 1024, 2048, 4096]))
+    L = int(rnd.integers(2, 5))
+    bits = int(rnd.choice([50, 55, 60]))
+    d = int(rnd.integers(1, 41))
+    n = int(rnd.integers(1, 6 * N + 1))
+    B = int(rnd.integers(1, 7))
+    switched = bool(rnd.random() < 0.4)
+    return (N, L, bits, 0, d), n, B, switched, int(rnd.integers(0, 1 << 30))
+
+
+@pytest.mark.parametrize("i", range(CASES))
+def test_random_configuration_matches_oracle(i):
+    cfg, n, B, switched, seed = _case(i)
+    N, L, bits, rule, d = cfg
+    ctx = S.sanns_ctx_create(*cfg)
+    variant = seed % len(S.sanns_mac_variants())
+    S.sanns_set_mac_variant(ctx, variant)
+    coords = inputs.uniform_coords(n, d, seed)
+    coords[: min(n, 3)] = 255
+    perm = inputs.permutation(n, seed + 1)
+    q = inputs.uniform_coords(B, d, seed + 2)
+    qids = np.arange(7, 7 + B, dtype=np.uint64) * 1009
+    sk = S.sanns_keygen(ctx, seed + 3)
+    db = S.sanns_encode_db(ctx, torch.from_numpy(coords).cuda(), torch.from_numpy(perm).cuda())
+    ct_in = S.sanns_encrypt_query(ctx, sk, torch.from_numpy(q).cuda(), seed + 4,
+                                  torch.from_numpy(qids).cuda())
+    if switched:
+        S.sanns_set_response_primes(ctx, 1)
+    out, srv = S.sanns_distances(ctx, db, ct_in, seed + 5, torch.from_numpy(qids).cuda())
+    resp = S.sanns_copy_responses(ctx, out) if switched else out
+    cli = S.sanns_decrypt_shares(ctx, sk, resp, n, torch.from_numpy(q).cuda())
+    S.sanns_device_status(ctx)
+    O = Oracle(*cfg)
+    s_, _ = O.keygen(seed + 3)
+    ct_np, resp_np, srv_np, cli_np = (x.cpu().numpy() for x in (ct_in, resp, srv, cli))
+    name = (cfg, n, B, switched, S.sanns_mac_variants()[variant])
+    for b in range(B):
+        full, want_srv = O.distances(ct_np[b], coords, perm, seed + 5, int(qids[b]))
+        assert np.array_equal(srv_np[b], want_srv), (name, b)
+        if switched:
+            want = O.mod_switch(full)
+            assert np.array_equal(resp_np[b, :, :, 0], want), (name, b)
+            want_cli = O.decrypt_shares_switched(want, s_, q[b], n)
+        else:
+            assert np.array_equal(resp_np[b], full), (name, b)
+            want_cli = O.decrypt_shares(full, s_, q[b], n)
+        assert np.array_equal(cli_np[b], want_cli), (name, b)
+        brute = np.sum((coords[perm].astype(np.int64) - q[b].astype(np.int64)) ** 2, axis=1)
+        assert np.array_equal((cli_np[b].astype(np.int64) + srv_np[b]) % O.t, brute), (name, b)
