@@ -69,3 +69,42 @@ def test_random_configuration_matches_oracle(i):
         assert np.array_equal(cli_np[b], want_cli), (name, b)
         brute = np.sum((coords[perm].astype(np.int64) - q[b].astype(np.int64)) ** 2, axis=1)
         assert np.array_equal((cli_np[b].astype(np.int64) + srv_np[b]) % O.t, brute), (name, b)
+
+
+@pytest.mark.parametrize("i", range(16))
+def test_random_batched_configuration_equals_per_query_and_oracle(i):
+    """The tensor-core path on seeded random shapes (ring, primes, d up to
+    the exactness limit 128, ragged database, 1..40 queries, tile shape,
+    scratch cap): every query equals the per-query path, and the first
+    query's blocks equal the oracle."""
+    rnd = np.random.default_rng(5000 + i)
+    N = int(rnd.choice([256, 512, 1024]))
+    L = int(rnd.integers(2, 5))
+    cfg = (N, L, int(rnd.choice([50, 60])), 0, int(rnd.integers(1, 129)))
+    d = cfg[4]
+    n = int(rnd.integers(1, 300 * 256 + 1))   # up to 300 blocks at N = 256 (several database tiles)
+    B = int(rnd.integers(1, 41))
+    tile = int(rnd.integers(0, 9))
+    scratch = int(rnd.choice([2, 8, 4096]))
+    seed = int(rnd.integers(0, 1 << 30))
+    ctx = S.sanns_ctx_create(*cfg)
+    coords = inputs.uniform_coords(n, d, seed)
+    perm = inputs.permutation(n, seed + 1)
+    q = inputs.uniform_coords(B, d, seed + 2)
+    qids = np.arange(B, dtype=np.uint64) * 31 + 5
+    sk = S.sanns_keygen(ctx, seed + 3)
+    db = S.sanns_encode_db(ctx, torch.from_numpy(coords).cuda(), torch.from_numpy(perm).cuda())
+    S.sanns_db_prepare_batched(ctx, db)
+    ct_in = S.sanns_encrypt_query(ctx, sk, torch.from_numpy(q).cuda(), seed + 4,
+                                  torch.from_numpy(qids).cuda())
+    S.sanns_batched_tune(ctx, scratch_mib=scratch, tile=tile)
+    qd = torch.from_numpy(qids).cuda()
+    out_b, srv_b = S.sanns_distances_batched(ctx, db, ct_in, seed + 5, qd)
+    S.sanns_device_status(ctx)
+    out_p, srv_p = S.sanns_distances(ctx, db, ct_in, seed + 5, qd)
+    name = (cfg, n, B, tile, scratch)
+    assert torch.equal(out_b, out_p) and torch.equal(srv_b, srv_p), name
+    O = Oracle(*cfg)
+    full, want_srv = O.distances(ct_in[0].cpu().numpy(), coords, perm, seed + 5, int(qids[0]))
+    assert np.array_equal(out_b[0].cpu().numpy(), full), name
+    assert np.array_equal(srv_b[0].cpu().numpy(), want_srv), name
