@@ -108,3 +108,77 @@ def test_random_batched_configuration_equals_per_query_and_oracle(i):
     full, want_srv = O.distances(ct_in[0].cpu().numpy(), coords, perm, seed + 5, int(qids[0]))
     assert np.array_equal(out_b[0].cpu().numpy(), full), name
     assert np.array_equal(srv_b[0].cpu().numpy(), want_srv), name
+
+
+def _gathered(offsets, members, probes):
+    parts = [members[offsets[c]:offsets[c + 1]] for c in probes]
+    return np.concatenate(parts).astype(np.uint32) if parts else np.zeros(0, np.uint32)
+
+
+@pytest.mark.parametrize("i", range(16))
+def test_random_gather_matches_oracle(i):
+    """The clustering gather on seeded random clusterings: ring, primes,
+    dimension, skewed cluster sizes (some empty), queries and probes per
+    query, with slot encoding, NTT-form or switched responses and circuit
+    privacy drawn at random; each query's responses and shares equal the
+    oracle's linear scan of its gathered list."""
+    rnd = np.random.default_rng(9000 + i)
+    N = int(rnd.choice([256, 1024, 4096]))
+    L = int(rnd.integers(2, 4))
+    cfg = (N, L, 60, 0, int(rnd.integers(1, 33)))
+    d = cfg[4]
+    n = int(rnd.integers(50, 4 * N + 1))
+    C = int(rnd.integers(2, 40))
+    B = int(rnd.integers(1, 7))
+    P = int(rnd.integers(1, C + 1))
+    slots = bool(rnd.random() < 0.25)
+    ntt = bool(rnd.random() < 0.25)
+    switched = (not ntt) and bool(rnd.random() < 0.3)
+    F = int(rnd.choice([0, 0, 0, 60]))
+    seed = int(rnd.integers(0, 1 << 30))
+    coords = inputs.uniform_coords(n, d, seed)
+    assign = rnd.choice(C, size=n, p=inputs.zipf_weights(C, 1.1))
+    offsets, members = inputs.clusters_csr(assign, C)
+    probes = np.stack([rnd.permutation(C)[:P] for _ in range(B)]).astype(np.uint32)
+    q = inputs.uniform_coords(B, d, seed + 1)
+    qids = np.arange(B, dtype=np.uint64) * 7 + 3
+    ctx = S.sanns_ctx_create(*cfg)
+    sk = S.sanns_keygen(ctx, seed + 2)
+    S.sanns_set_encoding(ctx, slots)
+    S.sanns_set_response_form(ctx, ntt)
+    pk = None
+    if F:
+        pk_d = S.sanns_public_key(ctx, sk, seed + 3)
+        S.sanns_set_circuit_privacy(ctx, pk_d, F)
+        pk = pk_d.cpu().numpy()
+    if switched:
+        S.sanns_set_response_primes(ctx, 1)
+    cl = S.sanns_clusters_create(ctx, torch.from_numpy(coords).cuda(), offsets,
+                                 torch.from_numpy(members).cuda())
+    ct_in = S.sanns_encrypt_query(ctx, sk, torch.from_numpy(q).cuda(), seed + 4,
+                                  torch.from_numpy(qids).cuda())
+    ct_out, srv, ids, n_b, k_b = S.sanns_distances_gather(ctx, cl, ct_in, probes, seed + 5,
+                                                          torch.from_numpy(qids).cuda())
+    S.sanns_device_status(ctx)
+    W = int(k_b.sum())
+    if switched and W:
+        ct_out = S.sanns_copy_responses(ctx, ct_out[:W].reshape(1, W, 2, L, N)).reshape(W, 2, N)
+    ct_out, srv, ids, ct_np = ct_out.cpu().numpy(), srv.cpu().numpy(), ids.cpu().numpy(), ct_in.cpu().numpy()
+    O = Oracle(*cfg)
+    name = (cfg, n, C, B, P, slots, ntt, switched, F)
+    kb0 = nb0 = 0
+    for b in range(B):
+        g = _gathered(offsets, members, probes[b])
+        assert int(n_b[b]) == len(g) and int(k_b[b]) == -(-len(g) // N), name
+        assert np.array_equal(ids[nb0:nb0 + len(g)], g), name
+        if len(g):
+            want, want_srv = O.distances(ct_np[b], coords, g, seed + 5, int(qids[b]), pk=pk, flood_bits=F,
+                                         slots=slots)
+            if ntt:
+                want = O.to_ntt_form(want)
+            elif switched:
+                want = O.mod_switch(want)
+            assert np.array_equal(ct_out[kb0:kb0 + int(k_b[b])], want), (name, b)
+            assert np.array_equal(srv[nb0:nb0 + len(g)], want_srv), (name, b)
+        kb0 += int(k_b[b])
+        nb0 += len(g)
